@@ -1,0 +1,323 @@
+"""Benchmark of the filament-fluid step on GB300.
+
+One JSON line on rank 0.  Default workload: the particle-count sweep's target
+point, 2^22 beads as 64-bead filaments on a 4096 x 4096 periodic grid (0.25
+bead per cell), FP32.  A "step" is one full time step (drive, PBD, binning,
+steric deposit, Gaussian filter, force + spread, LBM, interpolation and
+advance) of that world.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--impl ours|reference] [--no-cpu-baseline]
+
+value      particle-steps/s of mc_step replaying its CUDA graph, inputs
+           resident in HBM (the world's state, 1.8 GB, is larger than L2).
+e2e        the same metric through the C ABI from host buffers: world
+           creation from host arrays (H2D), K steps, state read-back (D2H).
+roofline   the LBM kernel (the dominant one): algorithmic bytes per launch
+           (88 B per cell) / its CUDA-event duration, against the measured
+           HBM copy bandwidth.
+cpu_baseline  the FP64 oracle on the host cores, one step of a 1/16 sample
+           of the workload (2^18 beads on 1024^2 at the same density).
+With --impl reference the oracle itself is the timed arm.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+STAGES = ["pbd", "bin_scan", "bin_scatter", "deposit", "blur", "force_spread", "lbm", "interp_advance"]
+LBM_BYTES_PER_CELL = 88          # read f 36 + F 8, write f' 36 + u 8
+STEP_BYTES_PER_CELL = 112        # grid traffic per step of the minimal fused form
+STEP_BYTES_PER_BEAD = 32
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--workload", default="c3_22", help="c3_<log2 N> (default c3_22) or c2")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stage-steps", type=int, default=50, help="steps of the per-stage timing pass")
+    return ap.parse_args()
+
+
+def make_spec(name: str, seed: int):
+    from paper_2607_02954_gb300 import synth
+    if name == "c2":
+        return synth.world_c2(seed), "c2: 512^2 grid, 4096 x 64 beads (262,144), FP32"
+    if name.startswith("c3_"):
+        n = int(name.split("_")[1])
+        side = synth.c3_side(n)
+        return synth.world_c3(n, seed), f"c3: 2^{n} beads as 64-bead filaments on {side}^2, FP32"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def sample_spec(name: str, seed: int):
+    """Bounded sample of the workload for the CPU oracle: same density and
+    filament shape, 1/16 of the area for the big sweep points."""
+    from paper_2607_02954_gb300 import synth
+    if name.startswith("c3_"):
+        n = int(name.split("_")[1])
+        side = synth.c3_side(n)
+        density = (2 ** n) / float(side * side)
+        s_side = max(256, side // 4)
+        s_n = int(round(density * s_side * s_side))
+        return synth.world_rows(s_side, s_n, seed), f"one oracle step of {s_n} beads on {s_side}^2 (same density)"
+    spec, _ = make_spec(name, seed)
+    return spec, f"one oracle step of the full {name} world"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sms:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def run_oracle_sample(spec, min_seconds: float, max_steps: int = 1000):
+    """Times oracle steps on the sample until min_seconds of CPU work."""
+    import torch
+    import oracle as O
+    ow = O.World(spec)
+    st = ow.initial_state()
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        st, _ = O.step(ow, st)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds or n >= max_steps:
+            break
+    return spec.N * n / el, n, el, torch.get_num_threads()
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    spec, desc = sample_spec(args.workload, 1)
+    import torch
+    import oracle as O
+    ow = O.World(spec)
+    st = ow.initial_state()
+    for _ in range(args.warmup):
+        st, _ = O.step(ow, st)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st, _ = O.step(ow, st)
+    el = time.perf_counter() - t0
+    v = spec.N * args.steps / el
+    line = {"impl": "reference", "metric": "particle-steps/s", "value": v, "unit": "particle-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "sample": desc},
+            "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": torch.get_num_threads(),
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2607_02954_gb300 import World, _lib
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_2607_02954_gb300.build import build
+        build()
+    lib = _lib.load()
+
+    spec, desc = make_spec(args.workload, seed=rank)
+    N, C = spec.N, spec.H * spec.W
+    world = World(spec, device=True)
+    stream = torch.cuda.current_stream()
+    sh = ctypes.c_void_p(stream.cuda_stream)
+
+    # warm-up (includes the one-time graph capture)
+    world.step(max(args.warmup, 16))
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region: K steps replayed from the CUDA graph -------------
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        world.step(args.steps)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    world.check()
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = ws * N * args.steps / (ms_max * 1e-3)
+
+    # ---- per-stage CUDA-event timing on the launching stream ------------
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)] for _ in range(args.stage_steps)]
+    for k in range(args.stage_steps):
+        evs[k][0].record(stream)
+        for s_i in range(len(STAGES)):
+            _lib.check(lib.mc_step_stage(world.handle, s_i, sh))
+            evs[k][s_i + 1].record(stream)
+    torch.cuda.synchronize()
+    stage_ms = {nm: sum(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.stage_steps)) / args.stage_steps
+                for i, nm in enumerate(STAGES)}
+    hbm_peak, peak_kind = measured_peaks()
+    lbm_bytes = LBM_BYTES_PER_CELL * C
+    lbm_gbs = lbm_bytes / (stage_ms["lbm"] * 1e-3) / 1e9
+    step_bytes = STEP_BYTES_PER_CELL * C + STEP_BYTES_PER_BEAD * N
+    step_gbs = step_bytes / (ms_max / args.steps * 1e-3) / 1e9
+    world.close()
+
+    # ---- end to end through the C ABI from host buffers -----------------
+    e2e_steps = max(16, min(args.steps, 200))
+    h2d = sum(np.asarray(getattr(spec, k)).nbytes for k in
+              ("x", "y", "theta", "L_rest", "theta0", "drive_amp", "drive_freq", "drive_phase", "fil_off"))
+    d2h = N * 4 * 4   # x, y, disp (2 floats)
+    barrier()
+    t0 = time.perf_counter()
+    w2 = World(spec)                      # host arrays -> device
+    w2.step(e2e_steps)
+    st = w2.state()                       # device -> host (synchronizes)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    w2.close()
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_val = ws * N * e2e_steps / float(e2e_t.item())
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    line = {
+        "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "grid": [spec.H, spec.W], "beads": N,
+                   "filaments": spec.n_fil, "parallelism": f"replicas x{ws}" if ws > 1 else "single world",
+                   "l2": "state 1.8 GB > L2: no flush needed" if C >= 4096 * 4096 else "state may fit in L2; per-step timing includes no flush"},
+        "e2e": {"value": e2e_val, "unit": "particle-steps/s", "steps": e2e_steps,
+                "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps},
+        "gpu_launches": args.steps * len(STAGES),
+        "roofline": {"bound": "hbm", "kernel": "k_lbm", "achieved": lbm_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": lbm_gbs / hbm_peak, "peak_kind": peak_kind, "traffic": None,
+                     "algorithmic_bytes_per_launch": lbm_bytes, "launch_ms": stage_ms["lbm"]},
+        "step_roofline": {"achieved": step_gbs, "frac": step_gbs / hbm_peak, "unit": "GB/s",
+                          "algorithmic_bytes_per_step": step_bytes},
+        "stage_ms": stage_ms,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        sspec, sdesc = sample_spec(args.workload, 1)
+        v, n, el, cores = run_oracle_sample(sspec, 10.0)
+        line["cpu_baseline"] = {"value": v, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{sdesc}; {n} step(s) in {el:.1f} s"}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

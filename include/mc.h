@@ -1,0 +1,203 @@
+/*
+ * mc.h - C ABI of the GB300 filament-fluid step library (libmc.so).
+ *
+ * The library advances "worlds" of the Microcosmos model (arXiv 2607.02954):
+ * elastic bead chains (filaments) immersed in a 2D periodic viscous fluid.
+ * One time step (Methods and Fields sections, Fluid-filament Interaction):
+ *   a1 rest-angle drive      theta_rest,j(t) = theta0_j + A_j sin(2 pi (freq_j t + phase_j))
+ *   a2 cell / bin indexing   counting sort of beads by 32x32-cell tile
+ *   a3 PBD                   n_pbd x (bending pass Eq. 1, position pass Eqs. 2-4);
+ *                            elastic force F_el = kappa (x_hat - X) / dt
+ *   a4 steric deposit        rho_s(c) = sum_i delta_h(c - X_i)
+ *   a5 Gaussian filter       rho_bar = G_sigma * rho_s (periodic, separable)
+ *   a6 force + spread        F_s,i = -k_rep sum_c delta_h(c - X_i) grad rho_bar(c)
+ *                            F(c)  = sum_i delta_h(c - X_i) (F_el,i + F_s,i)
+ *   a7 D2Q9 TRT LBM          collide (Guo forcing) + periodic streaming -> f, u
+ *   a8 IB interpolation      U_i = sum_c delta_h(c - X_i) u(c);  X += dt U (wrapped)
+ * delta_h is Peskin's 4-point kernel.  All device arithmetic is FP32.
+ *
+ * Conventions shared by every call:
+ *  - Every function returns mc_status.  MC_OK = 0.  On failure nothing is
+ *    enqueued and mc_last_error() describes the problem (thread-local text).
+ *    Nothing aborts the process.
+ *  - Streams are CUDA streams (cudaStream_t, passed as void*); NULL means the
+ *    legacy default stream.  Calls that take a stream are asynchronous on it
+ *    unless stated otherwise.
+ *  - Arrays passed in are copied; the caller keeps ownership.  mem_kind says
+ *    whether a pointer argument is host (MC_MEM_HOST) or device (MC_MEM_DEVICE)
+ *    memory.  Host input arrays may be reused as soon as the call returns.
+ *  - Grids are row-major [y][x] with W cells per row; population arrays are
+ *    [9][H][W] in the D2Q9 order c = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),
+ *    (-1,1),(-1,-1),(1,-1).
+ *  - Filaments are linear chains: filament f owns beads fil_off[f] ..
+ *    fil_off[f+1]-1 (at least 2 beads); it owns B_f - 1 edges and B_f - 2
+ *    joints, numbered consecutively across filaments (edge e joins beads
+ *    (a, a+1) of one filament; joint j sits between two consecutive edges).
+ *    N = fil_off[n_fil], E = N - n_fil, J = N - 2 n_fil.
+ */
+#ifndef MC_H
+#define MC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MC_ABI_VERSION 1
+
+typedef enum mc_status {
+  MC_OK = 0,
+  MC_ERR_INVALID_ARG = 1,  /* a size, pointer or value failed validation */
+  MC_ERR_OOM = 2,          /* device or host allocation failed */
+  MC_ERR_CUDA = 3,         /* a CUDA runtime call failed (text in mc_last_error) */
+  MC_ERR_TIMEOUT = 4,      /* a bounded wait gave up */
+  MC_ERR_UNSTABLE = 5,     /* the velocity watchdog tripped (|U| too large or not finite) */
+  MC_ERR_BUSY = 6,         /* result not ready yet / queue full */
+  MC_ERR_NOT_FOUND = 7     /* unknown ticket or handle */
+} mc_status;
+
+typedef enum mc_mem_kind { MC_MEM_HOST = 0, MC_MEM_DEVICE = 1 } mc_mem_kind;
+
+/* World constants.  The paper names these quantities (Methods: k_bend,
+ * k_shear, k_stretch per Eqs. 1-4; Fields: LBM relaxation tau, Gaussian
+ * filter of the steric density) but fixes none of their values.
+ *   nu       kinematic viscosity, tau+ = 3 nu + 1/2 (must give tau+ > 1/2)
+ *   dt       bead advance step (the lattice time step is 1)
+ *   Lambda   TRT magic parameter, tau- = 1/2 + Lambda / (tau+ - 1/2)
+ *   kappa    penalty stiffness turning the PBD correction into a force
+ *   k_bend, k_stretch, k_shear   PBD stiffnesses (Eqs. 1-4), in [0, 1]
+ *   k_rep    steric repulsion strength
+ *   sigma    Gaussian filter width in cells, 0 < sigma <= 2 (taps R = ceil(4 sigma))
+ *   orient   1: the position pass also turns the edge frame toward the edge
+ *            (Gauss-Newton step on |v - L d(theta)|^2); 0: positions only
+ *   n_pbd    PBD iterations per step, 0 <= n_pbd <= 64 */
+typedef struct mc_params {
+  float nu, dt, Lambda, kappa, k_bend, k_stretch, k_shear, k_rep, sigma, orient;
+  int n_pbd;
+} mc_params;
+
+/* The paper's statement of one world (Methods: filaments as graphs with
+ * per-edge orientation, rest length and rest angle; Fields: the grid).
+ *   H, W        grid size, multiples of 8, 8 <= H, W <= 8192
+ *   n_fil       number of filaments (>= 0), fil_off [n_fil + 1]
+ *   x, y        [N] bead positions (any finite value; wrapped into the box)
+ *   theta       [E] edge orientation angles (radians, not wrapped)
+ *   L_rest      [E] rest lengths (> 0)
+ *   theta0      [J] static part of the rest angles
+ *   drive_amp, drive_freq, drive_phase  [J] rest-angle drive: amplitude
+ *               (rad), frequency (cycles per step), phase (cycles)
+ *   f0          [9][H][W] initial populations minus the rest weights w_i
+ *               (pre-collision, as returned by mc_world_get_state); NULL =
+ *               fluid at rest (f = w_i)
+ *   t0          initial step counter (0 <= t0 < 2^24)
+ *   p           constants
+ *   mem_kind    where the array pointers live (fil_off always host memory) */
+typedef struct mc_world_desc {
+  int H, W;
+  int n_fil;
+  const int* fil_off;
+  const float* x;
+  const float* y;
+  const float* theta;
+  const float* L_rest;
+  const float* theta0;
+  const float* drive_amp;
+  const float* drive_freq;
+  const float* drive_phase;
+  const float* f0;
+  int64_t t0;
+  mc_params p;
+  int mem_kind;
+} mc_world_desc;
+
+typedef struct mc_world mc_world;
+
+typedef struct mc_world_info {
+  int H, W, n_fil, N, E, J;
+  int tile, n_bins;      /* binning tile edge (cells) and number of bins */
+  int64_t t;             /* step counter after all enqueued steps */
+  size_t device_bytes;   /* device memory held by the world */
+} mc_world_info;
+
+/* Fills p with the library's default constants. */
+mc_status mc_params_default(mc_params* p);
+
+/* Creates a world: validates the description, allocates its device memory
+ * (one stream-ordered allocation on `stream`, freed by mc_world_destroy),
+ * copies the inputs and enqueues the set-up kernels on `stream`.
+ * Errors: MC_ERR_INVALID_ARG (sizes, non-finite values, filaments with fewer
+ * than 2 beads, tau+ <= 1/2), MC_ERR_OOM, MC_ERR_CUDA. */
+mc_status mc_world_create(const mc_world_desc* desc, void* stream, mc_world** out);
+
+/* Releases a world.  Work already enqueued on the world must be complete or
+ * ordered before the stream the world was created on. */
+mc_status mc_world_destroy(mc_world* w);
+
+mc_status mc_world_info_get(const mc_world* w, mc_world_info* out);
+
+/* Advances one world by n_steps >= 0 time steps (a1..a8 each), enqueued on
+ * `stream`.  Steps are replayed from a captured CUDA graph.  Asynchronous:
+ * the velocity watchdog result is read with mc_world_check. */
+mc_status mc_step(mc_world* w, int n_steps, void* stream);
+
+/* Advances n_worlds distinct worlds of any sizes by n_steps each, every
+ * kernel covering all worlds at once (one launch per stage per step).
+ * Results are bitwise identical to advancing each world alone with mc_step.
+ * worlds is a host array of n_worlds distinct handles. */
+mc_status mc_step_batched(mc_world* const* worlds, int n_worlds, int n_steps, void* stream);
+
+/* Enqueues one stage of the next step on `stream` (for per-stage timing).
+ * Stages: 0 drive + PBD + elastic force + bin histogram (a1-a3), 1 bin
+ * offsets, 2 bin scatter (a2), 3 steric deposit (a4), 4 Gaussian filter (a5),
+ * 5 steric force + spread (a6), 6 LBM (a7), 7 interpolation + advance (a8).
+ * Enqueuing stages 0..7 in order is exactly one mc_step(w, 1) without the
+ * graph; any other use leaves the world in an unspecified state.  The step
+ * counter advances with stage 7.  Errors: MC_ERR_INVALID_ARG for an unknown
+ * stage. */
+mc_status mc_step_stage(mc_world* w, int stage, void* stream);
+#define MC_N_STAGES 8
+
+/* Copies the state after the enqueued steps.  Any output may be NULL.
+ *   x, y      [N] wrapped bead positions
+ *   theta     [E] edge angles
+ *   disp      [2N] interleaved (dx, dy) unwrapped displacement since creation
+ *   fdev      [9][H][W] pre-collision populations minus the rest weights w_i
+ * Outputs live in mem_kind memory.  With MC_MEM_HOST the call synchronizes
+ * `stream` before returning. */
+mc_status mc_world_get_state(const mc_world* w, float* x, float* y, float* theta, float* disp,
+                             float* fdev, int mem_kind, void* stream);
+
+/* Fields of the last completed step, for inspection and parity tests. */
+typedef enum mc_field {
+  MC_FIELD_FEL = 0,      /* [2N] elastic force per bead (a3) */
+  MC_FIELD_FS = 1,       /* [2N] steric force per bead (a6) */
+  MC_FIELD_UBEAD = 2,    /* [2N] interpolated velocity per bead (a8) */
+  MC_FIELD_RHO_S = 3,    /* [H*W] deposited steric density (a4) */
+  MC_FIELD_RHO_BAR = 4,  /* [H*W] filtered density (a5) */
+  MC_FIELD_FORCE = 5,    /* [2*H*W] interleaved (Fx, Fy) spread force density (a6) */
+  MC_FIELD_U = 6,        /* [2*H*W] interleaved (ux, uy) fluid velocity (a7) */
+  MC_FIELD_CELL = 7,     /* [N] int32 cell index (floor(y) mod H) W + (floor(x) mod W) (a2) */
+  MC_FIELD_BIN = 8,      /* [N] int32 bin (tile) index of each bead (a2) */
+  MC_FIELD_BIN_OFF = 9,  /* [n_bins + 1] int32 exclusive prefix sum of beads per bin (a2) */
+  MC_FIELD_BIN_BEADS = 10 /* [N] int32 bead ids in bin order (order inside a bin unspecified) */
+} mc_field;
+
+/* Copies one field (see mc_field for its size and type) into `out`. */
+mc_status mc_world_get_field(const mc_world* w, int field, void* out, int mem_kind, void* stream);
+
+/* Synchronizes `stream` and reads the world's watchdog: MC_OK, or
+ * MC_ERR_UNSTABLE when some step saw a non-finite or too large bead velocity
+ * (the flag stays set until mc_world_clear_flags). */
+mc_status mc_world_check(const mc_world* w, void* stream);
+mc_status mc_world_clear_flags(mc_world* w, void* stream);
+
+/* Thread-local description of the last error of this thread. */
+const char* mc_last_error(void);
+int mc_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MC_H */

@@ -1,0 +1,306 @@
+// Bead-parallel stages of one time step: drive + PBD + elastic force + bin
+// histogram (a1-a3), bin scatter (a2), IB interpolation + advance (a8), and
+// the per-world set-up / read-out kernels.
+#include "mc_internal.cuh"
+
+namespace mc {
+
+constexpr int kPbdFloatsPerBead = 10;
+
+// a1: theta_rest = theta0 + A sin(2 pi (freq t + phase)).  The phase in
+// cycles is reduced exactly: hi + lo = freq * t (two-product via FMA), and
+// only the fractional parts are added, so the angle keeps full precision at
+// large t.  t < 2^24 converts to float exactly.
+__device__ __forceinline__ float drive_angle(const float4 d, long long t) {
+  const float tf = (float)t;
+  const float hi = d.z * tf;
+  const float lo = fmaf(d.z, tf, -hi);
+  float fr = (hi - rintf(hi)) + lo + d.w;
+  fr -= rintf(fr);
+  return d.x + d.y * sinpif(2.0f * fr);
+}
+
+// One warp per filament.  The filament's edges, joints and bead corrections
+// live in a per-warp slice of shared memory; every pass of the Jacobi PBD
+// (Methods, Eqs. 1-4) reads the slice, then writes corrections, with a warp
+// barrier in between, so all corrections of a pass see the state before it.
+// Bead positions enter as edge vectors v0 = min_image(X_b - X_a) plus the
+// accumulated corrections, so the corrections keep full FP32 precision
+// whatever the magnitude of the coordinates.
+__global__ void __launch_bounds__(256) k_pbd(const WorldDev* __restrict__ worlds,
+                                             const int2* __restrict__ items, int n_items, int maxB) {
+  extern __shared__ float smem[];
+  const int wpb = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int item = blockIdx.x * wpb + warp;
+  if (item >= n_items) return;  // warp-uniform exit; the kernel has no block barrier
+  const int2 it = items[item];
+  const WorldDev& w = worlds[it.x];
+  const int f = it.y;
+  const int b0 = w.fil_off[f];
+  const int B = w.fil_off[f + 1] - b0;
+  const int nE = B - 1, nJ = B - 2;
+  const int e0 = b0 - f, j0 = b0 - 2 * f;
+  float* s = smem + (size_t)warp * maxB * kPbdFloatsPerBead;
+  float* vx = s;
+  float* vy = s + maxB;
+  float* th = s + 2 * maxB;
+  float* Lr = s + 3 * maxB;
+  float* ddx = s + 4 * maxB;
+  float* ddy = s + 5 * maxB;
+  float* dlx = s + 6 * maxB;
+  float* dly = s + 7 * maxB;
+  float* thr = s + 8 * maxB;
+  float* C = s + 9 * maxB;
+  const long long t = *w.t;
+  const int W = w.W, H = w.H;
+
+  for (int e = lane; e < nE; e += 32) {
+    const float4 pa = w.pos[b0 + e], pb = w.pos[b0 + e + 1];
+    int dcx = cell_x(pb) - cell_x(pa), dcy = cell_y(pb) - cell_y(pa);
+    if (2 * dcx > W) dcx -= W; else if (2 * dcx < -W) dcx += W;
+    if (2 * dcy > H) dcy -= H; else if (2 * dcy < -H) dcy += H;
+    vx[e] = (float)dcx + (pb.x - pa.x);
+    vy[e] = (float)dcy + (pb.y - pa.y);
+    th[e] = w.theta[e0 + e];
+    Lr[e] = w.L_rest[e0 + e];
+  }
+  for (int j = lane; j < nJ; j += 32) thr[j] = drive_angle(w.drive[j0 + j], t);
+  for (int i = lane; i < B; i += 32) {
+    dlx[i] = 0.0f;
+    dly[i] = 0.0f;
+  }
+  __syncwarp();
+
+  const float hb = 0.5f * w.k_bend;
+  const float hs = 0.5f * w.k_st;
+  const float ksh = w.k_sh;
+  const float ko = w.orient * hs * ksh;
+  for (int iter = 0; iter < w.n_pbd; ++iter) {
+    // bending pass (Eq. 1): C_j = (theta_{j+1} - theta_j) - theta_rest,j
+    for (int j = lane; j < nJ; j += 32) C[j] = th[j + 1] - th[j] - thr[j];
+    __syncwarp();
+    for (int e = lane; e < nE; e += 32) {
+      const float c1 = e < nJ ? C[e] : 0.0f;      // edge e is theta_1 of joint e
+      const float c0 = e > 0 ? C[e - 1] : 0.0f;   // ... and theta_2 of joint e-1
+      th[e] += hb * (c1 - c0);
+    }
+    __syncwarp();
+    // position pass (Eqs. 2-4) on the updated frames
+    for (int e = lane; e < nE; e += 32) {
+      const float x = vx[e] + (dlx[e + 1] - dlx[e]);
+      const float y = vy[e] + (dly[e + 1] - dly[e]);
+      const float L = Lr[e];
+      const float ell = sqrtf(x * x + y * y);
+      const float sc = (ell - L) / ell;
+      const float csx = sc * x, csy = sc * y;
+      float sn, cs;
+      sincosf(th[e], &sn, &cs);
+      ddx[e] = hs * (csx + ksh * (x - L * cs - csx));
+      ddy[e] = hs * (csy + ksh * (y - L * sn - csy));
+      th[e] += ko * (cs * y - sn * x) / L;   // frame turns toward the edge (orient)
+    }
+    __syncwarp();
+    for (int i = lane; i < B; i += 32) {
+      const float ax = i < nE ? ddx[i] : 0.0f, ay = i < nE ? ddy[i] : 0.0f;          // x_1 of edge i
+      const float bx = i > 0 ? ddx[i - 1] : 0.0f, by = i > 0 ? ddy[i - 1] : 0.0f;    // x_2 of edge i-1
+      dlx[i] += ax - bx;
+      dly[i] += ay - by;
+    }
+    __syncwarp();
+  }
+  for (int e = lane; e < nE; e += 32) w.theta[e0 + e] = th[e];
+
+  // elastic force F_el = kappa (x_hat - X) / dt, and the bin histogram (a2)
+  // with one atomic per group of lanes sharing a bin
+  for (int i0 = 0; i0 < B; i0 += 32) {
+    const int i = i0 + lane;
+    int bin = -1 - lane;
+    if (i < B) {
+      w.fel[b0 + i] = make_float2(w.kappa_dt * dlx[i], w.kappa_dt * dly[i]);
+      const float4 p = w.pos[b0 + i];
+      bin = (cell_y(p) / w.tile) * w.ntx + cell_x(p) / w.tile;
+      w.bead_bin[b0 + i] = bin;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, bin);
+    if (i < B && (__ffs(peers) - 1) == lane) atomicAdd(&w.bin_count[bin], __popc(peers));
+  }
+}
+
+// a2: scatter bead records into bin order.  Lanes of one warp that share a
+// bin take consecutive slots from one atomic.
+__global__ void __launch_bounds__(kBeadChunk) k_bin_scatter(const WorldDev* __restrict__ worlds,
+                                                            const int2* __restrict__ items) {
+  const int2 it = items[blockIdx.x];
+  const WorldDev& w = worlds[it.x];
+  const int i = it.y + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const bool valid = i < w.N;
+  const int bin = valid ? w.bead_bin[i] : -1 - lane;
+  const unsigned peers = __match_any_sync(0xffffffffu, bin);
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (valid && lane == leader) base = atomicAdd(&w.bin_cursor[bin], __popc(peers));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (valid) {
+    const int slot = base + __popc(peers & ((1u << lane) - 1u));
+    w.spos[slot] = w.pos[i];
+    w.sfel[slot] = w.fel[i];
+    w.sid[slot] = i;
+  }
+}
+
+// a8: U_i = sum_c delta_h(c - X_i) u(c) over the 4x4 stencil, then the
+// inertia-free advance X += dt U (cell index + fraction, wrapped) and the
+// unwrapped displacement D += dt U.  Thread 0 of each world's first block
+// advances the world's step counter (no other stage kernel reads it).
+__global__ void __launch_bounds__(kBeadChunk) k_interp_advance(const WorldDev* __restrict__ worlds,
+                                                               const int2* __restrict__ items) {
+  const int2 it = items[blockIdx.x];
+  const WorldDev& w = worlds[it.x];
+  if (it.y == 0 && threadIdx.x == 0) *w.t += 1;
+  const int i = it.y + threadIdx.x;
+  if (i >= w.N) return;
+  const int W = w.W, H = w.H;
+  float4 p = w.pos[i];
+  int cx = cell_x(p), cy = cell_y(p);
+  float wx[4], wy[4];
+  peskin4(p.x, wx);
+  peskin4(p.y, wy);
+  int ix[4], iy[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    ix[a] = wrap_once(cx - 1 + a, W);
+    iy[a] = wrap_once(cy - 1 + a, H) * W;
+  }
+  float Ux = 0.0f, Uy = 0.0f;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    float rx = 0.0f, ry = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const float2 v = w.u[iy[b] + ix[a]];
+      rx = fmaf(wx[a], v.x, rx);
+      ry = fmaf(wx[a], v.y, ry);
+    }
+    Ux = fmaf(wy[b], rx, Ux);
+    Uy = fmaf(wy[b], ry, Uy);
+  }
+  w.ubead[i] = make_float2(Ux, Uy);
+  const float m2 = Ux * Ux + Uy * Uy;
+  if (!(m2 <= w.u_max * w.u_max)) {   // also catches NaN
+    atomicOr(w.flags, kFlagUnstable);
+    return;
+  }
+  float fx = p.x + w.dt * Ux, fy = p.y + w.dt * Uy;
+  const float kx = floorf(fx), ky = floorf(fy);
+  fx -= kx;
+  fy -= ky;
+  cx += (int)kx;
+  cy += (int)ky;
+  if (fx >= 1.0f) { fx = 0.0f; cx += 1; }   // a tiny negative fraction rounded up to 1
+  if (fy >= 1.0f) { fy = 0.0f; cy += 1; }
+  cx = wrap_once(cx, W);
+  cy = wrap_once(cy, H);
+  w.pos[i] = make_float4(fx, fy, __int_as_float(cx), __int_as_float(cy));
+  float2 d = w.disp[i];
+  d.x += w.dt * Ux;
+  d.y += w.dt * Uy;
+  w.disp[i] = d;
+}
+
+// ---------------------------------------------------------------------------
+// Set-up and read-out (one world).
+// ---------------------------------------------------------------------------
+__constant__ int kCx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__constant__ int kCy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+// The stored state is post-collision (the LBM pulls on read).  Given
+// pre-collision populations f0, store g_i(c) = f0_i(c + c_i) so that pulling
+// g_i(c - c_i) returns f0_i(c).
+__global__ void k_unstream_in(const float* __restrict__ f0, float* __restrict__ g, int H, int W) {
+  const int HW = H * W;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 9 * HW) return;
+  const int i = idx / HW, c = idx - i * HW;
+  const int y = c / W, x = c - y * W;
+  const int sx = wrap_once(x + kCx[i], W), sy = wrap_once(y + kCy[i], H);
+  g[idx] = f0[i * HW + sy * W + sx];
+}
+
+__global__ void k_stream_out(const float* __restrict__ g, float* __restrict__ out, int H, int W) {
+  const int HW = H * W;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 9 * HW) return;
+  const int i = idx / HW, c = idx - i * HW;
+  const int y = c / W, x = c - y * W;
+  const int sx = wrap_once(x - kCx[i], W), sy = wrap_once(y - kCy[i], H);
+  out[idx] = g[i * HW + sy * W + sx];
+}
+
+__global__ void k_positions_out(const float4* __restrict__ pos, int N, float* x, float* y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const float4 p = pos[i];
+  if (x) x[i] = (float)cell_x(p) + p.x;
+  if (y) y[i] = (float)cell_y(p) + p.y;
+}
+
+__global__ void k_cells_out(const float4* __restrict__ pos, int N, int W, int* cell) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const float4 p = pos[i];
+  cell[i] = cell_y(p) * W + cell_x(p);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------
+static int pbd_warps_per_block(int maxB) {
+  const int per_warp = maxB * kPbdFloatsPerBead * (int)sizeof(float);
+  int wpb = (48 * 1024) / per_warp;
+  if (wpb > 8) wpb = 8;
+  if (wpb < 1) wpb = 1;
+  return wpb;
+}
+
+void launch_pbd(const Plan& p, cudaStream_t s) {
+  if (p.n_fil_items == 0) return;
+  const int wpb = pbd_warps_per_block(p.max_B);
+  const size_t smem = (size_t)wpb * p.max_B * kPbdFloatsPerBead * sizeof(float);
+  if (smem > 48 * 1024) {
+    cudaFuncSetAttribute(k_pbd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  const int grid = (p.n_fil_items + wpb - 1) / wpb;
+  k_pbd<<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, p.max_B);
+}
+
+void launch_bin_scatter(const Plan& p, cudaStream_t s) {
+  k_bin_scatter<<<p.n_bead_items, kBeadChunk, 0, s>>>(p.d_worlds, p.d_bead_items);
+}
+
+void launch_interp_advance(const Plan& p, cudaStream_t s) {
+  k_interp_advance<<<p.n_bead_items, kBeadChunk, 0, s>>>(p.d_worlds, p.d_bead_items);
+}
+
+void launch_unstream_in(const float* f0dev, float* g_dst, int H, int W, cudaStream_t s) {
+  const int n = 9 * H * W;
+  k_unstream_in<<<(n + 255) / 256, 256, 0, s>>>(f0dev, g_dst, H, W);
+}
+
+void launch_stream_out(const float* g_src, float* out, int H, int W, cudaStream_t s) {
+  const int n = 9 * H * W;
+  k_stream_out<<<(n + 255) / 256, 256, 0, s>>>(g_src, out, H, W);
+}
+
+void launch_positions_out(const WorldDev& w, float* x, float* y, cudaStream_t s) {
+  if (w.N == 0) return;
+  k_positions_out<<<(w.N + 255) / 256, 256, 0, s>>>(w.pos, w.N, x, y);
+}
+
+void launch_cells_out(const WorldDev& w, int* cell, cudaStream_t s) {
+  if (w.N == 0) return;
+  k_cells_out<<<(w.N + 255) / 256, 256, 0, s>>>(w.pos, w.N, w.W, cell);
+}
+
+}  // namespace mc

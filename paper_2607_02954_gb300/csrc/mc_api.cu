@@ -1,0 +1,609 @@
+// C ABI of libmc: world life cycle, plans (world tables + work items), step
+// replay through CUDA graphs, and state read-out.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "mc_internal.cuh"
+
+using mc::Plan;
+using mc::WorldDev;
+
+struct mc_world {
+  WorldDev h{};                 // device descriptor (host copy)
+  void* arena = nullptr;        // one allocation holding every device array
+  size_t bytes = 0;
+  cudaStream_t stream = nullptr;  // creation stream; the arena is freed on it
+  int64_t t = 0;                // step counter after all enqueued steps
+  int max_B = 2;
+  std::vector<int> fil_off;
+  Plan plan;                    // single-world plan
+  mc_params params{};
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+mc_status fail(mc_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+mc_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(MC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define MC_CUDA(call)                                      \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
+  } while (0)
+
+// Bump allocator inside one arena.
+struct Layout {
+  size_t off = 0;
+  template <class T>
+  size_t take(size_t n) {
+    off = (off + 255) & ~size_t(255);
+    const size_t at = off;
+    off += n * sizeof(T);
+    return at;
+  }
+};
+
+template <class T>
+T* at(void* base, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(base) + off);
+}
+
+bool finite_all(const float* a, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+// Copies n floats of either memory kind to a host vector.
+mc_status fetch(const float* src, size_t n, int kind, std::vector<float>& out, const char* name) {
+  out.resize(n);
+  if (n == 0) return MC_OK;
+  if (!src) return fail(MC_ERR_INVALID_ARG, std::string(name) + " is NULL");
+  if (kind == MC_MEM_HOST) {
+    std::memcpy(out.data(), src, n * sizeof(float));
+  } else {
+    MC_CUDA(cudaMemcpy(out.data(), src, n * sizeof(float), cudaMemcpyDeviceToHost));
+  }
+  return MC_OK;
+}
+
+mc_status validate_params(const mc_params& p) {
+  const float v[] = {p.nu, p.dt, p.Lambda, p.kappa, p.k_bend, p.k_stretch, p.k_shear, p.k_rep, p.sigma, p.orient};
+  for (float x : v)
+    if (!std::isfinite(x)) return fail(MC_ERR_INVALID_ARG, "non-finite constant in mc_params");
+  if (!(p.nu > 0.0f)) return fail(MC_ERR_INVALID_ARG, "nu must be > 0 (tau+ > 1/2)");
+  if (!(p.Lambda > 0.0f)) return fail(MC_ERR_INVALID_ARG, "Lambda must be > 0");
+  if (!(p.dt > 0.0f)) return fail(MC_ERR_INVALID_ARG, "dt must be > 0");
+  if (!(p.sigma > 0.0f && p.sigma <= 2.0f)) return fail(MC_ERR_INVALID_ARG, "sigma must be in (0, 2]");
+  if (p.n_pbd < 0 || p.n_pbd > mc::kMaxNpbd) return fail(MC_ERR_INVALID_ARG, "n_pbd must be in [0, 64]");
+  return MC_OK;
+}
+
+void fill_constants(WorldDev& h, const mc_params& p) {
+  const double tau_p = 3.0 * (double)p.nu + 0.5;
+  const double tau_m = 0.5 + (double)p.Lambda / (tau_p - 0.5);
+  h.dt = p.dt;
+  h.kappa_dt = (float)((double)p.kappa / (double)p.dt);
+  h.k_bend = p.k_bend;
+  h.k_st = p.k_stretch;
+  h.k_sh = p.k_shear;
+  h.k_rep = p.k_rep;
+  h.orient = p.orient;
+  h.n_pbd = p.n_pbd;
+  h.om_p = (float)(1.0 / tau_p);
+  h.om_m = (float)(1.0 / tau_m);
+  h.src_p = (float)(1.0 - 0.5 / tau_p);
+  h.src_m = (float)(1.0 - 0.5 / tau_m);
+  h.u_max = 0.5f;
+  const int R = (int)std::ceil(4.0 * (double)p.sigma);
+  h.R = R;
+  double sum = 0.0;
+  double g[2 * mc::kMaxR + 1];
+  for (int m = -R; m <= R; ++m) {
+    g[m + R] = std::exp(-(double)(m * m) / (2.0 * (double)p.sigma * (double)p.sigma));
+    sum += g[m + R];
+  }
+  for (int k = 0; k < 2 * mc::kMaxR + 1; ++k) h.taps[k] = k <= 2 * R ? (float)(g[k] / sum) : 0.0f;
+}
+
+void free_plan(Plan& p, cudaStream_t s) {
+  if (p.graph) cudaGraphExecDestroy(p.graph);
+  if (p.d_mem) cudaFreeAsync(p.d_mem, s);
+  p = Plan{};
+}
+
+mc_status build_plan(mc_world* const* ws, int n, cudaStream_t s, Plan& out) {
+  Plan p;
+  p.n_worlds = n;
+  std::vector<int2> fil, bead, tile, cell;
+  std::vector<WorldDev> table(n);
+  for (int k = 0; k < n; ++k) {
+    const mc_world* w = ws[k];
+    table[k] = w->h;
+    p.max_B = std::max(p.max_B, w->max_B);
+    for (int f = 0; f < w->h.n_fil; ++f) fil.push_back(make_int2(k, f));
+    const int nb = std::max(w->h.N, 1);
+    for (int b = 0; b < nb; b += mc::kBeadChunk) bead.push_back(make_int2(k, b));
+    for (int t = 0; t < w->h.n_bins; ++t) tile.push_back(make_int2(k, t));
+    const int HW = w->h.H * w->h.W;
+    for (int c = 0; c < HW; c += mc::kCellChunk) cell.push_back(make_int2(k, c));
+  }
+  Layout L;
+  const size_t o_w = L.take<WorldDev>(n);
+  const size_t o_f = L.take<int2>(fil.size());
+  const size_t o_b = L.take<int2>(bead.size());
+  const size_t o_t = L.take<int2>(tile.size());
+  const size_t o_c = L.take<int2>(cell.size());
+  std::vector<char> host(L.off);
+  std::memcpy(host.data() + o_w, table.data(), n * sizeof(WorldDev));
+  if (!fil.empty()) std::memcpy(host.data() + o_f, fil.data(), fil.size() * sizeof(int2));
+  std::memcpy(host.data() + o_b, bead.data(), bead.size() * sizeof(int2));
+  if (!tile.empty()) std::memcpy(host.data() + o_t, tile.data(), tile.size() * sizeof(int2));
+  std::memcpy(host.data() + o_c, cell.data(), cell.size() * sizeof(int2));
+  cudaError_t e = cudaMallocAsync(&p.d_mem, L.off, s);
+  if (e != cudaSuccess) return fail(MC_ERR_OOM, std::string("plan allocation: ") + cudaGetErrorString(e));
+  e = cudaMemcpyAsync(p.d_mem, host.data(), L.off, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "plan upload");
+  // pageable source: the copy is staged before cudaMemcpyAsync returns
+  p.d_worlds = at<WorldDev>(p.d_mem, o_w);
+  p.d_fil_items = at<int2>(p.d_mem, o_f);
+  p.d_bead_items = at<int2>(p.d_mem, o_b);
+  p.d_tile_items = at<int2>(p.d_mem, o_t);
+  p.d_cell_items = at<int2>(p.d_mem, o_c);
+  p.n_fil_items = (int)fil.size();
+  p.n_bead_items = (int)bead.size();
+  p.n_tile_items = (int)tile.size();
+  p.n_cell_items = (int)cell.size();
+  out = p;
+  return MC_OK;
+}
+
+constexpr int kGraphSteps = 16;
+
+cudaStream_t capture_stream() {
+  thread_local cudaStream_t cs = nullptr;
+  if (!cs) cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  return cs;
+}
+
+mc_status run_steps(Plan& p, int n, cudaStream_t s) {
+  if (n >= kGraphSteps) {
+    if (!p.graph) {
+      cudaStream_t cs = capture_stream();
+      MC_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      for (int k = 0; k < kGraphSteps; ++k) mc::enqueue_step(p, cs);
+      cudaGraph_t g = nullptr;
+      MC_CUDA(cudaStreamEndCapture(cs, &g));
+      cudaError_t e = cudaGraphInstantiate(&p.graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+      p.graph_steps = kGraphSteps;
+    }
+    while (n >= p.graph_steps) {
+      MC_CUDA(cudaGraphLaunch(p.graph, s));
+      n -= p.graph_steps;
+    }
+  }
+  for (int k = 0; k < n; ++k) mc::enqueue_step(p, s);
+  MC_CUDA(cudaGetLastError());
+  return MC_OK;
+}
+
+// Batched plans are cached by the exact list of world handles.
+std::mutex g_plan_mu;
+std::map<std::vector<mc_world*>, Plan>& plan_cache() {
+  static std::map<std::vector<mc_world*>, Plan> m;
+  return m;
+}
+
+void drop_plans_with(mc_world* w) {
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  auto& m = plan_cache();
+  for (auto it = m.begin(); it != m.end();) {
+    bool has = false;
+    for (auto* x : it->first) has |= (x == w);
+    if (has) {
+      free_plan(it->second, w->stream);
+      it = m.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mc_last_error(void) { return g_last_error.c_str(); }
+int mc_abi_version(void) { return MC_ABI_VERSION; }
+
+mc_status mc_params_default(mc_params* p) {
+  if (!p) return fail(MC_ERR_INVALID_ARG, "p is NULL");
+  p->nu = 0.1f;
+  p->dt = 1.0f;
+  p->Lambda = 0.25f;
+  p->kappa = 0.05f;
+  p->k_bend = 0.5f;
+  p->k_stretch = 0.5f;
+  p->k_shear = 0.25f;
+  p->k_rep = 0.5f;
+  p->sigma = 1.0f;
+  p->orient = 1.0f;
+  p->n_pbd = 4;
+  return MC_OK;
+}
+
+mc_status mc_world_create(const mc_world_desc* d, void* stream, mc_world** out) {
+  if (!d || !out) return fail(MC_ERR_INVALID_ARG, "desc or out is NULL");
+  *out = nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int H = d->H, W = d->W;
+  if (H < 8 || W < 8 || H % 8 || W % 8 || H > 8192 || W > 8192)
+    return fail(MC_ERR_INVALID_ARG, "H and W must be multiples of 8 in [8, 8192]");
+  if (d->n_fil < 0) return fail(MC_ERR_INVALID_ARG, "n_fil < 0");
+  if (d->mem_kind != MC_MEM_HOST && d->mem_kind != MC_MEM_DEVICE) return fail(MC_ERR_INVALID_ARG, "bad mem_kind");
+  if (d->t0 < 0 || d->t0 >= (int64_t(1) << 24)) return fail(MC_ERR_INVALID_ARG, "t0 must be in [0, 2^24)");
+  mc_status st = validate_params(d->p);
+  if (st != MC_OK) return st;
+  if (d->n_fil > 0 && !d->fil_off) return fail(MC_ERR_INVALID_ARG, "fil_off is NULL");
+  std::vector<int> fo(d->n_fil + 1, 0);
+  int max_B = 2;
+  for (int f = 0; f <= d->n_fil; ++f) fo[f] = d->n_fil > 0 ? d->fil_off[f] : 0;
+  if (fo[0] != 0) return fail(MC_ERR_INVALID_ARG, "fil_off[0] must be 0");
+  for (int f = 0; f < d->n_fil; ++f) {
+    const int B = fo[f + 1] - fo[f];
+    if (B < 2) return fail(MC_ERR_INVALID_ARG, "every filament needs at least 2 beads");
+    max_B = std::max(max_B, B);
+  }
+  if (max_B > 4096) return fail(MC_ERR_INVALID_ARG, "filaments are limited to 4096 beads");
+  const int N = fo[d->n_fil];
+  const int E = N - d->n_fil, J = N - 2 * d->n_fil;
+  const size_t HW = (size_t)H * W;
+
+  std::vector<float> x, y, th, Lr, t0v, amp, frq, phs, f0;
+  if ((st = fetch(d->x, N, d->mem_kind, x, "x")) || (st = fetch(d->y, N, d->mem_kind, y, "y")) ||
+      (st = fetch(d->theta, E, d->mem_kind, th, "theta")) || (st = fetch(d->L_rest, E, d->mem_kind, Lr, "L_rest")) ||
+      (st = fetch(d->theta0, J, d->mem_kind, t0v, "theta0")) ||
+      (st = fetch(d->drive_amp, J, d->mem_kind, amp, "drive_amp")) ||
+      (st = fetch(d->drive_freq, J, d->mem_kind, frq, "drive_freq")) ||
+      (st = fetch(d->drive_phase, J, d->mem_kind, phs, "drive_phase")))
+    return st;
+  if (d->f0 && (st = fetch(d->f0, 9 * HW, d->mem_kind, f0, "f0"))) return st;
+  if (!finite_all(x.data(), N) || !finite_all(y.data(), N) || !finite_all(th.data(), E) ||
+      !finite_all(Lr.data(), E) || !finite_all(t0v.data(), J) || !finite_all(amp.data(), J) ||
+      !finite_all(frq.data(), J) || !finite_all(phs.data(), J) || !finite_all(f0.data(), f0.size()))
+    return fail(MC_ERR_INVALID_ARG, "non-finite input value");
+  for (int e = 0; e < E; ++e)
+    if (!(Lr[e] > 0.0f)) return fail(MC_ERR_INVALID_ARG, "L_rest must be > 0");
+
+  // host images of the device arrays
+  std::vector<float4> pos(N), drive(J);
+  for (int i = 0; i < N; ++i) {
+    const double xd = std::fmod((double)x[i], (double)W), yd = std::fmod((double)y[i], (double)H);
+    float xw = (float)(xd < 0 ? xd + W : xd), yw = (float)(yd < 0 ? yd + H : yd);
+    if (xw >= (float)W) xw = 0.0f;
+    if (yw >= (float)H) yw = 0.0f;
+    const float cx = std::floor(xw), cy = std::floor(yw);
+    int icx, icy;
+    icx = (int)cx;
+    icy = (int)cy;
+    float4 p;
+    p.x = xw - cx;   // exact
+    p.y = yw - cy;
+    std::memcpy(&p.z, &icx, 4);
+    std::memcpy(&p.w, &icy, 4);
+    pos[i] = p;
+  }
+  for (int j = 0; j < J; ++j) drive[j] = make_float4(t0v[j], amp[j], frq[j], phs[j]);
+
+  mc_world* w = new mc_world();
+  w->stream = s;
+  w->t = d->t0;
+  w->max_B = max_B;
+  w->fil_off = fo;
+  w->params = d->p;
+  WorldDev& h = w->h;
+  h.H = H;
+  h.W = W;
+  h.N = N;
+  h.E = E;
+  h.J = J;
+  h.n_fil = d->n_fil;
+  h.tile = mc::kTile;
+  h.ntx = (W + mc::kTile - 1) / mc::kTile;
+  h.nty = (H + mc::kTile - 1) / mc::kTile;
+  h.n_bins = h.ntx * h.nty;
+  fill_constants(h, d->p);
+
+  Layout L;
+  const size_t o_fo = L.take<int>(d->n_fil + 1);
+  const size_t o_pos = L.take<float4>(N);
+  const size_t o_disp = L.take<float2>(N);
+  const size_t o_th = L.take<float>(E);
+  const size_t o_L = L.take<float>(E);
+  const size_t o_dr = L.take<float4>(J);
+  const size_t o_fel = L.take<float2>(N);
+  const size_t o_fs = L.take<float2>(N);
+  const size_t o_ub = L.take<float2>(N);
+  const size_t o_bb = L.take<int>(N);
+  const size_t o_bc = L.take<int>(h.n_bins);
+  const size_t o_bo = L.take<int>(h.n_bins + 1);
+  const size_t o_bcur = L.take<int>(h.n_bins);
+  const size_t o_sp = L.take<float4>(N);
+  const size_t o_sf = L.take<float2>(N);
+  const size_t o_sid = L.take<int>(N);
+  const size_t o_g0 = L.take<float>(9 * HW);
+  const size_t o_g1 = L.take<float>(9 * HW);
+  const size_t o_F = L.take<float2>(HW);
+  const size_t o_u = L.take<float2>(HW);
+  const size_t o_rs = L.take<float>(HW);
+  const size_t o_rb = L.take<float>(HW);
+  const size_t o_t = L.take<long long>(1);
+  const size_t o_fl = L.take<unsigned>(1);
+  w->bytes = L.off;
+  cudaError_t e = cudaMallocAsync(&w->arena, w->bytes, s);
+  if (e != cudaSuccess) {
+    delete w;
+    return fail(MC_ERR_OOM, std::string("world allocation: ") + cudaGetErrorString(e));
+  }
+  void* A = w->arena;
+  h.fil_off = at<int>(A, o_fo);
+  h.pos = at<float4>(A, o_pos);
+  h.disp = at<float2>(A, o_disp);
+  h.theta = at<float>(A, o_th);
+  h.L_rest = at<float>(A, o_L);
+  h.drive = at<float4>(A, o_dr);
+  h.fel = at<float2>(A, o_fel);
+  h.fs = at<float2>(A, o_fs);
+  h.ubead = at<float2>(A, o_ub);
+  h.bead_bin = at<int>(A, o_bb);
+  h.bin_count = at<int>(A, o_bc);
+  h.bin_off = at<int>(A, o_bo);
+  h.bin_cursor = at<int>(A, o_bcur);
+  h.spos = at<float4>(A, o_sp);
+  h.sfel = at<float2>(A, o_sf);
+  h.sid = at<int>(A, o_sid);
+  h.g[0] = at<float>(A, o_g0);
+  h.g[1] = at<float>(A, o_g1);
+  h.F = at<float2>(A, o_F);
+  h.u = at<float2>(A, o_u);
+  h.rho_s = at<float>(A, o_rs);
+  h.rho_b = at<float>(A, o_rb);
+  h.t = at<long long>(A, o_t);
+  h.flags = at<unsigned>(A, o_fl);
+
+  auto fail_free = [&](mc_status s2) {
+    cudaFreeAsync(w->arena, s);
+    delete w;
+    return s2;
+  };
+#define MC_CUDA_W(call)                                                  \
+  do {                                                                   \
+    cudaError_t e_ = (call);                                             \
+    if (e_ != cudaSuccess) return fail_free(cuda_fail(e_, #call));       \
+  } while (0)
+  MC_CUDA_W(cudaMemsetAsync(A, 0, w->bytes, s));
+  auto up = [&](void* dst, const void* src, size_t n) {
+    return n ? cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s) : cudaSuccess;
+  };
+  MC_CUDA_W(up((void*)h.fil_off, fo.data(), fo.size() * sizeof(int)));
+  MC_CUDA_W(up(h.pos, pos.data(), N * sizeof(float4)));
+  MC_CUDA_W(up(h.theta, th.data(), E * sizeof(float)));
+  MC_CUDA_W(up((void*)h.L_rest, Lr.data(), E * sizeof(float)));
+  MC_CUDA_W(up((void*)h.drive, drive.data(), J * sizeof(float4)));
+  const long long t0 = d->t0;
+  MC_CUDA_W(up(h.t, &t0, sizeof(long long)));
+  if (!f0.empty()) {
+    // stage f0 in the buffer the first step writes, then store its
+    // post-collision image in the buffer the first step reads
+    float* stage = h.g[(t0 + 1) & 1];
+    MC_CUDA_W(up(stage, f0.data(), 9 * HW * sizeof(float)));
+    mc::launch_unstream_in(stage, h.g[t0 & 1], H, W, s);
+    MC_CUDA_W(cudaGetLastError());
+  }
+  mc_world* self = w;
+  st = build_plan(&self, 1, s, w->plan);
+  if (st != MC_OK) return fail_free(st);
+#undef MC_CUDA_W
+  *out = w;
+  return MC_OK;
+}
+
+mc_status mc_world_destroy(mc_world* w) {
+  if (!w) return MC_OK;
+  drop_plans_with(w);
+  free_plan(w->plan, w->stream);
+  cudaFreeAsync(w->arena, w->stream);
+  delete w;
+  return MC_OK;
+}
+
+mc_status mc_world_info_get(const mc_world* w, mc_world_info* out) {
+  if (!w || !out) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+  out->H = w->h.H;
+  out->W = w->h.W;
+  out->n_fil = w->h.n_fil;
+  out->N = w->h.N;
+  out->E = w->h.E;
+  out->J = w->h.J;
+  out->tile = w->h.tile;
+  out->n_bins = w->h.n_bins;
+  out->t = w->t;
+  out->device_bytes = w->bytes;
+  return MC_OK;
+}
+
+mc_status mc_step(mc_world* w, int n_steps, void* stream) {
+  if (!w || n_steps < 0) return fail(MC_ERR_INVALID_ARG, "bad world or n_steps");
+  if (w->t + n_steps >= (int64_t(1) << 24)) return fail(MC_ERR_INVALID_ARG, "step counter would reach 2^24");
+  mc_status st = run_steps(w->plan, n_steps, static_cast<cudaStream_t>(stream));
+  if (st == MC_OK) w->t += n_steps;
+  return st;
+}
+
+mc_status mc_step_batched(mc_world* const* ws, int n, int n_steps, void* stream) {
+  if (!ws || n < 0 || n_steps < 0) return fail(MC_ERR_INVALID_ARG, "bad arguments");
+  if (n == 0 || n_steps == 0) return MC_OK;
+  std::vector<mc_world*> key(ws, ws + n);
+  for (int k = 0; k < n; ++k) {
+    if (!ws[k]) return fail(MC_ERR_INVALID_ARG, "NULL world in batch");
+    for (int j = 0; j < k; ++j)
+      if (ws[j] == ws[k]) return fail(MC_ERR_INVALID_ARG, "a world appears twice in the batch");
+    if (ws[k]->t + n_steps >= (int64_t(1) << 24)) return fail(MC_ERR_INVALID_ARG, "step counter would reach 2^24");
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Plan* plan = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto& m = plan_cache();
+    auto it = m.find(key);
+    if (it == m.end()) {
+      Plan p;
+      mc_status st = build_plan(ws, n, s, p);
+      if (st != MC_OK) return st;
+      it = m.emplace(key, p).first;
+    }
+    plan = &it->second;
+  }
+  mc_status st = run_steps(*plan, n_steps, s);
+  if (st == MC_OK)
+    for (int k = 0; k < n; ++k) ws[k]->t += n_steps;
+  return st;
+}
+
+mc_status mc_step_stage(mc_world* w, int stage, void* stream) {
+  if (!w || stage < 0 || stage >= MC_N_STAGES) return fail(MC_ERR_INVALID_ARG, "bad world or stage");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Plan& p = w->plan;
+  switch (stage) {
+    case 0: mc::launch_pbd(p, s); break;
+    case 1: mc::launch_bin_scan(p, s); break;
+    case 2: mc::launch_bin_scatter(p, s); break;
+    case 3: mc::launch_deposit(p, s); break;
+    case 4: mc::launch_blur(p, s); break;
+    case 5: mc::launch_force_spread(p, s); break;
+    case 6: mc::launch_lbm(p, s); break;
+    default:
+      mc::launch_interp_advance(p, s);
+      w->t += 1;
+      break;
+  }
+  MC_CUDA(cudaGetLastError());
+  return MC_OK;
+}
+
+mc_status mc_world_get_state(const mc_world* w, float* x, float* y, float* theta, float* disp, float* fdev,
+                             int mem_kind, void* stream) {
+  if (!w) return fail(MC_ERR_INVALID_ARG, "world is NULL");
+  if (mem_kind != MC_MEM_HOST && mem_kind != MC_MEM_DEVICE) return fail(MC_ERR_INVALID_ARG, "bad mem_kind");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const WorldDev& h = w->h;
+  const size_t HW = (size_t)h.H * h.W;
+  const bool host = mem_kind == MC_MEM_HOST;
+  // device scratch for outputs that need a kernel when the target is host memory
+  float *dx = nullptr, *dy = nullptr, *df = nullptr;
+  const size_t need = (host && (x || y) ? 2 * (size_t)h.N : 0) + (host && fdev ? 9 * HW : 0);
+  void* scratch = nullptr;
+  if (need) MC_CUDA(cudaMallocAsync(&scratch, need * sizeof(float), s));
+  float* sp = static_cast<float*>(scratch);
+  if (x || y) {
+    dx = host ? sp : x;
+    dy = host ? sp + h.N : y;
+    mc::launch_positions_out(h, x ? dx : nullptr, y ? dy : nullptr, s);
+    if (host) {
+      if (x && h.N) MC_CUDA(cudaMemcpyAsync(x, dx, h.N * sizeof(float), cudaMemcpyDeviceToHost, s));
+      if (y && h.N) MC_CUDA(cudaMemcpyAsync(y, dy, h.N * sizeof(float), cudaMemcpyDeviceToHost, s));
+    }
+    if (host) sp += 2 * (size_t)h.N;
+  }
+  const cudaMemcpyKind dk = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (theta && h.E) MC_CUDA(cudaMemcpyAsync(theta, h.theta, h.E * sizeof(float), dk, s));
+  if (disp && h.N) MC_CUDA(cudaMemcpyAsync(disp, h.disp, h.N * sizeof(float2), dk, s));
+  if (fdev) {
+    df = host ? sp : fdev;
+    mc::launch_stream_out(h.g[w->t & 1], df, h.H, h.W, s);
+    if (host) MC_CUDA(cudaMemcpyAsync(fdev, df, 9 * HW * sizeof(float), cudaMemcpyDeviceToHost, s));
+  }
+  MC_CUDA(cudaGetLastError());
+  if (scratch) MC_CUDA(cudaFreeAsync(scratch, s));
+  if (host) MC_CUDA(cudaStreamSynchronize(s));
+  return MC_OK;
+}
+
+mc_status mc_world_get_field(const mc_world* w, int field, void* out, int mem_kind, void* stream) {
+  if (!w || !out) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+  if (mem_kind != MC_MEM_HOST && mem_kind != MC_MEM_DEVICE) return fail(MC_ERR_INVALID_ARG, "bad mem_kind");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const WorldDev& h = w->h;
+  const size_t HW = (size_t)h.H * h.W;
+  const bool host = mem_kind == MC_MEM_HOST;
+  const cudaMemcpyKind dk = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  const void* src = nullptr;
+  size_t bytes = 0;
+  switch (field) {
+    case MC_FIELD_FEL: src = h.fel; bytes = h.N * sizeof(float2); break;
+    case MC_FIELD_FS: src = h.fs; bytes = h.N * sizeof(float2); break;
+    case MC_FIELD_UBEAD: src = h.ubead; bytes = h.N * sizeof(float2); break;
+    case MC_FIELD_RHO_S: src = h.rho_s; bytes = HW * sizeof(float); break;
+    case MC_FIELD_RHO_BAR: src = h.rho_b; bytes = HW * sizeof(float); break;
+    case MC_FIELD_FORCE: src = h.F; bytes = HW * sizeof(float2); break;
+    case MC_FIELD_U: src = h.u; bytes = HW * sizeof(float2); break;
+    case MC_FIELD_BIN: src = h.bead_bin; bytes = h.N * sizeof(int); break;
+    case MC_FIELD_BIN_OFF: src = h.bin_off; bytes = (h.n_bins + 1) * sizeof(int); break;
+    case MC_FIELD_BIN_BEADS: src = h.sid; bytes = h.N * sizeof(int); break;
+    case MC_FIELD_CELL: {
+      if (h.N == 0) return MC_OK;
+      int* dst = static_cast<int*>(out);
+      void* scratch = nullptr;
+      if (host) {
+        MC_CUDA(cudaMallocAsync(&scratch, h.N * sizeof(int), s));
+        dst = static_cast<int*>(scratch);
+      }
+      mc::launch_cells_out(h, dst, s);
+      MC_CUDA(cudaGetLastError());
+      if (host) {
+        MC_CUDA(cudaMemcpyAsync(out, dst, h.N * sizeof(int), cudaMemcpyDeviceToHost, s));
+        MC_CUDA(cudaFreeAsync(scratch, s));
+        MC_CUDA(cudaStreamSynchronize(s));
+      }
+      return MC_OK;
+    }
+    default:
+      return fail(MC_ERR_INVALID_ARG, "unknown field");
+  }
+  if (bytes) MC_CUDA(cudaMemcpyAsync(out, src, bytes, dk, s));
+  if (host) MC_CUDA(cudaStreamSynchronize(s));
+  return MC_OK;
+}
+
+mc_status mc_world_check(const mc_world* w, void* stream) {
+  if (!w) return fail(MC_ERR_INVALID_ARG, "world is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned flags = 0;
+  MC_CUDA(cudaMemcpyAsync(&flags, w->h.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  MC_CUDA(cudaStreamSynchronize(s));
+  if (flags & mc::kFlagUnstable) return fail(MC_ERR_UNSTABLE, "bead velocity watchdog tripped (|U| > 0.5 or not finite)");
+  return MC_OK;
+}
+
+mc_status mc_world_clear_flags(mc_world* w, void* stream) {
+  if (!w) return fail(MC_ERR_INVALID_ARG, "world is NULL");
+  MC_CUDA(cudaMemsetAsync(w->h.flags, 0, sizeof(unsigned), static_cast<cudaStream_t>(stream)));
+  return MC_OK;
+}
+
+}  // extern "C"

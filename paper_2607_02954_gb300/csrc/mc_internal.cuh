@@ -1,0 +1,122 @@
+// Internal types and device helpers of libmc (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mc.h"
+
+namespace mc {
+
+// Binning tile edge in cells.  A bead's 4x4 stencil reaches 2 cells below and
+// 1 cell above its own cell, so a tile only receives from its 3x3 tile
+// neighbourhood; grid sizes are multiples of 8, so ragged last tiles are at
+// least 8 cells wide.
+constexpr int kTile = 32;
+constexpr int kMaxR = 8;            // Gaussian half width ceil(4 sigma) <= 8
+constexpr int kBeadChunk = 256;     // beads per block of the bead-parallel kernels
+constexpr int kCellChunk = 256;     // cells per block of the LBM kernel
+constexpr int kMaxNpbd = 64;
+
+// Deposition accumulates in 64-bit fixed point with 40 fractional bits:
+// integer adds commute, so every deposited field is bitwise independent of
+// the order in which beads arrive (alone, batched or served).
+constexpr float kFixScale = 1099511627776.0f;      // 2^40
+constexpr float kFixInv = 9.094947017729282e-13f;  // 2^-40
+
+enum : unsigned { kFlagUnstable = 1u };
+
+// Everything the kernels need to know about one world.  Lives in device
+// memory as one entry of a world table; all pointers are device pointers.
+struct WorldDev {
+  int H, W, N, E, J, n_fil;
+  int tile, ntx, nty, n_bins;
+  int R, n_pbd;
+  float dt, kappa_dt, k_bend, k_st, k_sh, k_rep, orient;
+  float om_p, om_m, src_p, src_m;   // 1/tau+-, 1 - 1/(2 tau+-)
+  float u_max;                      // watchdog threshold on |U|
+  float taps[2 * kMaxR + 1];
+  const int* fil_off;     // [n_fil + 1]
+  float4* pos;            // [N]  (frac x, frac y, int cell x, int cell y)
+  float2* disp;           // [N]
+  float* theta;           // [E]
+  const float* L_rest;    // [E]
+  const float4* drive;    // [J]  (theta0, amp, freq, phase)
+  float2* fel;            // [N]
+  float2* fs;             // [N]
+  float2* ubead;          // [N]
+  int* bead_bin;          // [N]
+  int* bin_count;         // [n_bins]
+  int* bin_off;           // [n_bins + 1]
+  int* bin_cursor;        // [n_bins]
+  float4* spos;           // [N] positions in bin order
+  float2* sfel;           // [N] elastic forces in bin order
+  int* sid;               // [N] bead ids in bin order
+  float* g[2];            // [9 * H * W] post-collision population deviations (ping-pong)
+  float2* F;              // [H * W]
+  float2* u;              // [H * W]
+  float* rho_s;           // [H * W]
+  float* rho_b;           // [H * W]
+  long long* t;           // step counter
+  unsigned* flags;        // watchdog flags
+};
+
+// A set of worlds advanced together, with the work items of each stage.
+struct Plan {
+  int n_worlds = 0;
+  int max_B = 2;
+  int n_fil_items = 0, n_bead_items = 0, n_tile_items = 0, n_cell_items = 0;
+  WorldDev* d_worlds = nullptr;  // [n_worlds]
+  int2* d_fil_items = nullptr;   // (world, filament)
+  int2* d_bead_items = nullptr;  // (world, first bead)
+  int2* d_tile_items = nullptr;  // (world, tile)
+  int2* d_cell_items = nullptr;  // (world, first cell)
+  void* d_mem = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+};
+
+// --- stage launchers (one launch covers every world of the plan) ---------
+void launch_pbd(const Plan& p, cudaStream_t s);
+void launch_bin_scan(const Plan& p, cudaStream_t s);
+void launch_bin_scatter(const Plan& p, cudaStream_t s);
+void launch_deposit(const Plan& p, cudaStream_t s);
+void launch_blur(const Plan& p, cudaStream_t s);
+void launch_force_spread(const Plan& p, cudaStream_t s);
+void launch_lbm(const Plan& p, cudaStream_t s);
+void launch_interp_advance(const Plan& p, cudaStream_t s);
+void enqueue_step(const Plan& p, cudaStream_t s);
+constexpr int kKernelsPerStep = 8;
+
+// --- set-up / read-out kernels (one world) --------------------------------
+void launch_unstream_in(const float* f0dev, float* g_dst, int H, int W, cudaStream_t s);
+void launch_stream_out(const float* g_src, float* out, int H, int W, cudaStream_t s);
+void launch_positions_out(const WorldDev& w, float* x, float* y, cudaStream_t s);
+void launch_cells_out(const WorldDev& w, int* cell, cudaStream_t s);
+
+// --- device helpers -------------------------------------------------------
+__device__ __forceinline__ int wrap_once(int v, int n) {
+  // v in [-n, 2n): one conditional correction maps it into [0, n)
+  return v < 0 ? v + n : (v >= n ? v - n : v);
+}
+
+// Peskin's 4-point kernel phi at the four cells floor(X)-1 .. floor(X)+2
+// for fractional part a in [0, 1).  With s = sqrt(1 + 4a - 4a^2):
+//   phi(1+a) = (3 - 2a - s)/8, phi(a) = (3 - 2a + s)/8,
+//   phi(1-a) = (1 + 2a + s)/8, phi(2-a) = (1 + 2a - s)/8.
+__device__ __forceinline__ void peskin4(float a, float w[4]) {
+  const float s = sqrtf(fmaf(-4.0f * a, a, fmaf(4.0f, a, 1.0f)));
+  const float p = 3.0f - 2.0f * a, q = 1.0f + 2.0f * a;
+  w[0] = (p - s) * 0.125f;
+  w[1] = (p + s) * 0.125f;
+  w[2] = (q + s) * 0.125f;
+  w[3] = (q - s) * 0.125f;
+}
+
+__device__ __forceinline__ int cell_x(const float4& p) { return __float_as_int(p.z); }
+__device__ __forceinline__ int cell_y(const float4& p) { return __float_as_int(p.w); }
+
+__device__ __forceinline__ long long to_fix(float v) { return __float2ll_rn(v * kFixScale); }
+__device__ __forceinline__ float from_fix(long long v) { return __ll2float_rn(v) * kFixInv; }
+
+}  // namespace mc

@@ -284,50 +284,51 @@ def target_polyline(rng, H, W, n_vertices=16):
 
 def world_random(seed, side, n_fil, lengths=None, b_min=8, b_max=64, name=None, params=None,
                  amp_max=0.3, period=(50.0, 400.0)):
-    """One world of the batched/served workload: log-uniform bead counts, per
+    """One world of the batched/served workload (side: int or (H, W)): log-uniform bead counts, per
     joint drive amplitude ~U[0, amp_max], period ~U[period] steps and phase
     ~U[0, 1) cycles.  Filaments are placed by rejection sampling, or on a
     jittered lattice when the world is too crowded for it."""
     rng = np.random.default_rng(seed)
+    H, W = (side, side) if np.isscalar(side) else (int(side[0]), int(side[1]))
     if lengths is None:
         lengths = [int(round(math.exp(rng.uniform(math.log(b_min), math.log(b_max))))) for _ in range(n_fil)]
     lengths = [max(2, int(B)) for B in lengths]
     placed = None
-    if sum(lengths) * 8 <= side * side:
-        placed = place_rejection(rng, side, side, lengths, max_tries=200)
+    if sum(lengths) * 8 <= H * W:
+        placed = place_rejection(rng, H, W, lengths, max_tries=200)
     if placed is None:
-        placed = _place_dense(rng, side, lengths)
+        placed = _place_dense(rng, H, W, lengths)
     x, y, theta = placed
     _, E, J = _counts(lengths)
     theta0 = rng.uniform(-0.3, 0.3, J)
     amp = rng.uniform(0, amp_max, J)
     freq = 1.0 / rng.uniform(period[0], period[1], J)
     phase = rng.uniform(0, 1, J)
-    return _world(name or f"rand_{seed}", side, side, lengths, x, y, theta, theta0,
+    return _world(name or f"rand_{seed}", H, W, lengths, x, y, theta, theta0,
                   amp, freq, phase, params=params)
 
 
-def _place_dense(rng, side, lengths):
+def _place_dense(rng, H, W, lengths):
     """Row placement for crowded worlds: filaments laid head to tail along rows."""
     xs, ys, th = [], [], []
     pos_x, row = 0.0, 0
     rows = []
     for B in lengths:
-        if pos_x + B > side:
+        if pos_x + B > W:
             row += 1
             pos_x = 0.0
         rows.append((row, pos_x))
         pos_x += B
     n_rows = row + 1
-    assert n_rows <= side, "world too crowded"
-    pitch = side // n_rows
+    assert n_rows <= H, "world too crowded"
+    pitch = H // n_rows
     for B, (r, x0) in zip(lengths, rows):
         ox, oy = rng.uniform(0, 0.5), rng.uniform(0, 0.5)
         k = np.arange(B, dtype=np.float64)
         xs.append(x0 + ox + k)
         ys.append(np.full(B, r * pitch + oy))
         th.append(np.zeros(B - 1))
-    return _f32_wrap(np.concatenate(xs), side), _f32_wrap(np.concatenate(ys), side), \
+    return _f32_wrap(np.concatenate(xs), W), _f32_wrap(np.concatenate(ys), H), \
         np.concatenate(th).astype(np.float32)
 
 

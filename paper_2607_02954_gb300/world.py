@@ -1,0 +1,169 @@
+"""User-facing Python API over the C ABI: World, step_batched.
+
+Argument marshalling only: inputs go to mc_world_create as host (numpy) or
+device (torch CUDA tensor) pointers, every step runs in libmc's kernels, and
+outputs come back through mc_world_get_state / mc_world_get_field.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+
+from . import _lib as L
+from .synth import Params, WorldSpec
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def stream_handle(stream=None) -> ctypes.c_void_p:
+    """cudaStream_t of a torch stream (default: the current stream)."""
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def params_struct(p: Params) -> L.mc_params:
+    return L.mc_params(nu=p.nu, dt=p.dt, Lambda=p.Lambda, kappa=p.kappa, k_bend=p.k_bend,
+                       k_stretch=p.k_stretch, k_shear=p.k_shear, k_rep=p.k_rep, sigma=p.sigma,
+                       orient=p.orient, n_pbd=int(p.n_pbd))
+
+
+def default_params() -> Params:
+    c = L.mc_params()
+    L.check(L.load().mc_params_default(ctypes.byref(c)))
+    return Params(**{k: getattr(c, k) for k, _ in L.mc_params._fields_})
+
+
+_FLOAT_ARRAYS = ("x", "y", "theta", "L_rest", "theta0", "drive_amp", "drive_freq", "drive_phase")
+
+
+class World:
+    """One world resident on the GPU.
+
+    spec: a WorldSpec (host arrays).  With device=True the arrays are first
+    moved to torch CUDA tensors and handed over as device pointers, which is
+    the path the benchmark uses when inputs are already resident."""
+
+    def __init__(self, spec: WorldSpec, stream=None, device: bool = False):
+        lib = L.load()
+        self.spec = spec
+        keep = []
+        d = L.mc_world_desc()
+        d.H, d.W, d.n_fil = int(spec.H), int(spec.W), int(spec.n_fil)
+        fo = np.ascontiguousarray(spec.fil_off, dtype=np.int32)
+        keep.append(fo)
+        d.fil_off = fo.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        if device:
+            torch = _torch()
+            for name in _FLOAT_ARRAYS:
+                t = torch.as_tensor(np.ascontiguousarray(getattr(spec, name), np.float32)).cuda()
+                keep.append(t)
+                setattr(d, name, ctypes.c_void_p(t.data_ptr() if t.numel() else 0))
+            if spec.f0 is not None:
+                t = torch.as_tensor(np.ascontiguousarray(spec.f0, np.float32)).cuda()
+                keep.append(t)
+                d.f0 = ctypes.c_void_p(t.data_ptr())
+            d.mem_kind = L.MC_MEM_DEVICE
+            torch.cuda.synchronize()
+        else:
+            for name in _FLOAT_ARRAYS:
+                a = np.ascontiguousarray(getattr(spec, name), dtype=np.float32)
+                keep.append(a)
+                setattr(d, name, ctypes.c_void_p(a.ctypes.data if a.size else 0))
+            if spec.f0 is not None:
+                a = np.ascontiguousarray(spec.f0, dtype=np.float32)
+                keep.append(a)
+                d.f0 = ctypes.c_void_p(a.ctypes.data)
+            d.mem_kind = L.MC_MEM_HOST
+        d.t0 = int(spec.t0)
+        d.p = params_struct(spec.params)
+        h = ctypes.c_void_p()
+        L.check(lib.mc_world_create(ctypes.byref(d), stream_handle(stream), ctypes.byref(h)))
+        self._h = h
+        self._lib = lib
+
+    # -- life cycle ---------------------------------------------------------
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise RuntimeError("world destroyed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self._lib.mc_world_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> Dict[str, int]:
+        i = L.mc_world_info()
+        L.check(self._lib.mc_world_info_get(self.handle, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in L.mc_world_info._fields_}
+
+    # -- stepping -----------------------------------------------------------
+    def step(self, n_steps: int = 1, stream=None):
+        L.check(self._lib.mc_step(self.handle, int(n_steps), stream_handle(stream)))
+
+    def check(self, stream=None):
+        L.check(self._lib.mc_world_check(self.handle, stream_handle(stream)))
+
+    def clear_flags(self, stream=None):
+        L.check(self._lib.mc_world_clear_flags(self.handle, stream_handle(stream)))
+
+    # -- read-out -----------------------------------------------------------
+    def state(self, fluid: bool = False, stream=None) -> Dict[str, np.ndarray]:
+        """Host copies: x, y [N], theta [E], disp [N, 2], and fdev [9, H, W]
+        (populations minus rest weights) when fluid=True."""
+        s = self.spec
+        N, E = s.N, s.E
+        out = {"x": np.empty(N, np.float32), "y": np.empty(N, np.float32),
+               "theta": np.empty(E, np.float32), "disp": np.empty((N, 2), np.float32)}
+        if fluid:
+            out["fdev"] = np.empty((9, s.H, s.W), np.float32)
+        ptr = lambda k: ctypes.c_void_p(out[k].ctypes.data) if k in out and out[k].size else None
+        L.check(self._lib.mc_world_get_state(self.handle, ptr("x"), ptr("y"), ptr("theta"), ptr("disp"),
+                                             ptr("fdev"), L.MC_MEM_HOST, stream_handle(stream)))
+        return out
+
+    def state_device(self, stream=None):
+        """Device (torch) copies of x, y, theta, disp."""
+        torch = _torch()
+        s = self.spec
+        out = {"x": torch.empty(s.N, device="cuda"), "y": torch.empty(s.N, device="cuda"),
+               "theta": torch.empty(s.E, device="cuda"), "disp": torch.empty((s.N, 2), device="cuda")}
+        ptr = lambda k: ctypes.c_void_p(out[k].data_ptr()) if out[k].numel() else None
+        L.check(self._lib.mc_world_get_state(self.handle, ptr("x"), ptr("y"), ptr("theta"), ptr("disp"),
+                                             None, L.MC_MEM_DEVICE, stream_handle(stream)))
+        return out
+
+    def field(self, name: str, stream=None) -> np.ndarray:
+        """Host copy of one field of the last completed step (see mc_field)."""
+        s = self.spec
+        N, HW = s.N, s.H * s.W
+        info = self.info()
+        shapes = {"fel": ((N, 2), np.float32), "fs": ((N, 2), np.float32), "ubead": ((N, 2), np.float32),
+                  "rho_s": ((s.H, s.W), np.float32), "rho_bar": ((s.H, s.W), np.float32),
+                  "force": ((s.H, s.W, 2), np.float32), "u": ((s.H, s.W, 2), np.float32),
+                  "cell": ((N,), np.int32), "bin": ((N,), np.int32),
+                  "bin_off": ((info["n_bins"] + 1,), np.int32), "bin_beads": ((N,), np.int32)}
+        shape, dt = shapes[name]
+        out = np.empty(shape, dt)
+        L.check(self._lib.mc_world_get_field(self.handle, L.FIELDS[name], ctypes.c_void_p(out.ctypes.data),
+                                             L.MC_MEM_HOST, stream_handle(stream)))
+        return out
+
+
+def step_batched(worlds: Sequence[World], n_steps: int, stream=None):
+    """Advances distinct worlds together: one launch per stage per step."""
+    arr = (ctypes.c_void_p * len(worlds))(*[w.handle.value for w in worlds])
+    L.check(L.load().mc_step_batched(arr, len(worlds), int(n_steps), stream_handle(stream)))

@@ -1,0 +1,101 @@
+"""CPU checks of the C ABI library: it loads, exports every entry point that
+include/mc.h declares, and its host-side validation rejects bad worlds before
+touching the GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2607_02954_gb300 import _lib as L
+from paper_2607_02954_gb300 import synth
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "mc.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**(mc_[a-z0-9_]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary_calls():
+    names = declared_functions()
+    for must in ("mc_world_create", "mc_world_destroy", "mc_step", "mc_step_batched", "mc_world_get_state"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = L.load()
+    names = declared_functions()
+    assert names
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/mc.h but not exported"
+    assert set(names) == set(L.SIGNATURES), "binding signatures out of sync with include/mc.h"
+
+
+def test_defaults_match_the_frozen_constants():
+    p = L.mc_params()
+    assert L.load().mc_params_default(ctypes.byref(p)) == 0
+    ref = synth.Params()
+    for name, _ in L.mc_params._fields_:
+        assert abs(getattr(p, name) - getattr(ref, name)) < 1e-7, name
+
+
+def _desc(spec, **over):
+    from paper_2607_02954_gb300.world import params_struct
+    d = L.mc_world_desc()
+    d.H, d.W, d.n_fil = over.get("H", spec.H), over.get("W", spec.W), spec.n_fil
+    fo = np.ascontiguousarray(over.get("fil_off", spec.fil_off), np.int32)
+    keep = [fo]
+    d.fil_off = fo.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    for name in ("x", "y", "theta", "L_rest", "theta0", "drive_amp", "drive_freq", "drive_phase"):
+        a = np.ascontiguousarray(over.get(name, getattr(spec, name)), np.float32)
+        keep.append(a)
+        setattr(d, name, ctypes.c_void_p(a.ctypes.data if a.size else 0))
+    d.t0 = over.get("t0", 0)
+    d.p = params_struct(over.get("params", spec.params))
+    d.mem_kind = L.MC_MEM_HOST
+    return d, keep
+
+
+@pytest.mark.parametrize("case", ["H_not_mult8", "W_small", "short_filament", "nan_x", "bad_nu",
+                                  "bad_sigma", "neg_L", "bad_t0", "bad_npbd"])
+def test_create_rejects_invalid_worlds_on_host(case):
+    spec = synth.tiny_world(0, side=16, lengths=(5, 4))
+    over = {}
+    if case == "H_not_mult8":
+        over["H"] = 20
+    elif case == "W_small":
+        over["W"] = 0
+    elif case == "short_filament":
+        over["fil_off"] = np.array([0, 1, 9], np.int32)
+    elif case == "nan_x":
+        x = spec.x.copy()
+        x[2] = np.nan
+        over["x"] = x
+    elif case == "bad_nu":
+        over["params"] = synth.Params(nu=0.0)
+    elif case == "bad_sigma":
+        over["params"] = synth.Params(sigma=3.0)
+    elif case == "neg_L":
+        over["L_rest"] = -spec.L_rest
+    elif case == "bad_t0":
+        over["t0"] = 1 << 24
+    elif case == "bad_npbd":
+        over["params"] = synth.Params(n_pbd=65)
+    d, keep = _desc(spec, **over)
+    h = ctypes.c_void_p()
+    lib = L.load()
+    status = lib.mc_world_create(ctypes.byref(d), None, ctypes.byref(h))
+    assert status == 1, (case, status, lib.mc_last_error())
+    assert h.value is None
+    assert lib.mc_last_error()
+
+
+def test_step_rejects_null_world():
+    lib = L.load()
+    assert lib.mc_step(None, 1, None) == 1
+    assert lib.mc_step_batched(None, 1, 1, None) == 1

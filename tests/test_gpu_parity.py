@@ -1,0 +1,238 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances: cell, bin and bin-offset indices bit-exact (computed on identical
+float32 positions); per-step forces, densities and velocities within 1e-5 of
+the field's largest magnitude; bead positions within 1e-4 cells after 100
+steps.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2607_02954_gb300 import synth
+from tests.helpers import assert_field, oracle_one_step, periodic_diff, t2n
+
+pytestmark = pytest.mark.gpu
+
+RTOL_STEP = 1e-5
+
+
+def fel_floor(spec):
+    """Absolute accuracy floor of the elastic force in FP32: each PBD pass
+    corrects unit-length edge vectors whose float32 resolution is 2^-23, and
+    the force is kappa/dt times the summed corrections.  Matters only when
+    the whole world is close to rest (tiny forces)."""
+    p = spec.params
+    return p.kappa / p.dt * max(p.n_pbd, 1) * 2.0 ** -23
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_02954_gb300 import World  # noqa: F401  (loads libmc)
+    yield
+
+
+def _gpu_world(spec):
+    from paper_2607_02954_gb300 import World
+    return World(spec)
+
+
+def _compare_one_step(spec, rtol=RTOL_STEP):
+    ow, st0, st1, rec = oracle_one_step(spec)
+    gw = _gpu_world(spec)
+    gw.step(1)
+    gw.check()
+    H, W = spec.H, spec.W
+    out = {}
+    out["fel"] = assert_field("F_el", gw.field("fel"), t2n(rec["F_el"]), rtol, floor=fel_floor(spec))
+    out["fs"] = assert_field("F_s", gw.field("fs"), t2n(rec["F_s"]), rtol)
+    out["rho_s"] = assert_field("rho_s", gw.field("rho_s"), t2n(rec["rho_s"]), rtol)
+    out["rho_bar"] = assert_field("rho_bar", gw.field("rho_bar"), t2n(rec["rho_bar"]), rtol)
+    out["force"] = assert_field("F", gw.field("force"), t2n(rec["F"]).transpose(1, 2, 0), rtol)
+    out["u"] = assert_field("u", gw.field("u"), t2n(rec["u"]).transpose(1, 2, 0), rtol)
+    out["U"] = assert_field("U", gw.field("ubead"), t2n(rec["U"]), rtol)
+    s = gw.state(fluid=True)
+    X1 = t2n(st1.X)
+    if spec.N:
+        dx = periodic_diff(s["x"], X1[:, 0], W)
+        dy = periodic_diff(s["y"], X1[:, 1], H)
+        # returned coordinates are float32: allow their rounding (half an ulp of the box size)
+        tol = float(np.spacing(np.float32(max(H, W)))) + 1e-6
+        assert np.max(np.abs(dx)) < tol and np.max(np.abs(dy)) < tol
+    out["theta"] = assert_field("theta", s["theta"], t2n(st1.theta), 1e-6)
+    out["disp"] = assert_field("disp", s["disp"], t2n(st1.D), rtol)
+    fdev_want = t2n(st1.f - O.d2q9_weights()[:, None, None])
+    out["fdev"] = assert_field("fdev", s["fdev"], fdev_want, rtol)
+    assert gw.info()["t"] == spec.t0 + 1
+    gw.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# a2: cell and bin indices, bit-exact.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("maker", ["c1", "ragged", "tiny8", "edges"])
+def test_cell_and_bin_indices_bit_exact(maker):
+    if maker == "c1":
+        spec = synth.world_c1(0)
+    elif maker == "ragged":
+        spec = synth.world_random(3, (40, 72), 6)   # ragged 8-cell tiles on both axes
+    elif maker == "tiny8":
+        spec = synth.tiny_world(2, side=8, lengths=(3, 2))
+    else:
+        spec = synth.world_c1(1)
+        # beads on integer coordinates and just below the periodic edge
+        spec.x[:8] = np.float32(np.arange(8))
+        spec.x[8:12] = np.nextafter(np.float32(spec.W), np.float32(0))
+        spec.y[12:16] = np.float32(0.0)
+    gw = _gpu_world(spec)
+    cell_w, bin_w, off_w = O.cell_and_bin(spec.x, spec.y, spec.H, spec.W, gw.info()["tile"])
+    assert np.array_equal(gw.field("cell"), cell_w)
+    gw.step(1)
+    assert np.array_equal(gw.field("bin"), bin_w)
+    off = gw.field("bin_off")
+    assert np.array_equal(off, off_w)
+    beads = gw.field("bin_beads")
+    for b in range(len(off) - 1):
+        got = np.sort(beads[off[b]:off[b + 1]])
+        want = np.sort(np.nonzero(bin_w == b)[0])
+        assert np.array_equal(got, want), b
+    gw.close()
+
+
+# ---------------------------------------------------------------------------
+# a1-a8: every stage of one step from identical inputs.
+# ---------------------------------------------------------------------------
+def test_one_step_c1():
+    _compare_one_step(synth.world_c1(0))
+
+
+def test_one_step_random_fluid_and_late_drive():
+    spec = synth.world_c1(5)
+    rng = np.random.default_rng(9)
+    spec.f0 = synth.random_populations(rng, spec.H, spec.W, 2e-3)
+    spec.t0 = 12345
+    _compare_one_step(spec)
+
+
+@pytest.mark.parametrize("case", ["tiny8", "ragged", "single_dimer", "no_filaments", "long_filament",
+                                  "custom_params", "dense_rows"])
+def test_one_step_edge_cases(case):
+    rng = np.random.default_rng(1)
+    if case == "tiny8":
+        spec = synth.tiny_world(4, side=8, lengths=(3, 2))
+    elif case == "ragged":
+        spec = synth.world_random(7, (40, 72), 5)
+    elif case == "single_dimer":
+        spec = synth._world("dimer", 16, 24, [2], np.array([23.7, 0.6], np.float32), np.array([15.9, 0.2], np.float32),
+                            np.array([0.3], np.float32), np.zeros(0), np.zeros(0), np.zeros(0), np.zeros(0))
+    elif case == "no_filaments":
+        spec = synth._world("fluid", 24, 16, [], np.zeros(0, np.float32), np.zeros(0, np.float32),
+                            np.zeros(0, np.float32), np.zeros(0), np.zeros(0), np.zeros(0), np.zeros(0))
+        spec.f0 = synth.random_populations(rng, 24, 16, 1e-3)
+    elif case == "long_filament":
+        spec = synth.world_random(11, 256, 2, lengths=[1500, 40])
+    elif case == "custom_params":
+        spec = synth.world_c1(2)
+        spec.params = synth.Params(nu=0.5, Lambda=3.0 / 16.0, kappa=0.2, k_bend=0.8, k_stretch=0.9,
+                                   k_shear=0.6, k_rep=1.5, sigma=1.7, orient=0.0, n_pbd=7)
+    else:
+        spec = synth.world_rows(256, 4096, seed=3)
+    _compare_one_step(spec)
+
+
+def test_one_step_c2_full_size():
+    """512 x 512 grid with 262,144 beads: the whole step against the oracle."""
+    _compare_one_step(synth.world_c2(0))
+
+
+# ---------------------------------------------------------------------------
+# 100-step rollout (positions within 1e-4 cells).
+# ---------------------------------------------------------------------------
+def test_rollout_100_steps_c1():
+    spec = synth.world_c1(0)
+    ow = O.World(spec)
+    st = O.rollout(ow, 100)
+    gw = _gpu_world(spec)
+    gw.step(100)
+    gw.check()
+    s = gw.state()
+    X = t2n(st.X)
+    err = max(np.max(np.abs(periodic_diff(s["x"], X[:, 0], spec.W))),
+              np.max(np.abs(periodic_diff(s["y"], X[:, 1], spec.H))))
+    assert err < 1e-4, err
+    assert np.max(np.abs(s["disp"] - t2n(st.D))) < 1e-4
+    assert gw.info()["t"] == 100
+    gw.close()
+
+
+# ---------------------------------------------------------------------------
+# Batched and alone give bitwise identical worlds.
+# ---------------------------------------------------------------------------
+def test_batched_equals_alone_bitwise():
+    from paper_2607_02954_gb300 import step_batched
+    specs = [synth.world_random(s, side, nf) for s, side, nf in
+             [(1, 64, 3), (2, 128, 17), (3, 64, 1), (4, 256, 40), (5, 128, 8)]]
+    alone = []
+    for sp in specs:
+        w = _gpu_world(sp)
+        w.step(37)
+        alone.append(w.state(fluid=True))
+        w.close()
+    ws = [_gpu_world(sp) for sp in specs]
+    step_batched(ws, 20)
+    step_batched(ws, 17)
+    for w, a in zip(ws, alone):
+        b = w.state(fluid=True)
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
+        assert w.info()["t"] == 37
+        w.close()
+
+
+def test_graph_replay_equals_direct_steps_bitwise():
+    spec = synth.world_c1(3)
+    a = _gpu_world(spec)
+    for _ in range(20):
+        a.step(1)            # direct launches
+    b = _gpu_world(spec)
+    b.step(20)               # one 16-step graph replay + 4 direct steps
+    sa, sb = a.state(fluid=True), b.state(fluid=True)
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
+    a.close()
+    b.close()
+
+
+def test_device_inputs_equal_host_inputs():
+    from paper_2607_02954_gb300 import World
+    spec = synth.world_c1(6)
+    a, b = World(spec), World(spec, device=True)
+    a.step(5)
+    b.step(5)
+    sa, sb = a.state(fluid=True), b.state(fluid=True)
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
+
+
+def test_watchdog_flags_runaway_velocity():
+    """A fluid moving faster than the watchdog limit is reported, and the
+    world's other results stay finite; a calm world passes."""
+    spec = synth.tiny_world(0, side=16, lengths=(4,))
+    H, W = spec.H, spec.W
+    feq = O.equilibrium(torch.ones(H, W, dtype=torch.float64), torch.full((H, W), 0.6, dtype=torch.float64),
+                        torch.zeros(H, W, dtype=torch.float64))
+    spec.f0 = t2n(feq - O.d2q9_weights()[:, None, None]).astype(np.float32)
+    from paper_2607_02954_gb300._lib import MCError
+    w = _gpu_world(spec)
+    w.step(1)
+    with pytest.raises(MCError) as ei:
+        w.check()
+    assert ei.value.status == 5
+    w.clear_flags()
+    calm = _gpu_world(synth.tiny_world(0, side=16, lengths=(4,)))
+    calm.step(3)
+    calm.check()
