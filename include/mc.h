@@ -169,6 +169,26 @@ mc_status mc_step_stage(mc_world* w, int stage, void* stream);
 mc_status mc_world_get_state(const mc_world* w, float* x, float* y, float* theta, float* disp,
                              float* fdev, int mem_kind, void* stream);
 
+/* Allocation-free read-out of the bead positions into host memory.
+ * The paper has no counterpart: this is a library service.  It returns the
+ * same x, y as mc_world_get_state, for callers that cannot allocate device
+ * memory while reading results (mc_world_get_state allocates a device
+ * staging buffer per call): processes whose device memory is fully reserved
+ * by another allocator or capped by a fixed budget, and latency-critical
+ * loops where cudaMalloc / cudaFree may synchronize the device.
+ *   x, y    [N] host buffers (pageable or pinned) receiving wrapped positions
+ *   stream  the call enqueues a kernel and two copies on it, then
+ *           synchronizes it before returning
+ * Staging uses a file-scope device array sized for 2^20 beads (8 MiB) that
+ * every GPU loading the library holds until the process exits.  The first
+ * call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream
+ * capture.  All calls share the array: calls whose GPU work overlaps (for
+ * example on different streams) race on it.
+ * Errors: MC_ERR_INVALID_ARG for NULL arguments or a world with more than
+ * 2^20 beads (nothing is enqueued), MC_ERR_CUDA for a failed CUDA call. */
+mc_status mc_world_get_positions_noalloc(const mc_world* w, float* x, float* y, void* stream);
+
 /* Fields of the last completed step, for inspection and parity tests. */
 typedef enum mc_field {
   MC_FIELD_FEL = 0,      /* [2N] elastic force per bead (a3) */

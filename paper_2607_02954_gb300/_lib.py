@@ -62,6 +62,7 @@ SIGNATURES = {
     "mc_step_batched": (_i, [ctypes.POINTER(_vp), _i, _i, _vp]),
     "mc_step_stage": (_i, [_vp, _i, _vp]),
     "mc_world_get_state": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, _vp]),
+    "mc_world_get_positions_noalloc": (_i, [_vp, _vp, _vp, _vp]),
     "mc_world_get_field": (_i, [_vp, _i, _vp, _i, _vp]),
     "mc_world_check": (_i, [_vp, _vp]),
     "mc_world_clear_flags": (_i, [_vp, _vp]),

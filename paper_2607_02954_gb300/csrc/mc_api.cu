@@ -607,3 +607,8 @@ mc_status mc_world_clear_flags(mc_world* w, void* stream) {
 }
 
 }  // extern "C"
+
+namespace mc {
+const WorldDev& world_dev(const mc_world* w) { return w->h; }
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace mc

@@ -94,6 +94,10 @@ void launch_stream_out(const float* g_src, float* out, int H, int W, cudaStream_
 void launch_positions_out(const WorldDev& w, float* x, float* y, cudaStream_t s);
 void launch_cells_out(const WorldDev& w, int* cell, cudaStream_t s);
 
+// --- host accessors for code outside the ABI translation unit ------------
+const WorldDev& world_dev(const mc_world* w);
+void set_last_error(const char* msg);
+
 // --- device helpers -------------------------------------------------------
 __device__ __forceinline__ int wrap_once(int v, int n) {
   // v in [-n, 2n): one conditional correction maps it into [0, n)
