@@ -37,7 +37,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-STAGES = ["pbd", "bin_scan", "bin_scatter", "deposit", "blur", "force_spread", "lbm", "interp_advance"]
+STAGES = ["pbd", "bin_scan", "bin_scatter", "deposit_x", "force_spread", "lbm", "interp_advance"]
 LBM_BYTES_PER_CELL = 88          # read f 36 + F 8, write f' 36 + u 8
 STEP_BYTES_PER_CELL = 112        # grid traffic per step of the minimal fused form
 STEP_BYTES_PER_BEAD = 32
@@ -299,7 +299,7 @@ def main():
                    "l2": "state 1.8 GB > L2: no flush needed" if C >= 4096 * 4096 else "state may fit in L2; per-step timing includes no flush"},
         "e2e": {"value": e2e_val, "unit": "particle-steps/s", "steps": e2e_steps,
                 "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps},
-        "gpu_launches": args.steps * len(STAGES),
+        "gpu_launches": args.steps * (len(STAGES) + 1),   # the scan stage is two kernels
         "roofline": {"bound": "hbm", "kernel": "k_lbm", "achieved": lbm_gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": lbm_gbs / hbm_peak, "peak_kind": peak_kind, "traffic": None,
                      "algorithmic_bytes_per_launch": lbm_bytes, "launch_ms": stage_ms["lbm"]},

@@ -5,7 +5,7 @@
  * elastic bead chains (filaments) immersed in a 2D periodic viscous fluid.
  * One time step (Methods and Fields sections, Fluid-filament Interaction):
  *   a1 rest-angle drive      theta_rest,j(t) = theta0_j + A_j sin(2 pi (freq_j t + phase_j))
- *   a2 cell / bin indexing   counting sort of beads by 32x32-cell tile
+ *   a2 cell / bin indexing   counting sort of beads by 8x8-cell bin (row-major)
  *   a3 PBD                   n_pbd x (bending pass Eq. 1, position pass Eqs. 2-4);
  *                            elastic force F_el = kappa (x_hat - X) / dt
  *   a4 steric deposit        rho_s(c) = sum_i delta_h(c - X_i)
@@ -30,7 +30,7 @@
  *    [9][H][W] in the D2Q9 order c = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),
  *    (-1,1),(-1,-1),(1,-1).
  *  - Filaments are linear chains: filament f owns beads fil_off[f] ..
- *    fil_off[f+1]-1 (at least 2 beads); it owns B_f - 1 edges and B_f - 2
+ *    fil_off[f+1]-1 (2 to 3072 beads); it owns B_f - 1 edges and B_f - 2
  *    joints, numbered consecutively across filaments (edge e joins beads
  *    (a, a+1) of one filament; joint j sits between two consecutive edges).
  *    N = fil_off[n_fil], E = N - n_fil, J = N - 2 n_fil.
@@ -116,7 +116,7 @@ typedef struct mc_world mc_world;
 
 typedef struct mc_world_info {
   int H, W, n_fil, N, E, J;
-  int tile, n_bins;      /* binning tile edge (cells) and number of bins */
+  int bin_edge, n_bins;  /* bin edge in cells (8) and number of bins (H W / 64) */
   int64_t t;             /* step counter after all enqueued steps */
   size_t device_bytes;   /* device memory held by the world */
 } mc_world_info;
@@ -150,14 +150,14 @@ mc_status mc_step_batched(mc_world* const* worlds, int n_worlds, int n_steps, vo
 
 /* Enqueues one stage of the next step on `stream` (for per-stage timing).
  * Stages: 0 drive + PBD + elastic force + bin histogram (a1-a3), 1 bin
- * offsets, 2 bin scatter (a2), 3 steric deposit (a4), 4 Gaussian filter (a5),
- * 5 steric force + spread (a6), 6 LBM (a7), 7 interpolation + advance (a8).
- * Enqueuing stages 0..7 in order is exactly one mc_step(w, 1) without the
- * graph; any other use leaves the world in an unspecified state.  The step
- * counter advances with stage 7.  Errors: MC_ERR_INVALID_ARG for an unknown
- * stage. */
+ * offsets (two kernels), 2 bin scatter (a2), 3 steric deposit + x pass of
+ * the Gaussian filter (a4, a5), 4 y pass + steric force + spread (a5, a6),
+ * 5 LBM (a7), 6 interpolation + advance (a8).  Enqueuing stages 0..6 in
+ * order is exactly one mc_step(w, 1) without the graph; any other use leaves
+ * the world in an unspecified state.  The step counter advances with
+ * stage 6.  Errors: MC_ERR_INVALID_ARG for an unknown stage. */
 mc_status mc_step_stage(mc_world* w, int stage, void* stream);
-#define MC_N_STAGES 8
+#define MC_N_STAGES 7
 
 /* Copies the state after the enqueued steps.  Any output may be NULL.
  *   x, y      [N] wrapped bead positions
@@ -194,12 +194,12 @@ typedef enum mc_field {
   MC_FIELD_FEL = 0,      /* [2N] elastic force per bead (a3) */
   MC_FIELD_FS = 1,       /* [2N] steric force per bead (a6) */
   MC_FIELD_UBEAD = 2,    /* [2N] interpolated velocity per bead (a8) */
-  MC_FIELD_RHO_S = 3,    /* [H*W] deposited steric density (a4) */
-  MC_FIELD_RHO_BAR = 4,  /* [H*W] filtered density (a5) */
+  MC_FIELD_RHO_S = 3,    /* [H*W] deposited steric density (a4), recomputed on request */
+  MC_FIELD_RHO_BAR = 4,  /* [H*W] filtered density (a5), recomputed on request */
   MC_FIELD_FORCE = 5,    /* [2*H*W] interleaved (Fx, Fy) spread force density (a6) */
   MC_FIELD_U = 6,        /* [2*H*W] interleaved (ux, uy) fluid velocity (a7) */
   MC_FIELD_CELL = 7,     /* [N] int32 cell index (floor(y) mod H) W + (floor(x) mod W) (a2) */
-  MC_FIELD_BIN = 8,      /* [N] int32 bin (tile) index of each bead (a2) */
+  MC_FIELD_BIN = 8,      /* [N] int32 bin index (floor(y)/8) (W/8) + floor(x)/8 of each bead (a2) */
   MC_FIELD_BIN_OFF = 9,  /* [n_bins + 1] int32 exclusive prefix sum of beads per bin (a2) */
   MC_FIELD_BIN_BEADS = 10 /* [N] int32 bead ids in bin order (order inside a bin unspecified) */
 } mc_field;

@@ -47,7 +47,7 @@ class mc_world_desc(ctypes.Structure):
 
 class mc_world_info(ctypes.Structure):
     _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("n_fil", ctypes.c_int), ("N", ctypes.c_int),
-                ("E", ctypes.c_int), ("J", ctypes.c_int), ("tile", ctypes.c_int), ("n_bins", ctypes.c_int),
+                ("E", ctypes.c_int), ("J", ctypes.c_int), ("bin_edge", ctypes.c_int), ("n_bins", ctypes.c_int),
                 ("t", ctypes.c_int64), ("device_bytes", ctypes.c_size_t)]
 
 

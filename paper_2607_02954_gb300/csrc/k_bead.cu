@@ -5,7 +5,17 @@
 
 namespace mc {
 
-constexpr int kPbdFloatsPerBead = 10;
+constexpr int kPbdFloatsPerBead = 18;
+
+__device__ __forceinline__ void cpa16(void* sdst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cpa4(void* sdst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // a1: theta_rest = theta0 + A sin(2 pi (freq t + phase)).  The phase in
 // cycles is reduced exactly: hi + lo = freq * t (two-product via FMA), and
@@ -29,7 +39,7 @@ __device__ __forceinline__ float drive_angle(const float4 d, long long t) {
 // whatever the magnitude of the coordinates.
 __global__ void __launch_bounds__(256) k_pbd(const WorldDev* __restrict__ worlds,
                                              const int2* __restrict__ items, int n_items, int maxB) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(16) float smem[];   // maxB is a multiple of 4: float4 slices stay aligned
   const int wpb = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int item = blockIdx.x * wpb + warp;
@@ -52,20 +62,29 @@ __global__ void __launch_bounds__(256) k_pbd(const WorldDev* __restrict__ worlds
   float* dly = s + 7 * maxB;
   float* thr = s + 8 * maxB;
   float* C = s + 9 * maxB;
+  float4* P = reinterpret_cast<float4*>(s + 10 * maxB);    // bead positions
+  float4* D = reinterpret_cast<float4*>(s + 14 * maxB);    // joint drive parameters
   const long long t = *w.t;
   const int W = w.W, H = w.H;
 
+  // stage the filament's inputs in shared memory, every copy in flight at once
+  for (int i = lane; i < B; i += 32) cpa16(&P[i], &w.pos[b0 + i]);
   for (int e = lane; e < nE; e += 32) {
-    const float4 pa = w.pos[b0 + e], pb = w.pos[b0 + e + 1];
+    cpa4(&th[e], &w.theta[e0 + e]);
+    cpa4(&Lr[e], &w.L_rest[e0 + e]);
+  }
+  for (int j = lane; j < nJ; j += 32) cpa16(&D[j], &w.drive[j0 + j]);
+  cpa_wait_all();
+  __syncwarp();
+  for (int e = lane; e < nE; e += 32) {
+    const float4 pa = P[e], pb = P[e + 1];
     int dcx = cell_x(pb) - cell_x(pa), dcy = cell_y(pb) - cell_y(pa);
     if (2 * dcx > W) dcx -= W; else if (2 * dcx < -W) dcx += W;
     if (2 * dcy > H) dcy -= H; else if (2 * dcy < -H) dcy += H;
     vx[e] = (float)dcx + (pb.x - pa.x);
     vy[e] = (float)dcy + (pb.y - pa.y);
-    th[e] = w.theta[e0 + e];
-    Lr[e] = w.L_rest[e0 + e];
   }
-  for (int j = lane; j < nJ; j += 32) thr[j] = drive_angle(w.drive[j0 + j], t);
+  for (int j = lane; j < nJ; j += 32) thr[j] = drive_angle(D[j], t);
   for (int i = lane; i < B; i += 32) {
     dlx[i] = 0.0f;
     dly[i] = 0.0f;
@@ -111,20 +130,27 @@ __global__ void __launch_bounds__(256) k_pbd(const WorldDev* __restrict__ worlds
   }
   for (int e = lane; e < nE; e += 32) w.theta[e0 + e] = th[e];
 
-  // elastic force F_el = kappa (x_hat - X) / dt, and the bin histogram (a2)
+  // elastic force F_el = kappa (x_hat - X) / dt, and the 8x8-bin histogram (a2)
   // with one atomic per group of lanes sharing a bin
+  float fmax = 0.0f;
   for (int i0 = 0; i0 < B; i0 += 32) {
     const int i = i0 + lane;
     int bin = -1 - lane;
     if (i < B) {
-      w.fel[b0 + i] = make_float2(w.kappa_dt * dlx[i], w.kappa_dt * dly[i]);
-      const float4 p = w.pos[b0 + i];
-      bin = (cell_y(p) / w.tile) * w.ntx + cell_x(p) / w.tile;
+      const float2 fe = make_float2(w.kappa_dt * dlx[i], w.kappa_dt * dly[i]);
+      w.fel[b0 + i] = fe;
+      fmax = fmaxf(fmax, fmaxf(fabsf(fe.x), fabsf(fe.y)));
+      const float4 p = P[i];
+      bin = (cell_y(p) / kBin) * w.nbx + cell_x(p) / kBin;
       w.bead_bin[b0 + i] = bin;
     }
     const unsigned peers = __match_any_sync(0xffffffffu, bin);
     if (i < B && (__ffs(peers) - 1) == lane) atomicAdd(&w.bin_count[bin], __popc(peers));
   }
+  // largest |F_el| component of the world this step (bounds the spread's
+  // fixed-point scale); non-negative floats order like their bit patterns
+  for (int o = 16; o > 0; o >>= 1) fmax = fmaxf(fmax, __shfl_xor_sync(0xffffffffu, fmax, o));
+  if (lane == 0) atomicMax(&w.fel_max[t & 1], __float_as_uint(fmax));
 }
 
 // a2: scatter bead records into bin order.  Lanes of one warp that share a
@@ -158,7 +184,11 @@ __global__ void __launch_bounds__(kBeadChunk) k_interp_advance(const WorldDev* _
                                                                const int2* __restrict__ items) {
   const int2 it = items[blockIdx.x];
   const WorldDev& w = worlds[it.x];
-  if (it.y == 0 && threadIdx.x == 0) *w.t += 1;
+  if (it.y == 0 && threadIdx.x == 0) {
+    const long long t = *w.t + 1;
+    *w.t = t;
+    w.fel_max[t & 1] = 0u;   // slot of the next step; this step's stays readable
+  }
   const int i = it.y + threadIdx.x;
   if (i >= w.N) return;
   const int W = w.W, H = w.H;
@@ -266,13 +296,14 @@ static int pbd_warps_per_block(int maxB) {
 
 void launch_pbd(const Plan& p, cudaStream_t s) {
   if (p.n_fil_items == 0) return;
-  const int wpb = pbd_warps_per_block(p.max_B);
-  const size_t smem = (size_t)wpb * p.max_B * kPbdFloatsPerBead * sizeof(float);
+  const int mb = (p.max_B + 3) & ~3;
+  const int wpb = pbd_warps_per_block(mb);
+  const size_t smem = (size_t)wpb * mb * kPbdFloatsPerBead * sizeof(float);
   if (smem > 48 * 1024) {
     cudaFuncSetAttribute(k_pbd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
   const int grid = (p.n_fil_items + wpb - 1) / wpb;
-  k_pbd<<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, p.max_B);
+  k_pbd<<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
 }
 
 void launch_bin_scatter(const Plan& p, cudaStream_t s) {

@@ -1,273 +1,84 @@
-// Grid-side stages of one time step: bin offsets (a2), binned steric
-// deposit (a4), Gaussian filter (a5), steric force + IB force spread (a6) and
-// the fused D2Q9 TRT collide + stream (a7).
+// Grid-side stages of one time step: bin offsets (a2) and the fused D2Q9 TRT
+// collide + stream (a7).  The steric and spread stages (a4-a6) are in
+// k_steric.cu, the bead stages in k_bead.cu.
 #include "mc_internal.cuh"
 
 namespace mc {
 
 // ---------------------------------------------------------------------------
-// a2: exclusive prefix sum of the per-bin counts, one block per world.  Also
-// resets the counts for the next step and primes the scatter cursors.
+// a2: exclusive prefix sum of the per-bin bead counts, in blocks of
+// kScanChunk bins: k_scan_sums adds up each block, k_scan_apply offsets each
+// block by the sum of the world's earlier blocks and scans it.  Also resets
+// the counts for the next step and primes the scatter cursors.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_bin_scan(const WorldDev* __restrict__ worlds) {
-  const WorldDev& w = worlds[blockIdx.x];
-  __shared__ int warp_tot[32];
-  __shared__ int carry_s;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+__device__ __forceinline__ int block_sum_256(int v, int* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  int t = threadIdx.x < 8 ? red[threadIdx.x] : 0;
+  if (threadIdx.x < 32) {
+    for (int o = 4; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) red[8] = t;
+  }
+  __syncthreads();
+  const int r = red[8];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(256) k_scan_sums(const WorldDev* __restrict__ worlds,
+                                                   const int2* __restrict__ items) {
+  __shared__ int red[9];
+  const int2 it = items[blockIdx.x];
+  const WorldDev& w = worlds[it.x];
+  const int base = it.y * kScanChunk;
+  const int end = min(base + kScanChunk, w.n_bins);
+  int s = 0;
+  for (int k = base + threadIdx.x; k < end; k += blockDim.x) s += w.bin_count[k];
+  s = block_sum_256(s, red);
+  if (threadIdx.x == 0) w.chunk_sum[it.y] = s;
+}
+
+__global__ void __launch_bounds__(256) k_scan_apply(const WorldDev* __restrict__ worlds,
+                                                    const int2* __restrict__ items) {
+  __shared__ int red[9];
+  __shared__ int warp_tot[8];
+  const int2 it = items[blockIdx.x];
+  const WorldDev& w = worlds[it.x];
+  int pre = 0;
+  for (int k = threadIdx.x; k < it.y; k += blockDim.x) pre += w.chunk_sum[k];
+  pre = block_sum_256(pre, red);
   const int n = w.n_bins;
-  int carry = 0;
-  for (int base = 0; base < n; base += 1024) {
-    const int k = base + tid;
-    const int v = k < n ? w.bin_count[k] : 0;
-    int incl = v;
+  const int base = it.y * kScanChunk + threadIdx.x * 4;
+  int v[4];
+  int tsum = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    if (lane == 31) warp_tot[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-      int t = warp_tot[lane];
+  for (int j = 0; j < 4; ++j) {
+    v[j] = base + j < n ? w.bin_count[base + j] : 0;
+    tsum += v[j];
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int incl = tsum;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, t, o);
-        if (lane >= o) t += y;
-      }
-      warp_tot[lane] = t;   // inclusive over warps
-    }
-    __syncthreads();
-    const int warp_base = wid > 0 ? warp_tot[wid - 1] : 0;
-    const int excl = carry + warp_base + incl - v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  int wbase = 0;
+  for (int k = 0; k < wid; ++k) wbase += warp_tot[k];
+  int run = pre + wbase + incl - tsum;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int k = base + j;
     if (k < n) {
-      w.bin_off[k] = excl;
-      w.bin_cursor[k] = excl;
+      w.bin_off[k] = run;
+      w.bin_cursor[k] = run;
       w.bin_count[k] = 0;
+      run += v[j];
+      if (k == n - 1) w.bin_off[n] = run;
     }
-    if (tid == 1023) carry_s = carry + warp_tot[31];
-    __syncthreads();
-    carry = carry_s;
-    __syncthreads();
-  }
-  if (tid == 0) w.bin_off[n] = carry;
-}
-
-// ---------------------------------------------------------------------------
-// Tile geometry shared by the tile kernels.  A tile is a kTile x kTile block
-// of cells (ragged at the high edges); its beads are the beads of its bin.
-// ---------------------------------------------------------------------------
-struct TileGeom {
-  int tx, ty, x0, y0, tw, th;
-  int dx_lo, dx_hi, dy_lo, dy_hi;   // neighbour bin offsets, each bin once
-};
-
-__device__ __forceinline__ void nb_range(int nt, int& lo, int& hi) {
-  if (nt == 1) { lo = 0; hi = 0; }
-  else if (nt == 2) { lo = 0; hi = 1; }
-  else { lo = -1; hi = 1; }
-}
-
-__device__ __forceinline__ TileGeom tile_geom(const WorldDev& w, int tile) {
-  TileGeom g;
-  g.tx = tile % w.ntx;
-  g.ty = tile / w.ntx;
-  g.x0 = g.tx * w.tile;
-  g.y0 = g.ty * w.tile;
-  g.tw = min(w.tile, w.W - g.x0);
-  g.th = min(w.tile, w.H - g.y0);
-  nb_range(w.ntx, g.dx_lo, g.dx_hi);
-  nb_range(w.nty, g.dy_lo, g.dy_hi);
-  return g;
-}
-
-__device__ __forceinline__ int nb_bin(const WorldDev& w, const TileGeom& g, int ddx, int ddy) {
-  return wrap_once(g.ty + ddy, w.nty) * w.ntx + wrap_once(g.tx + ddx, w.ntx);
-}
-
-// Local tile coordinate of the four stencil cells c-1 .. c+2 along one axis,
-// or -1 for cells outside the tile.  c in [0, n), o in [0, n).
-__device__ __forceinline__ bool stencil_in_tile(int c, int o, int tw, int n, int l[4]) {
-  bool any = false;
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int v = wrap_once(c - 1 + a - o, n);
-    l[a] = v < tw ? v : -1;
-    any |= v < tw;
-  }
-  return any;
-}
-
-// ---------------------------------------------------------------------------
-// a4: rho_s(c) = sum_i delta_h(c - X_i).  One block per tile gathers the
-// beads of its 3x3 bin neighbourhood, accumulates the stencil weights that
-// fall inside the tile in shared memory (64-bit fixed point), and writes
-// every cell of the tile once.  No global atomics and no zeroing pass.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_deposit(const WorldDev* __restrict__ worlds,
-                                                 const int2* __restrict__ items) {
-  __shared__ unsigned long long acc[kTile * kTile];
-  const int2 it = items[blockIdx.x];
-  const WorldDev& w = worlds[it.x];
-  const TileGeom g = tile_geom(w, it.y);
-  for (int c = threadIdx.x; c < kTile * kTile; c += blockDim.x) acc[c] = 0ull;
-  __syncthreads();
-  for (int ddy = g.dy_lo; ddy <= g.dy_hi; ++ddy)
-    for (int ddx = g.dx_lo; ddx <= g.dx_hi; ++ddx) {
-      const int nb = nb_bin(w, g, ddx, ddy);
-      const int k1 = w.bin_off[nb + 1];
-      for (int k = w.bin_off[nb] + threadIdx.x; k < k1; k += blockDim.x) {
-        const float4 p = w.spos[k];
-        int lx[4], ly[4];
-        if (!stencil_in_tile(cell_x(p), g.x0, g.tw, w.W, lx)) continue;
-        if (!stencil_in_tile(cell_y(p), g.y0, g.th, w.H, ly)) continue;
-        float wx[4], wy[4];
-        peskin4(p.x, wx);
-        peskin4(p.y, wy);
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          if (ly[b] < 0) continue;
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            if (lx[a] < 0) continue;
-            atomicAdd(&acc[ly[b] * kTile + lx[a]], (unsigned long long)to_fix(wx[a] * wy[b]));
-          }
-        }
-      }
-    }
-  __syncthreads();
-  for (int c = threadIdx.x; c < g.tw * g.th; c += blockDim.x) {
-    const int ly = c / g.tw, lx = c - ly * g.tw;
-    w.rho_s[(g.y0 + ly) * w.W + g.x0 + lx] = from_fix((long long)acc[ly * kTile + lx]);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// a5: rho_bar = sum_m g_m rho_s(. - m e_x), then along y; periodic, taps
-// normalised and truncated at R.  One block per tile with an R-cell halo.
-// ---------------------------------------------------------------------------
-constexpr int kBlurIn = kTile + 2 * kMaxR;
-
-__global__ void __launch_bounds__(256) k_blur(const WorldDev* __restrict__ worlds,
-                                              const int2* __restrict__ items) {
-  __shared__ float in[kBlurIn * kBlurIn];
-  __shared__ float mid[kBlurIn * kTile];
-  const int2 it = items[blockIdx.x];
-  const WorldDev& w = worlds[it.x];
-  const TileGeom g = tile_geom(w, it.y);
-  const int R = w.R;
-  const int iw = g.tw + 2 * R, ih = g.th + 2 * R;
-  for (int c = threadIdx.x; c < iw * ih; c += blockDim.x) {
-    const int ly = c / iw, lx = c - ly * iw;
-    const int gy = wrap_once(g.y0 - R + ly, w.H), gx = wrap_once(g.x0 - R + lx, w.W);
-    in[ly * kBlurIn + lx] = w.rho_s[gy * w.W + gx];
-  }
-  __syncthreads();
-  for (int c = threadIdx.x; c < g.tw * ih; c += blockDim.x) {
-    const int ly = c / g.tw, lx = c - ly * g.tw;
-    float s = 0.0f;
-    for (int m = 0; m <= 2 * R; ++m) s = fmaf(w.taps[m], in[ly * kBlurIn + lx + m], s);
-    mid[ly * kTile + lx] = s;
-  }
-  __syncthreads();
-  for (int c = threadIdx.x; c < g.tw * g.th; c += blockDim.x) {
-    const int ly = c / g.tw, lx = c - ly * g.tw;
-    float s = 0.0f;
-    for (int m = 0; m <= 2 * R; ++m) s = fmaf(w.taps[m], mid[(ly + m) * kTile + lx], s);
-    w.rho_b[(g.y0 + ly) * w.W + g.x0 + lx] = s;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// a6: steric force F_s,i = -k_rep sum_c delta_h(c - X_i) grad rho_bar(c) with
-// central differences, then the IB spread F(c) = sum_i delta_h(c - X_i)
-// (F_el,i + F_s,i).  One block per tile: the tile's rho_bar window (4-cell
-// halo) is staged in shared memory; every bead of the 3x3 bin neighbourhood
-// whose stencil touches the tile gets its steric force from the window and is
-// spread into the tile (64-bit fixed point).  Beads of the tile's own bin also
-// store their steric force.  Each cell of the tile is written once.
-// ---------------------------------------------------------------------------
-constexpr int kWin = kTile + 8;
-
-__global__ void __launch_bounds__(256) k_force_spread(const WorldDev* __restrict__ worlds,
-                                                      const int2* __restrict__ items) {
-  __shared__ float win[kWin * kWin];
-  __shared__ unsigned long long accx[kTile * kTile];
-  __shared__ unsigned long long accy[kTile * kTile];
-  const int2 it = items[blockIdx.x];
-  const WorldDev& w = worlds[it.x];
-  const TileGeom g = tile_geom(w, it.y);
-  const int ww = g.tw + 8, wh = g.th + 8;
-  for (int c = threadIdx.x; c < ww * wh; c += blockDim.x) {
-    const int ly = c / ww, lx = c - ly * ww;
-    const int gy = wrap_once(g.y0 - 4 + ly, w.H), gx = wrap_once(g.x0 - 4 + lx, w.W);
-    win[ly * kWin + lx] = w.rho_b[gy * w.W + gx];
-  }
-  for (int c = threadIdx.x; c < kTile * kTile; c += blockDim.x) {
-    accx[c] = 0ull;
-    accy[c] = 0ull;
-  }
-  __syncthreads();
-  const float k_rep = w.k_rep;
-  for (int ddy = g.dy_lo; ddy <= g.dy_hi; ++ddy)
-    for (int ddx = g.dx_lo; ddx <= g.dx_hi; ++ddx) {
-      const int nb = nb_bin(w, g, ddx, ddy);
-      const bool own = nb == it.y;
-      const int k1 = w.bin_off[nb + 1];
-      for (int k = w.bin_off[nb] + threadIdx.x; k < k1; k += blockDim.x) {
-        const float4 p = w.spos[k];
-        const int cx = cell_x(p), cy = cell_y(p);
-        int lx[4], ly[4];
-        if (!stencil_in_tile(cx, g.x0, g.tw, w.W, lx)) continue;
-        if (!stencil_in_tile(cy, g.y0, g.th, w.H, ly)) continue;
-        // window coordinates: with several tiles on an axis pick the
-        // periodic image of the bead next to this tile; with one tile the
-        // window spans the whole axis plus a 4-cell margin.
-        int rx = cx - g.x0, ry = cy - g.y0;
-        if (w.ntx > 1) { if (rx < -4) rx += w.W; else if (rx > g.tw + 3) rx -= w.W; }
-        if (w.nty > 1) { if (ry < -4) ry += w.H; else if (ry > g.th + 3) ry -= w.H; }
-        float wx[4], wy[4];
-        peskin4(p.x, wx);
-        peskin4(p.y, wy);
-        float gsx = 0.0f, gsy = 0.0f;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const int ky = ry + 3 + b;
-          float rx_s = 0.0f, ry_s = 0.0f;
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            const int kx = rx + 3 + a;
-            const float gx = 0.5f * (win[ky * kWin + kx + 1] - win[ky * kWin + kx - 1]);
-            const float gy = 0.5f * (win[(ky + 1) * kWin + kx] - win[(ky - 1) * kWin + kx]);
-            rx_s = fmaf(wx[a], gx, rx_s);
-            ry_s = fmaf(wx[a], gy, ry_s);
-          }
-          gsx = fmaf(wy[b], rx_s, gsx);
-          gsy = fmaf(wy[b], ry_s, gsy);
-        }
-        const float2 Fs = make_float2(-k_rep * gsx, -k_rep * gsy);
-        if (own) w.fs[w.sid[k]] = Fs;
-        const float2 fe = w.sfel[k];
-        const float Fx = fe.x + Fs.x, Fy = fe.y + Fs.y;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          if (ly[b] < 0) continue;
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            if (lx[a] < 0) continue;
-            const float wgt = wx[a] * wy[b];
-            const int c = ly[b] * kTile + lx[a];
-            atomicAdd(&accx[c], (unsigned long long)to_fix(wgt * Fx));
-            atomicAdd(&accy[c], (unsigned long long)to_fix(wgt * Fy));
-          }
-        }
-      }
-    }
-  __syncthreads();
-  for (int c = threadIdx.x; c < g.tw * g.th; c += blockDim.x) {
-    const int ly = c / g.tw, lx = c - ly * g.tw;
-    const int s = ly * kTile + lx;
-    w.F[(g.y0 + ly) * w.W + g.x0 + lx] =
-        make_float2(from_fix((long long)accx[s]), from_fix((long long)accy[s]));
   }
 }
 
@@ -360,19 +171,8 @@ __global__ void __launch_bounds__(kCellChunk) k_lbm(const WorldDev* __restrict__
 // Launchers and the step sequence.
 // ---------------------------------------------------------------------------
 void launch_bin_scan(const Plan& p, cudaStream_t s) {
-  k_bin_scan<<<p.n_worlds, 1024, 0, s>>>(p.d_worlds);
-}
-
-void launch_deposit(const Plan& p, cudaStream_t s) {
-  if (p.n_tile_items) k_deposit<<<p.n_tile_items, 256, 0, s>>>(p.d_worlds, p.d_tile_items);
-}
-
-void launch_blur(const Plan& p, cudaStream_t s) {
-  if (p.n_tile_items) k_blur<<<p.n_tile_items, 256, 0, s>>>(p.d_worlds, p.d_tile_items);
-}
-
-void launch_force_spread(const Plan& p, cudaStream_t s) {
-  if (p.n_tile_items) k_force_spread<<<p.n_tile_items, 256, 0, s>>>(p.d_worlds, p.d_tile_items);
+  k_scan_sums<<<p.n_scan_items, 256, 0, s>>>(p.d_worlds, p.d_scan_items);
+  k_scan_apply<<<p.n_scan_items, 256, 0, s>>>(p.d_worlds, p.d_scan_items);
 }
 
 void launch_lbm(const Plan& p, cudaStream_t s) {
@@ -380,14 +180,13 @@ void launch_lbm(const Plan& p, cudaStream_t s) {
 }
 
 void enqueue_step(const Plan& p, cudaStream_t s) {
-  launch_pbd(p, s);             // a1 + a3 + a2 histogram
-  launch_bin_scan(p, s);        // a2 offsets
-  launch_bin_scatter(p, s);     // a2 scatter
-  launch_deposit(p, s);         // a4
-  launch_blur(p, s);            // a5
-  launch_force_spread(p, s);    // a6
-  launch_lbm(p, s);             // a7
-  launch_interp_advance(p, s);  // a8
+  launch_pbd(p, s);              // a1 + a3 + a2 histogram
+  launch_bin_scan(p, s);         // a2 offsets (two kernels)
+  launch_bin_scatter(p, s);      // a2 scatter
+  launch_deposit_x(p, s, 0);     // a4 + x pass of a5
+  launch_force_spread(p, s, 0);  // y pass of a5 + a6
+  launch_lbm(p, s);              // a7
+  launch_interp_advance(p, s);   // a8
 }
 
 }  // namespace mc

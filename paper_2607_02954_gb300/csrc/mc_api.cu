@@ -128,16 +128,19 @@ void free_plan(Plan& p, cudaStream_t s) {
 mc_status build_plan(mc_world* const* ws, int n, cudaStream_t s, Plan& out) {
   Plan p;
   p.n_worlds = n;
-  std::vector<int2> fil, bead, tile, cell;
+  p.max_R = 1;
+  std::vector<int2> fil, bead, tile, cell, scan;
   std::vector<WorldDev> table(n);
   for (int k = 0; k < n; ++k) {
     const mc_world* w = ws[k];
     table[k] = w->h;
     p.max_B = std::max(p.max_B, w->max_B);
+    p.max_R = std::max(p.max_R, w->h.R);
     for (int f = 0; f < w->h.n_fil; ++f) fil.push_back(make_int2(k, f));
     const int nb = std::max(w->h.N, 1);
     for (int b = 0; b < nb; b += mc::kBeadChunk) bead.push_back(make_int2(k, b));
-    for (int t = 0; t < w->h.n_bins; ++t) tile.push_back(make_int2(k, t));
+    for (int t = 0; t < w->h.n_tiles; ++t) tile.push_back(make_int2(k, t));
+    for (int c = 0; c < w->h.n_chunks; ++c) scan.push_back(make_int2(k, c));
     const int HW = w->h.H * w->h.W;
     for (int c = 0; c < HW; c += mc::kCellChunk) cell.push_back(make_int2(k, c));
   }
@@ -147,12 +150,14 @@ mc_status build_plan(mc_world* const* ws, int n, cudaStream_t s, Plan& out) {
   const size_t o_b = L.take<int2>(bead.size());
   const size_t o_t = L.take<int2>(tile.size());
   const size_t o_c = L.take<int2>(cell.size());
+  const size_t o_s = L.take<int2>(scan.size());
   std::vector<char> host(L.off);
   std::memcpy(host.data() + o_w, table.data(), n * sizeof(WorldDev));
   if (!fil.empty()) std::memcpy(host.data() + o_f, fil.data(), fil.size() * sizeof(int2));
   std::memcpy(host.data() + o_b, bead.data(), bead.size() * sizeof(int2));
   if (!tile.empty()) std::memcpy(host.data() + o_t, tile.data(), tile.size() * sizeof(int2));
   std::memcpy(host.data() + o_c, cell.data(), cell.size() * sizeof(int2));
+  std::memcpy(host.data() + o_s, scan.data(), scan.size() * sizeof(int2));
   cudaError_t e = cudaMallocAsync(&p.d_mem, L.off, s);
   if (e != cudaSuccess) return fail(MC_ERR_OOM, std::string("plan allocation: ") + cudaGetErrorString(e));
   e = cudaMemcpyAsync(p.d_mem, host.data(), L.off, cudaMemcpyHostToDevice, s);
@@ -163,10 +168,12 @@ mc_status build_plan(mc_world* const* ws, int n, cudaStream_t s, Plan& out) {
   p.d_bead_items = at<int2>(p.d_mem, o_b);
   p.d_tile_items = at<int2>(p.d_mem, o_t);
   p.d_cell_items = at<int2>(p.d_mem, o_c);
+  p.d_scan_items = at<int2>(p.d_mem, o_s);
   p.n_fil_items = (int)fil.size();
   p.n_bead_items = (int)bead.size();
   p.n_tile_items = (int)tile.size();
   p.n_cell_items = (int)cell.size();
+  p.n_scan_items = (int)scan.size();
   out = p;
   return MC_OK;
 }
@@ -269,7 +276,7 @@ mc_status mc_world_create(const mc_world_desc* d, void* stream, mc_world** out) 
     if (B < 2) return fail(MC_ERR_INVALID_ARG, "every filament needs at least 2 beads");
     max_B = std::max(max_B, B);
   }
-  if (max_B > 4096) return fail(MC_ERR_INVALID_ARG, "filaments are limited to 4096 beads");
+  if (max_B > 3072) return fail(MC_ERR_INVALID_ARG, "filaments are limited to 3072 beads");
   const int N = fo[d->n_fil];
   const int E = N - d->n_fil, J = N - 2 * d->n_fil;
   const size_t HW = (size_t)H * W;
@@ -323,10 +330,13 @@ mc_status mc_world_create(const mc_world_desc* d, void* stream, mc_world** out) 
   h.E = E;
   h.J = J;
   h.n_fil = d->n_fil;
-  h.tile = mc::kTile;
+  h.nbx = W / mc::kBin;
+  h.nby = H / mc::kBin;
+  h.n_bins = h.nbx * h.nby;
   h.ntx = (W + mc::kTile - 1) / mc::kTile;
   h.nty = (H + mc::kTile - 1) / mc::kTile;
-  h.n_bins = h.ntx * h.nty;
+  h.n_tiles = h.ntx * h.nty;
+  h.n_chunks = (h.n_bins + mc::kScanChunk - 1) / mc::kScanChunk;
   fill_constants(h, d->p);
 
   Layout L;
@@ -343,6 +353,7 @@ mc_status mc_world_create(const mc_world_desc* d, void* stream, mc_world** out) 
   const size_t o_bc = L.take<int>(h.n_bins);
   const size_t o_bo = L.take<int>(h.n_bins + 1);
   const size_t o_bcur = L.take<int>(h.n_bins);
+  const size_t o_cs = L.take<int>(h.n_chunks);
   const size_t o_sp = L.take<float4>(N);
   const size_t o_sf = L.take<float2>(N);
   const size_t o_sid = L.take<int>(N);
@@ -351,9 +362,12 @@ mc_status mc_world_create(const mc_world_desc* d, void* stream, mc_world** out) 
   const size_t o_F = L.take<float2>(HW);
   const size_t o_u = L.take<float2>(HW);
   const size_t o_rs = L.take<float>(HW);
+  const size_t o_rx = L.take<float>(HW);
   const size_t o_rb = L.take<float>(HW);
+  const size_t o_trm = L.take<float>(h.n_tiles);
   const size_t o_t = L.take<long long>(1);
   const size_t o_fl = L.take<unsigned>(1);
+  const size_t o_fm = L.take<unsigned>(2);
   w->bytes = L.off;
   cudaError_t e = cudaMallocAsync(&w->arena, w->bytes, s);
   if (e != cudaSuccess) {
@@ -374,6 +388,7 @@ mc_status mc_world_create(const mc_world_desc* d, void* stream, mc_world** out) 
   h.bin_count = at<int>(A, o_bc);
   h.bin_off = at<int>(A, o_bo);
   h.bin_cursor = at<int>(A, o_bcur);
+  h.chunk_sum = at<int>(A, o_cs);
   h.spos = at<float4>(A, o_sp);
   h.sfel = at<float2>(A, o_sf);
   h.sid = at<int>(A, o_sid);
@@ -382,9 +397,12 @@ mc_status mc_world_create(const mc_world_desc* d, void* stream, mc_world** out) 
   h.F = at<float2>(A, o_F);
   h.u = at<float2>(A, o_u);
   h.rho_s = at<float>(A, o_rs);
+  h.rho_x = at<float>(A, o_rx);
   h.rho_b = at<float>(A, o_rb);
+  h.tile_rho_max = at<float>(A, o_trm);
   h.t = at<long long>(A, o_t);
   h.flags = at<unsigned>(A, o_fl);
+  h.fel_max = at<unsigned>(A, o_fm);
 
   auto fail_free = [&](mc_status s2) {
     cudaFreeAsync(w->arena, s);
@@ -440,7 +458,7 @@ mc_status mc_world_info_get(const mc_world* w, mc_world_info* out) {
   out->N = w->h.N;
   out->E = w->h.E;
   out->J = w->h.J;
-  out->tile = w->h.tile;
+  out->bin_edge = mc::kBin;
   out->n_bins = w->h.n_bins;
   out->t = w->t;
   out->device_bytes = w->bytes;
@@ -493,10 +511,9 @@ mc_status mc_step_stage(mc_world* w, int stage, void* stream) {
     case 0: mc::launch_pbd(p, s); break;
     case 1: mc::launch_bin_scan(p, s); break;
     case 2: mc::launch_bin_scatter(p, s); break;
-    case 3: mc::launch_deposit(p, s); break;
-    case 4: mc::launch_blur(p, s); break;
-    case 5: mc::launch_force_spread(p, s); break;
-    case 6: mc::launch_lbm(p, s); break;
+    case 3: mc::launch_deposit_x(p, s, 0); break;
+    case 4: mc::launch_force_spread(p, s, 0); break;
+    case 5: mc::launch_lbm(p, s); break;
     default:
       mc::launch_interp_advance(p, s);
       w->t += 1;
@@ -558,8 +575,17 @@ mc_status mc_world_get_field(const mc_world* w, int field, void* out, int mem_ki
     case MC_FIELD_FEL: src = h.fel; bytes = h.N * sizeof(float2); break;
     case MC_FIELD_FS: src = h.fs; bytes = h.N * sizeof(float2); break;
     case MC_FIELD_UBEAD: src = h.ubead; bytes = h.N * sizeof(float2); break;
-    case MC_FIELD_RHO_S: src = h.rho_s; bytes = HW * sizeof(float); break;
-    case MC_FIELD_RHO_BAR: src = h.rho_b; bytes = HW * sizeof(float); break;
+    case MC_FIELD_RHO_S:
+    case MC_FIELD_RHO_BAR:
+      // the step keeps these in shared memory only: re-run the steric
+      // stages on the last step's binned beads with field output on (they
+      // are deterministic, so rho_x, F and F_s are rewritten identically)
+      mc::launch_deposit_x(w->plan, s, field == MC_FIELD_RHO_S);
+      if (field == MC_FIELD_RHO_BAR) mc::launch_force_spread(w->plan, s, 1, 1);
+      MC_CUDA(cudaGetLastError());
+      src = field == MC_FIELD_RHO_S ? (const void*)h.rho_s : (const void*)h.rho_b;
+      bytes = HW * sizeof(float);
+      break;
     case MC_FIELD_FORCE: src = h.F; bytes = HW * sizeof(float2); break;
     case MC_FIELD_U: src = h.u; bytes = HW * sizeof(float2); break;
     case MC_FIELD_BIN: src = h.bead_bin; bytes = h.N * sizeof(int); break;

@@ -8,21 +8,24 @@
 
 namespace mc {
 
-// Binning tile edge in cells.  A bead's 4x4 stencil reaches 2 cells below and
-// 1 cell above its own cell, so a tile only receives from its 3x3 tile
-// neighbourhood; grid sizes are multiples of 8, so ragged last tiles are at
-// least 8 cells wide.
+// Beads are counting-sorted by 8x8-cell bins (row-major over the bin grid);
+// the steric kernels work on 32x32-cell tiles.  Grid sizes are multiples of
+// 8, so bins are never ragged and ragged last tiles are at least 8 cells
+// wide.
+constexpr int kBin = 8;
 constexpr int kTile = 32;
+constexpr int kScanChunk = 1024;    // bins per block of the offset scan
 constexpr int kMaxR = 8;            // Gaussian half width ceil(4 sigma) <= 8
 constexpr int kBeadChunk = 256;     // beads per block of the bead-parallel kernels
 constexpr int kCellChunk = 256;     // cells per block of the LBM kernel
 constexpr int kMaxNpbd = 64;
 
-// Deposition accumulates in 64-bit fixed point with 40 fractional bits:
-// integer adds commute, so every deposited field is bitwise independent of
-// the order in which beads arrive (alone, batched or served).
-constexpr float kFixScale = 1099511627776.0f;      // 2^40
-constexpr float kFixInv = 9.094947017729282e-13f;  // 2^-40
+// Deposition accumulates in int32 fixed point in shared memory: integer adds
+// commute, so every deposited field is bitwise independent of the order in
+// which beads arrive (alone, batched or served).  Each tile picks a
+// power-of-two scale 2^k from a bound B on its largest cell sum of |terms|
+// (B 2^k < 2^30, k in [8, 40]), so no sum can overflow; the bound and hence
+// the scale depend only on the data.
 
 enum : unsigned { kFlagUnstable = 1u };
 
@@ -30,7 +33,9 @@ enum : unsigned { kFlagUnstable = 1u };
 // memory as one entry of a world table; all pointers are device pointers.
 struct WorldDev {
   int H, W, N, E, J, n_fil;
-  int tile, ntx, nty, n_bins;
+  int nbx, nby, n_bins;             // 8x8 bins
+  int ntx, nty, n_tiles;            // 32x32 tiles
+  int n_chunks;                     // scan blocks over the bins
   int R, n_pbd;
   float dt, kappa_dt, k_bend, k_st, k_sh, k_rep, orient;
   float om_p, om_m, src_p, src_m;   // 1/tau+-, 1 - 1/(2 tau+-)
@@ -49,15 +54,19 @@ struct WorldDev {
   int* bin_count;         // [n_bins]
   int* bin_off;           // [n_bins + 1]
   int* bin_cursor;        // [n_bins]
+  int* chunk_sum;         // [n_chunks]
   float4* spos;           // [N] positions in bin order
   float2* sfel;           // [N] elastic forces in bin order
   int* sid;               // [N] bead ids in bin order
   float* g[2];            // [9 * H * W] post-collision population deviations (ping-pong)
   float2* F;              // [H * W]
   float2* u;              // [H * W]
-  float* rho_s;           // [H * W]
-  float* rho_b;           // [H * W]
+  float* rho_s;           // [H * W] (written only on request)
+  float* rho_x;           // [H * W] x-filtered density
+  float* rho_b;           // [H * W] (written only on request)
+  float* tile_rho_max;    // [n_tiles] largest rho_s of each tile (fixed-point bound)
   long long* t;           // step counter
+  unsigned* fel_max;      // [2] largest |F_el| component of the step, by step parity (float bits)
   unsigned* flags;        // watchdog flags
 };
 
@@ -65,12 +74,14 @@ struct WorldDev {
 struct Plan {
   int n_worlds = 0;
   int max_B = 2;
-  int n_fil_items = 0, n_bead_items = 0, n_tile_items = 0, n_cell_items = 0;
+  int max_R = 4;                 // largest Gaussian half width among the worlds
+  int n_fil_items = 0, n_bead_items = 0, n_tile_items = 0, n_cell_items = 0, n_scan_items = 0;
   WorldDev* d_worlds = nullptr;  // [n_worlds]
   int2* d_fil_items = nullptr;   // (world, filament)
   int2* d_bead_items = nullptr;  // (world, first bead)
   int2* d_tile_items = nullptr;  // (world, tile)
   int2* d_cell_items = nullptr;  // (world, first cell)
+  int2* d_scan_items = nullptr;  // (world, scan chunk)
   void* d_mem = nullptr;
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
@@ -78,11 +89,13 @@ struct Plan {
 
 // --- stage launchers (one launch covers every world of the plan) ---------
 void launch_pbd(const Plan& p, cudaStream_t s);
-void launch_bin_scan(const Plan& p, cudaStream_t s);
+void launch_bin_scan(const Plan& p, cudaStream_t s);      // two kernels
 void launch_bin_scatter(const Plan& p, cudaStream_t s);
-void launch_deposit(const Plan& p, cudaStream_t s);
-void launch_blur(const Plan& p, cudaStream_t s);
-void launch_force_spread(const Plan& p, cudaStream_t s);
+// a4 + x pass of a5; store_fields also writes rho_s of each tile
+void launch_deposit_x(const Plan& p, cudaStream_t s, int store_fields);
+// y pass of a5 + a6; store_fields also writes rho_bar of each tile;
+// after_step = 1 when re-run after the step that produced the binned beads
+void launch_force_spread(const Plan& p, cudaStream_t s, int store_fields, int after_step = 0);
 void launch_lbm(const Plan& p, cudaStream_t s);
 void launch_interp_advance(const Plan& p, cudaStream_t s);
 void enqueue_step(const Plan& p, cudaStream_t s);
@@ -104,6 +117,11 @@ __device__ __forceinline__ int wrap_once(int v, int n) {
   return v < 0 ? v + n : (v >= n ? v - n : v);
 }
 
+__device__ __forceinline__ int wrap_mod(int v, int n) {
+  const int r = v % n;
+  return r < 0 ? r + n : r;
+}
+
 // Peskin's 4-point kernel phi at the four cells floor(X)-1 .. floor(X)+2
 // for fractional part a in [0, 1).  With s = sqrt(1 + 4a - 4a^2):
 //   phi(1+a) = (3 - 2a - s)/8, phi(a) = (3 - 2a + s)/8,
@@ -120,7 +138,14 @@ __device__ __forceinline__ void peskin4(float a, float w[4]) {
 __device__ __forceinline__ int cell_x(const float4& p) { return __float_as_int(p.z); }
 __device__ __forceinline__ int cell_y(const float4& p) { return __float_as_int(p.w); }
 
-__device__ __forceinline__ long long to_fix(float v) { return __float2ll_rn(v * kFixScale); }
-__device__ __forceinline__ float from_fix(long long v) { return __ll2float_rn(v) * kFixInv; }
+// Exponent k of the per-tile fixed-point scale for a bound on |cell sums|.
+__device__ __forceinline__ int fix_exponent(float bound) {
+  if (!(bound > 0.0f)) return 40;
+  if (!(bound < 1.0e30f)) return 8;
+  int e;
+  frexpf(bound, &e);   // bound < 2^e
+  const int k = 30 - e;
+  return k < 8 ? 8 : (k > 40 ? 40 : k);
+}
 
 }  // namespace mc

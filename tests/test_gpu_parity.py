@@ -89,7 +89,7 @@ def test_cell_and_bin_indices_bit_exact(maker):
         spec.x[8:12] = np.nextafter(np.float32(spec.W), np.float32(0))
         spec.y[12:16] = np.float32(0.0)
     gw = _gpu_world(spec)
-    cell_w, bin_w, off_w = O.cell_and_bin(spec.x, spec.y, spec.H, spec.W, gw.info()["tile"])
+    cell_w, bin_w, off_w = O.cell_and_bin(spec.x, spec.y, spec.H, spec.W, gw.info()["bin_edge"])
     assert np.array_equal(gw.field("cell"), cell_w)
     gw.step(1)
     assert np.array_equal(gw.field("bin"), bin_w)
