@@ -213,6 +213,63 @@ mc_status mc_world_get_field(const mc_world* w, int field, void* out, int mem_ki
 mc_status mc_world_check(const mc_world* w, void* stream);
 mc_status mc_world_clear_flags(mc_world* w, void* stream);
 
+/* ---- Rollout serving: continuous batching ---------------------------------
+ * Search loops (the paper's Neuroevolution and QD Search experiments,
+ * the paper Experiments) request rollouts as they go and read back a fitness,
+ * the mean displacement of the world's beads.  A server owns a scheduler
+ * thread and a CUDA stream on the device current at creation.  Requests wait
+ * in a queue until a slot is free and their device footprint fits the
+ * budget (a lone request larger than the budget is still admitted when
+ * nothing else runs); all admitted worlds advance together through the
+ * batched kernels, steps_per_tick steps at a time; finished worlds are
+ * released at once, which admits waiting requests.  Results are bitwise the
+ * same as running the world alone. */
+typedef struct mc_server mc_server;
+
+typedef struct mc_server_cfg {
+  size_t hbm_budget_bytes;  /* device memory the admitted worlds may hold */
+  int max_slots;            /* most worlds advanced at once (>= 1) */
+  int steps_per_tick;       /* steps between admission / retirement points (>= 1) */
+  int max_pending;          /* queue capacity; submit returns MC_ERR_BUSY beyond it */
+} mc_server_cfg;
+
+typedef struct mc_result {
+  double com_disp[2];       /* mean unwrapped bead displacement after n_steps */
+  int status;               /* MC_OK, MC_ERR_UNSTABLE, or the world's creation error */
+  int n_steps;
+  int64_t t_submit_ns;      /* steady-clock times of submit, admission, completion */
+  int64_t t_admit_ns;
+  int64_t t_done_ns;
+} mc_result;
+
+typedef struct mc_server_stats {
+  int64_t submitted, completed, steps_run, ticks, pending;
+} mc_server_stats;
+
+/* Starts a server (thread + stream).  Errors: MC_ERR_INVALID_ARG for
+ * non-positive settings, MC_ERR_CUDA. */
+mc_status mc_server_create(const mc_server_cfg* cfg, mc_server** out);
+
+/* Queues one rollout of n_steps >= 1 steps of the described world.  The
+ * description's arrays are copied before the call returns (device arrays
+ * with a synchronous copy).  Validation of sizes happens here
+ * (MC_ERR_INVALID_ARG); value checks happen at admission and show up in the
+ * result's status.  MC_ERR_BUSY when the queue is full. */
+mc_status mc_serve_submit(mc_server* s, const mc_world_desc* desc, int n_steps, uint64_t* ticket);
+
+/* Non-blocking: MC_OK and the result (once; the ticket is then forgotten),
+ * MC_ERR_BUSY while pending or running, MC_ERR_NOT_FOUND otherwise. */
+mc_status mc_serve_poll(mc_server* s, uint64_t ticket, mc_result* out);
+
+/* Blocks up to timeout_ms: MC_OK, MC_ERR_TIMEOUT or MC_ERR_NOT_FOUND. */
+mc_status mc_serve_wait(mc_server* s, uint64_t ticket, int timeout_ms, mc_result* out);
+
+mc_status mc_server_stats_get(mc_server* s, mc_server_stats* out);
+
+/* Stops the scheduler, drops queued requests and frees everything.  No
+ * other call on this server may run concurrently or afterwards. */
+mc_status mc_server_destroy(mc_server* s);
+
 /* Thread-local description of the last error of this thread. */
 const char* mc_last_error(void);
 int mc_abi_version(void);

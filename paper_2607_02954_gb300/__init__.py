@@ -9,7 +9,7 @@ from .synth import Params, WorldSpec  # noqa: F401
 
 
 def __getattr__(name):
-    if name in ("World", "step_batched", "default_params", "stream_handle"):
+    if name in ("World", "Server", "step_batched", "default_params", "stream_handle"):
         from . import world
         return getattr(world, name)
     raise AttributeError(name)

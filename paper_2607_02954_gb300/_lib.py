@@ -51,6 +51,20 @@ class mc_world_info(ctypes.Structure):
                 ("t", ctypes.c_int64), ("device_bytes", ctypes.c_size_t)]
 
 
+class mc_server_cfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int),
+                ("steps_per_tick", ctypes.c_int), ("max_pending", ctypes.c_int)]
+
+
+class mc_result(ctypes.Structure):
+    _fields_ = [("com_disp", ctypes.c_double * 2), ("status", ctypes.c_int), ("n_steps", ctypes.c_int),
+                ("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64), ("t_done_ns", ctypes.c_int64)]
+
+
+class mc_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "steps_run", "ticks", "pending")]
+
+
 # name -> (restype, argtypes): every entry point declared in include/mc.h
 _vp, _i, _i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
 SIGNATURES = {
@@ -66,6 +80,12 @@ SIGNATURES = {
     "mc_world_get_field": (_i, [_vp, _i, _vp, _i, _vp]),
     "mc_world_check": (_i, [_vp, _vp]),
     "mc_world_clear_flags": (_i, [_vp, _vp]),
+    "mc_server_create": (_i, [ctypes.POINTER(mc_server_cfg), ctypes.POINTER(_vp)]),
+    "mc_serve_submit": (_i, [_vp, ctypes.POINTER(mc_world_desc), _i, ctypes.POINTER(ctypes.c_uint64)]),
+    "mc_serve_poll": (_i, [_vp, ctypes.c_uint64, ctypes.POINTER(mc_result)]),
+    "mc_serve_wait": (_i, [_vp, ctypes.c_uint64, _i, ctypes.POINTER(mc_result)]),
+    "mc_server_stats_get": (_i, [_vp, ctypes.POINTER(mc_server_stats)]),
+    "mc_server_destroy": (_i, [_vp]),
     "mc_last_error": (ctypes.c_char_p, []),
     "mc_abi_version": (_i, []),
 }

@@ -13,17 +13,6 @@
 using mc::Plan;
 using mc::WorldDev;
 
-struct mc_world {
-  WorldDev h{};                 // device descriptor (host copy)
-  void* arena = nullptr;        // one allocation holding every device array
-  size_t bytes = 0;
-  cudaStream_t stream = nullptr;  // creation stream; the arena is freed on it
-  int64_t t = 0;                // step counter after all enqueued steps
-  int max_B = 2;
-  std::vector<int> fil_off;
-  Plan plan;                    // single-world plan
-  mc_params params{};
-};
 
 namespace {
 
@@ -233,6 +222,98 @@ void drop_plans_with(mc_world* w) {
 
 }  // namespace
 
+namespace mc {
+
+// Sizes of a world's arrays from its grid and bead counts.
+void world_sizes(WorldDev& h, int H, int W, int n_fil, int N) {
+  h.H = H;
+  h.W = W;
+  h.N = N;
+  h.n_fil = n_fil;
+  h.E = N - n_fil;
+  h.J = N - 2 * n_fil;
+  h.nbx = W / kBin;
+  h.nby = H / kBin;
+  h.n_bins = h.nbx * h.nby;
+  h.ntx = (W + kTile - 1) / kTile;
+  h.nty = (H + kTile - 1) / kTile;
+  h.n_tiles = h.ntx * h.nty;
+  h.n_chunks = (h.n_bins + kScanChunk - 1) / kScanChunk;
+}
+
+// Places every array of a world inside one arena (256-byte aligned slices).
+// With A == nullptr only returns the arena size in bytes.
+size_t world_layout(WorldDev& h, void* A) {
+  Layout L;
+  const int N = h.N, E = h.E, J = h.J;
+  const size_t HW = (size_t)h.H * h.W;
+  const size_t o_fo = L.take<int>(h.n_fil + 1);
+  const size_t o_pos = L.take<float4>(N);
+  const size_t o_disp = L.take<float2>(N);
+  const size_t o_th = L.take<float>(E);
+  const size_t o_L = L.take<float>(E);
+  const size_t o_dr = L.take<float4>(J);
+  const size_t o_fel = L.take<float2>(N);
+  const size_t o_fs = L.take<float2>(N);
+  const size_t o_ub = L.take<float2>(N);
+  const size_t o_bb = L.take<int>(N);
+  const size_t o_bc = L.take<int>(h.n_bins);
+  const size_t o_bo = L.take<int>(h.n_bins + 1);
+  const size_t o_bcur = L.take<int>(h.n_bins);
+  const size_t o_cs = L.take<int>(h.n_chunks);
+  const size_t o_sp = L.take<float4>(N);
+  const size_t o_sf = L.take<float2>(N);
+  const size_t o_sid = L.take<int>(N);
+  const size_t o_g0 = L.take<float>(9 * HW);
+  const size_t o_g1 = L.take<float>(9 * HW);
+  const size_t o_F = L.take<float2>(HW);
+  const size_t o_u = L.take<float2>(HW);
+  const size_t o_rs = L.take<float>(HW);
+  const size_t o_rx = L.take<float>(HW);
+  const size_t o_rb = L.take<float>(HW);
+  const size_t o_trm = L.take<float>(h.n_tiles);
+  const size_t o_t = L.take<long long>(1);
+  const size_t o_fl = L.take<unsigned>(1);
+  const size_t o_fm = L.take<unsigned>(2);
+  if (!A) return L.off;
+  h.fil_off = at<int>(A, o_fo);
+  h.pos = at<float4>(A, o_pos);
+  h.disp = at<float2>(A, o_disp);
+  h.theta = at<float>(A, o_th);
+  h.L_rest = at<float>(A, o_L);
+  h.drive = at<float4>(A, o_dr);
+  h.fel = at<float2>(A, o_fel);
+  h.fs = at<float2>(A, o_fs);
+  h.ubead = at<float2>(A, o_ub);
+  h.bead_bin = at<int>(A, o_bb);
+  h.bin_count = at<int>(A, o_bc);
+  h.bin_off = at<int>(A, o_bo);
+  h.bin_cursor = at<int>(A, o_bcur);
+  h.chunk_sum = at<int>(A, o_cs);
+  h.spos = at<float4>(A, o_sp);
+  h.sfel = at<float2>(A, o_sf);
+  h.sid = at<int>(A, o_sid);
+  h.g[0] = at<float>(A, o_g0);
+  h.g[1] = at<float>(A, o_g1);
+  h.F = at<float2>(A, o_F);
+  h.u = at<float2>(A, o_u);
+  h.rho_s = at<float>(A, o_rs);
+  h.rho_x = at<float>(A, o_rx);
+  h.rho_b = at<float>(A, o_rb);
+  h.tile_rho_max = at<float>(A, o_trm);
+  h.t = at<long long>(A, o_t);
+  h.flags = at<unsigned>(A, o_fl);
+  h.fel_max = at<unsigned>(A, o_fm);
+  return L.off;
+}
+
+// Plan and step helpers shared with the rollout server.
+mc_status plan_build(mc_world* const* ws, int n, cudaStream_t s, Plan& out) { return build_plan(ws, n, s, out); }
+mc_status plan_run(Plan& p, int n_steps, cudaStream_t s) { return run_steps(p, n_steps, s); }
+void plan_free(Plan& p, cudaStream_t s) { free_plan(p, s); }
+
+}  // namespace mc
+
 extern "C" {
 
 const char* mc_last_error(void) { return g_last_error.c_str(); }
@@ -324,85 +405,17 @@ mc_status mc_world_create(const mc_world_desc* d, void* stream, mc_world** out) 
   w->fil_off = fo;
   w->params = d->p;
   WorldDev& h = w->h;
-  h.H = H;
-  h.W = W;
-  h.N = N;
-  h.E = E;
-  h.J = J;
-  h.n_fil = d->n_fil;
-  h.nbx = W / mc::kBin;
-  h.nby = H / mc::kBin;
-  h.n_bins = h.nbx * h.nby;
-  h.ntx = (W + mc::kTile - 1) / mc::kTile;
-  h.nty = (H + mc::kTile - 1) / mc::kTile;
-  h.n_tiles = h.ntx * h.nty;
-  h.n_chunks = (h.n_bins + mc::kScanChunk - 1) / mc::kScanChunk;
+  mc::world_sizes(h, H, W, d->n_fil, N);
   fill_constants(h, d->p);
 
-  Layout L;
-  const size_t o_fo = L.take<int>(d->n_fil + 1);
-  const size_t o_pos = L.take<float4>(N);
-  const size_t o_disp = L.take<float2>(N);
-  const size_t o_th = L.take<float>(E);
-  const size_t o_L = L.take<float>(E);
-  const size_t o_dr = L.take<float4>(J);
-  const size_t o_fel = L.take<float2>(N);
-  const size_t o_fs = L.take<float2>(N);
-  const size_t o_ub = L.take<float2>(N);
-  const size_t o_bb = L.take<int>(N);
-  const size_t o_bc = L.take<int>(h.n_bins);
-  const size_t o_bo = L.take<int>(h.n_bins + 1);
-  const size_t o_bcur = L.take<int>(h.n_bins);
-  const size_t o_cs = L.take<int>(h.n_chunks);
-  const size_t o_sp = L.take<float4>(N);
-  const size_t o_sf = L.take<float2>(N);
-  const size_t o_sid = L.take<int>(N);
-  const size_t o_g0 = L.take<float>(9 * HW);
-  const size_t o_g1 = L.take<float>(9 * HW);
-  const size_t o_F = L.take<float2>(HW);
-  const size_t o_u = L.take<float2>(HW);
-  const size_t o_rs = L.take<float>(HW);
-  const size_t o_rx = L.take<float>(HW);
-  const size_t o_rb = L.take<float>(HW);
-  const size_t o_trm = L.take<float>(h.n_tiles);
-  const size_t o_t = L.take<long long>(1);
-  const size_t o_fl = L.take<unsigned>(1);
-  const size_t o_fm = L.take<unsigned>(2);
-  w->bytes = L.off;
+  w->bytes = mc::world_layout(h, nullptr);
   cudaError_t e = cudaMallocAsync(&w->arena, w->bytes, s);
   if (e != cudaSuccess) {
     delete w;
     return fail(MC_ERR_OOM, std::string("world allocation: ") + cudaGetErrorString(e));
   }
   void* A = w->arena;
-  h.fil_off = at<int>(A, o_fo);
-  h.pos = at<float4>(A, o_pos);
-  h.disp = at<float2>(A, o_disp);
-  h.theta = at<float>(A, o_th);
-  h.L_rest = at<float>(A, o_L);
-  h.drive = at<float4>(A, o_dr);
-  h.fel = at<float2>(A, o_fel);
-  h.fs = at<float2>(A, o_fs);
-  h.ubead = at<float2>(A, o_ub);
-  h.bead_bin = at<int>(A, o_bb);
-  h.bin_count = at<int>(A, o_bc);
-  h.bin_off = at<int>(A, o_bo);
-  h.bin_cursor = at<int>(A, o_bcur);
-  h.chunk_sum = at<int>(A, o_cs);
-  h.spos = at<float4>(A, o_sp);
-  h.sfel = at<float2>(A, o_sf);
-  h.sid = at<int>(A, o_sid);
-  h.g[0] = at<float>(A, o_g0);
-  h.g[1] = at<float>(A, o_g1);
-  h.F = at<float2>(A, o_F);
-  h.u = at<float2>(A, o_u);
-  h.rho_s = at<float>(A, o_rs);
-  h.rho_x = at<float>(A, o_rx);
-  h.rho_b = at<float>(A, o_rb);
-  h.tile_rho_max = at<float>(A, o_trm);
-  h.t = at<long long>(A, o_t);
-  h.flags = at<unsigned>(A, o_fl);
-  h.fel_max = at<unsigned>(A, o_fm);
+  mc::world_layout(h, A);
 
   auto fail_free = [&](mc_status s2) {
     cudaFreeAsync(w->arena, s);

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/mc.h"
 
 namespace mc {
@@ -107,6 +109,13 @@ void launch_stream_out(const float* g_src, float* out, int H, int W, cudaStream_
 void launch_positions_out(const WorldDev& w, float* x, float* y, cudaStream_t s);
 void launch_cells_out(const WorldDev& w, int* cell, cudaStream_t s);
 
+// --- world life cycle and plans (host, mc_api.cu) -------------------------
+void world_sizes(WorldDev& h, int H, int W, int n_fil, int N);
+size_t world_layout(WorldDev& h, void* arena);
+mc_status plan_build(mc_world* const* ws, int n, cudaStream_t s, Plan& out);
+mc_status plan_run(Plan& p, int n_steps, cudaStream_t s);
+void plan_free(Plan& p, cudaStream_t s);
+
 // --- host accessors for code outside the ABI translation unit ------------
 const WorldDev& world_dev(const mc_world* w);
 void set_last_error(const char* msg);
@@ -149,3 +158,16 @@ __device__ __forceinline__ int fix_exponent(float bound) {
 }
 
 }  // namespace mc
+
+// One world: its device descriptor, its arena and host-side bookkeeping.
+struct mc_world {
+  mc::WorldDev h{};               // device descriptor (host copy)
+  void* arena = nullptr;          // one allocation holding every device array
+  size_t bytes = 0;
+  cudaStream_t stream = nullptr;  // creation stream; the arena is freed on it
+  int64_t t = 0;                  // step counter after all enqueued steps
+  int max_B = 2;
+  std::vector<int> fil_off;
+  mc::Plan plan;                  // single-world plan
+  mc_params params{};
+};

@@ -42,6 +42,42 @@ def default_params() -> Params:
 _FLOAT_ARRAYS = ("x", "y", "theta", "L_rest", "theta0", "drive_amp", "drive_freq", "drive_phase")
 
 
+def make_desc(spec: WorldSpec, device: bool = False):
+    """mc_world_desc pointing at host (numpy) or device (torch) copies of the
+    spec's arrays; returns (desc, objects that must stay alive)."""
+    d = L.mc_world_desc()
+    keep = []
+    d.H, d.W, d.n_fil = int(spec.H), int(spec.W), int(spec.n_fil)
+    fo = np.ascontiguousarray(spec.fil_off, dtype=np.int32)
+    keep.append(fo)
+    d.fil_off = fo.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    if device:
+        torch = _torch()
+        for name in _FLOAT_ARRAYS:
+            t = torch.as_tensor(np.ascontiguousarray(getattr(spec, name), np.float32)).cuda()
+            keep.append(t)
+            setattr(d, name, ctypes.c_void_p(t.data_ptr() if t.numel() else 0))
+        if spec.f0 is not None:
+            t = torch.as_tensor(np.ascontiguousarray(spec.f0, np.float32)).cuda()
+            keep.append(t)
+            d.f0 = ctypes.c_void_p(t.data_ptr())
+        d.mem_kind = L.MC_MEM_DEVICE
+        torch.cuda.synchronize()
+    else:
+        for name in _FLOAT_ARRAYS:
+            a = np.ascontiguousarray(getattr(spec, name), dtype=np.float32)
+            keep.append(a)
+            setattr(d, name, ctypes.c_void_p(a.ctypes.data if a.size else 0))
+        if spec.f0 is not None:
+            a = np.ascontiguousarray(spec.f0, dtype=np.float32)
+            keep.append(a)
+            d.f0 = ctypes.c_void_p(a.ctypes.data)
+        d.mem_kind = L.MC_MEM_HOST
+    d.t0 = int(spec.t0)
+    d.p = params_struct(spec.params)
+    return d, keep
+
+
 class World:
     """One world resident on the GPU.
 
@@ -52,36 +88,7 @@ class World:
     def __init__(self, spec: WorldSpec, stream=None, device: bool = False):
         lib = L.load()
         self.spec = spec
-        keep = []
-        d = L.mc_world_desc()
-        d.H, d.W, d.n_fil = int(spec.H), int(spec.W), int(spec.n_fil)
-        fo = np.ascontiguousarray(spec.fil_off, dtype=np.int32)
-        keep.append(fo)
-        d.fil_off = fo.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
-        if device:
-            torch = _torch()
-            for name in _FLOAT_ARRAYS:
-                t = torch.as_tensor(np.ascontiguousarray(getattr(spec, name), np.float32)).cuda()
-                keep.append(t)
-                setattr(d, name, ctypes.c_void_p(t.data_ptr() if t.numel() else 0))
-            if spec.f0 is not None:
-                t = torch.as_tensor(np.ascontiguousarray(spec.f0, np.float32)).cuda()
-                keep.append(t)
-                d.f0 = ctypes.c_void_p(t.data_ptr())
-            d.mem_kind = L.MC_MEM_DEVICE
-            torch.cuda.synchronize()
-        else:
-            for name in _FLOAT_ARRAYS:
-                a = np.ascontiguousarray(getattr(spec, name), dtype=np.float32)
-                keep.append(a)
-                setattr(d, name, ctypes.c_void_p(a.ctypes.data if a.size else 0))
-            if spec.f0 is not None:
-                a = np.ascontiguousarray(spec.f0, dtype=np.float32)
-                keep.append(a)
-                d.f0 = ctypes.c_void_p(a.ctypes.data)
-            d.mem_kind = L.MC_MEM_HOST
-        d.t0 = int(spec.t0)
-        d.p = params_struct(spec.params)
+        d, keep = make_desc(spec, device)
         h = ctypes.c_void_p()
         L.check(lib.mc_world_create(ctypes.byref(d), stream_handle(stream), ctypes.byref(h)))
         self._h = h
@@ -167,3 +174,56 @@ def step_batched(worlds: Sequence[World], n_steps: int, stream=None):
     """Advances distinct worlds together: one launch per stage per step."""
     arr = (ctypes.c_void_p * len(worlds))(*[w.handle.value for w in worlds])
     L.check(L.load().mc_step_batched(arr, len(worlds), int(n_steps), stream_handle(stream)))
+
+
+def _result_dict(r: L.mc_result) -> Dict:
+    return {"com_disp": (r.com_disp[0], r.com_disp[1]), "status": r.status, "n_steps": r.n_steps,
+            "t_submit_ns": r.t_submit_ns, "t_admit_ns": r.t_admit_ns, "t_done_ns": r.t_done_ns}
+
+
+class Server:
+    """Continuous-batching rollout server (mc_server_*)."""
+
+    def __init__(self, hbm_budget_bytes: int = 16 << 30, max_slots: int = 4096, steps_per_tick: int = 10,
+                 max_pending: int = 1 << 20):
+        self._lib = L.load()
+        cfg = L.mc_server_cfg(hbm_budget_bytes=int(hbm_budget_bytes), max_slots=int(max_slots),
+                              steps_per_tick=int(steps_per_tick), max_pending=int(max_pending))
+        h = ctypes.c_void_p()
+        L.check(self._lib.mc_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, spec: WorldSpec, n_steps: int) -> int:
+        d, keep = make_desc(spec)
+        t = ctypes.c_uint64()
+        L.check(self._lib.mc_serve_submit(self._h, ctypes.byref(d), int(n_steps), ctypes.byref(t)))
+        return int(t.value)
+
+    def poll(self, ticket: int) -> Optional[Dict]:
+        r = L.mc_result()
+        st = self._lib.mc_serve_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(r))
+        if st == 6:   # MC_ERR_BUSY
+            return None
+        L.check(st)
+        return _result_dict(r)
+
+    def wait(self, ticket: int, timeout_ms: int = 600000) -> Dict:
+        r = L.mc_result()
+        L.check(self._lib.mc_serve_wait(self._h, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(r)))
+        return _result_dict(r)
+
+    def stats(self) -> Dict:
+        s = L.mc_server_stats()
+        L.check(self._lib.mc_server_stats_get(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in L.mc_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self._lib.mc_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
