@@ -213,6 +213,37 @@ mc_status mc_world_get_field(const mc_world* w, int field, void* out, int mem_ki
 mc_status mc_world_check(const mc_world* w, void* stream);
 mc_status mc_world_clear_flags(mc_world* w, void* stream);
 
+/* ---- Reverse mode ----------------------------------------------------------
+ * The Filament Folding experiment (the paper Experiments) optimises rest
+ * angles by gradients that flow through the whole simulation.  Here the
+ * gradient of a loss on the final unwrapped bead positions with respect to
+ * theta0 (the static rest angles) is computed by a hand-written adjoint of
+ * every stage, with checkpoint-and-recompute: the forward stores the state
+ * every ckpt_every steps, the backward re-runs one segment at a time from
+ * its checkpoint and reverses it step by step.  Device memory: one state
+ * record (16 N + 4 E + 36 H W bytes) per checkpoint and per step of one
+ * segment, plus adjoint buffers of about 150 bytes per cell. */
+
+/* Advances the world n_steps >= 1 steps (like mc_step) recording
+ * checkpoints every ckpt_every >= 1 steps.  Errors: MC_ERR_INVALID_ARG,
+ * MC_ERR_OOM, MC_ERR_CUDA. */
+mc_status mc_rollout_forward(mc_world* w, int n_steps, int ckpt_every, void* stream);
+
+/* Reverse sweep of the last mc_rollout_forward.  dL_dx, dL_dy: [N] device
+ * arrays, the loss gradient with respect to the final unwrapped positions
+ * (creation position + displacement).  Writes dL_dtheta0 [J] (device).
+ * The world ends in the final state of the rollout.  Errors:
+ * MC_ERR_INVALID_ARG when no rollout was recorded or the world was stepped
+ * since, or when filaments are too long for the adjoint kernel. */
+mc_status mc_rollout_backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* dL_dtheta0, void* stream);
+
+/* Folding loss with a polyline target (device arrays): loss[0] = mean over
+ * beads of the squared distance from the unwrapped position to the nearest
+ * segment of the polyline poly_xy [n_vertices][2]; dL_dx, dL_dy [N] its
+ * gradient.  loss is one device float (accumulated with atomics). */
+mc_status mc_loss_polyline(mc_world* w, const float* poly_xy, int n_vertices, float* loss, float* dL_dx,
+                           float* dL_dy, void* stream);
+
 /* ---- Rollout serving: continuous batching ---------------------------------
  * Search loops (the paper's Neuroevolution and QD Search experiments,
  * the paper Experiments) request rollouts as they go and read back a fitness,

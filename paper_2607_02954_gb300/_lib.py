@@ -80,6 +80,9 @@ SIGNATURES = {
     "mc_world_get_field": (_i, [_vp, _i, _vp, _i, _vp]),
     "mc_world_check": (_i, [_vp, _vp]),
     "mc_world_clear_flags": (_i, [_vp, _vp]),
+    "mc_rollout_forward": (_i, [_vp, _i, _i, _vp]),
+    "mc_rollout_backward": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "mc_loss_polyline": (_i, [_vp, _vp, _i, _vp, _vp, _vp, _vp]),
     "mc_server_create": (_i, [ctypes.POINTER(mc_server_cfg), ctypes.POINTER(_vp)]),
     "mc_serve_submit": (_i, [_vp, ctypes.POINTER(mc_world_desc), _i, ctypes.POINTER(ctypes.c_uint64)]),
     "mc_serve_poll": (_i, [_vp, ctypes.c_uint64, ctypes.POINTER(mc_result)]),

@@ -1,0 +1,574 @@
+// Reverse-mode (adjoint) kernels of one time step, and the folding loss.
+//
+// The paper differentiates its simulator end to end with automatic
+// differentiation (Filament Folding experiment); these kernels are the
+// hand-written transpose of each forward stage, applied in reverse order:
+//   a8  X^{n+1} = X^n + dt U,  U_i = sum_c w(c - X_i) u(c)
+//   a7  per cell (g^{n+1}, u) = collide(pull(g^n), F)
+//   a6  F(c) = sum_i w(c - X_i) Ftot_i,  F_s,i = -k_rep sum_c w(c - X_i) grad rho_bar(c)
+//   a5  rho_bar = G rho_s (G symmetric)
+//   a4  rho_s(c) = sum_i w(c - X_i)
+//   a3  F_el = kappa/dt (x_hat - X) with (x_hat, theta^{n+1}) = PBD(X^n, theta^n, theta_rest)
+//   a1  theta_rest = theta0 + drive(t)
+// w(c - X) = phi(c_x - X_x) phi(c_y - X_y) (Peskin 4-point); its gradient
+// with respect to X uses phi' at the same four cells per axis.  The adjoint
+// scatters (transposed gathers) use float atomics: gradients agree with the
+// exact reverse-mode result to rounding, not bitwise between runs.
+#include "mc_internal.cuh"
+
+namespace mc {
+
+// Peskin weights and their derivatives with respect to the bead coordinate:
+// with s = sqrt(1 + 4a - 4a^2), s' = (2 - 4a)/s.
+__device__ __forceinline__ void peskin4_d(float a, float w[4], float dw[4]) {
+  const float s = sqrtf(fmaf(-4.0f * a, a, fmaf(4.0f, a, 1.0f)));
+  const float ds = (2.0f - 4.0f * a) / s;
+  const float p = 3.0f - 2.0f * a, q = 1.0f + 2.0f * a;
+  w[0] = (p - s) * 0.125f;
+  w[1] = (p + s) * 0.125f;
+  w[2] = (q + s) * 0.125f;
+  w[3] = (q - s) * 0.125f;
+  dw[0] = (-2.0f - ds) * 0.125f;
+  dw[1] = (-2.0f + ds) * 0.125f;
+  dw[2] = (2.0f + ds) * 0.125f;
+  dw[3] = (2.0f - ds) * 0.125f;
+}
+
+struct Stencil {
+  float wx[4], wy[4], dx[4], dy[4];
+  int ix[4], iy[4];   // wrapped column / row-start indices
+};
+
+__device__ __forceinline__ Stencil make_stencil(const float4& p, int W, int H) {
+  Stencil s;
+  peskin4_d(p.x, s.wx, s.dx);
+  peskin4_d(p.y, s.wy, s.dy);
+  const int cx = cell_x(p), cy = cell_y(p);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    s.ix[a] = wrap_once(cx - 1 + a, W);
+    s.iy[a] = wrap_once(cy - 1 + a, H) * W;
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// a8 transposed: u_bar(c) += sum_i w(c - X_i) dt X_bar_i (float atomics).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_adj_spread_u(const WorldDev* __restrict__ wd, AdjDev a) {
+  const WorldDev& w = *wd;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= w.N) return;
+  const Stencil s = make_stencil(w.pos[i], w.W, w.H);
+  const float2 xb = a.adjX[i];
+  const float ux = w.dt * xb.x, uy = w.dt * xb.y;
+#pragma unroll
+  for (int b = 0; b < 4; ++b)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float wgt = s.wx[c] * s.wy[b];
+      float2* g = &a.ubar[s.iy[b] + s.ix[c]];
+      atomicAdd(&g->x, wgt * ux);
+      atomicAdd(&g->y, wgt * uy);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a7 transposed, per cell.  Forward (shifted populations d = f - w, pulled):
+//   drho = sum d, rho = 1 + drho, j = sum c d, u = (j + F/2)/rho,
+//   pair (i, opp): cu = c.u, cF = c.F, uu = u.u, uF = u.F,
+//     ep = w (drho + rho (4.5 cu^2 - 1.5 uu)), em = 3 w rho cu,
+//     sp = w (9 cu cF - 3 uF), sm = 3 w cF, dp = (d_i + d_o)/2, dm = (d_i - d_o)/2,
+//     even = -wp (dp - ep) + ap sp, odd = -wm (dm - em) + am sm,
+//     out_i = d_i + even + odd, out_o = d_o + even - odd;
+//   rest: e0 = w0 (drho - 1.5 rho uu), s0 = -3 w0 uF,
+//     out_0 = d_0 - wp (d_0 - e0) + ap s0.
+// Given out_bar (next step's population adjoint at this cell) and u_bar,
+// returns d_bar and F_bar; d_bar_i is pushed to the cell the population was
+// pulled from, so every adjoint population is written once.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_adj_lbm(const WorldDev* __restrict__ wd, AdjDev a, int src_parity) {
+  const WorldDev& w = *wd;
+  const int W = w.W, H = w.H, HW = H * W;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= HW) return;
+  const int y = c / W, x = c - y * W;
+  const int xm = x == 0 ? W - 1 : x - 1, xp = x == W - 1 ? 0 : x + 1;
+  const int ym = y == 0 ? H - 1 : y - 1, yp = y == H - 1 ? 0 : y + 1;
+  const int r0 = y * W, rm = ym * W, rp = yp * W;
+  // pull sources of populations 0..8 (same order as the forward kernel)
+  const int src[9] = {c, r0 + xm, rm + x, r0 + xp, rp + x, rm + xm, rm + xp, rp + xp, rp + xm};
+  const float* g = w.g[src_parity];
+  float d[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) d[i] = g[i * HW + src[i]];
+  const float2 F = w.F[c];
+  const float drho = ((d[0] + (d[1] + d[3])) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));
+  const float rho = 1.0f + drho;
+  const float jx = (d[1] - d[3]) + (d[5] - d[7]) + (d[8] - d[6]);
+  const float jy = (d[2] - d[4]) + (d[5] - d[7]) + (d[6] - d[8]);
+  const float inv = 1.0f / rho;
+  const float ux = (jx + 0.5f * F.x) * inv, uy = (jy + 0.5f * F.y) * inv;
+  const float uu = ux * ux + uy * uy, uF = ux * F.x + uy * F.y;
+  const float wp = w.om_p, wm = w.om_m, ap = w.src_p, am = w.src_m;
+
+  float ob[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) ob[i] = a.adjG_next[i * HW + c];
+  const float2 ubx = a.ubar[c];
+  float db[9];
+  float drho_b = 0.0f, rho_b = 0.0f, uu_b = 0.0f, uF_b = 0.0f;
+  float uxb = ubx.x, uyb = ubx.y, Fxb = 0.0f, Fyb = 0.0f;
+
+  // rest population
+  {
+    constexpr float w0 = 4.0f / 9.0f;
+    db[0] = (1.0f - wp) * ob[0];
+    const float e0b = wp * ob[0], s0b = ap * ob[0];
+    drho_b += w0 * e0b;
+    rho_b += -1.5f * w0 * uu * e0b;
+    uu_b += -1.5f * w0 * rho * e0b;
+    uF_b += -3.0f * w0 * s0b;
+  }
+  // opposite pairs (i, o) with lattice velocity (cx, cy)
+  constexpr int PI[4] = {1, 2, 5, 6}, PO[4] = {3, 4, 7, 8};
+  constexpr float PX[4] = {1.0f, 0.0f, 1.0f, -1.0f}, PY[4] = {0.0f, 1.0f, 1.0f, 1.0f};
+  constexpr float PW[4] = {1.0f / 9.0f, 1.0f / 9.0f, 1.0f / 36.0f, 1.0f / 36.0f};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int i = PI[k], o = PO[k];
+    const float cxv = PX[k], cyv = PY[k], wi = PW[k];
+    const float cu = cxv * ux + cyv * uy, cF = cxv * F.x + cyv * F.y;
+    const float evb = ob[i] + ob[o];
+    const float odb = ob[i] - ob[o];
+    const float dpb = -wp * evb, epb = wp * evb, spb = ap * evb;
+    const float dmb = -wm * odb, emb = wm * odb, smb = am * odb;
+    db[i] = ob[i] + 0.5f * dpb + 0.5f * dmb;
+    db[o] = ob[o] + 0.5f * dpb - 0.5f * dmb;
+    // ep = wi (drho + rho (4.5 cu^2 - 1.5 uu))
+    drho_b += wi * epb;
+    rho_b += wi * (4.5f * cu * cu - 1.5f * uu) * epb;
+    float cub = wi * rho * 9.0f * cu * epb;
+    uu_b += -1.5f * wi * rho * epb;
+    // em = 3 wi rho cu
+    rho_b += 3.0f * wi * cu * emb;
+    cub += 3.0f * wi * rho * emb;
+    // sp = wi (9 cu cF - 3 uF), sm = 3 wi cF
+    cub += 9.0f * wi * cF * spb;
+    float cFb = 9.0f * wi * cu * spb + 3.0f * wi * smb;
+    uF_b += -3.0f * wi * spb;
+    uxb += cxv * cub;
+    uyb += cyv * cub;
+    Fxb += cxv * cFb;
+    Fyb += cyv * cFb;
+  }
+  // uu = u.u, uF = u.F
+  uxb += 2.0f * ux * uu_b + F.x * uF_b;
+  uyb += 2.0f * uy * uu_b + F.y * uF_b;
+  Fxb += ux * uF_b;
+  Fyb += uy * uF_b;
+  // u = (j + F/2) / rho
+  const float jxb = uxb * inv, jyb = uyb * inv;
+  Fxb += 0.5f * jxb;
+  Fyb += 0.5f * jyb;
+  rho_b += -(uxb * ux + uyb * uy) * inv;
+  drho_b += rho_b;
+  // drho = sum d, j = sum c d
+  constexpr float CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1}, CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const float v = db[i] + drho_b + CX[i] * jxb + CY[i] * jyb;
+    a.adjG_cur[i * HW + src[i]] = v;   // adjoint of the pulled post-collision value
+  }
+  a.Fbar[c] = make_float2(Fxb, Fyb);
+}
+
+// ---------------------------------------------------------------------------
+// a8 and a6 gathers transposed, per bead:
+//   Ftot_bar_i = sum_c w F_bar(c)
+//   X_bar_i   += sum_c grad_X w [u(c).U_bar_i + F_bar(c).Ftot_i]
+// then Q(c) += w(c - X_i) Ftot_bar_i (float atomics) for the steric chain.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_adj_bead_a(const WorldDev* __restrict__ wd, AdjDev a) {
+  const WorldDev& w = *wd;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= w.N) return;
+  const Stencil s = make_stencil(w.pos[i], w.W, w.H);
+  const float2 xb = a.adjX[i];
+  const float Ubx = w.dt * xb.x, Uby = w.dt * xb.y;
+  const float2 fe = w.fel[i], fs = w.fs[i];
+  const float Ftx = fe.x + fs.x, Fty = fe.y + fs.y;
+  float ftbx = 0.0f, ftby = 0.0f, gx = 0.0f, gy = 0.0f;
+#pragma unroll
+  for (int b = 0; b < 4; ++b)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int k = s.iy[b] + s.ix[c];
+      const float2 u = w.u[k];
+      const float2 fb = a.Fbar[k];
+      const float wgt = s.wx[c] * s.wy[b];
+      ftbx = fmaf(wgt, fb.x, ftbx);
+      ftby = fmaf(wgt, fb.y, ftby);
+      const float q = u.x * Ubx + u.y * Uby + fb.x * Ftx + fb.y * Fty;
+      gx = fmaf(s.dx[c] * s.wy[b], q, gx);
+      gy = fmaf(s.wx[c] * s.dy[b], q, gy);
+    }
+  a.adjX[i] = make_float2(xb.x + gx, xb.y + gy);
+  a.fbt[i] = make_float2(ftbx, ftby);
+#pragma unroll
+  for (int b = 0; b < 4; ++b)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float wgt = s.wx[c] * s.wy[b];
+      float2* q = &a.Q[s.iy[b] + s.ix[c]];
+      atomicAdd(&q->x, wgt * ftbx);
+      atomicAdd(&q->y, wgt * ftby);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a6 gradient transposed: rho_bar_bar = -k_rep D^T Q with D the central
+// difference, (D^T v)(c) = (v_x(c - e_x) - v_x(c + e_x) + v_y(c - e_y) - v_y(c + e_y))/2.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_adj_rho(const WorldDev* __restrict__ wd, AdjDev a) {
+  const WorldDev& w = *wd;
+  const int W = w.W, H = w.H;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= H * W) return;
+  const int y = c / W, x = c - y * W;
+  const int xm = x == 0 ? W - 1 : x - 1, xp = x == W - 1 ? 0 : x + 1;
+  const int ym = y == 0 ? H - 1 : y - 1, yp = y == H - 1 ? 0 : y + 1;
+  const float v = a.Q[y * W + xm].x - a.Q[y * W + xp].x + a.Q[ym * W + x].y - a.Q[yp * W + x].y;
+  a.rbb[c] = -0.5f * w.k_rep * v;
+}
+
+// a5 transposed: the periodic separable filter (symmetric), x then y pass.
+__global__ void __launch_bounds__(256) k_adj_blur(const WorldDev* __restrict__ wd, const float* __restrict__ in,
+                                                  float* __restrict__ out, int along_y) {
+  const WorldDev& w = *wd;
+  const int W = w.W, H = w.H, R = w.R;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= H * W) return;
+  const int y = c / W, x = c - y * W;
+  float s = 0.0f;
+  if (along_y) {
+    for (int m = 0; m <= 2 * R; ++m) s = fmaf(w.taps[m], in[wrap_mod(y - R + m, H) * W + x], s);
+  } else {
+    for (int m = 0; m <= 2 * R; ++m) s = fmaf(w.taps[m], in[y * W + wrap_mod(x - R + m, W)], s);
+  }
+  out[c] = s;
+}
+
+// ---------------------------------------------------------------------------
+// a4 and the a6 gather transposed, per bead:
+//   X_bar_i += sum_c grad_X w [rho_s_bar(c) - k_rep grad rho_bar(c) . Ftot_bar_i]
+// and the elastic-force adjoint d_bar_i = kappa/dt Ftot_bar_i for the PBD.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_adj_bead_b(const WorldDev* __restrict__ wd, AdjDev a) {
+  const WorldDev& w = *wd;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= w.N) return;
+  const int W = w.W, H = w.H;
+  const float4 p = w.pos[i];
+  const Stencil s = make_stencil(p, W, H);
+  const float2 fb = a.fbt[i];
+  float gx = 0.0f, gy = 0.0f;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int row = s.iy[b];
+    const int rowm = wrap_once(cell_y(p) - 2 + b, H) * W, rowp = wrap_once(cell_y(p) + b, H) * W;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int col = s.ix[c];
+      const int colm = wrap_once(cell_x(p) - 2 + c, W), colp = wrap_once(cell_x(p) + c, W);
+      const float grx = 0.5f * (w.rho_b[row + colp] - w.rho_b[row + colm]);
+      const float gry = 0.5f * (w.rho_b[rowp + col] - w.rho_b[rowm + col]);
+      const float q = a.rsb[row + col] - w.k_rep * (grx * fb.x + gry * fb.y);
+      gx = fmaf(s.dx[c] * s.wy[b], q, gx);
+      gy = fmaf(s.wx[c] * s.dy[b], q, gy);
+    }
+  }
+  const float2 xb = a.adjX[i];
+  a.adjX[i] = make_float2(xb.x + gx, xb.y + gy);
+  a.dbar[i] = make_float2(w.kappa_dt * fb.x, w.kappa_dt * fb.y);
+}
+
+// ---------------------------------------------------------------------------
+// a3 + a1 transposed, one warp per filament.  The forward Jacobi PBD is
+// recomputed from (X^n, theta^n) keeping, per iteration, the frames after the
+// bending pass and the corrections before the position pass; then the
+// iterations are reversed:
+//   position pass (per edge, x = v0 + d_{e+1} - d_e, l = |x|, sc = 1 - L/l):
+//     D_e = hs [(1 - ksh) sc x + ksh (x - L d(theta))]
+//     theta_e += ko (cos y - sin x) / L
+//     d_i += D_i - D_{i-1}
+//   bending pass: C_j = theta_{j+1} - theta_j - theta_rest_j,
+//     theta_e += hb (C_e - C_{e-1})
+// Inputs: d_bar (from F_el), theta_bar of theta^{n+1}.  Outputs: X_bar +=
+// (through the edge vectors v0), theta_bar of theta^n, theta0_bar +=.
+// ---------------------------------------------------------------------------
+constexpr int kAdjPbdPerBead = 10;   // floats of working arrays per bead slot
+__global__ void __launch_bounds__(128) k_adj_pbd(const WorldDev* __restrict__ wd, AdjDev a,
+                                                 const int2* __restrict__ items, int n_items, int maxB,
+                                                 int n_pbd) {
+  extern __shared__ __align__(16) float smem[];
+  const WorldDev& w = *wd;
+  const int wpb = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int item = blockIdx.x * wpb + warp;
+  if (item >= n_items) return;
+  const int f = items[item].y;
+  const int b0 = w.fil_off[f];
+  const int B = w.fil_off[f + 1] - b0;
+  const int nE = B - 1, nJ = B - 2;
+  const int e0 = b0 - f, j0 = b0 - 2 * f;
+  const int per = maxB * (kAdjPbdPerBead + 3 * n_pbd + 2);
+  float* s = smem + (size_t)warp * per;
+  float* vx = s;
+  float* vy = s + maxB;
+  float* th = s + 2 * maxB;
+  float* Lr = s + 3 * maxB;
+  float* thr = s + 4 * maxB;
+  float* dx = s + 5 * maxB;     // corrections d (x); reused as d_bar later
+  float* dy = s + 6 * maxB;
+  float* Dx = s + 7 * maxB;     // per-edge D (x); reused for adjoint temporaries
+  float* Dy = s + 8 * maxB;
+  float* Cb = s + 9 * maxB;     // per-joint C / C_bar
+  float* tape = s + 10 * maxB;  // per iteration: theta after bend [maxB], d before pos [2 maxB]
+  const int W = w.W, H = w.H;
+  const long long t = *w.t;
+  for (int e = lane; e < nE; e += 32) {
+    const float4 pa = w.pos[b0 + e], pb = w.pos[b0 + e + 1];
+    int dcx = cell_x(pb) - cell_x(pa), dcy = cell_y(pb) - cell_y(pa);
+    if (2 * dcx > W) dcx -= W; else if (2 * dcx < -W) dcx += W;
+    if (2 * dcy > H) dcy -= H; else if (2 * dcy < -H) dcy += H;
+    vx[e] = (float)dcx + (pb.x - pa.x);
+    vy[e] = (float)dcy + (pb.y - pa.y);
+    th[e] = a.theta_n[e0 + e];
+    Lr[e] = w.L_rest[e0 + e];
+  }
+  for (int j = lane; j < nJ; j += 32) {
+    const float4 d = w.drive[j0 + j];
+    const float tf = (float)t;
+    const float hi = d.z * tf;
+    const float lo = fmaf(d.z, tf, -hi);
+    float fr = (hi - rintf(hi)) + lo + d.w;
+    fr -= rintf(fr);
+    thr[j] = d.x + d.y * sinpif(2.0f * fr);
+  }
+  for (int i = lane; i < B; i += 32) {
+    dx[i] = 0.0f;
+    dy[i] = 0.0f;
+  }
+  __syncwarp();
+  const float hb = 0.5f * w.k_bend, hs = 0.5f * w.k_st, ksh = w.k_sh;
+  const float ko = w.orient * hs * ksh;
+  // ---- forward recompute with tape ----
+  for (int it = 0; it < n_pbd; ++it) {
+    for (int j = lane; j < nJ; j += 32) Cb[j] = th[j + 1] - th[j] - thr[j];
+    __syncwarp();
+    for (int e = lane; e < nE; e += 32) {
+      const float c1 = e < nJ ? Cb[e] : 0.0f, c0 = e > 0 ? Cb[e - 1] : 0.0f;
+      th[e] += hb * (c1 - c0);
+    }
+    __syncwarp();
+    float* tp = tape + it * 3 * maxB;
+    for (int e = lane; e < nE; e += 32) tp[e] = th[e];
+    for (int i = lane; i < B; i += 32) {
+      tp[maxB + i] = dx[i];
+      tp[2 * maxB + i] = dy[i];
+    }
+    for (int e = lane; e < nE; e += 32) {
+      const float x = vx[e] + (dx[e + 1] - dx[e]);
+      const float y = vy[e] + (dy[e + 1] - dy[e]);
+      const float L = Lr[e];
+      const float ell = sqrtf(x * x + y * y);
+      const float sc = (ell - L) / ell;
+      float sn, cs;
+      sincosf(th[e], &sn, &cs);
+      Dx[e] = hs * (sc * x + ksh * (x - L * cs - sc * x));
+      Dy[e] = hs * (sc * y + ksh * (y - L * sn - sc * y));
+      th[e] += ko * (cs * y - sn * x) / L;
+    }
+    __syncwarp();
+    for (int i = lane; i < B; i += 32) {
+      const float ax = i < nE ? Dx[i] : 0.0f, ay = i < nE ? Dy[i] : 0.0f;
+      const float bx = i > 0 ? Dx[i - 1] : 0.0f, by = i > 0 ? Dy[i - 1] : 0.0f;
+      dx[i] += ax - bx;
+      dy[i] += ay - by;
+    }
+    __syncwarp();
+  }
+  // ---- reverse ----
+  // adjoint state: d_bar in dx/dy, theta_bar in th, theta_rest_bar in thr
+  // (theta_rest is no longer needed), edge-vector adjoint v0_bar after the tape
+  for (int i = lane; i < B; i += 32) {
+    const float2 db = a.dbar[b0 + i];
+    dx[i] = db.x;
+    dy[i] = db.y;
+  }
+  for (int e = lane; e < nE; e += 32) th[e] = a.adjTh[e0 + e];
+  for (int j = lane; j < nJ; j += 32) thr[j] = 0.0f;
+  float* v0bx = tape + n_pbd * 3 * maxB;
+  float* v0by = v0bx + maxB;
+  for (int e = lane; e < nE; e += 32) {
+    v0bx[e] = 0.0f;
+    v0by[e] = 0.0f;
+  }
+  __syncwarp();
+  for (int it = n_pbd - 1; it >= 0; --it) {
+    const float* tp = tape + it * 3 * maxB;
+    // position pass reverse: D_bar_e = d_bar_e - d_bar_{e+1}
+    for (int e = lane; e < nE; e += 32) {
+      const float Dbx = dx[e] - dx[e + 1], Dby = dy[e] - dy[e + 1];
+      const float thb = th[e];   // adjoint of theta after this pass
+      const float tb = tp[e];    // forward theta before this pass (after bend)
+      const float x = vx[e] + (tp[maxB + e + 1] - tp[maxB + e]);
+      const float y = vy[e] + (tp[2 * maxB + e + 1] - tp[2 * maxB + e]);
+      const float L = Lr[e];
+      const float ell = sqrtf(x * x + y * y);
+      const float sc = (ell - L) / ell;
+      float sn, cs;
+      sincosf(tb, &sn, &cs);
+      // D = hs [(1 - ksh) sc x + ksh x - ksh L d]
+      const float xd = x * Dbx + y * Dby;
+      const float kq = hs * (1.0f - ksh) * (L / (ell * ell * ell)) * xd;
+      float xbx = hs * ((1.0f - ksh) * sc + ksh) * Dbx + kq * x;
+      float xby = hs * ((1.0f - ksh) * sc + ksh) * Dby + kq * y;
+      float thb_new = thb + (-hs * ksh * L) * (-sn * Dbx + cs * Dby);
+      // theta += ko (cs y - sn x) / L
+      thb_new += thb * ko * (-sn * y - cs * x) / L;
+      xbx += thb * ko * (-sn) / L;
+      xby += thb * ko * cs / L;
+      Dx[e] = xbx;
+      Dy[e] = xby;
+      th[e] = thb_new;
+      v0bx[e] += xbx;
+      v0by[e] += xby;
+    }
+    __syncwarp();
+    // x = v0 + d_{e+1} - d_e: d_bar_i += x_bar_{i-1} - x_bar_i
+    for (int i = lane; i < B; i += 32) {
+      const float ax = i < nE ? Dx[i] : 0.0f, ay = i < nE ? Dy[i] : 0.0f;
+      const float bx = i > 0 ? Dx[i - 1] : 0.0f, by = i > 0 ? Dy[i - 1] : 0.0f;
+      dx[i] += bx - ax;
+      dy[i] += by - ay;
+    }
+    __syncwarp();
+    // bending pass reverse: C_bar_j = hb (theta_bar_j - theta_bar_{j+1})
+    for (int j = lane; j < nJ; j += 32) Cb[j] = hb * (th[j] - th[j + 1]);
+    __syncwarp();
+    for (int e = lane; e < nE; e += 32) {
+      const float in = e > 0 ? Cb[e - 1] : 0.0f;     // theta_e is theta_{j+1} of joint e-1
+      const float out = e < nJ ? Cb[e] : 0.0f;       // ... and theta_j of joint e
+      th[e] += in - out;
+    }
+    for (int j = lane; j < nJ; j += 32) thr[j] -= Cb[j];
+    __syncwarp();
+  }
+  // outputs
+  for (int e = lane; e < nE; e += 32) a.adjTh[e0 + e] = th[e];
+  for (int j = lane; j < nJ; j += 32) a.gth0[j0 + j] += thr[j];
+  for (int i = lane; i < B; i += 32) {
+    const float ax = i < nE ? v0bx[i] : 0.0f, ay = i < nE ? v0by[i] : 0.0f;        // X_i is x_1 of edge i
+    const float bx = i > 0 ? v0bx[i - 1] : 0.0f, by = i > 0 ? v0by[i - 1] : 0.0f;  // ... x_2 of edge i-1
+    float2 xb = a.adjX[b0 + i];
+    xb.x += bx - ax;
+    xb.y += by - ay;
+    a.adjX[b0 + i] = xb;
+  }
+}
+
+size_t adj_pbd_smem_per_warp(int maxB, int n_pbd) {
+  return (size_t)maxB * (kAdjPbdPerBead + 3 * n_pbd + 2) * sizeof(float);
+}
+
+// ---------------------------------------------------------------------------
+// Folding loss (Filament Folding experiment, with a polyline target): mean
+// over beads of the squared distance from the unwrapped position
+// P_i = X0_i + D_i to the nearest segment of the polyline, and dL/dP_i.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_loss_polyline(const WorldDev* __restrict__ wd, const float2* __restrict__ pos0,
+                                                       const float2* __restrict__ poly, int nv, float* loss,
+                                                       float* gx, float* gy) {
+  const WorldDev& w = *wd;
+  __shared__ float red[256];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float l = 0.0f;
+  if (i < w.N) {
+    const float2 d = w.disp[i];
+    const float px = pos0[i].x + d.x, py = pos0[i].y + d.y;
+    float best = 3.0e38f, qx = px, qy = py;
+    for (int k = 0; k + 1 < nv; ++k) {
+      const float2 A = poly[k], B = poly[k + 1];
+      const float abx = B.x - A.x, aby = B.y - A.y;
+      float tt = ((px - A.x) * abx + (py - A.y) * aby) / (abx * abx + aby * aby);
+      tt = fminf(fmaxf(tt, 0.0f), 1.0f);
+      const float cx = A.x + tt * abx, cy = A.y + tt * aby;
+      const float d2 = (px - cx) * (px - cx) + (py - cy) * (py - cy);
+      if (d2 < best) {
+        best = d2;
+        qx = cx;
+        qy = cy;
+      }
+    }
+    const float invN = 1.0f / (float)w.N;
+    l = best * invN;
+    gx[i] = 2.0f * (px - qx) * invN;
+    gy[i] = 2.0f * (py - qy) * invN;
+  }
+  red[threadIdx.x] = l;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(loss, red[0]);
+}
+
+__global__ void k_set_counter(long long* t, long long v, unsigned* fel_max) {
+  *t = v;
+  fel_max[0] = 0u;
+  fel_max[1] = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (one world).
+// ---------------------------------------------------------------------------
+static int blocks(int n) { return (n + 255) / 256; }
+
+void launch_adj_step(const Plan& p, const WorldDev& h, AdjDev a, int src_parity, cudaStream_t s) {
+  const WorldDev* wd = p.d_worlds;
+  const int HW = h.H * h.W;
+  cudaMemsetAsync(a.ubar, 0, HW * sizeof(float2), s);
+  cudaMemsetAsync(a.Q, 0, HW * sizeof(float2), s);
+  if (h.N) k_adj_spread_u<<<blocks(h.N), 256, 0, s>>>(wd, a);
+  k_adj_lbm<<<blocks(HW), 256, 0, s>>>(wd, a, src_parity);
+  if (h.N) k_adj_bead_a<<<blocks(h.N), 256, 0, s>>>(wd, a);
+  k_adj_rho<<<blocks(HW), 256, 0, s>>>(wd, a);
+  k_adj_blur<<<blocks(HW), 256, 0, s>>>(wd, a.rbb, a.tmp, 0);
+  k_adj_blur<<<blocks(HW), 256, 0, s>>>(wd, a.tmp, a.rsb, 1);
+  if (h.N) k_adj_bead_b<<<blocks(h.N), 256, 0, s>>>(wd, a);
+  if (p.n_fil_items) {
+    const int mb = (p.max_B + 3) & ~3;
+    const size_t per = adj_pbd_smem_per_warp(mb, h.n_pbd);
+    int wpb = (int)((48 * 1024) / per);
+    wpb = wpb < 1 ? 1 : (wpb > 4 ? 4 : wpb);
+    const size_t smem = per * wpb;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_adj_pbd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_adj_pbd<<<(p.n_fil_items + wpb - 1) / wpb, wpb * 32, smem, s>>>(wd, a, p.d_fil_items, p.n_fil_items, mb,
+                                                                     h.n_pbd);
+  }
+}
+
+void launch_loss_polyline(const Plan& p, const WorldDev& h, const float2* pos0, const float2* poly, int nv,
+                          float* loss, float* gx, float* gy, cudaStream_t s) {
+  cudaMemsetAsync(loss, 0, sizeof(float), s);
+  if (h.N) k_loss_polyline<<<blocks(h.N), 256, 0, s>>>(p.d_worlds, pos0, poly, nv, loss, gx, gy);
+}
+
+void launch_set_counter(const WorldDev& h, long long t, cudaStream_t s) {
+  k_set_counter<<<1, 1, 0, s>>>(h.t, t, h.fel_max);
+}
+
+}  // namespace mc

@@ -1,0 +1,239 @@
+// Reverse mode through a rollout: forward with checkpoints, then the adjoint
+// sweep with per-segment recompute (checkpoint-and-recompute every K steps).
+//
+// mc_rollout_forward   advances the world n steps and stores its state (bead
+//                      positions, edge angles, populations) every K steps and
+//                      at the end.
+// mc_rollout_backward  given dL/d(final unwrapped positions), walks the
+//                      segments from last to first: re-runs the segment's
+//                      forward from its checkpoint keeping every step's
+//                      state, then for each step from last to first restores
+//                      it, recomputes that step's intermediates with the
+//                      forward kernels and applies the adjoint kernels.
+//                      Accumulates dL/dtheta0 and leaves the world in its
+//                      final state.
+#include <algorithm>
+#include <cstring>
+#include <string>
+
+#include "mc_internal.cuh"
+
+namespace {
+
+mc_status afail(mc_status s, const std::string& m) {
+  mc::set_last_error(m.c_str());
+  return s;
+}
+
+#define MC_ACUDA(call)                                                                        \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return afail(MC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct StateSlot {
+  size_t pos, theta, g;   // byte offsets inside one state record
+  size_t bytes;
+};
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+StateSlot state_slot(const mc::WorldDev& h) {
+  StateSlot s;
+  s.pos = 0;
+  s.theta = align256((size_t)h.N * sizeof(float4));
+  s.g = s.theta + align256((size_t)h.E * sizeof(float));
+  s.bytes = s.g + align256((size_t)9 * h.H * h.W * sizeof(float));
+  return s;
+}
+
+mc_status save_state(const mc::WorldDev& h, int parity, char* rec, const StateSlot& sl, cudaStream_t s) {
+  const size_t HW = (size_t)h.H * h.W;
+  if (h.N) MC_ACUDA(cudaMemcpyAsync(rec + sl.pos, h.pos, h.N * sizeof(float4), cudaMemcpyDeviceToDevice, s));
+  if (h.E) MC_ACUDA(cudaMemcpyAsync(rec + sl.theta, h.theta, h.E * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  MC_ACUDA(cudaMemcpyAsync(rec + sl.g, h.g[parity], 9 * HW * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  return MC_OK;
+}
+
+mc_status load_state(const mc::WorldDev& h, int parity, const char* rec, const StateSlot& sl, cudaStream_t s) {
+  const size_t HW = (size_t)h.H * h.W;
+  if (h.N) MC_ACUDA(cudaMemcpyAsync(h.pos, rec + sl.pos, h.N * sizeof(float4), cudaMemcpyDeviceToDevice, s));
+  if (h.E) MC_ACUDA(cudaMemcpyAsync(h.theta, rec + sl.theta, h.E * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  MC_ACUDA(cudaMemcpyAsync(h.g[parity], rec + sl.g, 9 * HW * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  return MC_OK;
+}
+
+__global__ void k_interleave(const float* gx, const float* gy, float2* out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_float2(gx[i], gy[i]);
+}
+
+}  // namespace
+
+extern "C" {
+
+mc_status mc_rollout_forward(mc_world* w, int n_steps, int ckpt_every, void* stream) {
+  if (!w || n_steps < 1 || ckpt_every < 1) return afail(MC_ERR_INVALID_ARG, "need a world, n_steps >= 1, ckpt_every >= 1");
+  if (w->t + n_steps >= (int64_t(1) << 24)) return afail(MC_ERR_INVALID_ARG, "step counter would reach 2^24");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const mc::WorldDev& h = w->h;
+  const StateSlot sl = state_slot(h);
+  const int n_ck = (n_steps + ckpt_every - 1) / ckpt_every;
+  const size_t fin_disp = align256((size_t)h.N * sizeof(float2));
+  const size_t need = (size_t)(n_ck + 1) * sl.bytes + fin_disp;
+  if (w->tape_bytes < need) {
+    if (w->tape) cudaFreeAsync(w->tape, w->stream);
+    w->tape = nullptr;
+    w->tape_bytes = 0;
+    cudaError_t e = cudaMallocAsync(&w->tape, need, s);
+    if (e != cudaSuccess) return afail(MC_ERR_OOM, std::string("checkpoint allocation: ") + cudaGetErrorString(e));
+    w->tape_bytes = need;
+  }
+  char* tape = static_cast<char*>(w->tape);
+  w->tape_t0 = w->t;
+  w->tape_steps = n_steps;
+  w->tape_every = ckpt_every;
+  int done = 0;
+  for (int k = 0; k < n_ck; ++k) {
+    mc_status st = save_state(h, (int)(w->t & 1), tape + (size_t)k * sl.bytes, sl, s);
+    if (st != MC_OK) return st;
+    const int steps = std::min(ckpt_every, n_steps - done);
+    st = mc::plan_run(w->plan, steps, s);
+    if (st != MC_OK) return st;
+    w->t += steps;
+    done += steps;
+  }
+  mc_status st = save_state(h, (int)(w->t & 1), tape + (size_t)n_ck * sl.bytes, sl, s);
+  if (st != MC_OK) return st;
+  if (h.N)
+    MC_ACUDA(cudaMemcpyAsync(tape + (size_t)(n_ck + 1) * sl.bytes, h.disp, h.N * sizeof(float2),
+                             cudaMemcpyDeviceToDevice, s));
+  return MC_OK;
+}
+
+mc_status mc_rollout_backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* dL_dtheta0, void* stream) {
+  if (!w) return afail(MC_ERR_INVALID_ARG, "world is NULL");
+  if (!w->tape || w->tape_steps < 1) return afail(MC_ERR_INVALID_ARG, "no rollout recorded: call mc_rollout_forward first");
+  if (w->t != w->tape_t0 + w->tape_steps)
+    return afail(MC_ERR_INVALID_ARG, "the world was stepped after mc_rollout_forward");
+  const mc::WorldDev& h = w->h;
+  if ((h.N && (!dL_dx || !dL_dy)) || (h.J && !dL_dtheta0)) return afail(MC_ERR_INVALID_ARG, "NULL gradient pointer");
+  const int mb = (w->max_B + 3) & ~3;
+  if (mc::adj_pbd_smem_per_warp(mb, h.n_pbd) > 220 * 1024)
+    return afail(MC_ERR_INVALID_ARG, "filaments too long for the adjoint (reduce beads per filament or n_pbd)");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t HW = (size_t)h.H * h.W;
+  const StateSlot sl = state_slot(h);
+  const int K = w->tape_every, n = w->tape_steps;
+  const int n_ck = (n + K - 1) / K;
+  // adjoint work memory: buffers + one segment of per-step states
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align256(off + bytes);
+    return at;
+  };
+  const size_t o_adjX = take(h.N * sizeof(float2));
+  const size_t o_adjTh = take(h.E * sizeof(float));
+  const size_t o_gth0 = take(h.J * sizeof(float));
+  const size_t o_g0 = take(9 * HW * sizeof(float));
+  const size_t o_g1 = take(9 * HW * sizeof(float));
+  const size_t o_ub = take(HW * sizeof(float2));
+  const size_t o_Fb = take(HW * sizeof(float2));
+  const size_t o_Q = take(HW * sizeof(float2));
+  const size_t o_rbb = take(HW * sizeof(float));
+  const size_t o_tmp = take(HW * sizeof(float));
+  const size_t o_rsb = take(HW * sizeof(float));
+  const size_t o_fbt = take(h.N * sizeof(float2));
+  const size_t o_dbar = take(h.N * sizeof(float2));
+  const size_t o_seg = take((size_t)K * sl.bytes);
+  if (w->adj_bytes < off) {
+    if (w->adj) cudaFreeAsync(w->adj, w->stream);
+    w->adj = nullptr;
+    w->adj_bytes = 0;
+    cudaError_t e = cudaMallocAsync(&w->adj, off, s);
+    if (e != cudaSuccess) return afail(MC_ERR_OOM, std::string("adjoint allocation: ") + cudaGetErrorString(e));
+    w->adj_bytes = off;
+  }
+  char* A = static_cast<char*>(w->adj);
+  char* tape = static_cast<char*>(w->tape);
+  char* seg = A + o_seg;
+  mc::AdjDev a{};
+  a.adjX = reinterpret_cast<float2*>(A + o_adjX);
+  a.adjTh = reinterpret_cast<float*>(A + o_adjTh);
+  a.gth0 = reinterpret_cast<float*>(A + o_gth0);
+  float* adjG[2] = {reinterpret_cast<float*>(A + o_g0), reinterpret_cast<float*>(A + o_g1)};
+  a.ubar = reinterpret_cast<float2*>(A + o_ub);
+  a.Fbar = reinterpret_cast<float2*>(A + o_Fb);
+  a.Q = reinterpret_cast<float2*>(A + o_Q);
+  a.rbb = reinterpret_cast<float*>(A + o_rbb);
+  a.tmp = reinterpret_cast<float*>(A + o_tmp);
+  a.rsb = reinterpret_cast<float*>(A + o_rsb);
+  a.fbt = reinterpret_cast<float2*>(A + o_fbt);
+  a.dbar = reinterpret_cast<float2*>(A + o_dbar);
+
+  if (h.N) k_interleave<<<(h.N + 255) / 256, 256, 0, s>>>(dL_dx, dL_dy, a.adjX, h.N);
+  if (h.E) MC_ACUDA(cudaMemsetAsync(a.adjTh, 0, h.E * sizeof(float), s));
+  if (h.J) MC_ACUDA(cudaMemsetAsync(a.gth0, 0, h.J * sizeof(float), s));
+  MC_ACUDA(cudaMemsetAsync(adjG[0], 0, 9 * HW * sizeof(float), s));
+  int cur = 0;   // adjG[cur] holds the adjoint of the populations after the step being reversed
+  const int64_t t0 = w->tape_t0;
+  for (int k = n_ck - 1; k >= 0; --k) {
+    const int steps = std::min(K, n - k * K);
+    const int64_t tk = t0 + (int64_t)k * K;
+    // re-run the segment from its checkpoint, keeping every step's state
+    mc_status st = load_state(h, (int)(tk & 1), tape + (size_t)k * sl.bytes, sl, s);
+    if (st != MC_OK) return st;
+    mc::launch_set_counter(h, tk, s);
+    for (int q = 0; q < steps; ++q) {
+      st = save_state(h, (int)((tk + q) & 1), seg + (size_t)q * sl.bytes, sl, s);
+      if (st != MC_OK) return st;
+      mc::enqueue_step(w->plan, s);
+    }
+    for (int q = steps - 1; q >= 0; --q) {
+      const int64_t tn = tk + q;
+      const int par = (int)(tn & 1);
+      const char* rec = seg + (size_t)q * sl.bytes;
+      st = load_state(h, par, rec, sl, s);
+      if (st != MC_OK) return st;
+      mc::launch_set_counter(h, tn, s);
+      // this step's intermediates (F_el, F_s, rho_bar, F, u)
+      mc::launch_pbd(w->plan, s);
+      mc::launch_bin_scan(w->plan, s);
+      mc::launch_bin_scatter(w->plan, s);
+      mc::launch_deposit_x(w->plan, s, 0);
+      mc::launch_force_spread(w->plan, s, 1, 0);
+      mc::launch_lbm(w->plan, s);
+      a.adjG_next = adjG[cur];
+      a.adjG_cur = adjG[cur ^ 1];
+      a.theta_n = reinterpret_cast<const float*>(rec + sl.theta);
+      mc::launch_adj_step(w->plan, h, a, par, s);
+      cur ^= 1;
+    }
+    MC_ACUDA(cudaGetLastError());
+  }
+  if (h.J) MC_ACUDA(cudaMemcpyAsync(dL_dtheta0, a.gth0, h.J * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  // back to the final state of the rollout
+  const int64_t tf = t0 + n;
+  mc_status st = load_state(h, (int)(tf & 1), tape + (size_t)n_ck * sl.bytes, sl, s);
+  if (st != MC_OK) return st;
+  if (h.N)
+    MC_ACUDA(cudaMemcpyAsync(h.disp, tape + (size_t)(n_ck + 1) * sl.bytes, h.N * sizeof(float2),
+                             cudaMemcpyDeviceToDevice, s));
+  mc::launch_set_counter(h, tf, s);
+  MC_ACUDA(cudaGetLastError());
+  return MC_OK;
+}
+
+mc_status mc_loss_polyline(mc_world* w, const float* poly_xy, int n_vertices, float* loss, float* dL_dx, float* dL_dy,
+                           void* stream) {
+  if (!w || !poly_xy || !loss || n_vertices < 2) return afail(MC_ERR_INVALID_ARG, "need a world, >= 2 vertices, outputs");
+  const mc::WorldDev& h = w->h;
+  if (h.N && (!dL_dx || !dL_dy)) return afail(MC_ERR_INVALID_ARG, "NULL gradient pointer");
+  mc::launch_loss_polyline(w->plan, h, h.pos0, reinterpret_cast<const float2*>(poly_xy), n_vertices, loss, dL_dx,
+                           dL_dy, static_cast<cudaStream_t>(stream));
+  MC_ACUDA(cudaGetLastError());
+  return MC_OK;
+}
+
+}  // extern "C"

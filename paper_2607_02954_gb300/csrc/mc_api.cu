@@ -250,6 +250,7 @@ size_t world_layout(WorldDev& h, void* A) {
   const size_t o_fo = L.take<int>(h.n_fil + 1);
   const size_t o_pos = L.take<float4>(N);
   const size_t o_disp = L.take<float2>(N);
+  const size_t o_pos0 = L.take<float2>(N);
   const size_t o_th = L.take<float>(E);
   const size_t o_L = L.take<float>(E);
   const size_t o_dr = L.take<float4>(J);
@@ -279,6 +280,7 @@ size_t world_layout(WorldDev& h, void* A) {
   h.fil_off = at<int>(A, o_fo);
   h.pos = at<float4>(A, o_pos);
   h.disp = at<float2>(A, o_disp);
+  h.pos0 = at<float2>(A, o_pos0);
   h.theta = at<float>(A, o_th);
   h.L_rest = at<float>(A, o_L);
   h.drive = at<float4>(A, o_dr);
@@ -380,6 +382,7 @@ mc_status mc_world_create(const mc_world_desc* d, void* stream, mc_world** out) 
 
   // host images of the device arrays
   std::vector<float4> pos(N), drive(J);
+  std::vector<float2> pos0(N);
   for (int i = 0; i < N; ++i) {
     const double xd = std::fmod((double)x[i], (double)W), yd = std::fmod((double)y[i], (double)H);
     float xw = (float)(xd < 0 ? xd + W : xd), yw = (float)(yd < 0 ? yd + H : yd);
@@ -389,6 +392,7 @@ mc_status mc_world_create(const mc_world_desc* d, void* stream, mc_world** out) 
     int icx, icy;
     icx = (int)cx;
     icy = (int)cy;
+    pos0[i] = make_float2(xw, yw);
     float4 p;
     p.x = xw - cx;   // exact
     p.y = yw - cy;
@@ -433,6 +437,7 @@ mc_status mc_world_create(const mc_world_desc* d, void* stream, mc_world** out) 
   };
   MC_CUDA_W(up((void*)h.fil_off, fo.data(), fo.size() * sizeof(int)));
   MC_CUDA_W(up(h.pos, pos.data(), N * sizeof(float4)));
+  MC_CUDA_W(up(h.pos0, pos0.data(), N * sizeof(float2)));
   MC_CUDA_W(up(h.theta, th.data(), E * sizeof(float)));
   MC_CUDA_W(up((void*)h.L_rest, Lr.data(), E * sizeof(float)));
   MC_CUDA_W(up((void*)h.drive, drive.data(), J * sizeof(float4)));
@@ -458,6 +463,8 @@ mc_status mc_world_destroy(mc_world* w) {
   if (!w) return MC_OK;
   drop_plans_with(w);
   free_plan(w->plan, w->stream);
+  if (w->tape) cudaFreeAsync(w->tape, w->stream);
+  if (w->adj) cudaFreeAsync(w->adj, w->stream);
   cudaFreeAsync(w->arena, w->stream);
   delete w;
   return MC_OK;

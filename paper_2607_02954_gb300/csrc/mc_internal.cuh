@@ -46,6 +46,7 @@ struct WorldDev {
   const int* fil_off;     // [n_fil + 1]
   float4* pos;            // [N]  (frac x, frac y, int cell x, int cell y)
   float2* disp;           // [N]
+  float2* pos0;           // [N] positions at creation (unwrapped position = pos0 + disp)
   float* theta;           // [E]
   const float* L_rest;    // [E]
   const float4* drive;    // [J]  (theta0, amp, freq, phase)
@@ -70,6 +71,24 @@ struct WorldDev {
   long long* t;           // step counter
   unsigned* fel_max;      // [2] largest |F_el| component of the step, by step parity (float bits)
   unsigned* flags;        // watchdog flags
+};
+
+// Adjoint buffers of one world (reverse-mode sweep), all device pointers.
+struct AdjDev {
+  float2* adjX;            // [N] adjoint of the bead positions
+  float* adjTh;            // [E] adjoint of the edge angles
+  float* gth0;             // [J] accumulated gradient with respect to theta0
+  const float* adjG_next;  // [9 H W] adjoint of the populations after the step
+  float* adjG_cur;         // [9 H W] adjoint of the populations before it
+  float2* ubar;            // [H W] adjoint of the fluid velocity
+  float2* Fbar;            // [H W] adjoint of the force density
+  float2* Q;               // [H W] spread of the steric-force adjoint
+  float* rbb;              // [H W] adjoint of rho_bar
+  float* tmp;              // [H W] filter scratch
+  float* rsb;              // [H W] adjoint of rho_s
+  float2* fbt;             // [N] adjoint of F_el + F_s per bead
+  float2* dbar;            // [N] adjoint of the PBD correction
+  const float* theta_n;    // [E] edge angles at the start of the step
 };
 
 // A set of worlds advanced together, with the work items of each stage.
@@ -102,6 +121,13 @@ void launch_lbm(const Plan& p, cudaStream_t s);
 void launch_interp_advance(const Plan& p, cudaStream_t s);
 void enqueue_step(const Plan& p, cudaStream_t s);
 constexpr int kKernelsPerStep = 8;
+
+// --- adjoint (one world) ----------------------------------------------------
+void launch_adj_step(const Plan& p, const WorldDev& h, AdjDev a, int src_parity, cudaStream_t s);
+size_t adj_pbd_smem_per_warp(int maxB, int n_pbd);
+void launch_loss_polyline(const Plan& p, const WorldDev& h, const float2* pos0, const float2* poly, int nv,
+                          float* loss, float* gx, float* gy, cudaStream_t s);
+void launch_set_counter(const WorldDev& h, long long t, cudaStream_t s);
 
 // --- set-up / read-out kernels (one world) --------------------------------
 void launch_unstream_in(const float* f0dev, float* g_dst, int H, int W, cudaStream_t s);
@@ -170,4 +196,11 @@ struct mc_world {
   std::vector<int> fil_off;
   mc::Plan plan;                  // single-world plan
   mc_params params{};
+  // reverse-mode state (mc_rollout_forward / mc_rollout_backward)
+  void* tape = nullptr;           // checkpoints + final state
+  size_t tape_bytes = 0;
+  int tape_steps = 0, tape_every = 0;
+  int64_t tape_t0 = 0;
+  void* adj = nullptr;            // adjoint buffers + per-segment step tape
+  size_t adj_bytes = 0;
 };

@@ -153,6 +153,32 @@ class World:
                                              None, L.MC_MEM_DEVICE, stream_handle(stream)))
         return out
 
+    # -- reverse mode ---------------------------------------------------------
+    def rollout_forward(self, n_steps: int, ckpt_every: int = 100, stream=None):
+        L.check(self._lib.mc_rollout_forward(self.handle, int(n_steps), int(ckpt_every), stream_handle(stream)))
+
+    def rollout_backward(self, dL_dx, dL_dy, stream=None):
+        """dL_dx, dL_dy: torch CUDA float32 [N]; returns dL/dtheta0 as a torch CUDA tensor [J]."""
+        torch = _torch()
+        gx = dL_dx.contiguous().float()
+        gy = dL_dy.contiguous().float()
+        out = torch.empty(self.spec.J, device="cuda", dtype=torch.float32)
+        L.check(self._lib.mc_rollout_backward(self.handle, ctypes.c_void_p(gx.data_ptr()), ctypes.c_void_p(gy.data_ptr()),
+                                              ctypes.c_void_p(out.data_ptr() if out.numel() else 0), stream_handle(stream)))
+        return out
+
+    def loss_polyline(self, poly, stream=None):
+        """Folding loss against a polyline (numpy [V, 2]); returns (loss tensor [1], dL_dx, dL_dy)."""
+        torch = _torch()
+        pl = torch.as_tensor(np.ascontiguousarray(poly, np.float32)).cuda()
+        loss = torch.zeros(1, device="cuda", dtype=torch.float32)
+        gx = torch.empty(self.spec.N, device="cuda", dtype=torch.float32)
+        gy = torch.empty(self.spec.N, device="cuda", dtype=torch.float32)
+        L.check(self._lib.mc_loss_polyline(self.handle, ctypes.c_void_p(pl.data_ptr()), int(pl.shape[0]),
+                                           ctypes.c_void_p(loss.data_ptr()), ctypes.c_void_p(gx.data_ptr()),
+                                           ctypes.c_void_p(gy.data_ptr()), stream_handle(stream)))
+        return loss, gx, gy
+
     def field(self, name: str, stream=None) -> np.ndarray:
         """Host copy of one field of the last completed step (see mc_field)."""
         s = self.spec

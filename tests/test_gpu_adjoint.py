@@ -1,0 +1,144 @@
+"""GPU tests of the reverse mode (mc_rollout_forward / mc_rollout_backward).
+
+The hand-written adjoint in FP32 is compared with the FP64 oracle's
+reverse-mode gradient (torch.autograd through the oracle's rollout) and with
+FP64 central finite differences of the oracle's loss; the gradient must not
+depend on the checkpoint spacing.  Tolerance: 1e-3 of the gradient's scale.
+"""
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2607_02954_gb300 import synth
+from tests.helpers import t2n
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_02954_gb300 import World  # noqa: F401  (loads libmc)
+    yield
+
+
+def _gpu_grad(spec, n, K, gx, gy):
+    from paper_2607_02954_gb300 import World
+    w = World(spec)
+    w.rollout_forward(n, K)
+    g = w.rollout_backward(torch.as_tensor(gx, dtype=torch.float32).cuda(),
+                           torch.as_tensor(gy, dtype=torch.float32).cuda())
+    out = t2n(g).astype(np.float64)
+    w.close()
+    return out
+
+
+def _oracle_grad(spec, n, gx, gy):
+    ow = O.World(spec)
+    return t2n(O.final_position_gradient(ow, n, torch.as_tensor(gx, dtype=torch.float64),
+                                         torch.as_tensor(gy, dtype=torch.float64)))
+
+
+@pytest.mark.parametrize("case", ["tiny", "c1", "custom"])
+def test_adjoint_matches_oracle_reverse_mode(case):
+    rng = np.random.default_rng(3)
+    if case == "tiny":
+        spec, n, K = synth.tiny_world(3, side=32, lengths=(9, 7, 6)), 30, 7
+    elif case == "c1":
+        spec, n, K = synth.world_c1(1), 20, 8
+    else:
+        spec, n, K = synth.world_random(9, 64, 4), 25, 10
+        spec.params = synth.Params(nu=0.3, kappa=0.2, k_bend=0.7, k_stretch=0.6, k_shear=0.5, k_rep=1.0,
+                                   sigma=0.8, orient=1.0, n_pbd=3)
+    gx = rng.standard_normal(spec.N)
+    gy = rng.standard_normal(spec.N)
+    g_gpu = _gpu_grad(spec, n, K, gx, gy)
+    g_or = _oracle_grad(spec, n, gx, gy)
+    scale = np.max(np.abs(g_or))
+    assert scale > 0
+    err = np.max(np.abs(g_gpu - g_or))
+    assert err <= RTOL * scale, (err, scale)
+
+
+def test_adjoint_independent_of_checkpoint_spacing():
+    rng = np.random.default_rng(4)
+    spec, n = synth.tiny_world(5, side=32, lengths=(10, 8)), 30
+    gx, gy = rng.standard_normal(spec.N), rng.standard_normal(spec.N)
+    gs = [_gpu_grad(spec, n, K, gx, gy) for K in (1, 10, 30)]
+    scale = np.max(np.abs(gs[0]))
+    for g in gs[1:]:
+        assert np.max(np.abs(g - gs[0])) <= 1e-5 * scale
+
+
+def test_world_continues_from_the_final_state_after_backward():
+    from paper_2607_02954_gb300 import World
+    spec = synth.world_c1(4)
+    a, b = World(spec), World(spec)
+    a.step(12)
+    b.rollout_forward(12, 5)
+    b.rollout_backward(torch.zeros(spec.N, device="cuda"), torch.zeros(spec.N, device="cuda"))
+    sa, sb = a.state(fluid=True), b.state(fluid=True)
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
+    a.step(3)
+    b.step(3)
+    assert np.array_equal(a.state()["x"], b.state()["x"])
+
+
+def _fd_worker(args):
+    spec, n, poly, direction, eps = args
+    torch.set_num_threads(2)
+    ow = O.World(spec)
+    lp, _ = O.folding_loss(ow, n, poly, ow.theta0 + eps * torch.as_tensor(direction))
+    lm, _ = O.folding_loss(ow, n, poly, ow.theta0 - eps * torch.as_tensor(direction))
+    return (float(lp) - float(lm)) / (2 * eps)
+
+
+def test_folding_loss_and_gradient_against_finite_differences():
+    """Folding world (256 x 256 grid, 64 filaments x 48 beads, seeded polyline
+    target) over 200 steps with checkpoints every 100: GPU loss against the
+    oracle's, and the GPU gradient's directional derivatives against FP64
+    central differences of the oracle loss along 8 random directions."""
+    from paper_2607_02954_gb300 import World
+    spec, poly = synth.world_c5(0)
+    n, K = 200, 100
+    w = World(spec)
+    w.rollout_forward(n, K)
+    loss, gx, gy = w.loss_polyline(poly)
+    g = t2n(w.rollout_backward(gx, gy)).astype(np.float64)
+    w.close()
+    ow = O.World(spec)
+    want_loss, _ = O.folding_loss(ow, n, poly)
+    assert abs(float(loss.item()) - float(want_loss)) <= 1e-4 * abs(float(want_loss))
+    rng = np.random.default_rng(8)
+    dirs = []
+    for _ in range(8):
+        d = rng.standard_normal(spec.J)
+        dirs.append(d / np.linalg.norm(d))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(8) as pool:
+        fds = pool.map(_fd_worker, [(spec, n, poly, d, 1e-4) for d in dirs])
+    for d, fd in zip(dirs, fds):
+        ad = float(np.dot(g, d))
+        assert abs(ad - fd) <= RTOL * max(abs(fd), 1e-3 * np.linalg.norm(g)), (ad, fd)
+
+
+def test_rollout_fn_autograd_bridge():
+    from paper_2607_02954_gb300 import World
+    from paper_2607_02954_gb300.autograd import rollout_displacement
+    spec = synth.tiny_world(6, side=32, lengths=(8, 8))
+    th0 = torch.tensor(spec.theta0, device="cuda", requires_grad=True)
+    disp = rollout_displacement(th0, spec, 15, 4)
+    c = torch.linspace(-1, 1, disp.numel(), device="cuda").reshape(disp.shape)
+    (disp * c).sum().backward()
+    w = World(spec)
+    w.rollout_forward(15, 4)
+    direct = w.rollout_backward(c[:, 0].contiguous(), c[:, 1].contiguous())
+    assert torch.allclose(th0.grad, direct, rtol=1e-5, atol=1e-7)
+    w.close()
