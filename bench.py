@@ -48,7 +48,11 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
-    ap.add_argument("--workload", default="c3_22", help="c3_<log2 N> (default c3_22) or c2")
+    ap.add_argument("--workload", default="c3_22",
+                    help="c3_<log2 N> (default c3_22), c2, c4 (1024 worlds: batched vs per-world launches) "
+                         "or served (C4 worlds as Poisson-arriving 500-step rollouts)")
+    ap.add_argument("--arrival-rate", type=float, default=2000.0, help="served: requests per second")
+    ap.add_argument("--duration", type=float, default=2.0, help="served: seconds of arrivals")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stage-steps", type=int, default=50, help="steps of the per-stage timing pass")
@@ -198,10 +202,108 @@ def reference_arm(args):
     return 0
 
 
+def bench_batched(args):
+    """1024 uneven worlds: batched steps (one launch per stage for all worlds,
+    replayed from a CUDA graph) against plain per-world launches."""
+    import torch
+    from paper_2607_02954_gb300 import World, step_batched, synth
+    specs = synth.batch_c4(0)
+    worlds = [World(sp) for sp in specs]
+    n_beads = sum(sp.N for sp in specs)
+    n_cells = sum(sp.H * sp.W for sp in specs)
+    stream = torch.cuda.current_stream()
+    step_batched(worlds, max(args.warmup, 16))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        step_batched(worlds, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    batched = n_beads * args.steps / (ms * 1e-3)
+    plain_steps = 3
+    for w in worlds:
+        w.step(1)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(plain_steps):
+        for w in worlds:
+            w.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = e0.elapsed_time(e1)
+    plain = n_beads * plain_steps / (ms_plain * 1e-3)
+    for w in worlds:
+        w.check()
+        w.close()
+    return {"metric": "particle-steps/s", "value": batched, "unit": "particle-steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "c4", "worlds": len(specs), "beads": n_beads, "cells": n_cells,
+                       "description": "1024 worlds, side ~U{64,128,256}, 1-64 filaments x 8-64 beads (log-uniform)"},
+            "plain_per_world": {"value": plain, "ms_per_step": ms_plain / plain_steps,
+                                "launches_per_step": len(worlds) * 8},
+            "batched_over_plain": batched / plain, "gpu_launches": args.steps * 8, "clocks": clk.summary()}
+
+
+def bench_served(args):
+    """Rollout requests for C4 worlds arriving as a Poisson process; each
+    asks for a 500-step rollout and reads back the displacement."""
+    import random
+    from paper_2607_02954_gb300 import Server, synth
+    pool = synth.batch_c4(1, n_worlds=256)
+    rng = random.Random(7)
+    srv = Server(hbm_budget_bytes=64 << 30, max_slots=4096, steps_per_tick=10)
+    # warm-up: a few rollouts to load kernels
+    for t in [srv.submit(pool[k], 20) for k in range(8)]:
+        srv.wait(t)
+    n_req = int(args.arrival_rate * args.duration)
+    times, t = [], 0.0
+    for _ in range(n_req):
+        t += rng.expovariate(args.arrival_rate)
+        times.append(t)
+    tickets, sizes = [], []
+    with ClockSampler(0) as clk:
+        start = time.perf_counter()
+        for k, at in enumerate(times):
+            now = time.perf_counter() - start
+            if at > now:
+                time.sleep(at - now)
+            sp = pool[k % len(pool)]
+            tickets.append(srv.submit(sp, 500))
+            sizes.append(sp.N)
+        res = [srv.wait(tk) for tk in tickets]
+    bad = sum(1 for r in res if r["status"] != 0)
+    lat = sorted((r["t_done_ns"] - r["t_submit_ns"]) * 1e-6 for r in res)
+    span = (max(r["t_done_ns"] for r in res) - min(r["t_submit_ns"] for r in res)) * 1e-9
+    stats = srv.stats()
+    srv.close()
+    value = sum(sizes) * 500 / span
+    return {"metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": 1,
+            "steps": 500, "warmup": 8, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "served", "requests": n_req, "arrival_rate_per_s": args.arrival_rate,
+                       "rollout_steps": 500, "pool": "256 C4 worlds"},
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                           "max": lat[-1]},
+            "completed_per_s": n_req / span, "failed": bad, "server": stats, "clocks": clk.summary()}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload in ("c4", "served"):
+        import torch
+        torch.cuda.set_device(0)
+        from paper_2607_02954_gb300 import _lib
+        if not os.path.exists(_lib.LIB_PATH):
+            from paper_2607_02954_gb300.build import build
+            build()
+        line = bench_batched(args) if args.workload == "c4" else bench_served(args)
+        print(json.dumps(line), flush=True)
+        return 0
     import numpy as np
     import torch
 

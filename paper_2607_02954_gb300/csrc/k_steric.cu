@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(256) k_force_spread(const WorldDev* __restrict
   __shared__ int si[kForceCap];
   __shared__ float taps[2 * kMaxR + 1];
   __shared__ int s_start[kMaxSeg], s_pre[kMaxSeg + 1];
-  __shared__ float red[kWarps];
+  __shared__ float red[16];
   const int2 it = items[blockIdx.x];
   const WorldDev& w = worlds[it.x];
   const int W = w.W, H = w.H, R = w.R, ntx = w.ntx, nty = w.nty;
@@ -258,18 +258,39 @@ __global__ void __launch_bounds__(256) k_force_spread(const WorldDev* __restrict
   const int tw = min(kTile, W - x0), th = min(kTile, H - y0);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ww = tw + 8, wh = th + 8, lh = wh + 2 * R;
-  // rho_x rows [y0 - 4 - R, y0 + th + 4 + R) x columns [x0 - 4, x0 + tw + 4), wrapped
+  // 1. bead segments (one round trip), then every other load in one batch
+  if (warp == 0) build_segments(w, x0 - 2, x0 + tw, y0 - 2, y0 + th, s_start, s_pre, nullptr);
+  __syncthreads();
+  const int total = s_pre[kMaxSeg];
   {
-    const int gx0 = wrap_mod(x0 - 4 + lane, W);
-    const int gx1 = wrap_mod(x0 - 4 + 32 + lane, W);
+    // rho_x rows [y0 - 4 - R, y0 + th + 4 + R) x columns [x0 - 4, x0 + tw + 4), wrapped
+    // offsets reach at most 4 + R <= 12 cells outside the axis: one
+    // conditional correction suffices unless the axis is shorter than that
+    const int gx0 = W >= 16 ? wrap_once(x0 - 4 + lane, W) : wrap_mod(x0 - 4 + lane, W);
+    const int gx1 = W >= 44 ? wrap_once(x0 + 28 + lane, W) : wrap_mod(x0 + 28 + lane, W);
     for (int i = warp; i < lh; i += kWarps) {
-      const float* src = w.rho_x + (size_t)wrap_mod(y0 - 4 - R + i, H) * W;
+      const int gy = y0 - 4 - R + i;
+      const float* src = w.rho_x + (size_t)(H >= 2 * kMaxR + 8 ? wrap_once(gy, H) : wrap_mod(gy, H)) * W;
       if (lane < ww) cp_async4(&xb[i * kWin + lane], src + gx0);
       if (lane + 32 < ww) cp_async4(&xb[i * kWin + 32 + lane], src + gx1);
     }
   }
-  if (warp == 0) build_segments(w, x0 - 2, x0 + tw, y0 - 2, y0 + th, s_start, s_pre, nullptr);
+  const int n0 = min(kForceCap, total);
+  for (int v = threadIdx.x; v < n0; v += blockDim.x) {
+    const int slot = seg_slot(v, s_start, s_pre);
+    cp_async16(&sp[v], &w.spos[slot]);
+    cp_async8(&sf[v], &w.sfel[slot]);
+    cp_async4(&si[v], &w.sid[slot]);
+  }
   if (warp == 1 && lane <= 2 * R) taps[lane] = w.taps[lane];
+  // bound of the cell sums of weight * |F_el + F_s|:
+  //   |F_s| <= k_rep/2 max|rho_bar(c+1) - rho_bar(c-1)| <= k_rep/2 max rho_bar
+  //        <= k_rep/2 max rho_s over the 3x3 tiles around this one,
+  // times max rho_s of this tile (the sum of the spread weights of a cell)
+  if (warp == 2 && lane < 9) {
+    const int ty2 = wrap_once(ty + lane / 3 - 1, nty), tx2 = wrap_once(tx + lane % 3 - 1, ntx);
+    red[lane] = w.tile_rho_max[ty2 * ntx + tx2];
+  }
   for (int c = threadIdx.x; c < kTile * kTile; c += blockDim.x) {
     accx[c] = 0;
     accy[c] = 0;
@@ -279,6 +300,11 @@ __global__ void __launch_bounds__(256) k_force_spread(const WorldDev* __restrict
   const float rho_max = w.tile_rho_max[it.y];
   cp_async_wait_all();
   __syncthreads();
+  float rho_nb = red[0];
+  for (int k2 = 1; k2 < 9; ++k2) rho_nb = fmaxf(rho_nb, red[k2]);
+  const float k_rep = w.k_rep;
+  const int k = fix_exponent((fmax_el + 0.5f * k_rep * rho_nb) * rho_max * 1.0001f + 1e-30f);
+  const float scale = ldexpf(1.0f, k);
   for (int i = warp; i < wh; i += kWarps) {
     for (int j = lane; j < ww; j += 32) {
       float s = 0.0f;
@@ -288,29 +314,18 @@ __global__ void __launch_bounds__(256) k_force_spread(const WorldDev* __restrict
     }
   }
   __syncthreads();
-  // bound of the cell sums of weight * |F_el + F_s|: (max|F_el| + k_rep max|grad|) max rho_s
-  float gmax = 0.0f;
-  for (int i = 1 + warp; i < wh - 1; i += kWarps) {
-    for (int j = 1 + lane; j < ww - 1; j += 32) {
-      gmax = fmaxf(gmax, fabsf(win[i * kWin + j + 1] - win[i * kWin + j - 1]));
-      gmax = fmaxf(gmax, fabsf(win[(i + 1) * kWin + j] - win[(i - 1) * kWin + j]));
-    }
-  }
-  gmax = block_max(gmax, red);
-  const float k_rep = w.k_rep;
-  const int k = fix_exponent((fmax_el + 0.5f * k_rep * gmax) * rho_max * 1.0001f + 1e-30f);
-  const float scale = ldexpf(1.0f, k);
-  const int total = s_pre[kMaxSeg];
   for (int c0 = 0; c0 < total; c0 += kForceCap) {
     const int n = min(kForceCap, total - c0);
-    for (int v = threadIdx.x; v < n; v += blockDim.x) {
-      const int slot = seg_slot(c0 + v, s_start, s_pre);
-      cp_async16(&sp[v], &w.spos[slot]);
-      cp_async8(&sf[v], &w.sfel[slot]);
-      cp_async4(&si[v], &w.sid[slot]);
+    if (c0 > 0) {   // the first chunk was staged with the window
+      for (int v = threadIdx.x; v < n; v += blockDim.x) {
+        const int slot = seg_slot(c0 + v, s_start, s_pre);
+        cp_async16(&sp[v], &w.spos[slot]);
+        cp_async8(&sf[v], &w.sfel[slot]);
+        cp_async4(&si[v], &w.sid[slot]);
+      }
+      cp_async_wait_all();
+      __syncthreads();
     }
-    cp_async_wait_all();
-    __syncthreads();
     for (int v = threadIdx.x; v < n; v += blockDim.x) {
       const float4 p = sp[v];
       const int cx = cell_x(p), cy = cell_y(p);
