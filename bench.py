@@ -15,7 +15,9 @@ e2e        the same metric through the C ABI from host buffers: world
            creation from host arrays (H2D), K steps, state read-back (D2H).
 roofline   the LBM kernel (the dominant one): algorithmic bytes per launch
            (88 B per cell) / its CUDA-event duration, against the measured
-           HBM copy bandwidth.
+           HBM copy bandwidth.  traffic: DRAM bytes per launch from one ncu
+           capture of this workload, reported only while the kernel's source
+           is the one that was captured (else null).
 cpu_baseline  the FP64 oracle on the host cores, one step of a 1/16 sample
            of the workload (2^18 beads on 1024^2 at the same density).
 With --impl reference the oracle itself is the timed arm.
@@ -24,6 +26,7 @@ from __future__ import annotations
 
 import argparse
 import ctypes
+import hashlib
 import json
 import math
 import os
@@ -41,6 +44,18 @@ STAGES = ["pbd", "bin_scan", "bin_scatter", "deposit_x", "force_spread", "lbm", 
 LBM_BYTES_PER_CELL = 88          # read f 36 + F 8, write f' 36 + u 8
 STEP_BYTES_PER_CELL = 112        # grid traffic per step of the minimal fused form
 STEP_BYTES_PER_BEAD = 32
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_lbm launch, from an ncu
+# capture of the workload, keyed by the fingerprint of the kernel's source
+LBM_TRAFFIC = {("c3_22", "6a52e9faac09012f"): 738_779_136 + 684_287_488}
+
+
+def lbm_fingerprint() -> str:
+    """SHA-1 prefix of the LBM kernel's source (collision helper to the end of k_lbm)."""
+    src = open(os.path.join(ROOT, "paper_2607_02954_gb300", "csrc", "k_grid.cu")).read()
+    a = src.index("struct PairOut")
+    b = src.index("\n}\n", src.index(" k_lbm(")) + 3
+    return hashlib.sha1(src[a:b].encode()).hexdigest()[:16]
 
 
 def parse():
@@ -83,6 +98,21 @@ def sample_spec(name: str, seed: int):
         return synth.world_rows(s_side, s_n, seed), f"one oracle step of {s_n} beads on {s_side}^2 (same density)"
     spec, _ = make_spec(name, seed)
     return spec, f"one oracle step of the full {name} world"
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """Largest x over the ranks of the process group (x itself without one)."""
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, steps: int, seconds: float, world_size: int) -> float:
+    """Units all ranks processed per second of the slowest rank (weak scaling:
+    every rank advances its own world of the same size)."""
+    return world_size * units_per_rank * steps / seconds
 
 
 def dist_env():
@@ -345,11 +375,8 @@ def main():
         barrier()
     ms = ev0.elapsed_time(ev1)
     world.check()
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = ws * N * args.steps / (ms_max * 1e-3)
+    ms_max = max_over_ranks(ms, dist, "cuda")
+    value = whole_job_rate(N, args.steps, ms_max * 1e-3, ws)
 
     # ---- per-stage CUDA-event timing on the launching stream ------------
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)] for _ in range(args.stage_steps)]
@@ -381,10 +408,7 @@ def main():
     barrier()
     e2e_s = time.perf_counter() - t0
     w2.close()
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_val = ws * N * e2e_steps / float(e2e_t.item())
+    e2e_val = whole_job_rate(N, e2e_steps, max_over_ranks(e2e_s, dist, "cuda"), ws)
 
     if rank != 0:
         if dist is not None:
@@ -403,7 +427,8 @@ def main():
                 "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps},
         "gpu_launches": args.steps * (len(STAGES) + 1),   # the scan stage is two kernels
         "roofline": {"bound": "hbm", "kernel": "k_lbm", "achieved": lbm_gbs, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": lbm_gbs / hbm_peak, "peak_kind": peak_kind, "traffic": None,
+                     "frac": lbm_gbs / hbm_peak, "peak_kind": peak_kind,
+                     "traffic": LBM_TRAFFIC.get((args.workload, lbm_fingerprint())),
                      "algorithmic_bytes_per_launch": lbm_bytes, "launch_ms": stage_ms["lbm"]},
         "step_roofline": {"achieved": step_gbs, "frac": step_gbs / hbm_peak, "unit": "GB/s",
                           "algorithmic_bytes_per_step": step_bytes},

@@ -214,7 +214,7 @@ mc_status mc_world_check(const mc_world* w, void* stream);
 mc_status mc_world_clear_flags(mc_world* w, void* stream);
 
 /* ---- Reverse mode ----------------------------------------------------------
- * The Filament Folding experiment (the paper Experiments) optimises rest
+ * The Filament Folding experiment (Experiments section) optimises rest
  * angles by gradients that flow through the whole simulation.  Here the
  * gradient of a loss on the final unwrapped bead positions with respect to
  * theta0 (the static rest angles) is computed by a hand-written adjoint of
@@ -246,7 +246,7 @@ mc_status mc_loss_polyline(mc_world* w, const float* poly_xy, int n_vertices, fl
 
 /* ---- Rollout serving: continuous batching ---------------------------------
  * Search loops (the paper's Neuroevolution and QD Search experiments,
- * the paper Experiments) request rollouts as they go and read back a fitness,
+ * Experiments section) request rollouts as they go and read back a fitness,
  * the mean displacement of the world's beads.  A server owns a scheduler
  * thread and a CUDA stream on the device current at creation.  Requests wait
  * in a queue until a slot is free and their device footprint fits the

@@ -35,3 +35,39 @@ def periodic_diff(a, b, period):
 
 def t2n(t):
     return t.detach().cpu().numpy()
+
+
+def crop_world(spec, cx, cy, radius=16, side=256):
+    """Sub-world of `spec` around the point (cx, cy) for checking one bead of
+    a world too large for the oracle.
+
+    Keeps every filament with a bead within periodic Chebyshev distance
+    `radius` of the point, whole, translated by an integer so that the point
+    sits near the centre of a side x side periodic grid (translation by an
+    integer is exact in float32).  With the fluid at rest initially, one step
+    of a bead within 4 cells of the point, and of the grid cells within 2
+    cells of it, depends only on beads within 13 cells (stencil 2, gradient
+    1, filter R = 4, deposit 2, and the spread and interpolation stencils),
+    all of them kept, so the sub-world reproduces those values exactly.
+    Returns (sub-spec, index of each kept bead in `spec`, integer shift)."""
+    from paper_2607_02954_gb300 import synth
+    bx, by = int(np.floor(cx)), int(np.floor(cy))
+    dx = periodic_diff(spec.x, bx, spec.W)
+    dy = periodic_diff(spec.y, by, spec.H)
+    near = np.maximum(np.abs(dx), np.abs(dy)) <= radius
+    fil_of = np.repeat(np.arange(spec.n_fil), np.diff(spec.fil_off))
+    fils = np.unique(fil_of[near])
+    lengths = np.diff(spec.fil_off)[fils]
+    beads = np.concatenate([np.arange(spec.fil_off[f], spec.fil_off[f + 1]) for f in fils])
+    edges = np.concatenate([np.arange(spec.fil_off[f] - f, spec.fil_off[f + 1] - f - 1) for f in fils])
+    joints = np.concatenate([np.arange(spec.fil_off[f] - 2 * f, spec.fil_off[f + 1] - 2 * f - 2) for f in fils])
+    half = side // 2
+    x = half + dx[beads]
+    y = half + dy[beads]
+    assert x.min() >= 0 and x.max() < side and y.min() >= 0 and y.max() < side
+    sub = synth._world(f"crop of {spec.name}", side, side, list(lengths), x, y, spec.theta[edges],
+                       spec.theta0[joints], spec.drive_amp[joints], spec.drive_freq[joints],
+                       spec.drive_phase[joints], params=spec.params, t0=spec.t0)
+    sub.L_rest = spec.L_rest[edges].copy()
+    assert spec.f0 is None
+    return sub, beads, (bx - half, by - half)

@@ -11,7 +11,7 @@ import torch
 
 import oracle as O
 from paper_2607_02954_gb300 import synth
-from tests.helpers import assert_field, oracle_one_step, periodic_diff, t2n
+from tests.helpers import assert_field, crop_world, oracle_one_step, periodic_diff, t2n
 
 pytestmark = pytest.mark.gpu
 
@@ -147,6 +147,77 @@ def test_one_step_edge_cases(case):
 def test_one_step_c2_full_size():
     """512 x 512 grid with 262,144 beads: the whole step against the oracle."""
     _compare_one_step(synth.world_c2(0))
+
+
+def _full_size_samples(spec, rng, n_random=20):
+    """Random beads plus beads at the periodic seams and on tile corners."""
+    picks = list(rng.choice(spec.N, n_random, replace=False))
+    picks += [int(np.argmin(spec.x)), int(np.argmax(spec.x)), int(np.argmin(spec.y)), int(np.argmax(spec.y))]
+    corner = (np.mod(spec.x, 32.0) < 1.0) & (np.mod(spec.y, 32.0) < 1.0)
+    if corner.any():
+        picks += list(rng.choice(np.nonzero(corner)[0], min(4, int(corner.sum())), replace=False))
+    return picks
+
+
+def test_full_size_2_22_sampled():
+    """The benchmark's workload, 2^22 beads as 64-bead filaments on a 4096^2
+    grid, in the launch configuration the benchmark times (CUDA-graph replay
+    through mc_step).  After one step: for ~28 sampled beads, F_el, F_s, U,
+    the new position and the force and velocity on the 5x5 cells around the
+    bead against one oracle step of the sub-world around it (exact for those
+    values).  After 16 more steps of graph replay: the world equals one
+    advanced by direct launches bitwise, sum F_el = 0, sum F_s = 0,
+    sum F = sum (F_el + F_s), and the populations keep the mass."""
+    spec = synth.world_c3(22, 0)
+    H, W = spec.H, spec.W
+    gw = _gpu_world(spec)
+    gw.step(1)
+    gw.check()
+    fel, fs, ub = gw.field("fel"), gw.field("fs"), gw.field("ubead")
+    Fg, ug = gw.field("force"), gw.field("u")
+    st = gw.state()
+    rng = np.random.default_rng(22)
+    got = {k: [] for k in ("F_el", "F_s", "U", "X", "F", "u")}
+    want = {k: [] for k in got}
+    for i in _full_size_samples(spec, rng):
+        sub, beads, (sx, sy) = crop_world(spec, spec.x[i], spec.y[i])
+        _, _, st1, rec = oracle_one_step(sub)
+        k = int(np.nonzero(beads == i)[0][0])
+        got["F_el"].append(fel[i]); want["F_el"].append(t2n(rec["F_el"])[k])
+        got["F_s"].append(fs[i]); want["F_s"].append(t2n(rec["F_s"])[k])
+        got["U"].append(ub[i]); want["U"].append(t2n(rec["U"])[k])
+        X1 = t2n(st1.X)[k] + np.array([sx, sy], np.float64)
+        got["X"].append(np.array([periodic_diff(st["x"][i], X1[0], W), periodic_diff(st["y"][i], X1[1], H)]))
+        want["X"].append(np.zeros(2))
+        cx, cy = int(np.floor(spec.x[i])), int(np.floor(spec.y[i]))
+        for gy in range(cy - 2, cy + 3):
+            for gx in range(cx - 2, cx + 3):
+                got["F"].append(Fg[gy % H, gx % W]); want["F"].append(t2n(rec["F"])[:, (gy - sy) % sub.H, (gx - sx) % sub.W])
+                got["u"].append(ug[gy % H, gx % W]); want["u"].append(t2n(rec["u"])[:, (gy - sy) % sub.H, (gx - sx) % sub.W])
+    assert_field("F_el", np.array(got["F_el"]), np.array(want["F_el"]), RTOL_STEP, floor=fel_floor(spec))
+    for k in ("F_s", "U", "F", "u"):
+        assert_field(k, np.array(got[k]), np.array(want[k]), RTOL_STEP)
+    assert np.max(np.abs(np.array(got["X"]))) <= 0.5 * np.spacing(np.float32(W))
+    # whole-world properties of the same step
+    tot = lambda a: np.abs(np.asarray(a, np.float64)).sum(axis=tuple(range(a.ndim - 1)))
+    assert np.all(np.abs(fel.astype(np.float64).sum(0)) <= 1e-6 * tot(fel))
+    assert np.all(np.abs(fs.astype(np.float64).sum(0)) <= 1e-6 * tot(fs))
+    ftot = fel.astype(np.float64) + fs
+    assert np.all(np.abs(Fg.astype(np.float64).sum((0, 1)) - ftot.sum(0)) <= 1e-5 * tot(ftot))
+    del Fg, ug
+    # 16 steps of graph replay against 16 direct steps, bitwise
+    gd = _gpu_world(spec)
+    gd.step(1)
+    for _ in range(16):
+        gd.step(1)
+    gw.step(16)
+    a, b = gw.state_device(), gd.state_device()
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+    f = gw.state(fluid=True)["fdev"]
+    assert abs(float(f.astype(np.float64).sum())) <= 1e-6 * H * W
+    gw.close()
+    gd.close()
 
 
 # ---------------------------------------------------------------------------
