@@ -13,11 +13,12 @@ value      particle-steps/s of mc_step replaying its CUDA graph, inputs
            resident in HBM (the world's state, 1.8 GB, is larger than L2).
 e2e        the same metric through the C ABI from host buffers: world
            creation from host arrays (H2D), K steps, state read-back (D2H).
-roofline   the LBM kernel (the dominant one): algorithmic bytes per launch
-           (88 B per cell) / its CUDA-event duration, against the measured
-           HBM copy bandwidth.  traffic: DRAM bytes per launch from one ncu
-           capture of this workload, reported only while the kernel's source
-           is the one that was captured (else null).
+roofline   k_force_lbm (filter y pass, steric force, spread and LBM of a
+           tile; the dominant kernel): algorithmic bytes per launch (84 B per
+           cell + 36 B per bead) / its CUDA-event duration, against the
+           measured HBM copy bandwidth.  traffic: DRAM bytes per launch from
+           one ncu capture of this workload, reported only while the kernel's
+           sources are the ones that were captured (else null).
 cpu_baseline  the FP64 oracle on the host cores, one step of a 1/16 sample
            of the workload (2^18 beads on 1024^2 at the same density).
 With --impl reference the oracle itself is the timed arm.
@@ -40,22 +41,30 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-STAGES = ["pbd", "bin_scan", "bin_scatter", "deposit_x", "force_spread", "lbm", "interp_advance"]
-LBM_BYTES_PER_CELL = 88          # read f 36 + F 8, write f' 36 + u 8
+# the stages one step runs, with their mc_step_stage ids (the scan stage is two kernels)
+STAGES = [("pbd", 0), ("bin_scan", 1), ("bin_scatter", 2), ("deposit_x", 3), ("force_lbm", 7), ("interp_advance", 6)]
+KERNELS_PER_STEP = 7
+# k_force_lbm, the dominant kernel: per cell read f 36 + rho_x 4, write f' 36 + u 8;
+# per bead read the binned record (position 16, F_el 8, id 4), write F_s 8
+FORCE_LBM_BYTES_PER_CELL = 84
+FORCE_LBM_BYTES_PER_BEAD = 36
 STEP_BYTES_PER_CELL = 112        # grid traffic per step of the minimal fused form
 STEP_BYTES_PER_BEAD = 32
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_lbm launch, from an ncu
-# capture of the workload, keyed by the fingerprint of the kernel's source
-LBM_TRAFFIC = {("c3_22", "6a52e9faac09012f"): 738_779_136 + 684_287_488}
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the dominant
+# kernel, from an ncu capture of the workload, keyed by the fingerprint of the
+# sources the kernel is built from (reported only while they are unchanged)
+KERNEL_TRAFFIC = {}
+KERNEL_SOURCES = ["k_steric.cu", "mc_internal.cuh"]
 
 
-def lbm_fingerprint() -> str:
-    """SHA-1 prefix of the LBM kernel's source (collision helper to the end of k_lbm)."""
-    src = open(os.path.join(ROOT, "paper_2607_02954_gb300", "csrc", "k_grid.cu")).read()
-    a = src.index("struct PairOut")
-    b = src.index("\n}\n", src.index(" k_lbm(")) + 3
-    return hashlib.sha1(src[a:b].encode()).hexdigest()[:16]
+def kernel_fingerprint() -> str:
+    """SHA-1 prefix of the dominant kernel's source files."""
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2607_02954_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -382,15 +391,15 @@ def main():
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)] for _ in range(args.stage_steps)]
     for k in range(args.stage_steps):
         evs[k][0].record(stream)
-        for s_i in range(len(STAGES)):
-            _lib.check(lib.mc_step_stage(world.handle, s_i, sh))
+        for s_i, (_, sid) in enumerate(STAGES):
+            _lib.check(lib.mc_step_stage(world.handle, sid, sh))
             evs[k][s_i + 1].record(stream)
     torch.cuda.synchronize()
     stage_ms = {nm: sum(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.stage_steps)) / args.stage_steps
-                for i, nm in enumerate(STAGES)}
+                for i, (nm, _) in enumerate(STAGES)}
     hbm_peak, peak_kind = measured_peaks()
-    lbm_bytes = LBM_BYTES_PER_CELL * C
-    lbm_gbs = lbm_bytes / (stage_ms["lbm"] * 1e-3) / 1e9
+    top_bytes = FORCE_LBM_BYTES_PER_CELL * C + FORCE_LBM_BYTES_PER_BEAD * N
+    top_gbs = top_bytes / (stage_ms["force_lbm"] * 1e-3) / 1e9
     step_bytes = STEP_BYTES_PER_CELL * C + STEP_BYTES_PER_BEAD * N
     step_gbs = step_bytes / (ms_max / args.steps * 1e-3) / 1e9
     world.close()
@@ -425,11 +434,11 @@ def main():
                    "l2": "state 1.8 GB > L2: no flush needed" if C >= 4096 * 4096 else "state may fit in L2; per-step timing includes no flush"},
         "e2e": {"value": e2e_val, "unit": "particle-steps/s", "steps": e2e_steps,
                 "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps},
-        "gpu_launches": args.steps * (len(STAGES) + 1),   # the scan stage is two kernels
-        "roofline": {"bound": "hbm", "kernel": "k_lbm", "achieved": lbm_gbs, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": lbm_gbs / hbm_peak, "peak_kind": peak_kind,
-                     "traffic": LBM_TRAFFIC.get((args.workload, lbm_fingerprint())),
-                     "algorithmic_bytes_per_launch": lbm_bytes, "launch_ms": stage_ms["lbm"]},
+        "gpu_launches": args.steps * KERNELS_PER_STEP,
+        "roofline": {"bound": "hbm", "kernel": "k_force_lbm", "achieved": top_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": top_gbs / hbm_peak, "peak_kind": peak_kind,
+                     "traffic": KERNEL_TRAFFIC.get((args.workload, kernel_fingerprint())),
+                     "algorithmic_bytes_per_launch": top_bytes, "launch_ms": stage_ms["force_lbm"]},
         "step_roofline": {"achieved": step_gbs, "frac": step_gbs / hbm_peak, "unit": "GB/s",
                           "algorithmic_bytes_per_step": step_bytes},
         "stage_ms": stage_ms,

@@ -151,13 +151,17 @@ mc_status mc_step_batched(mc_world* const* worlds, int n_worlds, int n_steps, vo
 /* Enqueues one stage of the next step on `stream` (for per-stage timing).
  * Stages: 0 drive + PBD + elastic force + bin histogram (a1-a3), 1 bin
  * offsets (two kernels), 2 bin scatter (a2), 3 steric deposit + x pass of
- * the Gaussian filter (a4, a5), 4 y pass + steric force + spread (a5, a6),
- * 5 LBM (a7), 6 interpolation + advance (a8).  Enqueuing stages 0..6 in
- * order is exactly one mc_step(w, 1) without the graph; any other use leaves
- * the world in an unspecified state.  The step counter advances with
- * stage 6.  Errors: MC_ERR_INVALID_ARG for an unknown stage. */
+ * the Gaussian filter (a4, a5), 7 y pass + steric force + spread + LBM
+ * (a5-a7, one kernel, the force density handed to the collision in shared
+ * memory), 6 interpolation + advance (a8).  Enqueuing stages 0, 1, 2, 3, 7, 6
+ * in that order is exactly one mc_step(w, 1) without the graph.  Stages 4
+ * (y pass + steric force + spread, writes F) and 5 (LBM, reads F) are stage 7
+ * split in two kernels with F through device memory; 0, 1, 2, 3, 4, 5, 6
+ * give the same step bitwise.  Any other use leaves the world in an
+ * unspecified state.  The step counter advances with stage 6.  Errors:
+ * MC_ERR_INVALID_ARG for an unknown stage. */
 mc_status mc_step_stage(mc_world* w, int stage, void* stream);
-#define MC_N_STAGES 7
+#define MC_N_STAGES 8
 
 /* Copies the state after the enqueued steps.  Any output may be NULL.
  *   x, y      [N] wrapped bead positions
@@ -196,7 +200,7 @@ typedef enum mc_field {
   MC_FIELD_UBEAD = 2,    /* [2N] interpolated velocity per bead (a8) */
   MC_FIELD_RHO_S = 3,    /* [H*W] deposited steric density (a4), recomputed on request */
   MC_FIELD_RHO_BAR = 4,  /* [H*W] filtered density (a5), recomputed on request */
-  MC_FIELD_FORCE = 5,    /* [2*H*W] interleaved (Fx, Fy) spread force density (a6) */
+  MC_FIELD_FORCE = 5,    /* [2*H*W] interleaved (Fx, Fy) spread force density (a6), recomputed on request */
   MC_FIELD_U = 6,        /* [2*H*W] interleaved (ux, uy) fluid velocity (a7) */
   MC_FIELD_CELL = 7,     /* [N] int32 cell index (floor(y) mod H) W + (floor(x) mod W) (a2) */
   MC_FIELD_BIN = 8,      /* [N] int32 bin index (floor(y)/8) (W/8) + floor(x)/8 of each bead (a2) */

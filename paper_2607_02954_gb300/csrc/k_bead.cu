@@ -30,28 +30,132 @@ __device__ __forceinline__ float drive_angle(const float4 d, long long t) {
   return d.x + d.y * sinpif(2.0f * fr);
 }
 
-// One warp per filament.  The filament's edges, joints and bead corrections
-// live in a per-warp slice of shared memory; every pass of the Jacobi PBD
-// (Methods, Eqs. 1-4) reads the slice, then writes corrections, with a warp
-// barrier in between, so all corrections of a pass see the state before it.
-// Bead positions enter as edge vectors v0 = min_image(X_b - X_a) plus the
-// accumulated corrections, so the corrections keep full FP32 precision
-// whatever the magnitude of the coordinates.
-__global__ void __launch_bounds__(256) k_pbd(const WorldDev* __restrict__ worlds,
-                                             const int2* __restrict__ items, int n_items, int maxB) {
-  extern __shared__ __align__(16) float smem[];   // maxB is a multiple of 4: float4 slices stay aligned
-  const int wpb = blockDim.x >> 5;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int item = blockIdx.x * wpb + warp;
-  if (item >= n_items) return;  // warp-uniform exit; the kernel has no block barrier
-  const int2 it = items[item];
-  const WorldDev& w = worlds[it.x];
-  const int f = it.y;
-  const int b0 = w.fil_off[f];
-  const int B = w.fil_off[f + 1] - b0;
+// Constants of the PBD passes, read once per warp.
+struct PbdConst {
+  float hb, hs, ksh, ko, kappa_dt;
+  int n_pbd, W, H, nbx;
+};
+
+__device__ __forceinline__ PbdConst pbd_const(const WorldDev& w) {
+  PbdConst k;
+  k.hb = 0.5f * w.k_bend;
+  k.hs = 0.5f * w.k_st;
+  k.ksh = w.k_sh;
+  k.ko = w.orient * k.hs * k.ksh;
+  k.kappa_dt = w.kappa_dt;
+  k.n_pbd = w.n_pbd;
+  k.W = w.W;
+  k.H = w.H;
+  k.nbx = w.nbx;
+  return k;
+}
+
+// Edge vector min_image(X_b - X_a) from cell indices and fractions.
+__device__ __forceinline__ float2 edge_vec(const float4 pa, const float4 pb, int W, int H) {
+  int dcx = cell_x(pb) - cell_x(pa), dcy = cell_y(pb) - cell_y(pa);
+  if (2 * dcx > W) dcx -= W; else if (2 * dcx < -W) dcx += W;
+  if (2 * dcy > H) dcy -= H; else if (2 * dcy < -H) dcy += H;
+  return make_float2((float)dcx + (pb.x - pa.x), (float)dcy + (pb.y - pa.y));
+}
+
+// Position pass of one edge (Eqs. 2-4) with current edge vector (x, y),
+// rest length L and frame angle th: the correction (ddx, ddy) of its first
+// bead (the second gets the opposite), and the frame's turn toward the edge.
+__device__ __forceinline__ void edge_correction(float x, float y, float L, float& th, const PbdConst& k, float& ddx,
+                                                float& ddy) {
+  const float ell = sqrtf(x * x + y * y);
+  const float sc = (ell - L) / ell;
+  const float csx = sc * x, csy = sc * y;
+  float sn, cs;
+  sincosf(th, &sn, &cs);
+  ddx = k.hs * (csx + k.ksh * (x - L * cs - csx));
+  ddy = k.hs * (csy + k.ksh * (y - L * sn - csy));
+  th += k.ko * (cs * y - sn * x) / L;   // frame turns toward the edge (orient)
+}
+
+// F_el = kappa (x_hat - X) / dt of one bead, its 8x8 bin (a2) and one
+// histogram atomic per group of lanes sharing a bin.  Every lane calls this.
+__device__ __forceinline__ void bead_out(const WorldDev& w, const PbdConst& k, bool valid, int b, const float4 P,
+                                         float dlx, float dly, float& fmax) {
+  const int lane = threadIdx.x & 31;
+  int bin = -1 - lane;
+  if (valid) {
+    const float2 fe = make_float2(k.kappa_dt * dlx, k.kappa_dt * dly);
+    w.fel[b] = fe;
+    fmax = fmaxf(fmax, fmaxf(fabsf(fe.x), fabsf(fe.y)));
+    bin = (cell_y(P) / kBin) * k.nbx + cell_x(P) / kBin;
+    w.bead_bin[b] = bin;
+  }
+  const unsigned peers = __match_any_sync(0xffffffffu, bin);
+  if (valid && (__ffs(peers) - 1) == lane) atomicAdd(&w.bin_count[bin], __popc(peers));
+}
+
+// Jacobi PBD of a filament of at most 64 beads in registers: lane l holds
+// beads, edges and joints 2l and 2l + 1, and reads its neighbours' values by
+// warp shuffles.  The same arithmetic, in the same order, as pbd_smem.
+__device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, int b0, int B, int e0, int j0,
+                                          long long t) {
+  constexpr unsigned kAll = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
   const int nE = B - 1, nJ = B - 2;
-  const int e0 = b0 - f, j0 = b0 - 2 * f;
-  float* s = smem + (size_t)warp * maxB * kPbdFloatsPerBead;
+  const int i0 = 2 * lane, i1 = i0 + 1;
+  const bool hb0 = i0 < B, hb1 = i1 < B, he0 = i0 < nE, he1 = i1 < nE, hj0 = i0 < nJ, hj1 = i1 < nJ;
+  const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  const float4 P0 = hb0 ? w.pos[b0 + i0] : z4;
+  const float4 P1 = hb1 ? w.pos[b0 + i1] : z4;
+  float th0 = he0 ? w.theta[e0 + i0] : 0.0f;
+  float th1 = he1 ? w.theta[e0 + i1] : 0.0f;
+  const float L0 = he0 ? w.L_rest[e0 + i0] : 1.0f;
+  const float L1 = he1 ? w.L_rest[e0 + i1] : 1.0f;
+  const float thr0 = hj0 ? drive_angle(w.drive[j0 + i0], t) : 0.0f;
+  const float thr1 = hj1 ? drive_angle(w.drive[j0 + i1], t) : 0.0f;
+  float4 Pn;   // bead 2l + 2
+  Pn.x = __shfl_down_sync(kAll, P0.x, 1);
+  Pn.y = __shfl_down_sync(kAll, P0.y, 1);
+  Pn.z = __shfl_down_sync(kAll, P0.z, 1);
+  Pn.w = __shfl_down_sync(kAll, P0.w, 1);
+  const float2 v0 = edge_vec(P0, P1, k.W, k.H);
+  const float2 v1 = edge_vec(P1, Pn, k.W, k.H);
+  float dlx0 = 0.0f, dly0 = 0.0f, dlx1 = 0.0f, dly1 = 0.0f;
+  for (int iter = 0; iter < k.n_pbd; ++iter) {
+    // bending pass (Eq. 1): C_j = (theta_{j+1} - theta_j) - theta_rest,j
+    const float thn = __shfl_down_sync(kAll, th0, 1);
+    const float C0 = hj0 ? th1 - th0 - thr0 : 0.0f;
+    const float C1 = hj1 ? thn - th1 - thr1 : 0.0f;
+    const float Cm = __shfl_up_sync(kAll, C1, 1);   // C_{2l-1}
+    if (he0) th0 += k.hb * (C0 - (lane > 0 ? Cm : 0.0f));
+    if (he1) th1 += k.hb * (C1 - C0);
+    // position pass (Eqs. 2-4) on the updated frames
+    const float dlxn = __shfl_down_sync(kAll, dlx0, 1), dlyn = __shfl_down_sync(kAll, dly0, 1);
+    float ddx0 = 0.0f, ddy0 = 0.0f, ddx1 = 0.0f, ddy1 = 0.0f;
+    if (he0) edge_correction(v0.x + (dlx1 - dlx0), v0.y + (dly1 - dly0), L0, th0, k, ddx0, ddy0);
+    if (he1) edge_correction(v1.x + (dlxn - dlx1), v1.y + (dlyn - dly1), L1, th1, k, ddx1, ddy1);
+    const float ddxm = __shfl_up_sync(kAll, ddx1, 1), ddym = __shfl_up_sync(kAll, ddy1, 1);
+    if (hb0) {
+      dlx0 += ddx0 - (lane > 0 ? ddxm : 0.0f);
+      dly0 += ddy0 - (lane > 0 ? ddym : 0.0f);
+    }
+    if (hb1) {
+      dlx1 += ddx1 - ddx0;
+      dly1 += ddy1 - ddy0;
+    }
+  }
+  if (he0) w.theta[e0 + i0] = th0;
+  if (he1) w.theta[e0 + i1] = th1;
+  float fmax = 0.0f;
+  bead_out(w, k, hb0, b0 + i0, P0, dlx0, dly0, fmax);
+  bead_out(w, k, hb1, b0 + i1, P1, dlx1, dly1, fmax);
+  return fmax;
+}
+
+// Jacobi PBD of a filament of any length: the filament's edges, joints and
+// bead corrections live in a per-warp slice of shared memory; every pass
+// reads the slice, then writes corrections, with a warp barrier in between,
+// so all corrections of a pass see the state before it.
+__device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, int b0, int B, int e0, int j0,
+                                          long long t, float* s, int maxB) {
+  const int lane = threadIdx.x & 31;
+  const int nE = B - 1, nJ = B - 2;
   float* vx = s;
   float* vy = s + maxB;
   float* th = s + 2 * maxB;
@@ -64,9 +168,6 @@ __global__ void __launch_bounds__(256) k_pbd(const WorldDev* __restrict__ worlds
   float* C = s + 9 * maxB;
   float4* P = reinterpret_cast<float4*>(s + 10 * maxB);    // bead positions
   float4* D = reinterpret_cast<float4*>(s + 14 * maxB);    // joint drive parameters
-  const long long t = *w.t;
-  const int W = w.W, H = w.H;
-
   // stage the filament's inputs in shared memory, every copy in flight at once
   for (int i = lane; i < B; i += 32) cpa16(&P[i], &w.pos[b0 + i]);
   for (int e = lane; e < nE; e += 32) {
@@ -77,12 +178,9 @@ __global__ void __launch_bounds__(256) k_pbd(const WorldDev* __restrict__ worlds
   cpa_wait_all();
   __syncwarp();
   for (int e = lane; e < nE; e += 32) {
-    const float4 pa = P[e], pb = P[e + 1];
-    int dcx = cell_x(pb) - cell_x(pa), dcy = cell_y(pb) - cell_y(pa);
-    if (2 * dcx > W) dcx -= W; else if (2 * dcx < -W) dcx += W;
-    if (2 * dcy > H) dcy -= H; else if (2 * dcy < -H) dcy += H;
-    vx[e] = (float)dcx + (pb.x - pa.x);
-    vy[e] = (float)dcy + (pb.y - pa.y);
+    const float2 v = edge_vec(P[e], P[e + 1], k.W, k.H);
+    vx[e] = v.x;
+    vy[e] = v.y;
   }
   for (int j = lane; j < nJ; j += 32) thr[j] = drive_angle(D[j], t);
   for (int i = lane; i < B; i += 32) {
@@ -90,34 +188,19 @@ __global__ void __launch_bounds__(256) k_pbd(const WorldDev* __restrict__ worlds
     dly[i] = 0.0f;
   }
   __syncwarp();
-
-  const float hb = 0.5f * w.k_bend;
-  const float hs = 0.5f * w.k_st;
-  const float ksh = w.k_sh;
-  const float ko = w.orient * hs * ksh;
-  for (int iter = 0; iter < w.n_pbd; ++iter) {
-    // bending pass (Eq. 1): C_j = (theta_{j+1} - theta_j) - theta_rest,j
+  for (int iter = 0; iter < k.n_pbd; ++iter) {
     for (int j = lane; j < nJ; j += 32) C[j] = th[j + 1] - th[j] - thr[j];
     __syncwarp();
     for (int e = lane; e < nE; e += 32) {
       const float c1 = e < nJ ? C[e] : 0.0f;      // edge e is theta_1 of joint e
       const float c0 = e > 0 ? C[e - 1] : 0.0f;   // ... and theta_2 of joint e-1
-      th[e] += hb * (c1 - c0);
+      th[e] += k.hb * (c1 - c0);
     }
     __syncwarp();
-    // position pass (Eqs. 2-4) on the updated frames
     for (int e = lane; e < nE; e += 32) {
-      const float x = vx[e] + (dlx[e + 1] - dlx[e]);
-      const float y = vy[e] + (dly[e + 1] - dly[e]);
-      const float L = Lr[e];
-      const float ell = sqrtf(x * x + y * y);
-      const float sc = (ell - L) / ell;
-      const float csx = sc * x, csy = sc * y;
-      float sn, cs;
-      sincosf(th[e], &sn, &cs);
-      ddx[e] = hs * (csx + ksh * (x - L * cs - csx));
-      ddy[e] = hs * (csy + ksh * (y - L * sn - csy));
-      th[e] += ko * (cs * y - sn * x) / L;   // frame turns toward the edge (orient)
+      float the = th[e];
+      edge_correction(vx[e] + (dlx[e + 1] - dlx[e]), vy[e] + (dly[e + 1] - dly[e]), Lr[e], the, k, ddx[e], ddy[e]);
+      th[e] = the;
     }
     __syncwarp();
     for (int i = lane; i < B; i += 32) {
@@ -129,24 +212,38 @@ __global__ void __launch_bounds__(256) k_pbd(const WorldDev* __restrict__ worlds
     __syncwarp();
   }
   for (int e = lane; e < nE; e += 32) w.theta[e0 + e] = th[e];
-
-  // elastic force F_el = kappa (x_hat - X) / dt, and the 8x8-bin histogram (a2)
-  // with one atomic per group of lanes sharing a bin
   float fmax = 0.0f;
   for (int i0 = 0; i0 < B; i0 += 32) {
     const int i = i0 + lane;
-    int bin = -1 - lane;
-    if (i < B) {
-      const float2 fe = make_float2(w.kappa_dt * dlx[i], w.kappa_dt * dly[i]);
-      w.fel[b0 + i] = fe;
-      fmax = fmaxf(fmax, fmaxf(fabsf(fe.x), fabsf(fe.y)));
-      const float4 p = P[i];
-      bin = (cell_y(p) / kBin) * w.nbx + cell_x(p) / kBin;
-      w.bead_bin[b0 + i] = bin;
-    }
-    const unsigned peers = __match_any_sync(0xffffffffu, bin);
-    if (i < B && (__ffs(peers) - 1) == lane) atomicAdd(&w.bin_count[bin], __popc(peers));
+    bead_out(w, k, i < B, b0 + i, i < B ? P[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f), i < B ? dlx[i] : 0.0f,
+             i < B ? dly[i] : 0.0f, fmax);
   }
+  return fmax;
+}
+
+// One warp per filament (a1 + a3 + the a2 histogram).  Bead positions enter
+// as edge vectors v0 = min_image(X_b - X_a) plus the accumulated corrections,
+// so the corrections keep full FP32 precision whatever the magnitude of the
+// coordinates.  Filaments of at most 64 beads run in registers; longer ones
+// in the warp's slice of dynamic shared memory (maxB floats per array; zero
+// when no filament of the launch is longer than 64 beads).
+__global__ void __launch_bounds__(256) k_pbd(const WorldDev* __restrict__ worlds,
+                                             const int2* __restrict__ items, int n_items, int maxB) {
+  extern __shared__ __align__(16) float smem[];   // maxB is a multiple of 4: float4 slices stay aligned
+  const int wpb = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int item = blockIdx.x * wpb + warp;
+  if (item >= n_items) return;  // warp-uniform exit; the kernel has no block barrier
+  const int2 it = items[item];
+  const WorldDev& w = worlds[it.x];
+  const int f = it.y;
+  const int b0 = w.fil_off[f];
+  const int B = w.fil_off[f + 1] - b0;
+  const int e0 = b0 - f, j0 = b0 - 2 * f;
+  const long long t = *w.t;
+  const PbdConst k = pbd_const(w);
+  float fmax = B <= 64 ? pbd_regs(w, k, b0, B, e0, j0, t)
+                       : pbd_smem(w, k, b0, B, e0, j0, t, smem + (size_t)warp * maxB * kPbdFloatsPerBead, maxB);
   // largest |F_el| component of the world this step (bounds the spread's
   // fixed-point scale); non-negative floats order like their bit patterns
   for (int o = 16; o > 0; o >>= 1) fmax = fmaxf(fmax, __shfl_xor_sync(0xffffffffu, fmax, o));
@@ -298,7 +395,8 @@ void launch_pbd(const Plan& p, cudaStream_t s) {
   if (p.n_fil_items == 0) return;
   const int mb = (p.max_B + 3) & ~3;
   const int wpb = pbd_warps_per_block(mb);
-  const size_t smem = (size_t)wpb * mb * kPbdFloatsPerBead * sizeof(float);
+  // filaments of at most 64 beads need no shared memory
+  const size_t smem = p.max_B <= 64 ? 0 : (size_t)wpb * mb * kPbdFloatsPerBead * sizeof(float);
   if (smem > 48 * 1024) {
     cudaFuncSetAttribute(k_pbd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }

@@ -94,25 +94,6 @@ __global__ void __launch_bounds__(256) k_scan_apply(const WorldDev* __restrict__
 //   d*_i = d_i - (d+ - e+)/tau+ - (d- - e-)/tau- + (1 - 1/(2tau+)) S+ + (1 - 1/(2tau-)) S-
 // evaluated per opposite pair (i, opp(i)) from the even and odd parts.
 // ---------------------------------------------------------------------------
-struct PairOut {
-  float a, b;
-};
-
-__device__ __forceinline__ PairOut trt_pair(float di, float dib, float wi, float cu, float cF, float drho,
-                                            float rho, float uu, float uF, const WorldDev& w) {
-  const float ep = wi * (drho + rho * (4.5f * cu * cu - 1.5f * uu));
-  const float em = wi * rho * 3.0f * cu;
-  const float sp = wi * (9.0f * cu * cF - 3.0f * uF);
-  const float sm = wi * 3.0f * cF;
-  const float dp = 0.5f * (di + dib), dm = 0.5f * (di - dib);
-  const float even = -w.om_p * (dp - ep) + w.src_p * sp;
-  const float odd = -w.om_m * (dm - em) + w.src_m * sm;
-  PairOut o;
-  o.a = di + even + odd;
-  o.b = dib + even - odd;
-  return o;
-}
-
 __global__ void __launch_bounds__(kCellChunk) k_lbm(const WorldDev* __restrict__ worlds,
                                                     const int2* __restrict__ items) {
   const int2 it = items[blockIdx.x];
@@ -124,47 +105,8 @@ __global__ void __launch_bounds__(kCellChunk) k_lbm(const WorldDev* __restrict__
   const int xm = x == 0 ? W - 1 : x - 1, xp = x == W - 1 ? 0 : x + 1;
   const int ym = y == 0 ? H - 1 : y - 1, yp = y == H - 1 ? 0 : y + 1;
   const long long t = *w.t;
-  const float* __restrict__ src = w.g[t & 1];
-  float* __restrict__ dst = w.g[(t + 1) & 1];
-  const int r0 = y * W, rm = ym * W, rp = yp * W;
-  const float d0 = src[c];
-  const float d1 = src[1 * HW + r0 + xm];   // c = ( 1, 0) pulls from (x-1, y)
-  const float d2 = src[2 * HW + rm + x];    // ( 0, 1) from (x, y-1)
-  const float d3 = src[3 * HW + r0 + xp];   // (-1, 0) from (x+1, y)
-  const float d4 = src[4 * HW + rp + x];    // ( 0,-1) from (x, y+1)
-  const float d5 = src[5 * HW + rm + xm];   // ( 1, 1) from (x-1, y-1)
-  const float d6 = src[6 * HW + rm + xp];   // (-1, 1) from (x+1, y-1)
-  const float d7 = src[7 * HW + rp + xp];   // (-1,-1) from (x+1, y+1)
-  const float d8 = src[8 * HW + rp + xm];   // ( 1,-1) from (x-1, y+1)
-  const float2 F = w.F[c];
-
-  const float drho = ((d0 + (d1 + d3)) + (d2 + d4)) + ((d5 + d7) + (d6 + d8));
-  const float rho = 1.0f + drho;
-  const float jx = (d1 - d3) + (d5 - d7) + (d8 - d6);
-  const float jy = (d2 - d4) + (d5 - d7) + (d6 - d8);
-  const float inv = 1.0f / rho;
-  const float ux = (jx + 0.5f * F.x) * inv;
-  const float uy = (jy + 0.5f * F.y) * inv;
-  const float uu = ux * ux + uy * uy;
-  const float uF = ux * F.x + uy * F.y;
-
-  constexpr float w0 = 4.0f / 9.0f, w1 = 1.0f / 9.0f, w5 = 1.0f / 36.0f;
-  const float e0 = w0 * (drho - 1.5f * rho * uu);
-  const float s0 = w0 * (-3.0f * uF);
-  dst[c] = d0 - w.om_p * (d0 - e0) + w.src_p * s0;
-  const PairOut p13 = trt_pair(d1, d3, w1, ux, F.x, drho, rho, uu, uF, w);
-  const PairOut p24 = trt_pair(d2, d4, w1, uy, F.y, drho, rho, uu, uF, w);
-  const PairOut p57 = trt_pair(d5, d7, w5, ux + uy, F.x + F.y, drho, rho, uu, uF, w);
-  const PairOut p68 = trt_pair(d6, d8, w5, uy - ux, F.y - F.x, drho, rho, uu, uF, w);
-  dst[1 * HW + c] = p13.a;
-  dst[3 * HW + c] = p13.b;
-  dst[2 * HW + c] = p24.a;
-  dst[4 * HW + c] = p24.b;
-  dst[5 * HW + c] = p57.a;
-  dst[7 * HW + c] = p57.b;
-  dst[6 * HW + c] = p68.a;
-  dst[8 * HW + c] = p68.b;
-  w.u[c] = make_float2(ux, uy);
+  const LbmConst k{w.om_p, w.om_m, w.src_p, w.src_m};
+  w.u[c] = lbm_cell(w.g[t & 1], w.g[(t + 1) & 1], HW, y * W, ym * W, yp * W, x, xm, xp, w.F[c], k);
 }
 
 // ---------------------------------------------------------------------------
@@ -184,8 +126,7 @@ void enqueue_step(const Plan& p, cudaStream_t s) {
   launch_bin_scan(p, s);         // a2 offsets (two kernels)
   launch_bin_scatter(p, s);      // a2 scatter
   launch_deposit_x(p, s, 0);     // a4 + x pass of a5
-  launch_force_spread(p, s, 0);  // y pass of a5 + a6
-  launch_lbm(p, s);              // a7
+  launch_force_lbm(p, s);        // y pass of a5 + a6 + a7
   launch_interp_advance(p, s);   // a8
 }
 

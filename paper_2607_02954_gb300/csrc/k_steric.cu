@@ -1,5 +1,5 @@
 // a4-a6: steric deposit, Gaussian filter, steric force and immersed-boundary
-// force spread, in two tile kernels (one 32x32 tile of cells per block).
+// force spread, in tile kernels (one 32x32 tile of cells per block).
 //
 //   rho_s(c)  = sum_i delta_h(c - X_i)                        (a4, Fields)
 //   rho_bar   = G_sigma * rho_s, periodic, x pass then y pass  (a5, Fields)
@@ -14,17 +14,32 @@
 //                applies the y pass (rho_bar on the tile plus 4 cells),
 //                gathers the steric force of every bead whose stencil touches
 //                the tile, spreads F_el + F_s into the tile and writes F.
+// k_force_lbm    does the same and then the LBM step (a7) of the tile's
+//                cells with F taken from shared memory: the step's path.
 //
 // Beads are sorted by 8x8-cell bins in row-major order, so the beads that
 // can reach a tile lie in a few contiguous segments of the sorted arrays,
 // one per bin row (two where the row range wraps around the periodic edge).
 // Grid windows and bead records are staged in shared memory with cp.async,
 // every copy in flight at once, and all arithmetic reads shared memory.
+// The staged beads whose stencil reaches the tile are listed first (a
+// block-wide compaction), so the per-bead arithmetic runs on full warps.
 //
-// Periodic images: with several tiles on an axis a bead is taken at its
-// image in [-2, n - 2) relative to the tile origin; with one tile the tile is
-// the whole axis.  In both cases the tile column of stencil cell a is
-// wrap(rx - 1 + a) and it lies in the tile iff it is below the tile width.
+// Both kernels are compiled for each filter half width R (1..8) so that the
+// filter loops unroll with the taps in registers; a launch uses the largest R
+// of its worlds, and a world with a smaller R sees its taps padded with zeros
+// (which leaves every sum unchanged).  Everything that decides a result (the
+// bead ranges, the fixed-point scales) uses the world's own R.
+//
+// Stencil cells are accumulated in a halo-extended buffer (3 cells on each
+// side of the tile), so no per-cell wrap or bounds test is needed; cells
+// outside the tile belong to a neighbouring tile and are dropped, except on
+// an axis that one tile covers whole, where they are folded back
+// periodically before use.
+//
+// Periodic images: with several tiles on an axis a bead is taken at the one
+// image of it that can reach the tile (the reachable range is shorter than
+// the axis); with one tile the tile is the whole axis.
 #include "mc_internal.cuh"
 
 namespace mc {
@@ -32,12 +47,23 @@ namespace mc {
 namespace {
 
 constexpr int kMaxSeg = 32;
-constexpr int kRegX = kTile + 2 * kMaxR;   // deposit region columns (max)
-constexpr int kWin = kTile + 8;            // rho_bar window edge
-constexpr int kLoadRows = kTile + 8 + 2 * kMaxR;
-constexpr int kWarps = 8;
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
 constexpr int kDepCap = 1024;              // bead records staged per pass (deposit)
 constexpr int kForceCap = 640;             // bead records staged per pass (force)
+constexpr int kAx = kTile + 6;             // force accumulator edge: the tile and 3 halo cells a side
+constexpr int kWin = kTile + 8;            // rho_bar window edge: the tile and 4 cells a side
+
+template <int R>
+struct Geo {
+  static constexpr int kTaps = 2 * R + 1;
+  static constexpr int kL4 = (4 + 2 * R + 3) / 4;      // int4 loads per 4-column strip of the x pass
+  static constexpr int kDX0 = ((kTile + 2 * R + 11 + 3) / 4) * 4;
+  static constexpr int kDX1 = 4 * (kTile / 4 - 1) + 4 + 4 * kL4;
+  static constexpr int kDX = kDX0 > kDX1 ? kDX0 : kDX1;   // deposit accumulator row stride (ints)
+  static constexpr int kDY = kTile + 6;                    // deposit accumulator rows
+  static constexpr int kLoadRows = kWin + 2 * R;           // rho_x rows staged by the force kernel
+};
 
 __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
@@ -66,6 +92,7 @@ __device__ void build_segments(const WorldDev& w, int x_lo, int x_hi, int y_lo, 
                                int* s_pre, int* max_count) {
   const int lane = threadIdx.x & 31;
   const int nbx = w.nbx, nby = w.nby;
+  const int* bin_off = w.bin_off;
   int bx0 = floor_div(x_lo, kBin), bx1 = floor_div(x_hi, kBin);
   int by0 = floor_div(y_lo, kBin), by1 = floor_div(y_hi, kBin);
   if (bx1 - bx0 + 1 >= nbx) { bx0 = 0; bx1 = nbx - 1; }
@@ -90,8 +117,8 @@ __device__ void build_segments(const WorldDev& w, int x_lo, int x_hi, int y_lo, 
   int s0 = 0, len = 0;
   if (valid) {
     const int row = wrap_once(by0 + r, nby) * nbx;
-    s0 = w.bin_off[row + lo];
-    len = w.bin_off[row + hi + 1] - s0;
+    s0 = bin_off[row + lo];
+    len = bin_off[row + hi + 1] - s0;
   }
   int incl = len;
   for (int o = 1; o < 32; o <<= 1) {
@@ -107,7 +134,7 @@ __device__ void build_segments(const WorldDev& w, int x_lo, int x_hi, int y_lo, 
     for (int k = lane; k < ncol * nrow; k += 32) {
       const int rr = k / ncol, cc = k - rr * ncol;
       const int bin = wrap_once(by0 + rr, nby) * nbx + wrap_once(bx0 + cc, nbx);
-      m = max(m, w.bin_off[bin + 1] - w.bin_off[bin]);
+      m = max(m, bin_off[bin + 1] - bin_off[bin]);
     }
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) *max_count = m;
@@ -120,230 +147,373 @@ __device__ __forceinline__ int seg_slot(int v, const int* s_start, const int* s_
   return s_start[j] + v - s_pre[j];
 }
 
-// Periodic image of d in [-2, n - 2).
-__device__ __forceinline__ int image(int d, int n) {
-  if (d < -2) d += n;
-  else if (d >= n - 2) d -= n;
+// Periodic image of d in (-n, n) taken in [-lo, n - lo).
+__device__ __forceinline__ int image_lo(int d, int n, int lo) {
+  if (d < -lo) d += n;
+  else if (d >= n - lo) d -= n;
   return d;
 }
 
-__device__ __forceinline__ float block_max(float v, float* red) {
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+// Appends `code` to the block's list when `keep`; every lane of the warp
+// calls this together.  The list order depends on warp timing, which no
+// result depends on (the accumulation is in integers).
+__device__ __forceinline__ void list_push(bool keep, int code, int* list, int* s_cnt) {
+  const unsigned m = __ballot_sync(0xffffffffu, keep);
+  if (m == 0u) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(s_cnt, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (keep) list[base + __popc(m & ((1u << lane) - 1u))] = code;
+}
+
+// list code: staged slot v (10 bits), rx + 16 and ry + 16 (11 bits each)
+__device__ __forceinline__ int pack_code(int v, int rx, int ry) { return v | ((rx + 16) << 10) | ((ry + 16) << 21); }
+__device__ __forceinline__ int code_slot(int c) { return c & 1023; }
+__device__ __forceinline__ int code_rx(int c) { return ((c >> 10) & 2047) - 16; }
+__device__ __forceinline__ int code_ry(int c) { return (c >> 21) - 16; }
+
+template <typename T>
+__device__ __forceinline__ T block_max(T v, T* red) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  float m = red[0];
-  for (int k = 1; k < kWarps; ++k) m = fmaxf(m, red[k]);
+  T m = red[0];
+  for (int k = 1; k < kWarps; ++k) m = max(m, red[k]);
   __syncthreads();
   return m;
+}
+
+// Taps of a world with half width wR laid out for half width R >= wR.
+template <int R>
+__device__ __forceinline__ float padded_tap(const WorldDev& w, int wR, int m) {
+  const int k = m - (R - wR);
+  return (k >= 0 && k <= 2 * wR) ? w.taps[k] : 0.0f;
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------------------
 // a4 + the x pass of a5.
+//
+// Accumulator: row ly + 3 for tile rows ly in [-3, th + 3); column
+// lx + oxe for region columns lx, where the region is the tile plus wR
+// columns a side (origin x0, oxe = R + 4, so every 4-column strip of the x
+// pass starts on a 16-byte boundary) or, when that would cover the axis
+// more than once, the whole axis (origin 0, oxe = 4, folded).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_deposit_x(const WorldDev* __restrict__ worlds,
-                                                   const int2* __restrict__ items, int store_fields) {
-  __shared__ int acc[kTile * kRegX];
-  __shared__ float rsf[kTile * kRegX];
-  __shared__ float4 sp[kDepCap];
-  __shared__ float taps[2 * kMaxR + 1];
-  __shared__ int s_start[kMaxSeg], s_pre[kMaxSeg + 1], s_maxc;
-  __shared__ float red[kWarps];
+template <int R>
+__global__ void __launch_bounds__(kThreads) k_deposit_x(const WorldDev* __restrict__ worlds,
+                                                        const int2* __restrict__ items, int store_fields) {
+  using G = Geo<R>;
+  __shared__ __align__(16) int acc[G::kDY * G::kDX];
+  __shared__ __align__(16) float4 sp[kDepCap];
+  __shared__ int list[kDepCap];
+  __shared__ float tap_s[G::kTaps];
+  __shared__ int s_start[kMaxSeg], s_pre[kMaxSeg + 1], s_maxc, s_cnt;
+  __shared__ int red[kWarps];
   const int2 it = items[blockIdx.x];
   const WorldDev& w = worlds[it.x];
-  const int W = w.W, H = w.H, R = w.R, ntx = w.ntx;
+  const int W = w.W, H = w.H, wR = w.R, ntx = w.ntx, nty = w.nty;
+  const float4* __restrict__ spos = w.spos;
+  float* __restrict__ rho_x = w.rho_x;
+  float* __restrict__ rho_s_out = w.rho_s;
+  float* __restrict__ tile_max = w.tile_rho_max;
   const int tx = it.y % ntx, ty = it.y / ntx;
   const int x0 = tx * kTile, y0 = ty * kTile;
   const int tw = min(kTile, W - x0), th = min(kTile, H - y0);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // x: region = tile +- R columns, or the whole periodic axis when it is short
-  const bool full_x = W < tw + 2 * R + 3;
-  const int ox = full_x ? 0 : x0 - R;
-  const int extx = full_x ? W : tw + 2 * R;
-  const bool full_y = w.nty == 1;
-  if (warp == 0) build_segments(w, x0 - R - 2, x0 + tw + R, y0 - 2, y0 + th, s_start, s_pre, &s_maxc);
-  if (warp == 1 && lane <= 2 * R) taps[lane] = w.taps[lane];
-  for (int c = threadIdx.x; c < th * kRegX; c += blockDim.x) acc[c] = 0;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool full_x = W < tw + 2 * wR + 3;
+  const bool full_y = nty == 1;
+  const int cx0 = full_x ? 0 : x0;              // region column origin
+  const int oxe = full_x ? 4 : R + 4;           // accumulator column of region column 0
+  if (warp == 0) build_segments(w, x0 - wR - 2, x0 + tw + wR, y0 - 2, y0 + th, s_start, s_pre, &s_maxc);
+  if (warp == 1 && lane < G::kTaps) tap_s[lane] = padded_tap<R>(w, wR, lane);
+  for (int c = tid; c < G::kDY * G::kDX / 4; c += kThreads) reinterpret_cast<int4*>(acc)[c] = make_int4(0, 0, 0, 0);
+  if (tid == 0) s_cnt = 0;
   __syncthreads();
   const int total = s_pre[kMaxSeg];
   // a cell's 4x4 stencil neighbourhood overlaps at most 2x2 bins and each
   // bead adds at most 1/4: the cell sum is below the largest bin count
   const int k = fix_exponent((float)s_maxc + 1.0f);
-  const float scale = ldexpf(1.0f, k);
+  const float scale = pow2f(k);
   for (int c0 = 0; c0 < total; c0 += kDepCap) {
     const int n = min(kDepCap, total - c0);
-    for (int v = threadIdx.x; v < n; v += blockDim.x) cp_async16(&sp[v], &w.spos[seg_slot(c0 + v, s_start, s_pre)]);
+    for (int v = tid; v < n; v += kThreads) cp_async16(&sp[v], &spos[seg_slot(c0 + v, s_start, s_pre)]);
     cp_async_wait_all();
     __syncthreads();
-    for (int v = threadIdx.x; v < n; v += blockDim.x) {
-      const float4 p = sp[v];
-      int rx = cell_x(p) - ox, ry = cell_y(p) - y0;
-      if (!full_x) {
-        rx = image(rx, W);
-        if (rx > extx) continue;
+    for (int v0 = 0; v0 < n; v0 += kThreads) {
+      const int v = v0 + tid;
+      bool keep = false;
+      int rx = 0, ry = 0;
+      if (v < n) {
+        const float4 p = sp[v];
+        rx = cell_x(p) - cx0;
+        ry = cell_y(p) - y0;
+        keep = true;
+        if (!full_x) {
+          rx = image_lo(rx, W, wR + 2);
+          keep = rx <= tw + wR;
+        }
+        if (!full_y) {
+          ry = image_lo(ry, H, 2);
+          keep = keep && ry <= th;
+        }
       }
-      if (!full_y) {
-        ry = image(ry, H);
-        if (ry > th) continue;
-      }
+      list_push(keep, pack_code(v, rx, ry), list, &s_cnt);
+    }
+    __syncthreads();
+    const int cnt = s_cnt;
+    for (int q = tid; q < cnt; q += kThreads) {
+      const int code = list[q];
+      const float4 p = sp[code_slot(code)];
+      const int rx = code_rx(code), ry = code_ry(code);
       float wx[4], wy[4];
       peskin4(p.x, wx);
       peskin4(p.y, wy);
+      int* base = acc + (ry + 2) * G::kDX + rx - 1 + oxe;
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        const int row = wrap_once(ry - 1 + b, H);
-        if (row >= th) continue;
         const float sy = wy[b] * scale;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const int col = full_x ? wrap_once(rx - 1 + a, W) : rx - 1 + a;
-          if ((unsigned)col >= (unsigned)extx) continue;
-          atomicAdd(&acc[row * kRegX + col], __float2int_rn(wx[a] * sy));
-        }
+        for (int a = 0; a < 4; ++a) atomicAdd(base + b * G::kDX + a, __float2int_rn(wx[a] * sy));
       }
     }
     __syncthreads();
+    if (tid == 0) s_cnt = 0;
   }
-  const float inv = ldexpf(1.0f, -k);
-  const int cbase = full_x ? x0 : R;   // region column of tile column 0
-  float vmax = 0.0f;
-  for (int row = warp; row < th; row += kWarps) {
-    for (int col = lane; col < extx; col += 32) {
-      const float v = (float)acc[row * kRegX + col] * inv;
-      rsf[row * kRegX + col] = v;
-      const int lx = col - cbase;
-      if (lx >= 0 && lx < tw) {
-        vmax = fmaxf(vmax, v);
-        if (store_fields) w.rho_s[(y0 + row) * W + x0 + lx] = v;
-      }
+  if (full_x || full_y) {
+    // fold the stencil cells that wrapped around an axis the region covers whole
+    for (int c = tid; c < G::kDY * G::kDX; c += kThreads) {
+      const int ly = c / G::kDX - 3, lx = c % G::kDX - oxe;
+      const bool out_y = ly < 0 || ly >= th;
+      const bool out_x = full_x && (lx < 0 || lx >= W);
+      if ((!out_y && !out_x) || (out_y && !full_y)) continue;
+      const int v = acc[c];
+      if (v == 0) continue;
+      const int ly2 = out_y ? wrap_mod(ly, H) : ly;
+      const int lx2 = out_x ? wrap_mod(lx, W) : lx;
+      atomicAdd(&acc[(ly2 + 3) * G::kDX + lx2 + oxe], v);
+    }
+    __syncthreads();
+  }
+  const float inv = pow2f(-k);
+  const int col0 = x0 - cx0 + oxe;              // accumulator column of tile column 0
+  int vmax = 0;
+  for (int c = tid; c < th * kTile; c += kThreads) {
+    const int ly = c >> 5, lx = c & 31;
+    if (lx < tw) {
+      const int v = acc[(ly + 3) * G::kDX + col0 + lx];
+      vmax = max(vmax, v);
+      if (store_fields) rho_s_out[(size_t)(y0 + ly) * W + x0 + lx] = (float)v * inv;
     }
   }
-  vmax = block_max(vmax, red);   // includes the barrier the x pass needs
-  if (threadIdx.x == 0) w.tile_rho_max[it.y] = vmax;
-  for (int row = warp; row < th; row += kWarps) {
-    const float* r = rsf + row * kRegX;
-    if (lane < tw) {
-      float s = 0.0f;
-      if (full_x) {
-        for (int m = 0; m <= 2 * R; ++m) s = fmaf(taps[m], r[wrap_mod(x0 + lane - R + m, W)], s);
-      } else {
-        for (int m = 0; m <= 2 * R; ++m) s = fmaf(taps[m], r[lane + m], s);
+  vmax = block_max(vmax, red);
+  if (tid == 0) tile_max[it.y] = (float)vmax * inv;
+  // x pass with the fixed-point scale folded into the taps (a power of two:
+  // the same products as converting first)
+  float tp[G::kTaps];
+#pragma unroll
+  for (int m = 0; m < G::kTaps; ++m) tp[m] = tap_s[m] * inv;
+  if (!full_x) {
+    const int ly = tid >> 3, s = tid & 7;       // row, strip of 4 columns
+    if (ly < th && 4 * s < tw) {
+      const int4* src = reinterpret_cast<const int4*>(acc + (ly + 3) * G::kDX + 4 * s + oxe - R);
+      float v[4 * G::kL4];
+#pragma unroll
+      for (int q = 0; q < G::kL4; ++q) {
+        const int4 t4 = src[q];
+        v[4 * q] = (float)t4.x;
+        v[4 * q + 1] = (float)t4.y;
+        v[4 * q + 2] = (float)t4.z;
+        v[4 * q + 3] = (float)t4.w;
       }
-      w.rho_x[(y0 + row) * W + x0 + lane] = s;
+      float o[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float sacc = 0.0f;
+#pragma unroll
+        for (int m = 0; m < G::kTaps; ++m) sacc = fmaf(tp[m], v[j + m], sacc);
+        o[j] = sacc;
+      }
+      *reinterpret_cast<float4*>(rho_x + (size_t)(y0 + ly) * W + x0 + 4 * s) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+  } else {
+    for (int c = tid; c < th * tw; c += kThreads) {
+      const int ly = c / tw, lx = c - ly * tw;
+      const int* r = acc + (ly + 3) * G::kDX + oxe;
+      float sacc = 0.0f;
+#pragma unroll
+      for (int m = 0; m < G::kTaps; ++m) sacc = fmaf(tp[m], (float)r[wrap_mod(x0 + lx - R + m, W)], sacc);
+      rho_x[(size_t)(y0 + ly) * W + x0 + lx] = sacc;
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// The y pass of a5, and a6.
+// The y pass of a5, and a6, for one tile; the result stays in shared memory.
+//
+// Window: rho_x rows [y0 - 4 - R, y0 + th + 4 + R) x columns [x0 - 4,
+// x0 + tw + 4), periodic; rho_bar on window rows and columns [0, th + 8) x
+// [0, tw + 8) (tile cell (lx, ly) at window (lx + 4, ly + 4)).  Spread
+// accumulators: tile cell (lx, ly) at (lx + 3, ly + 3), F = acc 2^-k.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_force_spread(const WorldDev* __restrict__ worlds,
-                                                      const int2* __restrict__ items, int store_fields,
-                                                      int after_step) {
-  __shared__ float xb[kLoadRows * kWin];
-  __shared__ float win[kWin * kWin];
-  __shared__ int accx[kTile * kTile], accy[kTile * kTile];
-  __shared__ float4 sp[kForceCap];
-  __shared__ float2 sf[kForceCap];
-  __shared__ int si[kForceCap];
-  __shared__ float taps[2 * kMaxR + 1];
-  __shared__ int s_start[kMaxSeg], s_pre[kMaxSeg + 1];
-  __shared__ float red[16];
-  const int2 it = items[blockIdx.x];
-  const WorldDev& w = worlds[it.x];
-  const int W = w.W, H = w.H, R = w.R, ntx = w.ntx, nty = w.nty;
-  const int tx = it.y % ntx, ty = it.y / ntx;
-  const int x0 = tx * kTile, y0 = ty * kTile;
-  const int tw = min(kTile, W - x0), th = min(kTile, H - y0);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+template <int R>
+struct ForceSmem {
+  float xb[Geo<R>::kLoadRows * kWin];
+  float win[kWin * kWin];
+  int accx[kAx * kAx];
+  int accy[kAx * kAx];
+  float4 sp[kForceCap];
+  float2 sf[kForceCap];
+  int si[kForceCap];
+  int list[kForceCap];
+  float tap_s[Geo<R>::kTaps];
+  int s_start[kMaxSeg], s_pre[kMaxSeg + 1], s_cnt;
+  float red[16];
+};
+
+struct TileBox {
+  int x0, y0, tw, th;
+};
+
+// Returns k; accx/accy hold the tile's F 2^k (folded where needed) and the
+// block is synchronised.
+template <int R>
+__device__ __forceinline__ int force_tile(ForceSmem<R>& sm, const WorldDev& w, int tile, const TileBox& tb,
+                                          int store_fields, int after_step) {
+  using G = Geo<R>;
+  const int W = w.W, H = w.H, wR = w.R, ntx = w.ntx, nty = w.nty;
+  const float4* __restrict__ spos = w.spos;
+  const float2* __restrict__ sfel = w.sfel;
+  const int* __restrict__ sid = w.sid;
+  const float* __restrict__ rho_x = w.rho_x;
+  const float* __restrict__ tile_max = w.tile_rho_max;
+  float2* __restrict__ fs_out = w.fs;
+  float* __restrict__ rho_b = w.rho_b;
+  const float k_rep = w.k_rep;
+  const float fmax_el = __uint_as_float(w.fel_max[(*w.t - after_step) & 1]);
+  const int x0 = tb.x0, y0 = tb.y0, tw = tb.tw, th = tb.th;
+  const int tx = x0 / kTile, ty = y0 / kTile;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ww = tw + 8, wh = th + 8, lh = wh + 2 * R;
   // 1. bead segments (one round trip), then every other load in one batch
-  if (warp == 0) build_segments(w, x0 - 2, x0 + tw, y0 - 2, y0 + th, s_start, s_pre, nullptr);
-  __syncthreads();
-  const int total = s_pre[kMaxSeg];
-  {
-    // rho_x rows [y0 - 4 - R, y0 + th + 4 + R) x columns [x0 - 4, x0 + tw + 4), wrapped
-    // offsets reach at most 4 + R <= 12 cells outside the axis: one
-    // conditional correction suffices unless the axis is shorter than that
-    const int gx0 = W >= 16 ? wrap_once(x0 - 4 + lane, W) : wrap_mod(x0 - 4 + lane, W);
-    const int gx1 = W >= 44 ? wrap_once(x0 + 28 + lane, W) : wrap_mod(x0 + 28 + lane, W);
-    for (int i = warp; i < lh; i += kWarps) {
-      const int gy = y0 - 4 - R + i;
-      const float* src = w.rho_x + (size_t)(H >= 2 * kMaxR + 8 ? wrap_once(gy, H) : wrap_mod(gy, H)) * W;
-      if (lane < ww) cp_async4(&xb[i * kWin + lane], src + gx0);
-      if (lane + 32 < ww) cp_async4(&xb[i * kWin + 32 + lane], src + gx1);
-    }
-  }
-  const int n0 = min(kForceCap, total);
-  for (int v = threadIdx.x; v < n0; v += blockDim.x) {
-    const int slot = seg_slot(v, s_start, s_pre);
-    cp_async16(&sp[v], &w.spos[slot]);
-    cp_async8(&sf[v], &w.sfel[slot]);
-    cp_async4(&si[v], &w.sid[slot]);
-  }
-  if (warp == 1 && lane <= 2 * R) taps[lane] = w.taps[lane];
+  if (warp == 0) build_segments(w, x0 - 2, x0 + tw, y0 - 2, y0 + th, sm.s_start, sm.s_pre, nullptr);
+  if (warp == 1 && lane < G::kTaps) sm.tap_s[lane] = padded_tap<R>(w, wR, lane);
   // bound of the cell sums of weight * |F_el + F_s|:
   //   |F_s| <= k_rep/2 max|rho_bar(c+1) - rho_bar(c-1)| <= k_rep/2 max rho_bar
   //        <= k_rep/2 max rho_s over the 3x3 tiles around this one,
   // times max rho_s of this tile (the sum of the spread weights of a cell)
   if (warp == 2 && lane < 9) {
     const int ty2 = wrap_once(ty + lane / 3 - 1, nty), tx2 = wrap_once(tx + lane % 3 - 1, ntx);
-    red[lane] = w.tile_rho_max[ty2 * ntx + tx2];
+    sm.red[lane] = tile_max[ty2 * ntx + tx2];
   }
-  for (int c = threadIdx.x; c < kTile * kTile; c += blockDim.x) {
-    accx[c] = 0;
-    accy[c] = 0;
+  for (int c = tid; c < kAx * kAx / 4; c += kThreads) {
+    reinterpret_cast<int4*>(sm.accx)[c] = make_int4(0, 0, 0, 0);
+    reinterpret_cast<int4*>(sm.accy)[c] = make_int4(0, 0, 0, 0);
   }
-  const long long t = *w.t - after_step;
-  const float fmax_el = __uint_as_float(w.fel_max[t & 1]);
-  const float rho_max = w.tile_rho_max[it.y];
+  if (tid == 0) sm.s_cnt = 0;
+  const float rho_max = tile_max[tile];
+  __syncthreads();
+  const int total = sm.s_pre[kMaxSeg];
+  {
+    // the window in 16-byte chunks: a 4-column chunk never straddles the
+    // periodic edge (x0 and W are multiples of 8), rows reach at most
+    // 4 + R <= 12 cells outside the axis
+    const int nq = ww >> 2, rows_per_pass = kThreads / nq;
+    const int i0 = tid / nq, q = tid - i0 * nq;
+    if (i0 < rows_per_pass) {
+      const int col = wrap_once(x0 - 4 + 4 * q, W);
+      for (int i = i0; i < lh; i += rows_per_pass) {
+        const int gy = y0 - 4 - R + i;
+        const int row = H >= 12 ? wrap_once(gy, H) : wrap_mod(gy, H);
+        cp_async16(&sm.xb[i * kWin + 4 * q], rho_x + (size_t)row * W + col);
+      }
+    }
+  }
+  const int n0 = min(kForceCap, total);
+  for (int v = tid; v < n0; v += kThreads) {
+    const int slot = seg_slot(v, sm.s_start, sm.s_pre);
+    cp_async16(&sm.sp[v], &spos[slot]);
+    cp_async8(&sm.sf[v], &sfel[slot]);
+    cp_async4(&sm.si[v], &sid[slot]);
+  }
   cp_async_wait_all();
   __syncthreads();
-  float rho_nb = red[0];
-  for (int k2 = 1; k2 < 9; ++k2) rho_nb = fmaxf(rho_nb, red[k2]);
-  const float k_rep = w.k_rep;
+  float rho_nb = sm.red[0];
+  for (int k2 = 1; k2 < 9; ++k2) rho_nb = fmaxf(rho_nb, sm.red[k2]);
   const int k = fix_exponent((fmax_el + 0.5f * k_rep * rho_nb) * rho_max * 1.0001f + 1e-30f);
-  const float scale = ldexpf(1.0f, k);
-  for (int i = warp; i < wh; i += kWarps) {
-    for (int j = lane; j < ww; j += 32) {
-      float s = 0.0f;
-      for (int m = 0; m <= 2 * R; ++m) s = fmaf(taps[m], xb[(i + m) * kWin + j], s);
-      win[i * kWin + j] = s;
-      if (store_fields && i >= 4 && i < th + 4 && j >= 4 && j < tw + 4) w.rho_b[(y0 + i - 4) * W + x0 + j - 4] = s;
+  const float scale = pow2f(k);
+  {
+    // y pass, 8 window rows per thread
+    float tp[G::kTaps];
+#pragma unroll
+    for (int m = 0; m < G::kTaps; ++m) tp[m] = sm.tap_s[m];
+    const int nstrip = wh >> 3;
+    for (int c = tid; c < nstrip * ww; c += kThreads) {
+      const int s = c / ww, j = c - s * ww;
+      const float* src = sm.xb + (8 * s) * kWin + j;
+      float v[8 + 2 * R];
+#pragma unroll
+      for (int q = 0; q < 8 + 2 * R; ++q) v[q] = src[q * kWin];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        float sacc = 0.0f;
+#pragma unroll
+        for (int m = 0; m < G::kTaps; ++m) sacc = fmaf(tp[m], v[r + m], sacc);
+        const int i = 8 * s + r;
+        sm.win[i * kWin + j] = sacc;
+        if (store_fields && i >= 4 && i < th + 4 && j >= 4 && j < tw + 4)
+          rho_b[(size_t)(y0 + i - 4) * W + x0 + j - 4] = sacc;
+      }
     }
   }
   __syncthreads();
   for (int c0 = 0; c0 < total; c0 += kForceCap) {
     const int n = min(kForceCap, total - c0);
     if (c0 > 0) {   // the first chunk was staged with the window
-      for (int v = threadIdx.x; v < n; v += blockDim.x) {
-        const int slot = seg_slot(c0 + v, s_start, s_pre);
-        cp_async16(&sp[v], &w.spos[slot]);
-        cp_async8(&sf[v], &w.sfel[slot]);
-        cp_async4(&si[v], &w.sid[slot]);
+      for (int v = tid; v < n; v += kThreads) {
+        const int slot = seg_slot(c0 + v, sm.s_start, sm.s_pre);
+        cp_async16(&sm.sp[v], &spos[slot]);
+        cp_async8(&sm.sf[v], &sfel[slot]);
+        cp_async4(&sm.si[v], &sid[slot]);
       }
       cp_async_wait_all();
       __syncthreads();
     }
-    for (int v = threadIdx.x; v < n; v += blockDim.x) {
-      const float4 p = sp[v];
-      const int cx = cell_x(p), cy = cell_y(p);
-      int rx = cx - x0, ry = cy - y0;
-      if (ntx > 1) {
-        rx = image(rx, W);
-        if (rx < -2 || rx > tw) continue;
+    for (int v0 = 0; v0 < n; v0 += kThreads) {
+      const int v = v0 + tid;
+      bool keep = false;
+      int rx = 0, ry = 0;
+      if (v < n) {
+        const float4 p = sm.sp[v];
+        rx = cell_x(p) - x0;
+        ry = cell_y(p) - y0;
+        keep = true;
+        if (ntx > 1) {
+          rx = image_lo(rx, W, 2);
+          keep = rx <= tw;
+        }
+        if (nty > 1) {
+          ry = image_lo(ry, H, 2);
+          keep = keep && ry <= th;
+        }
       }
-      if (nty > 1) {
-        ry = image(ry, H);
-        if (ry < -2 || ry > th) continue;
-      }
+      list_push(keep, pack_code(v, rx, ry), sm.list, &sm.s_cnt);
+    }
+    __syncthreads();
+    const int cnt = sm.s_cnt;
+    for (int q = tid; q < cnt; q += kThreads) {
+      const int code = sm.list[q];
+      const int v = code_slot(code), rx = code_rx(code), ry = code_ry(code);
+      const float4 p = sm.sp[v];
       float wx[4], wy[4];
       peskin4(p.x, wx);
       peskin4(p.y, wy);
       // stencil cell a sits at window column rx + 3 + a; the central
       // differences read one cell further on each side
-      const float* base = win + (ry + 2) * kWin + rx + 2;
+      const float* base = sm.win + (ry + 2) * kWin + rx + 2;
       float gsx = 0.0f, gsy = 0.0f;
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
@@ -360,41 +530,144 @@ __global__ void __launch_bounds__(256) k_force_spread(const WorldDev* __restrict
         gsy = fmaf(wy[b], sy, gsy);
       }
       const float Fsx = -0.5f * k_rep * gsx, Fsy = -0.5f * k_rep * gsy;
-      if (cx >= x0 && cx < x0 + tw && cy >= y0 && cy < y0 + th) w.fs[si[v]] = make_float2(Fsx, Fsy);
-      const float2 fe = sf[v];
+      if (rx >= 0 && rx < tw && ry >= 0 && ry < th) fs_out[sm.si[v]] = make_float2(Fsx, Fsy);
+      const float2 fe = sm.sf[v];
       const float Fx = (fe.x + Fsx) * scale, Fy = (fe.y + Fsy) * scale;
+      float ax[4], ay[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        ax[a] = wx[a] * Fx;
+        ay[a] = wx[a] * Fy;
+      }
+      int* bx = sm.accx + (ry + 2) * kAx + rx + 2;
+      int* by = sm.accy + (ry + 2) * kAx + rx + 2;
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        const int ly = wrap_once(ry - 1 + b, H);
-        if (ly >= th) continue;
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-          const int lx = wrap_once(rx - 1 + a, W);
-          if (lx >= tw) continue;
-          const float wgt = wx[a] * wy[b];
-          atomicAdd(&accx[ly * kTile + lx], __float2int_rn(wgt * Fx));
-          atomicAdd(&accy[ly * kTile + lx], __float2int_rn(wgt * Fy));
+          atomicAdd(bx + b * kAx + a, __float2int_rn(wy[b] * ax[a]));
+          atomicAdd(by + b * kAx + a, __float2int_rn(wy[b] * ay[a]));
         }
       }
     }
     __syncthreads();
+    if (tid == 0) sm.s_cnt = 0;
   }
-  const float inv = ldexpf(1.0f, -k);
-  for (int ly = warp; ly < th; ly += kWarps) {
-    if (lane < tw) {
-      const int s = ly * kTile + lane;
-      w.F[(y0 + ly) * W + x0 + lane] = make_float2((float)accx[s] * inv, (float)accy[s] * inv);
+  if (ntx == 1 || nty == 1) {
+    // fold the stencil cells that wrapped around an axis this tile covers whole
+    const bool fx = ntx == 1, fy = nty == 1;
+    for (int c = tid; c < kAx * kAx; c += kThreads) {
+      const int ly = c / kAx - 3, lx = c % kAx - 3;
+      const bool out_y = ly < 0 || ly >= th, out_x = lx < 0 || lx >= tw;
+      if ((!out_y && !out_x) || (out_y && !fy) || (out_x && !fx)) continue;
+      const int vx = sm.accx[c], vy = sm.accy[c];
+      const int t2 = (wrap_mod(ly, th) + 3) * kAx + wrap_mod(lx, tw) + 3;
+      if (vx) atomicAdd(&sm.accx[t2], vx);
+      if (vy) atomicAdd(&sm.accy[t2], vy);
+    }
+    __syncthreads();
+  }
+  return k;
+}
+
+__device__ __forceinline__ TileBox tile_box(const WorldDev& w, int tile) {
+  TileBox b;
+  const int tx = tile % w.ntx, ty = tile / w.ntx;
+  b.x0 = tx * kTile;
+  b.y0 = ty * kTile;
+  b.tw = min(kTile, w.W - b.x0);
+  b.th = min(kTile, w.H - b.y0);
+  return b;
+}
+
+// y pass of a5 + a6: writes F.
+template <int R>
+__global__ void __launch_bounds__(kThreads) k_force_spread(const WorldDev* __restrict__ worlds,
+                                                           const int2* __restrict__ items, int store_fields,
+                                                           int after_step) {
+  __shared__ __align__(16) ForceSmem<R> sm;
+  const int2 it = items[blockIdx.x];
+  const WorldDev& w = worlds[it.x];
+  const TileBox tb = tile_box(w, it.y);
+  float2* __restrict__ F_out = w.F;
+  const int W = w.W;
+  const int k = force_tile<R>(sm, w, it.y, tb, store_fields, after_step);
+  const float inv = pow2f(-k);
+  const int lane = threadIdx.x & 31;
+  for (int ly = threadIdx.x >> 5; ly < tb.th; ly += kWarps) {
+    if (lane < tb.tw) {
+      const int s = (ly + 3) * kAx + lane + 3;
+      F_out[(size_t)(tb.y0 + ly) * W + tb.x0 + lane] = make_float2((float)sm.accx[s] * inv, (float)sm.accy[s] * inv);
     }
   }
 }
 
-void launch_deposit_x(const Plan& p, cudaStream_t s, int store_fields) {
-  if (p.n_tile_items) k_deposit_x<<<p.n_tile_items, 256, 0, s>>>(p.d_worlds, p.d_tile_items, store_fields);
+// y pass of a5 + a6 + a7 on the tile's cells: F goes from shared memory
+// straight into the collision (the same arithmetic as k_force_spread
+// followed by k_lbm, without F's round trip through HBM).
+template <int R>
+__global__ void __launch_bounds__(kThreads) k_force_lbm(const WorldDev* __restrict__ worlds,
+                                                        const int2* __restrict__ items) {
+  __shared__ __align__(16) ForceSmem<R> sm;
+  const int2 it = items[blockIdx.x];
+  const WorldDev& w = worlds[it.x];
+  const TileBox tb = tile_box(w, it.y);
+  const int W = w.W, H = w.H, HW = H * W;
+  const long long t = *w.t;
+  const float* __restrict__ src = w.g[t & 1];
+  float* __restrict__ dst = w.g[(t + 1) & 1];
+  float2* __restrict__ u_out = w.u;
+  const LbmConst kc{w.om_p, w.om_m, w.src_p, w.src_m};
+  const int k = force_tile<R>(sm, w, it.y, tb, 0, 0);
+  const float inv = pow2f(-k);
+  const int lane = threadIdx.x & 31;
+  if (lane < tb.tw) {
+    const int x = tb.x0 + lane;
+    const int xm = x == 0 ? W - 1 : x - 1, xp = x == W - 1 ? 0 : x + 1;
+    for (int ly = threadIdx.x >> 5; ly < tb.th; ly += kWarps) {
+      const int y = tb.y0 + ly;
+      const int ym = y == 0 ? H - 1 : y - 1, yp = y == H - 1 ? 0 : y + 1;
+      const int s = (ly + 3) * kAx + lane + 3;
+      const float2 F = make_float2((float)sm.accx[s] * inv, (float)sm.accy[s] * inv);
+      u_out[(size_t)y * W + x] = lbm_cell(src, dst, HW, y * W, ym * W, yp * W, x, xm, xp, F, kc);
+    }
+  }
 }
 
-void launch_force_spread(const Plan& p, cudaStream_t s, int store_fields, int after_step) {
-  if (p.n_tile_items)
-    k_force_spread<<<p.n_tile_items, 256, 0, s>>>(p.d_worlds, p.d_tile_items, store_fields, after_step);
+namespace {
+
+template <int R>
+void launch_steric(const Plan& p, cudaStream_t s, int which, int store_fields, int after_step) {
+  if (which == 0)
+    k_deposit_x<R><<<p.n_tile_items, kThreads, 0, s>>>(p.d_worlds, p.d_tile_items, store_fields);
+  else if (which == 1)
+    k_force_spread<R><<<p.n_tile_items, kThreads, 0, s>>>(p.d_worlds, p.d_tile_items, store_fields, after_step);
+  else
+    k_force_lbm<R><<<p.n_tile_items, kThreads, 0, s>>>(p.d_worlds, p.d_tile_items);
 }
+
+void dispatch_steric(const Plan& p, cudaStream_t s, int which, int store_fields, int after_step) {
+  if (!p.n_tile_items) return;
+  switch (p.max_R) {
+    case 1: launch_steric<1>(p, s, which, store_fields, after_step); break;
+    case 2: launch_steric<2>(p, s, which, store_fields, after_step); break;
+    case 3: launch_steric<3>(p, s, which, store_fields, after_step); break;
+    case 4: launch_steric<4>(p, s, which, store_fields, after_step); break;
+    case 5: launch_steric<5>(p, s, which, store_fields, after_step); break;
+    case 6: launch_steric<6>(p, s, which, store_fields, after_step); break;
+    case 7: launch_steric<7>(p, s, which, store_fields, after_step); break;
+    default: launch_steric<kMaxR>(p, s, which, store_fields, after_step); break;
+  }
+}
+
+}  // namespace
+
+void launch_deposit_x(const Plan& p, cudaStream_t s, int store_fields) { dispatch_steric(p, s, 0, store_fields, 0); }
+
+void launch_force_spread(const Plan& p, cudaStream_t s, int store_fields, int after_step) {
+  dispatch_steric(p, s, 1, store_fields, after_step);
+}
+
+void launch_force_lbm(const Plan& p, cudaStream_t s) { dispatch_steric(p, s, 2, 0, 0); }
 
 }  // namespace mc

@@ -534,6 +534,7 @@ mc_status mc_step_stage(mc_world* w, int stage, void* stream) {
     case 3: mc::launch_deposit_x(p, s, 0); break;
     case 4: mc::launch_force_spread(p, s, 0); break;
     case 5: mc::launch_lbm(p, s); break;
+    case 7: mc::launch_force_lbm(p, s); break;
     default:
       mc::launch_interp_advance(p, s);
       w->t += 1;
@@ -606,7 +607,14 @@ mc_status mc_world_get_field(const mc_world* w, int field, void* out, int mem_ki
       src = field == MC_FIELD_RHO_S ? (const void*)h.rho_s : (const void*)h.rho_b;
       bytes = HW * sizeof(float);
       break;
-    case MC_FIELD_FORCE: src = h.F; bytes = HW * sizeof(float2); break;
+    case MC_FIELD_FORCE:
+      // the step hands F from the spread to the collision in shared memory:
+      // re-run the spread on the last step's binned beads (deterministic)
+      mc::launch_force_spread(w->plan, s, 0, 1);
+      MC_CUDA(cudaGetLastError());
+      src = h.F;
+      bytes = HW * sizeof(float2);
+      break;
     case MC_FIELD_U: src = h.u; bytes = HW * sizeof(float2); break;
     case MC_FIELD_BIN: src = h.bead_bin; bytes = h.N * sizeof(int); break;
     case MC_FIELD_BIN_OFF: src = h.bin_off; bytes = (h.n_bins + 1) * sizeof(int); break;

@@ -118,6 +118,7 @@ void launch_deposit_x(const Plan& p, cudaStream_t s, int store_fields);
 // after_step = 1 when re-run after the step that produced the binned beads
 void launch_force_spread(const Plan& p, cudaStream_t s, int store_fields, int after_step = 0);
 void launch_lbm(const Plan& p, cudaStream_t s);
+void launch_force_lbm(const Plan& p, cudaStream_t s);   // y pass of a5 + a6 + a7 in one kernel
 void launch_interp_advance(const Plan& p, cudaStream_t s);
 void enqueue_step(const Plan& p, cudaStream_t s);
 constexpr int kKernelsPerStep = 8;
@@ -170,18 +171,92 @@ __device__ __forceinline__ void peskin4(float a, float w[4]) {
   w[3] = (q - s) * 0.125f;
 }
 
+// One cell of a7 (D2Q9 TRT with Guo forcing, shifted populations d = f - w):
+// pulls the nine populations of cell c = r0 + x from its neighbours in
+// `src` (rows r0, rm = row above in pull order y - 1, rp = y + 1; columns
+// x, xm = x - 1, xp = x + 1, all wrapped), collides with force density F,
+// stores the post-collision populations of c in `dst` (SoA, plane stride
+// HW) and returns the velocity u = (sum c_i f_i + F/2) / rho.
+struct LbmConst {
+  float om_p, om_m, src_p, src_m;   // 1/tau+-, 1 - 1/(2 tau+-)
+};
+
+struct PairOut {
+  float a, b;
+};
+
+__device__ __forceinline__ PairOut trt_pair(float di, float dib, float wi, float cu, float cF, float drho,
+                                            float rho, float uu, float uF, const LbmConst& k) {
+  const float ep = wi * (drho + rho * (4.5f * cu * cu - 1.5f * uu));
+  const float em = wi * rho * 3.0f * cu;
+  const float sp = wi * (9.0f * cu * cF - 3.0f * uF);
+  const float sm = wi * 3.0f * cF;
+  const float dp = 0.5f * (di + dib), dm = 0.5f * (di - dib);
+  const float even = -k.om_p * (dp - ep) + k.src_p * sp;
+  const float odd = -k.om_m * (dm - em) + k.src_m * sm;
+  PairOut o;
+  o.a = di + even + odd;
+  o.b = dib + even - odd;
+  return o;
+}
+
+__device__ __forceinline__ float2 lbm_cell(const float* __restrict__ src, float* __restrict__ dst, int HW, int r0,
+                                           int rm, int rp, int x, int xm, int xp, float2 F, const LbmConst& k) {
+  const int c = r0 + x;
+  const float d0 = src[c];
+  const float d1 = src[1 * HW + r0 + xm];   // c = ( 1, 0) pulls from (x-1, y)
+  const float d2 = src[2 * HW + rm + x];    // ( 0, 1) from (x, y-1)
+  const float d3 = src[3 * HW + r0 + xp];   // (-1, 0) from (x+1, y)
+  const float d4 = src[4 * HW + rp + x];    // ( 0,-1) from (x, y+1)
+  const float d5 = src[5 * HW + rm + xm];   // ( 1, 1) from (x-1, y-1)
+  const float d6 = src[6 * HW + rm + xp];   // (-1, 1) from (x+1, y-1)
+  const float d7 = src[7 * HW + rp + xp];   // (-1,-1) from (x+1, y+1)
+  const float d8 = src[8 * HW + rp + xm];   // ( 1,-1) from (x-1, y+1)
+  const float drho = ((d0 + (d1 + d3)) + (d2 + d4)) + ((d5 + d7) + (d6 + d8));
+  const float rho = 1.0f + drho;
+  const float jx = (d1 - d3) + (d5 - d7) + (d8 - d6);
+  const float jy = (d2 - d4) + (d5 - d7) + (d6 - d8);
+  const float inv = __frcp_rn(rho);
+  const float ux = (jx + 0.5f * F.x) * inv;
+  const float uy = (jy + 0.5f * F.y) * inv;
+  const float uu = ux * ux + uy * uy;
+  const float uF = ux * F.x + uy * F.y;
+  constexpr float w0 = 4.0f / 9.0f, w1 = 1.0f / 9.0f, w5 = 1.0f / 36.0f;
+  const float e0 = w0 * (drho - 1.5f * rho * uu);
+  const float s0 = w0 * (-3.0f * uF);
+  dst[c] = d0 - k.om_p * (d0 - e0) + k.src_p * s0;
+  const PairOut p13 = trt_pair(d1, d3, w1, ux, F.x, drho, rho, uu, uF, k);
+  const PairOut p24 = trt_pair(d2, d4, w1, uy, F.y, drho, rho, uu, uF, k);
+  const PairOut p57 = trt_pair(d5, d7, w5, ux + uy, F.x + F.y, drho, rho, uu, uF, k);
+  const PairOut p68 = trt_pair(d6, d8, w5, uy - ux, F.y - F.x, drho, rho, uu, uF, k);
+  dst[1 * HW + c] = p13.a;
+  dst[3 * HW + c] = p13.b;
+  dst[2 * HW + c] = p24.a;
+  dst[4 * HW + c] = p24.b;
+  dst[5 * HW + c] = p57.a;
+  dst[7 * HW + c] = p57.b;
+  dst[6 * HW + c] = p68.a;
+  dst[8 * HW + c] = p68.b;
+  return make_float2(ux, uy);
+}
+
 __device__ __forceinline__ int cell_x(const float4& p) { return __float_as_int(p.z); }
 __device__ __forceinline__ int cell_y(const float4& p) { return __float_as_int(p.w); }
 
-// Exponent k of the per-tile fixed-point scale for a bound on |cell sums|.
+// Exponent k of the per-tile fixed-point scale for a bound on |cell sums|:
+// the largest k in [8, 40] with bound * 2^k < 2^30.  With bound = m 2^e,
+// m in [0.5, 1), k = 30 - e; e is read from the exponent bits (a subnormal
+// bound gives e = -126 and k clamps to 40 as it would anyway).
 __device__ __forceinline__ int fix_exponent(float bound) {
   if (!(bound > 0.0f)) return 40;
   if (!(bound < 1.0e30f)) return 8;
-  int e;
-  frexpf(bound, &e);   // bound < 2^e
+  const int e = ((__float_as_int(bound) >> 23) & 255) - 126;
   const int k = 30 - e;
   return k < 8 ? 8 : (k > 40 ? 40 : k);
 }
+
+// 2^k for k in [-126, 127] (exact, from the exponent bits).
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
 
 }  // namespace mc
 

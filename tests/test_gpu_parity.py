@@ -264,6 +264,33 @@ def test_batched_equals_alone_bitwise():
         w.close()
 
 
+@pytest.mark.parametrize("side", [128, 40, 24])
+def test_stage_sequences_equal_the_step_bitwise(side):
+    """mc_step runs the fused spread + LBM kernel (stage 7); stages 0..6 run
+    the same step with F through device memory (stages 4 and 5).  Both, and
+    the fused stage sequence 0, 1, 2, 3, 7, 6, give the same world bitwise."""
+    import ctypes
+    from paper_2607_02954_gb300 import _lib
+    lib = _lib.load()
+    spec = synth.world_random(7, side, 6 if side < 64 else 20)
+    sh = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    worlds = [_gpu_world(spec) for _ in range(3)]
+    for _ in range(5):
+        worlds[0].step(1)
+        for sid in (0, 1, 2, 3, 4, 5, 6):
+            _lib.check(lib.mc_step_stage(worlds[1].handle, sid, sh))
+        for sid in (0, 1, 2, 3, 7, 6):
+            _lib.check(lib.mc_step_stage(worlds[2].handle, sid, sh))
+    torch.cuda.synchronize()
+    st = [w.state(fluid=True) for w in worlds]
+    for k in st[0]:
+        assert np.array_equal(st[0][k], st[1][k]), k
+        assert np.array_equal(st[0][k], st[2][k]), k
+    for w in worlds:
+        assert w.info()["t"] == 5
+        w.close()
+
+
 def test_graph_replay_equals_direct_steps_bitwise():
     spec = synth.world_c1(3)
     a = _gpu_world(spec)
