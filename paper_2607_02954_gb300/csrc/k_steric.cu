@@ -49,10 +49,11 @@ namespace {
 constexpr int kMaxSeg = 32;
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kDepCap = 1024;              // bead records staged per pass (deposit)
+constexpr int kDepCap = 640;              // bead records staged per pass (deposit)
 constexpr int kForceCap = 640;             // bead records staged per pass (force)
 constexpr int kAx = kTile + 6;             // force accumulator edge: the tile and 3 halo cells a side
 constexpr int kWin = kTile + 8;            // rho_bar window edge: the tile and 4 cells a side
+__constant__ int kLbmCy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};   // D2Q9 lattice velocities, y components
 
 template <int R>
 struct Geo {
@@ -129,21 +130,30 @@ __device__ void build_segments(const WorldDev& w, int x_lo, int x_hi, int y_lo, 
   s_pre[lane + 1] = incl;
   if (lane == 0) s_pre[0] = 0;
   if (max_count) {
+    // the box spans at most 8 bin columns (tile + 2 R + 3 <= 51 cells) and
+    // 16 bin rows; lane (rr, cc) = (lane / 8, lane % 8) covers 4 rows per round
     int m = 0;
     const int ncol = bx1 - bx0 + 1, nrow = by1 - by0 + 1;
-    for (int k = lane; k < ncol * nrow; k += 32) {
-      const int rr = k / ncol, cc = k - rr * ncol;
-      const int bin = wrap_once(by0 + rr, nby) * nbx + wrap_once(bx0 + cc, nbx);
-      m = max(m, bin_off[bin + 1] - bin_off[bin]);
+    const int cc = lane & 7;
+    for (int rr = lane >> 3; rr < nrow; rr += 4) {
+      if (cc < ncol) {
+        const int bin = wrap_once(by0 + rr, nby) * nbx + wrap_once(bx0 + cc, nbx);
+        m = max(m, bin_off[bin + 1] - bin_off[bin]);
+      }
     }
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) *max_count = m;
   }
 }
 
+// Slot of the v-th bead of the concatenated segments: the segment j with
+// s_pre[j] <= v < s_pre[j + 1] by binary search over the 33 prefix entries
+// (non-decreasing; empty segments repeat a value and are never chosen).
 __device__ __forceinline__ int seg_slot(int v, const int* s_start, const int* s_pre) {
   int j = 0;
-  while (v >= s_pre[j + 1]) ++j;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1)
+    if (v >= s_pre[j + step]) j += step;
   return s_start[j] + v - s_pre[j];
 }
 
@@ -204,7 +214,7 @@ __device__ __forceinline__ float padded_tap(const WorldDev& w, int wR, int m) {
 // more than once, the whole axis (origin 0, oxe = 4, folded).
 // ---------------------------------------------------------------------------
 template <int R>
-__global__ void __launch_bounds__(kThreads) k_deposit_x(const WorldDev* __restrict__ worlds,
+__global__ void __launch_bounds__(kThreads, 8) k_deposit_x(const WorldDev* __restrict__ worlds,
                                                         const int2* __restrict__ items, int store_fields) {
   using G = Geo<R>;
   __shared__ __align__(16) int acc[G::kDY * G::kDX];
@@ -378,8 +388,35 @@ struct TileBox {
   int x0, y0, tw, th;
 };
 
-// Returns k; accx/accy hold the tile's F 2^k (folded where needed) and the
-// block is synchronised.
+// Lists the n staged beads whose stencil reaches the tile (image taken on
+// axes with several tiles), packed with their tile-relative cell.
+template <int R>
+__device__ __forceinline__ void force_compact(ForceSmem<R>& sm, int n, const TileBox& tb, int W, int H, int ntx,
+                                              int nty) {
+  for (int v0 = 0; v0 < n; v0 += kThreads) {
+    const int v = v0 + threadIdx.x;
+    bool keep = false;
+    int rx = 0, ry = 0;
+    if (v < n) {
+      const float4 p = sm.sp[v];
+      rx = cell_x(p) - tb.x0;
+      ry = cell_y(p) - tb.y0;
+      keep = true;
+      if (ntx > 1) {
+        rx = image_lo(rx, W, 2);
+        keep = rx <= tb.tw;
+      }
+      if (nty > 1) {
+        ry = image_lo(ry, H, 2);
+        keep = keep && ry <= tb.th;
+      }
+    }
+    list_push(keep, pack_code(v, rx, ry), sm.list, &sm.s_cnt);
+  }
+}
+
+// Returns k: after the caller synchronises the block, accx/accy hold the
+// tile's F 2^k (before folding, see force_fold).
 template <int R>
 __device__ __forceinline__ int force_tile(ForceSmem<R>& sm, const WorldDev& w, int tile, const TileBox& tb,
                                           int store_fields, int after_step) {
@@ -398,7 +435,23 @@ __device__ __forceinline__ int force_tile(ForceSmem<R>& sm, const WorldDev& w, i
   const int tx = x0 / kTile, ty = y0 / kTile;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ww = tw + 8, wh = th + 8, lh = wh + 2 * R;
-  // 1. bead segments (one round trip), then every other load in one batch
+  // 1. the rho_x window (independent of the beads) and the bead segments
+  //    (one round trip), then the bead records in one batch
+  {
+    // the window in 16-byte chunks: a 4-column chunk never straddles the
+    // periodic edge (x0 and W are multiples of 8), rows reach at most
+    // 4 + R <= 12 cells outside the axis
+    const int nq = ww >> 2, rows_per_pass = kThreads / nq;
+    const int i0 = tid / nq, q = tid - i0 * nq;
+    if (i0 < rows_per_pass) {
+      const int col = wrap_once(x0 - 4 + 4 * q, W);
+      for (int i = i0; i < lh; i += rows_per_pass) {
+        const int gy = y0 - 4 - R + i;
+        const int row = H >= 12 ? wrap_once(gy, H) : wrap_mod(gy, H);
+        cp_async16(&sm.xb[i * kWin + 4 * q], rho_x + (size_t)row * W + col);
+      }
+    }
+  }
   if (warp == 0) build_segments(w, x0 - 2, x0 + tw, y0 - 2, y0 + th, sm.s_start, sm.s_pre, nullptr);
   if (warp == 1 && lane < G::kTaps) sm.tap_s[lane] = padded_tap<R>(w, wR, lane);
   // bound of the cell sums of weight * |F_el + F_s|:
@@ -417,21 +470,6 @@ __device__ __forceinline__ int force_tile(ForceSmem<R>& sm, const WorldDev& w, i
   const float rho_max = tile_max[tile];
   __syncthreads();
   const int total = sm.s_pre[kMaxSeg];
-  {
-    // the window in 16-byte chunks: a 4-column chunk never straddles the
-    // periodic edge (x0 and W are multiples of 8), rows reach at most
-    // 4 + R <= 12 cells outside the axis
-    const int nq = ww >> 2, rows_per_pass = kThreads / nq;
-    const int i0 = tid / nq, q = tid - i0 * nq;
-    if (i0 < rows_per_pass) {
-      const int col = wrap_once(x0 - 4 + 4 * q, W);
-      for (int i = i0; i < lh; i += rows_per_pass) {
-        const int gy = y0 - 4 - R + i;
-        const int row = H >= 12 ? wrap_once(gy, H) : wrap_mod(gy, H);
-        cp_async16(&sm.xb[i * kWin + 4 * q], rho_x + (size_t)row * W + col);
-      }
-    }
-  }
   const int n0 = min(kForceCap, total);
   for (int v = tid; v < n0; v += kThreads) {
     const int slot = seg_slot(v, sm.s_start, sm.s_pre);
@@ -445,6 +483,8 @@ __device__ __forceinline__ int force_tile(ForceSmem<R>& sm, const WorldDev& w, i
   for (int k2 = 1; k2 < 9; ++k2) rho_nb = fmaxf(rho_nb, sm.red[k2]);
   const int k = fix_exponent((fmax_el + 0.5f * k_rep * rho_nb) * rho_max * 1.0001f + 1e-30f);
   const float scale = pow2f(k);
+  // list the first chunk's beads that reach the tile, then the y pass
+  force_compact(sm, n0, tb, W, H, ntx, nty);
   {
     // y pass, 8 window rows per thread
     float tp[G::kTaps];
@@ -470,39 +510,7 @@ __device__ __forceinline__ int force_tile(ForceSmem<R>& sm, const WorldDev& w, i
     }
   }
   __syncthreads();
-  for (int c0 = 0; c0 < total; c0 += kForceCap) {
-    const int n = min(kForceCap, total - c0);
-    if (c0 > 0) {   // the first chunk was staged with the window
-      for (int v = tid; v < n; v += kThreads) {
-        const int slot = seg_slot(c0 + v, sm.s_start, sm.s_pre);
-        cp_async16(&sm.sp[v], &spos[slot]);
-        cp_async8(&sm.sf[v], &sfel[slot]);
-        cp_async4(&sm.si[v], &sid[slot]);
-      }
-      cp_async_wait_all();
-      __syncthreads();
-    }
-    for (int v0 = 0; v0 < n; v0 += kThreads) {
-      const int v = v0 + tid;
-      bool keep = false;
-      int rx = 0, ry = 0;
-      if (v < n) {
-        const float4 p = sm.sp[v];
-        rx = cell_x(p) - x0;
-        ry = cell_y(p) - y0;
-        keep = true;
-        if (ntx > 1) {
-          rx = image_lo(rx, W, 2);
-          keep = rx <= tw;
-        }
-        if (nty > 1) {
-          ry = image_lo(ry, H, 2);
-          keep = keep && ry <= th;
-        }
-      }
-      list_push(keep, pack_code(v, rx, ry), sm.list, &sm.s_cnt);
-    }
-    __syncthreads();
+  for (int c0 = 0;;) {
     const int cnt = sm.s_cnt;
     for (int q = tid; q < cnt; q += kThreads) {
       const int code = sm.list[q];
@@ -550,24 +558,41 @@ __device__ __forceinline__ int force_tile(ForceSmem<R>& sm, const WorldDev& w, i
         }
       }
     }
-    __syncthreads();
+    c0 += kForceCap;
+    if (c0 >= total) break;
+    __syncthreads();   // every thread is done with this chunk
     if (tid == 0) sm.s_cnt = 0;
-  }
-  if (ntx == 1 || nty == 1) {
-    // fold the stencil cells that wrapped around an axis this tile covers whole
-    const bool fx = ntx == 1, fy = nty == 1;
-    for (int c = tid; c < kAx * kAx; c += kThreads) {
-      const int ly = c / kAx - 3, lx = c % kAx - 3;
-      const bool out_y = ly < 0 || ly >= th, out_x = lx < 0 || lx >= tw;
-      if ((!out_y && !out_x) || (out_y && !fy) || (out_x && !fx)) continue;
-      const int vx = sm.accx[c], vy = sm.accy[c];
-      const int t2 = (wrap_mod(ly, th) + 3) * kAx + wrap_mod(lx, tw) + 3;
-      if (vx) atomicAdd(&sm.accx[t2], vx);
-      if (vy) atomicAdd(&sm.accy[t2], vy);
+    const int n = min(kForceCap, total - c0);
+    for (int v = tid; v < n; v += kThreads) {
+      const int slot = seg_slot(c0 + v, sm.s_start, sm.s_pre);
+      cp_async16(&sm.sp[v], &spos[slot]);
+      cp_async8(&sm.sf[v], &sfel[slot]);
+      cp_async4(&sm.si[v], &sid[slot]);
     }
+    cp_async_wait_all();
+    __syncthreads();
+    force_compact(sm, n, tb, W, H, ntx, nty);
     __syncthreads();
   }
-  return k;
+  return k;   // the caller synchronises before it reads the accumulators
+}
+
+// Folds the stencil cells that wrapped around an axis the tile covers whole
+// (one tile on that axis); call after the block has synchronised.
+template <int R>
+__device__ __forceinline__ void force_fold(ForceSmem<R>& sm, const TileBox& tb, int ntx, int nty) {
+  if (ntx > 1 && nty > 1) return;
+  const bool fx = ntx == 1, fy = nty == 1;
+  for (int c = threadIdx.x; c < kAx * kAx; c += kThreads) {
+    const int ly = c / kAx - 3, lx = c % kAx - 3;
+    const bool out_y = ly < 0 || ly >= tb.th, out_x = lx < 0 || lx >= tb.tw;
+    if ((!out_y && !out_x) || (out_y && !fy) || (out_x && !fx)) continue;
+    const int vx = sm.accx[c], vy = sm.accy[c];
+    const int t2 = (wrap_mod(ly, tb.th) + 3) * kAx + wrap_mod(lx, tb.tw) + 3;
+    if (vx) atomicAdd(&sm.accx[t2], vx);
+    if (vy) atomicAdd(&sm.accy[t2], vy);
+  }
+  __syncthreads();
 }
 
 __device__ __forceinline__ TileBox tile_box(const WorldDev& w, int tile) {
@@ -592,6 +617,8 @@ __global__ void __launch_bounds__(kThreads) k_force_spread(const WorldDev* __res
   float2* __restrict__ F_out = w.F;
   const int W = w.W;
   const int k = force_tile<R>(sm, w, it.y, tb, store_fields, after_step);
+  __syncthreads();
+  force_fold(sm, tb, w.ntx, w.nty);
   const float inv = pow2f(-k);
   const int lane = threadIdx.x & 31;
   for (int ly = threadIdx.x >> 5; ly < tb.th; ly += kWarps) {
@@ -606,7 +633,7 @@ __global__ void __launch_bounds__(kThreads) k_force_spread(const WorldDev* __res
 // straight into the collision (the same arithmetic as k_force_spread
 // followed by k_lbm, without F's round trip through HBM).
 template <int R>
-__global__ void __launch_bounds__(kThreads) k_force_lbm(const WorldDev* __restrict__ worlds,
+__global__ void __launch_bounds__(kThreads, 4) k_force_lbm(const WorldDev* __restrict__ worlds,
                                                         const int2* __restrict__ items) {
   __shared__ __align__(16) ForceSmem<R> sm;
   const int2 it = items[blockIdx.x];
@@ -618,19 +645,43 @@ __global__ void __launch_bounds__(kThreads) k_force_lbm(const WorldDev* __restri
   float* __restrict__ dst = w.g[(t + 1) & 1];
   float2* __restrict__ u_out = w.u;
   const LbmConst kc{w.om_p, w.om_m, w.src_p, w.src_m};
+  {
+    // start the DRAM reads of the collision now: the 128-byte row segments
+    // that the tile's cells pull from (plane i, rows y - c_iy) go to L2
+    // while the force phase runs
+    const int th = tb.th;
+    for (int c = threadIdx.x; c < 9 * th; c += kThreads) {
+      const int i = c / th, r = c - i * th;
+      const int y = wrap_once(tb.y0 + r - kLbmCy[i], H);
+      const float* a = src + (size_t)i * HW + (size_t)y * W + tb.x0;
+      asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a));
+    }
+  }
   const int k = force_tile<R>(sm, w, it.y, tb, 0, 0);
   const float inv = pow2f(-k);
-  const int lane = threadIdx.x & 31;
-  if (lane < tb.tw) {
-    const int x = tb.x0 + lane;
-    const int xm = x == 0 ? W - 1 : x - 1, xp = x == W - 1 ? 0 : x + 1;
-    for (int ly = threadIdx.x >> 5; ly < tb.th; ly += kWarps) {
-      const int y = tb.y0 + ly;
-      const int ym = y == 0 ? H - 1 : y - 1, yp = y == H - 1 ? 0 : y + 1;
-      const int s = (ly + 3) * kAx + lane + 3;
-      const float2 F = make_float2((float)sm.accx[s] * inv, (float)sm.accy[s] * inv);
-      u_out[(size_t)y * W + x] = lbm_cell(src, dst, HW, y * W, ym * W, yp * W, x, xm, xp, F, kc);
-    }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // each warp collides rows warp, warp + 8, ... of the tile; the populations
+  // of its next row are pulled before the current one is collided (the
+  // first before the barrier that completes the spread)
+  const bool active = lane < tb.tw && warp < tb.th;
+  const int x = tb.x0 + lane;
+  const int xm = x == 0 ? W - 1 : x - 1, xp = x == W - 1 ? 0 : x + 1;
+  LbmPull q;
+  int y = tb.y0 + warp;
+  if (active) lbm_pull(src, HW, y * W, (y == 0 ? H - 1 : y - 1) * W, (y == H - 1 ? 0 : y + 1) * W, x, xm, xp, q);
+  __syncthreads();
+  force_fold(sm, tb, w.ntx, w.nty);
+  if (!active) return;
+  for (int ly = warp; ly < tb.th; ly += kWarps) {
+    LbmPull qn;
+    const int yn = y + kWarps;
+    if (ly + kWarps < tb.th)
+      lbm_pull(src, HW, yn * W, (yn == 0 ? H - 1 : yn - 1) * W, (yn == H - 1 ? 0 : yn + 1) * W, x, xm, xp, qn);
+    const int s = (ly + 3) * kAx + lane + 3;
+    const float2 F = make_float2((float)sm.accx[s] * inv, (float)sm.accy[s] * inv);
+    u_out[(size_t)y * W + x] = lbm_collide(q, dst, HW, y * W + x, F, kc);
+    q = qn;
+    y = yn;
   }
 }
 

@@ -181,37 +181,54 @@ struct LbmConst {
   float om_p, om_m, src_p, src_m;   // 1/tau+-, 1 - 1/(2 tau+-)
 };
 
-struct PairOut {
-  float a, b;
-};
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 
-__device__ __forceinline__ PairOut trt_pair(float di, float dib, float wi, float cu, float cF, float drho,
-                                            float rho, float uu, float uF, const LbmConst& k) {
-  const float ep = wi * (drho + rho * (4.5f * cu * cu - 1.5f * uu));
-  const float em = wi * rho * 3.0f * cu;
-  const float sp = wi * (9.0f * cu * cF - 3.0f * uF);
-  const float sm = wi * 3.0f * cF;
-  const float dp = 0.5f * (di + dib), dm = 0.5f * (di - dib);
-  const float even = -k.om_p * (dp - ep) + k.src_p * sp;
-  const float odd = -k.om_m * (dm - em) + k.src_m * sm;
-  PairOut o;
-  o.a = di + even + odd;
-  o.b = dib + even - odd;
-  return o;
+// Two opposite pairs (i, opp(i)) at once in packed FP32x2 arithmetic (one
+// pair per component): with d+ = (d_i + d_opp)/2, d- = (d_i - d_opp)/2,
+//   e+ = w (drho + rho (4.5 (c.u)^2 - 1.5 u.u)),  e- = 3 w rho c.u,
+//   S+ = w (9 (c.u)(c.F) - 3 u.F),               S- = 3 w c.F,
+//   d*_i = d_i + even + odd,  d*_opp = d_opp + even - odd,
+//   even = -(d+ - e+)/tau+ + (1 - 1/(2 tau+)) S+,  odd = -(d- - e-)/tau- + (1 - 1/(2 tau-)) S-.
+__device__ __forceinline__ void trt_pairs(float2 di, float2 dib, float wi, float2 cu, float2 cF, float drho,
+                                          float rho, float uu, float uF, const LbmConst& k, float2& a, float2& b) {
+  const float2 c2 = __fmul2_rn(cu, cu);
+  const float2 t1 = __ffma2_rn(c2, f2(4.5f), f2(-1.5f * uu));
+  const float2 ep = __fmul2_rn(f2(wi), __ffma2_rn(f2(rho), t1, f2(drho)));
+  const float2 em = __fmul2_rn(f2(3.0f * wi * rho), cu);
+  const float2 sp = __ffma2_rn(__fmul2_rn(f2(9.0f * wi), cu), cF, f2(-3.0f * wi * uF));
+  const float2 sm = __fmul2_rn(f2(3.0f * wi), cF);
+  const float2 s = __fadd2_rn(di, dib);
+  const float2 d = __ffma2_rn(dib, f2(-1.0f), di);
+  const float2 even = __ffma2_rn(s, f2(-0.5f * k.om_p), __ffma2_rn(ep, f2(k.om_p), __fmul2_rn(f2(k.src_p), sp)));
+  const float2 odd = __ffma2_rn(d, f2(-0.5f * k.om_m), __ffma2_rn(em, f2(k.om_m), __fmul2_rn(f2(k.src_m), sm)));
+  a = __fadd2_rn(__fadd2_rn(di, even), odd);
+  b = __ffma2_rn(odd, f2(-1.0f), __fadd2_rn(dib, even));
 }
 
-__device__ __forceinline__ float2 lbm_cell(const float* __restrict__ src, float* __restrict__ dst, int HW, int r0,
-                                           int rm, int rp, int x, int xm, int xp, float2 F, const LbmConst& k) {
-  const int c = r0 + x;
-  const float d0 = src[c];
-  const float d1 = src[1 * HW + r0 + xm];   // c = ( 1, 0) pulls from (x-1, y)
-  const float d2 = src[2 * HW + rm + x];    // ( 0, 1) from (x, y-1)
-  const float d3 = src[3 * HW + r0 + xp];   // (-1, 0) from (x+1, y)
-  const float d4 = src[4 * HW + rp + x];    // ( 0,-1) from (x, y+1)
-  const float d5 = src[5 * HW + rm + xm];   // ( 1, 1) from (x-1, y-1)
-  const float d6 = src[6 * HW + rm + xp];   // (-1, 1) from (x+1, y-1)
-  const float d7 = src[7 * HW + rp + xp];   // (-1,-1) from (x+1, y+1)
-  const float d8 = src[8 * HW + rp + xm];   // ( 1,-1) from (x-1, y+1)
+// The nine pulled populations of cell (x, y) (see lbm_cell).
+struct LbmPull {
+  float d[9];
+};
+
+__device__ __forceinline__ void lbm_pull(const float* __restrict__ src, int HW, int r0, int rm, int rp, int x, int xm,
+                                         int xp, LbmPull& q) {
+  q.d[0] = src[r0 + x];
+  q.d[1] = src[1 * HW + r0 + xm];   // c = ( 1, 0) pulls from (x-1, y)
+  q.d[2] = src[2 * HW + rm + x];    // ( 0, 1) from (x, y-1)
+  q.d[3] = src[3 * HW + r0 + xp];   // (-1, 0) from (x+1, y)
+  q.d[4] = src[4 * HW + rp + x];    // ( 0,-1) from (x, y+1)
+  q.d[5] = src[5 * HW + rm + xm];   // ( 1, 1) from (x-1, y-1)
+  q.d[6] = src[6 * HW + rm + xp];   // (-1, 1) from (x+1, y-1)
+  q.d[7] = src[7 * HW + rp + xp];   // (-1,-1) from (x+1, y+1)
+  q.d[8] = src[8 * HW + rp + xm];   // ( 1,-1) from (x-1, y+1)
+}
+
+// Collision of cell c from its pulled populations: stores the post-collision
+// populations of c in `dst` and returns u.
+__device__ __forceinline__ float2 lbm_collide(const LbmPull& q, float* __restrict__ dst, int HW, int c, float2 F,
+                                              const LbmConst& k) {
+  const float d0 = q.d[0], d1 = q.d[1], d2 = q.d[2], d3 = q.d[3], d4 = q.d[4];
+  const float d5 = q.d[5], d6 = q.d[6], d7 = q.d[7], d8 = q.d[8];
   const float drho = ((d0 + (d1 + d3)) + (d2 + d4)) + ((d5 + d7) + (d6 + d8));
   const float rho = 1.0f + drho;
   const float jx = (d1 - d3) + (d5 - d7) + (d8 - d6);
@@ -225,19 +242,28 @@ __device__ __forceinline__ float2 lbm_cell(const float* __restrict__ src, float*
   const float e0 = w0 * (drho - 1.5f * rho * uu);
   const float s0 = w0 * (-3.0f * uF);
   dst[c] = d0 - k.om_p * (d0 - e0) + k.src_p * s0;
-  const PairOut p13 = trt_pair(d1, d3, w1, ux, F.x, drho, rho, uu, uF, k);
-  const PairOut p24 = trt_pair(d2, d4, w1, uy, F.y, drho, rho, uu, uF, k);
-  const PairOut p57 = trt_pair(d5, d7, w5, ux + uy, F.x + F.y, drho, rho, uu, uF, k);
-  const PairOut p68 = trt_pair(d6, d8, w5, uy - ux, F.y - F.x, drho, rho, uu, uF, k);
-  dst[1 * HW + c] = p13.a;
-  dst[3 * HW + c] = p13.b;
-  dst[2 * HW + c] = p24.a;
-  dst[4 * HW + c] = p24.b;
-  dst[5 * HW + c] = p57.a;
-  dst[7 * HW + c] = p57.b;
-  dst[6 * HW + c] = p68.a;
-  dst[8 * HW + c] = p68.b;
+  float2 a, b;
+  // pairs (1, 3) and (2, 4): c = (1, 0), (0, 1)
+  trt_pairs(make_float2(d1, d2), make_float2(d3, d4), w1, make_float2(ux, uy), F, drho, rho, uu, uF, k, a, b);
+  dst[1 * HW + c] = a.x;
+  dst[2 * HW + c] = a.y;
+  dst[3 * HW + c] = b.x;
+  dst[4 * HW + c] = b.y;
+  // pairs (5, 7) and (6, 8): c = (1, 1), (-1, 1)
+  trt_pairs(make_float2(d5, d6), make_float2(d7, d8), w5, make_float2(ux + uy, uy - ux),
+            make_float2(F.x + F.y, F.y - F.x), drho, rho, uu, uF, k, a, b);
+  dst[5 * HW + c] = a.x;
+  dst[6 * HW + c] = a.y;
+  dst[7 * HW + c] = b.x;
+  dst[8 * HW + c] = b.y;
   return make_float2(ux, uy);
+}
+
+__device__ __forceinline__ float2 lbm_cell(const float* __restrict__ src, float* __restrict__ dst, int HW, int r0,
+                                           int rm, int rp, int x, int xm, int xp, float2 F, const LbmConst& k) {
+  LbmPull q;
+  lbm_pull(src, HW, r0, rm, rp, x, xm, xp, q);
+  return lbm_collide(q, dst, HW, r0 + x, F, k);
 }
 
 __device__ __forceinline__ int cell_x(const float4& p) { return __float_as_int(p.z); }
