@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(kBeadChunk) k_bin_scatter(const WorldDev* __re
 // inertia-free advance X += dt U (cell index + fraction, wrapped) and the
 // unwrapped displacement D += dt U.  Thread 0 of each world's first block
 // advances the world's step counter (no other stage kernel reads it).
-__global__ void __launch_bounds__(kBeadChunk) k_interp_advance(const WorldDev* __restrict__ worlds,
+__global__ void __launch_bounds__(kBeadChunk, 8) k_interp_advance(const WorldDev* __restrict__ worlds,
                                                                const int2* __restrict__ items) {
   const int2 it = items[blockIdx.x];
   const WorldDev& w = worlds[it.x];

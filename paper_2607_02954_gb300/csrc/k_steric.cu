@@ -230,7 +230,8 @@ __global__ void __launch_bounds__(kThreads, 8) k_deposit_x(const WorldDev* __res
   float* __restrict__ rho_x = w.rho_x;
   float* __restrict__ rho_s_out = w.rho_s;
   float* __restrict__ tile_max = w.tile_rho_max;
-  const int tx = it.y % ntx, ty = it.y / ntx;
+  const int tx = it.y & 0xffff, ty = it.y >> 16;
+  const int tile = ty * ntx + tx;
   const int x0 = tx * kTile, y0 = ty * kTile;
   const int tw = min(kTile, W - x0), th = min(kTile, H - y0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_deposit_x(const WorldDev* __res
     }
   }
   vmax = block_max(vmax, red);
-  if (tid == 0) tile_max[it.y] = (float)vmax * inv;
+  if (tid == 0) tile_max[tile] = (float)vmax * inv;
   // x pass with the fixed-point scale folded into the taps (a power of two:
   // the same products as converting first)
   float tp[G::kTaps];
@@ -441,8 +442,16 @@ __device__ __forceinline__ int force_tile(ForceSmem<R>& sm, const WorldDev& w, i
     // the window in 16-byte chunks: a 4-column chunk never straddles the
     // periodic edge (x0 and W are multiples of 8), rows reach at most
     // 4 + R <= 12 cells outside the axis
-    const int nq = ww >> 2, rows_per_pass = kThreads / nq;
-    const int i0 = tid / nq, q = tid - i0 * nq;
+    const int nq = ww >> 2;
+    int rows_per_pass, i0;
+    if (nq == kWin / 4) {   // full tile: constant divisor
+      rows_per_pass = kThreads / (kWin / 4);
+      i0 = tid / (kWin / 4);
+    } else {
+      rows_per_pass = kThreads / nq;
+      i0 = tid / nq;
+    }
+    const int q = tid - i0 * nq;
     if (i0 < rows_per_pass) {
       const int col = wrap_once(x0 - 4 + 4 * q, W);
       for (int i = i0; i < lh; i += rows_per_pass) {
@@ -492,7 +501,10 @@ __device__ __forceinline__ int force_tile(ForceSmem<R>& sm, const WorldDev& w, i
     for (int m = 0; m < G::kTaps; ++m) tp[m] = sm.tap_s[m];
     const int nstrip = wh >> 3;
     for (int c = tid; c < nstrip * ww; c += kThreads) {
-      const int s = c / ww, j = c - s * ww;
+      int s;
+      if (ww == kWin) s = c / kWin;   // full tile: constant divisor
+      else s = c / ww;
+      const int j = c - s * ww;
       const float* src = sm.xb + (8 * s) * kWin + j;
       float v[8 + 2 * R];
 #pragma unroll
@@ -595,9 +607,9 @@ __device__ __forceinline__ void force_fold(ForceSmem<R>& sm, const TileBox& tb, 
   __syncthreads();
 }
 
-__device__ __forceinline__ TileBox tile_box(const WorldDev& w, int tile) {
+__device__ __forceinline__ TileBox tile_box(const WorldDev& w, int packed) {
   TileBox b;
-  const int tx = tile % w.ntx, ty = tile / w.ntx;
+  const int tx = packed & 0xffff, ty = packed >> 16;
   b.x0 = tx * kTile;
   b.y0 = ty * kTile;
   b.tw = min(kTile, w.W - b.x0);
@@ -616,7 +628,7 @@ __global__ void __launch_bounds__(kThreads) k_force_spread(const WorldDev* __res
   const TileBox tb = tile_box(w, it.y);
   float2* __restrict__ F_out = w.F;
   const int W = w.W;
-  const int k = force_tile<R>(sm, w, it.y, tb, store_fields, after_step);
+  const int k = force_tile<R>(sm, w, (tb.y0 / kTile) * w.ntx + tb.x0 / kTile, tb, store_fields, after_step);
   __syncthreads();
   force_fold(sm, tb, w.ntx, w.nty);
   const float inv = pow2f(-k);
@@ -650,14 +662,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_force_lbm(const WorldDev* __res
     // that the tile's cells pull from (plane i, rows y - c_iy) go to L2
     // while the force phase runs
     const int th = tb.th;
-    for (int c = threadIdx.x; c < 9 * th; c += kThreads) {
-      const int i = c / th, r = c - i * th;
+    for (int c = threadIdx.x; c < 9 * kTile; c += kThreads) {
+      const int i = c >> 5, r = c & (kTile - 1);
+      if (r >= th) continue;
       const int y = wrap_once(tb.y0 + r - kLbmCy[i], H);
       const float* a = src + (size_t)i * HW + (size_t)y * W + tb.x0;
       asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a));
     }
   }
-  const int k = force_tile<R>(sm, w, it.y, tb, 0, 0);
+  const int k = force_tile<R>(sm, w, (tb.y0 / kTile) * w.ntx + tb.x0 / kTile, tb, 0, 0);
   const float inv = pow2f(-k);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // each warp collides rows warp, warp + 8, ... of the tile; the populations

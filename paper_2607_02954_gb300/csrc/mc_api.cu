@@ -128,7 +128,8 @@ mc_status build_plan(mc_world* const* ws, int n, cudaStream_t s, Plan& out) {
     for (int f = 0; f < w->h.n_fil; ++f) fil.push_back(make_int2(k, f));
     const int nb = std::max(w->h.N, 1);
     for (int b = 0; b < nb; b += mc::kBeadChunk) bead.push_back(make_int2(k, b));
-    for (int t = 0; t < w->h.n_tiles; ++t) tile.push_back(make_int2(k, t));
+    for (int ty = 0; ty < w->h.nty; ++ty)   // tile items carry (tx, ty) packed: tx | ty << 16
+      for (int tx = 0; tx < w->h.ntx; ++tx) tile.push_back(make_int2(k, tx | (ty << 16)));
     for (int c = 0; c < w->h.n_chunks; ++c) scan.push_back(make_int2(k, c));
     const int HW = w->h.H * w->h.W;
     for (int c = 0; c < HW; c += mc::kCellChunk) cell.push_back(make_int2(k, c));

@@ -100,7 +100,7 @@ struct Plan {
   WorldDev* d_worlds = nullptr;  // [n_worlds]
   int2* d_fil_items = nullptr;   // (world, filament)
   int2* d_bead_items = nullptr;  // (world, first bead)
-  int2* d_tile_items = nullptr;  // (world, tile)
+  int2* d_tile_items = nullptr;  // (world, tx | ty << 16), row-major over the tiles
   int2* d_cell_items = nullptr;  // (world, first cell)
   int2* d_scan_items = nullptr;  // (world, scan chunk)
   void* d_mem = nullptr;
