@@ -241,6 +241,20 @@ mc_status mc_rollout_forward(mc_world* w, int n_steps, int ckpt_every, void* str
  * since, or when filaments are too long for the adjoint kernel. */
 mc_status mc_rollout_backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* dL_dtheta0, void* stream);
 
+/* As mc_rollout_backward, and also the gradients with respect to the
+ * physical parameters the paper's searches act on (Methods, Filaments:
+ * rest lengths and stiffnesses; the CPPN of the Neuroevolution experiment
+ * outputs L_rest):
+ *   dL_dL_rest [E] (device, may be NULL): with respect to each edge's rest
+ *              length;
+ *   dL_dk      [3] (device, may be NULL): with respect to k_bend,
+ *              k_stretch, k_shear of the world.
+ * The stiffness gradients are sums over all edges, joints, passes and steps
+ * taken with float atomics (not bitwise repeatable).  Errors as
+ * mc_rollout_backward. */
+mc_status mc_rollout_backward_params(mc_world* w, const float* dL_dx, const float* dL_dy, float* dL_dtheta0,
+                                     float* dL_dL_rest, float* dL_dk, void* stream);
+
 /* Folding loss with a polyline target (device arrays): loss[0] = mean over
  * beads of the squared distance from the unwrapped position to the nearest
  * segment of the polyline poly_xy [n_vertices][2]; dL_dx, dL_dy [N] its

@@ -25,6 +25,8 @@ One step n, from state (X^n, theta^n, f^n):
 from __future__ import annotations
 
 import math
+import copy
+import dataclasses
 from dataclasses import dataclass
 from typing import Dict, Optional
 
@@ -464,6 +466,27 @@ def folding_gradient(world: World, n_steps: int, poly):
     loss, _ = folding_loss(world, n_steps, poly, th0)
     (g,) = torch.autograd.grad(loss, th0)
     return float(loss.detach()), g
+
+
+def parameter_gradient(world: World, n_steps: int, gx: torch.Tensor, gy: torch.Tensor):
+    """Gradient of <g, X^0 + D^n> with respect to theta0, the rest lengths
+    L_rest and the PBD stiffnesses (k_bend, k_stretch, k_shear), by
+    reverse-mode automatic differentiation of the FP64 rollout with those
+    parameters as leaves (Methods, Filaments: the quantities the searches
+    and the folding optimisation act on)."""
+    th0 = world.theta0.clone().requires_grad_(True)
+    L = world.L_rest.clone().requires_grad_(True)
+    ks = [torch.tensor(v, dtype=F64, requires_grad=True)
+          for v in (world.c.k_bend, world.c.k_stretch, world.c.k_shear)]
+    w2 = copy.copy(world)
+    w2.L_rest = L
+    w2.c = dataclasses.replace(world.c, k_bend=ks[0], k_stretch=ks[1], k_shear=ks[2])
+    st = rollout(w2, n_steps, theta0=th0)
+    obj = (st.D[:, 0] * gx).sum() + (st.D[:, 1] * gy).sum()
+    g = torch.autograd.grad(obj, [th0, L] + ks, allow_unused=True)
+    z = lambda v, like: torch.zeros_like(like) if v is None else v
+    return {"theta0": z(g[0], th0), "L_rest": z(g[1], L),
+            "k": torch.stack([z(gi, k) for gi, k in zip(g[2:], ks)])}
 
 
 def final_position_gradient(world: World, n_steps: int, gx: torch.Tensor, gy: torch.Tensor):

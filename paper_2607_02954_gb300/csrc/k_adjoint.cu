@@ -295,9 +295,9 @@ __global__ void __launch_bounds__(256) k_adj_bead_b(const WorldDev* __restrict__
 
 // ---------------------------------------------------------------------------
 // a3 + a1 transposed, one warp per filament.  The forward Jacobi PBD is
-// recomputed from (X^n, theta^n) keeping, per iteration, the frames after the
-// bending pass and the corrections before the position pass; then the
-// iterations are reversed:
+// recomputed from (X^n, theta^n) keeping, per iteration, the frames before
+// and after the bending pass and the corrections before the position pass;
+// then the iterations are reversed:
 //   position pass (per edge, x = v0 + d_{e+1} - d_e, l = |x|, sc = 1 - L/l):
 //     D_e = hs [(1 - ksh) sc x + ksh (x - L d(theta))]
 //     theta_e += ko (cos y - sin x) / L
@@ -305,9 +305,13 @@ __global__ void __launch_bounds__(256) k_adj_bead_b(const WorldDev* __restrict__
 //   bending pass: C_j = theta_{j+1} - theta_j - theta_rest_j,
 //     theta_e += hb (C_e - C_{e-1})
 // Inputs: d_bar (from F_el), theta_bar of theta^{n+1}.  Outputs: X_bar +=
-// (through the edge vectors v0), theta_bar of theta^n, theta0_bar +=.
+// (through the edge vectors v0), theta_bar of theta^n, theta0_bar +=,
+// L_rest_bar += (per edge), and (k_bend, k_stretch, k_shear)_bar += (float
+// atomics, one per warp).
 // ---------------------------------------------------------------------------
-constexpr int kAdjPbdPerBead = 10;   // floats of working arrays per bead slot
+constexpr int kAdjPbdPerBead = 12;   // floats of working arrays per bead slot
+constexpr int kAdjTapePerPass = 4;   // per pass: theta before and after the bend pass, d (x, y)
+
 __global__ void __launch_bounds__(128) k_adj_pbd(const WorldDev* __restrict__ wd, AdjDev a,
                                                  const int2* __restrict__ items, int n_items, int maxB,
                                                  int n_pbd) {
@@ -322,7 +326,7 @@ __global__ void __launch_bounds__(128) k_adj_pbd(const WorldDev* __restrict__ wd
   const int B = w.fil_off[f + 1] - b0;
   const int nE = B - 1, nJ = B - 2;
   const int e0 = b0 - f, j0 = b0 - 2 * f;
-  const int per = maxB * (kAdjPbdPerBead + 3 * n_pbd + 2);
+  const int per = maxB * (kAdjPbdPerBead + kAdjTapePerPass * n_pbd + 2);
   float* s = smem + (size_t)warp * per;
   float* vx = s;
   float* vy = s + maxB;
@@ -334,7 +338,9 @@ __global__ void __launch_bounds__(128) k_adj_pbd(const WorldDev* __restrict__ wd
   float* Dx = s + 7 * maxB;     // per-edge D (x); reused for adjoint temporaries
   float* Dy = s + 8 * maxB;
   float* Cb = s + 9 * maxB;     // per-joint C / C_bar
-  float* tape = s + 10 * maxB;  // per iteration: theta after bend [maxB], d before pos [2 maxB]
+  float* thrb = s + 10 * maxB;  // adjoint of theta_rest
+  float* gLa = s + 11 * maxB;   // adjoint of L_rest, this step
+  float* tape = s + 12 * maxB;  // per pass: theta before bend, theta after bend, d (x), d (y)
   const int W = w.W, H = w.H;
   const long long t = *w.t;
   for (int e = lane; e < nE; e += 32) {
@@ -346,6 +352,7 @@ __global__ void __launch_bounds__(128) k_adj_pbd(const WorldDev* __restrict__ wd
     vy[e] = (float)dcy + (pb.y - pa.y);
     th[e] = a.theta_n[e0 + e];
     Lr[e] = w.L_rest[e0 + e];
+    gLa[e] = 0.0f;
   }
   for (int j = lane; j < nJ; j += 32) {
     const float4 d = w.drive[j0 + j];
@@ -355,6 +362,7 @@ __global__ void __launch_bounds__(128) k_adj_pbd(const WorldDev* __restrict__ wd
     float fr = (hi - rintf(hi)) + lo + d.w;
     fr -= rintf(fr);
     thr[j] = d.x + d.y * sinpif(2.0f * fr);
+    thrb[j] = 0.0f;
   }
   for (int i = lane; i < B; i += 32) {
     dx[i] = 0.0f;
@@ -362,9 +370,12 @@ __global__ void __launch_bounds__(128) k_adj_pbd(const WorldDev* __restrict__ wd
   }
   __syncwarp();
   const float hb = 0.5f * w.k_bend, hs = 0.5f * w.k_st, ksh = w.k_sh;
-  const float ko = w.orient * hs * ksh;
+  const float orient = w.orient;
+  const float ko = orient * hs * ksh;
   // ---- forward recompute with tape ----
   for (int it = 0; it < n_pbd; ++it) {
+    float* tp = tape + it * kAdjTapePerPass * maxB;
+    for (int e = lane; e < nE; e += 32) tp[e] = th[e];
     for (int j = lane; j < nJ; j += 32) Cb[j] = th[j + 1] - th[j] - thr[j];
     __syncwarp();
     for (int e = lane; e < nE; e += 32) {
@@ -372,11 +383,10 @@ __global__ void __launch_bounds__(128) k_adj_pbd(const WorldDev* __restrict__ wd
       th[e] += hb * (c1 - c0);
     }
     __syncwarp();
-    float* tp = tape + it * 3 * maxB;
-    for (int e = lane; e < nE; e += 32) tp[e] = th[e];
+    for (int e = lane; e < nE; e += 32) tp[maxB + e] = th[e];
     for (int i = lane; i < B; i += 32) {
-      tp[maxB + i] = dx[i];
-      tp[2 * maxB + i] = dy[i];
+      tp[2 * maxB + i] = dx[i];
+      tp[3 * maxB + i] = dy[i];
     }
     for (int e = lane; e < nE; e += 32) {
       const float x = vx[e] + (dx[e + 1] - dx[e]);
@@ -400,31 +410,31 @@ __global__ void __launch_bounds__(128) k_adj_pbd(const WorldDev* __restrict__ wd
     __syncwarp();
   }
   // ---- reverse ----
-  // adjoint state: d_bar in dx/dy, theta_bar in th, theta_rest_bar in thr
-  // (theta_rest is no longer needed), edge-vector adjoint v0_bar after the tape
+  // adjoint state: d_bar in dx/dy, theta_bar in th, edge-vector adjoint
+  // v0_bar after the tape; per-lane sums of the stiffness adjoints
   for (int i = lane; i < B; i += 32) {
     const float2 db = a.dbar[b0 + i];
     dx[i] = db.x;
     dy[i] = db.y;
   }
   for (int e = lane; e < nE; e += 32) th[e] = a.adjTh[e0 + e];
-  for (int j = lane; j < nJ; j += 32) thr[j] = 0.0f;
-  float* v0bx = tape + n_pbd * 3 * maxB;
+  float* v0bx = tape + n_pbd * kAdjTapePerPass * maxB;
   float* v0by = v0bx + maxB;
   for (int e = lane; e < nE; e += 32) {
     v0bx[e] = 0.0f;
     v0by[e] = 0.0f;
   }
+  float hbb = 0.0f, hsb = 0.0f, kshb = 0.0f;
   __syncwarp();
   for (int it = n_pbd - 1; it >= 0; --it) {
-    const float* tp = tape + it * 3 * maxB;
+    const float* tp = tape + it * kAdjTapePerPass * maxB;
     // position pass reverse: D_bar_e = d_bar_e - d_bar_{e+1}
     for (int e = lane; e < nE; e += 32) {
       const float Dbx = dx[e] - dx[e + 1], Dby = dy[e] - dy[e + 1];
-      const float thb = th[e];   // adjoint of theta after this pass
-      const float tb = tp[e];    // forward theta before this pass (after bend)
-      const float x = vx[e] + (tp[maxB + e + 1] - tp[maxB + e]);
-      const float y = vy[e] + (tp[2 * maxB + e + 1] - tp[2 * maxB + e]);
+      const float thb = th[e];          // adjoint of theta after this pass
+      const float tb = tp[maxB + e];    // forward theta before this pass (after bend)
+      const float x = vx[e] + (tp[2 * maxB + e + 1] - tp[2 * maxB + e]);
+      const float y = vy[e] + (tp[3 * maxB + e + 1] - tp[3 * maxB + e]);
       const float L = Lr[e];
       const float ell = sqrtf(x * x + y * y);
       const float sc = (ell - L) / ell;
@@ -437,9 +447,16 @@ __global__ void __launch_bounds__(128) k_adj_pbd(const WorldDev* __restrict__ wd
       float xby = hs * ((1.0f - ksh) * sc + ksh) * Dby + kq * y;
       float thb_new = thb + (-hs * ksh * L) * (-sn * Dbx + cs * Dby);
       // theta += ko (cs y - sn x) / L
+      const float turn = (cs * y - sn * x) / L;
       thb_new += thb * ko * (-sn * y - cs * x) / L;
       xbx += thb * ko * (-sn) / L;
       xby += thb * ko * cs / L;
+      // parameters: D = hs G, ko = orient hs ksh
+      const float rx = x - L * cs - sc * x, ry = y - L * sn - sc * y;
+      const float Gx = sc * x + ksh * rx, Gy = sc * y + ksh * ry;
+      hsb += Gx * Dbx + Gy * Dby + thb * orient * ksh * turn;
+      kshb += hs * (rx * Dbx + ry * Dby) + thb * orient * hs * turn;
+      gLa[e] += hs * (-(1.0f - ksh) * xd / ell - ksh * (cs * Dbx + sn * Dby)) - thb * ko * turn / L;
       Dx[e] = xbx;
       Dy[e] = xby;
       th[e] = thb_new;
@@ -455,20 +472,28 @@ __global__ void __launch_bounds__(128) k_adj_pbd(const WorldDev* __restrict__ wd
       dy[i] += by - ay;
     }
     __syncwarp();
-    // bending pass reverse: C_bar_j = hb (theta_bar_j - theta_bar_{j+1})
-    for (int j = lane; j < nJ; j += 32) Cb[j] = hb * (th[j] - th[j + 1]);
+    // bending pass reverse: C_bar_j = hb (theta_bar_j - theta_bar_{j+1});
+    // d theta_e / d hb = C_e - C_{e-1} with C from the angles before the pass
+    for (int j = lane; j < nJ; j += 32) {
+      const float dth = th[j] - th[j + 1];
+      hbb += (tp[j + 1] - tp[j] - thr[j]) * dth;
+      Cb[j] = hb * dth;
+    }
     __syncwarp();
     for (int e = lane; e < nE; e += 32) {
       const float in = e > 0 ? Cb[e - 1] : 0.0f;     // theta_e is theta_{j+1} of joint e-1
       const float out = e < nJ ? Cb[e] : 0.0f;       // ... and theta_j of joint e
       th[e] += in - out;
     }
-    for (int j = lane; j < nJ; j += 32) thr[j] -= Cb[j];
+    for (int j = lane; j < nJ; j += 32) thrb[j] -= Cb[j];
     __syncwarp();
   }
   // outputs
-  for (int e = lane; e < nE; e += 32) a.adjTh[e0 + e] = th[e];
-  for (int j = lane; j < nJ; j += 32) a.gth0[j0 + j] += thr[j];
+  for (int e = lane; e < nE; e += 32) {
+    a.adjTh[e0 + e] = th[e];
+    a.gL[e0 + e] += gLa[e];
+  }
+  for (int j = lane; j < nJ; j += 32) a.gth0[j0 + j] += thrb[j];
   for (int i = lane; i < B; i += 32) {
     const float ax = i < nE ? v0bx[i] : 0.0f, ay = i < nE ? v0by[i] : 0.0f;        // X_i is x_1 of edge i
     const float bx = i > 0 ? v0bx[i - 1] : 0.0f, by = i > 0 ? v0by[i - 1] : 0.0f;  // ... x_2 of edge i-1
@@ -477,10 +502,21 @@ __global__ void __launch_bounds__(128) k_adj_pbd(const WorldDev* __restrict__ wd
     xb.y += by - ay;
     a.adjX[b0 + i] = xb;
   }
+  // k_bend = 2 hb, k_stretch = 2 hs, k_shear = ksh
+  for (int o = 16; o > 0; o >>= 1) {
+    hbb += __shfl_xor_sync(0xffffffffu, hbb, o);
+    hsb += __shfl_xor_sync(0xffffffffu, hsb, o);
+    kshb += __shfl_xor_sync(0xffffffffu, kshb, o);
+  }
+  if (lane == 0) {
+    atomicAdd(&a.gk[0], 0.5f * hbb);
+    atomicAdd(&a.gk[1], 0.5f * hsb);
+    atomicAdd(&a.gk[2], kshb);
+  }
 }
 
 size_t adj_pbd_smem_per_warp(int maxB, int n_pbd) {
-  return (size_t)maxB * (kAdjPbdPerBead + 3 * n_pbd + 2) * sizeof(float);
+  return (size_t)maxB * (kAdjPbdPerBead + kAdjTapePerPass * n_pbd + 2) * sizeof(float);
 }
 
 // ---------------------------------------------------------------------------

@@ -111,7 +111,12 @@ mc_status mc_rollout_forward(mc_world* w, int n_steps, int ckpt_every, void* str
   return MC_OK;
 }
 
-mc_status mc_rollout_backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* dL_dtheta0, void* stream) {
+}  // extern "C"
+
+namespace {
+
+mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* dL_dtheta0, float* dL_dL_rest,
+                   float* dL_dk, void* stream) {
   if (!w) return afail(MC_ERR_INVALID_ARG, "world is NULL");
   if (!w->tape || w->tape_steps < 1) return afail(MC_ERR_INVALID_ARG, "no rollout recorded: call mc_rollout_forward first");
   if (w->t != w->tape_t0 + w->tape_steps)
@@ -136,6 +141,8 @@ mc_status mc_rollout_backward(mc_world* w, const float* dL_dx, const float* dL_d
   const size_t o_adjX = take(h.N * sizeof(float2));
   const size_t o_adjTh = take(h.E * sizeof(float));
   const size_t o_gth0 = take(h.J * sizeof(float));
+  const size_t o_gL = take(h.E * sizeof(float));
+  const size_t o_gk = take(3 * sizeof(float));
   const size_t o_g0 = take(9 * HW * sizeof(float));
   const size_t o_g1 = take(9 * HW * sizeof(float));
   const size_t o_ub = take(HW * sizeof(float2));
@@ -162,6 +169,8 @@ mc_status mc_rollout_backward(mc_world* w, const float* dL_dx, const float* dL_d
   a.adjX = reinterpret_cast<float2*>(A + o_adjX);
   a.adjTh = reinterpret_cast<float*>(A + o_adjTh);
   a.gth0 = reinterpret_cast<float*>(A + o_gth0);
+  a.gL = reinterpret_cast<float*>(A + o_gL);
+  a.gk = reinterpret_cast<float*>(A + o_gk);
   float* adjG[2] = {reinterpret_cast<float*>(A + o_g0), reinterpret_cast<float*>(A + o_g1)};
   a.ubar = reinterpret_cast<float2*>(A + o_ub);
   a.Fbar = reinterpret_cast<float2*>(A + o_Fb);
@@ -175,6 +184,8 @@ mc_status mc_rollout_backward(mc_world* w, const float* dL_dx, const float* dL_d
   if (h.N) k_interleave<<<(h.N + 255) / 256, 256, 0, s>>>(dL_dx, dL_dy, a.adjX, h.N);
   if (h.E) MC_ACUDA(cudaMemsetAsync(a.adjTh, 0, h.E * sizeof(float), s));
   if (h.J) MC_ACUDA(cudaMemsetAsync(a.gth0, 0, h.J * sizeof(float), s));
+  if (h.E) MC_ACUDA(cudaMemsetAsync(a.gL, 0, h.E * sizeof(float), s));
+  MC_ACUDA(cudaMemsetAsync(a.gk, 0, 3 * sizeof(float), s));
   MC_ACUDA(cudaMemsetAsync(adjG[0], 0, 9 * HW * sizeof(float), s));
   int cur = 0;   // adjG[cur] holds the adjoint of the populations after the step being reversed
   const int64_t t0 = w->tape_t0;
@@ -213,6 +224,9 @@ mc_status mc_rollout_backward(mc_world* w, const float* dL_dx, const float* dL_d
     MC_ACUDA(cudaGetLastError());
   }
   if (h.J) MC_ACUDA(cudaMemcpyAsync(dL_dtheta0, a.gth0, h.J * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if (dL_dL_rest && h.E)
+    MC_ACUDA(cudaMemcpyAsync(dL_dL_rest, a.gL, h.E * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if (dL_dk) MC_ACUDA(cudaMemcpyAsync(dL_dk, a.gk, 3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
   // back to the final state of the rollout
   const int64_t tf = t0 + n;
   mc_status st = load_state(h, (int)(tf & 1), tape + (size_t)n_ck * sl.bytes, sl, s);
@@ -223,6 +237,19 @@ mc_status mc_rollout_backward(mc_world* w, const float* dL_dx, const float* dL_d
   mc::launch_set_counter(h, tf, s);
   MC_ACUDA(cudaGetLastError());
   return MC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mc_status mc_rollout_backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* dL_dtheta0, void* stream) {
+  return backward(w, dL_dx, dL_dy, dL_dtheta0, nullptr, nullptr, stream);
+}
+
+mc_status mc_rollout_backward_params(mc_world* w, const float* dL_dx, const float* dL_dy, float* dL_dtheta0,
+                                     float* dL_dL_rest, float* dL_dk, void* stream) {
+  return backward(w, dL_dx, dL_dy, dL_dtheta0, dL_dL_rest, dL_dk, stream);
 }
 
 mc_status mc_loss_polyline(mc_world* w, const float* poly_xy, int n_vertices, float* loss, float* dL_dx, float* dL_dy,

@@ -78,6 +78,8 @@ struct AdjDev {
   float2* adjX;            // [N] adjoint of the bead positions
   float* adjTh;            // [E] adjoint of the edge angles
   float* gth0;             // [J] accumulated gradient with respect to theta0
+  float* gL;               // [E] accumulated gradient with respect to L_rest
+  float* gk;               // [3] accumulated gradient with respect to k_bend, k_stretch, k_shear
   const float* adjG_next;  // [9 H W] adjoint of the populations after the step
   float* adjG_cur;         // [9 H W] adjoint of the populations before it
   float2* ubar;            // [H W] adjoint of the fluid velocity

@@ -167,6 +167,23 @@ class World:
                                               ctypes.c_void_p(out.data_ptr() if out.numel() else 0), stream_handle(stream)))
         return out
 
+    def rollout_backward_params(self, dL_dx, dL_dy, stream=None):
+        """As rollout_backward, plus the rest-length and stiffness gradients:
+        returns {"theta0": [J], "L_rest": [E], "k": [3] (k_bend, k_stretch,
+        k_shear)} as torch CUDA tensors."""
+        torch = _torch()
+        gx = dL_dx.contiguous().float()
+        gy = dL_dy.contiguous().float()
+        s = self.spec
+        out = {"theta0": torch.empty(s.J, device="cuda", dtype=torch.float32),
+               "L_rest": torch.empty(s.E, device="cuda", dtype=torch.float32),
+               "k": torch.empty(3, device="cuda", dtype=torch.float32)}
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr() if t.numel() else 0)
+        L.check(self._lib.mc_rollout_backward_params(self.handle, ctypes.c_void_p(gx.data_ptr()),
+                                                     ctypes.c_void_p(gy.data_ptr()), ptr(out["theta0"]),
+                                                     ptr(out["L_rest"]), ptr(out["k"]), stream_handle(stream)))
+        return out
+
     def loss_polyline(self, poly, stream=None):
         """Folding loss against a polyline (numpy [V, 2]); returns (loss tensor [1], dL_dx, dL_dy)."""
         torch = _torch()

@@ -142,3 +142,34 @@ def test_rollout_fn_autograd_bridge():
     direct = w.rollout_backward(c[:, 0].contiguous(), c[:, 1].contiguous())
     assert torch.allclose(th0.grad, direct, rtol=1e-5, atol=1e-7)
     w.close()
+
+
+@pytest.mark.parametrize("case", ["tiny", "custom"])
+def test_rest_length_and_stiffness_gradients_match_oracle(case):
+    """mc_rollout_backward_params: gradients with respect to theta0, every
+    edge's rest length and (k_bend, k_stretch, k_shear) against the FP64
+    oracle's reverse mode, 1e-3 of each gradient's scale."""
+    from paper_2607_02954_gb300 import World
+    rng = np.random.default_rng(11)
+    if case == "tiny":
+        spec, n, K = synth.tiny_world(4, side=32, lengths=(9, 7, 6)), 25, 6
+    else:
+        spec, n, K = synth.world_random(12, 64, 5), 20, 7
+        spec.params = synth.Params(nu=0.3, kappa=0.2, k_bend=0.7, k_stretch=0.6, k_shear=0.5, k_rep=1.0,
+                                   sigma=0.8, orient=1.0, n_pbd=3)
+    gx = rng.standard_normal(spec.N)
+    gy = rng.standard_normal(spec.N)
+    w = World(spec)
+    w.rollout_forward(n, K)
+    g = w.rollout_backward_params(torch.as_tensor(gx, dtype=torch.float32).cuda(),
+                                  torch.as_tensor(gy, dtype=torch.float32).cuda())
+    w.close()
+    go = O.parameter_gradient(O.World(spec), n, torch.as_tensor(gx, dtype=torch.float64),
+                              torch.as_tensor(gy, dtype=torch.float64))
+    for key in ("theta0", "L_rest", "k"):
+        got = t2n(g[key]).astype(np.float64)
+        want = t2n(go[key])
+        scale = np.max(np.abs(want))
+        assert scale > 0, key
+        err = np.max(np.abs(got - want))
+        assert err <= RTOL * scale, (key, err, scale)
