@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define MC_ABI_VERSION 1
+#define MC_ABI_VERSION 2
 
 typedef enum mc_status {
   MC_OK = 0,
@@ -72,10 +72,16 @@ typedef enum mc_mem_kind { MC_MEM_HOST = 0, MC_MEM_DEVICE = 1 } mc_mem_kind;
  *   sigma    Gaussian filter width in cells, 0 < sigma <= 2 (taps R = ceil(4 sigma))
  *   orient   1: the position pass also turns the edge frame toward the edge
  *            (Gauss-Newton step on |v - L d(theta)|^2); 0: positions only
- *   n_pbd    PBD iterations per step, 0 <= n_pbd <= 64 */
+ *   n_pbd    PBD iterations per step, 0 <= n_pbd <= 64
+ *   pbd_order  0: Jacobi passes (every correction of a pass from the state
+ *            before it); 1: red-black passes (within each pass the joints or
+ *            edges of even index in their filament first, then the odd ones
+ *            from the updated state: a two-colour Gauss-Seidel sweep).  The
+ *            reverse mode supports order 0 only. */
 typedef struct mc_params {
   float nu, dt, Lambda, kappa, k_bend, k_stretch, k_shear, k_rep, sigma, orient;
   int n_pbd;
+  int pbd_order;
 } mc_params;
 
 /* The paper's statement of one world (Methods: filaments as graphs with

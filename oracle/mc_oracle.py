@@ -60,11 +60,13 @@ class Topology:
     edge_b: torch.Tensor   # [E] bead index of x_2
     joint_e1: torch.Tensor  # [J] edge index of theta_1
     joint_e2: torch.Tensor  # [J] edge index of theta_2
+    edge_color: torch.Tensor = None   # [E] parity of the edge's index within its filament
+    joint_color: torch.Tensor = None  # [J] parity of the joint's index within its filament
 
 
 def topology(fil_off) -> Topology:
     fil_off = [int(v) for v in fil_off]
-    ea, eb, j1, j2 = [], [], [], []
+    ea, eb, j1, j2, ec, jc = [], [], [], [], [], []
     e = 0
     for f in range(len(fil_off) - 1):
         b0, b1 = fil_off[f], fil_off[f + 1]
@@ -72,12 +74,14 @@ def topology(fil_off) -> Topology:
         for k in range(n_e):
             ea.append(b0 + k)
             eb.append(b0 + k + 1)
+            ec.append(k % 2)
         for k in range(n_e - 1):
             j1.append(e + k)
             j2.append(e + k + 1)
+            jc.append(k % 2)
         e += max(n_e, 0)
     as_t = lambda v: torch.tensor(v, dtype=torch.long)
-    return Topology(fil_off[-1], as_t(ea), as_t(eb), as_t(j1), as_t(j2))
+    return Topology(fil_off[-1], as_t(ea), as_t(eb), as_t(j1), as_t(j2), as_t(ec), as_t(jc))
 
 
 # ---------------------------------------------------------------------------
@@ -96,6 +100,7 @@ class Consts:
     sigma: float
     orient: float
     n_pbd: int
+    pbd_order: int = 0   # 0: Jacobi passes; 1: red-black (two-colour Gauss-Seidel) passes
 
     @property
     def tau_plus(self) -> float:
@@ -115,7 +120,7 @@ def consts(params) -> Consts:
     return Consts(nu=r(params.nu), dt=r(params.dt), Lambda=r(params.Lambda), kappa=r(params.kappa),
                   k_bend=r(params.k_bend), k_stretch=r(params.k_stretch), k_shear=r(params.k_shear),
                   k_rep=r(params.k_rep), sigma=r(params.sigma), orient=r(params.orient),
-                  n_pbd=int(params.n_pbd))
+                  n_pbd=int(params.n_pbd), pbd_order=int(getattr(params, "pbd_order", 0)))
 
 
 # ---------------------------------------------------------------------------
@@ -146,26 +151,32 @@ def wrap(X: torch.Tensor, period: float) -> torch.Tensor:
 # Eqs. 2-4), Jacobi form: every correction of one pass is computed from the
 # state before the pass and all are applied together.
 # ---------------------------------------------------------------------------
-def bend_pass(theta, theta_rest, topo: Topology, k_bend: float):
+def bend_pass(theta, theta_rest, topo: Topology, k_bend: float, color: Optional[int] = None):
     """Eq. 1: C = (theta_2 - theta_1) - theta_rest per joint;
-    theta_1 += k C / 2, theta_2 -= k C / 2."""
+    theta_1 += k C / 2, theta_2 -= k C / 2.  With color = 0 or 1 only the
+    joints of that index parity within their filament are corrected (they
+    share no edge)."""
     if topo.joint_e1.numel() == 0:
         return theta
     C = theta[topo.joint_e2] - theta[topo.joint_e1] - theta_rest
+    if color is not None:
+        C = torch.where(topo.joint_color == color, C, torch.zeros_like(C))
     dtheta = torch.zeros_like(theta)
     dtheta = dtheta.index_add(0, topo.joint_e1, 0.5 * k_bend * C)
     dtheta = dtheta.index_add(0, topo.joint_e2, -0.5 * k_bend * C)
     return theta + dtheta
 
 
-def position_pass(x, theta, L_rest, topo: Topology, c: Consts, H: int, W: int):
+def position_pass(x, theta, L_rest, topo: Topology, c: Consts, H: int, W: int, color: Optional[int] = None):
     """Eqs. 2-4 per edge with v = x_2 - x_1 (minimum image), d = (cos, sin)(theta):
         C_stretch = (|v| - L) v/|v|
         dx = k_stretch/2 [C_stretch + k_shear (v - L d - C_stretch)]
         x_1 += dx, x_2 -= dx.
     With orient = 1 the edge frame also turns toward v by the Gauss-Newton
     step of the Kirchhoff-Love error |v - L d(theta)|^2 scaled like Eq. 3:
-        theta += orient * k_stretch k_shear / 2 * (d_perp . v) / L."""
+        theta += orient * k_stretch k_shear / 2 * (d_perp . v) / L.
+    With color = 0 or 1 only the edges of that index parity within their
+    filament are corrected (they share no bead)."""
     if topo.edge_a.numel() == 0:
         return x, theta
     xa, xb = x[topo.edge_a], x[topo.edge_b]
@@ -179,19 +190,32 @@ def position_pass(x, theta, L_rest, topo: Topology, c: Consts, H: int, W: int):
     dy = 0.5 * c.k_stretch * (csy + c.k_shear * (vy - L_rest * dsin - csy))
     delta = torch.zeros_like(x)
     d = torch.stack([dx, dy], 1)
+    dtheta = c.orient * 0.5 * c.k_stretch * c.k_shear * (-dsin * vx + dcos * vy) / L_rest
+    if color is not None:
+        on = topo.edge_color == color
+        d = torch.where(on[:, None], d, torch.zeros_like(d))
+        dtheta = torch.where(on, dtheta, torch.zeros_like(dtheta))
     delta = delta.index_add(0, topo.edge_a, d)
     delta = delta.index_add(0, topo.edge_b, -d)
-    dtheta = c.orient * 0.5 * c.k_stretch * c.k_shear * (-dsin * vx + dcos * vy) / L_rest
     return x + delta, theta + dtheta
 
 
 def pbd(X, theta, theta_rest, L_rest, topo: Topology, c: Consts, H: int, W: int):
     """n_pbd iterations of (bending pass, position pass) from (X, theta)
-    (Methods: "Each iteration decouples the solver into two phases")."""
+    (Methods: "Each iteration decouples the solver into two phases").
+    pbd_order 0: Jacobi passes (every correction of a pass from the state
+    before it); 1: red-black passes (even-indexed joints or edges first, the
+    odd ones from the updated state: a two-colour Gauss-Seidel sweep)."""
     x, th = X, theta
     for _ in range(c.n_pbd):
-        th = bend_pass(th, theta_rest, topo, c.k_bend)
-        x, th = position_pass(x, th, L_rest, topo, c, H, W)
+        if c.pbd_order == 1:
+            th = bend_pass(th, theta_rest, topo, c.k_bend, color=0)
+            th = bend_pass(th, theta_rest, topo, c.k_bend, color=1)
+            x, th = position_pass(x, th, L_rest, topo, c, H, W, color=0)
+            x, th = position_pass(x, th, L_rest, topo, c, H, W, color=1)
+        else:
+            th = bend_pass(th, theta_rest, topo, c.k_bend)
+            x, th = position_pass(x, th, L_rest, topo, c, H, W)
     return x, th
 
 

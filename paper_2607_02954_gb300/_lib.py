@@ -30,7 +30,7 @@ class MCError(RuntimeError):
 class mc_params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_float) for n in
                 ("nu", "dt", "Lambda", "kappa", "k_bend", "k_stretch", "k_shear", "k_rep", "sigma", "orient")] + \
-               [("n_pbd", ctypes.c_int)]
+               [("n_pbd", ctypes.c_int), ("pbd_order", ctypes.c_int)]
 
 
 _fp = ctypes.POINTER(ctypes.c_float)
@@ -97,8 +97,12 @@ SIGNATURES = {
 _lib = None
 
 
+ABI_VERSION = 2   # MC_ABI_VERSION of include/mc.h that these structures mirror
+
+
 def load():
-    """Loads libmc.so once; raises if it is missing (build it with build())."""
+    """Loads libmc.so once; raises if it is missing (build it with build())
+    or was built from another version of the C ABI."""
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
@@ -108,6 +112,9 @@ def load():
             fn = getattr(lib, name)
             fn.restype = res
             fn.argtypes = args
+        if lib.mc_abi_version() != ABI_VERSION:
+            raise RuntimeError(f"libmc.so has C ABI version {lib.mc_abi_version()}, this binding expects "
+                               f"{ABI_VERSION}: rebuild it with paper_2607_02954_gb300.build.build()")
         _lib = lib
     return _lib
 

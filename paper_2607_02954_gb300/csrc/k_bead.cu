@@ -33,7 +33,7 @@ __device__ __forceinline__ float drive_angle(const float4 d, long long t) {
 // Constants of the PBD passes, read once per warp.
 struct PbdConst {
   float hb, hs, ksh, ko, kappa_dt;
-  int n_pbd, W, H, nbx;
+  int n_pbd, order, W, H, nbx;
 };
 
 __device__ __forceinline__ PbdConst pbd_const(const WorldDev& w) {
@@ -44,6 +44,7 @@ __device__ __forceinline__ PbdConst pbd_const(const WorldDev& w) {
   k.ko = w.orient * k.hs * k.ksh;
   k.kappa_dt = w.kappa_dt;
   k.n_pbd = w.n_pbd;
+  k.order = w.pbd_order;
   k.W = w.W;
   k.H = w.H;
   k.nbx = w.nbx;
@@ -117,7 +118,45 @@ __device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, 
   const float2 v0 = edge_vec(P0, P1, k.W, k.H);
   const float2 v1 = edge_vec(P1, Pn, k.W, k.H);
   float dlx0 = 0.0f, dly0 = 0.0f, dlx1 = 0.0f, dly1 = 0.0f;
-  for (int iter = 0; iter < k.n_pbd; ++iter) {
+  if (k.order == 1) {
+    for (int iter = 0; iter < k.n_pbd; ++iter) {
+      // bending pass (Eq. 1), joint 2l of every lane first, then joint 2l + 1
+      // from the updated angles: joint j moves theta_j by +h C_j and
+      // theta_{j+1} by -h C_j
+      const float C0 = hj0 ? th1 - th0 - thr0 : 0.0f;
+      if (hj0) {
+        th0 += k.hb * C0;
+        th1 -= k.hb * C0;
+      }
+      const float thn = __shfl_down_sync(kAll, th0, 1);   // theta_{2l+2}, updated
+      const float C1 = hj1 ? thn - th1 - thr1 : 0.0f;
+      if (hj1) th1 += k.hb * C1;
+      const float Cm = __shfl_up_sync(kAll, C1, 1);        // joint 2l-1 moves theta_{2l}
+      if (lane > 0) th0 -= k.hb * Cm;
+      // position pass (Eqs. 2-4), edge 2l first, then edge 2l + 1
+      float ddx0 = 0.0f, ddy0 = 0.0f;
+      if (he0) {
+        edge_correction(v0.x + (dlx1 - dlx0), v0.y + (dly1 - dly0), L0, th0, k, ddx0, ddy0);
+        dlx0 += ddx0;
+        dly0 += ddy0;
+        dlx1 -= ddx0;
+        dly1 -= ddy0;
+      }
+      const float dlxn = __shfl_down_sync(kAll, dlx0, 1), dlyn = __shfl_down_sync(kAll, dly0, 1);
+      float ddx1 = 0.0f, ddy1 = 0.0f;
+      if (he1) {
+        edge_correction(v1.x + (dlxn - dlx1), v1.y + (dlyn - dly1), L1, th1, k, ddx1, ddy1);
+        dlx1 += ddx1;
+        dly1 += ddy1;
+      }
+      const float ddxm = __shfl_up_sync(kAll, ddx1, 1), ddym = __shfl_up_sync(kAll, ddy1, 1);
+      if (lane > 0) {   // edge 2l-1 moves bead 2l (its second bead)
+        dlx0 -= ddxm;
+        dly0 -= ddym;
+      }
+    }
+  }
+  for (int iter = 0; iter < (k.order == 1 ? 0 : k.n_pbd); ++iter) {
     // bending pass (Eq. 1): C_j = (theta_{j+1} - theta_j) - theta_rest,j
     const float thn = __shfl_down_sync(kAll, th0, 1);
     const float C0 = hj0 ? th1 - th0 - thr0 : 0.0f;
@@ -188,7 +227,33 @@ __device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, 
     dly[i] = 0.0f;
   }
   __syncwarp();
-  for (int iter = 0; iter < k.n_pbd; ++iter) {
+  if (k.order == 1) {
+    // red-black passes: within a colour no two joints share an edge and no
+    // two edges share a bead, so the lanes update in place
+    for (int iter = 0; iter < k.n_pbd; ++iter) {
+      for (int c = 0; c < 2; ++c) {
+        for (int j = 2 * lane + c; j < nJ; j += 64) {
+          const float Cj = th[j + 1] - th[j] - thr[j];
+          th[j] += k.hb * Cj;
+          th[j + 1] -= k.hb * Cj;
+        }
+        __syncwarp();
+      }
+      for (int c = 0; c < 2; ++c) {
+        for (int e = 2 * lane + c; e < nE; e += 64) {
+          float the = th[e], ddxe, ddye;
+          edge_correction(vx[e] + (dlx[e + 1] - dlx[e]), vy[e] + (dly[e + 1] - dly[e]), Lr[e], the, k, ddxe, ddye);
+          th[e] = the;
+          dlx[e] += ddxe;
+          dly[e] += ddye;
+          dlx[e + 1] -= ddxe;
+          dly[e + 1] -= ddye;
+        }
+        __syncwarp();
+      }
+    }
+  }
+  for (int iter = 0; iter < (k.order == 1 ? 0 : k.n_pbd); ++iter) {
     for (int j = lane; j < nJ; j += 32) C[j] = th[j + 1] - th[j] - thr[j];
     __syncwarp();
     for (int e = lane; e < nE; e += 32) {

@@ -78,6 +78,7 @@ mc_status validate_params(const mc_params& p) {
   if (!(p.dt > 0.0f)) return fail(MC_ERR_INVALID_ARG, "dt must be > 0");
   if (!(p.sigma > 0.0f && p.sigma <= 2.0f)) return fail(MC_ERR_INVALID_ARG, "sigma must be in (0, 2]");
   if (p.n_pbd < 0 || p.n_pbd > mc::kMaxNpbd) return fail(MC_ERR_INVALID_ARG, "n_pbd must be in [0, 64]");
+  if (p.pbd_order != 0 && p.pbd_order != 1) return fail(MC_ERR_INVALID_ARG, "pbd_order must be 0 or 1");
   return MC_OK;
 }
 
@@ -92,6 +93,7 @@ void fill_constants(WorldDev& h, const mc_params& p) {
   h.k_rep = p.k_rep;
   h.orient = p.orient;
   h.n_pbd = p.n_pbd;
+  h.pbd_order = p.pbd_order;
   h.om_p = (float)(1.0 / tau_p);
   h.om_m = (float)(1.0 / tau_m);
   h.src_p = (float)(1.0 - 0.5 / tau_p);
@@ -335,6 +337,7 @@ mc_status mc_params_default(mc_params* p) {
   p->sigma = 1.0f;
   p->orient = 1.0f;
   p->n_pbd = 4;
+  p->pbd_order = 0;
   return MC_OK;
 }
 

@@ -38,7 +38,7 @@ struct WorldDev {
   int nbx, nby, n_bins;             // 8x8 bins
   int ntx, nty, n_tiles;            // 32x32 tiles
   int n_chunks;                     // scan blocks over the bins
-  int R, n_pbd;
+  int R, n_pbd, pbd_order;
   float dt, kappa_dt, k_bend, k_st, k_sh, k_rep, orient;
   float om_p, om_m, src_p, src_m;   // 1/tau+-, 1 - 1/(2 tau+-)
   float u_max;                      // watchdog threshold on |U|

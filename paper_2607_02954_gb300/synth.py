@@ -45,6 +45,7 @@ class Params:
             vector (Gauss-Newton step on the Kirchhoff-Love error), 0 = the
             literal reading where only positions move.
     n_pbd: PBD iterations (bend pass + position pass) per time step.
+    pbd_order: 0 Jacobi passes, 1 red-black (two-colour Gauss-Seidel) passes.
     """
 
     nu: float = 0.1
@@ -58,6 +59,7 @@ class Params:
     sigma: float = 1.0
     orient: float = 1.0
     n_pbd: int = 4
+    pbd_order: int = 0
 
 
 @dataclasses.dataclass

@@ -30,7 +30,8 @@ def stream_handle(stream=None) -> ctypes.c_void_p:
 def params_struct(p: Params) -> L.mc_params:
     return L.mc_params(nu=p.nu, dt=p.dt, Lambda=p.Lambda, kappa=p.kappa, k_bend=p.k_bend,
                        k_stretch=p.k_stretch, k_shear=p.k_shear, k_rep=p.k_rep, sigma=p.sigma,
-                       orient=p.orient, n_pbd=int(p.n_pbd))
+                       orient=p.orient, n_pbd=int(p.n_pbd),
+                       pbd_order=int(getattr(p, "pbd_order", 0)))
 
 
 def default_params() -> Params:

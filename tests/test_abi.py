@@ -62,7 +62,7 @@ def _desc(spec, **over):
 
 
 @pytest.mark.parametrize("case", ["H_not_mult8", "W_small", "short_filament", "nan_x", "bad_nu",
-                                  "bad_sigma", "neg_L", "bad_t0", "bad_npbd"])
+                                  "bad_sigma", "neg_L", "bad_t0", "bad_npbd", "bad_pbd_order"])
 def test_create_rejects_invalid_worlds_on_host(case):
     spec = synth.tiny_world(0, side=16, lengths=(5, 4))
     over = {}
@@ -86,6 +86,8 @@ def test_create_rejects_invalid_worlds_on_host(case):
         over["t0"] = 1 << 24
     elif case == "bad_npbd":
         over["params"] = synth.Params(n_pbd=65)
+    elif case == "bad_pbd_order":
+        over["params"] = synth.Params(pbd_order=2)
     d, keep = _desc(spec, **over)
     h = ctypes.c_void_p()
     lib = L.load()

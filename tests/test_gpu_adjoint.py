@@ -173,3 +173,16 @@ def test_rest_length_and_stiffness_gradients_match_oracle(case):
         assert scale > 0, key
         err = np.max(np.abs(got - want))
         assert err <= RTOL * scale, (key, err, scale)
+
+
+def test_reverse_mode_rejects_red_black_pbd():
+    from paper_2607_02954_gb300 import World
+    from paper_2607_02954_gb300._lib import MCError
+    spec = synth.tiny_world(7, side=32, lengths=(8, 6))
+    spec.params = synth.Params(pbd_order=1)
+    w = World(spec)
+    w.rollout_forward(5, 2)
+    with pytest.raises(MCError) as ei:
+        w.rollout_backward(torch.zeros(spec.N, device="cuda"), torch.zeros(spec.N, device="cuda"))
+    assert ei.value.status == 1
+    w.close()

@@ -119,7 +119,7 @@ def test_one_step_random_fluid_and_late_drive():
 
 
 @pytest.mark.parametrize("case", ["tiny8", "ragged", "single_dimer", "no_filaments", "long_filament",
-                                  "custom_params", "dense_rows"])
+                                  "custom_params", "dense_rows", "red_black", "red_black_long"])
 def test_one_step_edge_cases(case):
     rng = np.random.default_rng(1)
     if case == "tiny8":
@@ -135,6 +135,12 @@ def test_one_step_edge_cases(case):
         spec.f0 = synth.random_populations(rng, 24, 16, 1e-3)
     elif case == "long_filament":
         spec = synth.world_random(11, 256, 2, lengths=[1500, 40])
+    elif case == "red_black":
+        spec = synth.world_random(13, 128, 24)
+        spec.params = synth.Params(k_bend=0.8, k_stretch=0.7, k_shear=0.5, pbd_order=1, n_pbd=5)
+    elif case == "red_black_long":
+        spec = synth.world_random(14, 256, 3, lengths=[700, 65, 33])
+        spec.params = synth.Params(pbd_order=1)
     elif case == "custom_params":
         spec = synth.world_c1(2)
         spec.params = synth.Params(nu=0.5, Lambda=3.0 / 16.0, kappa=0.2, k_bend=0.8, k_stretch=0.9,
@@ -247,6 +253,7 @@ def test_batched_equals_alone_bitwise():
     from paper_2607_02954_gb300 import step_batched
     specs = [synth.world_random(s, side, nf) for s, side, nf in
              [(1, 64, 3), (2, 128, 17), (3, 64, 1), (4, 256, 40), (5, 128, 8)]]
+    specs[2].params = synth.Params(pbd_order=1, sigma=0.6)   # a red-black world with a narrower filter
     alone = []
     for sp in specs:
         w = _gpu_world(sp)

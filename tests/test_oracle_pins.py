@@ -14,6 +14,7 @@ import torch
 
 import oracle as O
 from paper_2607_02954_gb300 import synth
+from tests.helpers import t2n
 
 F64 = torch.float64
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -594,6 +595,67 @@ def test_T10_oracle_gradient_matches_finite_differences():
         fd = float(lp - lm) / (2 * eps)
         ad = float((g * d).sum())
         assert abs(fd - ad) <= 1e-6 * max(abs(ad), 1e-8) + 1e-11, (k, fd, ad)
+
+
+# ---------------------------------------------------------------------------
+# Red-black (two-colour Gauss-Seidel) PBD ordering: closed forms.
+# ---------------------------------------------------------------------------
+def test_red_black_bend_pass_closed_form():
+    """Three edges at (0, a, 0), rest angles 0, h = k_bend/2.  Joint 0 first:
+    theta_0 = h a, theta_1 = a (1 - h); then joint 1 from the updated theta_1:
+    C_1 = -a (1 - h), theta_1 = a (1 - h)^2, theta_2 = h a (1 - h).  (Jacobi
+    gives (h a, a (1 - 2h), h a).)"""
+    topo = O.topology([0, 4])
+    a, k = 0.3, 0.6
+    h = k / 2
+    th = torch.tensor([0.0, a, 0.0], dtype=F64)
+    tr = torch.zeros(2, dtype=F64)
+    th = O.bend_pass(th, tr, topo, k, color=0)
+    th = O.bend_pass(th, tr, topo, k, color=1)
+    want = [h * a, a * (1 - h) ** 2, h * a * (1 - h)]
+    assert np.allclose(t2n(th), want, rtol=0, atol=1e-15)
+    jac = O.bend_pass(torch.tensor([0.0, a, 0.0], dtype=F64), tr, topo, k)
+    assert np.allclose(t2n(jac), [h * a, a * (1 - 2 * h), h * a], rtol=0, atol=1e-15)
+
+
+def test_red_black_position_pass_closed_form():
+    """Beads at x = 0, 2, 4 on a line, L = 1, k_stretch = 1, no shear or
+    turning.  Edge 0 first: correction (2 - 1)/2 moves beads 0, 1 to 0.5, 1.5;
+    edge 1 then sees |v| = 2.5 and moves beads 1, 2 by 0.75: (0.5, 2.25, 3.25).
+    Jacobi moves both edges from the start: (0.5, 2, 3.5)."""
+    c = _consts(k_stretch=1.0, k_shear=0.0, orient=0.0)
+    topo, X = _chain([0.0, 2.0, 4.0], [5.0, 5.0, 5.0])
+    th = torch.zeros(2, dtype=F64)
+    L = torch.ones(2, dtype=F64)
+    x, _ = O.position_pass(X, th, L, topo, c, 32, 32, color=0)
+    x, _ = O.position_pass(x, th, L, topo, c, 32, 32, color=1)
+    assert np.allclose(t2n(x[:, 0]), [0.5, 2.25, 3.25], rtol=0, atol=1e-15)
+    xj, _ = O.position_pass(X, th, L, topo, c, 32, 32)
+    assert np.allclose(t2n(xj[:, 0]), [0.5, 2.0, 3.5], rtol=0, atol=1e-15)
+
+
+def test_red_black_colours_are_local_to_each_filament():
+    """Colours follow the index within the filament: a second filament's first
+    joint and edge are colour 0 whatever the first filament's length."""
+    topo = O.topology([0, 4, 9])   # 3 + 4 edges, 2 + 3 joints
+    assert t2n(topo.edge_color).tolist() == [0, 1, 0, 0, 1, 0, 1]
+    assert t2n(topo.joint_color).tolist() == [0, 1, 0, 1, 0]
+
+
+def test_red_black_rest_state_is_a_fixed_point():
+    """T1 for the red-black order: a straight filament at its rest shape with
+    no drive stays where it is, bitwise."""
+    spec = synth.tiny_world(0, side=32, lengths=(12,))
+    spec.theta = np.zeros(spec.E, np.float32)
+    spec.x = (5.0 + np.arange(12)).astype(np.float32)
+    spec.y = np.full(12, 7.0, np.float32)
+    spec.theta0 = np.zeros(spec.J, np.float32)
+    spec.drive_amp = np.zeros(spec.J, np.float32)
+    spec.params = synth.Params(k_rep=0.0, pbd_order=1)
+    w = O.World(spec)
+    st = w.initial_state()
+    x_hat, th = O.pbd(st.X, st.theta, torch.zeros(spec.J, dtype=F64), w.L_rest, w.topo, w.c, 32, 32)
+    assert torch.equal(x_hat, st.X) and torch.equal(th, st.theta)
 
 
 def _objective(w, n_steps, gx, gy, L_rest=None, ks=None):
