@@ -73,8 +73,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--workload", default="c3_22",
-                    help="c3_<log2 N> (default c3_22), c2, c4 (1024 worlds: batched vs per-world launches) "
-                         "or served (C4 worlds as Poisson-arriving 500-step rollouts)")
+                    help="c3_<log2 N> (default c3_22), c2, c4 (1024 worlds: batched vs per-world launches), "
+                         "served (C4 worlds as Poisson-arriving 500-step rollouts) or c5 (folding gradient: "
+                         "2000-step checkpointed rollout + loss + reverse sweep)")
+    ap.add_argument("--pbd-order", type=int, default=0, choices=[0, 1],
+                    help="PBD pass order of the stepped world: 0 Jacobi, 1 red-black")
     ap.add_argument("--arrival-rate", type=float, default=2000.0, help="served: requests per second")
     ap.add_argument("--duration", type=float, default=2.0, help="served: seconds of arrivals")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -83,7 +86,15 @@ def parse():
     return ap.parse_args()
 
 
-def make_spec(name: str, seed: int):
+def make_spec(name: str, seed: int, pbd_order: int = 0):
+    spec, desc = _make_spec(name, seed)
+    if pbd_order:
+        spec.params.pbd_order = pbd_order
+        desc += ", red-black PBD passes"
+    return spec, desc
+
+
+def _make_spec(name: str, seed: int):
     from paper_2607_02954_gb300 import synth
     if name == "c2":
         return synth.world_c2(seed), "c2: 512^2 grid, 4096 x 64 beads (262,144), FP32"
@@ -282,8 +293,75 @@ def bench_batched(args):
             "config": {"workload": "c4", "worlds": len(specs), "beads": n_beads, "cells": n_cells,
                        "description": "1024 worlds, side ~U{64,128,256}, 1-64 filaments x 8-64 beads (log-uniform)"},
             "plain_per_world": {"value": plain, "ms_per_step": ms_plain / plain_steps,
-                                "launches_per_step": len(worlds) * 8},
-            "batched_over_plain": batched / plain, "gpu_launches": args.steps * 8, "clocks": clk.summary()}
+                                "launches_per_step": len(worlds) * KERNELS_PER_STEP},
+            "batched_over_plain": batched / plain, "gpu_launches": args.steps * KERNELS_PER_STEP,
+            "clocks": clk.summary()}
+
+
+def bench_gradient(args):
+    """Folding gradient (reverse mode, the Filament Folding experiment's
+    loop): a 2000-step rollout of the folding world (256^2 grid, 64 x 48
+    beads) recorded with checkpoints every 100 steps, the polyline loss, and
+    the reverse sweep with the gradients with respect to theta0, L_rest and
+    the three stiffnesses.  value = forward particle-steps per second of the
+    whole gradient (forward + loss + backward)."""
+    import numpy as np
+    import torch
+    from paper_2607_02954_gb300 import World, synth
+    spec, poly = synth.world_c5(0)
+    n, K = 2000, 100
+    reps = max(1, min(args.steps, 5))
+    w = World(spec)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(1, min(args.warmup, 2))):
+        w.rollout_forward(50, 10)
+        loss, gx, gy = w.loss_polyline(poly)
+        w.rollout_backward_params(gx, gy)
+    torch.cuda.synchronize()
+    fwd, bwd = [], []
+    with ClockSampler(0) as clk:
+        for _ in range(reps):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            w.rollout_forward(n, K)
+            e[1].record(stream)
+            loss, gx, gy = w.loss_polyline(poly)
+            g = w.rollout_backward_params(gx, gy)
+            e[2].record(stream)
+            torch.cuda.synchronize()
+            fwd.append(e[0].elapsed_time(e[1]))
+            bwd.append(e[1].elapsed_time(e[2]))
+    w.check()
+    grad_norm = float(torch.linalg.vector_norm(g["theta0"]).item())
+    w.close()
+    ms_f, ms_b = statistics.median(fwd), statistics.median(bwd)
+    value = spec.N * n / ((ms_f + ms_b) * 1e-3)
+    line = {"metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": 1,
+            "steps": n, "warmup": 1, "ms_per_step": (ms_f + ms_b) / n, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "c5", "grid": [spec.H, spec.W], "beads": spec.N, "filaments": spec.n_fil,
+                       "rollout_steps": n, "ckpt_every": K, "repetitions": reps,
+                       "description": "folding gradient: checkpointed forward + polyline loss + reverse sweep "
+                                      "(theta0, L_rest, k_bend, k_stretch, k_shear)"},
+            "forward_ms": ms_f, "backward_ms": ms_b, "backward_over_forward": ms_b / ms_f,
+            "grad_norm_theta0": grad_norm, "clocks": clk.summary()}
+    if not args.no_cpu_baseline:
+        import oracle as O
+        t0 = time.perf_counter()
+        m = 200
+        ow = O.World(spec)
+        gxt = torch.as_tensor(t2n_host(gx), dtype=torch.float64)
+        gyt = torch.as_tensor(t2n_host(gy), dtype=torch.float64)
+        O.parameter_gradient(ow, m, gxt, gyt)
+        el = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": spec.N * m / el, "unit": "particle-steps/s", "cores": torch.get_num_threads(),
+                                "kind": "oracle", "sample": f"FP64 oracle reverse mode over {m} steps of the same world "
+                                                            f"({el:.1f} s)"}
+    return line
+
+
+def t2n_host(t):
+    return t.detach().cpu().numpy()
 
 
 def bench_served(args):
@@ -333,14 +411,19 @@ def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
-    if args.workload in ("c4", "served"):
+    if args.workload in ("c4", "served", "c5"):
         import torch
         torch.cuda.set_device(0)
         from paper_2607_02954_gb300 import _lib
         if not os.path.exists(_lib.LIB_PATH):
             from paper_2607_02954_gb300.build import build
             build()
-        line = bench_batched(args) if args.workload == "c4" else bench_served(args)
+        if args.workload == "c4":
+            line = bench_batched(args)
+        elif args.workload == "c5":
+            line = bench_gradient(args)
+        else:
+            line = bench_served(args)
         print(json.dumps(line), flush=True)
         return 0
     import numpy as np
@@ -359,7 +442,7 @@ def main():
         build()
     lib = _lib.load()
 
-    spec, desc = make_spec(args.workload, seed=rank)
+    spec, desc = make_spec(args.workload, seed=rank, pbd_order=args.pbd_order)
     N, C = spec.N, spec.H * spec.W
     world = World(spec, device=True)
     stream = torch.cuda.current_stream()
