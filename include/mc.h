@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define MC_ABI_VERSION 2
+#define MC_ABI_VERSION 3
 
 typedef enum mc_status {
   MC_OK = 0,
@@ -99,7 +99,16 @@ typedef struct mc_params {
  *               fluid at rest (f = w_i)
  *   t0          initial step counter (0 <= t0 < 2^24)
  *   p           constants
- *   mem_kind    where the array pointers live (fil_off always host memory) */
+ *   mem_kind    where the array pointers live (fil_off always host memory)
+ * Optional, NULL = absent (the Neuroevolution and QD Search experiments):
+ *   len_amp, len_freq, len_phase  [E] rest-length drive, all three or none:
+ *               L_rest(t) = L_rest (1 + len_amp sin(2 pi (len_freq t +
+ *               len_phase))), the controller's rest-length output; |len_amp| < 1
+ *   energy      [H][W] persistent scalar energy field (Gaussian packets in the
+ *               paper), sampled at every bead each step with the
+ *               interpolation kernel
+ *   observe     1: accumulate the behaviour descriptors and the collected
+ *               energy every step (see mc_world_get_observables); 0: off */
 typedef struct mc_world_desc {
   int H, W;
   int n_fil;
@@ -116,6 +125,11 @@ typedef struct mc_world_desc {
   int64_t t0;
   mc_params p;
   int mem_kind;
+  const float* len_amp;
+  const float* len_freq;
+  const float* len_phase;
+  const float* energy;
+  int observe;
 } mc_world_desc;
 
 typedef struct mc_world mc_world;
@@ -211,7 +225,8 @@ typedef enum mc_field {
   MC_FIELD_CELL = 7,     /* [N] int32 cell index (floor(y) mod H) W + (floor(x) mod W) (a2) */
   MC_FIELD_BIN = 8,      /* [N] int32 bin index (floor(y)/8) (W/8) + floor(x)/8 of each bead (a2) */
   MC_FIELD_BIN_OFF = 9,  /* [n_bins + 1] int32 exclusive prefix sum of beads per bin (a2) */
-  MC_FIELD_BIN_BEADS = 10 /* [N] int32 bead ids in bin order (order inside a bin unspecified) */
+  MC_FIELD_BIN_BEADS = 10, /* [N] int32 bead ids in bin order (order inside a bin unspecified) */
+  MC_FIELD_EBEAD = 11    /* [N] energy sampled at each bead in the last step (observe and energy set) */
 } mc_field;
 
 /* Copies one field (see mc_field for its size and type) into `out`. */
@@ -222,6 +237,21 @@ mc_status mc_world_get_field(const mc_world* w, int field, void* out, int mem_ki
  * (the flag stays set until mc_world_clear_flags). */
 mc_status mc_world_check(const mc_world* w, void* stream);
 mc_status mc_world_clear_flags(mc_world* w, void* stream);
+
+/* Search-side observables accumulated since creation (worlds created with
+ * observe = 1; zeros otherwise), QD Search and Neuroevolution experiments:
+ *   out[0] E_bend = sum over steps t >= 1 and joints of (theta_rest(t-1) -
+ *          theta_rest(t))^2  (Eq. 5)
+ *   out[1] E_pos  = sum over steps t >= 1 and edges of (L_rest(t-1) -
+ *          L_rest(t))^2  (Eq. 6; zero without a rest-length drive)
+ *   out[2] energy collected = sum over steps and beads of the energy field
+ *          at the bead's position at the start of the step
+ * t is the world's step counter when the step starts.  The sums are kept in
+ * 64-bit fixed point: each warp's per-step partial sum (32 beads, or one
+ * filament's joints and edges) is rounded to 2^-24, so the totals are
+ * bitwise the same alone, batched or served, and exact while below 5.5e11.
+ * out: 3 host doubles; the call synchronizes `stream`. */
+mc_status mc_world_get_observables(const mc_world* w, double* out, void* stream);
 
 /* ---- Reverse mode ----------------------------------------------------------
  * The Filament Folding experiment (Experiments section) optimises rest
@@ -290,6 +320,8 @@ typedef struct mc_server_cfg {
 
 typedef struct mc_result {
   double com_disp[2];       /* mean unwrapped bead displacement after n_steps */
+  double e_bend, e_pos;     /* behaviour descriptors over the rollout (Eqs. 5, 6; observe set) */
+  double energy;            /* energy collected over the rollout (observe and energy set) */
   int status;               /* MC_OK, MC_ERR_UNSTABLE, or the world's creation error */
   int n_steps;
   int64_t t_submit_ns;      /* steady-clock times of submit, admission, completion */

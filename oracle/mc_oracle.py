@@ -388,7 +388,22 @@ class World:
         self.amp = as64(spec.drive_amp)
         self.freq = as64(spec.drive_freq)
         self.phase = as64(spec.drive_phase)
+        # optional: rest-length drive [E] and energy field [H, W] (search experiments)
+        la = getattr(spec, "len_amp", None)
+        self.len_amp = None if la is None else as64(la)
+        self.len_freq = None if la is None else as64(spec.len_freq)
+        self.len_phase = None if la is None else as64(spec.len_phase)
+        en = getattr(spec, "energy", None)
+        self.energy = None if en is None else as64(en)
         self.spec = spec
+
+    def rest_lengths(self, n: int, L0: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """L_rest(n) = L0 (1 + A sin(2 pi (freq n + phase))) with a rest-length
+        drive (the controller's rest-length output), else L0."""
+        L0 = self.L_rest if L0 is None else L0
+        if self.len_amp is None:
+            return L0
+        return L0 * (1.0 + self.len_amp * torch.sin(2.0 * math.pi * (self.len_freq * float(n) + self.len_phase)))
 
     def initial_state(self) -> State:
         s = self.spec
@@ -408,7 +423,8 @@ def step(world: World, st: State, theta0: Optional[torch.Tensor] = None, record:
     c, H, W, topo = world.c, world.H, world.W, world.topo
     th0 = world.theta0 if theta0 is None else theta0
     theta_rest = rest_angles(th0, world.amp, world.freq, world.phase, st.t)          # a1
-    x_hat, theta_hat = pbd(st.X, st.theta, theta_rest, world.L_rest, topo, c, H, W)   # a3
+    L_rest = world.rest_lengths(st.t)
+    x_hat, theta_hat = pbd(st.X, st.theta, theta_rest, L_rest, topo, c, H, W)         # a3
     F_el = c.kappa * (x_hat - st.X) / c.dt
     idx, w = stencil(st.X, H, W)
     rho_s = spread(idx, w, torch.ones(st.X.shape[0], dtype=F64), H, W)                # a4
@@ -424,7 +440,42 @@ def step(world: World, st: State, theta0: Optional[torch.Tensor] = None, record:
     if record:
         rec = dict(theta_rest=theta_rest, x_hat=x_hat, F_el=F_el, rho_s=rho_s, rho_bar=rho_bar,
                    F_s=F_s, F=F, u=u, U=U)
+        rec.update(step_observables(world, st, idx, w, theta_rest, L_rest))
     return new, rec
+
+
+def step_observables(world: World, st: State, idx, w, theta_rest, L_rest) -> Dict[str, torch.Tensor]:
+    """What one step adds to the search observables (QD Search: Eqs. 5, 6;
+    Neuroevolution: energy sampled at the nodes):
+      e_bend = sum_j (theta_rest(t-1) - theta_rest(t))^2,
+      e_pos  = sum_e (L_rest(t-1) - L_rest(t))^2   (both 0 at t = 0),
+      e_bead = energy field at each bead (start of step, interpolation kernel),
+      energy = sum of e_bead."""
+    t = st.t
+    zero = torch.zeros((), dtype=F64)
+    if t >= 1:
+        prev = rest_angles(world.theta0, world.amp, world.freq, world.phase, t - 1)
+        e_bend = ((prev - theta_rest) ** 2).sum()
+        e_pos = ((world.rest_lengths(t - 1) - L_rest) ** 2).sum()
+    else:
+        e_bend, e_pos = zero, zero
+    if world.energy is not None:
+        e_bead = interpolate(idx, w, world.energy)
+        energy = e_bead.sum()
+    else:
+        e_bead, energy = None, zero
+    return dict(e_bend=e_bend, e_pos=e_pos, e_bead=e_bead, energy=energy)
+
+
+def observables(world: World, n_steps: int) -> Dict[str, float]:
+    """E_bend, E_pos and the energy collected over n_steps from the initial state."""
+    st = world.initial_state()
+    tot = {"e_bend": 0.0, "e_pos": 0.0, "energy": 0.0}
+    for _ in range(n_steps):
+        st, rec = step(world, st, record=True)
+        for k in tot:
+            tot[k] += float(rec[k])
+    return tot
 
 
 def rollout(world: World, n_steps: int, st: Optional[State] = None, theta0=None) -> State:

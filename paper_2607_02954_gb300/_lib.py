@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "MC_OK", 1: "MC_ERR_INVALID_ARG", 2: "MC_ERR_OOM", 3: "MC_ERR
                 4: "MC_ERR_TIMEOUT", 5: "MC_ERR_UNSTABLE", 6: "MC_ERR_BUSY", 7: "MC_ERR_NOT_FOUND"}
 
 FIELDS = {"fel": 0, "fs": 1, "ubead": 2, "rho_s": 3, "rho_bar": 4, "force": 5, "u": 6,
-          "cell": 7, "bin": 8, "bin_off": 9, "bin_beads": 10}
+          "cell": 7, "bin": 8, "bin_off": 9, "bin_beads": 10, "ebead": 11}
 
 
 class MCError(RuntimeError):
@@ -42,7 +42,9 @@ class mc_world_desc(ctypes.Structure):
                 ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("theta", ctypes.c_void_p),
                 ("L_rest", ctypes.c_void_p), ("theta0", ctypes.c_void_p), ("drive_amp", ctypes.c_void_p),
                 ("drive_freq", ctypes.c_void_p), ("drive_phase", ctypes.c_void_p), ("f0", ctypes.c_void_p),
-                ("t0", ctypes.c_int64), ("p", mc_params), ("mem_kind", ctypes.c_int)]
+                ("t0", ctypes.c_int64), ("p", mc_params), ("mem_kind", ctypes.c_int),
+                ("len_amp", ctypes.c_void_p), ("len_freq", ctypes.c_void_p), ("len_phase", ctypes.c_void_p),
+                ("energy", ctypes.c_void_p), ("observe", ctypes.c_int)]
 
 
 class mc_world_info(ctypes.Structure):
@@ -57,7 +59,8 @@ class mc_server_cfg(ctypes.Structure):
 
 
 class mc_result(ctypes.Structure):
-    _fields_ = [("com_disp", ctypes.c_double * 2), ("status", ctypes.c_int), ("n_steps", ctypes.c_int),
+    _fields_ = [("com_disp", ctypes.c_double * 2), ("e_bend", ctypes.c_double), ("e_pos", ctypes.c_double),
+                ("energy", ctypes.c_double), ("status", ctypes.c_int), ("n_steps", ctypes.c_int),
                 ("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64), ("t_done_ns", ctypes.c_int64)]
 
 
@@ -80,6 +83,7 @@ SIGNATURES = {
     "mc_world_get_field": (_i, [_vp, _i, _vp, _i, _vp]),
     "mc_world_check": (_i, [_vp, _vp]),
     "mc_world_clear_flags": (_i, [_vp, _vp]),
+    "mc_world_get_observables": (_i, [_vp, _vp, _vp]),
     "mc_rollout_forward": (_i, [_vp, _i, _i, _vp]),
     "mc_rollout_backward": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "mc_rollout_backward_params": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -97,7 +101,7 @@ SIGNATURES = {
 _lib = None
 
 
-ABI_VERSION = 2   # MC_ABI_VERSION of include/mc.h that these structures mirror
+ABI_VERSION = 3   # MC_ABI_VERSION of include/mc.h that these structures mirror
 
 
 def load():

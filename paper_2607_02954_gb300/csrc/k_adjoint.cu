@@ -351,17 +351,11 @@ __global__ void __launch_bounds__(128) k_adj_pbd(const WorldDev* __restrict__ wd
     vx[e] = (float)dcx + (pb.x - pa.x);
     vy[e] = (float)dcy + (pb.y - pa.y);
     th[e] = a.theta_n[e0 + e];
-    Lr[e] = w.L_rest[e0 + e];
+    Lr[e] = rest_length(w, e0 + e, t);
     gLa[e] = 0.0f;
   }
   for (int j = lane; j < nJ; j += 32) {
-    const float4 d = w.drive[j0 + j];
-    const float tf = (float)t;
-    const float hi = d.z * tf;
-    const float lo = fmaf(d.z, tf, -hi);
-    float fr = (hi - rintf(hi)) + lo + d.w;
-    fr -= rintf(fr);
-    thr[j] = d.x + d.y * sinpif(2.0f * fr);
+    thr[j] = drive_angle(w.drive[j0 + j], t);
     thrb[j] = 0.0f;
   }
   for (int i = lane; i < B; i += 32) {
@@ -491,7 +485,10 @@ __global__ void __launch_bounds__(128) k_adj_pbd(const WorldDev* __restrict__ wd
   // outputs
   for (int e = lane; e < nE; e += 32) {
     a.adjTh[e0 + e] = th[e];
-    a.gL[e0 + e] += gLa[e];
+    // with a rest-length drive L(t) = L0 (1 + A s(t)): dL(t)/dL0 = L(t)/L0
+    const float dLdL0 = w.ldrive ? 1.0f + w.ldrive[e0 + e].y * drive_sin(w.ldrive[e0 + e].z, w.ldrive[e0 + e].w, t)
+                                 : 1.0f;
+    a.gL[e0 + e] += gLa[e] * dLdL0;
   }
   for (int j = lane; j < nJ; j += 32) a.gth0[j0 + j] += thrb[j];
   for (int i = lane; i < B; i += 32) {

@@ -17,18 +17,8 @@ __device__ __forceinline__ void cpa4(void* sdst, const void* gsrc) {
 }
 __device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// a1: theta_rest = theta0 + A sin(2 pi (freq t + phase)).  The phase in
-// cycles is reduced exactly: hi + lo = freq * t (two-product via FMA), and
-// only the fractional parts are added, so the angle keeps full precision at
-// large t.  t < 2^24 converts to float exactly.
-__device__ __forceinline__ float drive_angle(const float4 d, long long t) {
-  const float tf = (float)t;
-  const float hi = d.z * tf;
-  const float lo = fmaf(d.z, tf, -hi);
-  float fr = (hi - rintf(hi)) + lo + d.w;
-  fr -= rintf(fr);
-  return d.x + d.y * sinpif(2.0f * fr);
-}
+
+__device__ __forceinline__ float sq(float v) { return v * v; }
 
 // Constants of the PBD passes, read once per warp.
 struct PbdConst {
@@ -106,10 +96,12 @@ __device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, 
   const float4 P1 = hb1 ? w.pos[b0 + i1] : z4;
   float th0 = he0 ? w.theta[e0 + i0] : 0.0f;
   float th1 = he1 ? w.theta[e0 + i1] : 0.0f;
-  const float L0 = he0 ? w.L_rest[e0 + i0] : 1.0f;
-  const float L1 = he1 ? w.L_rest[e0 + i1] : 1.0f;
-  const float thr0 = hj0 ? drive_angle(w.drive[j0 + i0], t) : 0.0f;
-  const float thr1 = hj1 ? drive_angle(w.drive[j0 + i1], t) : 0.0f;
+  const float L0 = he0 ? rest_length(w, e0 + i0, t) : 1.0f;
+  const float L1 = he1 ? rest_length(w, e0 + i1, t) : 1.0f;
+  const float4 z4d = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  const float4 D0 = hj0 ? w.drive[j0 + i0] : z4d, D1 = hj1 ? w.drive[j0 + i1] : z4d;
+  const float thr0 = hj0 ? drive_angle(D0, t) : 0.0f;
+  const float thr1 = hj1 ? drive_angle(D1, t) : 0.0f;
   float4 Pn;   // bead 2l + 2
   Pn.x = __shfl_down_sync(kAll, P0.x, 1);
   Pn.y = __shfl_down_sync(kAll, P0.y, 1);
@@ -184,6 +176,19 @@ __device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, 
   float fmax = 0.0f;
   bead_out(w, k, hb0, b0 + i0, P0, dlx0, dly0, fmax);
   bead_out(w, k, hb1, b0 + i1, P1, dlx1, dly1, fmax);
+  if (w.observe && t >= 1) {
+    // behaviour descriptors (Eqs. 5, 6): squared change of the rest angles
+    // and rest lengths from step t - 1 to step t
+    float eb = 0.0f, ep = 0.0f;
+    if (hj0) eb += sq(drive_angle(D0, t - 1) - thr0);
+    if (hj1) eb += sq(drive_angle(D1, t - 1) - thr1);
+    if (w.ldrive) {
+      if (he0) ep += sq(rest_length(w, e0 + i0, t - 1) - L0);
+      if (he1) ep += sq(rest_length(w, e0 + i1, t - 1) - L1);
+    }
+    obs_add_warp(&w.obs[0], eb);
+    obs_add_warp(&w.obs[1], ep);
+  }
   return fmax;
 }
 
@@ -211,7 +216,8 @@ __device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, 
   for (int i = lane; i < B; i += 32) cpa16(&P[i], &w.pos[b0 + i]);
   for (int e = lane; e < nE; e += 32) {
     cpa4(&th[e], &w.theta[e0 + e]);
-    cpa4(&Lr[e], &w.L_rest[e0 + e]);
+    if (!w.ldrive) cpa4(&Lr[e], &w.L_rest[e0 + e]);
+    else Lr[e] = drive_length(w.ldrive[e0 + e], t);
   }
   for (int j = lane; j < nJ; j += 32) cpa16(&D[j], &w.drive[j0 + j]);
   cpa_wait_all();
@@ -283,6 +289,14 @@ __device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, 
     bead_out(w, k, i < B, b0 + i, i < B ? P[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f), i < B ? dlx[i] : 0.0f,
              i < B ? dly[i] : 0.0f, fmax);
   }
+  if (w.observe && t >= 1) {
+    float eb = 0.0f, ep = 0.0f;
+    for (int j = lane; j < nJ; j += 32) eb += sq(drive_angle(D[j], t - 1) - thr[j]);
+    if (w.ldrive)
+      for (int e = lane; e < nE; e += 32) ep += sq(drive_length(w.ldrive[e0 + e], t - 1) - Lr[e]);
+    obs_add_warp(&w.obs[0], eb);
+    obs_add_warp(&w.obs[1], ep);
+  }
   return fmax;
 }
 
@@ -352,8 +366,31 @@ __global__ void __launch_bounds__(kBeadChunk, 8) k_interp_advance(const WorldDev
     w.fel_max[t & 1] = 0u;   // slot of the next step; this step's stays readable
   }
   const int i = it.y + threadIdx.x;
-  if (i >= w.N) return;
   const int W = w.W, H = w.H;
+  if (w.observe && w.energy) {
+    // the energy field at the bead's position at the start of the step,
+    // with the interpolation kernel; its warp sum is the energy collected
+    // (every lane of the block takes part in the warp sums)
+    float e = 0.0f;
+    if (i < w.N) {
+      const float4 q = w.pos[i];
+      float ex[4], ey[4];
+      peskin4(q.x, ex);
+      peskin4(q.y, ey);
+      const int qx = cell_x(q), qy = cell_y(q);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const float* row = w.energy + (size_t)wrap_once(qy - 1 + b, H) * W;
+        float r = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) r = fmaf(ex[a], row[wrap_once(qx - 1 + a, W)], r);
+        e = fmaf(ey[b], r, e);
+      }
+      w.ebead[i] = e;
+    }
+    obs_add_warp(&w.obs[2], e);
+  }
+  if (i >= w.N) return;
   float4 p = w.pos[i];
   int cx = cell_x(p), cy = cell_y(p);
   float wx[4], wy[4];

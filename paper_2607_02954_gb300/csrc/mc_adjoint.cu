@@ -144,6 +144,7 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
   const size_t o_gth0 = take(h.J * sizeof(float));
   const size_t o_gL = take(h.E * sizeof(float));
   const size_t o_gk = take(3 * sizeof(float));
+  const size_t o_obs = take(3 * sizeof(unsigned long long));
   const size_t o_g0 = take(9 * HW * sizeof(float));
   const size_t o_g1 = take(9 * HW * sizeof(float));
   const size_t o_ub = take(HW * sizeof(float2));
@@ -182,6 +183,8 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
   a.fbt = reinterpret_cast<float2*>(A + o_fbt);
   a.dbar = reinterpret_cast<float2*>(A + o_dbar);
 
+  // the recompute passes accumulate the observables again: keep the rollout's values
+  MC_ACUDA(cudaMemcpyAsync(A + o_obs, h.obs, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
   if (h.N) k_interleave<<<(h.N + 255) / 256, 256, 0, s>>>(dL_dx, dL_dy, a.adjX, h.N);
   if (h.E) MC_ACUDA(cudaMemsetAsync(a.adjTh, 0, h.E * sizeof(float), s));
   if (h.J) MC_ACUDA(cudaMemsetAsync(a.gth0, 0, h.J * sizeof(float), s));
@@ -236,6 +239,7 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
     MC_ACUDA(cudaMemcpyAsync(h.disp, tape + (size_t)(n_ck + 1) * sl.bytes, h.N * sizeof(float2),
                              cudaMemcpyDeviceToDevice, s));
   mc::launch_set_counter(h, tf, s);
+  MC_ACUDA(cudaMemcpyAsync(h.obs, A + o_obs, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
   MC_ACUDA(cudaGetLastError());
   return MC_OK;
 }

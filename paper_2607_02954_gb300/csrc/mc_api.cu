@@ -279,6 +279,10 @@ size_t world_layout(WorldDev& h, void* A) {
   const size_t o_t = L.take<long long>(1);
   const size_t o_fl = L.take<unsigned>(1);
   const size_t o_fm = L.take<unsigned>(2);
+  const size_t o_ld = L.take<float4>(h.has_ldrive ? E : 0);
+  const size_t o_en = L.take<float>(h.has_energy ? HW : 0);
+  const size_t o_eb = L.take<float>(h.has_energy ? N : 0);
+  const size_t o_ob = L.take<unsigned long long>(3);
   if (!A) return L.off;
   h.fil_off = at<int>(A, o_fo);
   h.pos = at<float4>(A, o_pos);
@@ -309,6 +313,10 @@ size_t world_layout(WorldDev& h, void* A) {
   h.t = at<long long>(A, o_t);
   h.flags = at<unsigned>(A, o_fl);
   h.fel_max = at<unsigned>(A, o_fm);
+  h.ldrive = h.has_ldrive ? at<float4>(A, o_ld) : nullptr;
+  h.energy = h.has_energy ? at<float>(A, o_en) : nullptr;
+  h.ebead = h.has_energy ? at<float>(A, o_eb) : nullptr;
+  h.obs = at<unsigned long long>(A, o_ob);
   return L.off;
 }
 
@@ -377,6 +385,20 @@ mc_status mc_world_create(const mc_world_desc* d, void* stream, mc_world** out) 
       (st = fetch(d->drive_phase, J, d->mem_kind, phs, "drive_phase")))
     return st;
   if (d->f0 && (st = fetch(d->f0, 9 * HW, d->mem_kind, f0, "f0"))) return st;
+  const int n_len = (d->len_amp != nullptr) + (d->len_freq != nullptr) + (d->len_phase != nullptr);
+  if (n_len != 0 && n_len != 3) return fail(MC_ERR_INVALID_ARG, "len_amp, len_freq, len_phase: all three or none");
+  std::vector<float> lamp, lfrq, lphs, energy;
+  if (n_len == 3 && ((st = fetch(d->len_amp, E, d->mem_kind, lamp, "len_amp")) ||
+                     (st = fetch(d->len_freq, E, d->mem_kind, lfrq, "len_freq")) ||
+                     (st = fetch(d->len_phase, E, d->mem_kind, lphs, "len_phase"))))
+    return st;
+  if (d->energy && (st = fetch(d->energy, HW, d->mem_kind, energy, "energy"))) return st;
+  if (!finite_all(lamp.data(), lamp.size()) || !finite_all(lfrq.data(), lfrq.size()) ||
+      !finite_all(lphs.data(), lphs.size()) || !finite_all(energy.data(), energy.size()))
+    return fail(MC_ERR_INVALID_ARG, "non-finite input value");
+  for (float a : lamp)
+    if (!(std::fabs(a) < 1.0f)) return fail(MC_ERR_INVALID_ARG, "|len_amp| must be < 1 (rest lengths stay > 0)");
+  if (d->observe != 0 && d->observe != 1) return fail(MC_ERR_INVALID_ARG, "observe must be 0 or 1");
   if (!finite_all(x.data(), N) || !finite_all(y.data(), N) || !finite_all(th.data(), E) ||
       !finite_all(Lr.data(), E) || !finite_all(t0v.data(), J) || !finite_all(amp.data(), J) ||
       !finite_all(frq.data(), J) || !finite_all(phs.data(), J) || !finite_all(f0.data(), f0.size()))
@@ -415,6 +437,9 @@ mc_status mc_world_create(const mc_world_desc* d, void* stream, mc_world** out) 
   WorldDev& h = w->h;
   mc::world_sizes(h, H, W, d->n_fil, N);
   fill_constants(h, d->p);
+  h.has_ldrive = n_len == 3;
+  h.has_energy = d->energy != nullptr;
+  h.observe = d->observe;
 
   w->bytes = mc::world_layout(h, nullptr);
   cudaError_t e = cudaMallocAsync(&w->arena, w->bytes, s);
@@ -445,6 +470,12 @@ mc_status mc_world_create(const mc_world_desc* d, void* stream, mc_world** out) 
   MC_CUDA_W(up(h.theta, th.data(), E * sizeof(float)));
   MC_CUDA_W(up((void*)h.L_rest, Lr.data(), E * sizeof(float)));
   MC_CUDA_W(up((void*)h.drive, drive.data(), J * sizeof(float4)));
+  if (h.has_ldrive) {
+    std::vector<float4> ld(E);
+    for (int e = 0; e < E; ++e) ld[e] = make_float4(Lr[e], lamp[e], lfrq[e], lphs[e]);
+    MC_CUDA_W(up((void*)h.ldrive, ld.data(), E * sizeof(float4)));
+  }
+  if (h.has_energy) MC_CUDA_W(up((void*)h.energy, energy.data(), HW * sizeof(float)));
   const long long t0 = d->t0;
   MC_CUDA_W(up(h.t, &t0, sizeof(long long)));
   if (!f0.empty()) {
@@ -623,6 +654,11 @@ mc_status mc_world_get_field(const mc_world* w, int field, void* out, int mem_ki
     case MC_FIELD_BIN: src = h.bead_bin; bytes = h.N * sizeof(int); break;
     case MC_FIELD_BIN_OFF: src = h.bin_off; bytes = (h.n_bins + 1) * sizeof(int); break;
     case MC_FIELD_BIN_BEADS: src = h.sid; bytes = h.N * sizeof(int); break;
+    case MC_FIELD_EBEAD:
+      if (!h.ebead) return fail(MC_ERR_INVALID_ARG, "the world has no energy field");
+      src = h.ebead;
+      bytes = h.N * sizeof(float);
+      break;
     case MC_FIELD_CELL: {
       if (h.N == 0) return MC_OK;
       int* dst = static_cast<int*>(out);
@@ -645,6 +681,16 @@ mc_status mc_world_get_field(const mc_world* w, int field, void* out, int mem_ki
   }
   if (bytes) MC_CUDA(cudaMemcpyAsync(out, src, bytes, dk, s));
   if (host) MC_CUDA(cudaStreamSynchronize(s));
+  return MC_OK;
+}
+
+mc_status mc_world_get_observables(const mc_world* w, double* out, void* stream) {
+  if (!w || !out) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long v[3];
+  MC_CUDA(cudaMemcpyAsync(v, w->h.obs, sizeof(v), cudaMemcpyDeviceToHost, s));
+  MC_CUDA(cudaStreamSynchronize(s));
+  for (int k = 0; k < 3; ++k) out[k] = (double)(long long)v[k] / (double)mc::kObsScale;
   return MC_OK;
 }
 

@@ -71,7 +71,18 @@ struct WorldDev {
   long long* t;           // step counter
   unsigned* fel_max;      // [2] largest |F_el| component of the step, by step parity (float bits)
   unsigned* flags;        // watchdog flags
+  // optional inputs and search-side observables
+  int has_ldrive, has_energy, observe;
+  const float4* ldrive;   // [E] (L0, amp, freq, phase) rest-length drive, or nullptr (static L_rest)
+  const float* energy;    // [H * W] energy field, or nullptr
+  float* ebead;           // [N] energy sampled at each bead (observe and energy)
+  unsigned long long* obs;  // [3] E_bend, E_pos, energy collected, fixed point 2^-24 (two's complement)
 };
+
+// Fixed-point scale of the observable sums (units of 2^-24): a warp's
+// per-step sum is rounded to the unit, and a world's total stays exact
+// while below 2^63 units (5.5e11).
+constexpr float kObsScale = 16777216.0f;
 
 // Adjoint buffers of one world (reverse-mode sweep), all device pointers.
 struct AdjDev {
@@ -266,6 +277,39 @@ __device__ __forceinline__ float2 lbm_cell(const float* __restrict__ src, float*
   LbmPull q;
   lbm_pull(src, HW, r0, rm, rp, x, xm, xp, q);
   return lbm_collide(q, dst, HW, r0 + x, F, k);
+}
+
+// sin(2 pi (freq t + phase)), phase in cycles, reduced exactly: hi + lo =
+// freq * t (two-product via FMA) and only the fractional parts are added,
+// so the angle keeps full precision at large t (t < 2^24 converts to float
+// exactly).
+__device__ __forceinline__ float drive_sin(float freq, float phase, long long t) {
+  const float tf = (float)t;
+  const float hi = freq * tf;
+  const float lo = fmaf(freq, tf, -hi);
+  float fr = (hi - rintf(hi)) + lo + phase;
+  fr -= rintf(fr);
+  return sinpif(2.0f * fr);
+}
+
+// a1: theta_rest = theta0 + A sin(2 pi (freq t + phase)), d = (theta0, A, freq, phase).
+__device__ __forceinline__ float drive_angle(const float4 d, long long t) { return d.x + d.y * drive_sin(d.z, d.w, t); }
+
+// Rest-length drive: L_rest = L0 (1 + A sin(2 pi (freq t + phase))), d = (L0, A, freq, phase).
+__device__ __forceinline__ float drive_length(const float4 d, long long t) {
+  return d.x * (1.0f + d.y * drive_sin(d.z, d.w, t));
+}
+
+// Rest length of edge e (global index) at step t.
+__device__ __forceinline__ float rest_length(const WorldDev& w, int e, long long t) {
+  return w.ldrive ? drive_length(w.ldrive[e], t) : w.L_rest[e];
+}
+
+// Adds a warp's sum of v (lanes in a fixed xor tree, so the same lanes and
+// values give the same bits) to a fixed-point observable.  Every lane calls.
+__device__ __forceinline__ void obs_add_warp(unsigned long long* acc, float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v != 0.0f) atomicAdd(acc, (unsigned long long)__float2ll_rn(v * kObsScale));
 }
 
 __device__ __forceinline__ int cell_x(const float4& p) { return __float_as_int(p.z); }

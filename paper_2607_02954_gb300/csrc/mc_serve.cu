@@ -39,6 +39,8 @@ struct Request {
   int H = 0, W = 0, n_fil = 0;
   std::vector<int> fil_off;
   std::vector<float> x, y, theta, L_rest, theta0, amp, freq, phase, f0;
+  std::vector<float> len_amp, len_freq, len_phase, energy;   // optional (empty = absent)
+  int observe = 0;
   int64_t t0 = 0;
   mc_params p{};
   size_t bytes = 0;
@@ -53,6 +55,8 @@ struct Slot {
   size_t bytes = 0;
   int64_t t_submit = 0, t_admit = 0;
 };
+
+constexpr size_t kRec = 40;   // 3 floats (mean displacement, flags) + pad, 3 int64 observables
 
 // Mean displacement of one world, fixed-order reduction (one block).
 __global__ void __launch_bounds__(256) k_mean_disp(const float2* __restrict__ disp, int N,
@@ -105,17 +109,19 @@ struct mc_server {
   size_t bytes_in_use = 0;
   mc::Plan plan;
   bool plan_valid = false;
-  float* d_out = nullptr;
-  float* h_out = nullptr;
+  char* d_out = nullptr;   // per finished world: kRec bytes (mean displacement, flags, observables)
+  char* h_out = nullptr;
   int out_cap = 0;
   mc_server_stats stats{};
 };
 
 namespace {
 
-size_t footprint(int H, int W, int n_fil, int N) {
+size_t footprint(int H, int W, int n_fil, int N, bool ldrive, bool energy) {
   mc::WorldDev h{};
   mc::world_sizes(h, H, W, n_fil, N);
+  h.has_ldrive = ldrive;
+  h.has_energy = energy;
   // arena plus this world's share of a plan (work items and table entry)
   const size_t items = (size_t)n_fil + (N / mc::kBeadChunk + 1) + h.n_tiles + (size_t)H * W / mc::kCellChunk + 1 +
                        h.n_chunks;
@@ -163,6 +169,11 @@ void scheduler(mc_server* s) {
       d.drive_freq = r.freq.data();
       d.drive_phase = r.phase.data();
       d.f0 = r.f0.empty() ? nullptr : r.f0.data();
+      d.len_amp = r.len_amp.empty() ? nullptr : r.len_amp.data();
+      d.len_freq = r.len_freq.empty() ? nullptr : r.len_freq.data();
+      d.len_phase = r.len_phase.empty() ? nullptr : r.len_phase.data();
+      d.energy = r.energy.empty() ? nullptr : r.energy.data();
+      d.observe = r.observe;
       d.t0 = r.t0;
       d.p = r.p;
       d.mem_kind = MC_MEM_HOST;
@@ -236,23 +247,32 @@ void scheduler(mc_server* s) {
       if (s->d_out) cudaFreeAsync(s->d_out, s->stream);
       if (s->h_out) cudaFreeHost(s->h_out);
       s->out_cap = std::max((int)fin.size(), 2 * s->out_cap);
-      cudaMallocAsync(&s->d_out, 3 * s->out_cap * sizeof(float), s->stream);
-      cudaMallocHost(&s->h_out, 3 * s->out_cap * sizeof(float));
+      cudaMallocAsync(&s->d_out, kRec * s->out_cap, s->stream);
+      cudaMallocHost(&s->h_out, kRec * s->out_cap);
     }
     for (int j = 0; j < (int)fin.size(); ++j) {
       const mc::WorldDev& h = s->active[fin[j]].w->h;
-      k_mean_disp<<<1, 256, 0, s->stream>>>(h.disp, h.N, h.flags, s->d_out + 3 * j);
+      k_mean_disp<<<1, 256, 0, s->stream>>>(h.disp, h.N, h.flags, reinterpret_cast<float*>(s->d_out + kRec * j));
+      cudaMemcpyAsync(s->d_out + kRec * j + 16, h.obs, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                      s->stream);
     }
-    cudaMemcpyAsync(s->h_out, s->d_out, 3 * fin.size() * sizeof(float), cudaMemcpyDeviceToHost, s->stream);
+    cudaMemcpyAsync(s->h_out, s->d_out, kRec * fin.size(), cudaMemcpyDeviceToHost, s->stream);
     const cudaError_t e = cudaStreamSynchronize(s->stream);
     const int64_t t = now_ns();
     for (int j = (int)fin.size() - 1; j >= 0; --j) {
       Slot sl = s->active[fin[j]];
       mc_result res{};
-      res.com_disp[0] = s->h_out[3 * j];
-      res.com_disp[1] = s->h_out[3 * j + 1];
+      float rec[3];
+      std::memcpy(rec, s->h_out + kRec * j, sizeof(rec));
+      res.com_disp[0] = rec[0];
+      res.com_disp[1] = rec[1];
       unsigned flags;
-      std::memcpy(&flags, &s->h_out[3 * j + 2], 4);
+      std::memcpy(&flags, &rec[2], 4);
+      long long obs[3];
+      std::memcpy(obs, s->h_out + kRec * j + 16, sizeof(obs));
+      res.e_bend = (double)obs[0] / (double)mc::kObsScale;
+      res.e_pos = (double)obs[1] / (double)mc::kObsScale;
+      res.energy = (double)obs[2] / (double)mc::kObsScale;
       res.status = e != cudaSuccess ? MC_ERR_CUDA : ((flags & mc::kFlagUnstable) ? MC_ERR_UNSTABLE : MC_OK);
       res.n_steps = sl.n_steps;
       res.t_submit_ns = sl.t_submit;
@@ -337,9 +357,14 @@ mc_status mc_serve_submit(mc_server* s, const mc_world_desc* d, int n_steps, uin
       (st = copy_in(d->drive_phase, J, d->mem_kind, r.phase, "drive_phase")))
     return st;
   if (d->f0 && (st = copy_in(d->f0, (size_t)9 * d->H * d->W, d->mem_kind, r.f0, "f0"))) return st;
+  if (d->len_amp && (st = copy_in(d->len_amp, E, d->mem_kind, r.len_amp, "len_amp"))) return st;
+  if (d->len_freq && (st = copy_in(d->len_freq, E, d->mem_kind, r.len_freq, "len_freq"))) return st;
+  if (d->len_phase && (st = copy_in(d->len_phase, E, d->mem_kind, r.len_phase, "len_phase"))) return st;
+  if (d->energy && (st = copy_in(d->energy, (size_t)d->H * d->W, d->mem_kind, r.energy, "energy"))) return st;
+  r.observe = d->observe;
   r.t0 = d->t0;
   r.p = d->p;
-  r.bytes = footprint(d->H, d->W, d->n_fil, N);
+  r.bytes = footprint(d->H, d->W, d->n_fil, N, d->len_amp != nullptr, d->energy != nullptr);
   r.t_submit = now_ns();
   std::lock_guard<std::mutex> lk(s->mu);
   if ((int)s->pending.size() >= s->cfg.max_pending) return serve_fail(MC_ERR_BUSY, "request queue is full");

@@ -79,6 +79,11 @@ class WorldSpec:
     f0: Optional[np.ndarray] = None   # float32 [9, H, W]: populations minus rest weights
     t0: int = 0
     name: str = ""
+    len_amp: Optional[np.ndarray] = None     # float32 [E] rest-length drive (all three or none)
+    len_freq: Optional[np.ndarray] = None    # float32 [E] cycles per step
+    len_phase: Optional[np.ndarray] = None   # float32 [E] cycles
+    energy: Optional[np.ndarray] = None      # float32 [H, W] energy field
+    observe: bool = False                    # accumulate the behaviour descriptors and collected energy
 
     @property
     def n_fil(self) -> int:
@@ -364,3 +369,36 @@ def tiny_world(seed=0, side=16, lengths=(6, 5), params=None, amp=0.1):
     theta0 = rng.uniform(-0.3, 0.3, J)
     return _world(f"tiny_{seed}", side, side, lengths, x, y, theta, theta0,
                   np.full(J, amp), np.full(J, 1.0 / 50.0), rng.uniform(0, 1, J), params=params)
+
+
+def energy_packets(rng, H, W, n_packets=8, amp=(0.2, 1.0), width=(2.0, 8.0)) -> np.ndarray:
+    """A persistent energy field of Gaussian packets at random positions
+    (Neuroevolution experiment's chemotaxis target): the sum over packets of
+    a_k exp(-|x - c_k|^2 / (2 s_k^2)) at the cell centres, periodic distance;
+    a_k ~ U[amp], s_k ~ U[width].  float32 [H, W]."""
+    ys, xs = np.meshgrid(np.arange(H, dtype=np.float64), np.arange(W, dtype=np.float64), indexing="ij")
+    field = np.zeros((H, W))
+    for _ in range(n_packets):
+        cx, cy = rng.uniform(0, W), rng.uniform(0, H)
+        a, s = rng.uniform(*amp), rng.uniform(*width)
+        dx = xs - cx
+        dx -= W * np.round(dx / W)
+        dy = ys - cy
+        dy -= H * np.round(dy / H)
+        field += a * np.exp(-(dx * dx + dy * dy) / (2.0 * s * s))
+    return field.astype(np.float32)
+
+
+def with_observables(spec: WorldSpec, seed: int, len_amp_max=0.2, period=(50.0, 400.0), n_packets=8) -> WorldSpec:
+    """Adds what the search experiments read: a rest-length drive per edge
+    (the controller's rest-length output; amplitude ~U[0, len_amp_max],
+    period ~U[period] steps, phase ~U[0, 1) cycles), an energy field of
+    Gaussian packets, and observe = True.  Returns spec (modified)."""
+    rng = np.random.default_rng(seed + 7919)
+    E = spec.E
+    spec.len_amp = rng.uniform(0.0, len_amp_max, E).astype(np.float32)
+    spec.len_freq = (1.0 / rng.uniform(*period, E)).astype(np.float32)
+    spec.len_phase = rng.uniform(0.0, 1.0, E).astype(np.float32)
+    spec.energy = energy_packets(rng, spec.H, spec.W, n_packets)
+    spec.observe = True
+    return spec

@@ -41,6 +41,7 @@ def default_params() -> Params:
 
 
 _FLOAT_ARRAYS = ("x", "y", "theta", "L_rest", "theta0", "drive_amp", "drive_freq", "drive_phase")
+_OPTIONAL_ARRAYS = ("f0", "len_amp", "len_freq", "len_phase", "energy")
 
 
 def make_desc(spec: WorldSpec, device: bool = False):
@@ -58,10 +59,12 @@ def make_desc(spec: WorldSpec, device: bool = False):
             t = torch.as_tensor(np.ascontiguousarray(getattr(spec, name), np.float32)).cuda()
             keep.append(t)
             setattr(d, name, ctypes.c_void_p(t.data_ptr() if t.numel() else 0))
-        if spec.f0 is not None:
-            t = torch.as_tensor(np.ascontiguousarray(spec.f0, np.float32)).cuda()
-            keep.append(t)
-            d.f0 = ctypes.c_void_p(t.data_ptr())
+        for name in _OPTIONAL_ARRAYS:
+            v = getattr(spec, name, None)
+            if v is not None:
+                t = torch.as_tensor(np.ascontiguousarray(v, np.float32)).cuda()
+                keep.append(t)
+                setattr(d, name, ctypes.c_void_p(t.data_ptr() if t.numel() else 0))
         d.mem_kind = L.MC_MEM_DEVICE
         torch.cuda.synchronize()
     else:
@@ -69,13 +72,16 @@ def make_desc(spec: WorldSpec, device: bool = False):
             a = np.ascontiguousarray(getattr(spec, name), dtype=np.float32)
             keep.append(a)
             setattr(d, name, ctypes.c_void_p(a.ctypes.data if a.size else 0))
-        if spec.f0 is not None:
-            a = np.ascontiguousarray(spec.f0, dtype=np.float32)
-            keep.append(a)
-            d.f0 = ctypes.c_void_p(a.ctypes.data)
+        for name in _OPTIONAL_ARRAYS:
+            v = getattr(spec, name, None)
+            if v is not None:
+                a = np.ascontiguousarray(v, dtype=np.float32)
+                keep.append(a)
+                setattr(d, name, ctypes.c_void_p(a.ctypes.data if a.size else 0))
         d.mem_kind = L.MC_MEM_HOST
     d.t0 = int(spec.t0)
     d.p = params_struct(spec.params)
+    d.observe = int(bool(getattr(spec, "observe", False)))
     return d, keep
 
 
@@ -185,6 +191,14 @@ class World:
                                                      ptr(out["L_rest"]), ptr(out["k"]), stream_handle(stream)))
         return out
 
+    def observables(self, stream=None) -> Dict[str, float]:
+        """Behaviour descriptors E_bend, E_pos and the energy collected since
+        creation (zeros unless the spec set observe)."""
+        out = (ctypes.c_double * 3)()
+        L.check(self._lib.mc_world_get_observables(self.handle, ctypes.cast(out, ctypes.c_void_p),
+                                                   stream_handle(stream)))
+        return {"e_bend": out[0], "e_pos": out[1], "energy": out[2]}
+
     def loss_polyline(self, poly, stream=None):
         """Folding loss against a polyline (numpy [V, 2]); returns (loss tensor [1], dL_dx, dL_dy)."""
         torch = _torch()
@@ -205,7 +219,7 @@ class World:
         shapes = {"fel": ((N, 2), np.float32), "fs": ((N, 2), np.float32), "ubead": ((N, 2), np.float32),
                   "rho_s": ((s.H, s.W), np.float32), "rho_bar": ((s.H, s.W), np.float32),
                   "force": ((s.H, s.W, 2), np.float32), "u": ((s.H, s.W, 2), np.float32),
-                  "cell": ((N,), np.int32), "bin": ((N,), np.int32),
+                  "cell": ((N,), np.int32), "bin": ((N,), np.int32), "ebead": ((N,), np.float32),
                   "bin_off": ((info["n_bins"] + 1,), np.int32), "bin_beads": ((N,), np.int32)}
         shape, dt = shapes[name]
         out = np.empty(shape, dt)
@@ -221,7 +235,8 @@ def step_batched(worlds: Sequence[World], n_steps: int, stream=None):
 
 
 def _result_dict(r: L.mc_result) -> Dict:
-    return {"com_disp": (r.com_disp[0], r.com_disp[1]), "status": r.status, "n_steps": r.n_steps,
+    return {"com_disp": (r.com_disp[0], r.com_disp[1]), "e_bend": r.e_bend, "e_pos": r.e_pos,
+            "energy": r.energy, "status": r.status, "n_steps": r.n_steps,
             "t_submit_ns": r.t_submit_ns, "t_admit_ns": r.t_admit_ns, "t_done_ns": r.t_done_ns}
 
 

@@ -658,6 +658,62 @@ def test_red_black_rest_state_is_a_fixed_point():
     assert torch.equal(x_hat, st.X) and torch.equal(th, st.theta)
 
 
+# ---------------------------------------------------------------------------
+# Search observables (QD Search Eqs. 5, 6; the Neuroevolution energy field).
+# ---------------------------------------------------------------------------
+def _observed_world(A=0.2, a=0.1, nu=0.25, energy=None):
+    spec = synth.tiny_world(3, side=32, lengths=(6, 5, 4))
+    spec.drive_amp = np.full(spec.J, A, np.float32)
+    spec.drive_freq = np.full(spec.J, nu, np.float32)
+    spec.drive_phase = np.zeros(spec.J, np.float32)
+    spec.len_amp = np.full(spec.E, a, np.float32)
+    spec.len_freq = np.full(spec.E, nu, np.float32)
+    spec.len_phase = np.zeros(spec.E, np.float32)
+    spec.energy = energy
+    spec.observe = True
+    return spec
+
+
+def test_behaviour_descriptors_closed_form():
+    """Drive and rest-length drive at frequency 1/4 cycle per step, phase 0:
+    sin(2 pi t / 4) runs 0, 1, 0, -1, so every step t >= 1 changes each rest
+    angle by A and each rest length by L0 a in magnitude.  Over n steps from
+    t = 0: E_bend = (n - 1) J A^2 and E_pos = (n - 1) E (L0 a)^2."""
+    A, a, n = 0.2, 0.1, 9
+    spec = _observed_world(A, a)
+    obs = O.observables(O.World(spec), n)
+    L0 = float(spec.L_rest[0])
+    A, a = float(np.float32(A)), float(np.float32(a))   # the inputs are float32
+    assert abs(obs["e_bend"] - (n - 1) * spec.J * A * A) < 1e-12
+    assert abs(obs["e_pos"] - (n - 1) * spec.E * (L0 * a) ** 2) < 1e-12
+    assert obs["energy"] == 0.0
+
+
+def test_energy_collected_from_a_constant_field_is_exact():
+    """The interpolation weights of a bead sum to one: a constant field E0
+    gives N E0 per step whatever the positions."""
+    E0, n = 0.37, 5
+    spec = _observed_world(energy=np.full((32, 32), E0, np.float32))
+    obs = O.observables(O.World(spec), n)
+    assert abs(obs["energy"] - n * spec.N * float(np.float32(E0))) < 1e-10
+
+
+def test_energy_sample_of_a_linear_field_is_the_field_at_the_bead():
+    """Peskin's kernel reproduces linear functions: on E(c) = 0.01 c_x +
+    0.02 c_y + 0.5 (cell centres, beads away from the periodic seam) each
+    bead samples exactly 0.01 X + 0.02 Y + 0.5."""
+    ys, xs = np.meshgrid(np.arange(32.0), np.arange(32.0), indexing="ij")
+    field = (0.01 * xs + 0.02 * ys + 0.5).astype(np.float64)
+    spec = _observed_world(energy=field)
+    spec.x = (8.0 + np.linspace(0, 12, spec.N)).astype(np.float32)
+    spec.y = (10.0 + np.linspace(0, 9, spec.N)).astype(np.float32)
+    w = O.World(spec)
+    st = w.initial_state()
+    _, rec = O.step(w, st, record=True)
+    want = 0.01 * t2n(st.X[:, 0]) + 0.02 * t2n(st.X[:, 1]) + 0.5
+    assert np.allclose(t2n(rec["e_bead"]), want, rtol=0, atol=1e-13)
+
+
 def _objective(w, n_steps, gx, gy, L_rest=None, ks=None):
     import copy
     import dataclasses
