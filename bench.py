@@ -78,6 +78,8 @@ def parse():
                          "2000-step checkpointed rollout + loss + reverse sweep)")
     ap.add_argument("--pbd-order", type=int, default=0, choices=[0, 1],
                     help="PBD pass order of the stepped world: 0 Jacobi, 1 red-black")
+    ap.add_argument("--observe", action="store_true",
+                    help="step workloads: add a rest-length drive, an energy field and the observables")
     ap.add_argument("--arrival-rate", type=float, default=2000.0, help="served: requests per second")
     ap.add_argument("--duration", type=float, default=2.0, help="served: seconds of arrivals")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -86,11 +88,15 @@ def parse():
     return ap.parse_args()
 
 
-def make_spec(name: str, seed: int, pbd_order: int = 0):
+def make_spec(name: str, seed: int, pbd_order: int = 0, observe: bool = False):
     spec, desc = _make_spec(name, seed)
     if pbd_order:
         spec.params.pbd_order = pbd_order
         desc += ", red-black PBD passes"
+    if observe:
+        from paper_2607_02954_gb300 import synth
+        synth.with_observables(spec, seed)
+        desc += ", rest-length drive + energy field + observables"
     return spec, desc
 
 
@@ -369,7 +375,9 @@ def bench_served(args):
     asks for a 500-step rollout and reads back the displacement."""
     import random
     from paper_2607_02954_gb300 import Server, synth
-    pool = synth.batch_c4(1, n_worlds=256)
+    # the search workload: every rollout returns its fitness inputs (mean
+    # displacement, collected energy) and behaviour descriptors
+    pool = [synth.with_observables(sp, k) for k, sp in enumerate(synth.batch_c4(1, n_worlds=256))]
     rng = random.Random(7)
     srv = Server(hbm_budget_bytes=64 << 30, max_slots=4096, steps_per_tick=10)
     # warm-up: a few rollouts to load kernels
@@ -401,7 +409,8 @@ def bench_served(args):
             "steps": 500, "warmup": 8, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "served", "requests": n_req, "arrival_rate_per_s": args.arrival_rate,
-                       "rollout_steps": 500, "pool": "256 C4 worlds"},
+                       "rollout_steps": 500,
+                       "pool": "256 C4 worlds with rest-length drive, energy field and observables"},
             "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                            "max": lat[-1]},
             "completed_per_s": n_req / span, "failed": bad, "server": stats, "clocks": clk.summary()}
@@ -442,7 +451,7 @@ def main():
         build()
     lib = _lib.load()
 
-    spec, desc = make_spec(args.workload, seed=rank, pbd_order=args.pbd_order)
+    spec, desc = make_spec(args.workload, seed=rank, pbd_order=args.pbd_order, observe=args.observe)
     N, C = spec.N, spec.H * spec.W
     world = World(spec, device=True)
     stream = torch.cuda.current_stream()
