@@ -78,6 +78,8 @@ def parse():
                          "2000-step checkpointed rollout + loss + reverse sweep)")
     ap.add_argument("--pbd-order", type=int, default=0, choices=[0, 1],
                     help="PBD pass order of the stepped world: 0 Jacobi, 1 red-black")
+    ap.add_argument("--loss", default="polyline", choices=["polyline", "splat"],
+                    help="c5: folding loss, distance to a polyline or the paper's splatted-density MSE (128^2)")
     ap.add_argument("--observe", action="store_true",
                     help="step workloads: add a rest-length drive, an energy field and the observables")
     ap.add_argument("--arrival-rate", type=float, default=2000.0, help="served: requests per second")
@@ -315,13 +317,15 @@ def bench_gradient(args):
     import torch
     from paper_2607_02954_gb300 import World, synth
     spec, poly = synth.world_c5(0)
+    target = synth.target_image(np.random.default_rng(0), 128)
+    loss_fn = (lambda w: w.loss_splat(target, 1.0)) if args.loss == "splat" else (lambda w: w.loss_polyline(poly))
     n, K = 2000, 100
     reps = max(1, min(args.steps, 5))
     w = World(spec)
     stream = torch.cuda.current_stream()
     for _ in range(max(1, min(args.warmup, 2))):
         w.rollout_forward(50, 10)
-        loss, gx, gy = w.loss_polyline(poly)
+        loss, gx, gy = loss_fn(w)
         w.rollout_backward_params(gx, gy)
     torch.cuda.synchronize()
     fwd, bwd = [], []
@@ -331,7 +335,7 @@ def bench_gradient(args):
             e[0].record(stream)
             w.rollout_forward(n, K)
             e[1].record(stream)
-            loss, gx, gy = w.loss_polyline(poly)
+            loss, gx, gy = loss_fn(w)
             g = w.rollout_backward_params(gx, gy)
             e[2].record(stream)
             torch.cuda.synchronize()
@@ -347,7 +351,8 @@ def bench_gradient(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "c5", "grid": [spec.H, spec.W], "beads": spec.N, "filaments": spec.n_fil,
                        "rollout_steps": n, "ckpt_every": K, "repetitions": reps,
-                       "description": "folding gradient: checkpointed forward + polyline loss + reverse sweep "
+                       "loss": args.loss,
+                       "description": f"folding gradient: checkpointed forward + {args.loss} loss + reverse sweep "
                                       "(theta0, L_rest, k_bend, k_stretch, k_shear)"},
             "forward_ms": ms_f, "backward_ms": ms_b, "backward_over_forward": ms_b / ms_f,
             "grad_norm_theta0": grad_norm, "clocks": clk.summary()}

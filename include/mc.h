@@ -298,6 +298,21 @@ mc_status mc_rollout_backward_params(mc_world* w, const float* dL_dx, const floa
 mc_status mc_loss_polyline(mc_world* w, const float* poly_xy, int n_vertices, float* loss, float* dL_dx,
                            float* dL_dy, void* stream);
 
+/* The paper's folding loss (Filament Folding experiment): mean squared
+ * error between the Gaussian-splatted bead density of the world's current
+ * positions and target [R][R] (device, row-major, row = y), an image of
+ * R x R pixels covering the periodic domain.  Pixel (px, py) is centred at
+ * ((px + 1/2) W/R, (py + 1/2) H/R); a bead at image coordinates
+ * u = (X R/W, Y R/H) adds exp(-|c - u|^2 / (2 sigma^2)) (sigma in pixels) to
+ * the pixels c with px in floor(u_x) - K .. floor(u_x) + K and likewise py,
+ * periodic, K = ceil(4 sigma); no normalisation.  loss: one device float;
+ * dL_dx, dL_dy [N] (device): its gradient with respect to the positions,
+ * the input of mc_rollout_backward.  The image is accumulated in 64-bit
+ * fixed point, so the loss is bitwise repeatable.  8 <= R <= 1024,
+ * 0 < sigma <= 4.  Allocates R^2 * 12 bytes of scratch for the call. */
+mc_status mc_loss_splat(mc_world* w, const float* target, int R, float sigma, float* loss, float* dL_dx,
+                        float* dL_dy, void* stream);
+
 /* ---- Rollout serving: continuous batching ---------------------------------
  * Search loops (the paper's Neuroevolution and QD Search experiments,
  * Experiments section) request rollouts as they go and read back a fitness,

@@ -533,6 +533,44 @@ def folding_loss(world: World, n_steps: int, poly, theta0: Optional[torch.Tensor
     return polyline_loss(X0 + st.D, poly), st
 
 
+# ---------------------------------------------------------------------------
+# The paper's folding loss (Filament Folding experiment): mean squared error
+# between the Gaussian-splatted particle density at the final step and a
+# target image of R x R pixels covering the periodic domain.  Readings: pixel
+# (px, py) has its centre at ((px + 1/2) W/R, (py + 1/2) H/R); a bead at image
+# coordinates u = (X R/W, Y R/H) adds exp(-|c - u|^2 / (2 s^2)) to the
+# (2K + 1)^2 pixels c with px in floor(u_x) - K .. floor(u_x) + K (same in y,
+# periodic), K = ceil(4 s), s in pixels; no normalisation.
+# ---------------------------------------------------------------------------
+def splat_image(X: torch.Tensor, H: int, W: int, R: int, s: float) -> torch.Tensor:
+    K = int(math.ceil(4.0 * s))
+    ux = X[:, 0] * (R / W)
+    uy = X[:, 1] * (R / H)
+    offs = torch.arange(-K, K + 1, dtype=F64)
+    px = torch.floor(ux).detach()[:, None] + offs[None, :]      # [N, 2K+1]
+    py = torch.floor(uy).detach()[:, None] + offs[None, :]
+    gx = torch.exp(-((px + 0.5 - ux[:, None]) ** 2) / (2.0 * s * s))
+    gy = torch.exp(-((py + 0.5 - uy[:, None]) ** 2) / (2.0 * s * s))
+    ix = torch.remainder(px.long(), R)
+    iy = torch.remainder(py.long(), R)
+    idx = (iy[:, :, None] * R + ix[:, None, :]).reshape(X.shape[0], -1)
+    val = (gy[:, :, None] * gx[:, None, :]).reshape(X.shape[0], -1)
+    img = torch.zeros(R * R, dtype=F64).index_add(0, idx.reshape(-1), val.reshape(-1))
+    return img.reshape(R, R)
+
+
+def splat_loss(X: torch.Tensor, target: torch.Tensor, H: int, W: int, s: float) -> torch.Tensor:
+    R = int(target.shape[0])
+    d = splat_image(X, H, W, R, s) - target
+    return (d * d).mean()
+
+
+def splat_folding_loss(world: World, n_steps: int, target, s: float, theta0: Optional[torch.Tensor] = None):
+    st = rollout(world, n_steps, theta0=theta0)
+    target = torch.as_tensor(np.asarray(target, np.float64))
+    return splat_loss(st.X, target, world.H, world.W, s), st
+
+
 def folding_gradient(world: World, n_steps: int, poly):
     """dL/dtheta0 by reverse-mode automatic differentiation of the FP64
     rollout (the paper differentiates its simulator end to end with JAX;

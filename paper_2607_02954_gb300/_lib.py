@@ -88,6 +88,7 @@ SIGNATURES = {
     "mc_rollout_backward": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "mc_rollout_backward_params": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "mc_loss_polyline": (_i, [_vp, _vp, _i, _vp, _vp, _vp, _vp]),
+    "mc_loss_splat": (_i, [_vp, _vp, _i, ctypes.c_float, _vp, _vp, _vp, _vp]),
     "mc_server_create": (_i, [ctypes.POINTER(mc_server_cfg), ctypes.POINTER(_vp)]),
     "mc_serve_submit": (_i, [_vp, ctypes.POINTER(mc_world_desc), _i, ctypes.POINTER(ctypes.c_uint64)]),
     "mc_serve_poll": (_i, [_vp, ctypes.c_uint64, ctypes.POINTER(mc_result)]),

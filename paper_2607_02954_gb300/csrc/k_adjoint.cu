@@ -594,6 +594,100 @@ void launch_adj_step(const Plan& p, const WorldDev& h, AdjDev a, int src_parity,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Folding loss with an image target (Filament Folding experiment): mean
+// squared error between the Gaussian-splatted bead density at the final step
+// and a target image of R x R pixels covering the periodic domain.  Pixel
+// (px, py) has its centre at ((px + 1/2) W/R, (py + 1/2) H/R); a bead at
+// image coordinates u = (X R/W, Y R/H) adds exp(-|c - u|^2 / (2 s^2)) to the
+// pixels with px in floor(u_x) - K .. floor(u_x) + K (same in y, periodic),
+// K = ceil(4 s).  The image accumulates in 64-bit fixed point (2^-32 units),
+// so it does not depend on the order of the beads.
+// ---------------------------------------------------------------------------
+constexpr double kSplatScale = 4294967296.0;   // 2^32
+
+__device__ __forceinline__ float2 image_coords(const float4 p, float sx, float sy) {
+  return make_float2(((float)cell_x(p) + p.x) * sx, ((float)cell_y(p) + p.y) * sy);
+}
+
+__global__ void __launch_bounds__(256) k_splat_accum(const WorldDev* __restrict__ wd, int R, float sx, float sy,
+                                                     float inv2s2, int K, unsigned long long* __restrict__ acc) {
+  const WorldDev& w = *wd;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= w.N) return;
+  const float2 u = image_coords(w.pos[i], sx, sy);
+  const int bx = (int)floorf(u.x), by = (int)floorf(u.y);
+  for (int b = -K; b <= K; ++b) {
+    const float dy = (float)(by + b) + 0.5f - u.y;
+    const float gy = expf(-dy * dy * inv2s2);
+    const int row = ((by + b) % R + R) % R;
+    for (int a = -K; a <= K; ++a) {
+      const float dx = (float)(bx + a) + 0.5f - u.x;
+      const float g = gy * expf(-dx * dx * inv2s2);
+      const int col = ((bx + a) % R + R) % R;
+      atomicAdd(&acc[row * R + col], (unsigned long long)__double2ull_rn((double)g * kSplatScale));
+    }
+  }
+}
+
+// One block: diff = I - T per pixel and loss = mean(diff^2), summed in a fixed order.
+__global__ void __launch_bounds__(256) k_splat_loss(const unsigned long long* __restrict__ acc,
+                                                    const float* __restrict__ target, int RR, float* __restrict__ diff,
+                                                    float* loss) {
+  __shared__ float red[256];
+  float sum = 0.0f;
+  for (int q = threadIdx.x; q < RR; q += blockDim.x) {
+    const float d = (float)((double)acc[q] / kSplatScale) - target[q];
+    diff[q] = d;
+    sum = fmaf(d, d, sum);
+  }
+  red[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss[0] = red[0] / (float)RR;
+}
+
+// dL/dX_i = (2 / R^2) sum_c diff(c) dG(c - u_i)/du * du/dX, dG/du = G (c - u) / s^2.
+__global__ void __launch_bounds__(256) k_splat_grad(const WorldDev* __restrict__ wd, int R, float sx, float sy,
+                                                    float inv2s2, int K, const float* __restrict__ diff,
+                                                    float* __restrict__ gx, float* __restrict__ gy) {
+  const WorldDev& w = *wd;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= w.N) return;
+  const float2 u = image_coords(w.pos[i], sx, sy);
+  const int bx = (int)floorf(u.x), by = (int)floorf(u.y);
+  float ax = 0.0f, ay = 0.0f;
+  for (int b = -K; b <= K; ++b) {
+    const float dy = (float)(by + b) + 0.5f - u.y;
+    const float wy = expf(-dy * dy * inv2s2);
+    const int row = ((by + b) % R + R) % R;
+    for (int a = -K; a <= K; ++a) {
+      const float dx = (float)(bx + a) + 0.5f - u.x;
+      const float g = wy * expf(-dx * dx * inv2s2) * diff[row * R + ((bx + a) % R + R) % R];
+      ax = fmaf(g, dx, ax);
+      ay = fmaf(g, dy, ay);
+    }
+  }
+  // dG/du = G (c - u) / s^2 = 2 G (c - u) inv2s2
+  const float c = 2.0f / (float)(R * R) * 2.0f * inv2s2;
+  gx[i] = c * ax * sx;
+  gy[i] = c * ay * sy;
+}
+
+void launch_loss_splat(const Plan& p, const WorldDev& h, const float* target, int R, float sigma,
+                       unsigned long long* acc, float* diff, float* loss, float* gx, float* gy, cudaStream_t s) {
+  const int K = (int)ceilf(4.0f * sigma);
+  const float sx = (float)R / (float)h.W, sy = (float)R / (float)h.H;
+  const float inv2s2 = 1.0f / (2.0f * sigma * sigma);
+  cudaMemsetAsync(acc, 0, (size_t)R * R * sizeof(unsigned long long), s);
+  if (h.N) k_splat_accum<<<blocks(h.N), 256, 0, s>>>(p.d_worlds, R, sx, sy, inv2s2, K, acc);
+  k_splat_loss<<<1, 256, 0, s>>>(acc, target, R * R, diff, loss);
+  if (h.N) k_splat_grad<<<blocks(h.N), 256, 0, s>>>(p.d_worlds, R, sx, sy, inv2s2, K, diff, gx, gy);
+}
+
 void launch_loss_polyline(const Plan& p, const WorldDev& h, const float2* pos0, const float2* poly, int nv,
                           float* loss, float* gx, float* gy, cudaStream_t s) {
   cudaMemsetAsync(loss, 0, sizeof(float), s);

@@ -268,4 +268,24 @@ mc_status mc_loss_polyline(mc_world* w, const float* poly_xy, int n_vertices, fl
   return MC_OK;
 }
 
+mc_status mc_loss_splat(mc_world* w, const float* target, int R, float sigma, float* loss, float* dL_dx, float* dL_dy,
+                        void* stream) {
+  if (!w || !target || !loss) return afail(MC_ERR_INVALID_ARG, "need a world, a target image and a loss output");
+  if (R < 8 || R > 1024) return afail(MC_ERR_INVALID_ARG, "R must be in [8, 1024]");
+  if (!(sigma > 0.0f && sigma <= 4.0f)) return afail(MC_ERR_INVALID_ARG, "sigma must be in (0, 4] pixels");
+  const mc::WorldDev& h = w->h;
+  if (h.N && (!dL_dx || !dL_dy)) return afail(MC_ERR_INVALID_ARG, "NULL gradient pointer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t RR = (size_t)R * R;
+  void* scratch = nullptr;
+  MC_ACUDA(cudaMallocAsync(&scratch, RR * (sizeof(unsigned long long) + sizeof(float)), s));
+  auto* acc = static_cast<unsigned long long*>(scratch);
+  auto* diff = reinterpret_cast<float*>(acc + RR);
+  mc::launch_loss_splat(w->plan, h, target, R, sigma, acc, diff, loss, dL_dx, dL_dy, s);
+  const cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(scratch, s);
+  MC_ACUDA(e);
+  return MC_OK;
+}
+
 }  // extern "C"

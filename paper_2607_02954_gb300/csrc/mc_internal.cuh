@@ -139,6 +139,8 @@ constexpr int kKernelsPerStep = 8;
 // --- adjoint (one world) ----------------------------------------------------
 void launch_adj_step(const Plan& p, const WorldDev& h, AdjDev a, int src_parity, cudaStream_t s);
 size_t adj_pbd_smem_per_warp(int maxB, int n_pbd);
+void launch_loss_splat(const Plan& p, const WorldDev& h, const float* target, int R, float sigma,
+                       unsigned long long* acc, float* diff, float* loss, float* gx, float* gy, cudaStream_t s);
 void launch_loss_polyline(const Plan& p, const WorldDev& h, const float2* pos0, const float2* poly, int nv,
                           float* loss, float* gx, float* gy, cudaStream_t s);
 void launch_set_counter(const WorldDev& h, long long t, cudaStream_t s);

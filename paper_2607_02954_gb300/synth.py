@@ -402,3 +402,18 @@ def with_observables(spec: WorldSpec, seed: int, len_amp_max=0.2, period=(50.0, 
     spec.energy = energy_packets(rng, spec.H, spec.W, n_packets)
     spec.observe = True
     return spec
+
+
+def target_image(rng, R=128, n_strokes=3, width=2.5) -> np.ndarray:
+    """Seeded stand-in for a handwritten digit (the folding target): a few
+    smooth strokes, each a quadratic Bezier curve between random points in
+    the central part of an R x R image, drawn with a Gaussian profile of the
+    given width in pixels; values in [0, 1].  float32 [R, R]."""
+    ys, xs = np.meshgrid(np.arange(R) + 0.5, np.arange(R) + 0.5, indexing="ij")
+    img = np.zeros((R, R))
+    for _ in range(n_strokes):
+        P = rng.uniform(0.25 * R, 0.75 * R, (3, 2))
+        for t in np.linspace(0.0, 1.0, 4 * R):
+            c = (1 - t) ** 2 * P[0] + 2 * (1 - t) * t * P[1] + t ** 2 * P[2]
+            img = np.maximum(img, np.exp(-((xs - c[0]) ** 2 + (ys - c[1]) ** 2) / (2.0 * width ** 2)))
+    return img.astype(np.float32)

@@ -211,6 +211,21 @@ class World:
                                            ctypes.c_void_p(gy.data_ptr()), stream_handle(stream)))
         return loss, gx, gy
 
+    def loss_splat(self, target, sigma: float = 1.0, stream=None):
+        """The splat folding loss against an R x R target image (numpy or
+        torch); returns (loss tensor [1], dL_dx, dL_dy) on the GPU."""
+        torch = _torch()
+        tg = torch.as_tensor(np.ascontiguousarray(target, np.float32) if isinstance(target, np.ndarray) else target)
+        tg = tg.float().contiguous().cuda()
+        loss = torch.zeros(1, device="cuda", dtype=torch.float32)
+        gx = torch.empty(self.spec.N, device="cuda", dtype=torch.float32)
+        gy = torch.empty(self.spec.N, device="cuda", dtype=torch.float32)
+        L.check(self._lib.mc_loss_splat(self.handle, ctypes.c_void_p(tg.data_ptr()), int(tg.shape[0]),
+                                        float(sigma), ctypes.c_void_p(loss.data_ptr()),
+                                        ctypes.c_void_p(gx.data_ptr()), ctypes.c_void_p(gy.data_ptr()),
+                                        stream_handle(stream)))
+        return loss, gx, gy
+
     def field(self, name: str, stream=None) -> np.ndarray:
         """Host copy of one field of the last completed step (see mc_field)."""
         s = self.spec

@@ -186,3 +186,42 @@ def test_reverse_mode_rejects_red_black_pbd():
         w.rollout_backward(torch.zeros(spec.N, device="cuda"), torch.zeros(spec.N, device="cuda"))
     assert ei.value.status == 1
     w.close()
+
+
+@pytest.mark.parametrize("R,sigma", [(128, 1.0), (64, 2.3)])
+def test_splat_loss_and_gradient_match_oracle(R, sigma):
+    """mc_loss_splat on the creation positions: loss and its position
+    gradient against the oracle's autograd, 1e-5."""
+    from paper_2607_02954_gb300 import World
+    spec, _ = synth.world_c5(1)
+    target = synth.target_image(np.random.default_rng(2), R)
+    w = World(spec)
+    loss, gx, gy = w.loss_splat(target, sigma)
+    w.close()
+    X = torch.tensor(np.stack([spec.x, spec.y], 1), dtype=torch.float64, requires_grad=True)
+    want = O.splat_loss(X, torch.as_tensor(target, dtype=torch.float64), spec.H, spec.W, sigma)
+    (g,) = torch.autograd.grad(want, X)
+    assert abs(float(loss.item()) - float(want.detach())) <= 1e-5 * float(want.detach())
+    got = np.stack([t2n(gx), t2n(gy)], 1).astype(np.float64)
+    assert np.max(np.abs(got - t2n(g))) <= 1e-5 * np.max(np.abs(t2n(g)))
+
+
+def test_splat_folding_gradient_matches_oracle():
+    """The paper's folding objective end to end: rollout, splat loss at the
+    final step, reverse sweep; dL/dtheta0 against the oracle's reverse mode
+    through the whole rollout, 1e-3."""
+    from paper_2607_02954_gb300 import World
+    spec = synth.tiny_world(9, side=64, lengths=(30, 24))
+    R, sigma, n, K = 32, 1.0, 25, 8
+    target = synth.target_image(np.random.default_rng(9), R)
+    w = World(spec)
+    w.rollout_forward(n, K)
+    loss, gx, gy = w.loss_splat(target, sigma)
+    g = t2n(w.rollout_backward(gx, gy)).astype(np.float64)
+    w.close()
+    ow = O.World(spec)
+    th0 = ow.theta0.clone().requires_grad_(True)
+    want, _ = O.splat_folding_loss(ow, n, target, sigma, theta0=th0)
+    (go,) = torch.autograd.grad(want, th0)
+    assert abs(float(loss.item()) - float(want)) <= 1e-4 * float(want)
+    assert np.max(np.abs(g - t2n(go))) <= RTOL * np.max(np.abs(t2n(go)))

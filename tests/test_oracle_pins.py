@@ -714,6 +714,60 @@ def test_energy_sample_of_a_linear_field_is_the_field_at_the_bead():
     assert np.allclose(t2n(rec["e_bead"]), want, rtol=0, atol=1e-13)
 
 
+# ---------------------------------------------------------------------------
+# The splat folding loss (Filament Folding experiment).
+# ---------------------------------------------------------------------------
+def test_splat_of_one_bead_closed_form():
+    """A bead at a pixel centre: the pixel reads exp(0) = 1, the pixel
+    (a, b) away reads exp(-(a^2 + b^2) / (2 s^2)), the total is
+    (sum_k exp(-k^2 / (2 s^2)))^2 over |k| <= ceil(4 s), also across the
+    periodic seam."""
+    H = W = 64
+    R, s = 32, 1.3
+    K = int(math.ceil(4 * s))
+    g1 = sum(math.exp(-k * k / (2 * s * s)) for k in range(-K, K + 1))
+    for px, py in ((10, 20), (0, 31)):
+        X = torch.tensor([[(px + 0.5) * W / R, (py + 0.5) * H / R]], dtype=F64)
+        img = O.splat_image(X, H, W, R, s)
+        assert abs(float(img[py, px]) - 1.0) < 1e-15
+        assert abs(float(img[(py + 2) % R, (px - 1) % R]) - math.exp(-5 / (2 * s * s))) < 1e-15
+        assert abs(float(img.sum()) - g1 * g1) < 1e-12
+
+
+def test_splat_translates_with_the_bead():
+    """Moving every bead by one pixel (W/R cells) rolls the image by one pixel."""
+    H, W, R, s = 48, 64, 32, 0.9
+    rng = np.random.default_rng(3)
+    X = torch.tensor(np.stack([rng.uniform(0, W, 7), rng.uniform(0, H, 7)], 1), dtype=F64)
+    a = O.splat_image(X, H, W, R, s)
+    b = O.splat_image(X + torch.tensor([W / R, 0.0], dtype=F64), H, W, R, s)
+    assert torch.allclose(torch.roll(a, 1, dims=1), b, rtol=0, atol=1e-13)
+
+
+def test_splat_loss_gradient_matches_finite_differences():
+    H = W = 64
+    R, s = 32, 1.1
+    rng = np.random.default_rng(4)
+    X = torch.tensor(np.stack([rng.uniform(10, 50, 9), rng.uniform(10, 50, 9)], 1), dtype=F64, requires_grad=True)
+    target = torch.tensor(synth.target_image(rng, R), dtype=F64)
+    loss = O.splat_loss(X, target, H, W, s)
+    (g,) = torch.autograd.grad(loss, X)
+    eps = 1e-6
+    for i in range(3):
+        for k in range(2):
+            Xp = X.detach().clone()
+            Xm = X.detach().clone()
+            Xp[i, k] += eps
+            Xm[i, k] -= eps
+            fd = float(O.splat_loss(Xp, target, H, W, s) - O.splat_loss(Xm, target, H, W, s)) / (2 * eps)
+            assert abs(fd - float(g[i, k])) <= 1e-6 * abs(float(g[i, k])) + 1e-12
+    # the target equal to the splat of X: zero loss and zero gradient
+    own = O.splat_image(X.detach(), H, W, R, s)
+    l0 = O.splat_loss(X, own, H, W, s)
+    (g0,) = torch.autograd.grad(l0, X)
+    assert float(l0) == 0.0 and float(g0.abs().max()) == 0.0
+
+
 def _objective(w, n_steps, gx, gy, L_rest=None, ks=None):
     import copy
     import dataclasses
