@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define MC_ABI_VERSION 3
+#define MC_ABI_VERSION 4
 
 typedef enum mc_status {
   MC_OK = 0,
@@ -77,11 +77,20 @@ typedef enum mc_mem_kind { MC_MEM_HOST = 0, MC_MEM_DEVICE = 1 } mc_mem_kind;
  *            before it); 1: red-black passes (within each pass the joints or
  *            edges of even index in their filament first, then the odd ones
  *            from the updated state: a two-colour Gauss-Seidel sweep).  The
- *            reverse mode supports order 0 only. */
+ *            reverse mode supports order 0 only.
+ *   layers   1: the beads are the immersed-boundary points; 2: two-layer
+ *            filament (Fluid-filament Interaction): each bead couples to the
+ *            fluid at X +- layer_half n (n the filament's unit normal at the
+ *            bead), spreading half its force at each point and moving with
+ *            the mean of the two interpolated velocities; 0 < layer_half <= 2
+ *            cells.  The steric field stays on the beads.  The reverse mode
+ *            supports layers = 1 only. */
 typedef struct mc_params {
   float nu, dt, Lambda, kappa, k_bend, k_stretch, k_shear, k_rep, sigma, orient;
   int n_pbd;
   int pbd_order;
+  int layers;
+  float layer_half;
 } mc_params;
 
 /* The paper's statement of one world (Methods: filaments as graphs with

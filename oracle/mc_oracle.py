@@ -101,6 +101,8 @@ class Consts:
     orient: float
     n_pbd: int
     pbd_order: int = 0   # 0: Jacobi passes; 1: red-black (two-colour Gauss-Seidel) passes
+    layers: int = 1      # 1: beads are the immersed-boundary points; 2: two-layer filament
+    layer_half: float = 0.5   # half distance between the two layers (cells)
 
     @property
     def tau_plus(self) -> float:
@@ -120,7 +122,8 @@ def consts(params) -> Consts:
     return Consts(nu=r(params.nu), dt=r(params.dt), Lambda=r(params.Lambda), kappa=r(params.kappa),
                   k_bend=r(params.k_bend), k_stretch=r(params.k_stretch), k_shear=r(params.k_shear),
                   k_rep=r(params.k_rep), sigma=r(params.sigma), orient=r(params.orient),
-                  n_pbd=int(params.n_pbd), pbd_order=int(getattr(params, "pbd_order", 0)))
+                  n_pbd=int(params.n_pbd), pbd_order=int(getattr(params, "pbd_order", 0)),
+                  layers=int(getattr(params, "layers", 1)), layer_half=r(getattr(params, "layer_half", 0.5)))
 
 
 # ---------------------------------------------------------------------------
@@ -416,6 +419,36 @@ class World:
                      f=f, D=torch.zeros_like(X), t=int(s.t0))
 
 
+# ---------------------------------------------------------------------------
+# Two-layer filament (Fluid-filament Interaction: the single filament is
+# broadcast into a two-layer version of itself so that the fluid sees a solid
+# object).  Reading: the layers sit at X +- delta n, n the unit normal of the
+# filament at the bead.
+# ---------------------------------------------------------------------------
+def bead_normals(X: torch.Tensor, topo: Topology, H: int, W: int) -> torch.Tensor:
+    """n = (-t_y, t_x) with t the normalised sum of the unit vectors of the
+    bead's edges (its one edge at a filament end); where the two unit vectors
+    nearly cancel (|sum| < 1e-3, a chain folded back on itself) t is the
+    bead's outgoing edge, the incoming one at the last bead."""
+    N = X.shape[0]
+    xa, xb = X[topo.edge_a], X[topo.edge_b]
+    v = torch.stack([min_image(xb[:, 0] - xa[:, 0], W), min_image(xb[:, 1] - xa[:, 1], H)], 1)
+    vh = v / torch.sqrt((v * v).sum(1, keepdim=True))
+    out = torch.zeros(N, 2, dtype=F64).index_add(0, topo.edge_a, vh)
+    inc = torch.zeros(N, 2, dtype=F64).index_add(0, topo.edge_b, vh)
+    s = out + inc
+    ns = torch.sqrt((s * s).sum(1, keepdim=True))
+    has_out = torch.zeros(N, dtype=torch.bool)
+    has_out[topo.edge_a] = True
+    fallback = torch.where(has_out[:, None], out, inc)
+    t = torch.where(ns >= 1e-3, s / ns.clamp_min(1e-300), fallback)
+    return torch.stack([-t[:, 1], t[:, 0]], 1)
+
+
+def layer_point(X: torch.Tensor, n: torch.Tensor, d: float, H: int, W: int) -> torch.Tensor:
+    return torch.stack([wrap(X[:, 0] + d * n[:, 0], W), wrap(X[:, 1] + d * n[:, 1], H)], 1)
+
+
 def step(world: World, st: State, theta0: Optional[torch.Tensor] = None, record: bool = False):
     """One time step in the order a1..a8 (see the module docstring).
     theta0 may be given to differentiate with respect to the rest angles.
@@ -431,9 +464,20 @@ def step(world: World, st: State, theta0: Optional[torch.Tensor] = None, record:
     rho_bar = gaussian_blur(rho_s, c.sigma)                                            # a5
     grad = central_gradient(rho_bar)
     F_s = -c.k_rep * interpolate(idx, w, grad)                                          # a6
-    F = spread(idx, w, F_el + F_s, H, W)
-    f_new, u = lbm_step(st.f, F, c)                                                     # a7
-    U = interpolate(idx, w, u)                                                          # a8
+    if c.layers == 2:
+        # two-layer filament: each bead couples to the fluid at X +- delta n
+        # with half its force, and moves with the mean of the two velocities
+        nrm = bead_normals(st.X, topo, H, W)
+        ip, wp = stencil(layer_point(st.X, nrm, c.layer_half, H, W), H, W)
+        im, wm = stencil(layer_point(st.X, nrm, -c.layer_half, H, W), H, W)
+        half = 0.5 * (F_el + F_s)
+        F = spread(ip, wp, half, H, W) + spread(im, wm, half, H, W)
+        f_new, u = lbm_step(st.f, F, c)                                                 # a7
+        U = 0.5 * (interpolate(ip, wp, u) + interpolate(im, wm, u))                     # a8
+    else:
+        F = spread(idx, w, F_el + F_s, H, W)
+        f_new, u = lbm_step(st.f, F, c)                                                 # a7
+        U = interpolate(idx, w, u)                                                      # a8
     X_new = torch.stack([wrap(st.X[:, 0] + c.dt * U[:, 0], W), wrap(st.X[:, 1] + c.dt * U[:, 1], H)], 1)
     new = State(X=X_new, theta=theta_hat, f=f_new, D=st.D + c.dt * U, t=st.t + 1)
     rec = None

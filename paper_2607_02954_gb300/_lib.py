@@ -30,7 +30,8 @@ class MCError(RuntimeError):
 class mc_params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_float) for n in
                 ("nu", "dt", "Lambda", "kappa", "k_bend", "k_stretch", "k_shear", "k_rep", "sigma", "orient")] + \
-               [("n_pbd", ctypes.c_int), ("pbd_order", ctypes.c_int)]
+               [("n_pbd", ctypes.c_int), ("pbd_order", ctypes.c_int), ("layers", ctypes.c_int),
+                ("layer_half", ctypes.c_float)]
 
 
 _fp = ctypes.POINTER(ctypes.c_float)
@@ -102,7 +103,7 @@ SIGNATURES = {
 _lib = None
 
 
-ABI_VERSION = 3   # MC_ABI_VERSION of include/mc.h that these structures mirror
+ABI_VERSION = 4   # MC_ABI_VERSION of include/mc.h that these structures mirror
 
 
 def load():

@@ -64,6 +64,32 @@ __device__ __forceinline__ void edge_correction(float x, float y, float L, float
   th += k.ko * (cs * y - sn * x) / L;   // frame turns toward the edge (orient)
 }
 
+// Unit normal of the filament at a bead (two-layer coupling): t is the
+// normalised sum of the unit vectors of the bead's outgoing and incoming
+// edges; where they nearly cancel (|sum| < 1e-3, a chain folded back) t is
+// the outgoing edge, the incoming one at the last bead; n = (-t_y, t_x).
+__device__ __forceinline__ float2 unit2(float2 v) {
+  const float r = rsqrtf(v.x * v.x + v.y * v.y);
+  return make_float2(v.x * r, v.y * r);
+}
+
+__device__ __forceinline__ float2 bead_normal(float2 out, bool has_out, float2 in, bool has_in) {
+  float sx = 0.0f, sy = 0.0f;
+  if (has_out) {
+    sx += out.x;
+    sy += out.y;
+  }
+  if (has_in) {
+    sx += in.x;
+    sy += in.y;
+  }
+  const float ns = sqrtf(sx * sx + sy * sy);
+  float2 t;
+  if (ns >= 1e-3f) t = make_float2(sx / ns, sy / ns);
+  else t = has_out ? out : in;
+  return make_float2(-t.y, t.x);
+}
+
 // F_el = kappa (x_hat - X) / dt of one bead, its 8x8 bin (a2) and one
 // histogram atomic per group of lanes sharing a bin.  Every lane calls this.
 __device__ __forceinline__ void bead_out(const WorldDev& w, const PbdConst& k, bool valid, int b, const float4 P,
@@ -109,6 +135,16 @@ __device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, 
   Pn.w = __shfl_down_sync(kAll, P0.w, 1);
   const float2 v0 = edge_vec(P0, P1, k.W, k.H);
   const float2 v1 = edge_vec(P1, Pn, k.W, k.H);
+  if (w.layers == 2) {
+    // filament normals at beads 2l, 2l + 1 from X^n
+    const float2 z2 = make_float2(0.0f, 0.0f);
+    const float2 u0 = he0 ? unit2(v0) : z2, u1 = he1 ? unit2(v1) : z2;
+    float2 um;   // edge 2l - 1, incoming at bead 2l
+    um.x = __shfl_up_sync(kAll, u1.x, 1);
+    um.y = __shfl_up_sync(kAll, u1.y, 1);
+    if (hb0) w.nrm[b0 + i0] = bead_normal(u0, he0, um, lane > 0);
+    if (hb1) w.nrm[b0 + i1] = bead_normal(u1, he1, u0, true);
+  }
   float dlx0 = 0.0f, dly0 = 0.0f, dlx1 = 0.0f, dly1 = 0.0f;
   if (k.order == 1) {
     for (int iter = 0; iter < k.n_pbd; ++iter) {
@@ -233,6 +269,14 @@ __device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, 
     dly[i] = 0.0f;
   }
   __syncwarp();
+  if (w.layers == 2) {
+    for (int i = lane; i < B; i += 32) {
+      const float2 z2 = make_float2(0.0f, 0.0f);
+      const float2 out = i < nE ? unit2(make_float2(vx[i], vy[i])) : z2;
+      const float2 in = i > 0 ? unit2(make_float2(vx[i - 1], vy[i - 1])) : z2;
+      w.nrm[b0 + i] = bead_normal(out, i < nE, in, i > 0);
+    }
+  }
   if (k.order == 1) {
     // red-black passes: within a colour no two joints share an edge and no
     // two edges share a bead, so the lanes update in place
@@ -352,6 +396,103 @@ __global__ void __launch_bounds__(kBeadChunk) k_bin_scatter(const WorldDev* __re
   }
 }
 
+// ---------------------------------------------------------------------------
+// Two-layer filament (Fluid-filament Interaction): the immersed-boundary
+// points of bead i are X_i +- delta n_i.
+// ---------------------------------------------------------------------------
+// Cell and fraction of the point X + d n for X = (cell, fraction) in p.
+__device__ __forceinline__ void layer_cell(const float4 p, float2 n, float d, int W, int H, int& cx, int& cy,
+                                           float& fx, float& fy) {
+  fx = p.x + d * n.x;
+  fy = p.y + d * n.y;
+  const float kx = floorf(fx), ky = floorf(fy);
+  fx -= kx;
+  fy -= ky;
+  cx = cell_x(p) + (int)kx;
+  cy = cell_y(p) + (int)ky;
+  if (fx >= 1.0f) { fx = 0.0f; cx += 1; }
+  if (fy >= 1.0f) { fy = 0.0f; cy += 1; }
+  cx = wrap_once(cx, W);   // |d| <= 2 keeps the offset within one period (W, H >= 8)
+  cy = wrap_once(cy, H);
+}
+
+__device__ __forceinline__ float2 layer_velocity(const WorldDev& w, const float4 p, float2 n, float d) {
+  int cx, cy;
+  float fx, fy;
+  layer_cell(p, n, d, w.W, w.H, cx, cy, fx, fy);
+  float wx[4], wy[4];
+  peskin4(fx, wx);
+  peskin4(fy, wy);
+  float Ux = 0.0f, Uy = 0.0f;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const float2* row = w.u + (size_t)wrap_once(cy - 1 + b, w.H) * w.W;
+    float rx = 0.0f, ry = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const float2 v = row[wrap_once(cx - 1 + a, w.W)];
+      rx = fmaf(wx[a], v.x, rx);
+      ry = fmaf(wx[a], v.y, ry);
+    }
+    Ux = fmaf(wy[b], rx, Ux);
+    Uy = fmaf(wy[b], ry, Uy);
+  }
+  return make_float2(Ux, Uy);
+}
+
+constexpr double kLayerScale = 1099511627776.0;   // 2^40: fixed point of the layer spread
+
+// Spread of half of F_el + F_s at each layer point of every bead of
+// two-layer worlds, in 64-bit fixed point (bitwise independent of order).
+// Beads are read through the step's binned records, so the positions are
+// those at the start of the step even when the spread is re-run later.
+__global__ void __launch_bounds__(kBeadChunk) k_layer_spread(const WorldDev* __restrict__ worlds,
+                                                             const int2* __restrict__ items) {
+  const int2 it = items[blockIdx.x];
+  const WorldDev& w = worlds[it.x];
+  if (w.layers != 2) return;
+  const int slot = it.y + threadIdx.x;
+  if (slot >= w.N) return;
+  const int W = w.W, H = w.H;
+  const int i = w.sid[slot];
+  const float4 p = w.spos[slot];
+  const float2 n = w.nrm[i], fe = w.sfel[slot], fs = w.fs[i];
+  const float hx = 0.5f * (fe.x + fs.x), hy = 0.5f * (fe.y + fs.y);
+  for (int side = 0; side < 2; ++side) {
+    int cx, cy;
+    float fx, fy;
+    layer_cell(p, n, side ? -w.layer_half : w.layer_half, W, H, cx, cy, fx, fy);
+    float wx[4], wy[4];
+    peskin4(fx, wx);
+    peskin4(fy, wy);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      unsigned long long* row = w.facc + 2 * (size_t)wrap_once(cy - 1 + b, H) * W;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const float g = wx[a] * wy[b];
+        unsigned long long* c = row + 2 * wrap_once(cx - 1 + a, W);
+        atomicAdd(c, (unsigned long long)__double2ll_rn((double)(g * hx) * kLayerScale));
+        atomicAdd(c + 1, (unsigned long long)__double2ll_rn((double)(g * hy) * kLayerScale));
+      }
+    }
+  }
+}
+
+// F = the layer spread, and the accumulator cleared for the next step.
+__global__ void __launch_bounds__(kCellChunk) k_layer_finish(const WorldDev* __restrict__ worlds,
+                                                             const int2* __restrict__ items) {
+  const int2 it = items[blockIdx.x];
+  const WorldDev& w = worlds[it.x];
+  if (w.layers != 2) return;
+  const int c = it.y + threadIdx.x;
+  if (c >= w.H * w.W) return;
+  const long long ax = (long long)w.facc[2 * c], ay = (long long)w.facc[2 * c + 1];
+  w.F[c] = make_float2((float)((double)ax / kLayerScale), (float)((double)ay / kLayerScale));
+  w.facc[2 * c] = 0ull;
+  w.facc[2 * c + 1] = 0ull;
+}
+
 // a8: U_i = sum_c delta_h(c - X_i) u(c) over the 4x4 stencil, then the
 // inertia-free advance X += dt U (cell index + fraction, wrapped) and the
 // unwrapped displacement D += dt U.  Thread 0 of each world's first block
@@ -403,17 +544,25 @@ __global__ void __launch_bounds__(kBeadChunk, 8) k_interp_advance(const WorldDev
     iy[a] = wrap_once(cy - 1 + a, H) * W;
   }
   float Ux = 0.0f, Uy = 0.0f;
+  if (w.layers == 2) {
+    // two-layer filament: mean of the velocities at X +- delta n
+    const float2 n = w.nrm[i];
+    const float2 Up = layer_velocity(w, p, n, w.layer_half), Um = layer_velocity(w, p, n, -w.layer_half);
+    Ux = 0.5f * (Up.x + Um.x);
+    Uy = 0.5f * (Up.y + Um.y);
+  } else {
 #pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    float rx = 0.0f, ry = 0.0f;
+    for (int b = 0; b < 4; ++b) {
+      float rx = 0.0f, ry = 0.0f;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const float2 v = w.u[iy[b] + ix[a]];
-      rx = fmaf(wx[a], v.x, rx);
-      ry = fmaf(wx[a], v.y, ry);
+      for (int a = 0; a < 4; ++a) {
+        const float2 v = w.u[iy[b] + ix[a]];
+        rx = fmaf(wx[a], v.x, rx);
+        ry = fmaf(wx[a], v.y, ry);
+      }
+      Ux = fmaf(wy[b], rx, Ux);
+      Uy = fmaf(wy[b], ry, Uy);
     }
-    Ux = fmaf(wy[b], rx, Ux);
-    Uy = fmaf(wy[b], ry, Uy);
   }
   w.ubead[i] = make_float2(Ux, Uy);
   const float m2 = Ux * Ux + Uy * Uy;
@@ -508,6 +657,12 @@ void launch_pbd(const Plan& p, cudaStream_t s) {
 
 void launch_bin_scatter(const Plan& p, cudaStream_t s) {
   k_bin_scatter<<<p.n_bead_items, kBeadChunk, 0, s>>>(p.d_worlds, p.d_bead_items);
+}
+
+void launch_layer_spread(const Plan& p, cudaStream_t s) {
+  if (!p.any_layered) return;
+  k_layer_spread<<<p.n_bead_items, kBeadChunk, 0, s>>>(p.d_worlds, p.d_bead_items);
+  if (p.n_cell_items) k_layer_finish<<<p.n_cell_items, kCellChunk, 0, s>>>(p.d_worlds, p.d_cell_items);
 }
 
 void launch_interp_advance(const Plan& p, cudaStream_t s) {

@@ -95,9 +95,10 @@ __global__ void __launch_bounds__(256) k_scan_apply(const WorldDev* __restrict__
 // evaluated per opposite pair (i, opp(i)) from the even and odd parts.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kCellChunk) k_lbm(const WorldDev* __restrict__ worlds,
-                                                    const int2* __restrict__ items) {
+                                                    const int2* __restrict__ items, int layered_only) {
   const int2 it = items[blockIdx.x];
   const WorldDev& w = worlds[it.x];
+  if (layered_only && w.layers != 2) return;
   const int W = w.W, H = w.H, HW = H * W;
   const int c = it.y + threadIdx.x;
   if (c >= HW) return;
@@ -117,8 +118,8 @@ void launch_bin_scan(const Plan& p, cudaStream_t s) {
   k_scan_apply<<<p.n_scan_items, 256, 0, s>>>(p.d_worlds, p.d_scan_items);
 }
 
-void launch_lbm(const Plan& p, cudaStream_t s) {
-  if (p.n_cell_items) k_lbm<<<p.n_cell_items, kCellChunk, 0, s>>>(p.d_worlds, p.d_cell_items);
+void launch_lbm(const Plan& p, cudaStream_t s, int layered_only) {
+  if (p.n_cell_items) k_lbm<<<p.n_cell_items, kCellChunk, 0, s>>>(p.d_worlds, p.d_cell_items, layered_only);
 }
 
 void enqueue_step(const Plan& p, cudaStream_t s) {

@@ -432,6 +432,7 @@ __device__ __forceinline__ int force_tile(ForceSmem<R>& sm, const WorldDev& w, i
   float* __restrict__ rho_b = w.rho_b;
   const float k_rep = w.k_rep;
   const float fmax_el = __uint_as_float(w.fel_max[(*w.t - after_step) & 1]);
+  const bool layered = w.layers == 2;
   const int x0 = tb.x0, y0 = tb.y0, tw = tb.tw, th = tb.th;
   const int tx = x0 / kTile, ty = y0 / kTile;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -551,6 +552,7 @@ __device__ __forceinline__ int force_tile(ForceSmem<R>& sm, const WorldDev& w, i
       }
       const float Fsx = -0.5f * k_rep * gsx, Fsy = -0.5f * k_rep * gsy;
       if (rx >= 0 && rx < tw && ry >= 0 && ry < th) fs_out[sm.si[v]] = make_float2(Fsx, Fsy);
+      if (layered) continue;   // two-layer worlds spread at their layer points (k_layer_spread)
       const float2 fe = sm.sf[v];
       const float Fx = (fe.x + Fsx) * scale, Fy = (fe.y + Fsy) * scale;
       float ax[4], ay[4];
@@ -657,7 +659,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_force_lbm(const WorldDev* __res
   float* __restrict__ dst = w.g[(t + 1) & 1];
   float2* __restrict__ u_out = w.u;
   const LbmConst kc{w.om_p, w.om_m, w.src_p, w.src_m};
-  {
+  const bool layered = w.layers == 2;
+  if (!layered) {
     // start the DRAM reads of the collision now: the 128-byte row segments
     // that the tile's cells pull from (plane i, rows y - c_iy) go to L2
     // while the force phase runs
@@ -671,6 +674,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_force_lbm(const WorldDev* __res
     }
   }
   const int k = force_tile<R>(sm, w, (tb.y0 / kTile) * w.ntx + tb.x0 / kTile, tb, 0, 0);
+  if (layered) return;   // F_s only: the layer spread and the collision follow in their own kernels
   const float inv = pow2f(-k);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // each warp collides rows warp, warp + 8, ... of the tile; the populations
@@ -728,10 +732,18 @@ void dispatch_steric(const Plan& p, cudaStream_t s, int which, int store_fields,
 
 void launch_deposit_x(const Plan& p, cudaStream_t s, int store_fields) { dispatch_steric(p, s, 0, store_fields, 0); }
 
+// Two-layer worlds get F from their layer points after the tile pass.
 void launch_force_spread(const Plan& p, cudaStream_t s, int store_fields, int after_step) {
   dispatch_steric(p, s, 1, store_fields, after_step);
+  launch_layer_spread(p, s);
 }
 
-void launch_force_lbm(const Plan& p, cudaStream_t s) { dispatch_steric(p, s, 2, 0, 0); }
+void launch_force_lbm(const Plan& p, cudaStream_t s) {
+  dispatch_steric(p, s, 2, 0, 0);
+  if (p.any_layered) {
+    launch_layer_spread(p, s);
+    launch_lbm(p, s, 1);
+  }
+}
 
 }  // namespace mc

@@ -79,6 +79,9 @@ mc_status validate_params(const mc_params& p) {
   if (!(p.sigma > 0.0f && p.sigma <= 2.0f)) return fail(MC_ERR_INVALID_ARG, "sigma must be in (0, 2]");
   if (p.n_pbd < 0 || p.n_pbd > mc::kMaxNpbd) return fail(MC_ERR_INVALID_ARG, "n_pbd must be in [0, 64]");
   if (p.pbd_order != 0 && p.pbd_order != 1) return fail(MC_ERR_INVALID_ARG, "pbd_order must be 0 or 1");
+  if (p.layers != 1 && p.layers != 2) return fail(MC_ERR_INVALID_ARG, "layers must be 1 or 2");
+  if (p.layers == 2 && !(p.layer_half > 0.0f && p.layer_half <= 2.0f))
+    return fail(MC_ERR_INVALID_ARG, "layer_half must be in (0, 2] cells");
   return MC_OK;
 }
 
@@ -94,6 +97,8 @@ void fill_constants(WorldDev& h, const mc_params& p) {
   h.orient = p.orient;
   h.n_pbd = p.n_pbd;
   h.pbd_order = p.pbd_order;
+  h.layers = p.layers;
+  h.layer_half = p.layer_half;
   h.om_p = (float)(1.0 / tau_p);
   h.om_m = (float)(1.0 / tau_m);
   h.src_p = (float)(1.0 - 0.5 / tau_p);
@@ -120,6 +125,7 @@ mc_status build_plan(mc_world* const* ws, int n, cudaStream_t s, Plan& out) {
   Plan p;
   p.n_worlds = n;
   p.max_R = 1;
+  p.any_layered = false;
   std::vector<int2> fil, bead, tile, cell, scan;
   std::vector<WorldDev> table(n);
   for (int k = 0; k < n; ++k) {
@@ -127,6 +133,7 @@ mc_status build_plan(mc_world* const* ws, int n, cudaStream_t s, Plan& out) {
     table[k] = w->h;
     p.max_B = std::max(p.max_B, w->max_B);
     p.max_R = std::max(p.max_R, w->h.R);
+    p.any_layered = p.any_layered || w->h.layers == 2;
     for (int f = 0; f < w->h.n_fil; ++f) fil.push_back(make_int2(k, f));
     const int nb = std::max(w->h.N, 1);
     for (int b = 0; b < nb; b += mc::kBeadChunk) bead.push_back(make_int2(k, b));
@@ -283,6 +290,8 @@ size_t world_layout(WorldDev& h, void* A) {
   const size_t o_en = L.take<float>(h.has_energy ? HW : 0);
   const size_t o_eb = L.take<float>(h.has_energy ? N : 0);
   const size_t o_ob = L.take<unsigned long long>(3);
+  const size_t o_nr = L.take<float2>(h.layers == 2 ? N : 0);
+  const size_t o_fa = L.take<unsigned long long>(h.layers == 2 ? 2 * HW : 0);
   if (!A) return L.off;
   h.fil_off = at<int>(A, o_fo);
   h.pos = at<float4>(A, o_pos);
@@ -317,6 +326,8 @@ size_t world_layout(WorldDev& h, void* A) {
   h.energy = h.has_energy ? at<float>(A, o_en) : nullptr;
   h.ebead = h.has_energy ? at<float>(A, o_eb) : nullptr;
   h.obs = at<unsigned long long>(A, o_ob);
+  h.nrm = h.layers == 2 ? at<float2>(A, o_nr) : nullptr;
+  h.facc = h.layers == 2 ? at<unsigned long long>(A, o_fa) : nullptr;
   return L.off;
 }
 
@@ -346,6 +357,8 @@ mc_status mc_params_default(mc_params* p) {
   p->orient = 1.0f;
   p->n_pbd = 4;
   p->pbd_order = 0;
+  p->layers = 1;
+  p->layer_half = 0.5f;
   return MC_OK;
 }
 

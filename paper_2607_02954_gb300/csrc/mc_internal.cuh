@@ -73,6 +73,10 @@ struct WorldDev {
   unsigned* flags;        // watchdog flags
   // optional inputs and search-side observables
   int has_ldrive, has_energy, observe;
+  int layers;             // 1 or 2 (two-layer filament)
+  float layer_half;       // half distance between the layers (cells)
+  float2* nrm;            // [N] filament unit normal at each bead (layers == 2)
+  unsigned long long* facc;  // [2 H W] fixed-point spread of the layer points (layers == 2)
   const float4* ldrive;   // [E] (L0, amp, freq, phase) rest-length drive, or nullptr (static L_rest)
   const float* energy;    // [H * W] energy field, or nullptr
   float* ebead;           // [N] energy sampled at each bead (observe and energy)
@@ -109,6 +113,7 @@ struct Plan {
   int n_worlds = 0;
   int max_B = 2;
   int max_R = 4;                 // largest Gaussian half width among the worlds
+  bool any_layered = false;      // some world is a two-layer filament world
   int n_fil_items = 0, n_bead_items = 0, n_tile_items = 0, n_cell_items = 0, n_scan_items = 0;
   WorldDev* d_worlds = nullptr;  // [n_worlds]
   int2* d_fil_items = nullptr;   // (world, filament)
@@ -130,7 +135,8 @@ void launch_deposit_x(const Plan& p, cudaStream_t s, int store_fields);
 // y pass of a5 + a6; store_fields also writes rho_bar of each tile;
 // after_step = 1 when re-run after the step that produced the binned beads
 void launch_force_spread(const Plan& p, cudaStream_t s, int store_fields, int after_step = 0);
-void launch_lbm(const Plan& p, cudaStream_t s);
+void launch_lbm(const Plan& p, cudaStream_t s, int layered_only = 0);   // layered_only: two-layer worlds only
+void launch_layer_spread(const Plan& p, cudaStream_t s);   // two-layer worlds: F from the layer points
 void launch_force_lbm(const Plan& p, cudaStream_t s);   // y pass of a5 + a6 + a7 in one kernel
 void launch_interp_advance(const Plan& p, cudaStream_t s);
 void enqueue_step(const Plan& p, cudaStream_t s);

@@ -117,11 +117,12 @@ struct mc_server {
 
 namespace {
 
-size_t footprint(int H, int W, int n_fil, int N, bool ldrive, bool energy) {
+size_t footprint(int H, int W, int n_fil, int N, bool ldrive, bool energy, int layers) {
   mc::WorldDev h{};
   mc::world_sizes(h, H, W, n_fil, N);
   h.has_ldrive = ldrive;
   h.has_energy = energy;
+  h.layers = layers;
   // arena plus this world's share of a plan (work items and table entry)
   const size_t items = (size_t)n_fil + (N / mc::kBeadChunk + 1) + h.n_tiles + (size_t)H * W / mc::kCellChunk + 1 +
                        h.n_chunks;
@@ -364,7 +365,7 @@ mc_status mc_serve_submit(mc_server* s, const mc_world_desc* d, int n_steps, uin
   r.observe = d->observe;
   r.t0 = d->t0;
   r.p = d->p;
-  r.bytes = footprint(d->H, d->W, d->n_fil, N, d->len_amp != nullptr, d->energy != nullptr);
+  r.bytes = footprint(d->H, d->W, d->n_fil, N, d->len_amp != nullptr, d->energy != nullptr, d->p.layers);
   r.t_submit = now_ns();
   std::lock_guard<std::mutex> lk(s->mu);
   if ((int)s->pending.size() >= s->cfg.max_pending) return serve_fail(MC_ERR_BUSY, "request queue is full");

@@ -46,6 +46,8 @@ class Params:
             literal reading where only positions move.
     n_pbd: PBD iterations (bend pass + position pass) per time step.
     pbd_order: 0 Jacobi passes, 1 red-black (two-colour Gauss-Seidel) passes.
+    layers: 1 = the beads are the immersed-boundary points; 2 = two-layer
+            filament, points at X +- layer_half n (n the filament normal).
     """
 
     nu: float = 0.1
@@ -60,6 +62,8 @@ class Params:
     orient: float = 1.0
     n_pbd: int = 4
     pbd_order: int = 0
+    layers: int = 1
+    layer_half: float = 0.5
 
 
 @dataclasses.dataclass

@@ -31,7 +31,8 @@ def params_struct(p: Params) -> L.mc_params:
     return L.mc_params(nu=p.nu, dt=p.dt, Lambda=p.Lambda, kappa=p.kappa, k_bend=p.k_bend,
                        k_stretch=p.k_stretch, k_shear=p.k_shear, k_rep=p.k_rep, sigma=p.sigma,
                        orient=p.orient, n_pbd=int(p.n_pbd),
-                       pbd_order=int(getattr(p, "pbd_order", 0)))
+                       pbd_order=int(getattr(p, "pbd_order", 0)), layers=int(getattr(p, "layers", 1)),
+                       layer_half=float(getattr(p, "layer_half", 0.5)))
 
 
 def default_params() -> Params:

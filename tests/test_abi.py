@@ -62,7 +62,8 @@ def _desc(spec, **over):
 
 
 @pytest.mark.parametrize("case", ["H_not_mult8", "W_small", "short_filament", "nan_x", "bad_nu",
-                                  "bad_sigma", "neg_L", "bad_t0", "bad_npbd", "bad_pbd_order"])
+                                  "bad_sigma", "neg_L", "bad_t0", "bad_npbd", "bad_pbd_order",
+                                  "bad_layers", "bad_layer_half"])
 def test_create_rejects_invalid_worlds_on_host(case):
     spec = synth.tiny_world(0, side=16, lengths=(5, 4))
     over = {}
@@ -88,6 +89,10 @@ def test_create_rejects_invalid_worlds_on_host(case):
         over["params"] = synth.Params(n_pbd=65)
     elif case == "bad_pbd_order":
         over["params"] = synth.Params(pbd_order=2)
+    elif case == "bad_layers":
+        over["params"] = synth.Params(layers=3)
+    elif case == "bad_layer_half":
+        over["params"] = synth.Params(layers=2, layer_half=0.0)
     d, keep = _desc(spec, **over)
     h = ctypes.c_void_p()
     lib = L.load()

@@ -119,7 +119,8 @@ def test_one_step_random_fluid_and_late_drive():
 
 
 @pytest.mark.parametrize("case", ["tiny8", "ragged", "single_dimer", "no_filaments", "long_filament",
-                                  "custom_params", "dense_rows", "red_black", "red_black_long"])
+                                  "custom_params", "dense_rows", "red_black", "red_black_long", "two_layer",
+                                  "two_layer_long", "two_layer_small"])
 def test_one_step_edge_cases(case):
     rng = np.random.default_rng(1)
     if case == "tiny8":
@@ -135,6 +136,15 @@ def test_one_step_edge_cases(case):
         spec.f0 = synth.random_populations(rng, 24, 16, 1e-3)
     elif case == "long_filament":
         spec = synth.world_random(11, 256, 2, lengths=[1500, 40])
+    elif case == "two_layer":
+        spec = synth.world_random(15, 128, 20)
+        spec.params = synth.Params(layers=2, layer_half=0.8)
+    elif case == "two_layer_long":
+        spec = synth.world_random(16, 256, 3, lengths=[900, 50, 2])
+        spec.params = synth.Params(layers=2, layer_half=1.7, pbd_order=1)
+    elif case == "two_layer_small":
+        spec = synth.tiny_world(17, side=16, lengths=(7, 5))
+        spec.params = synth.Params(layers=2, layer_half=2.0)
     elif case == "red_black":
         spec = synth.world_random(13, 128, 24)
         spec.params = synth.Params(k_bend=0.8, k_stretch=0.7, k_shear=0.5, pbd_order=1, n_pbd=5)
@@ -254,6 +264,7 @@ def test_batched_equals_alone_bitwise():
     specs = [synth.world_random(s, side, nf) for s, side, nf in
              [(1, 64, 3), (2, 128, 17), (3, 64, 1), (4, 256, 40), (5, 128, 8)]]
     specs[2].params = synth.Params(pbd_order=1, sigma=0.6)   # a red-black world with a narrower filter
+    specs[3].params = synth.Params(layers=2, layer_half=0.9)  # a two-layer world
     alone = []
     for sp in specs:
         w = _gpu_world(sp)
@@ -271,8 +282,8 @@ def test_batched_equals_alone_bitwise():
         w.close()
 
 
-@pytest.mark.parametrize("side", [128, 40, 24])
-def test_stage_sequences_equal_the_step_bitwise(side):
+@pytest.mark.parametrize("side,layers", [(128, 1), (40, 1), (24, 1), (64, 2)])
+def test_stage_sequences_equal_the_step_bitwise(side, layers):
     """mc_step runs the fused spread + LBM kernel (stage 7); stages 0..6 run
     the same step with F through device memory (stages 4 and 5).  Both, and
     the fused stage sequence 0, 1, 2, 3, 7, 6, give the same world bitwise."""
@@ -280,6 +291,7 @@ def test_stage_sequences_equal_the_step_bitwise(side):
     from paper_2607_02954_gb300 import _lib
     lib = _lib.load()
     spec = synth.world_random(7, side, 6 if side < 64 else 20)
+    spec.params = synth.Params(layers=layers, layer_half=1.1)
     sh = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     worlds = [_gpu_world(spec) for _ in range(3)]
     for _ in range(5):

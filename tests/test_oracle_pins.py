@@ -14,7 +14,7 @@ import torch
 
 import oracle as O
 from paper_2607_02954_gb300 import synth
-from tests.helpers import t2n
+from tests.helpers import oracle_one_step, t2n
 
 F64 = torch.float64
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -766,6 +766,58 @@ def test_splat_loss_gradient_matches_finite_differences():
     l0 = O.splat_loss(X, own, H, W, s)
     (g0,) = torch.autograd.grad(l0, X)
     assert float(l0) == 0.0 and float(g0.abs().max()) == 0.0
+
+
+# ---------------------------------------------------------------------------
+# Two-layer filament.
+# ---------------------------------------------------------------------------
+def test_bead_normals_closed_form():
+    """A straight chain at angle phi has normal (-sin phi, cos phi) at every
+    bead; a right-angle corner has the bisector's normal (-1, 1)/sqrt 2; a
+    chain folded back on itself takes its outgoing edge."""
+    phi = 0.7
+    xs = 5.0 + np.arange(5) * math.cos(phi)
+    ys = 6.0 + np.arange(5) * math.sin(phi)
+    topo, X = _chain(xs, ys)
+    n = t2n(O.bead_normals(X, topo, 32, 32))
+    assert np.allclose(n, [[-math.sin(phi), math.cos(phi)]] * 5, rtol=0, atol=1e-14)
+    topo, X = _chain([5.0, 6.0, 6.0], [5.0, 5.0, 6.0])
+    n = t2n(O.bead_normals(X, topo, 32, 32))
+    assert np.allclose(n[1], [-1 / math.sqrt(2), 1 / math.sqrt(2)], rtol=0, atol=1e-15)
+    topo, X = _chain([5.0, 6.0, 5.0], [5.0, 5.0, 5.0])
+    n = t2n(O.bead_normals(X, topo, 32, 32))
+    assert np.allclose(n[0], [0.0, 1.0], rtol=0, atol=1e-15)    # edge (1, 0)
+    assert np.allclose(n[1], [0.0, -1.0], rtol=0, atol=1e-15)   # folded: its outgoing edge (-1, 0)
+    assert np.allclose(n[2], [0.0, -1.0], rtol=0, atol=1e-15)   # last bead: incoming edge (-1, 0)
+
+
+def test_two_layers_at_zero_separation_equal_one_layer():
+    spec = synth.tiny_world(4, side=32, lengths=(9, 6))
+    one = oracle_one_step(spec)[3]
+    spec.params = synth.Params(layers=2, layer_half=0.0)
+    two = oracle_one_step(spec)[3]
+    for k in ("F", "u", "U"):
+        assert torch.allclose(one[k], two[k], rtol=0, atol=1e-15), k
+
+
+def test_two_layer_coupling_keeps_momentum_and_reproduces_linear_flow():
+    """The spread force sums to the beads' total force, and the mean of the
+    two layer velocities of a linear velocity field is its value at the bead."""
+    spec = synth.tiny_world(5, side=48, lengths=(12, 9))
+    spec.params = synth.Params(layers=2, layer_half=1.3)
+    _, st0, _, rec = oracle_one_step(spec)
+    tot = (rec["F_el"] + rec["F_s"]).sum(0)
+    assert torch.allclose(rec["F"].sum((1, 2)), tot, rtol=0, atol=1e-13)
+    w = O.World(spec)
+    nrm = O.bead_normals(st0.X, w.topo, 48, 48)
+    ys, xs = torch.meshgrid(torch.arange(48, dtype=F64), torch.arange(48, dtype=F64), indexing="ij")
+    u = torch.stack([0.01 * xs - 0.02 * ys + 0.1, 0.03 * xs + 0.005 * ys], 0)
+    ip, wp = O.stencil(O.layer_point(st0.X, nrm, 1.3, 48, 48), 48, 48)
+    im, wm = O.stencil(O.layer_point(st0.X, nrm, -1.3, 48, 48), 48, 48)
+    U = 0.5 * (O.interpolate(ip, wp, u) + O.interpolate(im, wm, u))
+    X = st0.X
+    want = torch.stack([0.01 * X[:, 0] - 0.02 * X[:, 1] + 0.1, 0.03 * X[:, 0] + 0.005 * X[:, 1]], 1)
+    assert torch.allclose(U, want, rtol=0, atol=1e-13)
 
 
 def _objective(w, n_steps, gx, gy, L_rest=None, ks=None):
