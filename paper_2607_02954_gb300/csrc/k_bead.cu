@@ -110,6 +110,7 @@ __device__ __forceinline__ void bead_out(const WorldDev& w, const PbdConst& k, b
 // Jacobi PBD of a filament of at most 64 beads in registers: lane l holds
 // beads, edges and joints 2l and 2l + 1, and reads its neighbours' values by
 // warp shuffles.  The same arithmetic, in the same order, as pbd_smem.
+template <bool kExt>
 __device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, int b0, int B, int e0, int j0,
                                           long long t) {
   constexpr unsigned kAll = 0xffffffffu;
@@ -122,12 +123,10 @@ __device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, 
   const float4 P1 = hb1 ? w.pos[b0 + i1] : z4;
   float th0 = he0 ? w.theta[e0 + i0] : 0.0f;
   float th1 = he1 ? w.theta[e0 + i1] : 0.0f;
-  const float L0 = he0 ? rest_length(w, e0 + i0, t) : 1.0f;
-  const float L1 = he1 ? rest_length(w, e0 + i1, t) : 1.0f;
-  const float4 z4d = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  const float4 D0 = hj0 ? w.drive[j0 + i0] : z4d, D1 = hj1 ? w.drive[j0 + i1] : z4d;
-  const float thr0 = hj0 ? drive_angle(D0, t) : 0.0f;
-  const float thr1 = hj1 ? drive_angle(D1, t) : 0.0f;
+  const float L0 = he0 ? (kExt ? rest_length(w, e0 + i0, t) : w.L_rest[e0 + i0]) : 1.0f;
+  const float L1 = he1 ? (kExt ? rest_length(w, e0 + i1, t) : w.L_rest[e0 + i1]) : 1.0f;
+  const float thr0 = hj0 ? drive_angle(w.drive[j0 + i0], t) : 0.0f;
+  const float thr1 = hj1 ? drive_angle(w.drive[j0 + i1], t) : 0.0f;
   float4 Pn;   // bead 2l + 2
   Pn.x = __shfl_down_sync(kAll, P0.x, 1);
   Pn.y = __shfl_down_sync(kAll, P0.y, 1);
@@ -135,7 +134,7 @@ __device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, 
   Pn.w = __shfl_down_sync(kAll, P0.w, 1);
   const float2 v0 = edge_vec(P0, P1, k.W, k.H);
   const float2 v1 = edge_vec(P1, Pn, k.W, k.H);
-  if (w.layers == 2) {
+  if (kExt && w.layers == 2) {
     // filament normals at beads 2l, 2l + 1 from X^n
     const float2 z2 = make_float2(0.0f, 0.0f);
     const float2 u0 = he0 ? unit2(v0) : z2, u1 = he1 ? unit2(v1) : z2;
@@ -212,12 +211,12 @@ __device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, 
   float fmax = 0.0f;
   bead_out(w, k, hb0, b0 + i0, P0, dlx0, dly0, fmax);
   bead_out(w, k, hb1, b0 + i1, P1, dlx1, dly1, fmax);
-  if (w.observe && t >= 1) {
+  if (kExt && w.observe && t >= 1) {
     // behaviour descriptors (Eqs. 5, 6): squared change of the rest angles
     // and rest lengths from step t - 1 to step t
     float eb = 0.0f, ep = 0.0f;
-    if (hj0) eb += sq(drive_angle(D0, t - 1) - thr0);
-    if (hj1) eb += sq(drive_angle(D1, t - 1) - thr1);
+    if (hj0) eb += sq(drive_angle(w.drive[j0 + i0], t - 1) - thr0);
+    if (hj1) eb += sq(drive_angle(w.drive[j0 + i1], t - 1) - thr1);
     if (w.ldrive) {
       if (he0) ep += sq(rest_length(w, e0 + i0, t - 1) - L0);
       if (he1) ep += sq(rest_length(w, e0 + i1, t - 1) - L1);
@@ -232,6 +231,7 @@ __device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, 
 // bead corrections live in a per-warp slice of shared memory; every pass
 // reads the slice, then writes corrections, with a warp barrier in between,
 // so all corrections of a pass see the state before it.
+template <bool kExt>
 __device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, int b0, int B, int e0, int j0,
                                           long long t, float* s, int maxB) {
   const int lane = threadIdx.x & 31;
@@ -252,7 +252,7 @@ __device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, 
   for (int i = lane; i < B; i += 32) cpa16(&P[i], &w.pos[b0 + i]);
   for (int e = lane; e < nE; e += 32) {
     cpa4(&th[e], &w.theta[e0 + e]);
-    if (!w.ldrive) cpa4(&Lr[e], &w.L_rest[e0 + e]);
+    if (!kExt || !w.ldrive) cpa4(&Lr[e], &w.L_rest[e0 + e]);
     else Lr[e] = drive_length(w.ldrive[e0 + e], t);
   }
   for (int j = lane; j < nJ; j += 32) cpa16(&D[j], &w.drive[j0 + j]);
@@ -269,7 +269,7 @@ __device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, 
     dly[i] = 0.0f;
   }
   __syncwarp();
-  if (w.layers == 2) {
+  if (kExt && w.layers == 2) {
     for (int i = lane; i < B; i += 32) {
       const float2 z2 = make_float2(0.0f, 0.0f);
       const float2 out = i < nE ? unit2(make_float2(vx[i], vy[i])) : z2;
@@ -333,7 +333,7 @@ __device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, 
     bead_out(w, k, i < B, b0 + i, i < B ? P[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f), i < B ? dlx[i] : 0.0f,
              i < B ? dly[i] : 0.0f, fmax);
   }
-  if (w.observe && t >= 1) {
+  if (kExt && w.observe && t >= 1) {
     float eb = 0.0f, ep = 0.0f;
     for (int j = lane; j < nJ; j += 32) eb += sq(drive_angle(D[j], t - 1) - thr[j]);
     if (w.ldrive)
@@ -350,6 +350,7 @@ __device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, 
 // coordinates.  Filaments of at most 64 beads run in registers; longer ones
 // in the warp's slice of dynamic shared memory (maxB floats per array; zero
 // when no filament of the launch is longer than 64 beads).
+template <bool kExt>
 __global__ void __launch_bounds__(256) k_pbd(const WorldDev* __restrict__ worlds,
                                              const int2* __restrict__ items, int n_items, int maxB) {
   extern __shared__ __align__(16) float smem[];   // maxB is a multiple of 4: float4 slices stay aligned
@@ -365,8 +366,8 @@ __global__ void __launch_bounds__(256) k_pbd(const WorldDev* __restrict__ worlds
   const int e0 = b0 - f, j0 = b0 - 2 * f;
   const long long t = *w.t;
   const PbdConst k = pbd_const(w);
-  float fmax = B <= 64 ? pbd_regs(w, k, b0, B, e0, j0, t)
-                       : pbd_smem(w, k, b0, B, e0, j0, t, smem + (size_t)warp * maxB * kPbdFloatsPerBead, maxB);
+  float fmax = B <= 64 ? pbd_regs<kExt>(w, k, b0, B, e0, j0, t)
+                       : pbd_smem<kExt>(w, k, b0, B, e0, j0, t, smem + (size_t)warp * maxB * kPbdFloatsPerBead, maxB);
   // largest |F_el| component of the world this step (bounds the spread's
   // fixed-point scale); non-negative floats order like their bit patterns
   for (int o = 16; o > 0; o >>= 1) fmax = fmaxf(fmax, __shfl_xor_sync(0xffffffffu, fmax, o));
@@ -497,7 +498,8 @@ __global__ void __launch_bounds__(kCellChunk) k_layer_finish(const WorldDev* __r
 // inertia-free advance X += dt U (cell index + fraction, wrapped) and the
 // unwrapped displacement D += dt U.  Thread 0 of each world's first block
 // advances the world's step counter (no other stage kernel reads it).
-__global__ void __launch_bounds__(kBeadChunk, 8) k_interp_advance(const WorldDev* __restrict__ worlds,
+template <bool kExt>
+__global__ void __launch_bounds__(kBeadChunk) k_interp_advance(const WorldDev* __restrict__ worlds,
                                                                const int2* __restrict__ items) {
   const int2 it = items[blockIdx.x];
   const WorldDev& w = worlds[it.x];
@@ -508,7 +510,7 @@ __global__ void __launch_bounds__(kBeadChunk, 8) k_interp_advance(const WorldDev
   }
   const int i = it.y + threadIdx.x;
   const int W = w.W, H = w.H;
-  if (w.observe && w.energy) {
+  if (kExt && w.observe && w.energy) {
     // the energy field at the bead's position at the start of the step,
     // with the interpolation kernel; its warp sum is the energy collected
     // (every lane of the block takes part in the warp sums)
@@ -544,7 +546,7 @@ __global__ void __launch_bounds__(kBeadChunk, 8) k_interp_advance(const WorldDev
     iy[a] = wrap_once(cy - 1 + a, H) * W;
   }
   float Ux = 0.0f, Uy = 0.0f;
-  if (w.layers == 2) {
+  if (kExt && w.layers == 2) {
     // two-layer filament: mean of the velocities at X +- delta n
     const float2 n = w.nrm[i];
     const float2 Up = layer_velocity(w, p, n, w.layer_half), Um = layer_velocity(w, p, n, -w.layer_half);
@@ -648,11 +650,12 @@ void launch_pbd(const Plan& p, cudaStream_t s) {
   const int wpb = pbd_warps_per_block(mb);
   // filaments of at most 64 beads need no shared memory
   const size_t smem = p.max_B <= 64 ? 0 : (size_t)wpb * mb * kPbdFloatsPerBead * sizeof(float);
-  if (smem > 48 * 1024) {
-    cudaFuncSetAttribute(k_pbd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  }
   const int grid = (p.n_fil_items + wpb - 1) / wpb;
-  k_pbd<<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
+  // worlds with a rest-length drive, observables or two layers need the
+  // extended kernel; it computes every other world exactly as the plain one
+  auto kern = p.any_ext ? k_pbd<true> : k_pbd<false>;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kern<<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
 }
 
 void launch_bin_scatter(const Plan& p, cudaStream_t s) {
@@ -666,7 +669,8 @@ void launch_layer_spread(const Plan& p, cudaStream_t s) {
 }
 
 void launch_interp_advance(const Plan& p, cudaStream_t s) {
-  k_interp_advance<<<p.n_bead_items, kBeadChunk, 0, s>>>(p.d_worlds, p.d_bead_items);
+  if (p.any_ext) k_interp_advance<true><<<p.n_bead_items, kBeadChunk, 0, s>>>(p.d_worlds, p.d_bead_items);
+  else k_interp_advance<false><<<p.n_bead_items, kBeadChunk, 0, s>>>(p.d_worlds, p.d_bead_items);
 }
 
 void launch_unstream_in(const float* f0dev, float* g_dst, int H, int W, cudaStream_t s) {

@@ -370,19 +370,32 @@ __global__ void __launch_bounds__(kThreads, 8) k_deposit_x(const WorldDev* __res
 // [0, tw + 8) (tile cell (lx, ly) at window (lx + 4, ly + 4)).  Spread
 // accumulators: tile cell (lx, ly) at (lx + 3, ly + 3), F = acc 2^-k.
 // ---------------------------------------------------------------------------
+// Inputs of one tile, staged before its compute (double-buffered by the
+// persistent kernel).
 template <int R>
-struct ForceSmem {
-  float xb[Geo<R>::kLoadRows * kWin];
-  float win[kWin * kWin];
-  int accx[kAx * kAx];
-  int accy[kAx * kAx];
-  float4 sp[kForceCap];
+struct TileIn {
+  float xb[Geo<R>::kLoadRows * kWin];   // rho_x window
+  float4 sp[kForceCap];                 // bead records of the first chunk
   float2 sf[kForceCap];
   int si[kForceCap];
-  int list[kForceCap];
+  int s_start[kMaxSeg], s_pre[kMaxSeg + 1];
+  float nbmax[9];                       // largest rho_s of the 3x3 tiles around
   float tap_s[Geo<R>::kTaps];
-  int s_start[kMaxSeg], s_pre[kMaxSeg + 1], s_cnt;
-  float red[16];
+};
+
+// Working arrays of the tile being computed.
+struct TileWork {
+  float win[kWin * kWin];               // rho_bar window
+  int accx[kAx * kAx];                  // spread accumulators
+  int accy[kAx * kAx];
+  int list[kForceCap];
+  int s_cnt;
+};
+
+template <int R>
+struct ForceSmem {
+  TileIn<R> in;
+  TileWork wk;
 };
 
 struct TileBox {
@@ -392,14 +405,14 @@ struct TileBox {
 // Lists the n staged beads whose stencil reaches the tile (image taken on
 // axes with several tiles), packed with their tile-relative cell.
 template <int R>
-__device__ __forceinline__ void force_compact(ForceSmem<R>& sm, int n, const TileBox& tb, int W, int H, int ntx,
-                                              int nty) {
+__device__ __forceinline__ void force_compact(const TileIn<R>& in, TileWork& wk, int n, const TileBox& tb, int W,
+                                              int H, int ntx, int nty) {
   for (int v0 = 0; v0 < n; v0 += kThreads) {
     const int v = v0 + threadIdx.x;
     bool keep = false;
     int rx = 0, ry = 0;
     if (v < n) {
-      const float4 p = sm.sp[v];
+      const float4 p = in.sp[v];
       rx = cell_x(p) - tb.x0;
       ry = cell_y(p) - tb.y0;
       keep = true;
@@ -412,101 +425,124 @@ __device__ __forceinline__ void force_compact(ForceSmem<R>& sm, int n, const Til
         keep = keep && ry <= tb.th;
       }
     }
-    list_push(keep, pack_code(v, rx, ry), sm.list, &sm.s_cnt);
+    list_push(keep, pack_code(v, rx, ry), wk.list, &wk.s_cnt);
   }
 }
 
-// Returns k: after the caller synchronises the block, accx/accy hold the
-// tile's F 2^k (before folding, see force_fold).
+// Stage 1 of a tile: the rho_x window rows [y0 - 4 - R, y0 + th + 4 + R) x
+// columns [x0 - 4, x0 + tw + 4) in 16-byte cp.async chunks (independent of
+// the beads).  A 4-column chunk never straddles the periodic edge (x0 and W
+// are multiples of 8); rows reach at most 4 + R <= 12 cells outside the axis.
 template <int R>
-__device__ __forceinline__ int force_tile(ForceSmem<R>& sm, const WorldDev& w, int tile, const TileBox& tb,
-                                          int store_fields, int after_step) {
-  using G = Geo<R>;
-  const int W = w.W, H = w.H, wR = w.R, ntx = w.ntx, nty = w.nty;
-  const float4* __restrict__ spos = w.spos;
-  const float2* __restrict__ sfel = w.sfel;
-  const int* __restrict__ sid = w.sid;
+__device__ __forceinline__ void tile_stage_window(TileIn<R>& in, const WorldDev& w, const TileBox& tb) {
+  const int W = w.W, H = w.H, tid = threadIdx.x;
   const float* __restrict__ rho_x = w.rho_x;
-  const float* __restrict__ tile_max = w.tile_rho_max;
-  float2* __restrict__ fs_out = w.fs;
-  float* __restrict__ rho_b = w.rho_b;
-  const float k_rep = w.k_rep;
-  const float fmax_el = __uint_as_float(w.fel_max[(*w.t - after_step) & 1]);
-  const bool layered = w.layers == 2;
-  const int x0 = tb.x0, y0 = tb.y0, tw = tb.tw, th = tb.th;
-  const int tx = x0 / kTile, ty = y0 / kTile;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int ww = tw + 8, wh = th + 8, lh = wh + 2 * R;
-  // 1. the rho_x window (independent of the beads) and the bead segments
-  //    (one round trip), then the bead records in one batch
-  {
-    // the window in 16-byte chunks: a 4-column chunk never straddles the
-    // periodic edge (x0 and W are multiples of 8), rows reach at most
-    // 4 + R <= 12 cells outside the axis
-    const int nq = ww >> 2;
-    int rows_per_pass, i0;
-    if (nq == kWin / 4) {   // full tile: constant divisor
-      rows_per_pass = kThreads / (kWin / 4);
-      i0 = tid / (kWin / 4);
-    } else {
-      rows_per_pass = kThreads / nq;
-      i0 = tid / nq;
-    }
-    const int q = tid - i0 * nq;
-    if (i0 < rows_per_pass) {
-      const int col = wrap_once(x0 - 4 + 4 * q, W);
-      for (int i = i0; i < lh; i += rows_per_pass) {
-        const int gy = y0 - 4 - R + i;
-        const int row = H >= 12 ? wrap_once(gy, H) : wrap_mod(gy, H);
-        cp_async16(&sm.xb[i * kWin + 4 * q], rho_x + (size_t)row * W + col);
-      }
+  const int ww = tb.tw + 8, lh = tb.th + 8 + 2 * R;
+  const int nq = ww >> 2;
+  int rows_per_pass, i0;
+  if (nq == kWin / 4) {   // full tile: constant divisor
+    rows_per_pass = kThreads / (kWin / 4);
+    i0 = tid / (kWin / 4);
+  } else {
+    rows_per_pass = kThreads / nq;
+    i0 = tid / nq;
+  }
+  const int q = tid - i0 * nq;
+  if (i0 < rows_per_pass) {
+    const int col = wrap_once(tb.x0 - 4 + 4 * q, W);
+    for (int i = i0; i < lh; i += rows_per_pass) {
+      const int gy = tb.y0 - 4 - R + i;
+      const int row = H >= 12 ? wrap_once(gy, H) : wrap_mod(gy, H);
+      cp_async16(&in.xb[i * kWin + 4 * q], rho_x + (size_t)row * W + col);
     }
   }
-  if (warp == 0) build_segments(w, x0 - 2, x0 + tw, y0 - 2, y0 + th, sm.s_start, sm.s_pre, nullptr);
-  if (warp == 1 && lane < G::kTaps) sm.tap_s[lane] = padded_tap<R>(w, wR, lane);
+}
+
+// Stage 2 (warps 0-2, plain loads): the bead segments of the bins that reach
+// the tile, the filter taps, and the largest rho_s of the 3x3 tiles around.
+template <int R>
+__device__ __forceinline__ void tile_stage_meta(TileIn<R>& in, const WorldDev& w, const TileBox& tb) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) build_segments(w, tb.x0 - 2, tb.x0 + tb.tw, tb.y0 - 2, tb.y0 + tb.th, in.s_start, in.s_pre, nullptr);
+  if (warp == 1 && lane < Geo<R>::kTaps) in.tap_s[lane] = padded_tap<R>(w, w.R, lane);
   // bound of the cell sums of weight * |F_el + F_s|:
   //   |F_s| <= k_rep/2 max|rho_bar(c+1) - rho_bar(c-1)| <= k_rep/2 max rho_bar
   //        <= k_rep/2 max rho_s over the 3x3 tiles around this one,
   // times max rho_s of this tile (the sum of the spread weights of a cell)
   if (warp == 2 && lane < 9) {
-    const int ty2 = wrap_once(ty + lane / 3 - 1, nty), tx2 = wrap_once(tx + lane % 3 - 1, ntx);
-    sm.red[lane] = tile_max[ty2 * ntx + tx2];
+    const int tx = tb.x0 / kTile, ty = tb.y0 / kTile;
+    const int ty2 = wrap_once(ty + lane / 3 - 1, w.nty), tx2 = wrap_once(tx + lane % 3 - 1, w.ntx);
+    in.nbmax[lane] = w.tile_rho_max[ty2 * w.ntx + tx2];
   }
-  for (int c = tid; c < kAx * kAx / 4; c += kThreads) {
-    reinterpret_cast<int4*>(sm.accx)[c] = make_int4(0, 0, 0, 0);
-    reinterpret_cast<int4*>(sm.accy)[c] = make_int4(0, 0, 0, 0);
+}
+
+// Stage 3 (after stage 2 is visible to the block): cp.async of the bead
+// records of the first chunk.
+template <int R>
+__device__ __forceinline__ void tile_stage_records(TileIn<R>& in, const WorldDev& w) {
+  const int n0 = min(kForceCap, in.s_pre[kMaxSeg]);
+  const float4* __restrict__ spos = w.spos;
+  const float2* __restrict__ sfel = w.sfel;
+  const int* __restrict__ sid = w.sid;
+  for (int v = threadIdx.x; v < n0; v += kThreads) {
+    const int slot = seg_slot(v, in.s_start, in.s_pre);
+    cp_async16(&in.sp[v], &spos[slot]);
+    cp_async8(&in.sf[v], &sfel[slot]);
+    cp_async4(&in.si[v], &sid[slot]);
   }
-  if (tid == 0) sm.s_cnt = 0;
-  const float rho_max = tile_max[tile];
-  __syncthreads();
-  const int total = sm.s_pre[kMaxSeg];
+}
+
+// Zeroes the spread accumulators and the list count (before the barrier
+// that precedes tile_compute).
+__device__ __forceinline__ void tile_clear(TileWork& wk) {
+  for (int c = threadIdx.x; c < kAx * kAx / 4; c += kThreads) {
+    reinterpret_cast<int4*>(wk.accx)[c] = make_int4(0, 0, 0, 0);
+    reinterpret_cast<int4*>(wk.accy)[c] = make_int4(0, 0, 0, 0);
+  }
+  if (threadIdx.x == 0) wk.s_cnt = 0;
+}
+
+// The y pass of a5 and a6 for one tile whose inputs have landed (all stages
+// complete and visible, accumulators cleared).  Returns k: after the caller
+// synchronises the block, accx/accy hold the tile's F 2^k (before folding,
+// see force_fold).
+template <int R>
+__device__ __forceinline__ int tile_compute(TileIn<R>& in, TileWork& wk, const WorldDev& w, int tile,
+                                            const TileBox& tb, int store_fields, int after_step) {
+  using G = Geo<R>;
+  const int W = w.W, H = w.H, ntx = w.ntx, nty = w.nty;
+  const float4* __restrict__ spos = w.spos;
+  const float2* __restrict__ sfel = w.sfel;
+  const int* __restrict__ sid = w.sid;
+  float2* __restrict__ fs_out = w.fs;
+  float* __restrict__ rho_b = w.rho_b;
+  const float k_rep = w.k_rep;
+  const float fmax_el = __uint_as_float(w.fel_max[(*w.t - after_step) & 1]);
+  const float rho_max = w.tile_rho_max[tile];
+  const bool layered = w.layers == 2;
+  const int x0 = tb.x0, y0 = tb.y0, tw = tb.tw, th = tb.th;
+  const int tid = threadIdx.x;
+  const int ww = tw + 8, wh = th + 8;
+  const int total = in.s_pre[kMaxSeg];
   const int n0 = min(kForceCap, total);
-  for (int v = tid; v < n0; v += kThreads) {
-    const int slot = seg_slot(v, sm.s_start, sm.s_pre);
-    cp_async16(&sm.sp[v], &spos[slot]);
-    cp_async8(&sm.sf[v], &sfel[slot]);
-    cp_async4(&sm.si[v], &sid[slot]);
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  float rho_nb = sm.red[0];
-  for (int k2 = 1; k2 < 9; ++k2) rho_nb = fmaxf(rho_nb, sm.red[k2]);
+  float rho_nb = in.nbmax[0];
+  for (int k2 = 1; k2 < 9; ++k2) rho_nb = fmaxf(rho_nb, in.nbmax[k2]);
   const int k = fix_exponent((fmax_el + 0.5f * k_rep * rho_nb) * rho_max * 1.0001f + 1e-30f);
   const float scale = pow2f(k);
   // list the first chunk's beads that reach the tile, then the y pass
-  force_compact(sm, n0, tb, W, H, ntx, nty);
+  force_compact(in, wk, n0, tb, W, H, ntx, nty);
   {
     // y pass, 8 window rows per thread
     float tp[G::kTaps];
 #pragma unroll
-    for (int m = 0; m < G::kTaps; ++m) tp[m] = sm.tap_s[m];
+    for (int m = 0; m < G::kTaps; ++m) tp[m] = in.tap_s[m];
     const int nstrip = wh >> 3;
     for (int c = tid; c < nstrip * ww; c += kThreads) {
       int s;
       if (ww == kWin) s = c / kWin;   // full tile: constant divisor
       else s = c / ww;
       const int j = c - s * ww;
-      const float* src = sm.xb + (8 * s) * kWin + j;
+      const float* src = in.xb + (8 * s) * kWin + j;
       float v[8 + 2 * R];
 #pragma unroll
       for (int q = 0; q < 8 + 2 * R; ++q) v[q] = src[q * kWin];
@@ -516,7 +552,7 @@ __device__ __forceinline__ int force_tile(ForceSmem<R>& sm, const WorldDev& w, i
 #pragma unroll
         for (int m = 0; m < G::kTaps; ++m) sacc = fmaf(tp[m], v[r + m], sacc);
         const int i = 8 * s + r;
-        sm.win[i * kWin + j] = sacc;
+        wk.win[i * kWin + j] = sacc;
         if (store_fields && i >= 4 && i < th + 4 && j >= 4 && j < tw + 4)
           rho_b[(size_t)(y0 + i - 4) * W + x0 + j - 4] = sacc;
       }
@@ -524,17 +560,17 @@ __device__ __forceinline__ int force_tile(ForceSmem<R>& sm, const WorldDev& w, i
   }
   __syncthreads();
   for (int c0 = 0;;) {
-    const int cnt = sm.s_cnt;
+    const int cnt = wk.s_cnt;
     for (int q = tid; q < cnt; q += kThreads) {
-      const int code = sm.list[q];
+      const int code = wk.list[q];
       const int v = code_slot(code), rx = code_rx(code), ry = code_ry(code);
-      const float4 p = sm.sp[v];
+      const float4 p = in.sp[v];
       float wx[4], wy[4];
       peskin4(p.x, wx);
       peskin4(p.y, wy);
       // stencil cell a sits at window column rx + 3 + a; the central
       // differences read one cell further on each side
-      const float* base = sm.win + (ry + 2) * kWin + rx + 2;
+      const float* base = wk.win + (ry + 2) * kWin + rx + 2;
       float gsx = 0.0f, gsy = 0.0f;
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
@@ -551,9 +587,9 @@ __device__ __forceinline__ int force_tile(ForceSmem<R>& sm, const WorldDev& w, i
         gsy = fmaf(wy[b], sy, gsy);
       }
       const float Fsx = -0.5f * k_rep * gsx, Fsy = -0.5f * k_rep * gsy;
-      if (rx >= 0 && rx < tw && ry >= 0 && ry < th) fs_out[sm.si[v]] = make_float2(Fsx, Fsy);
+      if (rx >= 0 && rx < tw && ry >= 0 && ry < th) fs_out[in.si[v]] = make_float2(Fsx, Fsy);
       if (layered) continue;   // two-layer worlds spread at their layer points (k_layer_spread)
-      const float2 fe = sm.sf[v];
+      const float2 fe = in.sf[v];
       const float Fx = (fe.x + Fsx) * scale, Fy = (fe.y + Fsy) * scale;
       float ax[4], ay[4];
 #pragma unroll
@@ -561,8 +597,8 @@ __device__ __forceinline__ int force_tile(ForceSmem<R>& sm, const WorldDev& w, i
         ax[a] = wx[a] * Fx;
         ay[a] = wx[a] * Fy;
       }
-      int* bx = sm.accx + (ry + 2) * kAx + rx + 2;
-      int* by = sm.accy + (ry + 2) * kAx + rx + 2;
+      int* bx = wk.accx + (ry + 2) * kAx + rx + 2;
+      int* by = wk.accy + (ry + 2) * kAx + rx + 2;
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
 #pragma unroll
@@ -575,36 +611,49 @@ __device__ __forceinline__ int force_tile(ForceSmem<R>& sm, const WorldDev& w, i
     c0 += kForceCap;
     if (c0 >= total) break;
     __syncthreads();   // every thread is done with this chunk
-    if (tid == 0) sm.s_cnt = 0;
+    if (tid == 0) wk.s_cnt = 0;
     const int n = min(kForceCap, total - c0);
     for (int v = tid; v < n; v += kThreads) {
-      const int slot = seg_slot(c0 + v, sm.s_start, sm.s_pre);
-      cp_async16(&sm.sp[v], &spos[slot]);
-      cp_async8(&sm.sf[v], &sfel[slot]);
-      cp_async4(&sm.si[v], &sid[slot]);
+      const int slot = seg_slot(c0 + v, in.s_start, in.s_pre);
+      cp_async16(&in.sp[v], &spos[slot]);
+      cp_async8(&in.sf[v], &sfel[slot]);
+      cp_async4(&in.si[v], &sid[slot]);
     }
     cp_async_wait_all();
     __syncthreads();
-    force_compact(sm, n, tb, W, H, ntx, nty);
+    force_compact(in, wk, n, tb, W, H, ntx, nty);
     __syncthreads();
   }
   return k;   // the caller synchronises before it reads the accumulators
 }
 
+// One tile staged and computed (the non-persistent kernels).
+template <int R>
+__device__ __forceinline__ int force_tile(ForceSmem<R>& sm, const WorldDev& w, int tile, const TileBox& tb,
+                                          int store_fields, int after_step) {
+  tile_stage_window(sm.in, w, tb);
+  tile_stage_meta(sm.in, w, tb);
+  tile_clear(sm.wk);
+  __syncthreads();
+  tile_stage_records(sm.in, w);
+  cp_async_wait_all();
+  __syncthreads();
+  return tile_compute(sm.in, sm.wk, w, tile, tb, store_fields, after_step);
+}
+
 // Folds the stencil cells that wrapped around an axis the tile covers whole
 // (one tile on that axis); call after the block has synchronised.
-template <int R>
-__device__ __forceinline__ void force_fold(ForceSmem<R>& sm, const TileBox& tb, int ntx, int nty) {
+__device__ __forceinline__ void force_fold(TileWork& wk, const TileBox& tb, int ntx, int nty) {
   if (ntx > 1 && nty > 1) return;
   const bool fx = ntx == 1, fy = nty == 1;
   for (int c = threadIdx.x; c < kAx * kAx; c += kThreads) {
     const int ly = c / kAx - 3, lx = c % kAx - 3;
     const bool out_y = ly < 0 || ly >= tb.th, out_x = lx < 0 || lx >= tb.tw;
     if ((!out_y && !out_x) || (out_y && !fy) || (out_x && !fx)) continue;
-    const int vx = sm.accx[c], vy = sm.accy[c];
+    const int vx = wk.accx[c], vy = wk.accy[c];
     const int t2 = (wrap_mod(ly, tb.th) + 3) * kAx + wrap_mod(lx, tb.tw) + 3;
-    if (vx) atomicAdd(&sm.accx[t2], vx);
-    if (vy) atomicAdd(&sm.accy[t2], vy);
+    if (vx) atomicAdd(&wk.accx[t2], vx);
+    if (vy) atomicAdd(&wk.accy[t2], vy);
   }
   __syncthreads();
 }
@@ -632,54 +681,44 @@ __global__ void __launch_bounds__(kThreads) k_force_spread(const WorldDev* __res
   const int W = w.W;
   const int k = force_tile<R>(sm, w, (tb.y0 / kTile) * w.ntx + tb.x0 / kTile, tb, store_fields, after_step);
   __syncthreads();
-  force_fold(sm, tb, w.ntx, w.nty);
+  force_fold(sm.wk, tb, w.ntx, w.nty);
   const float inv = pow2f(-k);
   const int lane = threadIdx.x & 31;
   for (int ly = threadIdx.x >> 5; ly < tb.th; ly += kWarps) {
     if (lane < tb.tw) {
       const int s = (ly + 3) * kAx + lane + 3;
-      F_out[(size_t)(tb.y0 + ly) * W + tb.x0 + lane] = make_float2((float)sm.accx[s] * inv, (float)sm.accy[s] * inv);
+      F_out[(size_t)(tb.y0 + ly) * W + tb.x0 + lane] = make_float2((float)sm.wk.accx[s] * inv, (float)sm.wk.accy[s] * inv);
     }
   }
 }
 
-// y pass of a5 + a6 + a7 on the tile's cells: F goes from shared memory
-// straight into the collision (the same arithmetic as k_force_spread
-// followed by k_lbm, without F's round trip through HBM).
-template <int R>
-__global__ void __launch_bounds__(kThreads, 4) k_force_lbm(const WorldDev* __restrict__ worlds,
-                                                        const int2* __restrict__ items) {
-  __shared__ __align__(16) ForceSmem<R> sm;
-  const int2 it = items[blockIdx.x];
-  const WorldDev& w = worlds[it.x];
-  const TileBox tb = tile_box(w, it.y);
+// The tile's population rows (plane i, rows y - c_iy, 128-byte segments) to L2.
+__device__ __forceinline__ void prefetch_populations(const WorldDev& w, const TileBox& tb) {
+  const float* src = w.g[*w.t & 1];
+  const int W = w.W, H = w.H;
+  const size_t HW = (size_t)H * W;
+  for (int c = threadIdx.x; c < 9 * kTile; c += kThreads) {
+    const int i = c >> 5, r = c & (kTile - 1);
+    if (r >= tb.th) continue;
+    const int y = wrap_once(tb.y0 + r - kLbmCy[i], H);
+    const float* a = src + (size_t)i * HW + (size_t)y * W + tb.x0;
+    asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a));
+  }
+}
+
+// a7 on the tile's cells with F = acc 2^-k from shared memory.  Each warp
+// collides rows warp, warp + 8, ...; the populations of its next row are
+// pulled before the current one is collided (the first before the barrier
+// that completes the spread).
+__device__ __forceinline__ void tile_lbm(TileWork& wk, const WorldDev& w, const TileBox& tb, int k) {
   const int W = w.W, H = w.H, HW = H * W;
   const long long t = *w.t;
   const float* __restrict__ src = w.g[t & 1];
   float* __restrict__ dst = w.g[(t + 1) & 1];
   float2* __restrict__ u_out = w.u;
   const LbmConst kc{w.om_p, w.om_m, w.src_p, w.src_m};
-  const bool layered = w.layers == 2;
-  if (!layered) {
-    // start the DRAM reads of the collision now: the 128-byte row segments
-    // that the tile's cells pull from (plane i, rows y - c_iy) go to L2
-    // while the force phase runs
-    const int th = tb.th;
-    for (int c = threadIdx.x; c < 9 * kTile; c += kThreads) {
-      const int i = c >> 5, r = c & (kTile - 1);
-      if (r >= th) continue;
-      const int y = wrap_once(tb.y0 + r - kLbmCy[i], H);
-      const float* a = src + (size_t)i * HW + (size_t)y * W + tb.x0;
-      asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a));
-    }
-  }
-  const int k = force_tile<R>(sm, w, (tb.y0 / kTile) * w.ntx + tb.x0 / kTile, tb, 0, 0);
-  if (layered) return;   // F_s only: the layer spread and the collision follow in their own kernels
   const float inv = pow2f(-k);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // each warp collides rows warp, warp + 8, ... of the tile; the populations
-  // of its next row are pulled before the current one is collided (the
-  // first before the barrier that completes the spread)
   const bool active = lane < tb.tw && warp < tb.th;
   const int x = tb.x0 + lane;
   const int xm = x == 0 ? W - 1 : x - 1, xp = x == W - 1 ? 0 : x + 1;
@@ -687,7 +726,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_force_lbm(const WorldDev* __res
   int y = tb.y0 + warp;
   if (active) lbm_pull(src, HW, y * W, (y == 0 ? H - 1 : y - 1) * W, (y == H - 1 ? 0 : y + 1) * W, x, xm, xp, q);
   __syncthreads();
-  force_fold(sm, tb, w.ntx, w.nty);
+  force_fold(wk, tb, w.ntx, w.nty);
   if (!active) return;
   for (int ly = warp; ly < tb.th; ly += kWarps) {
     LbmPull qn;
@@ -695,23 +734,43 @@ __global__ void __launch_bounds__(kThreads, 4) k_force_lbm(const WorldDev* __res
     if (ly + kWarps < tb.th)
       lbm_pull(src, HW, yn * W, (yn == 0 ? H - 1 : yn - 1) * W, (yn == H - 1 ? 0 : yn + 1) * W, x, xm, xp, qn);
     const int s = (ly + 3) * kAx + lane + 3;
-    const float2 F = make_float2((float)sm.accx[s] * inv, (float)sm.accy[s] * inv);
+    const float2 F = make_float2((float)wk.accx[s] * inv, (float)wk.accy[s] * inv);
     u_out[(size_t)y * W + x] = lbm_collide(q, dst, HW, y * W + x, F, kc);
     q = qn;
     y = yn;
   }
 }
 
+// y pass of a5 + a6 + a7 on one tile: the force density goes from shared
+// memory straight into the collision (the same arithmetic as k_force_spread
+// followed by k_lbm, without F's round trip through HBM).  The tile's
+// population rows are prefetched into L2 on entry, so their DRAM reads
+// overlap the force phase.
+template <int R>
+__global__ void __launch_bounds__(kThreads, 4) k_force_lbm(const WorldDev* __restrict__ worlds,
+                                                           const int2* __restrict__ items) {
+  __shared__ __align__(16) ForceSmem<R> sm;
+  const int2 it = items[blockIdx.x];
+  const WorldDev& w = worlds[it.x];
+  const TileBox tb = tile_box(w, it.y);
+  const bool layered = w.layers == 2;
+  if (!layered) prefetch_populations(w, tb);
+  const int k = force_tile<R>(sm, w, (tb.y0 / kTile) * w.ntx + tb.x0 / kTile, tb, 0, 0);
+  // two-layer worlds: F_s only; their layer spread and collision follow in their own kernels
+  if (!layered) tile_lbm(sm.wk, w, tb, k);
+}
+
 namespace {
 
 template <int R>
 void launch_steric(const Plan& p, cudaStream_t s, int which, int store_fields, int after_step) {
-  if (which == 0)
+  if (which == 0) {
     k_deposit_x<R><<<p.n_tile_items, kThreads, 0, s>>>(p.d_worlds, p.d_tile_items, store_fields);
-  else if (which == 1)
+  } else if (which == 1) {
     k_force_spread<R><<<p.n_tile_items, kThreads, 0, s>>>(p.d_worlds, p.d_tile_items, store_fields, after_step);
-  else
+  } else {
     k_force_lbm<R><<<p.n_tile_items, kThreads, 0, s>>>(p.d_worlds, p.d_tile_items);
+  }
 }
 
 void dispatch_steric(const Plan& p, cudaStream_t s, int which, int store_fields, int after_step) {

@@ -126,6 +126,7 @@ mc_status build_plan(mc_world* const* ws, int n, cudaStream_t s, Plan& out) {
   p.n_worlds = n;
   p.max_R = 1;
   p.any_layered = false;
+  p.any_ext = false;
   std::vector<int2> fil, bead, tile, cell, scan;
   std::vector<WorldDev> table(n);
   for (int k = 0; k < n; ++k) {
@@ -134,6 +135,7 @@ mc_status build_plan(mc_world* const* ws, int n, cudaStream_t s, Plan& out) {
     p.max_B = std::max(p.max_B, w->max_B);
     p.max_R = std::max(p.max_R, w->h.R);
     p.any_layered = p.any_layered || w->h.layers == 2;
+    p.any_ext = p.any_ext || w->h.layers == 2 || w->h.observe || w->h.has_ldrive;
     for (int f = 0; f < w->h.n_fil; ++f) fil.push_back(make_int2(k, f));
     const int nb = std::max(w->h.N, 1);
     for (int b = 0; b < nb; b += mc::kBeadChunk) bead.push_back(make_int2(k, b));

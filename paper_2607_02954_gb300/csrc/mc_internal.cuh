@@ -114,6 +114,7 @@ struct Plan {
   int max_B = 2;
   int max_R = 4;                 // largest Gaussian half width among the worlds
   bool any_layered = false;      // some world is a two-layer filament world
+  bool any_ext = false;          // some world has two layers, observables or a rest-length drive
   int n_fil_items = 0, n_bead_items = 0, n_tile_items = 0, n_cell_items = 0, n_scan_items = 0;
   WorldDev* d_worlds = nullptr;  // [n_worlds]
   int2* d_fil_items = nullptr;   // (world, filament)
