@@ -323,14 +323,19 @@ def bench_gradient(args):
     reps = max(1, min(args.steps, 5))
     w = World(spec)
     stream = torch.cuda.current_stream()
-    for _ in range(max(1, min(args.warmup, 2))):
-        w.rollout_forward(50, 10)
-        loss, gx, gy = loss_fn(w)
-        w.rollout_backward_params(gx, gy)
+    # the optimisation loop of the Filament Folding experiment on one world:
+    # new rest angles, back to the start, rollout, loss, reverse sweep (the
+    # warm-up iteration captures the sweep's graph; the timed ones replay it)
+    theta0 = spec.theta0.copy()
+    w.rollout_forward(n, K)
+    loss, gx, gy = loss_fn(w)
+    w.rollout_backward_params(gx, gy)
     torch.cuda.synchronize()
     fwd, bwd = [], []
     with ClockSampler(0) as clk:
         for _ in range(reps):
+            w.rollout_rewind()
+            w.set_rest(theta0=theta0)
             e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             e[0].record(stream)
             w.rollout_forward(n, K)
@@ -341,6 +346,7 @@ def bench_gradient(args):
             torch.cuda.synchronize()
             fwd.append(e[0].elapsed_time(e[1]))
             bwd.append(e[1].elapsed_time(e[2]))
+            theta0 = theta0 - 1e-3 * t2n_host(g["theta0"]).astype(np.float32)   # a gradient step
     w.check()
     grad_norm = float(torch.linalg.vector_norm(g["theta0"]).item())
     w.close()

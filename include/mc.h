@@ -278,10 +278,27 @@ mc_status mc_world_get_observables(const mc_world* w, double* out, void* stream)
  * MC_ERR_OOM, MC_ERR_CUDA. */
 mc_status mc_rollout_forward(mc_world* w, int n_steps, int ckpt_every, void* stream);
 
+/* Returns the world to the start of the last mc_rollout_forward (its first
+ * checkpoint, displacement, observables and step counter), so an
+ * optimisation loop can re-run the same rollout with new parameters on the
+ * same world: its buffers and its captured reverse sweep are reused.  The
+ * recorded rollout stays; a backward needs a new forward first.  Errors:
+ * MC_ERR_INVALID_ARG when no rollout was recorded. */
+mc_status mc_rollout_rewind(mc_world* w, void* stream);
+
+/* Replaces the static rest angles theta0 [J] and/or the rest lengths L_rest
+ * [E] (the quantities the folding optimisation and the searches change);
+ * either may be NULL.  Arrays in mem_kind memory; host arrays are checked
+ * (finite, L_rest > 0) and the call synchronizes `stream`; device arrays are
+ * used as given.  With a rest-length drive the new L_rest is its L0. */
+mc_status mc_world_set_rest(mc_world* w, const float* theta0, const float* L_rest, int mem_kind, void* stream);
+
 /* Reverse sweep of the last mc_rollout_forward.  dL_dx, dL_dy: [N] device
  * arrays, the loss gradient with respect to the final unwrapped positions
  * (creation position + displacement).  Writes dL_dtheta0 [J] (device).
- * The world ends in the final state of the rollout.  Errors:
+ * The world ends in the final state of the rollout.  The sweep is captured
+ * as a CUDA graph on first use and replayed while the rollout length,
+ * checkpoint spacing, start step and buffers stay the same.  Errors:
  * MC_ERR_INVALID_ARG when no rollout was recorded or the world was stepped
  * since, or when filaments are too long for the adjoint kernel. */
 mc_status mc_rollout_backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* dL_dtheta0, void* stream);

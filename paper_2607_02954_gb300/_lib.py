@@ -87,6 +87,8 @@ SIGNATURES = {
     "mc_world_get_observables": (_i, [_vp, _vp, _vp]),
     "mc_rollout_forward": (_i, [_vp, _i, _i, _vp]),
     "mc_rollout_backward": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "mc_rollout_rewind": (_i, [_vp, _vp]),
+    "mc_world_set_rest": (_i, [_vp, _vp, _vp, _i, _vp]),
     "mc_rollout_backward_params": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "mc_loss_polyline": (_i, [_vp, _vp, _i, _vp, _vp, _vp, _vp]),
     "mc_loss_splat": (_i, [_vp, _vp, _i, ctypes.c_float, _vp, _vp, _vp, _vp]),

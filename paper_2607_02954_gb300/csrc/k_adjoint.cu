@@ -588,10 +588,35 @@ void launch_adj_step(const Plan& p, const WorldDev& h, AdjDev a, int src_parity,
     int wpb = (int)((48 * 1024) / per);
     wpb = wpb < 1 ? 1 : (wpb > 4 ? 4 : wpb);
     const size_t smem = per * wpb;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_adj_pbd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_adj_pbd<<<(p.n_fil_items + wpb - 1) / wpb, wpb * 32, smem, s>>>(wd, a, p.d_fil_items, p.n_fil_items, mb,
                                                                      h.n_pbd);
   }
+}
+
+void adj_setup(const Plan& p, const WorldDev& h) {
+  const int mb = (p.max_B + 3) & ~3;
+  const size_t per = adj_pbd_smem_per_warp(mb, h.n_pbd);
+  if (per > 48 * 1024) cudaFuncSetAttribute(k_adj_pbd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)per);
+}
+
+// theta0 [J] into the drive records' first component, L_rest [E] into the
+// rest lengths (and the rest-length drive's L0); either may be NULL.
+__global__ void k_set_rest(float4* drive, int J, const float* theta0, float* L_rest, float4* ldrive, int E,
+                           const float* L_new) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (theta0 && i < J) drive[i].x = theta0[i];
+  if (L_new && i < E) {
+    L_rest[i] = L_new[i];
+    if (ldrive) ldrive[i].x = L_new[i];
+  }
+}
+
+void launch_set_rest(const WorldDev& h, const float* theta0, const float* L_rest, cudaStream_t s) {
+  const int n = h.J > h.E ? h.J : h.E;
+  if (n > 0 && (theta0 || L_rest))
+    k_set_rest<<<(n + 255) / 256, 256, 0, s>>>(const_cast<float4*>(h.drive), h.J, theta0,
+                                               const_cast<float*>(h.L_rest), const_cast<float4*>(h.ldrive), h.E,
+                                               L_rest);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,6 +1,8 @@
 // Bead-parallel stages of one time step: drive + PBD + elastic force + bin
 // histogram (a1-a3), bin scatter (a2), IB interpolation + advance (a8), and
 // the per-world set-up / read-out kernels.
+#include <mutex>
+
 #include "mc_internal.cuh"
 
 namespace mc {
@@ -654,8 +656,18 @@ void launch_pbd(const Plan& p, cudaStream_t s) {
   // worlds with a rest-length drive, observables or two layers need the
   // extended kernel; it computes every other world exactly as the plain one
   auto kern = p.any_ext ? k_pbd<true> : k_pbd<false>;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   kern<<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
+}
+
+// Shared-memory limits set once per process, outside any stream capture: the
+// PBD kernel stages up to 8 warps' filaments of at most 3072 beads.
+void kernel_setup() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const int most = 227 * 1024;
+    cudaFuncSetAttribute(k_pbd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(k_pbd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+  });
 }
 
 void launch_bin_scatter(const Plan& p, cudaStream_t s) {

@@ -47,6 +47,27 @@ StateSlot state_slot(const mc::WorldDev& h) {
   return s;
 }
 
+// After the n_ck checkpoints and the final state: the final displacement,
+// and the start's displacement and observables.
+struct TapeTail {
+  size_t disp_end, disp0, obs0, end;
+};
+
+TapeTail tape_tail(const mc::WorldDev& h, int n_ck, const StateSlot& sl) {
+  TapeTail t;
+  t.disp_end = (size_t)(n_ck + 1) * sl.bytes;
+  t.disp0 = t.disp_end + align256((size_t)h.N * sizeof(float2));
+  t.obs0 = t.disp0 + align256((size_t)h.N * sizeof(float2));
+  t.end = t.obs0 + 256;
+  return t;
+}
+
+cudaStream_t adj_capture_stream() {
+  thread_local cudaStream_t cs = nullptr;
+  if (!cs) cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  return cs;
+}
+
 mc_status save_state(const mc::WorldDev& h, int parity, char* rec, const StateSlot& sl, cudaStream_t s) {
   const size_t HW = (size_t)h.H * h.W;
   if (h.N) MC_ACUDA(cudaMemcpyAsync(rec + sl.pos, h.pos, h.N * sizeof(float4), cudaMemcpyDeviceToDevice, s));
@@ -79,8 +100,8 @@ mc_status mc_rollout_forward(mc_world* w, int n_steps, int ckpt_every, void* str
   const mc::WorldDev& h = w->h;
   const StateSlot sl = state_slot(h);
   const int n_ck = (n_steps + ckpt_every - 1) / ckpt_every;
-  const size_t fin_disp = align256((size_t)h.N * sizeof(float2));
-  const size_t need = (size_t)(n_ck + 1) * sl.bytes + fin_disp;
+  const TapeTail tl = tape_tail(h, n_ck, sl);
+  const size_t need = tl.end;
   if (w->tape_bytes < need) {
     if (w->tape) cudaFreeAsync(w->tape, w->stream);
     w->tape = nullptr;
@@ -93,6 +114,9 @@ mc_status mc_rollout_forward(mc_world* w, int n_steps, int ckpt_every, void* str
   w->tape_t0 = w->t;
   w->tape_steps = n_steps;
   w->tape_every = ckpt_every;
+  // the start's displacement and observables (the checkpoints hold the rest), for mc_rollout_rewind
+  if (h.N) MC_ACUDA(cudaMemcpyAsync(tape + tl.disp0, h.disp, h.N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  MC_ACUDA(cudaMemcpyAsync(tape + tl.obs0, h.obs, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
   int done = 0;
   for (int k = 0; k < n_ck; ++k) {
     mc_status st = save_state(h, (int)(w->t & 1), tape + (size_t)k * sl.bytes, sl, s);
@@ -105,15 +129,128 @@ mc_status mc_rollout_forward(mc_world* w, int n_steps, int ckpt_every, void* str
   }
   mc_status st = save_state(h, (int)(w->t & 1), tape + (size_t)n_ck * sl.bytes, sl, s);
   if (st != MC_OK) return st;
-  if (h.N)
-    MC_ACUDA(cudaMemcpyAsync(tape + (size_t)(n_ck + 1) * sl.bytes, h.disp, h.N * sizeof(float2),
-                             cudaMemcpyDeviceToDevice, s));
+  if (h.N) MC_ACUDA(cudaMemcpyAsync(tape + tl.disp_end, h.disp, h.N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  return MC_OK;
+}
+
+mc_status mc_rollout_rewind(mc_world* w, void* stream) {
+  if (!w) return afail(MC_ERR_INVALID_ARG, "world is NULL");
+  if (!w->tape || w->tape_steps < 1) return afail(MC_ERR_INVALID_ARG, "no rollout recorded: call mc_rollout_forward first");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const mc::WorldDev& h = w->h;
+  const StateSlot sl = state_slot(h);
+  const int n_ck = (w->tape_steps + w->tape_every - 1) / w->tape_every;
+  const TapeTail tl = tape_tail(h, n_ck, sl);
+  const char* tape = static_cast<const char*>(w->tape);
+  mc_status st = load_state(h, (int)(w->tape_t0 & 1), tape, sl, s);
+  if (st != MC_OK) return st;
+  if (h.N) MC_ACUDA(cudaMemcpyAsync(h.disp, tape + tl.disp0, h.N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  MC_ACUDA(cudaMemcpyAsync(h.obs, tape + tl.obs0, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
+  mc::launch_set_counter(h, w->tape_t0, s);
+  MC_ACUDA(cudaGetLastError());
+  w->t = w->tape_t0;
+  return MC_OK;
+}
+
+mc_status mc_world_set_rest(mc_world* w, const float* theta0, const float* L_rest, int mem_kind, void* stream) {
+  if (!w) return afail(MC_ERR_INVALID_ARG, "world is NULL");
+  if (mem_kind != MC_MEM_HOST && mem_kind != MC_MEM_DEVICE) return afail(MC_ERR_INVALID_ARG, "bad mem_kind");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const mc::WorldDev& h = w->h;
+  const size_t J = h.J, E = h.E;
+  const float* dth = theta0;
+  const float* dL = L_rest;
+  void* stage = nullptr;
+  if (mem_kind == MC_MEM_HOST) {
+    for (size_t j = 0; theta0 && j < J; ++j)
+      if (!std::isfinite(theta0[j])) return afail(MC_ERR_INVALID_ARG, "non-finite theta0");
+    for (size_t e = 0; L_rest && e < E; ++e)
+      if (!(std::isfinite(L_rest[e]) && L_rest[e] > 0.0f)) return afail(MC_ERR_INVALID_ARG, "L_rest must be finite and > 0");
+    const size_t bytes = ((theta0 ? J : 0) + (L_rest ? E : 0)) * sizeof(float);
+    if (bytes) {
+      MC_ACUDA(cudaMallocAsync(&stage, bytes, s));
+      float* p = static_cast<float*>(stage);
+      if (theta0 && J) MC_ACUDA(cudaMemcpyAsync(p, theta0, J * sizeof(float), cudaMemcpyHostToDevice, s));
+      if (L_rest && E)
+        MC_ACUDA(cudaMemcpyAsync(p + (theta0 ? J : 0), L_rest, E * sizeof(float), cudaMemcpyHostToDevice, s));
+      dth = theta0 ? p : nullptr;
+      dL = L_rest ? p + (theta0 ? J : 0) : nullptr;
+    }
+  }
+  mc::launch_set_rest(h, dth, dL, s);
+  const cudaError_t e = cudaGetLastError();
+  if (stage) cudaFreeAsync(stage, s);
+  if (mem_kind == MC_MEM_HOST) MC_ACUDA(cudaStreamSynchronize(s));   // the host arrays may go away
+  MC_ACUDA(e);
   return MC_OK;
 }
 
 }  // extern "C"
 
 namespace {
+
+// The reverse sweep proper (no caller memory: captured into a graph):
+// zero the adjoints, re-run each segment from its checkpoint keeping every
+// step's state, reverse its steps, and return to the rollout's final state.
+mc_status sweep(mc_world* w, mc::AdjDev a, float* const adjG[2], char* obs_keep, char* seg, const StateSlot& sl,
+                int n_ck, cudaStream_t s) {
+  const mc::WorldDev& h = w->h;
+  const size_t HW = (size_t)h.H * h.W;
+  const int K = w->tape_every, n = w->tape_steps;
+  char* tape = static_cast<char*>(w->tape);
+  // the recompute passes accumulate the observables again: keep the rollout's values
+  MC_ACUDA(cudaMemcpyAsync(obs_keep, h.obs, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
+  if (h.E) MC_ACUDA(cudaMemsetAsync(a.adjTh, 0, h.E * sizeof(float), s));
+  if (h.J) MC_ACUDA(cudaMemsetAsync(a.gth0, 0, h.J * sizeof(float), s));
+  if (h.E) MC_ACUDA(cudaMemsetAsync(a.gL, 0, h.E * sizeof(float), s));
+  MC_ACUDA(cudaMemsetAsync(a.gk, 0, 3 * sizeof(float), s));
+  MC_ACUDA(cudaMemsetAsync(adjG[0], 0, 9 * HW * sizeof(float), s));
+  int cur = 0;   // adjG[cur] holds the adjoint of the populations after the step being reversed
+  const int64_t t0 = w->tape_t0;
+  for (int k = n_ck - 1; k >= 0; --k) {
+    const int steps = std::min(K, n - k * K);
+    const int64_t tk = t0 + (int64_t)k * K;
+    mc_status st = load_state(h, (int)(tk & 1), tape + (size_t)k * sl.bytes, sl, s);
+    if (st != MC_OK) return st;
+    mc::launch_set_counter(h, tk, s);
+    for (int q = 0; q < steps; ++q) {
+      st = save_state(h, (int)((tk + q) & 1), seg + (size_t)q * sl.bytes, sl, s);
+      if (st != MC_OK) return st;
+      mc::enqueue_step(w->plan, s);
+    }
+    for (int q = steps - 1; q >= 0; --q) {
+      const int64_t tn = tk + q;
+      const int par = (int)(tn & 1);
+      const char* rec = seg + (size_t)q * sl.bytes;
+      st = load_state(h, par, rec, sl, s);
+      if (st != MC_OK) return st;
+      mc::launch_set_counter(h, tn, s);
+      // this step's intermediates (F_el, F_s, rho_bar, F, u)
+      mc::launch_pbd(w->plan, s);
+      mc::launch_bin_scan(w->plan, s);
+      mc::launch_bin_scatter(w->plan, s);
+      mc::launch_deposit_x(w->plan, s, 0);
+      mc::launch_force_spread(w->plan, s, 1, 0);
+      mc::launch_lbm(w->plan, s);
+      a.adjG_next = adjG[cur];
+      a.adjG_cur = adjG[cur ^ 1];
+      a.theta_n = reinterpret_cast<const float*>(rec + sl.theta);
+      mc::launch_adj_step(w->plan, h, a, par, s);
+      cur ^= 1;
+    }
+    MC_ACUDA(cudaGetLastError());
+  }
+  // back to the final state of the rollout
+  const int64_t tf = t0 + n;
+  const TapeTail tl = tape_tail(h, n_ck, sl);
+  mc_status st = load_state(h, (int)(tf & 1), tape + (size_t)n_ck * sl.bytes, sl, s);
+  if (st != MC_OK) return st;
+  if (h.N) MC_ACUDA(cudaMemcpyAsync(h.disp, tape + tl.disp_end, h.N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  mc::launch_set_counter(h, tf, s);
+  MC_ACUDA(cudaMemcpyAsync(h.obs, obs_keep, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
+  MC_ACUDA(cudaGetLastError());
+  return MC_OK;
+}
 
 mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* dL_dtheta0, float* dL_dL_rest,
                    float* dL_dk, void* stream) {
@@ -184,64 +321,37 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
   a.fbt = reinterpret_cast<float2*>(A + o_fbt);
   a.dbar = reinterpret_cast<float2*>(A + o_dbar);
 
-  // the recompute passes accumulate the observables again: keep the rollout's values
-  MC_ACUDA(cudaMemcpyAsync(A + o_obs, h.obs, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
+  // inputs (caller memory): outside the cached graph
   if (h.N) k_interleave<<<(h.N + 255) / 256, 256, 0, s>>>(dL_dx, dL_dy, a.adjX, h.N);
-  if (h.E) MC_ACUDA(cudaMemsetAsync(a.adjTh, 0, h.E * sizeof(float), s));
-  if (h.J) MC_ACUDA(cudaMemsetAsync(a.gth0, 0, h.J * sizeof(float), s));
-  if (h.E) MC_ACUDA(cudaMemsetAsync(a.gL, 0, h.E * sizeof(float), s));
-  MC_ACUDA(cudaMemsetAsync(a.gk, 0, 3 * sizeof(float), s));
-  MC_ACUDA(cudaMemsetAsync(adjG[0], 0, 9 * HW * sizeof(float), s));
-  int cur = 0;   // adjG[cur] holds the adjoint of the populations after the step being reversed
-  const int64_t t0 = w->tape_t0;
-  for (int k = n_ck - 1; k >= 0; --k) {
-    const int steps = std::min(K, n - k * K);
-    const int64_t tk = t0 + (int64_t)k * K;
-    // re-run the segment from its checkpoint, keeping every step's state
-    mc_status st = load_state(h, (int)(tk & 1), tape + (size_t)k * sl.bytes, sl, s);
-    if (st != MC_OK) return st;
-    mc::launch_set_counter(h, tk, s);
-    for (int q = 0; q < steps; ++q) {
-      st = save_state(h, (int)((tk + q) & 1), seg + (size_t)q * sl.bytes, sl, s);
-      if (st != MC_OK) return st;
-      mc::enqueue_step(w->plan, s);
+  MC_ACUDA(cudaGetLastError());
+  // the reverse sweep, captured once per (rollout length, checkpoint spacing,
+  // start step, buffers) and replayed
+  const BwdKey key{n, K, w->tape_t0, w->tape, w->adj};
+  if (!w->bwd_exec || !(key == w->bwd_key)) {
+    if (w->bwd_exec) cudaGraphExecDestroy(w->bwd_exec);
+    w->bwd_exec = nullptr;
+    mc::adj_setup(w->plan, h);
+    cudaStream_t cs = adj_capture_stream();
+    MC_ACUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const mc_status st = sweep(w, a, adjG, A + o_obs, seg, sl, n_ck, cs);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+    if (st != MC_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
     }
-    for (int q = steps - 1; q >= 0; --q) {
-      const int64_t tn = tk + q;
-      const int par = (int)(tn & 1);
-      const char* rec = seg + (size_t)q * sl.bytes;
-      st = load_state(h, par, rec, sl, s);
-      if (st != MC_OK) return st;
-      mc::launch_set_counter(h, tn, s);
-      // this step's intermediates (F_el, F_s, rho_bar, F, u)
-      mc::launch_pbd(w->plan, s);
-      mc::launch_bin_scan(w->plan, s);
-      mc::launch_bin_scatter(w->plan, s);
-      mc::launch_deposit_x(w->plan, s, 0);
-      mc::launch_force_spread(w->plan, s, 1, 0);
-      mc::launch_lbm(w->plan, s);
-      a.adjG_next = adjG[cur];
-      a.adjG_cur = adjG[cur ^ 1];
-      a.theta_n = reinterpret_cast<const float*>(rec + sl.theta);
-      mc::launch_adj_step(w->plan, h, a, par, s);
-      cur ^= 1;
-    }
-    MC_ACUDA(cudaGetLastError());
+    MC_ACUDA(ec);
+    const cudaError_t ei = cudaGraphInstantiate(&w->bwd_exec, g, 0);
+    cudaGraphDestroy(g);
+    MC_ACUDA(ei);
+    w->bwd_key = key;
   }
+  MC_ACUDA(cudaGraphLaunch(w->bwd_exec, s));
+  // outputs (caller memory)
   if (h.J) MC_ACUDA(cudaMemcpyAsync(dL_dtheta0, a.gth0, h.J * sizeof(float), cudaMemcpyDeviceToDevice, s));
   if (dL_dL_rest && h.E)
     MC_ACUDA(cudaMemcpyAsync(dL_dL_rest, a.gL, h.E * sizeof(float), cudaMemcpyDeviceToDevice, s));
   if (dL_dk) MC_ACUDA(cudaMemcpyAsync(dL_dk, a.gk, 3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
-  // back to the final state of the rollout
-  const int64_t tf = t0 + n;
-  mc_status st = load_state(h, (int)(tf & 1), tape + (size_t)n_ck * sl.bytes, sl, s);
-  if (st != MC_OK) return st;
-  if (h.N)
-    MC_ACUDA(cudaMemcpyAsync(h.disp, tape + (size_t)(n_ck + 1) * sl.bytes, h.N * sizeof(float2),
-                             cudaMemcpyDeviceToDevice, s));
-  mc::launch_set_counter(h, tf, s);
-  MC_ACUDA(cudaMemcpyAsync(h.obs, A + o_obs, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
-  MC_ACUDA(cudaGetLastError());
   return MC_OK;
 }
 

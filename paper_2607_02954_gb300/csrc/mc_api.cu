@@ -124,6 +124,7 @@ void free_plan(Plan& p, cudaStream_t s) {
 mc_status build_plan(mc_world* const* ws, int n, cudaStream_t s, Plan& out) {
   Plan p;
   p.n_worlds = n;
+  mc::kernel_setup();
   p.max_R = 1;
   p.any_layered = false;
   p.any_ext = false;
@@ -513,6 +514,7 @@ mc_status mc_world_destroy(mc_world* w) {
   if (!w) return MC_OK;
   drop_plans_with(w);
   free_plan(w->plan, w->stream);
+  if (w->bwd_exec) cudaGraphExecDestroy(w->bwd_exec);
   if (w->tape) cudaFreeAsync(w->tape, w->stream);
   if (w->adj) cudaFreeAsync(w->adj, w->stream);
   cudaFreeAsync(w->arena, w->stream);

@@ -146,6 +146,9 @@ constexpr int kKernelsPerStep = 8;
 // --- adjoint (one world) ----------------------------------------------------
 void launch_adj_step(const Plan& p, const WorldDev& h, AdjDev a, int src_parity, cudaStream_t s);
 size_t adj_pbd_smem_per_warp(int maxB, int n_pbd);
+void adj_setup(const Plan& p, const WorldDev& h);   // host set-up of the adjoint kernels (before capture)
+void launch_set_rest(const WorldDev& h, const float* theta0, const float* L_rest, cudaStream_t s);
+void kernel_setup();   // one-time host set-up of the kernels' shared-memory limits
 void launch_loss_splat(const Plan& p, const WorldDev& h, const float* target, int R, float sigma,
                        unsigned long long* acc, float* diff, float* loss, float* gx, float* gy, cudaStream_t s);
 void launch_loss_polyline(const Plan& p, const WorldDev& h, const float2* pos0, const float2* poly, int nv,
@@ -342,6 +345,15 @@ __device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) 
 }  // namespace mc
 
 // One world: its device descriptor, its arena and host-side bookkeeping.
+// What a captured reverse sweep depends on (mc_rollout_backward caches one per world).
+struct BwdKey {
+  int n = 0, K = 0;
+  int64_t t0 = -1;
+  void* tape = nullptr;
+  void* adj = nullptr;
+  bool operator==(const BwdKey& o) const { return n == o.n && K == o.K && t0 == o.t0 && tape == o.tape && adj == o.adj; }
+};
+
 struct mc_world {
   mc::WorldDev h{};               // device descriptor (host copy)
   void* arena = nullptr;          // one allocation holding every device array
@@ -359,4 +371,6 @@ struct mc_world {
   int64_t tape_t0 = 0;
   void* adj = nullptr;            // adjoint buffers + per-segment step tape
   size_t adj_bytes = 0;
+  cudaGraphExec_t bwd_exec = nullptr;   // captured reverse sweep
+  BwdKey bwd_key;
 };

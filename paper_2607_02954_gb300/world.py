@@ -165,6 +165,31 @@ class World:
     def rollout_forward(self, n_steps: int, ckpt_every: int = 100, stream=None):
         L.check(self._lib.mc_rollout_forward(self.handle, int(n_steps), int(ckpt_every), stream_handle(stream)))
 
+    def rollout_rewind(self, stream=None):
+        """Back to the start of the last recorded rollout (see mc_rollout_rewind)."""
+        L.check(self._lib.mc_rollout_rewind(self.handle, stream_handle(stream)))
+
+    def set_rest(self, theta0=None, L_rest=None, stream=None):
+        """New static rest angles [J] and/or rest lengths [E] (numpy or torch CUDA)."""
+        torch = _torch()
+        keep, ptrs = [], []
+        on_device = any(isinstance(v, torch.Tensor) and v.is_cuda for v in (theta0, L_rest) if v is not None)
+        for v in (theta0, L_rest):
+            if v is None:
+                ptrs.append(None)
+            elif on_device:
+                t = torch.as_tensor(v).float().contiguous().cuda()
+                keep.append(t)
+                ptrs.append(ctypes.c_void_p(t.data_ptr()))
+            else:
+                a = np.ascontiguousarray(v, np.float32)
+                keep.append(a)
+                ptrs.append(ctypes.c_void_p(a.ctypes.data))
+        L.check(self._lib.mc_world_set_rest(self.handle, ptrs[0], ptrs[1],
+                                            L.MC_MEM_DEVICE if on_device else L.MC_MEM_HOST, stream_handle(stream)))
+        if on_device:
+            torch.cuda.current_stream().synchronize()
+
     def rollout_backward(self, dL_dx, dL_dy, stream=None):
         """dL_dx, dL_dy: torch CUDA float32 [N]; returns dL/dtheta0 as a torch CUDA tensor [J]."""
         torch = _torch()

@@ -226,3 +226,59 @@ def test_splat_folding_gradient_matches_oracle():
     (go,) = torch.autograd.grad(want, th0)
     assert abs(float(loss.item()) - float(want.detach())) <= 1e-4 * float(want.detach())
     assert np.max(np.abs(g - t2n(go))) <= RTOL * np.max(np.abs(t2n(go)))
+
+
+def test_rewind_and_set_rest_reproduce_fresh_worlds_bitwise():
+    """An optimisation loop on one world: rewinding to the rollout's start and
+    setting new rest angles gives exactly the rollout of a world created with
+    those rest angles."""
+    from paper_2607_02954_gb300 import World
+    spec = synth.tiny_world(10, side=64, lengths=(20, 14, 9))
+    n, K = 30, 8
+    rng = np.random.default_rng(12)
+    th_new = (spec.theta0 + 0.1 * rng.standard_normal(spec.J)).astype(np.float32)
+    w = World(spec)
+    w.rollout_forward(n, K)
+    first = w.state(fluid=True)
+    w.rollout_rewind()
+    w.set_rest(theta0=th_new)
+    w.rollout_forward(n, K)
+    moved = w.state(fluid=True)
+    w.rollout_rewind()
+    w.set_rest(theta0=spec.theta0)
+    w.rollout_forward(n, K)
+    again = w.state(fluid=True)
+    w.close()
+    spec2 = synth.tiny_world(10, side=64, lengths=(20, 14, 9))
+    spec2.theta0 = th_new
+    ref = World(spec2)
+    ref.step(n)
+    want = ref.state(fluid=True)
+    ref.close()
+    for k in first:
+        assert np.array_equal(moved[k], want[k]), k
+        assert np.array_equal(again[k], first[k]), k
+
+
+def test_replayed_reverse_sweep_matches_the_captured_one():
+    """The second backward of the same rollout (rewind + forward) replays the
+    captured sweep; the gradient agrees with the first one (float atomics:
+    to rounding) and with the oracle."""
+    from paper_2607_02954_gb300 import World
+    spec = synth.tiny_world(11, side=32, lengths=(9, 8))
+    n, K = 24, 5
+    rng = np.random.default_rng(13)
+    gx = torch.as_tensor(rng.standard_normal(spec.N), dtype=torch.float32).cuda()
+    gy = torch.as_tensor(rng.standard_normal(spec.N), dtype=torch.float32).cuda()
+    w = World(spec)
+    w.rollout_forward(n, K)
+    g1 = t2n(w.rollout_backward(gx, gy)).astype(np.float64)
+    w.rollout_rewind()
+    w.rollout_forward(n, K)
+    g2 = t2n(w.rollout_backward(gx, gy)).astype(np.float64)
+    w.close()
+    scale = np.max(np.abs(g1))
+    assert np.max(np.abs(g1 - g2)) <= 1e-5 * scale
+    go = t2n(O.final_position_gradient(O.World(spec), n, torch.as_tensor(t2n(gx), dtype=torch.float64),
+                                       torch.as_tensor(t2n(gy), dtype=torch.float64)))
+    assert np.max(np.abs(g2 - go)) <= RTOL * np.max(np.abs(go))
