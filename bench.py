@@ -44,6 +44,12 @@ if ROOT not in sys.path:
 # the stages one step runs, with their mc_step_stage ids (the scan stage is two kernels)
 STAGES = [("pbd", 0), ("bin_scan", 1), ("bin_scatter", 2), ("deposit_x", 3), ("force_lbm", 7), ("interp_advance", 6)]
 KERNELS_PER_STEP = 7
+GRAPH_STEPS = 16   # mc_step replays graphs of 16 steps: PBD, then 15 x (previous advance + PBD), 16 x (scan (2),
+                   # scatter, deposit, force + LBM), and the last advance = 97 kernels; leftover steps run 7 each
+
+
+def graph_launches(steps: int) -> int:
+    return (steps // GRAPH_STEPS) * (2 + GRAPH_STEPS * 6 - 1) + (steps % GRAPH_STEPS) * KERNELS_PER_STEP
 # k_force_lbm, the dominant kernel: per cell read f 36 + rho_x 4, write f' 36 + u 8;
 # per bead read the binned record (position 16, F_el 8, id 4), write F_s 8
 FORCE_LBM_BYTES_PER_CELL = 84
@@ -537,7 +543,7 @@ def main():
                    "l2": "state 1.8 GB > L2: no flush needed" if C >= 4096 * 4096 else "state may fit in L2; per-step timing includes no flush"},
         "e2e": {"value": e2e_val, "unit": "particle-steps/s", "steps": e2e_steps,
                 "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps},
-        "gpu_launches": args.steps * KERNELS_PER_STEP,
+        "gpu_launches": graph_launches(args.steps),
         "roofline": {"bound": "hbm", "kernel": "k_force_lbm", "achieved": top_gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": top_gbs / hbm_peak, "peak_kind": peak_kind,
                      "traffic": KERNEL_TRAFFIC.get((args.workload, kernel_fingerprint())),

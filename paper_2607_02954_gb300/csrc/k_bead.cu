@@ -20,6 +20,65 @@ __device__ __forceinline__ void cpa4(void* sdst, const void* gsrc) {
 __device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 
+// a8 for one bead at p = X^n with interpolated velocity U: the velocity
+// record, the watchdog (|U| > u_max or non-finite: flag the world, keep the
+// bead), X^{n+1} = wrap(X^n + dt U) in cell + fraction form, D += dt U.
+// Returns X^{n+1} (X^n when the watchdog fired).
+__device__ __forceinline__ float4 advance_tail(const WorldDev& w, int i, float4 p, float Ux, float Uy) {
+  w.ubead[i] = make_float2(Ux, Uy);
+  const float m2 = Ux * Ux + Uy * Uy;
+  if (!(m2 <= w.u_max * w.u_max)) {   // also catches NaN
+    atomicOr(w.flags, kFlagUnstable);
+    return p;
+  }
+  const int W = w.W, H = w.H;
+  int cx = cell_x(p), cy = cell_y(p);
+  float fx = p.x + w.dt * Ux, fy = p.y + w.dt * Uy;
+  const float kx = floorf(fx), ky = floorf(fy);
+  fx -= kx;
+  fy -= ky;
+  cx += (int)kx;
+  cy += (int)ky;
+  if (fx >= 1.0f) { fx = 0.0f; cx += 1; }   // a tiny negative fraction rounded up to 1
+  if (fy >= 1.0f) { fy = 0.0f; cy += 1; }
+  cx = wrap_once(cx, W);
+  cy = wrap_once(cy, H);
+  const float4 q = make_float4(fx, fy, __int_as_float(cx), __int_as_float(cy));
+  w.pos[i] = q;
+  float2 d = w.disp[i];
+  d.x += w.dt * Ux;
+  d.y += w.dt * Uy;
+  w.disp[i] = d;
+  return q;
+}
+
+// U_i = sum_c delta_h(c - X_i) u(c) over the 4x4 stencil of p.
+__device__ __forceinline__ float2 interp_u(const WorldDev& w, const float4 p) {
+  const int W = w.W, H = w.H;
+  const int cx = cell_x(p), cy = cell_y(p);
+  float wx[4], wy[4];
+  peskin4(p.x, wx);
+  peskin4(p.y, wy);
+  int ix[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) ix[a] = wrap_once(cx - 1 + a, W);
+  float Ux = 0.0f, Uy = 0.0f;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const float2* row = w.u + (size_t)wrap_once(cy - 1 + b, H) * W;
+    float rx = 0.0f, ry = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const float2 v = row[ix[a]];
+      rx = fmaf(wx[a], v.x, rx);
+      ry = fmaf(wx[a], v.y, ry);
+    }
+    Ux = fmaf(wy[b], rx, Ux);
+    Uy = fmaf(wy[b], ry, Uy);
+  }
+  return make_float2(Ux, Uy);
+}
+
 __device__ __forceinline__ float sq(float v) { return v * v; }
 
 // Constants of the PBD passes, read once per warp.
@@ -112,7 +171,7 @@ __device__ __forceinline__ void bead_out(const WorldDev& w, const PbdConst& k, b
 // Jacobi PBD of a filament of at most 64 beads in registers: lane l holds
 // beads, edges and joints 2l and 2l + 1, and reads its neighbours' values by
 // warp shuffles.  The same arithmetic, in the same order, as pbd_smem.
-template <bool kExt>
+template <bool kExt, bool kAdvance>
 __device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, int b0, int B, int e0, int j0,
                                           long long t) {
   constexpr unsigned kAll = 0xffffffffu;
@@ -121,8 +180,19 @@ __device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, 
   const int i0 = 2 * lane, i1 = i0 + 1;
   const bool hb0 = i0 < B, hb1 = i1 < B, he0 = i0 < nE, he1 = i1 < nE, hj0 = i0 < nJ, hj1 = i1 < nJ;
   const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  const float4 P0 = hb0 ? w.pos[b0 + i0] : z4;
-  const float4 P1 = hb1 ? w.pos[b0 + i1] : z4;
+  float4 P0 = hb0 ? w.pos[b0 + i0] : z4;
+  float4 P1 = hb1 ? w.pos[b0 + i1] : z4;
+  if (kAdvance) {
+    // a8 of the previous step for the lane's beads, then this step's PBD from X^n
+    if (hb0) {
+      const float2 U = interp_u(w, P0);
+      P0 = advance_tail(w, b0 + i0, P0, U.x, U.y);
+    }
+    if (hb1) {
+      const float2 U = interp_u(w, P1);
+      P1 = advance_tail(w, b0 + i1, P1, U.x, U.y);
+    }
+  }
   float th0 = he0 ? w.theta[e0 + i0] : 0.0f;
   float th1 = he1 ? w.theta[e0 + i1] : 0.0f;
   const float L0 = he0 ? (kExt ? rest_length(w, e0 + i0, t) : w.L_rest[e0 + i0]) : 1.0f;
@@ -233,7 +303,7 @@ __device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, 
 // bead corrections live in a per-warp slice of shared memory; every pass
 // reads the slice, then writes corrections, with a warp barrier in between,
 // so all corrections of a pass see the state before it.
-template <bool kExt>
+template <bool kExt, bool kAdvance>
 __device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, int b0, int B, int e0, int j0,
                                           long long t, float* s, int maxB) {
   const int lane = threadIdx.x & 31;
@@ -251,7 +321,16 @@ __device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, 
   float4* P = reinterpret_cast<float4*>(s + 10 * maxB);    // bead positions
   float4* D = reinterpret_cast<float4*>(s + 14 * maxB);    // joint drive parameters
   // stage the filament's inputs in shared memory, every copy in flight at once
-  for (int i = lane; i < B; i += 32) cpa16(&P[i], &w.pos[b0 + i]);
+  if (kAdvance) {
+    // a8 of the previous step, the advanced positions staged directly
+    for (int i = lane; i < B; i += 32) {
+      const float4 p = w.pos[b0 + i];
+      const float2 U = interp_u(w, p);
+      P[i] = advance_tail(w, b0 + i, p, U.x, U.y);
+    }
+  } else {
+    for (int i = lane; i < B; i += 32) cpa16(&P[i], &w.pos[b0 + i]);
+  }
   for (int e = lane; e < nE; e += 32) {
     cpa4(&th[e], &w.theta[e0 + e]);
     if (!kExt || !w.ldrive) cpa4(&Lr[e], &w.L_rest[e0 + e]);
@@ -352,8 +431,8 @@ __device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, 
 // coordinates.  Filaments of at most 64 beads run in registers; longer ones
 // in the warp's slice of dynamic shared memory (maxB floats per array; zero
 // when no filament of the launch is longer than 64 beads).
-template <bool kExt>
-__global__ void __launch_bounds__(256) k_pbd(const WorldDev* __restrict__ worlds,
+template <bool kExt, bool kAdvance>
+__global__ void __launch_bounds__(256, 4) k_pbd(const WorldDev* __restrict__ worlds,
                                              const int2* __restrict__ items, int n_items, int maxB) {
   extern __shared__ __align__(16) float smem[];   // maxB is a multiple of 4: float4 slices stay aligned
   const int wpb = blockDim.x >> 5;
@@ -366,10 +445,13 @@ __global__ void __launch_bounds__(256) k_pbd(const WorldDev* __restrict__ worlds
   const int b0 = w.fil_off[f];
   const int B = w.fil_off[f + 1] - b0;
   const int e0 = b0 - f, j0 = b0 - 2 * f;
-  const long long t = *w.t;
+  // with kAdvance the counter still holds the previous step (the scan of
+  // this step advances it)
+  const long long t = *w.t + (kAdvance ? 1 : 0);
   const PbdConst k = pbd_const(w);
-  float fmax = B <= 64 ? pbd_regs<kExt>(w, k, b0, B, e0, j0, t)
-                       : pbd_smem<kExt>(w, k, b0, B, e0, j0, t, smem + (size_t)warp * maxB * kPbdFloatsPerBead, maxB);
+  float fmax = B <= 64 ? pbd_regs<kExt, kAdvance>(w, k, b0, B, e0, j0, t)
+                       : pbd_smem<kExt, kAdvance>(w, k, b0, B, e0, j0, t,
+                                                  smem + (size_t)warp * maxB * kPbdFloatsPerBead, maxB);
   // largest |F_el| component of the world this step (bounds the spread's
   // fixed-point scale); non-negative floats order like their bit patterns
   for (int o = 16; o > 0; o >>= 1) fmax = fmaxf(fmax, __shfl_xor_sync(0xffffffffu, fmax, o));
@@ -505,11 +587,7 @@ __global__ void __launch_bounds__(kBeadChunk) k_interp_advance(const WorldDev* _
                                                                const int2* __restrict__ items) {
   const int2 it = items[blockIdx.x];
   const WorldDev& w = worlds[it.x];
-  if (it.y == 0 && threadIdx.x == 0) {
-    const long long t = *w.t + 1;
-    *w.t = t;
-    w.fel_max[t & 1] = 0u;   // slot of the next step; this step's stays readable
-  }
+  if (it.y == 0 && threadIdx.x == 0) *w.t += 1;
   const int i = it.y + threadIdx.x;
   const int W = w.W, H = w.H;
   if (kExt && w.observe && w.energy) {
@@ -536,59 +614,17 @@ __global__ void __launch_bounds__(kBeadChunk) k_interp_advance(const WorldDev* _
     obs_add_warp(&w.obs[2], e);
   }
   if (i >= w.N) return;
-  float4 p = w.pos[i];
-  int cx = cell_x(p), cy = cell_y(p);
-  float wx[4], wy[4];
-  peskin4(p.x, wx);
-  peskin4(p.y, wy);
-  int ix[4], iy[4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    ix[a] = wrap_once(cx - 1 + a, W);
-    iy[a] = wrap_once(cy - 1 + a, H) * W;
-  }
-  float Ux = 0.0f, Uy = 0.0f;
+  const float4 p = w.pos[i];
+  float2 U;
   if (kExt && w.layers == 2) {
     // two-layer filament: mean of the velocities at X +- delta n
     const float2 n = w.nrm[i];
     const float2 Up = layer_velocity(w, p, n, w.layer_half), Um = layer_velocity(w, p, n, -w.layer_half);
-    Ux = 0.5f * (Up.x + Um.x);
-    Uy = 0.5f * (Up.y + Um.y);
+    U = make_float2(0.5f * (Up.x + Um.x), 0.5f * (Up.y + Um.y));
   } else {
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      float rx = 0.0f, ry = 0.0f;
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const float2 v = w.u[iy[b] + ix[a]];
-        rx = fmaf(wx[a], v.x, rx);
-        ry = fmaf(wx[a], v.y, ry);
-      }
-      Ux = fmaf(wy[b], rx, Ux);
-      Uy = fmaf(wy[b], ry, Uy);
-    }
+    U = interp_u(w, p);
   }
-  w.ubead[i] = make_float2(Ux, Uy);
-  const float m2 = Ux * Ux + Uy * Uy;
-  if (!(m2 <= w.u_max * w.u_max)) {   // also catches NaN
-    atomicOr(w.flags, kFlagUnstable);
-    return;
-  }
-  float fx = p.x + w.dt * Ux, fy = p.y + w.dt * Uy;
-  const float kx = floorf(fx), ky = floorf(fy);
-  fx -= kx;
-  fy -= ky;
-  cx += (int)kx;
-  cy += (int)ky;
-  if (fx >= 1.0f) { fx = 0.0f; cx += 1; }   // a tiny negative fraction rounded up to 1
-  if (fy >= 1.0f) { fy = 0.0f; cy += 1; }
-  cx = wrap_once(cx, W);
-  cy = wrap_once(cy, H);
-  w.pos[i] = make_float4(fx, fy, __int_as_float(cx), __int_as_float(cy));
-  float2 d = w.disp[i];
-  d.x += w.dt * Ux;
-  d.y += w.dt * Uy;
-  w.disp[i] = d;
+  advance_tail(w, i, p, U.x, U.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -655,8 +691,19 @@ void launch_pbd(const Plan& p, cudaStream_t s) {
   const int grid = (p.n_fil_items + wpb - 1) / wpb;
   // worlds with a rest-length drive, observables or two layers need the
   // extended kernel; it computes every other world exactly as the plain one
-  auto kern = p.any_ext ? k_pbd<true> : k_pbd<false>;
+  auto kern = p.any_ext ? k_pbd<true, false> : k_pbd<false, false>;
   kern<<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
+}
+
+// a8 of the previous step fused with this step's a1-a3 (plans without the
+// extended features): the counter is advanced by this step's scan.
+void launch_advance_pbd(const Plan& p, cudaStream_t s) {
+  if (p.n_fil_items == 0) return;
+  const int mb = (p.max_B + 3) & ~3;
+  const int wpb = pbd_warps_per_block(mb);
+  const size_t smem = p.max_B <= 64 ? 0 : (size_t)wpb * mb * kPbdFloatsPerBead * sizeof(float);
+  const int grid = (p.n_fil_items + wpb - 1) / wpb;
+  k_pbd<false, true><<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
 }
 
 // Shared-memory limits set once per process, outside any stream capture: the
@@ -665,8 +712,9 @@ void kernel_setup() {
   static std::once_flag once;
   std::call_once(once, [] {
     const int most = 227 * 1024;
-    cudaFuncSetAttribute(k_pbd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    cudaFuncSetAttribute(k_pbd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(k_pbd<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(k_pbd<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(k_pbd<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
   });
 }
 

@@ -26,11 +26,21 @@ __device__ __forceinline__ int block_sum_256(int v, int* red) {
   return r;
 }
 
+// The first block of each world also keeps the step counter's bookkeeping:
+// with inc_t (the step's PBD ran fused with the previous step's advance,
+// which left the counter behind) it advances the counter, and it clears the
+// next step's F_el-maximum slot (this step's, written by the PBD, stays
+// readable for the spread).
 __global__ void __launch_bounds__(256) k_scan_sums(const WorldDev* __restrict__ worlds,
-                                                   const int2* __restrict__ items) {
+                                                   const int2* __restrict__ items, int inc_t) {
   __shared__ int red[9];
   const int2 it = items[blockIdx.x];
   const WorldDev& w = worlds[it.x];
+  if (it.y == 0 && threadIdx.x == 0) {
+    const long long t = *w.t + inc_t;
+    if (inc_t) *w.t = t;
+    w.fel_max[(t + 1) & 1] = 0u;
+  }
   const int base = it.y * kScanChunk;
   const int end = min(base + kScanChunk, w.n_bins);
   int s = 0;
@@ -113,13 +123,32 @@ __global__ void __launch_bounds__(kCellChunk) k_lbm(const WorldDev* __restrict__
 // ---------------------------------------------------------------------------
 // Launchers and the step sequence.
 // ---------------------------------------------------------------------------
-void launch_bin_scan(const Plan& p, cudaStream_t s) {
-  k_scan_sums<<<p.n_scan_items, 256, 0, s>>>(p.d_worlds, p.d_scan_items);
+void launch_bin_scan(const Plan& p, cudaStream_t s, int inc_t) {
+  k_scan_sums<<<p.n_scan_items, 256, 0, s>>>(p.d_worlds, p.d_scan_items, inc_t);
   k_scan_apply<<<p.n_scan_items, 256, 0, s>>>(p.d_worlds, p.d_scan_items);
 }
 
 void launch_lbm(const Plan& p, cudaStream_t s, int layered_only) {
   if (p.n_cell_items) k_lbm<<<p.n_cell_items, kCellChunk, 0, s>>>(p.d_worlds, p.d_cell_items, layered_only);
+}
+
+// n steps; in plans without the extended features every step after the
+// first runs its PBD fused with the previous step's advance (the same
+// arithmetic, one kernel and one position round trip fewer).
+void enqueue_steps(const Plan& p, int n, cudaStream_t s) {
+  if (p.any_ext || n < 2) {
+    for (int k = 0; k < n; ++k) enqueue_step(p, s);
+    return;
+  }
+  for (int k = 0; k < n; ++k) {
+    if (k == 0) launch_pbd(p, s);
+    else launch_advance_pbd(p, s);   // a8 of step k - 1 + a1-a3 of step k
+    launch_bin_scan(p, s, k > 0);
+    launch_bin_scatter(p, s);
+    launch_deposit_x(p, s, 0);
+    launch_force_lbm(p, s);
+  }
+  launch_interp_advance(p, s);
 }
 
 void enqueue_step(const Plan& p, cudaStream_t s) {

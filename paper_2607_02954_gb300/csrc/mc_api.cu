@@ -193,7 +193,7 @@ mc_status run_steps(Plan& p, int n, cudaStream_t s) {
     if (!p.graph) {
       cudaStream_t cs = capture_stream();
       MC_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-      for (int k = 0; k < kGraphSteps; ++k) mc::enqueue_step(p, cs);
+      mc::enqueue_steps(p, kGraphSteps, cs);
       cudaGraph_t g = nullptr;
       MC_CUDA(cudaStreamEndCapture(cs, &g));
       cudaError_t e = cudaGraphInstantiate(&p.graph, g, 0);

@@ -129,7 +129,7 @@ struct Plan {
 
 // --- stage launchers (one launch covers every world of the plan) ---------
 void launch_pbd(const Plan& p, cudaStream_t s);
-void launch_bin_scan(const Plan& p, cudaStream_t s);      // two kernels
+void launch_bin_scan(const Plan& p, cudaStream_t s, int inc_t = 0);      // two kernels
 void launch_bin_scatter(const Plan& p, cudaStream_t s);
 // a4 + x pass of a5; store_fields also writes rho_s of each tile
 void launch_deposit_x(const Plan& p, cudaStream_t s, int store_fields);
@@ -141,6 +141,8 @@ void launch_layer_spread(const Plan& p, cudaStream_t s);   // two-layer worlds: 
 void launch_force_lbm(const Plan& p, cudaStream_t s);   // y pass of a5 + a6 + a7 in one kernel
 void launch_interp_advance(const Plan& p, cudaStream_t s);
 void enqueue_step(const Plan& p, cudaStream_t s);
+void enqueue_steps(const Plan& p, int n, cudaStream_t s);   // n steps, fused bead stages where possible
+void launch_advance_pbd(const Plan& p, cudaStream_t s);
 constexpr int kKernelsPerStep = 8;
 
 // --- adjoint (one world) ----------------------------------------------------
