@@ -103,6 +103,8 @@ class Consts:
     pbd_order: int = 0   # 0: Jacobi passes; 1: red-black (two-colour Gauss-Seidel) passes
     layers: int = 1      # 1: beads are the immersed-boundary points; 2: two-layer filament
     layer_half: float = 0.5   # half distance between the two layers (cells)
+    ib: int = 0          # 0: penalty coupling (F_el spread); 1: direct forcing with MDF passes
+    mdf_iters: int = 0   # multi-direct-forcing passes per step (ib = 1)
 
     @property
     def tau_plus(self) -> float:
@@ -123,7 +125,8 @@ def consts(params) -> Consts:
                   k_bend=r(params.k_bend), k_stretch=r(params.k_stretch), k_shear=r(params.k_shear),
                   k_rep=r(params.k_rep), sigma=r(params.sigma), orient=r(params.orient),
                   n_pbd=int(params.n_pbd), pbd_order=int(getattr(params, "pbd_order", 0)),
-                  layers=int(getattr(params, "layers", 1)), layer_half=r(getattr(params, "layer_half", 0.5)))
+                  layers=int(getattr(params, "layers", 1)), layer_half=r(getattr(params, "layer_half", 0.5)),
+                  ib=int(getattr(params, "ib", 0)), mdf_iters=int(getattr(params, "mdf_iters", 0)))
 
 
 # ---------------------------------------------------------------------------
@@ -453,6 +456,8 @@ def step(world: World, st: State, theta0: Optional[torch.Tensor] = None, record:
     """One time step in the order a1..a8 (see the module docstring).
     theta0 may be given to differentiate with respect to the rest angles.
     Returns (new state, dict of intermediates or None)."""
+    if world.c.ib == 1:
+        return step_direct_forcing(world, st, theta0, record)
     c, H, W, topo = world.c, world.H, world.W, world.topo
     th0 = world.theta0 if theta0 is None else theta0
     theta_rest = rest_angles(th0, world.amp, world.freq, world.phase, st.t)          # a1
@@ -484,6 +489,63 @@ def step(world: World, st: State, theta0: Optional[torch.Tensor] = None, record:
     if record:
         rec = dict(theta_rest=theta_rest, x_hat=x_hat, F_el=F_el, rho_s=rho_s, rho_bar=rho_bar,
                    F_s=F_s, F=F, u=u, U=U)
+        rec.update(step_observables(world, st, idx, w, theta_rest, L_rest))
+    return new, rec
+
+
+# ---------------------------------------------------------------------------
+# Direct forcing with Multi-Direct Forcing (Fluid-filament Interaction: the
+# nodes sample the fluid velocity for their drag, the filament broadcasts its
+# own velocity back onto the grid, and MDF, Wang et al. 2008, is named among
+# the practices against leakage).  Reading, in the paper's order of the two
+# exchanges:
+#   1. the steric force F_s (a4-a6) acts on the fluid as a body force, and
+#      u* = (sum_i c_i f_i + F/2)/rho is the fluid velocity before the
+#      filament's forcing (the half-force velocity of Guo's scheme);
+#   2. drag: each node is carried by the fluid, X~ = X + dt U*, U* = I[u*](X);
+#   3. the filament's own motion: PBD from X~ gives x_hat, and the node
+#      velocity is U_s = U* + (x_hat - X~)/dt;
+#   4. broadcast: m passes of direct forcing make the fluid at the nodes move
+#      with U_s: dF_i = 2 rho_i (U_s,i - I[u](X_i)) (rho_i = I[rho](X_i); a
+#      force density F moves the half-force velocity by F/(2 rho)), then
+#      F += S[dF], u += S[dF]/(2 rho);
+#   5. a7 with the total F; the nodes move with their own velocity:
+#      X^{n+1} = X + dt U_s.
+# The per-node force the filament exerts is sum over the passes of dF_i.
+# ---------------------------------------------------------------------------
+def step_direct_forcing(world: World, st: State, theta0: Optional[torch.Tensor] = None, record: bool = False):
+    c, H, W, topo = world.c, world.H, world.W, world.topo
+    th0 = world.theta0 if theta0 is None else theta0
+    theta_rest = rest_angles(th0, world.amp, world.freq, world.phase, st.t)          # a1
+    L_rest = world.rest_lengths(st.t)
+    idx, w = stencil(st.X, H, W)
+    rho_s = spread(idx, w, torch.ones(st.X.shape[0], dtype=F64), H, W)                # a4
+    rho_bar = gaussian_blur(rho_s, c.sigma)                                            # a5
+    grad = central_gradient(rho_bar)
+    F_s = -c.k_rep * interpolate(idx, w, grad)                                          # a6
+    F = spread(idx, w, F_s, H, W)
+    rho, ux, uy = macroscopic(st.f, F)                                                  # 1
+    u = torch.stack([ux, uy], 0)
+    U_star = interpolate(idx, w, u)
+    X_pred = torch.stack([wrap(st.X[:, 0] + c.dt * U_star[:, 0], W),                  # 2
+                          wrap(st.X[:, 1] + c.dt * U_star[:, 1], H)], 1)
+    x_hat, theta_hat = pbd(X_pred, st.theta, theta_rest, L_rest, topo, c, H, W)       # 3
+    U_s = U_star + (x_hat - X_pred) / c.dt
+    F_ib = torch.zeros_like(U_s)
+    for _ in range(c.mdf_iters):                                                        # 4
+        r = interpolate(idx, w, rho)
+        dF = 2.0 * r[:, None] * (U_s - interpolate(idx, w, u))
+        G = spread(idx, w, dF, H, W)
+        F = F + G
+        u = u + G / (2.0 * rho)
+        F_ib = F_ib + dF
+    f_new, u_new = lbm_step(st.f, F, c)                                                 # 5
+    X_new = torch.stack([wrap(st.X[:, 0] + c.dt * U_s[:, 0], W), wrap(st.X[:, 1] + c.dt * U_s[:, 1], H)], 1)
+    new = State(X=X_new, theta=theta_hat, f=f_new, D=st.D + c.dt * U_s, t=st.t + 1)
+    rec = None
+    if record:
+        rec = dict(theta_rest=theta_rest, x_hat=x_hat, F_el=F_ib, rho_s=rho_s, rho_bar=rho_bar,
+                   F_s=F_s, F=F, u=u_new, U=U_s, U_star=U_star, u_mdf=u)
         rec.update(step_observables(world, st, idx, w, theta_rest, L_rest))
     return new, rec
 

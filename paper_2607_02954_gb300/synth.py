@@ -48,6 +48,10 @@ class Params:
     pbd_order: 0 Jacobi passes, 1 red-black (two-colour Gauss-Seidel) passes.
     layers: 1 = the beads are the immersed-boundary points; 2 = two-layer
             filament, points at X +- layer_half n (n the filament normal).
+    ib: 0 = penalty coupling (kappa spreads the PBD correction as a force);
+        1 = direct forcing: the fluid carries the nodes, PBD corrects them,
+        and mdf_iters passes of multi-direct forcing make the fluid at the
+        nodes follow the corrected motion (kappa unused).
     """
 
     nu: float = 0.1
@@ -64,6 +68,8 @@ class Params:
     pbd_order: int = 0
     layers: int = 1
     layer_half: float = 0.5
+    ib: int = 0
+    mdf_iters: int = 0
 
 
 @dataclasses.dataclass

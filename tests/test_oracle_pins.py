@@ -939,3 +939,107 @@ def test_step_steric_force_is_pairwise_repulsion():
     _, rec = O.step(w, st, record=True)
     brute = _pairwise_steric(np.stack([x.astype(np.float64), y.astype(np.float64)], 1), 16, 16, w.c)
     assert np.allclose(rec["F_s"].numpy(), brute, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Direct forcing with multi-direct forcing passes (Fluid-filament Interaction).
+# ---------------------------------------------------------------------------
+def _uniform_flow_f0(H, W, u0):
+    feq = O.equilibrium(torch.ones(H, W, dtype=F64), torch.full((H, W), u0[0], dtype=F64),
+                        torch.full((H, W), u0[1], dtype=F64))
+    return (feq - O.d2q9_weights()[:, None, None]).numpy().astype(np.float32)
+
+
+def test_direct_forcing_rest_filament_rides_a_uniform_flow():
+    """A straight filament at its rest shape in a uniform flow: the fluid
+    already moves every node with the filament's own velocity, so the direct
+    forcing is zero, the flow stays uniform and every node moves by dt u."""
+    B = 8
+    x = np.float32(4.25) + np.arange(B, dtype=np.float32)
+    y = np.full(B, 9.6, np.float32)
+    spec = synth._world("rest", 24, 24, [B], x, y, np.zeros(B - 1, np.float32), np.zeros(B - 2),
+                        np.zeros(B - 2), np.zeros(B - 2), np.zeros(B - 2),
+                        params=synth.Params(k_rep=0.0, ib=1, mdf_iters=4))
+    spec.f0 = _uniform_flow_f0(24, 24, (0.02, -0.013))
+    w = O.World(spec)
+    st = w.initial_state()
+    rho, ux, uy = O.macroscopic(st.f, torch.zeros(2, 24, 24, dtype=F64))
+    f0 = st.f.clone()
+    for _ in range(3):
+        st, rec = O.step(w, st, record=True)
+        assert float(rec["F_el"].abs().max()) < 1e-12
+    assert torch.allclose(st.f, f0, atol=1e-14)
+    assert torch.allclose(st.D[:, 0], torch.full((B,), 3 * float(ux[0, 0]), dtype=F64), atol=1e-13)
+    assert torch.allclose(st.D[:, 1], torch.full((B,), 3 * float(uy[0, 0]), dtype=F64), atol=1e-13)
+
+
+@pytest.mark.parametrize("m", [1, 2, 5])
+def test_mdf_pass_shrinks_an_isolated_node_residual_by_55_over_64(m):
+    """Fluid at rest (rho = 1) and two nodes whose stencils do not overlap:
+    one pass changes the velocity interpolated at a node by
+    sum_c delta_h(c - X)^2 (U_s - U) = (3/8)^2 (U_s - U) (the Peskin kernel's
+    sum of squares is 3/8 per axis), so after m passes the node velocity
+    misses U_s by (1 - 9/64)^m of the initial miss."""
+    x = np.array([5.3, 16.8], np.float32)
+    y = np.array([7.45, 7.2], np.float32)
+    spec = synth._world("iso", 24, 24, [2], x, y, np.zeros(1, np.float32), np.zeros(0), np.zeros(0),
+                        np.zeros(0), np.zeros(0), params=synth.Params(k_rep=0.0, ib=1, mdf_iters=m))
+    spec.L_rest = np.array([10.0], np.float32)   # stretched: PBD moves the nodes
+    w = O.World(spec)
+    st = w.initial_state()
+    _, rec = O.step(w, st, record=True)
+    idx, wt = O.stencil(st.X, 24, 24)
+    U_end = O.interpolate(idx, wt, rec["u_mdf"])
+    miss0 = rec["U_star"] - rec["U"]
+    assert float(miss0.abs().max()) > 1e-3
+    assert torch.allclose(U_end - rec["U"], (55.0 / 64.0) ** m * miss0, atol=1e-13)
+
+
+def test_direct_forcing_changes_fluid_momentum_by_the_total_force():
+    """Guo forcing adds the force density to the momentum of every cell, and
+    the spread keeps the sum of the node forces: over one step the fluid
+    momentum changes by sum_i (F_s,i + F_ib,i)."""
+    spec = synth.tiny_world(4, side=16, lengths=(6, 5, 4))
+    spec.params = synth.Params(ib=1, mdf_iters=3)
+    w = O.World(spec)
+    st = w.initial_state()
+
+    def momentum(f):
+        return torch.stack([sum(cx * f[i] for i, (cx, cy) in enumerate(O.D2Q9_C)).sum(),
+                            sum(cy * f[i] for i, (cx, cy) in enumerate(O.D2Q9_C)).sum()])
+
+    new, rec = O.step(w, st, record=True)
+    total = (rec["F_s"] + rec["F_el"]).sum(0)
+    assert float(rec["F_el"].abs().max()) > 1e-4
+    assert torch.allclose(momentum(new.f) - momentum(st.f), total, atol=1e-13)
+
+
+def test_direct_forcing_dimer_in_shear_is_carried_then_restored():
+    """A vertical dimer at its rest length in the shear flow u = (g (y - yc), 0):
+    the fluid carries the nodes to X~ (stretching the edge), the stretch pass
+    with unit stiffness restores the length along the carried edge, and the
+    nodes end there: X^{n+1} = X~ -/+ (l - L)/2 e_hat, |X1 - X0| = L."""
+    g, yc, L = 0.01, 13.7, 3.0
+    H = W = 32
+    yy = torch.arange(H, dtype=F64)[:, None].expand(H, W)
+    feq = O.equilibrium(torch.ones(H, W, dtype=F64), g * (yy - yc), torch.zeros(H, W, dtype=F64))
+    x = np.array([10.3, 10.3], np.float32)
+    y = np.array([12.2, 12.2 + L], np.float32)
+    p = synth.Params(k_rep=0.0, k_stretch=1.0, k_shear=0.0, k_bend=0.0, ib=1, mdf_iters=2)
+    spec = synth._world("shear", H, W, [2], x, y, np.array([math.pi / 2], np.float32), np.zeros(0),
+                        np.zeros(0), np.zeros(0), np.zeros(0), params=p)
+    spec.L_rest = np.array([L], np.float32)
+    spec.f0 = (feq - O.d2q9_weights()[:, None, None]).numpy().astype(np.float32)
+    w = O.World(spec)
+    st = w.initial_state()
+    new, rec = O.step(w, st, record=True)
+    X = st.X
+    Xt = X + torch.stack([g * (X[:, 1] - yc), torch.zeros(2, dtype=F64)], 1)   # dt = 1
+    e = Xt[1] - Xt[0]
+    ell = float(torch.sqrt((e * e).sum()))
+    assert ell > L + 1e-5
+    eh = e / ell
+    want = torch.stack([Xt[0] + 0.5 * (ell - L) * eh, Xt[1] - 0.5 * (ell - L) * eh])
+    assert torch.allclose(new.X, want, atol=1e-8)       # f0 rounded to float32
+    d = new.X[1] - new.X[0]
+    assert abs(float(torch.sqrt((d * d).sum())) - L) < 1e-12
