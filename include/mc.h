@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define MC_ABI_VERSION 4
+#define MC_ABI_VERSION 5
 
 typedef enum mc_status {
   MC_OK = 0,
@@ -84,13 +84,29 @@ typedef enum mc_mem_kind { MC_MEM_HOST = 0, MC_MEM_DEVICE = 1 } mc_mem_kind;
  *            bead), spreading half its force at each point and moving with
  *            the mean of the two interpolated velocities; 0 < layer_half <= 2
  *            cells.  The steric field stays on the beads.  The reverse mode
- *            supports layers = 1 only. */
+ *            supports layers = 1 only.
+ *   ib       immersed-boundary coupling (Fluid-filament Interaction).
+ *            0: penalty, F_el = kappa (x_hat - X)/dt spread as a force and
+ *            the beads move with the interpolated fluid velocity.
+ *            1: direct forcing with multi-direct-forcing (MDF) passes: the
+ *            steric force acts on the fluid, the fluid velocity before the
+ *            filament's forcing u* = (sum_i c_i f_i + F_s/2)/rho carries the
+ *            beads to X~ = X + dt I[u*](X), PBD from X~ gives x_hat, and each
+ *            bead takes the velocity U_s = I[u*](X) + (x_hat - X~)/dt; then
+ *            mdf_iters passes force the fluid to follow it (per bead
+ *            dF = 2 I[rho](X) (U_s - I[u](X)), F += S[dF], u += S[dF]/(2 rho)),
+ *            the LBM steps with the total force and X^{n+1} = X + dt U_s.
+ *            kappa is unused; needs layers = 1; no reverse mode.
+ *   mdf_iters  MDF passes per step with ib = 1, 0 <= mdf_iters <= 64 (0: the
+ *            filament does not force the fluid). */
 typedef struct mc_params {
   float nu, dt, Lambda, kappa, k_bend, k_stretch, k_shear, k_rep, sigma, orient;
   int n_pbd;
   int pbd_order;
   int layers;
   float layer_half;
+  int ib;
+  int mdf_iters;
 } mc_params;
 
 /* The paper's statement of one world (Methods: filaments as graphs with
@@ -188,7 +204,8 @@ mc_status mc_step_batched(mc_world* const* worlds, int n_worlds, int n_steps, vo
  * split in two kernels with F through device memory; 0, 1, 2, 3, 4, 5, 6
  * give the same step bitwise.  Any other use leaves the world in an
  * unspecified state.  The step counter advances with stage 6.  Errors:
- * MC_ERR_INVALID_ARG for an unknown stage. */
+ * MC_ERR_INVALID_ARG for an unknown stage or a world with ib = 1 (its
+ * step has more stages; mc_step runs them). */
 mc_status mc_step_stage(mc_world* w, int stage, void* stream);
 #define MC_N_STAGES 8
 
@@ -224,12 +241,13 @@ mc_status mc_world_get_positions_noalloc(const mc_world* w, float* x, float* y, 
 
 /* Fields of the last completed step, for inspection and parity tests. */
 typedef enum mc_field {
-  MC_FIELD_FEL = 0,      /* [2N] elastic force per bead (a3) */
+  MC_FIELD_FEL = 0,      /* [2N] elastic force per bead (a3); with ib = 1 the summed MDF force per bead */
   MC_FIELD_FS = 1,       /* [2N] steric force per bead (a6) */
-  MC_FIELD_UBEAD = 2,    /* [2N] interpolated velocity per bead (a8) */
+  MC_FIELD_UBEAD = 2,    /* [2N] interpolated velocity per bead (a8); with ib = 1 the bead velocity U_s */
   MC_FIELD_RHO_S = 3,    /* [H*W] deposited steric density (a4), recomputed on request */
   MC_FIELD_RHO_BAR = 4,  /* [H*W] filtered density (a5), recomputed on request */
-  MC_FIELD_FORCE = 5,    /* [2*H*W] interleaved (Fx, Fy) spread force density (a6), recomputed on request */
+  MC_FIELD_FORCE = 5,    /* [2*H*W] interleaved (Fx, Fy) spread force density (a6), recomputed on request
+                            (with ib = 1 the step's total force, steric spread plus MDF passes) */
   MC_FIELD_U = 6,        /* [2*H*W] interleaved (ux, uy) fluid velocity (a7) */
   MC_FIELD_CELL = 7,     /* [N] int32 cell index (floor(y) mod H) W + (floor(x) mod W) (a2) */
   MC_FIELD_BIN = 8,      /* [N] int32 bin index (floor(y)/8) (W/8) + floor(x)/8 of each bead (a2) */

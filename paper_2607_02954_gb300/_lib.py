@@ -31,7 +31,7 @@ class mc_params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_float) for n in
                 ("nu", "dt", "Lambda", "kappa", "k_bend", "k_stretch", "k_shear", "k_rep", "sigma", "orient")] + \
                [("n_pbd", ctypes.c_int), ("pbd_order", ctypes.c_int), ("layers", ctypes.c_int),
-                ("layer_half", ctypes.c_float)]
+                ("layer_half", ctypes.c_float), ("ib", ctypes.c_int), ("mdf_iters", ctypes.c_int)]
 
 
 _fp = ctypes.POINTER(ctypes.c_float)
@@ -105,7 +105,7 @@ SIGNATURES = {
 _lib = None
 
 
-ABI_VERSION = 4   # MC_ABI_VERSION of include/mc.h that these structures mirror
+ABI_VERSION = 5   # MC_ABI_VERSION of include/mc.h that these structures mirror
 
 
 def load():

@@ -20,17 +20,8 @@ __device__ __forceinline__ void cpa4(void* sdst, const void* gsrc) {
 __device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 
-// a8 for one bead at p = X^n with interpolated velocity U: the velocity
-// record, the watchdog (|U| > u_max or non-finite: flag the world, keep the
-// bead), X^{n+1} = wrap(X^n + dt U) in cell + fraction form, D += dt U.
-// Returns X^{n+1} (X^n when the watchdog fired).
-__device__ __forceinline__ float4 advance_tail(const WorldDev& w, int i, float4 p, float Ux, float Uy) {
-  w.ubead[i] = make_float2(Ux, Uy);
-  const float m2 = Ux * Ux + Uy * Uy;
-  if (!(m2 <= w.u_max * w.u_max)) {   // also catches NaN
-    atomicOr(w.flags, kFlagUnstable);
-    return p;
-  }
+// X + dt U in cell + fraction form, wrapped, for X = p.
+__device__ __forceinline__ float4 advance_pos(const WorldDev& w, float4 p, float Ux, float Uy) {
   const int W = w.W, H = w.H;
   int cx = cell_x(p), cy = cell_y(p);
   float fx = p.x + w.dt * Ux, fy = p.y + w.dt * Uy;
@@ -43,7 +34,21 @@ __device__ __forceinline__ float4 advance_tail(const WorldDev& w, int i, float4 
   if (fy >= 1.0f) { fy = 0.0f; cy += 1; }
   cx = wrap_once(cx, W);
   cy = wrap_once(cy, H);
-  const float4 q = make_float4(fx, fy, __int_as_float(cx), __int_as_float(cy));
+  return make_float4(fx, fy, __int_as_float(cx), __int_as_float(cy));
+}
+
+// a8 for one bead at p = X^n with velocity U: the velocity record, the
+// watchdog (|U| > u_max or non-finite: flag the world, keep the bead),
+// X^{n+1} = wrap(X^n + dt U) in cell + fraction form, D += dt U.
+// Returns X^{n+1} (X^n when the watchdog fired).
+__device__ __forceinline__ float4 advance_tail(const WorldDev& w, int i, float4 p, float Ux, float Uy) {
+  w.ubead[i] = make_float2(Ux, Uy);
+  const float m2 = Ux * Ux + Uy * Uy;
+  if (!(m2 <= w.u_max * w.u_max)) {   // also catches NaN
+    atomicOr(w.flags, kFlagUnstable);
+    return p;
+  }
+  const float4 q = advance_pos(w, p, Ux, Uy);
   w.pos[i] = q;
   float2 d = w.disp[i];
   d.x += w.dt * Ux;
@@ -83,7 +88,7 @@ __device__ __forceinline__ float sq(float v) { return v * v; }
 
 // Constants of the PBD passes, read once per warp.
 struct PbdConst {
-  float hb, hs, ksh, ko, kappa_dt;
+  float hb, hs, ksh, ko, kappa_dt, dt;
   int n_pbd, order, W, H, nbx;
 };
 
@@ -94,6 +99,7 @@ __device__ __forceinline__ PbdConst pbd_const(const WorldDev& w) {
   k.ksh = w.k_sh;
   k.ko = w.orient * k.hs * k.ksh;
   k.kappa_dt = w.kappa_dt;
+  k.dt = w.dt;
   k.n_pbd = w.n_pbd;
   k.order = w.pbd_order;
   k.W = w.W;
@@ -153,8 +159,19 @@ __device__ __forceinline__ float2 bead_normal(float2 out, bool has_out, float2 i
 
 // F_el = kappa (x_hat - X) / dt of one bead, its 8x8 bin (a2) and one
 // histogram atomic per group of lanes sharing a bin.  Every lane calls this.
+// With direct forcing (kMode 2) the bead's output is instead its velocity
+// U_s = U* + dl/dt, U* (the fluid's, stored in ubead by the prediction) plus
+// the PBD correction of the carried position.
+template <int kMode>
 __device__ __forceinline__ void bead_out(const WorldDev& w, const PbdConst& k, bool valid, int b, const float4 P,
                                          float dlx, float dly, float& fmax) {
+  if (kMode == 2) {
+    if (valid) {
+      const float2 U = w.ubead[b];
+      w.ubead[b] = make_float2(U.x + dlx / k.dt, U.y + dly / k.dt);
+    }
+    return;
+  }
   const int lane = threadIdx.x & 31;
   int bin = -1 - lane;
   if (valid) {
@@ -171,7 +188,7 @@ __device__ __forceinline__ void bead_out(const WorldDev& w, const PbdConst& k, b
 // Jacobi PBD of a filament of at most 64 beads in registers: lane l holds
 // beads, edges and joints 2l and 2l + 1, and reads its neighbours' values by
 // warp shuffles.  The same arithmetic, in the same order, as pbd_smem.
-template <bool kExt, bool kAdvance>
+template <bool kExt, int kMode>
 __device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, int b0, int B, int e0, int j0,
                                           long long t) {
   constexpr unsigned kAll = 0xffffffffu;
@@ -182,7 +199,7 @@ __device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, 
   const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   float4 P0 = hb0 ? w.pos[b0 + i0] : z4;
   float4 P1 = hb1 ? w.pos[b0 + i1] : z4;
-  if (kAdvance) {
+  if (kMode == 1) {
     // a8 of the previous step for the lane's beads, then this step's PBD from X^n
     if (hb0) {
       const float2 U = interp_u(w, P0);
@@ -191,6 +208,18 @@ __device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, 
     if (hb1) {
       const float2 U = interp_u(w, P1);
       P1 = advance_tail(w, b0 + i1, P1, U.x, U.y);
+    }
+  } else if (kMode == 2) {
+    // direct forcing: the fluid (u* in u) carries the beads, PBD starts there
+    if (hb0) {
+      const float2 U = interp_u(w, P0);
+      w.ubead[b0 + i0] = U;
+      P0 = advance_pos(w, P0, U.x, U.y);
+    }
+    if (hb1) {
+      const float2 U = interp_u(w, P1);
+      w.ubead[b0 + i1] = U;
+      P1 = advance_pos(w, P1, U.x, U.y);
     }
   }
   float th0 = he0 ? w.theta[e0 + i0] : 0.0f;
@@ -281,8 +310,8 @@ __device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, 
   if (he0) w.theta[e0 + i0] = th0;
   if (he1) w.theta[e0 + i1] = th1;
   float fmax = 0.0f;
-  bead_out(w, k, hb0, b0 + i0, P0, dlx0, dly0, fmax);
-  bead_out(w, k, hb1, b0 + i1, P1, dlx1, dly1, fmax);
+  bead_out<kMode>(w, k, hb0, b0 + i0, P0, dlx0, dly0, fmax);
+  bead_out<kMode>(w, k, hb1, b0 + i1, P1, dlx1, dly1, fmax);
   if (kExt && w.observe && t >= 1) {
     // behaviour descriptors (Eqs. 5, 6): squared change of the rest angles
     // and rest lengths from step t - 1 to step t
@@ -303,7 +332,7 @@ __device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, 
 // bead corrections live in a per-warp slice of shared memory; every pass
 // reads the slice, then writes corrections, with a warp barrier in between,
 // so all corrections of a pass see the state before it.
-template <bool kExt, bool kAdvance>
+template <bool kExt, int kMode>
 __device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, int b0, int B, int e0, int j0,
                                           long long t, float* s, int maxB) {
   const int lane = threadIdx.x & 31;
@@ -321,12 +350,20 @@ __device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, 
   float4* P = reinterpret_cast<float4*>(s + 10 * maxB);    // bead positions
   float4* D = reinterpret_cast<float4*>(s + 14 * maxB);    // joint drive parameters
   // stage the filament's inputs in shared memory, every copy in flight at once
-  if (kAdvance) {
+  if (kMode == 1) {
     // a8 of the previous step, the advanced positions staged directly
     for (int i = lane; i < B; i += 32) {
       const float4 p = w.pos[b0 + i];
       const float2 U = interp_u(w, p);
       P[i] = advance_tail(w, b0 + i, p, U.x, U.y);
+    }
+  } else if (kMode == 2) {
+    // direct forcing: the positions the fluid (u* in u) carries the beads to
+    for (int i = lane; i < B; i += 32) {
+      const float4 p = w.pos[b0 + i];
+      const float2 U = interp_u(w, p);
+      w.ubead[b0 + i] = U;
+      P[i] = advance_pos(w, p, U.x, U.y);
     }
   } else {
     for (int i = lane; i < B; i += 32) cpa16(&P[i], &w.pos[b0 + i]);
@@ -411,8 +448,8 @@ __device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, 
   float fmax = 0.0f;
   for (int i0 = 0; i0 < B; i0 += 32) {
     const int i = i0 + lane;
-    bead_out(w, k, i < B, b0 + i, i < B ? P[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f), i < B ? dlx[i] : 0.0f,
-             i < B ? dly[i] : 0.0f, fmax);
+    bead_out<kMode>(w, k, i < B, b0 + i, i < B ? P[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f), i < B ? dlx[i] : 0.0f,
+                    i < B ? dly[i] : 0.0f, fmax);
   }
   if (kExt && w.observe && t >= 1) {
     float eb = 0.0f, ep = 0.0f;
@@ -431,7 +468,7 @@ __device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, 
 // coordinates.  Filaments of at most 64 beads run in registers; longer ones
 // in the warp's slice of dynamic shared memory (maxB floats per array; zero
 // when no filament of the launch is longer than 64 beads).
-template <bool kExt, bool kAdvance>
+template <bool kExt, int kMode>
 __global__ void __launch_bounds__(256, 4) k_pbd(const WorldDev* __restrict__ worlds,
                                              const int2* __restrict__ items, int n_items, int maxB) {
   extern __shared__ __align__(16) float smem[];   // maxB is a multiple of 4: float4 slices stay aligned
@@ -441,17 +478,19 @@ __global__ void __launch_bounds__(256, 4) k_pbd(const WorldDev* __restrict__ wor
   if (item >= n_items) return;  // warp-uniform exit; the kernel has no block barrier
   const int2 it = items[item];
   const WorldDev& w = worlds[it.x];
+  if ((kMode == 2) != (w.ib == 1)) return;   // direct-forcing worlds run their PBD after the steric spread
   const int f = it.y;
   const int b0 = w.fil_off[f];
   const int B = w.fil_off[f + 1] - b0;
   const int e0 = b0 - f, j0 = b0 - 2 * f;
-  // with kAdvance the counter still holds the previous step (the scan of
+  // with kMode 1 the counter still holds the previous step (the scan of
   // this step advances it)
-  const long long t = *w.t + (kAdvance ? 1 : 0);
+  const long long t = *w.t + (kMode == 1 ? 1 : 0);
   const PbdConst k = pbd_const(w);
-  float fmax = B <= 64 ? pbd_regs<kExt, kAdvance>(w, k, b0, B, e0, j0, t)
-                       : pbd_smem<kExt, kAdvance>(w, k, b0, B, e0, j0, t,
-                                                  smem + (size_t)warp * maxB * kPbdFloatsPerBead, maxB);
+  float fmax = B <= 64 ? pbd_regs<kExt, kMode>(w, k, b0, B, e0, j0, t)
+                       : pbd_smem<kExt, kMode>(w, k, b0, B, e0, j0, t,
+                                               smem + (size_t)warp * maxB * kPbdFloatsPerBead, maxB);
+  if (kMode == 2) return;
   // largest |F_el| component of the world this step (bounds the spread's
   // fixed-point scale); non-negative floats order like their bit patterns
   for (int o = 16; o > 0; o >>= 1) fmax = fmaxf(fmax, __shfl_xor_sync(0xffffffffu, fmax, o));
@@ -616,7 +655,9 @@ __global__ void __launch_bounds__(kBeadChunk) k_interp_advance(const WorldDev* _
   if (i >= w.N) return;
   const float4 p = w.pos[i];
   float2 U;
-  if (kExt && w.layers == 2) {
+  if (kExt && w.ib == 1) {
+    U = w.ubead[i];   // direct forcing: the bead's own velocity U_s
+  } else if (kExt && w.layers == 2) {
     // two-layer filament: mean of the velocities at X +- delta n
     const float2 n = w.nrm[i];
     const float2 Up = layer_velocity(w, p, n, w.layer_half), Um = layer_velocity(w, p, n, -w.layer_half);
@@ -691,8 +732,19 @@ void launch_pbd(const Plan& p, cudaStream_t s) {
   const int grid = (p.n_fil_items + wpb - 1) / wpb;
   // worlds with a rest-length drive, observables or two layers need the
   // extended kernel; it computes every other world exactly as the plain one
-  auto kern = p.any_ext ? k_pbd<true, false> : k_pbd<false, false>;
+  auto kern = p.any_ext ? k_pbd<true, 0> : k_pbd<false, 0>;
   kern<<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
+}
+
+// The PBD of direct-forcing worlds (from the positions the fluid carries
+// the beads to; the others return at once).
+void launch_pbd_mdf(const Plan& p, cudaStream_t s) {
+  if (p.n_fil_items == 0) return;
+  const int mb = (p.max_B + 3) & ~3;
+  const int wpb = pbd_warps_per_block(mb);
+  const size_t smem = p.max_B <= 64 ? 0 : (size_t)wpb * mb * kPbdFloatsPerBead * sizeof(float);
+  const int grid = (p.n_fil_items + wpb - 1) / wpb;
+  k_pbd<true, 2><<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
 }
 
 // a8 of the previous step fused with this step's a1-a3 (plans without the
@@ -703,7 +755,7 @@ void launch_advance_pbd(const Plan& p, cudaStream_t s) {
   const int wpb = pbd_warps_per_block(mb);
   const size_t smem = p.max_B <= 64 ? 0 : (size_t)wpb * mb * kPbdFloatsPerBead * sizeof(float);
   const int grid = (p.n_fil_items + wpb - 1) / wpb;
-  k_pbd<false, true><<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
+  k_pbd<false, 1><<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
 }
 
 // Shared-memory limits set once per process, outside any stream capture: the
@@ -712,9 +764,10 @@ void kernel_setup() {
   static std::once_flag once;
   std::call_once(once, [] {
     const int most = 227 * 1024;
-    cudaFuncSetAttribute(k_pbd<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    cudaFuncSetAttribute(k_pbd<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    cudaFuncSetAttribute(k_pbd<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(k_pbd<false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(k_pbd<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(k_pbd<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(k_pbd<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
   });
 }
 

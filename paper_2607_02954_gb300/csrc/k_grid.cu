@@ -152,6 +152,21 @@ void enqueue_steps(const Plan& p, int n, cudaStream_t s) {
 }
 
 void enqueue_step(const Plan& p, cudaStream_t s) {
+  if (p.any_mdf) {
+    // direct forcing: the steric spread and the MDF passes write F to device
+    // memory before the LBM (the other worlds of the plan take the same
+    // unfused sequence, which gives their step bitwise)
+    launch_pbd(p, s);
+    launch_mdf_bins(p, s);
+    launch_bin_scan(p, s);
+    launch_bin_scatter(p, s);
+    launch_deposit_x(p, s, 0);
+    launch_force_spread(p, s, 0);
+    launch_mdf(p, s);
+    launch_lbm(p, s);
+    launch_interp_advance(p, s);
+    return;
+  }
   launch_pbd(p, s);              // a1 + a3 + a2 histogram
   launch_bin_scan(p, s);         // a2 offsets (two kernels)
   launch_bin_scatter(p, s);      // a2 scatter

@@ -684,6 +684,9 @@ __global__ void __launch_bounds__(kThreads) k_force_spread(const WorldDev* __res
   force_fold(sm.wk, tb, w.ntx, w.nty);
   const float inv = pow2f(-k);
   const int lane = threadIdx.x & 31;
+  // a direct-forcing world's F holds the step's total force (steric spread
+  // plus MDF passes): a re-run for the density fields leaves it
+  if (store_fields && w.ib == 1) return;
   for (int ly = threadIdx.x >> 5; ly < tb.th; ly += kWarps) {
     if (lane < tb.tw) {
       const int s = (ly + 3) * kAx + lane + 3;

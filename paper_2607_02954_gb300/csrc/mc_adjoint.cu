@@ -262,6 +262,7 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
   if ((h.N && (!dL_dx || !dL_dy)) || (h.J && !dL_dtheta0)) return afail(MC_ERR_INVALID_ARG, "NULL gradient pointer");
   if (h.pbd_order != 0) return afail(MC_ERR_INVALID_ARG, "the reverse mode supports Jacobi PBD (pbd_order 0) only");
   if (h.layers != 1) return afail(MC_ERR_INVALID_ARG, "the reverse mode supports layers = 1 only");
+  if (h.ib != 0) return afail(MC_ERR_INVALID_ARG, "the reverse mode supports the penalty coupling (ib = 0) only");
   const int mb = (w->max_B + 3) & ~3;
   if (mc::adj_pbd_smem_per_warp(mb, h.n_pbd) > 220 * 1024)
     return afail(MC_ERR_INVALID_ARG, "filaments too long for the adjoint (reduce beads per filament or n_pbd)");

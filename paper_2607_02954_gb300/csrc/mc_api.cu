@@ -82,6 +82,9 @@ mc_status validate_params(const mc_params& p) {
   if (p.layers != 1 && p.layers != 2) return fail(MC_ERR_INVALID_ARG, "layers must be 1 or 2");
   if (p.layers == 2 && !(p.layer_half > 0.0f && p.layer_half <= 2.0f))
     return fail(MC_ERR_INVALID_ARG, "layer_half must be in (0, 2] cells");
+  if (p.ib != 0 && p.ib != 1) return fail(MC_ERR_INVALID_ARG, "ib must be 0 or 1");
+  if (p.ib == 1 && p.layers != 1) return fail(MC_ERR_INVALID_ARG, "direct forcing (ib = 1) needs layers = 1");
+  if (p.mdf_iters < 0 || p.mdf_iters > 64) return fail(MC_ERR_INVALID_ARG, "mdf_iters must be in [0, 64]");
   return MC_OK;
 }
 
@@ -99,6 +102,8 @@ void fill_constants(WorldDev& h, const mc_params& p) {
   h.pbd_order = p.pbd_order;
   h.layers = p.layers;
   h.layer_half = p.layer_half;
+  h.ib = p.ib;
+  h.mdf_iters = p.ib == 1 ? p.mdf_iters : 0;
   h.om_p = (float)(1.0 / tau_p);
   h.om_m = (float)(1.0 / tau_m);
   h.src_p = (float)(1.0 - 0.5 / tau_p);
@@ -127,6 +132,8 @@ mc_status build_plan(mc_world* const* ws, int n, cudaStream_t s, Plan& out) {
   mc::kernel_setup();
   p.max_R = 1;
   p.any_layered = false;
+  p.any_mdf = false;
+  p.max_mdf = 0;
   p.any_ext = false;
   std::vector<int2> fil, bead, tile, cell, scan;
   std::vector<WorldDev> table(n);
@@ -136,7 +143,9 @@ mc_status build_plan(mc_world* const* ws, int n, cudaStream_t s, Plan& out) {
     p.max_B = std::max(p.max_B, w->max_B);
     p.max_R = std::max(p.max_R, w->h.R);
     p.any_layered = p.any_layered || w->h.layers == 2;
-    p.any_ext = p.any_ext || w->h.layers == 2 || w->h.observe || w->h.has_ldrive;
+    p.any_mdf = p.any_mdf || w->h.ib == 1;
+    p.max_mdf = std::max(p.max_mdf, w->h.mdf_iters);
+    p.any_ext = p.any_ext || w->h.layers == 2 || w->h.observe || w->h.has_ldrive || w->h.ib == 1;
     for (int f = 0; f < w->h.n_fil; ++f) fil.push_back(make_int2(k, f));
     const int nb = std::max(w->h.N, 1);
     for (int b = 0; b < nb; b += mc::kBeadChunk) bead.push_back(make_int2(k, b));
@@ -294,7 +303,9 @@ size_t world_layout(WorldDev& h, void* A) {
   const size_t o_eb = L.take<float>(h.has_energy ? N : 0);
   const size_t o_ob = L.take<unsigned long long>(3);
   const size_t o_nr = L.take<float2>(h.layers == 2 ? N : 0);
-  const size_t o_fa = L.take<unsigned long long>(h.layers == 2 ? 2 * HW : 0);
+  const bool fixed_spread = h.layers == 2 || h.ib == 1;
+  const size_t o_fa = L.take<unsigned long long>(fixed_spread ? 2 * HW : 0);
+  const size_t o_mr = L.take<float>(h.ib == 1 ? HW : 0);
   if (!A) return L.off;
   h.fil_off = at<int>(A, o_fo);
   h.pos = at<float4>(A, o_pos);
@@ -330,7 +341,8 @@ size_t world_layout(WorldDev& h, void* A) {
   h.ebead = h.has_energy ? at<float>(A, o_eb) : nullptr;
   h.obs = at<unsigned long long>(A, o_ob);
   h.nrm = h.layers == 2 ? at<float2>(A, o_nr) : nullptr;
-  h.facc = h.layers == 2 ? at<unsigned long long>(A, o_fa) : nullptr;
+  h.facc = fixed_spread ? at<unsigned long long>(A, o_fa) : nullptr;
+  h.mrho = h.ib == 1 ? at<float>(A, o_mr) : nullptr;
   return L.off;
 }
 
@@ -362,6 +374,8 @@ mc_status mc_params_default(mc_params* p) {
   p->pbd_order = 0;
   p->layers = 1;
   p->layer_half = 0.5f;
+  p->ib = 0;
+  p->mdf_iters = 0;
   return MC_OK;
 }
 
@@ -577,6 +591,7 @@ mc_status mc_step_batched(mc_world* const* ws, int n, int n_steps, void* stream)
 
 mc_status mc_step_stage(mc_world* w, int stage, void* stream) {
   if (!w || stage < 0 || stage >= MC_N_STAGES) return fail(MC_ERR_INVALID_ARG, "bad world or stage");
+  if (w->h.ib == 1) return fail(MC_ERR_INVALID_ARG, "per-stage steps are defined for the penalty coupling (ib = 0)");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const Plan& p = w->plan;
   switch (stage) {
@@ -661,8 +676,9 @@ mc_status mc_world_get_field(const mc_world* w, int field, void* out, int mem_ki
       break;
     case MC_FIELD_FORCE:
       // the step hands F from the spread to the collision in shared memory:
-      // re-run the spread on the last step's binned beads (deterministic)
-      mc::launch_force_spread(w->plan, s, 0, 1);
+      // re-run the spread on the last step's binned beads (deterministic);
+      // a direct-forcing step leaves its total F in device memory
+      if (h.ib != 1) mc::launch_force_spread(w->plan, s, 0, 1);
       MC_CUDA(cudaGetLastError());
       src = h.F;
       bytes = HW * sizeof(float2);

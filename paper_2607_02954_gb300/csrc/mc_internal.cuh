@@ -75,8 +75,10 @@ struct WorldDev {
   int has_ldrive, has_energy, observe;
   int layers;             // 1 or 2 (two-layer filament)
   float layer_half;       // half distance between the layers (cells)
+  int ib, mdf_iters;      // coupling (0 penalty, 1 direct forcing) and MDF passes per step
+  float* mrho;            // [H * W] fluid density of the step (ib == 1)
   float2* nrm;            // [N] filament unit normal at each bead (layers == 2)
-  unsigned long long* facc;  // [2 H W] fixed-point spread of the layer points (layers == 2)
+  unsigned long long* facc;  // [2 H W] fixed-point spread of the layer points or MDF passes (layers == 2, ib == 1)
   const float4* ldrive;   // [E] (L0, amp, freq, phase) rest-length drive, or nullptr (static L_rest)
   const float* energy;    // [H * W] energy field, or nullptr
   float* ebead;           // [N] energy sampled at each bead (observe and energy)
@@ -114,7 +116,9 @@ struct Plan {
   int max_B = 2;
   int max_R = 4;                 // largest Gaussian half width among the worlds
   bool any_layered = false;      // some world is a two-layer filament world
-  bool any_ext = false;          // some world has two layers, observables or a rest-length drive
+  bool any_mdf = false;          // some world couples by direct forcing (ib == 1)
+  int max_mdf = 0;               // most MDF passes of a world
+  bool any_ext = false;          // some world has two layers, observables, a rest-length drive or direct forcing
   int n_fil_items = 0, n_bead_items = 0, n_tile_items = 0, n_cell_items = 0, n_scan_items = 0;
   WorldDev* d_worlds = nullptr;  // [n_worlds]
   int2* d_fil_items = nullptr;   // (world, filament)
@@ -140,6 +144,11 @@ void launch_lbm(const Plan& p, cudaStream_t s, int layered_only = 0);   // layer
 void launch_layer_spread(const Plan& p, cudaStream_t s);   // two-layer worlds: F from the layer points
 void launch_force_lbm(const Plan& p, cudaStream_t s);   // y pass of a5 + a6 + a7 in one kernel
 void launch_interp_advance(const Plan& p, cudaStream_t s);
+// direct forcing (ib == 1 worlds; the others return at once): bins and a
+// zero F_el before the steric spread, then u*, the predicted PBD and the
+// MDF passes after it
+void launch_mdf_bins(const Plan& p, cudaStream_t s);
+void launch_mdf(const Plan& p, cudaStream_t s);
 void enqueue_step(const Plan& p, cudaStream_t s);
 void enqueue_steps(const Plan& p, int n, cudaStream_t s);   // n steps, fused bead stages where possible
 void launch_advance_pbd(const Plan& p, cudaStream_t s);

@@ -32,7 +32,8 @@ def params_struct(p: Params) -> L.mc_params:
                        k_stretch=p.k_stretch, k_shear=p.k_shear, k_rep=p.k_rep, sigma=p.sigma,
                        orient=p.orient, n_pbd=int(p.n_pbd),
                        pbd_order=int(getattr(p, "pbd_order", 0)), layers=int(getattr(p, "layers", 1)),
-                       layer_half=float(getattr(p, "layer_half", 0.5)))
+                       layer_half=float(getattr(p, "layer_half", 0.5)), ib=int(getattr(p, "ib", 0)),
+                       mdf_iters=int(getattr(p, "mdf_iters", 0)))
 
 
 def default_params() -> Params:

@@ -63,7 +63,7 @@ def _desc(spec, **over):
 
 @pytest.mark.parametrize("case", ["H_not_mult8", "W_small", "short_filament", "nan_x", "bad_nu",
                                   "bad_sigma", "neg_L", "bad_t0", "bad_npbd", "bad_pbd_order",
-                                  "bad_layers", "bad_layer_half"])
+                                  "bad_layers", "bad_layer_half", "bad_ib", "ib_two_layers", "bad_mdf_iters"])
 def test_create_rejects_invalid_worlds_on_host(case):
     spec = synth.tiny_world(0, side=16, lengths=(5, 4))
     over = {}
@@ -93,6 +93,12 @@ def test_create_rejects_invalid_worlds_on_host(case):
         over["params"] = synth.Params(layers=3)
     elif case == "bad_layer_half":
         over["params"] = synth.Params(layers=2, layer_half=0.0)
+    elif case == "bad_ib":
+        over["params"] = synth.Params(ib=2)
+    elif case == "ib_two_layers":
+        over["params"] = synth.Params(ib=1, mdf_iters=2, layers=2)
+    elif case == "bad_mdf_iters":
+        over["params"] = synth.Params(ib=1, mdf_iters=65)
     d, keep = _desc(spec, **over)
     h = ctypes.c_void_p()
     lib = L.load()
