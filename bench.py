@@ -48,6 +48,12 @@ GRAPH_STEPS = 16   # mc_step replays graphs of 16 steps: PBD, then 15 x (previou
                    # scatter, deposit, force + LBM), and the last advance = 97 kernels; leftover steps run 7 each
 
 
+def mdf_launches(steps: int, m: int) -> int:
+    """Kernels of direct-forcing steps (always the unfused sequence): PBD (returns), bins, scan (2),
+    scatter, deposit, steric spread, moments, predicted PBD, m x (force, update), LBM, advance."""
+    return steps * (11 + 2 * m)
+
+
 def graph_launches(steps: int) -> int:
     return (steps // GRAPH_STEPS) * (2 + GRAPH_STEPS * 6 - 1) + (steps % GRAPH_STEPS) * KERNELS_PER_STEP
 # k_force_lbm, the dominant kernel: per cell read f 36 + rho_x 4, write f' 36 + u 8;
@@ -86,6 +92,8 @@ def parse():
                     help="PBD pass order of the stepped world: 0 Jacobi, 1 red-black")
     ap.add_argument("--loss", default="polyline", choices=["polyline", "splat"],
                     help="c5: folding loss, distance to a polyline or the paper's splatted-density MSE (128^2)")
+    ap.add_argument("--mdf-iters", type=int, default=-1,
+                    help="c3/c2 workloads: couple by direct forcing with this many MDF passes (default: penalty)")
     ap.add_argument("--observe", action="store_true",
                     help="step workloads: add a rest-length drive, an energy field and the observables")
     ap.add_argument("--arrival-rate", type=float, default=2000.0, help="served: requests per second")
@@ -96,11 +104,15 @@ def parse():
     return ap.parse_args()
 
 
-def make_spec(name: str, seed: int, pbd_order: int = 0, observe: bool = False):
+def make_spec(name: str, seed: int, pbd_order: int = 0, observe: bool = False, mdf_iters: int = -1):
     spec, desc = _make_spec(name, seed)
     if pbd_order:
         spec.params.pbd_order = pbd_order
         desc += ", red-black PBD passes"
+    if mdf_iters >= 0:
+        spec.params.ib = 1
+        spec.params.mdf_iters = mdf_iters
+        desc += f", direct forcing with {mdf_iters} MDF passes"
     if observe:
         from paper_2607_02954_gb300 import synth
         synth.with_observables(spec, seed)
@@ -119,7 +131,7 @@ def _make_spec(name: str, seed: int):
     raise SystemExit(f"unknown workload {name}")
 
 
-def sample_spec(name: str, seed: int):
+def sample_spec(name: str, seed: int, params=None):
     """Bounded sample of the workload for the CPU oracle: same density and
     filament shape, 1/16 of the area for the big sweep points."""
     from paper_2607_02954_gb300 import synth
@@ -129,8 +141,13 @@ def sample_spec(name: str, seed: int):
         density = (2 ** n) / float(side * side)
         s_side = max(256, side // 4)
         s_n = int(round(density * s_side * s_side))
-        return synth.world_rows(s_side, s_n, seed), f"one oracle step of {s_n} beads on {s_side}^2 (same density)"
+        spec = synth.world_rows(s_side, s_n, seed)
+        if params is not None:
+            spec.params = params
+        return spec, f"one oracle step of {s_n} beads on {s_side}^2 (same density)"
     spec, _ = make_spec(name, seed)
+    if params is not None:
+        spec.params = params
     return spec, f"one oracle step of the full {name} world"
 
 
@@ -468,7 +485,9 @@ def main():
         build()
     lib = _lib.load()
 
-    spec, desc = make_spec(args.workload, seed=rank, pbd_order=args.pbd_order, observe=args.observe)
+    spec, desc = make_spec(args.workload, seed=rank, pbd_order=args.pbd_order, observe=args.observe,
+                           mdf_iters=args.mdf_iters)
+    mdf = args.mdf_iters >= 0
     N, C = spec.N, spec.H * spec.W
     world = World(spec, device=True)
     stream = torch.cuda.current_stream()
@@ -497,18 +516,20 @@ def main():
     value = whole_job_rate(N, args.steps, ms_max * 1e-3, ws)
 
     # ---- per-stage CUDA-event timing on the launching stream ------------
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)] for _ in range(args.stage_steps)]
-    for k in range(args.stage_steps):
+    # (direct-forcing worlds have no per-stage entry: their step runs more kernels)
+    n_stage = 0 if mdf else args.stage_steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)] for _ in range(n_stage)]
+    for k in range(n_stage):
         evs[k][0].record(stream)
         for s_i, (_, sid) in enumerate(STAGES):
             _lib.check(lib.mc_step_stage(world.handle, sid, sh))
             evs[k][s_i + 1].record(stream)
     torch.cuda.synchronize()
-    stage_ms = {nm: sum(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.stage_steps)) / args.stage_steps
-                for i, (nm, _) in enumerate(STAGES)}
+    stage_ms = {nm: sum(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(n_stage)) / n_stage
+                for i, (nm, _) in enumerate(STAGES)} if n_stage else None
     hbm_peak, peak_kind = measured_peaks()
     top_bytes = FORCE_LBM_BYTES_PER_CELL * C + FORCE_LBM_BYTES_PER_BEAD * N
-    top_gbs = top_bytes / (stage_ms["force_lbm"] * 1e-3) / 1e9
+    top_gbs = top_bytes / (stage_ms["force_lbm"] * 1e-3) / 1e9 if stage_ms else None
     step_bytes = STEP_BYTES_PER_CELL * C + STEP_BYTES_PER_BEAD * N
     step_gbs = step_bytes / (ms_max / args.steps * 1e-3) / 1e9
     world.close()
@@ -543,18 +564,21 @@ def main():
                    "l2": "state 1.8 GB > L2: no flush needed" if C >= 4096 * 4096 else "state may fit in L2; per-step timing includes no flush"},
         "e2e": {"value": e2e_val, "unit": "particle-steps/s", "steps": e2e_steps,
                 "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps},
-        "gpu_launches": graph_launches(args.steps),
-        "roofline": {"bound": "hbm", "kernel": "k_force_lbm", "achieved": top_gbs, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": top_gbs / hbm_peak, "peak_kind": peak_kind,
-                     "traffic": KERNEL_TRAFFIC.get((args.workload, kernel_fingerprint())),
-                     "algorithmic_bytes_per_launch": top_bytes, "launch_ms": stage_ms["force_lbm"]},
+        "gpu_launches": mdf_launches(args.steps, args.mdf_iters) if mdf else graph_launches(args.steps),
+        "roofline": None if mdf else {
+            "bound": "hbm", "kernel": "k_force_lbm", "achieved": top_gbs, "peak": hbm_peak, "unit": "GB/s",
+            "frac": top_gbs / hbm_peak, "peak_kind": peak_kind,
+            "traffic": KERNEL_TRAFFIC.get((args.workload, kernel_fingerprint())),
+            "algorithmic_bytes_per_launch": top_bytes, "launch_ms": stage_ms["force_lbm"]},
         "step_roofline": {"achieved": step_gbs, "frac": step_gbs / hbm_peak, "unit": "GB/s",
                           "algorithmic_bytes_per_step": step_bytes},
         "stage_ms": stage_ms,
         "clocks": clk.summary(),
     }
+    if mdf:
+        line["step_roofline"]["note"] = "penalty-step bytes: a lower bound of the direct-forcing step's traffic"
     if not args.no_cpu_baseline and ws == 1:
-        sspec, sdesc = sample_spec(args.workload, 1)
+        sspec, sdesc = sample_spec(args.workload, 1, params=spec.params)
         v, n, el, cores = run_oracle_sample(sspec, 10.0)
         line["cpu_baseline"] = {"value": v, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
                                 "sample": f"{sdesc}; {n} step(s) in {el:.1f} s"}

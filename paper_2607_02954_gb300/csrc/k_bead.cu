@@ -517,6 +517,7 @@ __global__ void __launch_bounds__(kBeadChunk) k_bin_scatter(const WorldDev* __re
     w.spos[slot] = w.pos[i];
     w.sfel[slot] = w.fel[i];
     w.sid[slot] = i;
+    if (w.bead_slot) w.bead_slot[i] = slot;   // direct forcing: the MDF passes write dF to the slot
   }
 }
 

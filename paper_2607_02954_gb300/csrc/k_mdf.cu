@@ -11,9 +11,12 @@
 //   k_pbd<.., 2>    X~ = X + dt I[u*](X), PBD from X~, and each bead's
 //                   velocity U_s = I[u*](X) + (x_hat - X~)/dt (in ubead);
 //   m passes of     k_mdf_force:  dF_i = 2 I[rho](X_i) (U_s,i - I[u](X_i)),
-//                                 added to F_el,i and spread in 64-bit
-//                                 fixed point (bitwise independent of order);
-//                   k_mdf_update: F += S[dF], u += S[dF] / (2 rho);
+//                                 added to F_el,i and written to the bead's
+//                                 slot of the bin-ordered records;
+//                   k_mdf_spread: per 32x32 tile (k_steric.cu) the spread
+//                                 S[dF] in int32 fixed point (bitwise
+//                                 independent of order), then F += S[dF],
+//                                 u += S[dF] / (2 rho) on the tile's cells;
 //   (LBM with the total F, then X^{n+1} = X + dt U_s: the penalty path's
 //   kernels, the advance reading U_s).
 // Every kernel returns at once for the worlds of a batch that couple by
@@ -23,8 +26,6 @@
 namespace mc {
 
 namespace {
-
-constexpr double kMdfScale = 1099511627776.0;   // 2^40: fixed point of the MDF spread
 
 // a2 for a direct-forcing world: the bin of every bead from X (its PBD runs
 // after the steric spread), one histogram atomic per group of lanes sharing
@@ -70,86 +71,59 @@ __global__ void __launch_bounds__(kCellChunk) k_mdf_moments(const WorldDev* __re
   const float2 F = w.F[c];
   w.u[c] = make_float2((jx + 0.5f * F.x) * inv, (jy + 0.5f * F.y) * inv);
   w.mrho[c] = rho;
+  if (c == 0) {
+    w.mdf_max[0] = 0u;
+    w.mdf_max[1] = 0u;
+  }
 }
 
 // Pass `pass` of a direct-forcing world: the force that makes the fluid at
-// each bead move with U_s, and its spread.
+// each bead move with U_s, into F_el and the bead's bin-ordered slot, and
+// the pass's largest component (bounds the spread's fixed-point scale).
 __global__ void __launch_bounds__(kBeadChunk) k_mdf_force(const WorldDev* __restrict__ worlds,
                                                           const int2* __restrict__ items, int pass) {
   const int2 it = items[blockIdx.x];
   const WorldDev& w = worlds[it.x];
   if (w.ib != 1 || pass >= w.mdf_iters) return;
   const int i = it.y + threadIdx.x;
-  if (i >= w.N) return;
-  const int W = w.W, H = w.H;
-  const float4 p = w.pos[i];
-  const int cx = cell_x(p), cy = cell_y(p);
-  float wx[4], wy[4];
-  peskin4(p.x, wx);
-  peskin4(p.y, wy);
-  int ix[4];
+  float m = 0.0f;
+  if (i < w.N) {
+    const int W = w.W, H = w.H;
+    const float4 p = w.pos[i];
+    const int cx = cell_x(p), cy = cell_y(p);
+    float wx[4], wy[4];
+    peskin4(p.x, wx);
+    peskin4(p.y, wy);
+    int ix[4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a) ix[a] = wrap_once(cx - 1 + a, W);
-  int iy[4];
+    for (int a = 0; a < 4; ++a) ix[a] = wrap_once(cx - 1 + a, W);
+    float Ux = 0.0f, Uy = 0.0f, r = 0.0f;
 #pragma unroll
-  for (int b = 0; b < 4; ++b) iy[b] = wrap_once(cy - 1 + b, H);
-  float Ux = 0.0f, Uy = 0.0f, r = 0.0f;
+    for (int b = 0; b < 4; ++b) {
+      const size_t row = (size_t)wrap_once(cy - 1 + b, H) * W;
+      float rx = 0.0f, ry = 0.0f, rr = 0.0f;
 #pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    const float2* row = w.u + (size_t)iy[b] * W;
-    const float* rrow = w.mrho + (size_t)iy[b] * W;
-    float rx = 0.0f, ry = 0.0f, rr = 0.0f;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const float2 v = row[ix[a]];
-      rx = fmaf(wx[a], v.x, rx);
-      ry = fmaf(wx[a], v.y, ry);
-      rr = fmaf(wx[a], rrow[ix[a]], rr);
+      for (int a = 0; a < 4; ++a) {
+        const float2 v = w.u[row + ix[a]];
+        rx = fmaf(wx[a], v.x, rx);
+        ry = fmaf(wx[a], v.y, ry);
+        rr = fmaf(wx[a], w.mrho[row + ix[a]], rr);
+      }
+      Ux = fmaf(wy[b], rx, Ux);
+      Uy = fmaf(wy[b], ry, Uy);
+      r = fmaf(wy[b], rr, r);
     }
-    Ux = fmaf(wy[b], rx, Ux);
-    Uy = fmaf(wy[b], ry, Uy);
-    r = fmaf(wy[b], rr, r);
+    const float2 Us = w.ubead[i];
+    const float2 dF = make_float2(2.0f * r * (Us.x - Ux), 2.0f * r * (Us.y - Uy));
+    float2 fe = w.fel[i];
+    fe.x += dF.x;
+    fe.y += dF.y;
+    w.fel[i] = fe;
+    w.sfel[w.bead_slot[i]] = dF;
+    m = fmaxf(fabsf(dF.x), fabsf(dF.y));
   }
-  const float2 Us = w.ubead[i];
-  const float dFx = 2.0f * r * (Us.x - Ux), dFy = 2.0f * r * (Us.y - Uy);
-  float2 fe = w.fel[i];
-  fe.x += dFx;
-  fe.y += dFy;
-  w.fel[i] = fe;
-#pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    unsigned long long* row = w.facc + 2 * (size_t)iy[b] * W;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const float g = wx[a] * wy[b];
-      unsigned long long* c = row + 2 * ix[a];
-      atomicAdd(c, (unsigned long long)__double2ll_rn((double)(g * dFx) * kMdfScale));
-      atomicAdd(c + 1, (unsigned long long)__double2ll_rn((double)(g * dFy) * kMdfScale));
-    }
-  }
-}
-
-// F += S[dF], u += S[dF] / (2 rho), and the accumulator cleared.
-__global__ void __launch_bounds__(kCellChunk) k_mdf_update(const WorldDev* __restrict__ worlds,
-                                                           const int2* __restrict__ items, int pass) {
-  const int2 it = items[blockIdx.x];
-  const WorldDev& w = worlds[it.x];
-  if (w.ib != 1 || pass >= w.mdf_iters) return;
-  const int c = it.y + threadIdx.x;
-  if (c >= w.H * w.W) return;
-  const long long ax = (long long)w.facc[2 * c], ay = (long long)w.facc[2 * c + 1];
-  const float Gx = (float)((double)ax / kMdfScale), Gy = (float)((double)ay / kMdfScale);
-  float2 F = w.F[c];
-  F.x += Gx;
-  F.y += Gy;
-  w.F[c] = F;
-  const float h = 2.0f * w.mrho[c];
-  float2 u = w.u[c];
-  u.x += Gx / h;
-  u.y += Gy / h;
-  w.u[c] = u;
-  w.facc[2 * c] = 0ull;
-  w.facc[2 * c + 1] = 0ull;
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(&w.mdf_max[pass & 1], __float_as_uint(m));
 }
 
 }  // namespace
@@ -167,7 +141,7 @@ void launch_mdf(const Plan& p, cudaStream_t s) {
   launch_pbd_mdf(p, s);
   for (int k = 0; k < p.max_mdf; ++k) {
     k_mdf_force<<<p.n_bead_items, kBeadChunk, 0, s>>>(p.d_worlds, p.d_bead_items, k);
-    if (p.n_cell_items) k_mdf_update<<<p.n_cell_items, kCellChunk, 0, s>>>(p.d_worlds, p.d_cell_items, k);
+    launch_mdf_spread(p, s, k);
   }
 }
 

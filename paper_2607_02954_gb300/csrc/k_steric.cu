@@ -763,6 +763,110 @@ __global__ void __launch_bounds__(kThreads, 4) k_force_lbm(const WorldDev* __res
   if (!layered) tile_lbm(sm.wk, w, tb, k);
 }
 
+// One MDF pass of the direct-forcing worlds on one tile: the spread of the
+// beads' dF (bin-ordered, in sfel) in int32 fixed point, then
+// F += S[dF] and u += S[dF] / (2 rho) on the tile's cells.  The scale's
+// bound is the pass's largest |dF| component times the tile's largest
+// rho_s (the sum of the spread weights of a cell).
+__global__ void __launch_bounds__(kThreads) k_mdf_spread(const WorldDev* __restrict__ worlds,
+                                                         const int2* __restrict__ items, int pass) {
+  __shared__ __align__(16) float4 sp[kForceCap];
+  __shared__ __align__(8) float2 sf[kForceCap];
+  __shared__ TileWork wk;
+  __shared__ int s_start[kMaxSeg], s_pre[kMaxSeg + 1];
+  const int2 it = items[blockIdx.x];
+  const WorldDev& w = worlds[it.x];
+  if (w.ib != 1 || pass >= w.mdf_iters) return;
+  const TileBox tb = tile_box(w, it.y);
+  const int W = w.W, H = w.H, ntx = w.ntx, nty = w.nty;
+  const int tile = (tb.y0 / kTile) * ntx + tb.x0 / kTile;
+  const int tid = threadIdx.x;
+  if ((tid >> 5) == 0) build_segments(w, tb.x0 - 2, tb.x0 + tb.tw, tb.y0 - 2, tb.y0 + tb.th, s_start, s_pre, nullptr);
+  tile_clear(wk);
+  // the next pass's maximum slot (its force kernel follows this kernel)
+  if (tile == 0 && tid == 0) w.mdf_max[(pass + 1) & 1] = 0u;
+  __syncthreads();
+  const float dmax = __uint_as_float(w.mdf_max[pass & 1]);
+  const int k = fix_exponent(dmax * w.tile_rho_max[tile] * 1.0001f + 1e-30f);
+  const float scale = pow2f(k);
+  const int total = s_pre[kMaxSeg];
+  for (int c0 = 0; c0 < total; c0 += kForceCap) {
+    const int n = min(kForceCap, total - c0);
+    for (int v = tid; v < n; v += kThreads) {
+      const int slot = seg_slot(c0 + v, s_start, s_pre);
+      cp_async16(&sp[v], &w.spos[slot]);
+      cp_async8(&sf[v], &w.sfel[slot]);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int v0 = 0; v0 < n; v0 += kThreads) {
+      const int v = v0 + tid;
+      bool keep = false;
+      int rx = 0, ry = 0;
+      if (v < n) {
+        const float4 p = sp[v];
+        rx = cell_x(p) - tb.x0;
+        ry = cell_y(p) - tb.y0;
+        keep = true;
+        if (ntx > 1) {
+          rx = image_lo(rx, W, 2);
+          keep = rx <= tb.tw;
+        }
+        if (nty > 1) {
+          ry = image_lo(ry, H, 2);
+          keep = keep && ry <= tb.th;
+        }
+      }
+      list_push(keep, pack_code(v, rx, ry), wk.list, &wk.s_cnt);
+    }
+    __syncthreads();
+    const int cnt = wk.s_cnt;
+    for (int q = tid; q < cnt; q += kThreads) {
+      const int code = wk.list[q];
+      const int v = code_slot(code), rx = code_rx(code), ry = code_ry(code);
+      const float4 p = sp[v];
+      const float2 dF = sf[v];
+      float wx[4], wy[4];
+      peskin4(p.x, wx);
+      peskin4(p.y, wy);
+      const float Fx = dF.x * scale, Fy = dF.y * scale;
+      int* bx = wk.accx + (ry + 2) * kAx + rx + 2;
+      int* by = wk.accy + (ry + 2) * kAx + rx + 2;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const float g = wx[a] * wy[b];
+          atomicAdd(bx + b * kAx + a, __float2int_rn(g * Fx));
+          atomicAdd(by + b * kAx + a, __float2int_rn(g * Fy));
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0) wk.s_cnt = 0;
+  }
+  __syncthreads();
+  force_fold(wk, tb, ntx, nty);
+  const float inv = pow2f(-k);
+  const int lane = tid & 31;
+  for (int ly = tid >> 5; ly < tb.th; ly += kWarps) {
+    if (lane < tb.tw) {
+      const int sidx = (ly + 3) * kAx + lane + 3;
+      const size_t c = (size_t)(tb.y0 + ly) * W + tb.x0 + lane;
+      const float Gx = (float)wk.accx[sidx] * inv, Gy = (float)wk.accy[sidx] * inv;
+      float2 F = w.F[c];
+      F.x += Gx;
+      F.y += Gy;
+      w.F[c] = F;
+      const float h = 2.0f * w.mrho[c];
+      float2 u = w.u[c];
+      u.x += Gx / h;
+      u.y += Gy / h;
+      w.u[c] = u;
+    }
+  }
+}
+
 namespace {
 
 template <int R>
@@ -798,6 +902,10 @@ void launch_deposit_x(const Plan& p, cudaStream_t s, int store_fields) { dispatc
 void launch_force_spread(const Plan& p, cudaStream_t s, int store_fields, int after_step) {
   dispatch_steric(p, s, 1, store_fields, after_step);
   launch_layer_spread(p, s);
+}
+
+void launch_mdf_spread(const Plan& p, cudaStream_t s, int pass) {
+  if (p.n_tile_items) k_mdf_spread<<<p.n_tile_items, kThreads, 0, s>>>(p.d_worlds, p.d_tile_items, pass);
 }
 
 void launch_force_lbm(const Plan& p, cudaStream_t s) {

@@ -303,9 +303,11 @@ size_t world_layout(WorldDev& h, void* A) {
   const size_t o_eb = L.take<float>(h.has_energy ? N : 0);
   const size_t o_ob = L.take<unsigned long long>(3);
   const size_t o_nr = L.take<float2>(h.layers == 2 ? N : 0);
-  const bool fixed_spread = h.layers == 2 || h.ib == 1;
-  const size_t o_fa = L.take<unsigned long long>(fixed_spread ? 2 * HW : 0);
-  const size_t o_mr = L.take<float>(h.ib == 1 ? HW : 0);
+  const size_t o_fa = L.take<unsigned long long>(h.layers == 2 ? 2 * HW : 0);
+  const bool df = h.ib == 1;
+  const size_t o_mr = L.take<float>(df ? HW : 0);
+  const size_t o_bs = L.take<int>(df ? N : 0);
+  const size_t o_mm = L.take<unsigned>(df ? 2 : 0);
   if (!A) return L.off;
   h.fil_off = at<int>(A, o_fo);
   h.pos = at<float4>(A, o_pos);
@@ -341,8 +343,10 @@ size_t world_layout(WorldDev& h, void* A) {
   h.ebead = h.has_energy ? at<float>(A, o_eb) : nullptr;
   h.obs = at<unsigned long long>(A, o_ob);
   h.nrm = h.layers == 2 ? at<float2>(A, o_nr) : nullptr;
-  h.facc = fixed_spread ? at<unsigned long long>(A, o_fa) : nullptr;
-  h.mrho = h.ib == 1 ? at<float>(A, o_mr) : nullptr;
+  h.facc = h.layers == 2 ? at<unsigned long long>(A, o_fa) : nullptr;
+  h.mrho = df ? at<float>(A, o_mr) : nullptr;
+  h.bead_slot = df ? at<int>(A, o_bs) : nullptr;
+  h.mdf_max = df ? at<unsigned>(A, o_mm) : nullptr;
   return L.off;
 }
 
