@@ -710,9 +710,9 @@ __device__ __forceinline__ void prefetch_populations(const WorldDev& w, const Ti
 }
 
 // a7 on the tile's cells with F = acc 2^-k from shared memory.  Each warp
-// collides rows warp, warp + 8, ...; the populations of its next row are
-// pulled before the current one is collided (the first before the barrier
-// that completes the spread).
+// collides rows warp, warp + 8, ...; the first row's populations are pulled
+// before the barrier that completes the spread (pulling one row ahead in the
+// loop measured slower: register pressure).
 __device__ __forceinline__ void tile_lbm(TileWork& wk, const WorldDev& w, const TileBox& tb, int k) {
   const int W = w.W, H = w.H, HW = H * W;
   const long long t = *w.t;
@@ -732,15 +732,12 @@ __device__ __forceinline__ void tile_lbm(TileWork& wk, const WorldDev& w, const 
   force_fold(wk, tb, w.ntx, w.nty);
   if (!active) return;
   for (int ly = warp; ly < tb.th; ly += kWarps) {
-    LbmPull qn;
-    const int yn = y + kWarps;
-    if (ly + kWarps < tb.th)
-      lbm_pull(src, HW, yn * W, (yn == 0 ? H - 1 : yn - 1) * W, (yn == H - 1 ? 0 : yn + 1) * W, x, xm, xp, qn);
+    if (ly != warp)
+      lbm_pull(src, HW, y * W, (y == 0 ? H - 1 : y - 1) * W, (y == H - 1 ? 0 : y + 1) * W, x, xm, xp, q);
     const int s = (ly + 3) * kAx + lane + 3;
     const float2 F = make_float2((float)wk.accx[s] * inv, (float)wk.accy[s] * inv);
     u_out[(size_t)y * W + x] = lbm_collide(q, dst, HW, y * W + x, F, kc);
-    q = qn;
-    y = yn;
+    y += kWarps;
   }
 }
 
