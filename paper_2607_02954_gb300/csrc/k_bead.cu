@@ -698,6 +698,27 @@ __global__ void k_stream_out(const float* __restrict__ g, float* __restrict__ ou
   out[idx] = g[i * HW + sy * W + sx];
 }
 
+// A world's set-up from its raw inputs: each position wrapped into the box
+// in double precision (fmod is exact) and split into cell index + fraction,
+// the creation positions, the drive records (theta0, A, freq, phase) and the
+// rest-length drive records (L0 = L_rest, amp, freq, phase).
+__global__ void k_world_init(WorldDev h, const float* x, const float* y, const float* t0, const float* amp,
+                             const float* frq, const float* phs, const float* la, const float* lf,
+                             const float* lp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < h.N) {
+    const double xd = fmod((double)x[i], (double)h.W), yd = fmod((double)y[i], (double)h.H);
+    float xw = (float)(xd < 0 ? xd + h.W : xd), yw = (float)(yd < 0 ? yd + h.H : yd);
+    if (xw >= (float)h.W) xw = 0.0f;
+    if (yw >= (float)h.H) yw = 0.0f;
+    const float cx = floorf(xw), cy = floorf(yw);
+    h.pos0[i] = make_float2(xw, yw);
+    h.pos[i] = make_float4(xw - cx, yw - cy, __int_as_float((int)cx), __int_as_float((int)cy));
+  }
+  if (i < h.J) const_cast<float4*>(h.drive)[i] = make_float4(t0[i], amp[i], frq[i], phs[i]);
+  if (la && i < h.E) const_cast<float4*>(h.ldrive)[i] = make_float4(h.L_rest[i], la[i], lf[i], lp[i]);
+}
+
 __global__ void k_positions_out(const float4* __restrict__ pos, int N, float* x, float* y) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -795,6 +816,12 @@ void launch_unstream_in(const float* f0dev, float* g_dst, int H, int W, cudaStre
 void launch_stream_out(const float* g_src, float* out, int H, int W, cudaStream_t s) {
   const int n = 9 * H * W;
   k_stream_out<<<(n + 255) / 256, 256, 0, s>>>(g_src, out, H, W);
+}
+
+void launch_world_init(const WorldDev& w, const float* const raw[9], cudaStream_t s) {
+  if (w.N == 0) return;
+  k_world_init<<<(w.N + 255) / 256, 256, 0, s>>>(w, raw[0], raw[1], raw[2], raw[3], raw[4], raw[5], raw[6], raw[7],
+                                                 raw[8]);
 }
 
 void launch_positions_out(const WorldDev& w, float* x, float* y, cudaStream_t s) {

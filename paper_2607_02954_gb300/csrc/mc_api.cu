@@ -56,19 +56,6 @@ bool finite_all(const float* a, size_t n) {
   return true;
 }
 
-// Copies n floats of either memory kind to a host vector.
-mc_status fetch(const float* src, size_t n, int kind, std::vector<float>& out, const char* name) {
-  out.resize(n);
-  if (n == 0) return MC_OK;
-  if (!src) return fail(MC_ERR_INVALID_ARG, std::string(name) + " is NULL");
-  if (kind == MC_MEM_HOST) {
-    std::memcpy(out.data(), src, n * sizeof(float));
-  } else {
-    MC_CUDA(cudaMemcpy(out.data(), src, n * sizeof(float), cudaMemcpyDeviceToHost));
-  }
-  return MC_OK;
-}
-
 mc_status validate_params(const mc_params& p) {
   const float v[] = {p.nu, p.dt, p.Lambda, p.kappa, p.k_bend, p.k_stretch, p.k_shear, p.k_rep, p.sigma, p.orient};
   for (float x : v)
@@ -410,57 +397,51 @@ mc_status mc_world_create(const mc_world_desc* d, void* stream, mc_world** out) 
   const int E = N - d->n_fil, J = N - 2 * d->n_fil;
   const size_t HW = (size_t)H * W;
 
-  std::vector<float> x, y, th, Lr, t0v, amp, frq, phs, f0;
-  if ((st = fetch(d->x, N, d->mem_kind, x, "x")) || (st = fetch(d->y, N, d->mem_kind, y, "y")) ||
-      (st = fetch(d->theta, E, d->mem_kind, th, "theta")) || (st = fetch(d->L_rest, E, d->mem_kind, Lr, "L_rest")) ||
-      (st = fetch(d->theta0, J, d->mem_kind, t0v, "theta0")) ||
-      (st = fetch(d->drive_amp, J, d->mem_kind, amp, "drive_amp")) ||
-      (st = fetch(d->drive_freq, J, d->mem_kind, frq, "drive_freq")) ||
-      (st = fetch(d->drive_phase, J, d->mem_kind, phs, "drive_phase")))
+  // Inputs: host pointers for validation (the caller's arrays, or host
+  // copies of device arrays) and, later, device pointers for the set-up
+  // kernel (the caller's device arrays, or a staging buffer the host arrays
+  // are uploaded to).
+  const bool on_host = d->mem_kind == MC_MEM_HOST;
+  std::vector<std::vector<float>> keep;
+  auto view = [&](const float* p, size_t n, const char* name, const float*& hv) -> mc_status {
+    hv = nullptr;
+    if (n == 0) return MC_OK;
+    if (!p) return fail(MC_ERR_INVALID_ARG, std::string(name) + " is NULL");
+    if (on_host) {
+      hv = p;
+      return MC_OK;
+    }
+    keep.emplace_back(n);
+    MC_CUDA(cudaMemcpy(keep.back().data(), p, n * sizeof(float), cudaMemcpyDeviceToHost));
+    hv = keep.back().data();
+    return MC_OK;
+  };
+  auto finite = [](const float* a, size_t n) { return !a || finite_all(a, n); };
+  const float *hx, *hy, *hth, *hL, *ht0, *hamp, *hfrq, *hphs;
+  const float *hf0 = nullptr, *hla = nullptr, *hlf = nullptr, *hlp = nullptr, *hen = nullptr;
+  if ((st = view(d->x, N, "x", hx)) || (st = view(d->y, N, "y", hy)) || (st = view(d->theta, E, "theta", hth)) ||
+      (st = view(d->L_rest, E, "L_rest", hL)) || (st = view(d->theta0, J, "theta0", ht0)) ||
+      (st = view(d->drive_amp, J, "drive_amp", hamp)) || (st = view(d->drive_freq, J, "drive_freq", hfrq)) ||
+      (st = view(d->drive_phase, J, "drive_phase", hphs)))
     return st;
-  if (d->f0 && (st = fetch(d->f0, 9 * HW, d->mem_kind, f0, "f0"))) return st;
+  if (d->f0 && (st = view(d->f0, 9 * HW, "f0", hf0))) return st;
   const int n_len = (d->len_amp != nullptr) + (d->len_freq != nullptr) + (d->len_phase != nullptr);
   if (n_len != 0 && n_len != 3) return fail(MC_ERR_INVALID_ARG, "len_amp, len_freq, len_phase: all three or none");
-  std::vector<float> lamp, lfrq, lphs, energy;
-  if (n_len == 3 && ((st = fetch(d->len_amp, E, d->mem_kind, lamp, "len_amp")) ||
-                     (st = fetch(d->len_freq, E, d->mem_kind, lfrq, "len_freq")) ||
-                     (st = fetch(d->len_phase, E, d->mem_kind, lphs, "len_phase"))))
+  if (n_len == 3 && ((st = view(d->len_amp, E, "len_amp", hla)) || (st = view(d->len_freq, E, "len_freq", hlf)) ||
+                     (st = view(d->len_phase, E, "len_phase", hlp))))
     return st;
-  if (d->energy && (st = fetch(d->energy, HW, d->mem_kind, energy, "energy"))) return st;
-  if (!finite_all(lamp.data(), lamp.size()) || !finite_all(lfrq.data(), lfrq.size()) ||
-      !finite_all(lphs.data(), lphs.size()) || !finite_all(energy.data(), energy.size()))
+  if (d->energy && (st = view(d->energy, HW, "energy", hen))) return st;
+  if (!finite(hla, E) || !finite(hlf, E) || !finite(hlp, E) || !finite(hen, HW))
     return fail(MC_ERR_INVALID_ARG, "non-finite input value");
-  for (float a : lamp)
-    if (!(std::fabs(a) < 1.0f)) return fail(MC_ERR_INVALID_ARG, "|len_amp| must be < 1 (rest lengths stay > 0)");
+  if (hla)
+    for (int e = 0; e < E; ++e)
+      if (!(std::fabs(hla[e]) < 1.0f)) return fail(MC_ERR_INVALID_ARG, "|len_amp| must be < 1 (rest lengths stay > 0)");
   if (d->observe != 0 && d->observe != 1) return fail(MC_ERR_INVALID_ARG, "observe must be 0 or 1");
-  if (!finite_all(x.data(), N) || !finite_all(y.data(), N) || !finite_all(th.data(), E) ||
-      !finite_all(Lr.data(), E) || !finite_all(t0v.data(), J) || !finite_all(amp.data(), J) ||
-      !finite_all(frq.data(), J) || !finite_all(phs.data(), J) || !finite_all(f0.data(), f0.size()))
+  if (!finite(hx, N) || !finite(hy, N) || !finite(hth, E) || !finite(hL, E) || !finite(ht0, J) ||
+      !finite(hamp, J) || !finite(hfrq, J) || !finite(hphs, J) || !finite(hf0, 9 * HW))
     return fail(MC_ERR_INVALID_ARG, "non-finite input value");
   for (int e = 0; e < E; ++e)
-    if (!(Lr[e] > 0.0f)) return fail(MC_ERR_INVALID_ARG, "L_rest must be > 0");
-
-  // host images of the device arrays
-  std::vector<float4> pos(N), drive(J);
-  std::vector<float2> pos0(N);
-  for (int i = 0; i < N; ++i) {
-    const double xd = std::fmod((double)x[i], (double)W), yd = std::fmod((double)y[i], (double)H);
-    float xw = (float)(xd < 0 ? xd + W : xd), yw = (float)(yd < 0 ? yd + H : yd);
-    if (xw >= (float)W) xw = 0.0f;
-    if (yw >= (float)H) yw = 0.0f;
-    const float cx = std::floor(xw), cy = std::floor(yw);
-    int icx, icy;
-    icx = (int)cx;
-    icy = (int)cy;
-    pos0[i] = make_float2(xw, yw);
-    float4 p;
-    p.x = xw - cx;   // exact
-    p.y = yw - cy;
-    std::memcpy(&p.z, &icx, 4);
-    std::memcpy(&p.w, &icy, 4);
-    pos[i] = p;
-  }
-  for (int j = 0; j < J; ++j) drive[j] = make_float4(t0v[j], amp[j], frq[j], phs[j]);
+    if (!(hL[e] > 0.0f)) return fail(MC_ERR_INVALID_ARG, "L_rest must be > 0");
 
   mc_world* w = new mc_world();
   w->stream = s;
@@ -495,30 +476,64 @@ mc_status mc_world_create(const mc_world_desc* d, void* stream, mc_world** out) 
     if (e_ != cudaSuccess) return fail_free(cuda_fail(e_, #call));       \
   } while (0)
   MC_CUDA_W(cudaMemsetAsync(A, 0, w->bytes, s));
-  auto up = [&](void* dst, const void* src, size_t n) {
-    return n ? cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s) : cudaSuccess;
+  const cudaMemcpyKind kind = on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  auto up = [&](void* dst, const void* src, size_t n, cudaMemcpyKind k) {
+    return n ? cudaMemcpyAsync(dst, src, n, k, s) : cudaSuccess;
   };
-  MC_CUDA_W(up((void*)h.fil_off, fo.data(), fo.size() * sizeof(int)));
-  MC_CUDA_W(up(h.pos, pos.data(), N * sizeof(float4)));
-  MC_CUDA_W(up(h.pos0, pos0.data(), N * sizeof(float2)));
-  MC_CUDA_W(up(h.theta, th.data(), E * sizeof(float)));
-  MC_CUDA_W(up((void*)h.L_rest, Lr.data(), E * sizeof(float)));
-  MC_CUDA_W(up((void*)h.drive, drive.data(), J * sizeof(float4)));
-  if (h.has_ldrive) {
-    std::vector<float4> ld(E);
-    for (int e = 0; e < E; ++e) ld[e] = make_float4(Lr[e], lamp[e], lfrq[e], lphs[e]);
-    MC_CUDA_W(up((void*)h.ldrive, ld.data(), E * sizeof(float4)));
+  MC_CUDA_W(up((void*)h.fil_off, fo.data(), fo.size() * sizeof(int), cudaMemcpyHostToDevice));
+  MC_CUDA_W(up(h.theta, d->theta, E * sizeof(float), kind));
+  MC_CUDA_W(up((void*)h.L_rest, d->L_rest, E * sizeof(float), kind));
+  if (h.has_energy) MC_CUDA_W(up((void*)h.energy, d->energy, HW * sizeof(float), kind));
+  // raw per-bead, per-joint and per-edge inputs on the device for the set-up
+  // kernel (positions wrapped and split into cell + fraction, drive records)
+  const float* raw[9] = {d->x, d->y, d->theta0, d->drive_amp, d->drive_freq, d->drive_phase,
+                         n_len == 3 ? d->len_amp : nullptr, n_len == 3 ? d->len_freq : nullptr,
+                         n_len == 3 ? d->len_phase : nullptr};
+  const size_t cnt[9] = {(size_t)N, (size_t)N, (size_t)J, (size_t)J, (size_t)J, (size_t)J,
+                         (size_t)E, (size_t)E, (size_t)E};
+  float* staging = nullptr;
+  if (on_host) {
+    size_t tot = 0;
+    for (int k = 0; k < 9; ++k) tot += raw[k] ? cnt[k] : 0;
+    if (tot) MC_CUDA_W(cudaMallocAsync((void**)&staging, tot * sizeof(float), s));
+    size_t off = 0;
+    for (int k = 0; k < 9; ++k) {
+      if (!raw[k] || !cnt[k]) continue;
+      const cudaError_t e2 = up(staging + off, raw[k], cnt[k] * sizeof(float), cudaMemcpyHostToDevice);
+      if (e2 != cudaSuccess) {
+        cudaFreeAsync(staging, s);
+        return fail_free(cuda_fail(e2, "input upload"));
+      }
+      raw[k] = staging + off;
+      off += cnt[k];
+    }
   }
-  if (h.has_energy) MC_CUDA_W(up((void*)h.energy, energy.data(), HW * sizeof(float)));
+  mc::launch_world_init(h, raw, s);
+  if (staging) cudaFreeAsync(staging, s);
+  MC_CUDA_W(cudaGetLastError());
   const long long t0 = d->t0;
-  MC_CUDA_W(up(h.t, &t0, sizeof(long long)));
-  if (!f0.empty()) {
+  MC_CUDA_W(up(h.t, &t0, sizeof(long long), cudaMemcpyHostToDevice));
+  if (d->f0) {
     // stage f0 in the buffer the first step writes, then store its
     // post-collision image in the buffer the first step reads
     float* stage = h.g[(t0 + 1) & 1];
-    MC_CUDA_W(up(stage, f0.data(), 9 * HW * sizeof(float)));
+    MC_CUDA_W(up(stage, d->f0, 9 * HW * sizeof(float), kind));
     mc::launch_unstream_in(stage, h.g[t0 & 1], H, W, s);
     MC_CUDA_W(cudaGetLastError());
+  }
+  // copies from page-locked host memory are still in flight: finish them
+  // before returning, so the caller may free or reuse its arrays at once
+  if (on_host) {
+    bool pinned = false;
+    const float* srcs[] = {d->x, d->y, d->theta, d->L_rest, d->theta0, d->drive_amp, d->drive_freq,
+                           d->drive_phase, d->len_amp, d->len_freq, d->len_phase, d->energy, d->f0};
+    for (const float* p : srcs) {
+      if (!p) continue;
+      cudaPointerAttributes at{};
+      if (cudaPointerGetAttributes(&at, p) == cudaSuccess && at.type == cudaMemoryTypeHost) pinned = true;
+      (void)cudaGetLastError();
+    }
+    if (pinned) MC_CUDA_W(cudaStreamSynchronize(s));
   }
   mc_world* self = w;
   st = build_plan(&self, 1, s, w->plan);

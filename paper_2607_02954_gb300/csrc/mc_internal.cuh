@@ -173,6 +173,10 @@ void launch_set_counter(const WorldDev& h, long long t, cudaStream_t s);
 void launch_unstream_in(const float* f0dev, float* g_dst, int H, int W, cudaStream_t s);
 void launch_stream_out(const float* g_src, float* out, int H, int W, cudaStream_t s);
 void launch_positions_out(const WorldDev& w, float* x, float* y, cudaStream_t s);
+// positions, creation positions, drive and rest-length drive records from the
+// raw device arrays x, y [N], theta0, amp, freq, phase [J], len_amp,
+// len_freq, len_phase [E] (the last three may be null)
+void launch_world_init(const WorldDev& w, const float* const raw[9], cudaStream_t s);
 void launch_cells_out(const WorldDev& w, int* cell, cudaStream_t s);
 
 // --- world life cycle and plans (host, mc_api.cu) -------------------------

@@ -102,3 +102,43 @@ def test_mdf_worlds_refuse_reverse_mode_and_stages():
         z = torch.zeros(spec.N, dtype=torch.float32, device="cuda")
         w.rollout_backward(z, z)
     w.close()
+
+
+def test_mdf_served_mix_equals_alone_bitwise():
+    """Direct-forcing requests served among penalty requests (worlds joining
+    and leaving the batch) give the same result as served alone."""
+    from paper_2607_02954_gb300 import Server
+    specs = [(_mdf(synth.world_random(40 + k, 64, 3 + k), 2 + k % 3), 25 + 5 * k) if k % 2 == 0
+             else (synth.world_random(40 + k, 64, 4), 30) for k in range(6)]
+    srv = Server(max_slots=3, steps_per_tick=6)
+    mixed = [srv.wait(t) for t in [srv.submit(sp, n) for sp, n in specs]]
+    srv.close()
+    for (sp, n), r in zip(specs, mixed):
+        assert r["status"] == 0 and r["n_steps"] == n
+        alone = Server(max_slots=1, steps_per_tick=11)
+        ra = alone.wait(alone.submit(sp, n))
+        alone.close()
+        assert ra["com_disp"] == r["com_disp"], (ra, r)
+
+
+@pytest.mark.parametrize("variant", ["red_black", "observables"])
+def test_mdf_with_other_features_matches_oracle(variant):
+    """Direct forcing with red-black PBD, and with a rest-length drive,
+    energy field and observables: one step against the oracle, and the
+    observables after 20 steps."""
+    from tests.test_gpu_parity import _compare_one_step
+    spec = synth.world_c1(7)
+    if variant == "red_black":
+        spec.params = synth.Params(pbd_order=1, ib=1, mdf_iters=3)
+        _compare_one_step(spec)
+        return
+    spec.params = synth.Params(ib=1, mdf_iters=3)
+    synth.with_observables(spec, 3)
+    _compare_one_step(spec)
+    want = O.observables(O.World(spec), 20)
+    w = _world(spec)
+    w.step(20)
+    got = w.observables()
+    w.close()
+    for k in ("e_bend", "e_pos", "energy"):
+        assert abs(got[k] - want[k]) <= 1e-5 * max(abs(want[k]), 1.0), (k, got[k], want[k])
