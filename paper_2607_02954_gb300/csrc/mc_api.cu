@@ -6,6 +6,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "mc_internal.cuh"
@@ -50,10 +51,27 @@ T* at(void* base, size_t off) {
   return reinterpret_cast<T*>(static_cast<char*>(base) + off);
 }
 
+// Whether ok(a[i]) holds for every i < n; arrays of more than 2^20 values
+// are split over up to 8 host threads.
+template <class F>
+bool all_of(const float* a, size_t n, F ok) {
+  const size_t kChunk = size_t(1) << 20;
+  const int nt = n <= kChunk ? 1 : (int)std::min<size_t>(8, (n + kChunk - 1) / kChunk);
+  auto run = [&](size_t lo, size_t hi) {
+    for (size_t i = lo; i < hi; ++i)
+      if (!ok(a[i])) return false;
+    return true;
+  };
+  if (nt == 1) return run(0, n);
+  std::vector<char> res(nt, 1);
+  std::vector<std::thread> th;
+  for (int k = 0; k < nt; ++k) th.emplace_back([&, k] { res[k] = run(n * k / nt, n * (k + 1) / nt); });
+  for (auto& t : th) t.join();
+  return std::all_of(res.begin(), res.end(), [](char r) { return r != 0; });
+}
+
 bool finite_all(const float* a, size_t n) {
-  for (size_t i = 0; i < n; ++i)
-    if (!std::isfinite(a[i])) return false;
-  return true;
+  return all_of(a, n, [](float v) { return std::isfinite(v); });
 }
 
 mc_status validate_params(const mc_params& p) {
@@ -433,15 +451,13 @@ mc_status mc_world_create(const mc_world_desc* d, void* stream, mc_world** out) 
   if (d->energy && (st = view(d->energy, HW, "energy", hen))) return st;
   if (!finite(hla, E) || !finite(hlf, E) || !finite(hlp, E) || !finite(hen, HW))
     return fail(MC_ERR_INVALID_ARG, "non-finite input value");
-  if (hla)
-    for (int e = 0; e < E; ++e)
-      if (!(std::fabs(hla[e]) < 1.0f)) return fail(MC_ERR_INVALID_ARG, "|len_amp| must be < 1 (rest lengths stay > 0)");
+  if (hla && !all_of(hla, E, [](float v) { return std::fabs(v) < 1.0f; }))
+    return fail(MC_ERR_INVALID_ARG, "|len_amp| must be < 1 (rest lengths stay > 0)");
   if (d->observe != 0 && d->observe != 1) return fail(MC_ERR_INVALID_ARG, "observe must be 0 or 1");
   if (!finite(hx, N) || !finite(hy, N) || !finite(hth, E) || !finite(hL, E) || !finite(ht0, J) ||
       !finite(hamp, J) || !finite(hfrq, J) || !finite(hphs, J) || !finite(hf0, 9 * HW))
     return fail(MC_ERR_INVALID_ARG, "non-finite input value");
-  for (int e = 0; e < E; ++e)
-    if (!(hL[e] > 0.0f)) return fail(MC_ERR_INVALID_ARG, "L_rest must be > 0");
+  if (hL && !all_of(hL, E, [](float v) { return v > 0.0f; })) return fail(MC_ERR_INVALID_ARG, "L_rest must be > 0");
 
   mc_world* w = new mc_world();
   w->stream = s;
