@@ -536,7 +536,7 @@ def main():
     world.close()
 
     # ---- end to end through the C ABI from pinned host buffers ----------
-    e2e_steps = max(16, min(args.steps, 200))
+    e2e_steps = max(16, min(args.steps, 4000))   # the timed run's step count (bounded)
     in_keys = ("x", "y", "theta", "L_rest", "theta0", "drive_amp", "drive_freq", "drive_phase")
     pinned = copy.copy(spec)
     for k in in_keys:   # page-locked copies of the input arrays (numpy views of pinned tensors)
