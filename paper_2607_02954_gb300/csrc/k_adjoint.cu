@@ -573,8 +573,7 @@ static int blocks(int n) { return (n + 255) / 256; }
 void launch_adj_step(const Plan& p, const WorldDev& h, AdjDev a, int src_parity, cudaStream_t s) {
   const WorldDev* wd = p.d_worlds;
   const int HW = h.H * h.W;
-  cudaMemsetAsync(a.ubar, 0, HW * sizeof(float2), s);
-  cudaMemsetAsync(a.Q, 0, HW * sizeof(float2), s);
+  // (u_bar and Q are cleared by the caller before each step)
   if (h.N) k_adj_spread_u<<<blocks(h.N), 256, 0, s>>>(wd, a);
   k_adj_lbm<<<blocks(HW), 256, 0, s>>>(wd, a, src_parity);
   if (h.N) k_adj_bead_a<<<blocks(h.N), 256, 0, s>>>(wd, a);

@@ -7,9 +7,9 @@
 // mc_rollout_backward  given dL/d(final unwrapped positions), walks the
 //                      segments from last to first: re-runs the segment's
 //                      forward from its checkpoint keeping every step's
-//                      state, then for each step from last to first restores
-//                      it, recomputes that step's intermediates with the
-//                      forward kernels and applies the adjoint kernels.
+//                      state and intermediates (F_el, F_s, rho_bar, u, F), then
+//                      for each step from last to first restores them and
+//                      applies the adjoint kernels.
 //                      Accumulates dL/dtheta0 and leaves the world in its
 //                      final state.
 #include <algorithm>
@@ -82,6 +82,81 @@ mc_status load_state(const mc::WorldDev& h, int parity, const char* rec, const S
   if (h.E) MC_ACUDA(cudaMemcpyAsync(h.theta, rec + sl.theta, h.E * sizeof(float), cudaMemcpyDeviceToDevice, s));
   MC_ACUDA(cudaMemcpyAsync(h.g[parity], rec + sl.g, 9 * HW * sizeof(float), cudaMemcpyDeviceToDevice, s));
   return MC_OK;
+}
+
+// One step of a segment record: the state at the start of the step (as a
+// checkpoint) followed by the step's intermediates the adjoint reads.
+struct StepSlot {
+  StateSlot st;
+  size_t fel, fs, rho_b, u, F;
+  size_t bytes;
+};
+
+StepSlot step_slot(const mc::WorldDev& h) {
+  StepSlot s;
+  s.st = state_slot(h);
+  const size_t HW = (size_t)h.H * h.W;
+  s.fel = s.st.bytes;
+  s.fs = s.fel + align256((size_t)h.N * sizeof(float2));
+  s.rho_b = s.fs + align256((size_t)h.N * sizeof(float2));
+  s.u = s.rho_b + align256(HW * sizeof(float));
+  s.F = s.u + align256(HW * sizeof(float2));
+  s.bytes = s.F + align256(HW * sizeof(float2));
+  return s;
+}
+
+// After a recomputed step: its intermediates (F_el, F_s, rho_bar, u, F) into
+// `cur`, and, with `next`, the state the next step starts from (positions,
+// edge angles, the populations of parity `par`).
+__global__ void k_seg_save(const mc::WorldDev* __restrict__ wd, char* cur, char* next, int par, StepSlot sl) {
+  const mc::WorldDev& h = *wd;
+  const size_t HW = (size_t)h.H * h.W, n9 = 9 * HW;
+  const size_t total = n9 > (size_t)h.N ? n9 : (size_t)h.N;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    if (i < (size_t)h.N) {
+      reinterpret_cast<float2*>(cur + sl.fel)[i] = h.fel[i];
+      reinterpret_cast<float2*>(cur + sl.fs)[i] = h.fs[i];
+      if (next) reinterpret_cast<float4*>(next + sl.st.pos)[i] = h.pos[i];
+    }
+    if (next && i < (size_t)h.E) reinterpret_cast<float*>(next + sl.st.theta)[i] = h.theta[i];
+    if (i < HW) {
+      reinterpret_cast<float*>(cur + sl.rho_b)[i] = h.rho_b[i];
+      reinterpret_cast<float2*>(cur + sl.u)[i] = h.u[i];
+      reinterpret_cast<float2*>(cur + sl.F)[i] = h.F[i];
+    }
+    if (next && i < n9) reinterpret_cast<float*>(next + sl.st.g)[i] = h.g[par][i];
+  }
+}
+
+// Before a step's adjoint: the world's positions, populations of parity
+// `par` and intermediates from the record, the step counter, and the
+// per-step adjoint accumulators (u_bar, Q) cleared.
+__global__ void k_seg_restore(const mc::WorldDev* __restrict__ wd, const char* rec, int par, long long t,
+                              StepSlot sl, float2* ubar, float2* Q) {
+  const mc::WorldDev& h = *wd;
+  const size_t HW = (size_t)h.H * h.W, n9 = 9 * HW;
+  const size_t total = n9 > (size_t)h.N ? n9 : (size_t)h.N;
+  const size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i0 == 0) {
+    *h.t = t;
+    h.fel_max[0] = 0u;
+    h.fel_max[1] = 0u;
+  }
+  for (size_t i = i0; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    if (i < (size_t)h.N) {
+      h.pos[i] = reinterpret_cast<const float4*>(rec + sl.st.pos)[i];
+      h.fel[i] = reinterpret_cast<const float2*>(rec + sl.fel)[i];
+      h.fs[i] = reinterpret_cast<const float2*>(rec + sl.fs)[i];
+    }
+    if (i < HW) {
+      h.rho_b[i] = reinterpret_cast<const float*>(rec + sl.rho_b)[i];
+      h.u[i] = reinterpret_cast<const float2*>(rec + sl.u)[i];
+      h.F[i] = reinterpret_cast<const float2*>(rec + sl.F)[i];
+      ubar[i] = make_float2(0.0f, 0.0f);
+      Q[i] = make_float2(0.0f, 0.0f);
+    }
+    if (i < n9) h.g[par][i] = reinterpret_cast<const float*>(rec + sl.st.g)[i];
+  }
 }
 
 __global__ void k_interleave(const float* gx, const float* gy, float2* out, int n) {
@@ -198,6 +273,10 @@ mc_status sweep(mc_world* w, mc::AdjDev a, float* const adjG[2], char* obs_keep,
   const size_t HW = (size_t)h.H * h.W;
   const int K = w->tape_every, n = w->tape_steps;
   char* tape = static_cast<char*>(w->tape);
+  const StepSlot ss = step_slot(h);
+  const mc::WorldDev* wd = w->plan.d_worlds;
+  const size_t total = std::max((size_t)9 * HW, (size_t)h.N);
+  const int grid = (int)std::min<size_t>((total + 255) / 256, 4096);
   // the recompute passes accumulate the observables again: keep the rollout's values
   MC_ACUDA(cudaMemcpyAsync(obs_keep, h.obs, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
   if (h.E) MC_ACUDA(cudaMemsetAsync(a.adjTh, 0, h.E * sizeof(float), s));
@@ -213,28 +292,30 @@ mc_status sweep(mc_world* w, mc::AdjDev a, float* const adjG[2], char* obs_keep,
     mc_status st = load_state(h, (int)(tk & 1), tape + (size_t)k * sl.bytes, sl, s);
     if (st != MC_OK) return st;
     mc::launch_set_counter(h, tk, s);
+    st = save_state(h, (int)(tk & 1), seg, sl, s);   // the segment's first state
+    if (st != MC_OK) return st;
+    // the segment's forward, keeping every step's state and intermediates
+    // (the unfused stages: the same step bitwise, with rho_bar and u in memory)
     for (int q = 0; q < steps; ++q) {
-      st = save_state(h, (int)((tk + q) & 1), seg + (size_t)q * sl.bytes, sl, s);
-      if (st != MC_OK) return st;
-      mc::enqueue_step(w->plan, s);
-    }
-    for (int q = steps - 1; q >= 0; --q) {
-      const int64_t tn = tk + q;
-      const int par = (int)(tn & 1);
-      const char* rec = seg + (size_t)q * sl.bytes;
-      st = load_state(h, par, rec, sl, s);
-      if (st != MC_OK) return st;
-      mc::launch_set_counter(h, tn, s);
-      // this step's intermediates (F_el, F_s, rho_bar, F, u)
       mc::launch_pbd(w->plan, s);
       mc::launch_bin_scan(w->plan, s);
       mc::launch_bin_scatter(w->plan, s);
       mc::launch_deposit_x(w->plan, s, 0);
       mc::launch_force_spread(w->plan, s, 1, 0);
       mc::launch_lbm(w->plan, s);
+      mc::launch_interp_advance(w->plan, s);
+      char* next = q + 1 < steps ? seg + (size_t)(q + 1) * ss.bytes : nullptr;
+      k_seg_save<<<grid, 256, 0, s>>>(wd, seg + (size_t)q * ss.bytes, next, (int)((tk + q + 1) & 1), ss);
+    }
+    MC_ACUDA(cudaGetLastError());
+    for (int q = steps - 1; q >= 0; --q) {
+      const int64_t tn = tk + q;
+      const int par = (int)(tn & 1);
+      const char* rec = seg + (size_t)q * ss.bytes;
+      k_seg_restore<<<grid, 256, 0, s>>>(wd, rec, par, (long long)tn, ss, a.ubar, a.Q);
       a.adjG_next = adjG[cur];
       a.adjG_cur = adjG[cur ^ 1];
-      a.theta_n = reinterpret_cast<const float*>(rec + sl.theta);
+      a.theta_n = reinterpret_cast<const float*>(rec + ss.st.theta);
       mc::launch_adj_step(w->plan, h, a, par, s);
       cur ^= 1;
     }
@@ -294,7 +375,7 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
   const size_t o_rsb = take(HW * sizeof(float));
   const size_t o_fbt = take(h.N * sizeof(float2));
   const size_t o_dbar = take(h.N * sizeof(float2));
-  const size_t o_seg = take((size_t)K * sl.bytes);
+  const size_t o_seg = take((size_t)K * step_slot(h).bytes);
   if (w->adj_bytes < off) {
     if (w->adj) cudaFreeAsync(w->adj, w->stream);
     w->adj = nullptr;
