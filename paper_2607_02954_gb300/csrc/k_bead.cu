@@ -468,16 +468,17 @@ __device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, 
 // coordinates.  Filaments of at most 64 beads run in registers; longer ones
 // in the warp's slice of dynamic shared memory (maxB floats per array; zero
 // when no filament of the launch is longer than 64 beads).
-template <bool kExt, int kMode>
+template <bool kExt, int kMode, bool kSingle>
 __global__ void __launch_bounds__(256, 4) k_pbd(const WorldDev* __restrict__ worlds,
-                                             const int2* __restrict__ items, int n_items, int maxB) {
+                                             const int2* __restrict__ items, int n_items, int maxB,
+                                             const __grid_constant__ WorldDev w1) {
   extern __shared__ __align__(16) float smem[];   // maxB is a multiple of 4: float4 slices stay aligned
   const int wpb = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int item = blockIdx.x * wpb + warp;
   if (item >= n_items) return;  // warp-uniform exit; the kernel has no block barrier
-  const int2 it = items[item];
-  const WorldDev& w = worlds[it.x];
+  const int2 it = kSingle ? make_int2(0, item) : items[item];
+  const WorldDev& w = kSingle ? w1 : worlds[it.x];
   if ((kMode == 2) != (w.ib == 1)) return;   // direct-forcing worlds run their PBD after the steric spread
   const int f = it.y;
   const int b0 = w.fil_off[f];
@@ -499,10 +500,12 @@ __global__ void __launch_bounds__(256, 4) k_pbd(const WorldDev* __restrict__ wor
 
 // a2: scatter bead records into bin order.  Lanes of one warp that share a
 // bin take consecutive slots from one atomic.
+template <bool kSingle>
 __global__ void __launch_bounds__(kBeadChunk) k_bin_scatter(const WorldDev* __restrict__ worlds,
-                                                            const int2* __restrict__ items) {
-  const int2 it = items[blockIdx.x];
-  const WorldDev& w = worlds[it.x];
+                                                            const int2* __restrict__ items,
+                                                            const __grid_constant__ WorldDev w1) {
+  const int2 it = kSingle ? make_int2(0, (int)blockIdx.x * kBeadChunk) : items[blockIdx.x];
+  const WorldDev& w = kSingle ? w1 : worlds[it.x];
   const int i = it.y + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const bool valid = i < w.N;
@@ -622,11 +625,12 @@ __global__ void __launch_bounds__(kCellChunk) k_layer_finish(const WorldDev* __r
 // inertia-free advance X += dt U (cell index + fraction, wrapped) and the
 // unwrapped displacement D += dt U.  Thread 0 of each world's first block
 // advances the world's step counter (no other stage kernel reads it).
-template <bool kExt>
+template <bool kExt, bool kSingle>
 __global__ void __launch_bounds__(kBeadChunk) k_interp_advance(const WorldDev* __restrict__ worlds,
-                                                               const int2* __restrict__ items) {
-  const int2 it = items[blockIdx.x];
-  const WorldDev& w = worlds[it.x];
+                                                               const int2* __restrict__ items,
+                                                               const __grid_constant__ WorldDev w1) {
+  const int2 it = kSingle ? make_int2(0, (int)blockIdx.x * kBeadChunk) : items[blockIdx.x];
+  const WorldDev& w = kSingle ? w1 : worlds[it.x];
   if (it.y == 0 && threadIdx.x == 0) *w.t += 1;
   const int i = it.y + threadIdx.x;
   const int W = w.W, H = w.H;
@@ -754,8 +758,8 @@ void launch_pbd(const Plan& p, cudaStream_t s) {
   const int grid = (p.n_fil_items + wpb - 1) / wpb;
   // worlds with a rest-length drive, observables or two layers need the
   // extended kernel; it computes every other world exactly as the plain one
-  auto kern = p.any_ext ? k_pbd<true, 0> : k_pbd<false, 0>;
-  kern<<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
+  auto kern = p.any_ext ? k_pbd<true, 0, false> : k_pbd<false, 0, false>;
+  kern<<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb, p.h_world0);
 }
 
 // The PBD of direct-forcing worlds (from the positions the fluid carries
@@ -766,7 +770,7 @@ void launch_pbd_mdf(const Plan& p, cudaStream_t s) {
   const int wpb = pbd_warps_per_block(mb);
   const size_t smem = p.max_B <= 64 ? 0 : (size_t)wpb * mb * kPbdFloatsPerBead * sizeof(float);
   const int grid = (p.n_fil_items + wpb - 1) / wpb;
-  k_pbd<true, 2><<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
+  k_pbd<true, 2, false><<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb, p.h_world0);
 }
 
 // a8 of the previous step fused with this step's a1-a3 (plans without the
@@ -777,7 +781,7 @@ void launch_advance_pbd(const Plan& p, cudaStream_t s) {
   const int wpb = pbd_warps_per_block(mb);
   const size_t smem = p.max_B <= 64 ? 0 : (size_t)wpb * mb * kPbdFloatsPerBead * sizeof(float);
   const int grid = (p.n_fil_items + wpb - 1) / wpb;
-  k_pbd<false, 1><<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
+  k_pbd<false, 1, false><<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb, p.h_world0);
 }
 
 // Shared-memory limits set once per process, outside any stream capture: the
@@ -786,15 +790,15 @@ void kernel_setup() {
   static std::once_flag once;
   std::call_once(once, [] {
     const int most = 227 * 1024;
-    cudaFuncSetAttribute(k_pbd<false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    cudaFuncSetAttribute(k_pbd<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    cudaFuncSetAttribute(k_pbd<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    cudaFuncSetAttribute(k_pbd<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    for (auto f : {k_pbd<false, 0, false>, k_pbd<true, 0, false>, k_pbd<false, 1, false>, k_pbd<true, 2, false>})
+      cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
   });
 }
 
 void launch_bin_scatter(const Plan& p, cudaStream_t s) {
-  k_bin_scatter<<<p.n_bead_items, kBeadChunk, 0, s>>>(p.d_worlds, p.d_bead_items);
+  // (data moves only: the single-world path cannot change a result)
+  if (p.n_worlds == 1) k_bin_scatter<true><<<p.n_bead_items, kBeadChunk, 0, s>>>(p.d_worlds, p.d_bead_items, p.h_world0);
+  else k_bin_scatter<false><<<p.n_bead_items, kBeadChunk, 0, s>>>(p.d_worlds, p.d_bead_items, p.h_world0);
 }
 
 void launch_layer_spread(const Plan& p, cudaStream_t s) {
@@ -804,8 +808,8 @@ void launch_layer_spread(const Plan& p, cudaStream_t s) {
 }
 
 void launch_interp_advance(const Plan& p, cudaStream_t s) {
-  if (p.any_ext) k_interp_advance<true><<<p.n_bead_items, kBeadChunk, 0, s>>>(p.d_worlds, p.d_bead_items);
-  else k_interp_advance<false><<<p.n_bead_items, kBeadChunk, 0, s>>>(p.d_worlds, p.d_bead_items);
+  auto kern = p.any_ext ? k_interp_advance<true, false> : k_interp_advance<false, false>;
+  kern<<<p.n_bead_items, kBeadChunk, 0, s>>>(p.d_worlds, p.d_bead_items, p.h_world0);
 }
 
 void launch_unstream_in(const float* f0dev, float* g_dst, int H, int W, cudaStream_t s) {

@@ -31,11 +31,13 @@ __device__ __forceinline__ int block_sum_256(int v, int* red) {
 // which left the counter behind) it advances the counter, and it clears the
 // next step's F_el-maximum slot (this step's, written by the PBD, stays
 // readable for the spread).
+template <bool kSingle>
 __global__ void __launch_bounds__(256) k_scan_sums(const WorldDev* __restrict__ worlds,
-                                                   const int2* __restrict__ items, int inc_t) {
+                                                   const int2* __restrict__ items, int inc_t,
+                                                   const __grid_constant__ WorldDev w1) {
   __shared__ int red[9];
-  const int2 it = items[blockIdx.x];
-  const WorldDev& w = worlds[it.x];
+  const int2 it = kSingle ? make_int2(0, (int)blockIdx.x) : items[blockIdx.x];
+  const WorldDev& w = kSingle ? w1 : worlds[it.x];
   if (it.y == 0 && threadIdx.x == 0) {
     const long long t = *w.t + inc_t;
     if (inc_t) *w.t = t;
@@ -49,12 +51,14 @@ __global__ void __launch_bounds__(256) k_scan_sums(const WorldDev* __restrict__ 
   if (threadIdx.x == 0) w.chunk_sum[it.y] = s;
 }
 
+template <bool kSingle>
 __global__ void __launch_bounds__(256) k_scan_apply(const WorldDev* __restrict__ worlds,
-                                                    const int2* __restrict__ items) {
+                                                    const int2* __restrict__ items,
+                                                    const __grid_constant__ WorldDev w1) {
   __shared__ int red[9];
   __shared__ int warp_tot[8];
-  const int2 it = items[blockIdx.x];
-  const WorldDev& w = worlds[it.x];
+  const int2 it = kSingle ? make_int2(0, (int)blockIdx.x) : items[blockIdx.x];
+  const WorldDev& w = kSingle ? w1 : worlds[it.x];
   int pre = 0;
   for (int k = threadIdx.x; k < it.y; k += blockDim.x) pre += w.chunk_sum[k];
   pre = block_sum_256(pre, red);
@@ -124,8 +128,13 @@ __global__ void __launch_bounds__(kCellChunk) k_lbm(const WorldDev* __restrict__
 // Launchers and the step sequence.
 // ---------------------------------------------------------------------------
 void launch_bin_scan(const Plan& p, cudaStream_t s, int inc_t) {
-  k_scan_sums<<<p.n_scan_items, 256, 0, s>>>(p.d_worlds, p.d_scan_items, inc_t);
-  k_scan_apply<<<p.n_scan_items, 256, 0, s>>>(p.d_worlds, p.d_scan_items);
+  if (p.n_worlds == 1) {   // integer work only: the single-world path cannot change a result
+    k_scan_sums<true><<<p.n_scan_items, 256, 0, s>>>(p.d_worlds, p.d_scan_items, inc_t, p.h_world0);
+    k_scan_apply<true><<<p.n_scan_items, 256, 0, s>>>(p.d_worlds, p.d_scan_items, p.h_world0);
+  } else {
+    k_scan_sums<false><<<p.n_scan_items, 256, 0, s>>>(p.d_worlds, p.d_scan_items, inc_t, p.h_world0);
+    k_scan_apply<false><<<p.n_scan_items, 256, 0, s>>>(p.d_worlds, p.d_scan_items, p.h_world0);
+  }
 }
 
 void launch_lbm(const Plan& p, cudaStream_t s, int layered_only) {

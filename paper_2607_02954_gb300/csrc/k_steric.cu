@@ -195,6 +195,13 @@ __device__ __forceinline__ T block_max(T v, T* red) {
   return m;
 }
 
+// The tile item of this block in a launch over the tiles of one world
+// (row-major, as the plan lists them).
+__device__ __forceinline__ int2 single_tile_item(const WorldDev& w) {
+  const unsigned ntx = (unsigned)w.ntx;
+  return make_int2(0, (int)(blockIdx.x % ntx) | ((int)(blockIdx.x / ntx) << 16));
+}
+
 // Taps of a world with half width wR laid out for half width R >= wR.
 template <int R>
 __device__ __forceinline__ float padded_tap(const WorldDev& w, int wR, int m) {
@@ -213,9 +220,10 @@ __device__ __forceinline__ float padded_tap(const WorldDev& w, int wR, int m) {
 // pass starts on a 16-byte boundary) or, when that would cover the axis
 // more than once, the whole axis (origin 0, oxe = 4, folded).
 // ---------------------------------------------------------------------------
-template <int R>
+template <int R, bool kSingle>
 __global__ void __launch_bounds__(kThreads, 8) k_deposit_x(const WorldDev* __restrict__ worlds,
-                                                        const int2* __restrict__ items, int store_fields) {
+                                                        const int2* __restrict__ items, int store_fields,
+                                                        const __grid_constant__ WorldDev w1) {
   using G = Geo<R>;
   __shared__ __align__(16) int acc[G::kDY * G::kDX];
   __shared__ __align__(16) float4 sp[kDepCap];
@@ -223,8 +231,8 @@ __global__ void __launch_bounds__(kThreads, 8) k_deposit_x(const WorldDev* __res
   __shared__ float tap_s[G::kTaps];
   __shared__ int s_start[kMaxSeg], s_pre[kMaxSeg + 1], s_maxc, s_cnt;
   __shared__ int red[kWarps];
-  const int2 it = items[blockIdx.x];
-  const WorldDev& w = worlds[it.x];
+  const int2 it = kSingle ? single_tile_item(w1) : items[blockIdx.x];
+  const WorldDev& w = kSingle ? w1 : worlds[it.x];
   const int W = w.W, H = w.H, wR = w.R, ntx = w.ntx, nty = w.nty;
   const float4* __restrict__ spos = w.spos;
   float* __restrict__ rho_x = w.rho_x;
@@ -746,12 +754,13 @@ __device__ __forceinline__ void tile_lbm(TileWork& wk, const WorldDev& w, const 
 // followed by k_lbm, without F's round trip through HBM).  The tile's
 // population rows are prefetched into L2 on entry, so their DRAM reads
 // overlap the force phase.
-template <int R>
+template <int R, bool kSingle>
 __global__ void __launch_bounds__(kThreads, 4) k_force_lbm(const WorldDev* __restrict__ worlds,
-                                                           const int2* __restrict__ items) {
+                                                           const int2* __restrict__ items,
+                                                           const __grid_constant__ WorldDev w1) {
   __shared__ __align__(16) ForceSmem<R> sm;
-  const int2 it = items[blockIdx.x];
-  const WorldDev& w = worlds[it.x];
+  const int2 it = kSingle ? single_tile_item(w1) : items[blockIdx.x];
+  const WorldDev& w = kSingle ? w1 : worlds[it.x];
   const TileBox tb = tile_box(w, it.y);
   const bool layered = w.layers == 2;
   if (!layered) prefetch_populations(w, tb);
@@ -869,11 +878,17 @@ namespace {
 template <int R>
 void launch_steric(const Plan& p, cudaStream_t s, int which, int store_fields, int after_step) {
   if (which == 0) {
-    k_deposit_x<R><<<p.n_tile_items, kThreads, 0, s>>>(p.d_worlds, p.d_tile_items, store_fields);
+    if (p.n_worlds == 1)
+      k_deposit_x<R, true><<<p.n_tile_items, kThreads, 0, s>>>(p.d_worlds, p.d_tile_items, store_fields, p.h_world0);
+    else
+      k_deposit_x<R, false><<<p.n_tile_items, kThreads, 0, s>>>(p.d_worlds, p.d_tile_items, store_fields, p.h_world0);
   } else if (which == 1) {
     k_force_spread<R><<<p.n_tile_items, kThreads, 0, s>>>(p.d_worlds, p.d_tile_items, store_fields, after_step);
   } else {
-    k_force_lbm<R><<<p.n_tile_items, kThreads, 0, s>>>(p.d_worlds, p.d_tile_items);
+    if (p.n_worlds == 1)
+      k_force_lbm<R, true><<<p.n_tile_items, kThreads, 0, s>>>(p.d_worlds, p.d_tile_items, p.h_world0);
+    else
+      k_force_lbm<R, false><<<p.n_tile_items, kThreads, 0, s>>>(p.d_worlds, p.d_tile_items, p.h_world0);
   }
 }
 

@@ -190,6 +190,7 @@ mc_status build_plan(mc_world* const* ws, int n, cudaStream_t s, Plan& out) {
   p.n_tile_items = (int)tile.size();
   p.n_cell_items = (int)cell.size();
   p.n_scan_items = (int)scan.size();
+  if (n == 1) p.h_world0 = table[0];
   out = p;
   return MC_OK;
 }

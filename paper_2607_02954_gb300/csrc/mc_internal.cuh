@@ -115,6 +115,11 @@ struct AdjDev {
 // A set of worlds advanced together, with the work items of each stage.
 struct Plan {
   int n_worlds = 0;
+  // A plan of one world also passes that world's descriptor to the step's
+  // kernels as a __grid_constant__ parameter: its fields come from the
+  // parameter space and each block's work item from its index, so a block
+  // starts without a dependent load of the item list and the world table.
+  WorldDev h_world0{};
   int max_B = 2;
   int max_R = 4;                 // largest Gaussian half width among the worlds
   bool any_layered = false;      // some world is a two-layer filament world
