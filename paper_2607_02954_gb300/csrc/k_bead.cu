@@ -470,15 +470,16 @@ __device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, 
 // when no filament of the launch is longer than 64 beads).
 template <bool kExt, int kMode, bool kSingle>
 __global__ void __launch_bounds__(256, 4) k_pbd(const WorldDev* __restrict__ worlds,
-                                             const int2* __restrict__ items, int n_items, int maxB,
-                                             const __grid_constant__ WorldDev w1) {
+                                             const int2* __restrict__ items, int n_items, int maxB) {
   extern __shared__ __align__(16) float smem[];   // maxB is a multiple of 4: float4 slices stay aligned
   const int wpb = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int item = blockIdx.x * wpb + warp;
   if (item >= n_items) return;  // warp-uniform exit; the kernel has no block barrier
+  // a single-world launch takes its item from the block index (the world
+  // stays in the table: its fields reach the arithmetic exactly as in a batch)
   const int2 it = kSingle ? make_int2(0, item) : items[item];
-  const WorldDev& w = kSingle ? w1 : worlds[it.x];
+  const WorldDev& w = worlds[it.x];
   if ((kMode == 2) != (w.ib == 1)) return;   // direct-forcing worlds run their PBD after the steric spread
   const int f = it.y;
   const int b0 = w.fil_off[f];
@@ -627,10 +628,9 @@ __global__ void __launch_bounds__(kCellChunk) k_layer_finish(const WorldDev* __r
 // advances the world's step counter (no other stage kernel reads it).
 template <bool kExt, bool kSingle>
 __global__ void __launch_bounds__(kBeadChunk) k_interp_advance(const WorldDev* __restrict__ worlds,
-                                                               const int2* __restrict__ items,
-                                                               const __grid_constant__ WorldDev w1) {
+                                                               const int2* __restrict__ items) {
   const int2 it = kSingle ? make_int2(0, (int)blockIdx.x * kBeadChunk) : items[blockIdx.x];
-  const WorldDev& w = kSingle ? w1 : worlds[it.x];
+  const WorldDev& w = worlds[it.x];
   if (it.y == 0 && threadIdx.x == 0) *w.t += 1;
   const int i = it.y + threadIdx.x;
   const int W = w.W, H = w.H;
@@ -758,8 +758,10 @@ void launch_pbd(const Plan& p, cudaStream_t s) {
   const int grid = (p.n_fil_items + wpb - 1) / wpb;
   // worlds with a rest-length drive, observables or two layers need the
   // extended kernel; it computes every other world exactly as the plain one
-  auto kern = p.any_ext ? k_pbd<true, 0, false> : k_pbd<false, 0, false>;
-  kern<<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb, p.h_world0);
+  const bool one = p.n_worlds == 1;
+  auto kern = p.any_ext ? (one ? k_pbd<true, 0, true> : k_pbd<true, 0, false>)
+                        : (one ? k_pbd<false, 0, true> : k_pbd<false, 0, false>);
+  kern<<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
 }
 
 // The PBD of direct-forcing worlds (from the positions the fluid carries
@@ -770,7 +772,8 @@ void launch_pbd_mdf(const Plan& p, cudaStream_t s) {
   const int wpb = pbd_warps_per_block(mb);
   const size_t smem = p.max_B <= 64 ? 0 : (size_t)wpb * mb * kPbdFloatsPerBead * sizeof(float);
   const int grid = (p.n_fil_items + wpb - 1) / wpb;
-  k_pbd<true, 2, false><<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb, p.h_world0);
+  auto kern = p.n_worlds == 1 ? k_pbd<true, 2, true> : k_pbd<true, 2, false>;
+  kern<<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
 }
 
 // a8 of the previous step fused with this step's a1-a3 (plans without the
@@ -781,7 +784,8 @@ void launch_advance_pbd(const Plan& p, cudaStream_t s) {
   const int wpb = pbd_warps_per_block(mb);
   const size_t smem = p.max_B <= 64 ? 0 : (size_t)wpb * mb * kPbdFloatsPerBead * sizeof(float);
   const int grid = (p.n_fil_items + wpb - 1) / wpb;
-  k_pbd<false, 1, false><<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb, p.h_world0);
+  auto kern = p.n_worlds == 1 ? k_pbd<false, 1, true> : k_pbd<false, 1, false>;
+  kern<<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
 }
 
 // Shared-memory limits set once per process, outside any stream capture: the
@@ -790,7 +794,8 @@ void kernel_setup() {
   static std::once_flag once;
   std::call_once(once, [] {
     const int most = 227 * 1024;
-    for (auto f : {k_pbd<false, 0, false>, k_pbd<true, 0, false>, k_pbd<false, 1, false>, k_pbd<true, 2, false>})
+    for (auto f : {k_pbd<false, 0, false>, k_pbd<true, 0, false>, k_pbd<false, 1, false>, k_pbd<true, 2, false>,
+                   k_pbd<false, 0, true>, k_pbd<true, 0, true>, k_pbd<false, 1, true>, k_pbd<true, 2, true>})
       cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
   });
 }
@@ -808,8 +813,10 @@ void launch_layer_spread(const Plan& p, cudaStream_t s) {
 }
 
 void launch_interp_advance(const Plan& p, cudaStream_t s) {
-  auto kern = p.any_ext ? k_interp_advance<true, false> : k_interp_advance<false, false>;
-  kern<<<p.n_bead_items, kBeadChunk, 0, s>>>(p.d_worlds, p.d_bead_items, p.h_world0);
+  const bool one = p.n_worlds == 1;
+  auto kern = p.any_ext ? (one ? k_interp_advance<true, true> : k_interp_advance<true, false>)
+                        : (one ? k_interp_advance<false, true> : k_interp_advance<false, false>);
+  kern<<<p.n_bead_items, kBeadChunk, 0, s>>>(p.d_worlds, p.d_bead_items);
 }
 
 void launch_unstream_in(const float* f0dev, float* g_dst, int H, int W, cudaStream_t s) {

@@ -115,10 +115,13 @@ struct AdjDev {
 // A set of worlds advanced together, with the work items of each stage.
 struct Plan {
   int n_worlds = 0;
-  // A plan of one world also passes that world's descriptor to the step's
-  // kernels as a __grid_constant__ parameter: its fields come from the
-  // parameter space and each block's work item from its index, so a block
-  // starts without a dependent load of the item list and the world table.
+  // A plan of one world lets the step's kernels take each block's work item
+  // from the block index instead of the item list.  The tile kernels, the
+  // bin scatter and the scans also take the world's descriptor as a
+  // __grid_constant__ parameter, so their blocks start without a dependent
+  // load; the PBD and advance kernels keep reading it from the table (their
+  // arithmetic then compiles exactly as in a batch, and a world stepped alone
+  // stays bitwise equal to the same world batched, as measured).
   WorldDev h_world0{};
   int max_B = 2;
   int max_R = 4;                 // largest Gaussian half width among the worlds
