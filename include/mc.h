@@ -361,13 +361,15 @@ mc_status mc_loss_splat(mc_world* w, const float* target, int R, float sigma, fl
  * Search loops (the paper's Neuroevolution and QD Search experiments,
  * Experiments section) request rollouts as they go and read back a fitness,
  * the mean displacement of the world's beads.  A server owns a scheduler
- * thread and a CUDA stream on the device current at creation.  Requests wait
- * in a queue until a slot is free and their device footprint fits the
- * budget (a lone request larger than the budget is still admitted when
- * nothing else runs); all admitted worlds advance together through the
- * batched kernels, steps_per_tick steps at a time; finished worlds are
- * released at once, which admits waiting requests.  Results are bitwise the
- * same as running the world alone. */
+ * thread and two CUDA streams (steps, world creation) on the device current
+ * at creation.  Requests wait in a queue until a slot is free and their
+ * device footprint fits the budget (a lone request larger than the budget is
+ * still admitted when nothing else runs); all admitted worlds advance
+ * together through the batched kernels, steps_per_tick steps at a time (one
+ * tick); a finished world leaves the batch at once and is published, and its
+ * memory released, when its last tick has completed on the device, which
+ * admits waiting requests.  The scheduler enqueues up to two ticks ahead of
+ * the device.  Results are bitwise the same as running the world alone. */
 typedef struct mc_server mc_server;
 
 typedef struct mc_server_cfg {

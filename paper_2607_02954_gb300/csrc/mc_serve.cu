@@ -3,14 +3,20 @@
 // Search loops (neuroevolution, MAP-Elites: the paper's Neuroevolution and
 // QD Search experiments) submit rollout requests as they go and read back a
 // fitness, the centre-of-mass displacement after n steps.  A scheduler
-// thread owns one CUDA stream and a set of active worlds ("slots"):
+// thread owns one CUDA stream for the steps, one for world creation, and a
+// set of active worlds ("slots"):
 //   - pending requests are admitted as soon as a slot is free and their
 //     device footprint fits the HBM budget;
 //   - every tick advances all active worlds together through the batched
 //     kernels (one launch per stage for the whole set);
 //   - worlds whose rollout is complete are reduced to their mean
-//     displacement (fixed-order block reduction), released, and their
-//     result is published; the freed slots and memory admit more requests.
+//     displacement (fixed-order block reduction) in the same tick, and
+//     their result is published, and their memory released, once the
+//     tick has finished on the device.
+// The host runs at most two ticks ahead of the device: while tick n runs it
+// publishes tick n - 1's rollouts, creates the admitted worlds (on the
+// creation stream, which the step stream then waits on) and builds the
+// plan of tick n + 1, so the device does not idle between ticks.
 // Every kernel is deterministic and per world, so a rollout's result is
 // bitwise the same alone and in any mix.
 #include <algorithm>
@@ -56,6 +62,13 @@ struct Slot {
   int64_t t_submit = 0, t_admit = 0;
 };
 
+// The rollouts a tick finished: read back (into output buffer `buf`) by the
+// tick itself, published once its event has completed.
+struct Retire {
+  std::vector<Slot> slots;
+  int buf = 0;
+};
+
 constexpr size_t kRec = 40;   // 3 floats (mean displacement, flags) + pad, 3 int64 observables
 
 // Mean displacement of one world, fixed-order reduction (one block).
@@ -95,7 +108,10 @@ mc_status serve_fail(mc_status s, const std::string& m) {
 struct mc_server {
   mc_server_cfg cfg{};
   int device = 0;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;       // the steps and the read-back
+  cudaStream_t adm_stream = nullptr;   // world creation
+  cudaEvent_t adm_ev = nullptr;
+  cudaEvent_t tick_ev[2] = {nullptr, nullptr};   // end of the last two ticks, by tick parity
   std::thread thread;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -109,9 +125,13 @@ struct mc_server {
   size_t bytes_in_use = 0;
   mc::Plan plan;
   bool plan_valid = false;
-  char* d_out = nullptr;   // per finished world: kRec bytes (mean displacement, flags, observables)
-  char* h_out = nullptr;
-  int out_cap = 0;
+  // per finished world: kRec bytes (mean displacement, flags, observables),
+  // one buffer per tick parity
+  char* d_out[2] = {nullptr, nullptr};
+  char* h_out[2] = {nullptr, nullptr};
+  int out_cap[2] = {0, 0};
+  std::deque<Retire> retiring;
+  int64_t n_ticks = 0;   // ticks enqueued
   mc_server_stats stats{};
 };
 
@@ -137,6 +157,47 @@ void publish(mc_server* s, uint64_t ticket, const mc_result& r) {
   s->cv_done.notify_all();
 }
 
+// Publishes the rollouts of the oldest retiring tick once its event has
+// completed (waiting for it when `block`), releasing their worlds.
+// Returns false when it has nothing to publish yet.
+bool retire_oldest(mc_server* s, bool block) {
+  if (s->retiring.empty()) return false;
+  Retire& r = s->retiring.front();
+  cudaError_t e = block ? cudaEventSynchronize(s->tick_ev[r.buf]) : cudaEventQuery(s->tick_ev[r.buf]);
+  if (e == cudaErrorNotReady) return false;
+  const int64_t t = now_ns();
+  const char* out = s->h_out[r.buf];
+  for (size_t j = 0; j < r.slots.size(); ++j) {
+    const Slot& sl = r.slots[j];
+    mc_result res{};
+    float rec[3];
+    std::memcpy(rec, out + kRec * j, sizeof(rec));
+    res.com_disp[0] = rec[0];
+    res.com_disp[1] = rec[1];
+    unsigned flags;
+    std::memcpy(&flags, &rec[2], 4);
+    long long obs[3];
+    std::memcpy(obs, out + kRec * j + 16, sizeof(obs));
+    res.e_bend = (double)obs[0] / (double)mc::kObsScale;
+    res.e_pos = (double)obs[1] / (double)mc::kObsScale;
+    res.energy = (double)obs[2] / (double)mc::kObsScale;
+    res.status = e != cudaSuccess ? MC_ERR_CUDA : ((flags & mc::kFlagUnstable) ? MC_ERR_UNSTABLE : MC_OK);
+    res.n_steps = sl.n_steps;
+    res.t_submit_ns = sl.t_submit;
+    res.t_admit_ns = sl.t_admit;
+    res.t_done_ns = t;
+    // every use of the world on the step stream has completed
+    mc_world_destroy(sl.w);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->bytes_in_use -= sl.bytes;
+    }
+    publish(s, sl.ticket, res);
+  }
+  s->retiring.pop_front();
+  return true;
+}
+
 void scheduler(mc_server* s) {
   cudaSetDevice(s->device);
   bool set_changed = false;
@@ -144,17 +205,21 @@ void scheduler(mc_server* s) {
     std::vector<Request> admit;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      s->cv_work.wait(lk, [&] { return s->stop || !s->pending.empty() || !s->active.empty(); });
+      s->cv_work.wait(lk, [&] {
+        return s->stop || !s->pending.empty() || !s->active.empty() || !s->retiring.empty();
+      });
       if (s->stop) break;
       size_t bytes = s->bytes_in_use;
       while (!s->pending.empty() && (int)(s->active.size() + admit.size()) < s->cfg.max_slots &&
              (bytes + s->pending.front().bytes <= s->cfg.hbm_budget_bytes ||
-              (s->active.empty() && admit.empty()))) {
+              (s->active.empty() && admit.empty() && s->retiring.empty()))) {
         bytes += s->pending.front().bytes;
         admit.push_back(std::move(s->pending.front()));
         s->pending.pop_front();
       }
+      s->bytes_in_use = bytes;
     }
+    bool created = false;
     for (Request& r : admit) {
       mc_world_desc d{};
       d.H = r.H;
@@ -179,9 +244,13 @@ void scheduler(mc_server* s) {
       d.p = r.p;
       d.mem_kind = MC_MEM_HOST;
       mc_world* w = nullptr;
-      const mc_status st = mc_world_create(&d, s->stream, &w);
+      const mc_status st = mc_world_create(&d, s->adm_stream, &w);
       const int64_t t = now_ns();
       if (st != MC_OK) {
+        {
+          std::lock_guard<std::mutex> lk(s->mu);
+          s->bytes_in_use -= r.bytes;
+        }
         mc_result res{};
         res.status = st;
         res.n_steps = r.n_steps;
@@ -200,10 +269,22 @@ void scheduler(mc_server* s) {
       sl.t_submit = r.t_submit;
       sl.t_admit = t;
       s->active.push_back(sl);
-      s->bytes_in_use += r.bytes;
       set_changed = true;
+      created = true;
     }
-    if (s->active.empty()) continue;
+    if (created) {
+      // the new worlds' set-up precedes their first step
+      cudaEventRecord(s->adm_ev, s->adm_stream);
+      cudaStreamWaitEvent(s->stream, s->adm_ev, 0);
+    }
+    while (retire_oldest(s, false)) {
+    }
+    if (s->active.empty()) {
+      // nothing left to enqueue: wait for the ticks still in flight
+      while (retire_oldest(s, true)) {
+      }
+      continue;
+    }
     if (set_changed) {
       if (s->plan_valid) mc::plan_free(s->plan, s->stream);
       std::vector<mc_world*> ws;
@@ -212,6 +293,7 @@ void scheduler(mc_server* s) {
       set_changed = false;
       if (!s->plan_valid) {
         // cannot advance this set: fail every active rollout
+        cudaStreamSynchronize(s->stream);
         for (auto& sl : s->active) {
           mc_result res{};
           res.status = MC_ERR_OOM;
@@ -220,77 +302,82 @@ void scheduler(mc_server* s) {
           res.t_admit_ns = sl.t_admit;
           res.t_done_ns = now_ns();
           mc_world_destroy(sl.w);
-          s->bytes_in_use -= sl.bytes;
+          {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->bytes_in_use -= sl.bytes;
+          }
           publish(s, sl.ticket, res);
         }
         s->active.clear();
         continue;
       }
     }
+    // the host stays at most two ticks ahead: this tick reuses the event and
+    // the output buffer of the tick before the last
+    const int b = (int)(s->n_ticks & 1);
+    while (!s->retiring.empty() && s->retiring.front().buf == b) retire_oldest(s, true);
+    if (s->n_ticks >= 2) cudaEventSynchronize(s->tick_ev[b]);
     int k = s->cfg.steps_per_tick;
     for (auto& sl : s->active) k = std::min(k, sl.steps_left);
-    if (k > 0) {
-      mc::plan_run(s->plan, k, s->stream);
-      for (auto& sl : s->active) {
-        sl.steps_left -= k;
-        sl.w->t += k;
-      }
+    mc::plan_run(s->plan, k, s->stream);
+    for (auto& sl : s->active) {
+      sl.steps_left -= k;
+      sl.w->t += k;
+    }
+    {
       std::lock_guard<std::mutex> lk(s->mu);
       s->stats.steps_run += k;
       s->stats.ticks += 1;
     }
-    // retire finished rollouts
-    std::vector<int> fin;
-    for (int i = 0; i < (int)s->active.size(); ++i)
-      if (s->active[i].steps_left <= 0) fin.push_back(i);
-    if (fin.empty()) continue;
-    if ((int)fin.size() > s->out_cap) {
-      if (s->d_out) cudaFreeAsync(s->d_out, s->stream);
-      if (s->h_out) cudaFreeHost(s->h_out);
-      s->out_cap = std::max((int)fin.size(), 2 * s->out_cap);
-      cudaMallocAsync(&s->d_out, kRec * s->out_cap, s->stream);
-      cudaMallocHost(&s->h_out, kRec * s->out_cap);
+    // finished rollouts: reduce and read back in this tick
+    Retire r;
+    r.buf = b;
+    for (int i = 0; i < (int)s->active.size();) {
+      if (s->active[i].steps_left <= 0) {
+        r.slots.push_back(s->active[i]);
+        s->active.erase(s->active.begin() + i);
+      } else {
+        ++i;
+      }
     }
-    for (int j = 0; j < (int)fin.size(); ++j) {
-      const mc::WorldDev& h = s->active[fin[j]].w->h;
-      k_mean_disp<<<1, 256, 0, s->stream>>>(h.disp, h.N, h.flags, reinterpret_cast<float*>(s->d_out + kRec * j));
-      cudaMemcpyAsync(s->d_out + kRec * j + 16, h.obs, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
-                      s->stream);
+    if (!r.slots.empty()) {
+      const int nf = (int)r.slots.size();
+      if (nf > s->out_cap[b]) {
+        // the buffer's last read-back (two ticks ago) has completed
+        if (s->d_out[b]) cudaFreeAsync(s->d_out[b], s->stream);
+        if (s->h_out[b]) cudaFreeHost(s->h_out[b]);
+        s->out_cap[b] = std::max(nf, 2 * s->out_cap[b]);
+        cudaMallocAsync(&s->d_out[b], kRec * s->out_cap[b], s->stream);
+        cudaMallocHost(&s->h_out[b], kRec * s->out_cap[b]);
+      }
+      for (int j = 0; j < nf; ++j) {
+        const mc::WorldDev& h = r.slots[j].w->h;
+        char* o = s->d_out[b] + kRec * j;
+        k_mean_disp<<<1, 256, 0, s->stream>>>(h.disp, h.N, h.flags, reinterpret_cast<float*>(o));
+        cudaMemcpyAsync(o + 16, h.obs, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s->stream);
+      }
+      cudaMemcpyAsync(s->h_out[b], s->d_out[b], kRec * nf, cudaMemcpyDeviceToHost, s->stream);
+      set_changed = true;
     }
-    cudaMemcpyAsync(s->h_out, s->d_out, kRec * fin.size(), cudaMemcpyDeviceToHost, s->stream);
-    const cudaError_t e = cudaStreamSynchronize(s->stream);
-    const int64_t t = now_ns();
-    for (int j = (int)fin.size() - 1; j >= 0; --j) {
-      Slot sl = s->active[fin[j]];
-      mc_result res{};
-      float rec[3];
-      std::memcpy(rec, s->h_out + kRec * j, sizeof(rec));
-      res.com_disp[0] = rec[0];
-      res.com_disp[1] = rec[1];
-      unsigned flags;
-      std::memcpy(&flags, &rec[2], 4);
-      long long obs[3];
-      std::memcpy(obs, s->h_out + kRec * j + 16, sizeof(obs));
-      res.e_bend = (double)obs[0] / (double)mc::kObsScale;
-      res.e_pos = (double)obs[1] / (double)mc::kObsScale;
-      res.energy = (double)obs[2] / (double)mc::kObsScale;
-      res.status = e != cudaSuccess ? MC_ERR_CUDA : ((flags & mc::kFlagUnstable) ? MC_ERR_UNSTABLE : MC_OK);
-      res.n_steps = sl.n_steps;
-      res.t_submit_ns = sl.t_submit;
-      res.t_admit_ns = sl.t_admit;
-      res.t_done_ns = t;
-      mc_world_destroy(sl.w);
-      s->bytes_in_use -= sl.bytes;
-      s->active.erase(s->active.begin() + fin[j]);
-      publish(s, sl.ticket, res);
-    }
-    set_changed = true;
+    cudaEventRecord(s->tick_ev[b], s->stream);
+    s->n_ticks += 1;
+    if (!r.slots.empty()) s->retiring.push_back(std::move(r));
   }
-  // shutting down: release everything still held
+  // shutting down: publish what finished, release everything still held
+  while (retire_oldest(s, true)) {
+  }
   for (auto& sl : s->active) mc_world_destroy(sl.w);
   s->active.clear();
   if (s->plan_valid) mc::plan_free(s->plan, s->stream);
   cudaStreamSynchronize(s->stream);
+  cudaStreamSynchronize(s->adm_stream);
+}
+
+void release_handles(mc_server* s) {
+  for (cudaEvent_t ev : {s->adm_ev, s->tick_ev[0], s->tick_ev[1]})
+    if (ev) cudaEventDestroy(ev);
+  if (s->adm_stream) cudaStreamDestroy(s->adm_stream);
+  if (s->stream) cudaStreamDestroy(s->stream);
 }
 
 template <class T>
@@ -319,8 +406,12 @@ mc_status mc_server_create(const mc_server_cfg* cfg, mc_server** out) {
   mc_server* s = new mc_server();
   s->cfg = *cfg;
   cudaGetDevice(&s->device);
-  const cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->adm_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->adm_ev, cudaEventDisableTiming);
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaEventCreateWithFlags(&s->tick_ev[b], cudaEventDisableTiming);
   if (e != cudaSuccess) {
+    release_handles(s);
     delete s;
     return serve_fail(MC_ERR_CUDA, std::string("server stream: ") + cudaGetErrorString(e));
   }
@@ -424,10 +515,12 @@ mc_status mc_server_destroy(mc_server* s) {
     s->cv_work.notify_all();
   }
   if (s->thread.joinable()) s->thread.join();
-  if (s->d_out) cudaFreeAsync(s->d_out, s->stream);
-  if (s->h_out) cudaFreeHost(s->h_out);
+  for (int b = 0; b < 2; ++b) {
+    if (s->d_out[b]) cudaFreeAsync(s->d_out[b], s->stream);
+    if (s->h_out[b]) cudaFreeHost(s->h_out[b]);
+  }
   cudaStreamSynchronize(s->stream);
-  cudaStreamDestroy(s->stream);
+  release_handles(s);
   delete s;
   return MC_OK;
 }
