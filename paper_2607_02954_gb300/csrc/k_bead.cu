@@ -84,6 +84,96 @@ __device__ __forceinline__ float2 interp_u(const WorldDev& w, const float4 p) {
   return make_float2(Ux, Uy);
 }
 
+// ---------------------------------------------------------------------------
+// Two-layer filament (Fluid-filament Interaction): the immersed-boundary
+// points of bead i are X_i +- delta n_i.
+// ---------------------------------------------------------------------------
+// Cell and fraction of the point X + d n for X = (cell, fraction) in p.
+__device__ __forceinline__ void layer_cell(const float4 p, float2 n, float d, int W, int H, int& cx, int& cy,
+                                           float& fx, float& fy) {
+  fx = p.x + d * n.x;
+  fy = p.y + d * n.y;
+  const float kx = floorf(fx), ky = floorf(fy);
+  fx -= kx;
+  fy -= ky;
+  cx = cell_x(p) + (int)kx;
+  cy = cell_y(p) + (int)ky;
+  if (fx >= 1.0f) { fx = 0.0f; cx += 1; }
+  if (fy >= 1.0f) { fy = 0.0f; cy += 1; }
+  cx = wrap_once(cx, W);   // |d| <= 2 keeps the offset within one period (W, H >= 8)
+  cy = wrap_once(cy, H);
+}
+
+__device__ __forceinline__ float2 layer_velocity(const WorldDev& w, const float4 p, float2 n, float d) {
+  int cx, cy;
+  float fx, fy;
+  layer_cell(p, n, d, w.W, w.H, cx, cy, fx, fy);
+  float wx[4], wy[4];
+  peskin4(fx, wx);
+  peskin4(fy, wy);
+  float Ux = 0.0f, Uy = 0.0f;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const float2* row = w.u + (size_t)wrap_once(cy - 1 + b, w.H) * w.W;
+    float rx = 0.0f, ry = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const float2 v = row[wrap_once(cx - 1 + a, w.W)];
+      rx = fmaf(wx[a], v.x, rx);
+      ry = fmaf(wx[a], v.y, ry);
+    }
+    Ux = fmaf(wy[b], rx, Ux);
+    Uy = fmaf(wy[b], ry, Uy);
+  }
+  return make_float2(Ux, Uy);
+}
+
+constexpr double kLayerScale = 1099511627776.0;   // 2^40: fixed point of the layer spread
+
+// The energy field sampled at p with the interpolation kernel.
+__device__ __forceinline__ float energy_sample(const WorldDev& w, const float4 q) {
+  const int W = w.W, H = w.H;
+  float ex[4], ey[4];
+  peskin4(q.x, ex);
+  peskin4(q.y, ey);
+  const int qx = cell_x(q), qy = cell_y(q);
+  float e = 0.0f;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const float* row = w.energy + (size_t)wrap_once(qy - 1 + b, H) * W;
+    float r = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) r = fmaf(ex[a], row[wrap_once(qx - 1 + a, W)], r);
+    e = fmaf(ey[b], r, e);
+  }
+  return e;
+}
+
+// a8's velocity of bead i at p = X^n: the interpolated fluid velocity, or,
+// for a two-layer filament, the mean of the velocities at X +- delta n.
+// With observables and an energy field (kExt), also the bead's energy
+// sample at X^n, stored in ebead and added to q in fixed point.
+// The energy bead i collects at p (observables with an energy field): stored
+// in ebead and added to q in fixed point.
+__device__ __forceinline__ void bead_energy(const WorldDev& w, int i, const float4 p, long long& q) {
+  if (w.observe && w.energy) {
+    const float e = energy_sample(w, p);
+    w.ebead[i] = e;
+    q += obs_q(e);
+  }
+}
+
+template <bool kExt>
+__device__ __forceinline__ float2 bead_velocity(const WorldDev& w, int i, const float4 p, long long& q) {
+  if (kExt) bead_energy(w, i, p, q);
+  if (kExt && w.layers == 2) {
+    const float2 n = w.nrm[i];
+    const float2 Up = layer_velocity(w, p, n, w.layer_half), Um = layer_velocity(w, p, n, -w.layer_half);
+    return make_float2(0.5f * (Up.x + Um.x), 0.5f * (Up.y + Um.y));
+  }
+  return interp_u(w, p);
+}
+
 __device__ __forceinline__ float sq(float v) { return v * v; }
 
 // Constants of the PBD passes, read once per warp.
@@ -201,14 +291,16 @@ __device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, 
   float4 P1 = hb1 ? w.pos[b0 + i1] : z4;
   if (kMode == 1) {
     // a8 of the previous step for the lane's beads, then this step's PBD from X^n
+    long long q = 0;
     if (hb0) {
-      const float2 U = interp_u(w, P0);
+      const float2 U = bead_velocity<kExt>(w, b0 + i0, P0, q);
       P0 = advance_tail(w, b0 + i0, P0, U.x, U.y);
     }
     if (hb1) {
-      const float2 U = interp_u(w, P1);
+      const float2 U = bead_velocity<kExt>(w, b0 + i1, P1, q);
       P1 = advance_tail(w, b0 + i1, P1, U.x, U.y);
     }
+    if (kExt && w.observe && w.energy) obs_add_warp(&w.obs[2], q);
   } else if (kMode == 2) {
     // direct forcing: the fluid (u* in u) carries the beads, PBD starts there
     if (hb0) {
@@ -322,8 +414,8 @@ __device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, 
       if (he0) ep += sq(rest_length(w, e0 + i0, t - 1) - L0);
       if (he1) ep += sq(rest_length(w, e0 + i1, t - 1) - L1);
     }
-    obs_add_warp(&w.obs[0], eb);
-    obs_add_warp(&w.obs[1], ep);
+    obs_add_warp(&w.obs[0], obs_q(eb));
+    obs_add_warp(&w.obs[1], obs_q(ep));
   }
   return fmax;
 }
@@ -352,11 +444,13 @@ __device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, 
   // stage the filament's inputs in shared memory, every copy in flight at once
   if (kMode == 1) {
     // a8 of the previous step, the advanced positions staged directly
+    long long q = 0;
     for (int i = lane; i < B; i += 32) {
       const float4 p = w.pos[b0 + i];
-      const float2 U = interp_u(w, p);
+      const float2 U = bead_velocity<kExt>(w, b0 + i, p, q);
       P[i] = advance_tail(w, b0 + i, p, U.x, U.y);
     }
+    if (kExt && w.observe && w.energy) obs_add_warp(&w.obs[2], q);
   } else if (kMode == 2) {
     // direct forcing: the positions the fluid (u* in u) carries the beads to
     for (int i = lane; i < B; i += 32) {
@@ -456,8 +550,8 @@ __device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, 
     for (int j = lane; j < nJ; j += 32) eb += sq(drive_angle(D[j], t - 1) - thr[j]);
     if (w.ldrive)
       for (int e = lane; e < nE; e += 32) ep += sq(drive_length(w.ldrive[e0 + e], t - 1) - Lr[e]);
-    obs_add_warp(&w.obs[0], eb);
-    obs_add_warp(&w.obs[1], ep);
+    obs_add_warp(&w.obs[0], obs_q(eb));
+    obs_add_warp(&w.obs[1], obs_q(ep));
   }
   return fmax;
 }
@@ -525,52 +619,6 @@ __global__ void __launch_bounds__(kBeadChunk) k_bin_scatter(const WorldDev* __re
   }
 }
 
-// ---------------------------------------------------------------------------
-// Two-layer filament (Fluid-filament Interaction): the immersed-boundary
-// points of bead i are X_i +- delta n_i.
-// ---------------------------------------------------------------------------
-// Cell and fraction of the point X + d n for X = (cell, fraction) in p.
-__device__ __forceinline__ void layer_cell(const float4 p, float2 n, float d, int W, int H, int& cx, int& cy,
-                                           float& fx, float& fy) {
-  fx = p.x + d * n.x;
-  fy = p.y + d * n.y;
-  const float kx = floorf(fx), ky = floorf(fy);
-  fx -= kx;
-  fy -= ky;
-  cx = cell_x(p) + (int)kx;
-  cy = cell_y(p) + (int)ky;
-  if (fx >= 1.0f) { fx = 0.0f; cx += 1; }
-  if (fy >= 1.0f) { fy = 0.0f; cy += 1; }
-  cx = wrap_once(cx, W);   // |d| <= 2 keeps the offset within one period (W, H >= 8)
-  cy = wrap_once(cy, H);
-}
-
-__device__ __forceinline__ float2 layer_velocity(const WorldDev& w, const float4 p, float2 n, float d) {
-  int cx, cy;
-  float fx, fy;
-  layer_cell(p, n, d, w.W, w.H, cx, cy, fx, fy);
-  float wx[4], wy[4];
-  peskin4(fx, wx);
-  peskin4(fy, wy);
-  float Ux = 0.0f, Uy = 0.0f;
-#pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    const float2* row = w.u + (size_t)wrap_once(cy - 1 + b, w.H) * w.W;
-    float rx = 0.0f, ry = 0.0f;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const float2 v = row[wrap_once(cx - 1 + a, w.W)];
-      rx = fmaf(wx[a], v.x, rx);
-      ry = fmaf(wx[a], v.y, ry);
-    }
-    Ux = fmaf(wy[b], rx, Ux);
-    Uy = fmaf(wy[b], ry, Uy);
-  }
-  return make_float2(Ux, Uy);
-}
-
-constexpr double kLayerScale = 1099511627776.0;   // 2^40: fixed point of the layer spread
-
 // Spread of half of F_el + F_s at each layer point of every bead of
 // two-layer worlds, in 64-bit fixed point (bitwise independent of order).
 // Beads are read through the step's binned records, so the positions are
@@ -633,43 +681,23 @@ __global__ void __launch_bounds__(kBeadChunk) k_interp_advance(const WorldDev* _
   const WorldDev& w = worlds[it.x];
   if (it.y == 0 && threadIdx.x == 0) *w.t += 1;
   const int i = it.y + threadIdx.x;
-  const int W = w.W, H = w.H;
-  if (kExt && w.observe && w.energy) {
-    // the energy field at the bead's position at the start of the step,
-    // with the interpolation kernel; its warp sum is the energy collected
-    // (every lane of the block takes part in the warp sums)
-    float e = 0.0f;
-    if (i < w.N) {
-      const float4 q = w.pos[i];
-      float ex[4], ey[4];
-      peskin4(q.x, ex);
-      peskin4(q.y, ey);
-      const int qx = cell_x(q), qy = cell_y(q);
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const float* row = w.energy + (size_t)wrap_once(qy - 1 + b, H) * W;
-        float r = 0.0f;
-#pragma unroll
-        for (int a = 0; a < 4; ++a) r = fmaf(ex[a], row[wrap_once(qx - 1 + a, W)], r);
-        e = fmaf(ey[b], r, e);
-      }
-      w.ebead[i] = e;
+  // the velocity at the bead's position at the start of the step (and, with
+  // observables, the energy sampled there; every lane of the block takes
+  // part in the warp sum)
+  long long q = 0;
+  float4 p = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  float2 U = make_float2(0.0f, 0.0f);
+  if (i < w.N) {
+    p = w.pos[i];
+    if (kExt && w.ib == 1) {
+      U = w.ubead[i];   // direct forcing: the bead's own velocity U_s
+      bead_energy(w, i, p, q);
+    } else {
+      U = bead_velocity<kExt>(w, i, p, q);
     }
-    obs_add_warp(&w.obs[2], e);
   }
+  if (kExt && w.observe && w.energy) obs_add_warp(&w.obs[2], q);
   if (i >= w.N) return;
-  const float4 p = w.pos[i];
-  float2 U;
-  if (kExt && w.ib == 1) {
-    U = w.ubead[i];   // direct forcing: the bead's own velocity U_s
-  } else if (kExt && w.layers == 2) {
-    // two-layer filament: mean of the velocities at X +- delta n
-    const float2 n = w.nrm[i];
-    const float2 Up = layer_velocity(w, p, n, w.layer_half), Um = layer_velocity(w, p, n, -w.layer_half);
-    U = make_float2(0.5f * (Up.x + Um.x), 0.5f * (Up.y + Um.y));
-  } else {
-    U = interp_u(w, p);
-  }
   advance_tail(w, i, p, U.x, U.y);
 }
 
@@ -776,15 +804,17 @@ void launch_pbd_mdf(const Plan& p, cudaStream_t s) {
   kern<<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
 }
 
-// a8 of the previous step fused with this step's a1-a3 (plans without the
-// extended features): the counter is advanced by this step's scan.
+// a8 of the previous step fused with this step's a1-a3 (plans without
+// direct-forcing worlds): the counter is advanced by this step's scan.
 void launch_advance_pbd(const Plan& p, cudaStream_t s) {
   if (p.n_fil_items == 0) return;
   const int mb = (p.max_B + 3) & ~3;
   const int wpb = pbd_warps_per_block(mb);
   const size_t smem = p.max_B <= 64 ? 0 : (size_t)wpb * mb * kPbdFloatsPerBead * sizeof(float);
   const int grid = (p.n_fil_items + wpb - 1) / wpb;
-  auto kern = p.n_worlds == 1 ? k_pbd<false, 1, true> : k_pbd<false, 1, false>;
+  const bool one = p.n_worlds == 1;
+  auto kern = p.any_ext ? (one ? k_pbd<true, 1, true> : k_pbd<true, 1, false>)
+                        : (one ? k_pbd<false, 1, true> : k_pbd<false, 1, false>);
   kern<<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
 }
 
@@ -794,8 +824,9 @@ void kernel_setup() {
   static std::once_flag once;
   std::call_once(once, [] {
     const int most = 227 * 1024;
-    for (auto f : {k_pbd<false, 0, false>, k_pbd<true, 0, false>, k_pbd<false, 1, false>, k_pbd<true, 2, false>,
-                   k_pbd<false, 0, true>, k_pbd<true, 0, true>, k_pbd<false, 1, true>, k_pbd<true, 2, true>})
+    for (auto f : {k_pbd<false, 0, false>, k_pbd<true, 0, false>, k_pbd<false, 1, false>, k_pbd<true, 1, false>,
+                   k_pbd<true, 2, false>, k_pbd<false, 0, true>, k_pbd<true, 0, true>, k_pbd<false, 1, true>,
+                   k_pbd<true, 1, true>, k_pbd<true, 2, true>})
       cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
   });
 }

@@ -141,11 +141,11 @@ void launch_lbm(const Plan& p, cudaStream_t s, int layered_only) {
   if (p.n_cell_items) k_lbm<<<p.n_cell_items, kCellChunk, 0, s>>>(p.d_worlds, p.d_cell_items, layered_only);
 }
 
-// n steps; in plans without the extended features every step after the
+// n steps; in plans without direct-forcing worlds every step after the
 // first runs its PBD fused with the previous step's advance (the same
 // arithmetic, one kernel and one position round trip fewer).
 void enqueue_steps(const Plan& p, int n, cudaStream_t s) {
-  if (p.any_ext || n < 2) {
+  if (p.any_mdf || n < 2) {
     for (int k = 0; k < n; ++k) enqueue_step(p, s);
     return;
   }

@@ -253,6 +253,20 @@ __global__ void __launch_bounds__(kThreads, 8) k_deposit_x(const WorldDev* __res
   if (tid == 0) s_cnt = 0;
   __syncthreads();
   const int total = s_pre[kMaxSeg];
+  if (total == 0) {
+    // no bead reaches the region: rho_s, rho_x and the tile maximum are zero
+    // (what the passes below give for an empty accumulator, bitwise)
+    // (tw is a multiple of 8, so each 4-column strip is whole and aligned)
+    const int ly = tid >> 3, s = tid & 7;
+    if (ly < th && 4 * s < tw) {
+      const size_t c = (size_t)(y0 + ly) * W + x0 + 4 * s;
+      const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      *reinterpret_cast<float4*>(rho_x + c) = z;
+      if (store_fields) *reinterpret_cast<float4*>(rho_s_out + c) = z;
+    }
+    if (tid == 0) tile_max[tile] = 0.0f;
+    return;
+  }
   // a cell's 4x4 stencil neighbourhood overlaps at most 2x2 bins and each
   // bead adds at most 1/4: the cell sum is below the largest bin count
   const int k = fix_exponent((float)s_maxc + 1.0f);
@@ -539,8 +553,9 @@ __device__ __forceinline__ int tile_compute(TileIn<R>& in, TileWork& wk, const W
   const float scale = pow2f(k);
   // list the first chunk's beads that reach the tile, then the y pass
   force_compact(in, wk, n0, tb, W, H, ntx, nty);
-  {
-    // y pass, 8 window rows per thread
+  if (total > 0 || store_fields) {
+    // y pass, 8 window rows per thread (only the beads' gradients and the
+    // rho_bar field read it)
     float tp[G::kTaps];
 #pragma unroll
     for (int m = 0; m < G::kTaps; ++m) tp[m] = in.tap_s[m];

@@ -221,7 +221,7 @@ mc_status run_steps(Plan& p, int n, cudaStream_t s) {
       n -= p.graph_steps;
     }
   }
-  for (int k = 0; k < n; ++k) mc::enqueue_step(p, s);
+  if (n > 0) mc::enqueue_steps(p, n, s);
   MC_CUDA(cudaGetLastError());
   return MC_OK;
 }

@@ -343,11 +343,15 @@ __device__ __forceinline__ float rest_length(const WorldDev& w, int e, long long
   return w.ldrive ? drive_length(w.ldrive[e], t) : w.L_rest[e];
 }
 
-// Adds a warp's sum of v (lanes in a fixed xor tree, so the same lanes and
-// values give the same bits) to a fixed-point observable.  Every lane calls.
-__device__ __forceinline__ void obs_add_warp(unsigned long long* acc, float v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0 && v != 0.0f) atomicAdd(acc, (unsigned long long)__float2ll_rn(v * kObsScale));
+// A contribution to an observable in its fixed point (2^-24 resolution).
+__device__ __forceinline__ long long obs_q(float v) { return __float2ll_rn(v * kObsScale); }
+
+// Adds a warp's sum of fixed-point contributions to an observable.  Integer
+// sums are exact, so the total does not depend on how contributions are
+// grouped into lanes, warps or launches.  Every lane calls.
+__device__ __forceinline__ void obs_add_warp(unsigned long long* acc, long long q) {
+  for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+  if ((threadIdx.x & 31) == 0 && q != 0) atomicAdd(acc, (unsigned long long)q);
 }
 
 __device__ __forceinline__ int cell_x(const float4& p) { return __float_as_int(p.z); }

@@ -2,8 +2,9 @@
 E_pos of Eqs. 5-6 and the energy collected from the energy field), with a
 rest-length drive and an energy field.
 
-Tolerance: 1e-5 of the oracle's value plus the fixed-point quantum, 2^-25
-per warp and step (each warp's per-step partial sum is rounded to 2^-24).
+Tolerance: 1e-5 of the oracle's value plus half the fixed-point quantum,
+2^-25, per rounded term (each bead's energy sample, and each lane's
+per-step partial sum of joints or edges, is rounded to 2^-24).
 """
 import numpy as np
 import pytest
@@ -31,9 +32,9 @@ def _spec(seed, side=96, n_fil=10, **kw):
 
 
 def _terms(spec, n_steps):
-    """Upper bound on the number of warp partial sums per observable."""
-    warps = max(spec.n_fil, 1) + (spec.N + 31) // 32 + spec.N // 256 + 1
-    return warps * n_steps
+    """Upper bound on the number of rounded terms per observable: one per
+    bead (energy) or one per lane of a filament's warp (E_bend, E_pos)."""
+    return (spec.N + 32 * max(spec.n_fil, 1)) * n_steps
 
 
 @pytest.mark.parametrize("seed,lengths", [(21, None), (22, [300, 40, 12])])
