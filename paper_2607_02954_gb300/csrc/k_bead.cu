@@ -565,6 +565,8 @@ __device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, 
 template <bool kExt, int kMode, bool kSingle>
 __global__ void __launch_bounds__(256, 4) k_pbd(const WorldDev* __restrict__ worlds,
                                              const int2* __restrict__ items, int n_items, int maxB) {
+  pdl_trigger();
+  pdl_wait();
   extern __shared__ __align__(16) float smem[];   // maxB is a multiple of 4: float4 slices stay aligned
   const int wpb = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -599,6 +601,8 @@ template <bool kSingle>
 __global__ void __launch_bounds__(kBeadChunk) k_bin_scatter(const WorldDev* __restrict__ worlds,
                                                             const int2* __restrict__ items,
                                                             const __grid_constant__ WorldDev w1) {
+  pdl_trigger();
+  pdl_wait();
   const int2 it = kSingle ? make_int2(0, (int)blockIdx.x * kBeadChunk) : items[blockIdx.x];
   const WorldDev& w = kSingle ? w1 : worlds[it.x];
   const int i = it.y + threadIdx.x;
@@ -625,6 +629,8 @@ __global__ void __launch_bounds__(kBeadChunk) k_bin_scatter(const WorldDev* __re
 // those at the start of the step even when the spread is re-run later.
 __global__ void __launch_bounds__(kBeadChunk) k_layer_spread(const WorldDev* __restrict__ worlds,
                                                              const int2* __restrict__ items) {
+  pdl_trigger();
+  pdl_wait();
   const int2 it = items[blockIdx.x];
   const WorldDev& w = worlds[it.x];
   if (w.layers != 2) return;
@@ -659,6 +665,8 @@ __global__ void __launch_bounds__(kBeadChunk) k_layer_spread(const WorldDev* __r
 // F = the layer spread, and the accumulator cleared for the next step.
 __global__ void __launch_bounds__(kCellChunk) k_layer_finish(const WorldDev* __restrict__ worlds,
                                                              const int2* __restrict__ items) {
+  pdl_trigger();
+  pdl_wait();
   const int2 it = items[blockIdx.x];
   const WorldDev& w = worlds[it.x];
   if (w.layers != 2) return;
@@ -677,6 +685,8 @@ __global__ void __launch_bounds__(kCellChunk) k_layer_finish(const WorldDev* __r
 template <bool kExt, bool kSingle>
 __global__ void __launch_bounds__(kBeadChunk) k_interp_advance(const WorldDev* __restrict__ worlds,
                                                                const int2* __restrict__ items) {
+  pdl_trigger();
+  pdl_wait();
   const int2 it = kSingle ? make_int2(0, (int)blockIdx.x * kBeadChunk) : items[blockIdx.x];
   const WorldDev& w = worlds[it.x];
   if (it.y == 0 && threadIdx.x == 0) *w.t += 1;
@@ -711,6 +721,8 @@ __constant__ int kCy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 // pre-collision populations f0, store g_i(c) = f0_i(c + c_i) so that pulling
 // g_i(c - c_i) returns f0_i(c).
 __global__ void k_unstream_in(const float* __restrict__ f0, float* __restrict__ g, int H, int W) {
+  pdl_trigger();
+  pdl_wait();
   const int HW = H * W;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= 9 * HW) return;
@@ -721,6 +733,8 @@ __global__ void k_unstream_in(const float* __restrict__ f0, float* __restrict__ 
 }
 
 __global__ void k_stream_out(const float* __restrict__ g, float* __restrict__ out, int H, int W) {
+  pdl_trigger();
+  pdl_wait();
   const int HW = H * W;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= 9 * HW) return;
@@ -737,6 +751,8 @@ __global__ void k_stream_out(const float* __restrict__ g, float* __restrict__ ou
 __global__ void k_world_init(WorldDev h, const float* x, const float* y, const float* t0, const float* amp,
                              const float* frq, const float* phs, const float* la, const float* lf,
                              const float* lp) {
+  pdl_trigger();
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < h.N) {
     const double xd = fmod((double)x[i], (double)h.W), yd = fmod((double)y[i], (double)h.H);
@@ -752,6 +768,8 @@ __global__ void k_world_init(WorldDev h, const float* x, const float* y, const f
 }
 
 __global__ void k_positions_out(const float4* __restrict__ pos, int N, float* x, float* y) {
+  pdl_trigger();
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const float4 p = pos[i];
@@ -760,6 +778,8 @@ __global__ void k_positions_out(const float4* __restrict__ pos, int N, float* x,
 }
 
 __global__ void k_cells_out(const float4* __restrict__ pos, int N, int W, int* cell) {
+  pdl_trigger();
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const float4 p = pos[i];
@@ -789,7 +809,7 @@ void launch_pbd(const Plan& p, cudaStream_t s) {
   const bool one = p.n_worlds == 1;
   auto kern = p.any_ext ? (one ? k_pbd<true, 0, true> : k_pbd<true, 0, false>)
                         : (one ? k_pbd<false, 0, true> : k_pbd<false, 0, false>);
-  kern<<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
+  launch_pdl(kern, grid, wpb * 32, smem, s, p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
 }
 
 // The PBD of direct-forcing worlds (from the positions the fluid carries
@@ -801,7 +821,7 @@ void launch_pbd_mdf(const Plan& p, cudaStream_t s) {
   const size_t smem = p.max_B <= 64 ? 0 : (size_t)wpb * mb * kPbdFloatsPerBead * sizeof(float);
   const int grid = (p.n_fil_items + wpb - 1) / wpb;
   auto kern = p.n_worlds == 1 ? k_pbd<true, 2, true> : k_pbd<true, 2, false>;
-  kern<<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
+  launch_pdl(kern, grid, wpb * 32, smem, s, p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
 }
 
 // a8 of the previous step fused with this step's a1-a3 (plans without
@@ -815,7 +835,7 @@ void launch_advance_pbd(const Plan& p, cudaStream_t s) {
   const bool one = p.n_worlds == 1;
   auto kern = p.any_ext ? (one ? k_pbd<true, 1, true> : k_pbd<true, 1, false>)
                         : (one ? k_pbd<false, 1, true> : k_pbd<false, 1, false>);
-  kern<<<grid, wpb * 32, smem, s>>>(p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
+  launch_pdl(kern, grid, wpb * 32, smem, s, p.d_worlds, p.d_fil_items, p.n_fil_items, mb);
 }
 
 // Shared-memory limits set once per process, outside any stream capture: the
@@ -833,8 +853,8 @@ void kernel_setup() {
 
 void launch_bin_scatter(const Plan& p, cudaStream_t s) {
   // (data moves only: the single-world path cannot change a result)
-  if (p.n_worlds == 1) k_bin_scatter<true><<<p.n_bead_items, kBeadChunk, 0, s>>>(p.d_worlds, p.d_bead_items, p.h_world0);
-  else k_bin_scatter<false><<<p.n_bead_items, kBeadChunk, 0, s>>>(p.d_worlds, p.d_bead_items, p.h_world0);
+  if (p.n_worlds == 1) launch_pdl(k_bin_scatter<true>, p.n_bead_items, kBeadChunk, 0, s, p.d_worlds, p.d_bead_items, p.h_world0);
+  else launch_pdl(k_bin_scatter<false>, p.n_bead_items, kBeadChunk, 0, s, p.d_worlds, p.d_bead_items, p.h_world0);
 }
 
 void launch_layer_spread(const Plan& p, cudaStream_t s) {
@@ -847,7 +867,7 @@ void launch_interp_advance(const Plan& p, cudaStream_t s) {
   const bool one = p.n_worlds == 1;
   auto kern = p.any_ext ? (one ? k_interp_advance<true, true> : k_interp_advance<true, false>)
                         : (one ? k_interp_advance<false, true> : k_interp_advance<false, false>);
-  kern<<<p.n_bead_items, kBeadChunk, 0, s>>>(p.d_worlds, p.d_bead_items);
+  launch_pdl(kern, p.n_bead_items, kBeadChunk, 0, s, p.d_worlds, p.d_bead_items);
 }
 
 void launch_unstream_in(const float* f0dev, float* g_dst, int H, int W, cudaStream_t s) {

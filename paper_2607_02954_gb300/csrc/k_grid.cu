@@ -35,6 +35,8 @@ template <bool kSingle>
 __global__ void __launch_bounds__(256) k_scan_sums(const WorldDev* __restrict__ worlds,
                                                    const int2* __restrict__ items, int inc_t,
                                                    const __grid_constant__ WorldDev w1) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ int red[9];
   const int2 it = kSingle ? make_int2(0, (int)blockIdx.x) : items[blockIdx.x];
   const WorldDev& w = kSingle ? w1 : worlds[it.x];
@@ -55,6 +57,8 @@ template <bool kSingle>
 __global__ void __launch_bounds__(256) k_scan_apply(const WorldDev* __restrict__ worlds,
                                                     const int2* __restrict__ items,
                                                     const __grid_constant__ WorldDev w1) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ int red[9];
   __shared__ int warp_tot[8];
   const int2 it = kSingle ? make_int2(0, (int)blockIdx.x) : items[blockIdx.x];
@@ -110,6 +114,8 @@ __global__ void __launch_bounds__(256) k_scan_apply(const WorldDev* __restrict__
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kCellChunk) k_lbm(const WorldDev* __restrict__ worlds,
                                                     const int2* __restrict__ items, int layered_only) {
+  pdl_trigger();
+  pdl_wait();
   const int2 it = items[blockIdx.x];
   const WorldDev& w = worlds[it.x];
   if (layered_only && w.layers != 2) return;
@@ -129,11 +135,11 @@ __global__ void __launch_bounds__(kCellChunk) k_lbm(const WorldDev* __restrict__
 // ---------------------------------------------------------------------------
 void launch_bin_scan(const Plan& p, cudaStream_t s, int inc_t) {
   if (p.n_worlds == 1) {   // integer work only: the single-world path cannot change a result
-    k_scan_sums<true><<<p.n_scan_items, 256, 0, s>>>(p.d_worlds, p.d_scan_items, inc_t, p.h_world0);
-    k_scan_apply<true><<<p.n_scan_items, 256, 0, s>>>(p.d_worlds, p.d_scan_items, p.h_world0);
+    launch_pdl(k_scan_sums<true>, p.n_scan_items, 256, 0, s, p.d_worlds, p.d_scan_items, inc_t, p.h_world0);
+    launch_pdl(k_scan_apply<true>, p.n_scan_items, 256, 0, s, p.d_worlds, p.d_scan_items, p.h_world0);
   } else {
-    k_scan_sums<false><<<p.n_scan_items, 256, 0, s>>>(p.d_worlds, p.d_scan_items, inc_t, p.h_world0);
-    k_scan_apply<false><<<p.n_scan_items, 256, 0, s>>>(p.d_worlds, p.d_scan_items, p.h_world0);
+    launch_pdl(k_scan_sums<false>, p.n_scan_items, 256, 0, s, p.d_worlds, p.d_scan_items, inc_t, p.h_world0);
+    launch_pdl(k_scan_apply<false>, p.n_scan_items, 256, 0, s, p.d_worlds, p.d_scan_items, p.h_world0);
   }
 }
 

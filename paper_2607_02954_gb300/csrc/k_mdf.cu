@@ -32,6 +32,8 @@ namespace {
 // a bin, and F_el = 0 (the MDF passes accumulate the bead forces in it).
 __global__ void __launch_bounds__(kBeadChunk) k_mdf_bins(const WorldDev* __restrict__ worlds,
                                                          const int2* __restrict__ items) {
+  pdl_trigger();
+  pdl_wait();
   const int2 it = items[blockIdx.x];
   const WorldDev& w = worlds[it.x];
   if (w.ib != 1) return;
@@ -51,6 +53,8 @@ __global__ void __launch_bounds__(kBeadChunk) k_mdf_bins(const WorldDev* __restr
 // u* and rho of every cell from the pulled populations and the steric F.
 __global__ void __launch_bounds__(kCellChunk) k_mdf_moments(const WorldDev* __restrict__ worlds,
                                                             const int2* __restrict__ items) {
+  pdl_trigger();
+  pdl_wait();
   const int2 it = items[blockIdx.x];
   const WorldDev& w = worlds[it.x];
   if (w.ib != 1) return;
@@ -82,6 +86,8 @@ __global__ void __launch_bounds__(kCellChunk) k_mdf_moments(const WorldDev* __re
 // the pass's largest component (bounds the spread's fixed-point scale).
 __global__ void __launch_bounds__(kBeadChunk) k_mdf_force(const WorldDev* __restrict__ worlds,
                                                           const int2* __restrict__ items, int pass) {
+  pdl_trigger();
+  pdl_wait();
   const int2 it = items[blockIdx.x];
   const WorldDev& w = worlds[it.x];
   if (w.ib != 1 || pass >= w.mdf_iters) return;

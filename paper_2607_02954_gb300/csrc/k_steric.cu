@@ -224,6 +224,8 @@ template <int R, bool kSingle>
 __global__ void __launch_bounds__(kThreads, 8) k_deposit_x(const WorldDev* __restrict__ worlds,
                                                         const int2* __restrict__ items, int store_fields,
                                                         const __grid_constant__ WorldDev w1) {
+  pdl_trigger();
+  pdl_wait();
   using G = Geo<R>;
   __shared__ __align__(16) int acc[G::kDY * G::kDX];
   __shared__ __align__(16) float4 sp[kDepCap];
@@ -696,6 +698,8 @@ template <int R>
 __global__ void __launch_bounds__(kThreads) k_force_spread(const WorldDev* __restrict__ worlds,
                                                            const int2* __restrict__ items, int store_fields,
                                                            int after_step) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ __align__(16) ForceSmem<R> sm;
   const int2 it = items[blockIdx.x];
   const WorldDev& w = worlds[it.x];
@@ -773,6 +777,8 @@ template <int R, bool kSingle>
 __global__ void __launch_bounds__(kThreads, 4) k_force_lbm(const WorldDev* __restrict__ worlds,
                                                            const int2* __restrict__ items,
                                                            const __grid_constant__ WorldDev w1) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ __align__(16) ForceSmem<R> sm;
   const int2 it = kSingle ? single_tile_item(w1) : items[blockIdx.x];
   const WorldDev& w = kSingle ? w1 : worlds[it.x];
@@ -791,6 +797,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_force_lbm(const WorldDev* __res
 // rho_s (the sum of the spread weights of a cell).
 __global__ void __launch_bounds__(kThreads) k_mdf_spread(const WorldDev* __restrict__ worlds,
                                                          const int2* __restrict__ items, int pass) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ __align__(16) float4 sp[kForceCap];
   __shared__ __align__(8) float2 sf[kForceCap];
   __shared__ TileWork wk;
@@ -894,16 +902,16 @@ template <int R>
 void launch_steric(const Plan& p, cudaStream_t s, int which, int store_fields, int after_step) {
   if (which == 0) {
     if (p.n_worlds == 1)
-      k_deposit_x<R, true><<<p.n_tile_items, kThreads, 0, s>>>(p.d_worlds, p.d_tile_items, store_fields, p.h_world0);
+      launch_pdl(k_deposit_x<R, true>, p.n_tile_items, kThreads, 0, s, p.d_worlds, p.d_tile_items, store_fields, p.h_world0);
     else
-      k_deposit_x<R, false><<<p.n_tile_items, kThreads, 0, s>>>(p.d_worlds, p.d_tile_items, store_fields, p.h_world0);
+      launch_pdl(k_deposit_x<R, false>, p.n_tile_items, kThreads, 0, s, p.d_worlds, p.d_tile_items, store_fields, p.h_world0);
   } else if (which == 1) {
     k_force_spread<R><<<p.n_tile_items, kThreads, 0, s>>>(p.d_worlds, p.d_tile_items, store_fields, after_step);
   } else {
     if (p.n_worlds == 1)
-      k_force_lbm<R, true><<<p.n_tile_items, kThreads, 0, s>>>(p.d_worlds, p.d_tile_items, p.h_world0);
+      launch_pdl(k_force_lbm<R, true>, p.n_tile_items, kThreads, 0, s, p.d_worlds, p.d_tile_items, p.h_world0);
     else
-      k_force_lbm<R, false><<<p.n_tile_items, kThreads, 0, s>>>(p.d_worlds, p.d_tile_items, p.h_world0);
+      launch_pdl(k_force_lbm<R, false>, p.n_tile_items, kThreads, 0, s, p.d_worlds, p.d_tile_items, p.h_world0);
   }
 }
 

@@ -170,6 +170,26 @@ void launch_adj_step(const Plan& p, const WorldDev& h, AdjDev a, int src_parity,
 size_t adj_pbd_smem_per_warp(int maxB, int n_pbd);
 void adj_setup(const Plan& p, const WorldDev& h);   // host set-up of the adjoint kernels (before capture)
 void launch_set_rest(const WorldDev& h, const float* theta0, const float* L_rest, cudaStream_t s);
+// Launches kernel k, with programmatic stream serialization (see pdl_wait)
+// unless the stream is being captured into a graph.  Direct launches (server
+// ticks, short runs) gain from it; in a replayed graph, programmatic edges
+// measured slower than plain ones.
+template <typename... P, typename... A>
+inline void launch_pdl(void (*k)(P...), unsigned grid, unsigned block, size_t smem, cudaStream_t s, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  cfg.attrs = at;
+  cfg.numAttrs = cs == cudaStreamCaptureStatusNone ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k, args...);
+}
 void kernel_setup();   // one-time host set-up of the kernels' shared-memory limits
 void launch_loss_splat(const Plan& p, const WorldDev& h, const float* target, int R, float sigma,
                        unsigned long long* acc, float* diff, float* loss, float* gx, float* gy, cudaStream_t s);
@@ -342,6 +362,16 @@ __device__ __forceinline__ float drive_length(const float4 d, long long t) {
 __device__ __forceinline__ float rest_length(const WorldDev& w, int e, long long t) {
   return w.ldrive ? drive_length(w.ldrive[e], t) : w.L_rest[e];
 }
+
+// Programmatic dependent launch.  The step's kernels may be launched so that
+// a kernel's blocks are scheduled while its predecessor drains:
+// pdl_trigger lets the next kernel launch once every block of this one has
+// started, and pdl_wait blocks until every prerequisite grid has completed
+// and its memory operations are visible (it returns at once in a kernel
+// launched without the attribute).  Every kernel of the step files calls
+// both first, before it touches device memory.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // A contribution to an observable in its fixed point (2^-24 resolution).
 __device__ __forceinline__ long long obs_q(float v) { return __float2ll_rn(v * kObsScale); }
