@@ -51,8 +51,9 @@ GRAPH_STEPS = 16   # mc_step replays graphs of 16 steps: PBD, then 15 x (previou
 
 def mdf_launches(steps: int, m: int) -> int:
     """Kernels of direct-forcing steps (always the unfused sequence): PBD (returns), bins, scan (2),
-    scatter, deposit, steric spread, moments, predicted PBD, m x (force, update), LBM, advance."""
-    return steps * (11 + 2 * m)
+    scatter, deposit, steric spread, moments, predicted PBD, m passes (one tile kernel each), LBM,
+    advance."""
+    return steps * (11 + m)
 
 
 def graph_launches(steps: int) -> int:

@@ -258,7 +258,9 @@ __device__ __forceinline__ void bead_out(const WorldDev& w, const PbdConst& k, b
   if (kMode == 2) {
     if (valid) {
       const float2 U = w.ubead[b];
-      w.ubead[b] = make_float2(U.x + dlx / k.dt, U.y + dly / k.dt);
+      const float2 Us = make_float2(U.x + dlx / k.dt, U.y + dly / k.dt);
+      w.ubead[b] = Us;
+      w.sus[w.bead_slot[b]] = Us;   // the MDF passes read U_s in bin order
     }
     return;
   }
@@ -619,7 +621,7 @@ __global__ void __launch_bounds__(kBeadChunk) k_bin_scatter(const WorldDev* __re
     w.spos[slot] = w.pos[i];
     w.sfel[slot] = w.fel[i];
     w.sid[slot] = i;
-    if (w.bead_slot) w.bead_slot[i] = slot;   // direct forcing: the MDF passes write dF to the slot
+    if (w.bead_slot) w.bead_slot[i] = slot;   // direct forcing: U_s goes to the bead's slot
   }
 }
 

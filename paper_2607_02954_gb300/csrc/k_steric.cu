@@ -668,7 +668,8 @@ __device__ __forceinline__ int force_tile(ForceSmem<R>& sm, const WorldDev& w, i
 
 // Folds the stencil cells that wrapped around an axis the tile covers whole
 // (one tile on that axis); call after the block has synchronised.
-__device__ __forceinline__ void force_fold(TileWork& wk, const TileBox& tb, int ntx, int nty) {
+template <class Work>
+__device__ __forceinline__ void force_fold(Work& wk, const TileBox& tb, int ntx, int nty) {
   if (ntx > 1 && nty > 1) return;
   const bool fx = ntx == 1, fy = nty == 1;
   for (int c = threadIdx.x; c < kAx * kAx; c += kThreads) {
@@ -790,77 +791,186 @@ __global__ void __launch_bounds__(kThreads, 4) k_force_lbm(const WorldDev* __res
   if (!layered) tile_lbm(sm.wk, w, tb, k);
 }
 
-// One MDF pass of the direct-forcing worlds on one tile: the spread of the
-// beads' dF (bin-ordered, in sfel) in int32 fixed point, then
-// F += S[dF] and u += S[dF] / (2 rho) on the tile's cells.  The scale's
-// bound is the pass's largest |dF| component times the tile's largest
-// rho_s (the sum of the spread weights of a cell).
-__global__ void __launch_bounds__(kThreads) k_mdf_spread(const WorldDev* __restrict__ worlds,
-                                                         const int2* __restrict__ items, int pass) {
+// One MDF pass of the direct-forcing worlds on one tile, Jacobi in u.  Every
+// bead whose stencil reaches the tile gets
+//   dF_i = 2 I[rho](X_i) (U_s,i - I[u](X_i))
+// from the pass's input velocity (u for even passes, u2 for odd ones) and
+// rho, both staged with a 3-cell halo; then the tile's cells get
+// F += S[dF] and u' = u + S[dF] / (2 rho) in the other velocity buffer, and
+// the tile that holds a bead adds its dF to F_el.  A bead near a tile edge
+// is evaluated by each tile its stencil reaches, from the same inputs in the
+// same order, so every tile uses the same dF bitwise.  The spread is in
+// int32 fixed point with the scale from the largest |dF| component among
+// the tile's beads times the tile's largest rho_s (the sum of the spread
+// weights of a cell): bitwise independent of order.  The dF of a tile's
+// beads are kept in shared memory when they fit one staging pass, and are
+// evaluated again in a second sweep otherwise.
+constexpr int kMwy = kTile + 6;   // window rows: the tile and 3 cells a side
+constexpr int kMwx = kTile + 8;   // window columns: the tile and 4 cells a side (16-byte chunks)
+
+struct MdfSmem {
+  float4 sp[kForceCap];   // staged bead records
+  float2 su[kForceCap];   // their U_s
+  float2 df[kForceCap];   // their dF (one-pass tiles)
+  int si[kForceCap];      // their bead indices
+  float2 uw[kMwy * kMwx];   // input velocity window
+  float rw[kMwy * kMwx];    // density window
+  int accx[kAx * kAx];    // spread accumulators
+  int accy[kAx * kAx];
+  int list[kForceCap];
+  int s_cnt;
+  int s_start[kMaxSeg], s_pre[kMaxSeg + 1];
+  float red[kWarps];
+};
+
+// dF of the staged bead v whose tile-relative cell is (rx, ry) in [-2, tw] x
+// [-2, th]: its stencil cells sit at window rows ry + 2 .. ry + 5 and
+// columns rx + 3 .. rx + 6.
+__device__ __forceinline__ float2 mdf_bead_force(const MdfSmem& sm, int v, int rx, int ry) {
+  const float4 p = sm.sp[v];
+  float wx[4], wy[4];
+  peskin4(p.x, wx);
+  peskin4(p.y, wy);
+  float Ux = 0.0f, Uy = 0.0f, r = 0.0f;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int row = (ry + 2 + b) * kMwx + rx + 3;
+    float ax = 0.0f, ay = 0.0f, ar = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const float2 v2 = sm.uw[row + a];
+      ax = fmaf(wx[a], v2.x, ax);
+      ay = fmaf(wx[a], v2.y, ay);
+      ar = fmaf(wx[a], sm.rw[row + a], ar);
+    }
+    Ux = fmaf(wy[b], ax, Ux);
+    Uy = fmaf(wy[b], ay, Uy);
+    r = fmaf(wy[b], ar, r);
+  }
+  const float2 Us = sm.su[v];
+  return make_float2(2.0f * r * (Us.x - Ux), 2.0f * r * (Us.y - Uy));
+}
+
+// Stages chunk c0 of the tile's bead segments and lists the beads whose
+// stencil reaches the tile (the block synchronises inside).
+__device__ __forceinline__ int mdf_stage_chunk(MdfSmem& sm, const WorldDev& w, const TileBox& tb, int c0, int total) {
+  const int tid = threadIdx.x;
+  const int W = w.W, H = w.H, ntx = w.ntx, nty = w.nty;
+  const int n = min(kForceCap, total - c0);
+  for (int v = tid; v < n; v += kThreads) {
+    const int slot = seg_slot(c0 + v, sm.s_start, sm.s_pre);
+    cp_async16(&sm.sp[v], &w.spos[slot]);
+    cp_async8(&sm.su[v], &w.sus[slot]);
+    cp_async4(&sm.si[v], &w.sid[slot]);
+  }
+  cp_async_wait_all();
+  if (tid == 0) sm.s_cnt = 0;
+  __syncthreads();
+  for (int v0 = 0; v0 < n; v0 += kThreads) {
+    const int v = v0 + tid;
+    bool keep = false;
+    int rx = 0, ry = 0;
+    if (v < n) {
+      const float4 p = sm.sp[v];
+      rx = cell_x(p) - tb.x0;
+      ry = cell_y(p) - tb.y0;
+      keep = true;
+      if (ntx > 1) {
+        rx = image_lo(rx, W, 2);
+        keep = rx <= tb.tw;
+      }
+      if (nty > 1) {
+        ry = image_lo(ry, H, 2);
+        keep = keep && ry <= tb.th;
+      }
+    }
+    list_push(keep, pack_code(v, rx, ry), sm.list, &sm.s_cnt);
+  }
+  __syncthreads();
+  return sm.s_cnt;
+}
+
+__global__ void __launch_bounds__(kThreads) k_mdf_pass(const WorldDev* __restrict__ worlds,
+                                                       const int2* __restrict__ items, int pass) {
   pdl_trigger();
   pdl_wait();
-  __shared__ __align__(16) float4 sp[kForceCap];
-  __shared__ __align__(8) float2 sf[kForceCap];
-  __shared__ TileWork wk;
-  __shared__ int s_start[kMaxSeg], s_pre[kMaxSeg + 1];
+  __shared__ __align__(16) MdfSmem sm;
   const int2 it = items[blockIdx.x];
   const WorldDev& w = worlds[it.x];
   if (w.ib != 1 || pass >= w.mdf_iters) return;
   const TileBox tb = tile_box(w, it.y);
   const int W = w.W, H = w.H, ntx = w.ntx, nty = w.nty;
   const int tile = (tb.y0 / kTile) * ntx + tb.x0 / kTile;
-  const int tid = threadIdx.x;
-  if ((tid >> 5) == 0) build_segments(w, tb.x0 - 2, tb.x0 + tb.tw, tb.y0 - 2, tb.y0 + tb.th, s_start, s_pre, nullptr);
-  tile_clear(wk);
-  // the next pass's maximum slot (its force kernel follows this kernel)
-  if (tile == 0 && tid == 0) w.mdf_max[(pass + 1) & 1] = 0u;
-  __syncthreads();
-  const float dmax = __uint_as_float(w.mdf_max[pass & 1]);
-  const int k = fix_exponent(dmax * w.tile_rho_max[tile] * 1.0001f + 1e-30f);
-  const float scale = pow2f(k);
-  const int total = s_pre[kMaxSeg];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float2* __restrict__ u_in = (pass & 1) ? w.u2 : w.u;
+  float2* __restrict__ u_out = (pass & 1) ? w.u : w.u2;
+  if (warp == 0) build_segments(w, tb.x0 - 2, tb.x0 + tb.tw, tb.y0 - 2, tb.y0 + tb.th, sm.s_start, sm.s_pre, nullptr);
+  // the velocity and density windows, rows y0 - 3 .. y0 + th + 2 and
+  // columns x0 - 4 .. x0 + tw + 3, periodic (W, H >= 8: one wrap at most),
+  // in 16-byte chunks (2 velocities or 4 densities; x0 and W are multiples
+  // of 8, so a chunk never straddles the periodic edge)
+  const bool full = tb.tw == kTile;   // full tile: constant divisors
+  const int nu = full ? kMwx / 2 : (tb.tw + 8) >> 1, nr = full ? kMwx / 4 : (tb.tw + 8) >> 2, wh = tb.th + 6;
+  for (int c = tid; c < wh * nu; c += kThreads) {
+    const int i = full ? c / (kMwx / 2) : c / nu, j = 2 * (c - i * nu);
+    const size_t g = (size_t)wrap_once(tb.y0 - 3 + i, H) * W + wrap_once(tb.x0 - 4 + j, W);
+    cp_async16(&sm.uw[i * kMwx + j], &u_in[g]);
+  }
+  for (int c = tid; c < wh * nr; c += kThreads) {
+    const int i = full ? c / (kMwx / 4) : c / nr, j = 4 * (c - i * nr);
+    const size_t g = (size_t)wrap_once(tb.y0 - 3 + i, H) * W + wrap_once(tb.x0 - 4 + j, W);
+    cp_async16(&sm.rw[i * kMwx + j], &w.mrho[g]);
+  }
+  for (int c = tid; c < kAx * kAx / 4; c += kThreads) {
+    reinterpret_cast<int4*>(sm.accx)[c] = make_int4(0, 0, 0, 0);
+    reinterpret_cast<int4*>(sm.accy)[c] = make_int4(0, 0, 0, 0);
+  }
+  __syncthreads();   // segments visible (the windows land with the first chunk's wait)
+  const int total = sm.s_pre[kMaxSeg];
+  const bool one_pass = total <= kForceCap;
+  // sweep 1: dF of every listed bead and their largest component
+  float m = 0.0f;
   for (int c0 = 0; c0 < total; c0 += kForceCap) {
-    const int n = min(kForceCap, total - c0);
-    for (int v = tid; v < n; v += kThreads) {
-      const int slot = seg_slot(c0 + v, s_start, s_pre);
-      cp_async16(&sp[v], &w.spos[slot]);
-      cp_async8(&sf[v], &w.sfel[slot]);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    for (int v0 = 0; v0 < n; v0 += kThreads) {
-      const int v = v0 + tid;
-      bool keep = false;
-      int rx = 0, ry = 0;
-      if (v < n) {
-        const float4 p = sp[v];
-        rx = cell_x(p) - tb.x0;
-        ry = cell_y(p) - tb.y0;
-        keep = true;
-        if (ntx > 1) {
-          rx = image_lo(rx, W, 2);
-          keep = rx <= tb.tw;
-        }
-        if (nty > 1) {
-          ry = image_lo(ry, H, 2);
-          keep = keep && ry <= tb.th;
-        }
-      }
-      list_push(keep, pack_code(v, rx, ry), wk.list, &wk.s_cnt);
-    }
-    __syncthreads();
-    const int cnt = wk.s_cnt;
+    if (c0 > 0) __syncthreads();   // the previous chunk is no longer read
+    const int cnt = mdf_stage_chunk(sm, w, tb, c0, total);
     for (int q = tid; q < cnt; q += kThreads) {
-      const int code = wk.list[q];
+      const int code = sm.list[q];
+      const int v = code_slot(code);
+      const float2 dF = mdf_bead_force(sm, v, code_rx(code), code_ry(code));
+      if (one_pass) sm.df[v] = dF;
+      m = fmaxf(m, fmaxf(fabsf(dF.x), fabsf(dF.y)));
+    }
+  }
+  if (total == 0) cp_async_wait_all();
+  m = block_max(m, sm.red);   // also orders the df writes before sweep 2
+  const int k = fix_exponent(m * w.tile_rho_max[tile] * 1.0001f + 1e-30f);
+  const float scale = pow2f(k);
+  // sweep 2: the spread, and F_el += dF on the bead's own tile
+  float2* __restrict__ fel = w.fel;
+  for (int c0 = 0; c0 < total; c0 += kForceCap) {
+    int cnt = sm.s_cnt;
+    if (!one_pass) {
+      __syncthreads();
+      cnt = mdf_stage_chunk(sm, w, tb, c0, total);
+    }
+    for (int q = tid; q < cnt; q += kThreads) {
+      const int code = sm.list[q];
       const int v = code_slot(code), rx = code_rx(code), ry = code_ry(code);
-      const float4 p = sp[v];
-      const float2 dF = sf[v];
+      const float2 dF = one_pass ? sm.df[v] : mdf_bead_force(sm, v, rx, ry);
+      if (rx >= 0 && rx < tb.tw && ry >= 0 && ry < tb.th) {
+        // the bead's own tile is its one writer in this pass: the adds
+        // need no return value and leave the same bits in any order
+        const int i = sm.si[v];
+        atomicAdd(&fel[i].x, dF.x);
+        atomicAdd(&fel[i].y, dF.y);
+      }
+      const float4 p = sm.sp[v];
       float wx[4], wy[4];
       peskin4(p.x, wx);
       peskin4(p.y, wy);
       const float Fx = dF.x * scale, Fy = dF.y * scale;
-      int* bx = wk.accx + (ry + 2) * kAx + rx + 2;
-      int* by = wk.accy + (ry + 2) * kAx + rx + 2;
+      int* bx = sm.accx + (ry + 2) * kAx + rx + 2;
+      int* by = sm.accy + (ry + 2) * kAx + rx + 2;
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
 #pragma unroll
@@ -871,27 +981,31 @@ __global__ void __launch_bounds__(kThreads) k_mdf_spread(const WorldDev* __restr
         }
       }
     }
-    __syncthreads();
-    if (tid == 0) wk.s_cnt = 0;
   }
   __syncthreads();
-  force_fold(wk, tb, ntx, nty);
+  force_fold(sm, tb, ntx, nty);
   const float inv = pow2f(-k);
-  const int lane = tid & 31;
-  for (int ly = tid >> 5; ly < tb.th; ly += kWarps) {
-    if (lane < tb.tw) {
+  // the warp's rows warp, warp + 8, ...: every F load in flight at once
+  float2* __restrict__ Fg = w.F;
+  constexpr int kRows = kTile / kWarps;
+  float2 Fv[kRows];
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) {
+    const int ly = warp + r * kWarps;
+    if (ly < tb.th && lane < tb.tw) Fv[r] = Fg[(size_t)(tb.y0 + ly) * W + tb.x0 + lane];
+  }
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) {
+    const int ly = warp + r * kWarps;
+    if (ly < tb.th && lane < tb.tw) {
       const int sidx = (ly + 3) * kAx + lane + 3;
+      const int widx = (ly + 3) * kMwx + lane + 4;
       const size_t c = (size_t)(tb.y0 + ly) * W + tb.x0 + lane;
-      const float Gx = (float)wk.accx[sidx] * inv, Gy = (float)wk.accy[sidx] * inv;
-      float2 F = w.F[c];
-      F.x += Gx;
-      F.y += Gy;
-      w.F[c] = F;
-      const float h = 2.0f * w.mrho[c];
-      float2 u = w.u[c];
-      u.x += Gx / h;
-      u.y += Gy / h;
-      w.u[c] = u;
+      const float Gx = (float)sm.accx[sidx] * inv, Gy = (float)sm.accy[sidx] * inv;
+      Fg[c] = make_float2(Fv[r].x + Gx, Fv[r].y + Gy);
+      const float ih = __frcp_rn(2.0f * sm.rw[widx]);   // 1 / (2 rho), correctly rounded
+      const float2 u = sm.uw[widx];
+      u_out[c] = make_float2(fmaf(Gx, ih, u.x), fmaf(Gy, ih, u.y));
     }
   }
 }
@@ -939,8 +1053,8 @@ void launch_force_spread(const Plan& p, cudaStream_t s, int store_fields, int af
   launch_layer_spread(p, s);
 }
 
-void launch_mdf_spread(const Plan& p, cudaStream_t s, int pass) {
-  if (p.n_tile_items) k_mdf_spread<<<p.n_tile_items, kThreads, 0, s>>>(p.d_worlds, p.d_tile_items, pass);
+void launch_mdf_pass(const Plan& p, cudaStream_t s, int pass) {
+  if (p.n_tile_items) k_mdf_pass<<<p.n_tile_items, kThreads, 0, s>>>(p.d_worlds, p.d_tile_items, pass);
 }
 
 void launch_force_lbm(const Plan& p, cudaStream_t s) {

@@ -313,7 +313,8 @@ size_t world_layout(WorldDev& h, void* A) {
   const bool df = h.ib == 1;
   const size_t o_mr = L.take<float>(df ? HW : 0);
   const size_t o_bs = L.take<int>(df ? N : 0);
-  const size_t o_mm = L.take<unsigned>(df ? 2 : 0);
+  const size_t o_u2 = L.take<float2>(df ? HW : 0);
+  const size_t o_su = L.take<float2>(df ? N : 0);
   if (!A) return L.off;
   h.fil_off = at<int>(A, o_fo);
   h.pos = at<float4>(A, o_pos);
@@ -352,7 +353,8 @@ size_t world_layout(WorldDev& h, void* A) {
   h.facc = h.layers == 2 ? at<unsigned long long>(A, o_fa) : nullptr;
   h.mrho = df ? at<float>(A, o_mr) : nullptr;
   h.bead_slot = df ? at<int>(A, o_bs) : nullptr;
-  h.mdf_max = df ? at<unsigned>(A, o_mm) : nullptr;
+  h.u2 = df ? at<float2>(A, o_u2) : nullptr;
+  h.sus = df ? at<float2>(A, o_su) : nullptr;
   return L.off;
 }
 

@@ -78,7 +78,8 @@ struct WorldDev {
   int ib, mdf_iters;      // coupling (0 penalty, 1 direct forcing) and MDF passes per step
   float* mrho;            // [H * W] fluid density of the step (ib == 1)
   int* bead_slot;         // [N] slot of each bead in the bin-ordered arrays (ib == 1, else nullptr)
-  unsigned* mdf_max;      // [2] largest |dF| component of an MDF pass, by pass parity (float bits; ib == 1)
+  float2* u2;             // [H * W] second velocity buffer: MDF passes alternate u -> u2 -> u (ib == 1)
+  float2* sus;            // [N] U_s in bin order (ib == 1)
   float2* nrm;            // [N] filament unit normal at each bead (layers == 2)
   unsigned long long* facc;  // [2 H W] fixed-point spread of the layer points (layers == 2)
   const float4* ldrive;   // [E] (L0, amp, freq, phase) rest-length drive, or nullptr (static L_rest)
@@ -159,7 +160,7 @@ void launch_interp_advance(const Plan& p, cudaStream_t s);
 // MDF passes after it
 void launch_mdf_bins(const Plan& p, cudaStream_t s);
 void launch_mdf(const Plan& p, cudaStream_t s);
-void launch_mdf_spread(const Plan& p, cudaStream_t s, int pass);   // k_steric.cu: one pass's spread + update
+void launch_mdf_pass(const Plan& p, cudaStream_t s, int pass);   // k_steric.cu: one MDF pass (tile kernel)
 void enqueue_step(const Plan& p, cudaStream_t s);
 void enqueue_steps(const Plan& p, int n, cudaStream_t s);   // n steps, fused bead stages where possible
 void launch_advance_pbd(const Plan& p, cudaStream_t s);
