@@ -227,36 +227,69 @@ __global__ void __launch_bounds__(256) k_adj_bead_a(const WorldDev* __restrict__
 }
 
 // ---------------------------------------------------------------------------
-// a6 gradient transposed: rho_bar_bar = -k_rep D^T Q with D the central
-// difference, (D^T v)(c) = (v_x(c - e_x) - v_x(c + e_x) + v_y(c - e_y) - v_y(c + e_y))/2.
+// a6 gradient transposed and a5 transposed, one 32x32 tile per block:
+//   rho_bar_bar = -k_rep D^T Q with D the central difference,
+//     (D^T v)(c) = (v_x(c - e_x) - v_x(c + e_x) + v_y(c - e_y) - v_y(c + e_y))/2,
+//   then the periodic separable filter (symmetric), x pass then y pass.
+// rho_bar_bar is formed on the tile plus R cells a side from Q staged with
+// one more cell, the x pass on the tile's columns over those rows, the y
+// pass on the tile; the sums run in the same order as cell-wise passes over
+// the whole grid, so the result does not depend on the tiling.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_adj_rho(const WorldDev* __restrict__ wd, AdjDev a) {
-  const WorldDev& w = *wd;
-  const int W = w.W, H = w.H;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= H * W) return;
-  const int y = c / W, x = c - y * W;
-  const int xm = x == 0 ? W - 1 : x - 1, xp = x == W - 1 ? 0 : x + 1;
-  const int ym = y == 0 ? H - 1 : y - 1, yp = y == H - 1 ? 0 : y + 1;
-  const float v = a.Q[y * W + xm].x - a.Q[y * W + xp].x + a.Q[ym * W + x].y - a.Q[yp * W + x].y;
-  a.rbb[c] = -0.5f * w.k_rep * v;
-}
-
-// a5 transposed: the periodic separable filter (symmetric), x then y pass.
-__global__ void __launch_bounds__(256) k_adj_blur(const WorldDev* __restrict__ wd, const float* __restrict__ in,
-                                                  float* __restrict__ out, int along_y) {
+__global__ void __launch_bounds__(256) k_adj_rho_blur(const WorldDev* __restrict__ wd, AdjDev a) {
+  constexpr int kE = kTile + 2 * kMaxR;   // row and column capacity of the rho_bar_bar region
+  constexpr int kQ = kE + 2;              // Q window capacity
+  __shared__ float2 q[kQ * kQ];
+  __shared__ float rb[kE * kE];
+  __shared__ float tm[kE * kTile];
   const WorldDev& w = *wd;
   const int W = w.W, H = w.H, R = w.R;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= H * W) return;
-  const int y = c / W, x = c - y * W;
-  float s = 0.0f;
-  if (along_y) {
-    for (int m = 0; m <= 2 * R; ++m) s = fmaf(w.taps[m], in[wrap_mod(y - R + m, H) * W + x], s);
-  } else {
-    for (int m = 0; m <= 2 * R; ++m) s = fmaf(w.taps[m], in[y * W + wrap_mod(x - R + m, W)], s);
+  const int ntx = (W + kTile - 1) / kTile;
+  const int x0 = (int)(blockIdx.x % ntx) * kTile, y0 = (int)(blockIdx.x / ntx) * kTile;
+  const int tw = min(kTile, W - x0), th = min(kTile, H - y0);
+  const int ew = tw + 2 * R, eh = th + 2 * R;   // region: rows y0 - R .., columns x0 - R ..
+  const int qw = ew + 2, qh = eh + 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  // rows by warp, columns by lane (no divisions); wrap by at most two periods
+  for (int i = warp; i < qh; i += nw) {
+    int gy = y0 - R - 1 + i;
+    while (gy < 0) gy += H;
+    while (gy >= H) gy -= H;
+    const float2* __restrict__ row = a.Q + (size_t)gy * W;
+    for (int j = lane; j < qw; j += 32) {
+      int gx = x0 - R - 1 + j;
+      while (gx < 0) gx += W;
+      while (gx >= W) gx -= W;
+      q[i * kQ + j] = row[gx];
+    }
   }
-  out[c] = s;
+  __syncthreads();
+  const float kq = -0.5f * w.k_rep;
+  for (int i = warp; i < eh; i += nw) {
+    for (int j = lane; j < ew; j += 32) {
+      const float2* r = q + (i + 1) * kQ + j + 1;
+      const float v = r[-1].x - r[1].x + r[-kQ].y - r[kQ].y;
+      rb[i * kE + j] = kq * v;
+    }
+  }
+  __syncthreads();
+  for (int i = warp; i < eh; i += nw) {
+    if (lane < tw) {
+      const float* r = rb + i * kE + lane;
+      float acc = 0.0f;
+      for (int m = 0; m <= 2 * R; ++m) acc = fmaf(w.taps[m], r[m], acc);
+      tm[i * kTile + lane] = acc;
+    }
+  }
+  __syncthreads();
+  for (int i = warp; i < th; i += nw) {
+    if (lane < tw) {
+      const float* r = tm + i * kTile + lane;
+      float acc = 0.0f;
+      for (int m = 0; m <= 2 * R; ++m) acc = fmaf(w.taps[m], r[m * kTile], acc);
+      a.rsb[(size_t)(y0 + i) * W + x0 + lane] = acc;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -294,7 +327,8 @@ __global__ void __launch_bounds__(256) k_adj_bead_b(const WorldDev* __restrict__
 }
 
 // ---------------------------------------------------------------------------
-// a3 + a1 transposed, one warp per filament.  The forward Jacobi PBD is
+// a3 + a1 transposed, one block of two warps per filament (each thread
+// holds at most one edge of a filament of up to 64 beads per loop trip).  The forward Jacobi PBD is
 // recomputed from (X^n, theta^n) keeping, per iteration, the frames before
 // and after the bending pass and the corrections before the position pass;
 // then the iterations are reversed:
@@ -309,25 +343,24 @@ __global__ void __launch_bounds__(256) k_adj_bead_b(const WorldDev* __restrict__
 // L_rest_bar += (per edge), and (k_bend, k_stretch, k_shear)_bar += (float
 // atomics, one per warp).
 // ---------------------------------------------------------------------------
+constexpr int kAdjPbdThreads = 64;  // threads per filament
 constexpr int kAdjPbdPerBead = 12;   // floats of working arrays per bead slot
 constexpr int kAdjTapePerPass = 4;   // per pass: theta before and after the bend pass, d (x, y)
 
-__global__ void __launch_bounds__(128) k_adj_pbd(const WorldDev* __restrict__ wd, AdjDev a,
-                                                 const int2* __restrict__ items, int n_items, int maxB,
-                                                 int n_pbd) {
+__global__ void __launch_bounds__(kAdjPbdThreads) k_adj_pbd(const WorldDev* __restrict__ wd, AdjDev a,
+                                                            const int2* __restrict__ items, int n_items,
+                                                            int maxB, int n_pbd) {
   extern __shared__ __align__(16) float smem[];
   const WorldDev& w = *wd;
-  const int wpb = blockDim.x >> 5;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int item = blockIdx.x * wpb + warp;
-  if (item >= n_items) return;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int item = blockIdx.x;
+  if (item >= n_items) return;   // block-uniform
   const int f = items[item].y;
   const int b0 = w.fil_off[f];
   const int B = w.fil_off[f + 1] - b0;
   const int nE = B - 1, nJ = B - 2;
   const int e0 = b0 - f, j0 = b0 - 2 * f;
-  const int per = maxB * (kAdjPbdPerBead + kAdjTapePerPass * n_pbd + 2);
-  float* s = smem + (size_t)warp * per;
+  float* s = smem;
   float* vx = s;
   float* vy = s + maxB;
   float* th = s + 2 * maxB;
@@ -343,7 +376,7 @@ __global__ void __launch_bounds__(128) k_adj_pbd(const WorldDev* __restrict__ wd
   float* tape = s + 12 * maxB;  // per pass: theta before bend, theta after bend, d (x), d (y)
   const int W = w.W, H = w.H;
   const long long t = *w.t;
-  for (int e = lane; e < nE; e += 32) {
+  for (int e = tid; e < nE; e += kAdjPbdThreads) {
     const float4 pa = w.pos[b0 + e], pb = w.pos[b0 + e + 1];
     int dcx = cell_x(pb) - cell_x(pa), dcy = cell_y(pb) - cell_y(pa);
     if (2 * dcx > W) dcx -= W; else if (2 * dcx < -W) dcx += W;
@@ -354,35 +387,35 @@ __global__ void __launch_bounds__(128) k_adj_pbd(const WorldDev* __restrict__ wd
     Lr[e] = rest_length(w, e0 + e, t);
     gLa[e] = 0.0f;
   }
-  for (int j = lane; j < nJ; j += 32) {
+  for (int j = tid; j < nJ; j += kAdjPbdThreads) {
     thr[j] = drive_angle(w.drive[j0 + j], t);
     thrb[j] = 0.0f;
   }
-  for (int i = lane; i < B; i += 32) {
+  for (int i = tid; i < B; i += kAdjPbdThreads) {
     dx[i] = 0.0f;
     dy[i] = 0.0f;
   }
-  __syncwarp();
+  __syncthreads();
   const float hb = 0.5f * w.k_bend, hs = 0.5f * w.k_st, ksh = w.k_sh;
   const float orient = w.orient;
   const float ko = orient * hs * ksh;
   // ---- forward recompute with tape ----
   for (int it = 0; it < n_pbd; ++it) {
     float* tp = tape + it * kAdjTapePerPass * maxB;
-    for (int e = lane; e < nE; e += 32) tp[e] = th[e];
-    for (int j = lane; j < nJ; j += 32) Cb[j] = th[j + 1] - th[j] - thr[j];
-    __syncwarp();
-    for (int e = lane; e < nE; e += 32) {
+    for (int e = tid; e < nE; e += kAdjPbdThreads) tp[e] = th[e];
+    for (int j = tid; j < nJ; j += kAdjPbdThreads) Cb[j] = th[j + 1] - th[j] - thr[j];
+    __syncthreads();
+    for (int e = tid; e < nE; e += kAdjPbdThreads) {
       const float c1 = e < nJ ? Cb[e] : 0.0f, c0 = e > 0 ? Cb[e - 1] : 0.0f;
       th[e] += hb * (c1 - c0);
     }
-    __syncwarp();
-    for (int e = lane; e < nE; e += 32) tp[maxB + e] = th[e];
-    for (int i = lane; i < B; i += 32) {
+    __syncthreads();
+    for (int e = tid; e < nE; e += kAdjPbdThreads) tp[maxB + e] = th[e];
+    for (int i = tid; i < B; i += kAdjPbdThreads) {
       tp[2 * maxB + i] = dx[i];
       tp[3 * maxB + i] = dy[i];
     }
-    for (int e = lane; e < nE; e += 32) {
+    for (int e = tid; e < nE; e += kAdjPbdThreads) {
       const float x = vx[e] + (dx[e + 1] - dx[e]);
       const float y = vy[e] + (dy[e + 1] - dy[e]);
       const float L = Lr[e];
@@ -394,36 +427,36 @@ __global__ void __launch_bounds__(128) k_adj_pbd(const WorldDev* __restrict__ wd
       Dy[e] = hs * (sc * y + ksh * (y - L * sn - sc * y));
       th[e] += ko * (cs * y - sn * x) / L;
     }
-    __syncwarp();
-    for (int i = lane; i < B; i += 32) {
+    __syncthreads();
+    for (int i = tid; i < B; i += kAdjPbdThreads) {
       const float ax = i < nE ? Dx[i] : 0.0f, ay = i < nE ? Dy[i] : 0.0f;
       const float bx = i > 0 ? Dx[i - 1] : 0.0f, by = i > 0 ? Dy[i - 1] : 0.0f;
       dx[i] += ax - bx;
       dy[i] += ay - by;
     }
-    __syncwarp();
+    __syncthreads();
   }
   // ---- reverse ----
   // adjoint state: d_bar in dx/dy, theta_bar in th, edge-vector adjoint
   // v0_bar after the tape; per-lane sums of the stiffness adjoints
-  for (int i = lane; i < B; i += 32) {
+  for (int i = tid; i < B; i += kAdjPbdThreads) {
     const float2 db = a.dbar[b0 + i];
     dx[i] = db.x;
     dy[i] = db.y;
   }
-  for (int e = lane; e < nE; e += 32) th[e] = a.adjTh[e0 + e];
+  for (int e = tid; e < nE; e += kAdjPbdThreads) th[e] = a.adjTh[e0 + e];
   float* v0bx = tape + n_pbd * kAdjTapePerPass * maxB;
   float* v0by = v0bx + maxB;
-  for (int e = lane; e < nE; e += 32) {
+  for (int e = tid; e < nE; e += kAdjPbdThreads) {
     v0bx[e] = 0.0f;
     v0by[e] = 0.0f;
   }
   float hbb = 0.0f, hsb = 0.0f, kshb = 0.0f;
-  __syncwarp();
+  __syncthreads();
   for (int it = n_pbd - 1; it >= 0; --it) {
     const float* tp = tape + it * kAdjTapePerPass * maxB;
     // position pass reverse: D_bar_e = d_bar_e - d_bar_{e+1}
-    for (int e = lane; e < nE; e += 32) {
+    for (int e = tid; e < nE; e += kAdjPbdThreads) {
       const float Dbx = dx[e] - dx[e + 1], Dby = dy[e] - dy[e + 1];
       const float thb = th[e];          // adjoint of theta after this pass
       const float tb = tp[maxB + e];    // forward theta before this pass (after bend)
@@ -457,41 +490,41 @@ __global__ void __launch_bounds__(128) k_adj_pbd(const WorldDev* __restrict__ wd
       v0bx[e] += xbx;
       v0by[e] += xby;
     }
-    __syncwarp();
+    __syncthreads();
     // x = v0 + d_{e+1} - d_e: d_bar_i += x_bar_{i-1} - x_bar_i
-    for (int i = lane; i < B; i += 32) {
+    for (int i = tid; i < B; i += kAdjPbdThreads) {
       const float ax = i < nE ? Dx[i] : 0.0f, ay = i < nE ? Dy[i] : 0.0f;
       const float bx = i > 0 ? Dx[i - 1] : 0.0f, by = i > 0 ? Dy[i - 1] : 0.0f;
       dx[i] += bx - ax;
       dy[i] += by - ay;
     }
-    __syncwarp();
+    __syncthreads();
     // bending pass reverse: C_bar_j = hb (theta_bar_j - theta_bar_{j+1});
     // d theta_e / d hb = C_e - C_{e-1} with C from the angles before the pass
-    for (int j = lane; j < nJ; j += 32) {
+    for (int j = tid; j < nJ; j += kAdjPbdThreads) {
       const float dth = th[j] - th[j + 1];
       hbb += (tp[j + 1] - tp[j] - thr[j]) * dth;
       Cb[j] = hb * dth;
     }
-    __syncwarp();
-    for (int e = lane; e < nE; e += 32) {
+    __syncthreads();
+    for (int e = tid; e < nE; e += kAdjPbdThreads) {
       const float in = e > 0 ? Cb[e - 1] : 0.0f;     // theta_e is theta_{j+1} of joint e-1
       const float out = e < nJ ? Cb[e] : 0.0f;       // ... and theta_j of joint e
       th[e] += in - out;
     }
-    for (int j = lane; j < nJ; j += 32) thrb[j] -= Cb[j];
-    __syncwarp();
+    for (int j = tid; j < nJ; j += kAdjPbdThreads) thrb[j] -= Cb[j];
+    __syncthreads();
   }
   // outputs
-  for (int e = lane; e < nE; e += 32) {
+  for (int e = tid; e < nE; e += kAdjPbdThreads) {
     a.adjTh[e0 + e] = th[e];
     // with a rest-length drive L(t) = L0 (1 + A s(t)): dL(t)/dL0 = L(t)/L0
     const float dLdL0 = w.ldrive ? 1.0f + w.ldrive[e0 + e].y * drive_sin(w.ldrive[e0 + e].z, w.ldrive[e0 + e].w, t)
                                  : 1.0f;
     a.gL[e0 + e] += gLa[e] * dLdL0;
   }
-  for (int j = lane; j < nJ; j += 32) a.gth0[j0 + j] += thrb[j];
-  for (int i = lane; i < B; i += 32) {
+  for (int j = tid; j < nJ; j += kAdjPbdThreads) a.gth0[j0 + j] += thrb[j];
+  for (int i = tid; i < B; i += kAdjPbdThreads) {
     const float ax = i < nE ? v0bx[i] : 0.0f, ay = i < nE ? v0by[i] : 0.0f;        // X_i is x_1 of edge i
     const float bx = i > 0 ? v0bx[i - 1] : 0.0f, by = i > 0 ? v0by[i - 1] : 0.0f;  // ... x_2 of edge i-1
     float2 xb = a.adjX[b0 + i];
@@ -505,14 +538,14 @@ __global__ void __launch_bounds__(128) k_adj_pbd(const WorldDev* __restrict__ wd
     hsb += __shfl_xor_sync(0xffffffffu, hsb, o);
     kshb += __shfl_xor_sync(0xffffffffu, kshb, o);
   }
-  if (lane == 0) {
+  if (lane == 0) {   // one partial per warp
     atomicAdd(&a.gk[0], 0.5f * hbb);
     atomicAdd(&a.gk[1], 0.5f * hsb);
     atomicAdd(&a.gk[2], kshb);
   }
 }
 
-size_t adj_pbd_smem_per_warp(int maxB, int n_pbd) {
+size_t adj_pbd_smem_per_filament(int maxB, int n_pbd) {
   return (size_t)maxB * (kAdjPbdPerBead + kAdjTapePerPass * n_pbd + 2) * sizeof(float);
 }
 
@@ -577,24 +610,18 @@ void launch_adj_step(const Plan& p, const WorldDev& h, AdjDev a, int src_parity,
   if (h.N) k_adj_spread_u<<<blocks(h.N), 256, 0, s>>>(wd, a);
   k_adj_lbm<<<blocks(HW), 256, 0, s>>>(wd, a, src_parity);
   if (h.N) k_adj_bead_a<<<blocks(h.N), 256, 0, s>>>(wd, a);
-  k_adj_rho<<<blocks(HW), 256, 0, s>>>(wd, a);
-  k_adj_blur<<<blocks(HW), 256, 0, s>>>(wd, a.rbb, a.tmp, 0);
-  k_adj_blur<<<blocks(HW), 256, 0, s>>>(wd, a.tmp, a.rsb, 1);
+  k_adj_rho_blur<<<h.ntx * h.nty, 256, 0, s>>>(wd, a);
   if (h.N) k_adj_bead_b<<<blocks(h.N), 256, 0, s>>>(wd, a);
   if (p.n_fil_items) {
     const int mb = (p.max_B + 3) & ~3;
-    const size_t per = adj_pbd_smem_per_warp(mb, h.n_pbd);
-    int wpb = (int)((48 * 1024) / per);
-    wpb = wpb < 1 ? 1 : (wpb > 4 ? 4 : wpb);
-    const size_t smem = per * wpb;
-    k_adj_pbd<<<(p.n_fil_items + wpb - 1) / wpb, wpb * 32, smem, s>>>(wd, a, p.d_fil_items, p.n_fil_items, mb,
-                                                                     h.n_pbd);
+    const size_t smem = adj_pbd_smem_per_filament(mb, h.n_pbd);
+    k_adj_pbd<<<p.n_fil_items, kAdjPbdThreads, smem, s>>>(wd, a, p.d_fil_items, p.n_fil_items, mb, h.n_pbd);
   }
 }
 
 void adj_setup(const Plan& p, const WorldDev& h) {
   const int mb = (p.max_B + 3) & ~3;
-  const size_t per = adj_pbd_smem_per_warp(mb, h.n_pbd);
+  const size_t per = adj_pbd_smem_per_filament(mb, h.n_pbd);
   if (per > 48 * 1024) cudaFuncSetAttribute(k_adj_pbd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)per);
 }
 

@@ -345,7 +345,7 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
   if (h.layers != 1) return afail(MC_ERR_INVALID_ARG, "the reverse mode supports layers = 1 only");
   if (h.ib != 0) return afail(MC_ERR_INVALID_ARG, "the reverse mode supports the penalty coupling (ib = 0) only");
   const int mb = (w->max_B + 3) & ~3;
-  if (mc::adj_pbd_smem_per_warp(mb, h.n_pbd) > 220 * 1024)
+  if (mc::adj_pbd_smem_per_filament(mb, h.n_pbd) > 220 * 1024)
     return afail(MC_ERR_INVALID_ARG, "filaments too long for the adjoint (reduce beads per filament or n_pbd)");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t HW = (size_t)h.H * h.W;
@@ -370,8 +370,6 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
   const size_t o_ub = take(HW * sizeof(float2));
   const size_t o_Fb = take(HW * sizeof(float2));
   const size_t o_Q = take(HW * sizeof(float2));
-  const size_t o_rbb = take(HW * sizeof(float));
-  const size_t o_tmp = take(HW * sizeof(float));
   const size_t o_rsb = take(HW * sizeof(float));
   const size_t o_fbt = take(h.N * sizeof(float2));
   const size_t o_dbar = take(h.N * sizeof(float2));
@@ -397,8 +395,6 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
   a.ubar = reinterpret_cast<float2*>(A + o_ub);
   a.Fbar = reinterpret_cast<float2*>(A + o_Fb);
   a.Q = reinterpret_cast<float2*>(A + o_Q);
-  a.rbb = reinterpret_cast<float*>(A + o_rbb);
-  a.tmp = reinterpret_cast<float*>(A + o_tmp);
   a.rsb = reinterpret_cast<float*>(A + o_rsb);
   a.fbt = reinterpret_cast<float2*>(A + o_fbt);
   a.dbar = reinterpret_cast<float2*>(A + o_dbar);

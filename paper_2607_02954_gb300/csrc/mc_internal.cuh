@@ -105,8 +105,6 @@ struct AdjDev {
   float2* ubar;            // [H W] adjoint of the fluid velocity
   float2* Fbar;            // [H W] adjoint of the force density
   float2* Q;               // [H W] spread of the steric-force adjoint
-  float* rbb;              // [H W] adjoint of rho_bar
-  float* tmp;              // [H W] filter scratch
   float* rsb;              // [H W] adjoint of rho_s
   float2* fbt;             // [N] adjoint of F_el + F_s per bead
   float2* dbar;            // [N] adjoint of the PBD correction
@@ -168,7 +166,7 @@ constexpr int kKernelsPerStep = 8;
 
 // --- adjoint (one world) ----------------------------------------------------
 void launch_adj_step(const Plan& p, const WorldDev& h, AdjDev a, int src_parity, cudaStream_t s);
-size_t adj_pbd_smem_per_warp(int maxB, int n_pbd);
+size_t adj_pbd_smem_per_filament(int maxB, int n_pbd);
 void adj_setup(const Plan& p, const WorldDev& h);   // host set-up of the adjoint kernels (before capture)
 void launch_set_rest(const WorldDev& h, const float* theta0, const float* L_rest, cudaStream_t s);
 // Launches kernel k, with programmatic stream serialization (see pdl_wait)

@@ -41,8 +41,10 @@ def _mdf(spec, m):
     return spec
 
 
-@pytest.mark.parametrize("case,m", [("c1", 1), ("c1", 4), ("fluid", 4), ("tiny", 3), ("long", 2)])
+@pytest.mark.parametrize("case,m", [("c1", 1), ("c1", 4), ("fluid", 4), ("tiny", 3), ("long", 2), ("dense", 3)])
 def test_mdf_one_step_matches_oracle(case, m):
+    """("dense": 2560 beads on 64^2, so more beads reach a tile than one
+    staging pass holds, and the pass kernel evaluates dF twice.)"""
     from tests.test_gpu_parity import _compare_one_step
     if case == "c1":
         spec = synth.world_c1(2)
@@ -51,8 +53,10 @@ def test_mdf_one_step_matches_oracle(case, m):
         spec.f0 = synth.random_populations(np.random.default_rng(4), spec.H, spec.W, 2e-3)
     elif case == "tiny":
         spec = synth.tiny_world(3, side=16, lengths=(6, 5, 3))
-    else:
+    elif case == "long":
         spec = synth.world_random(6, 64, 3, lengths=[80, 70, 12])   # filaments beyond 64 beads
+    else:
+        spec = synth.world_random(8, 64, 40, lengths=[64] * 40)
     _compare_one_step(_mdf(spec, m))
 
 
