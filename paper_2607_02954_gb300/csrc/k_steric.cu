@@ -115,13 +115,32 @@ __device__ void build_segments(const WorldDev& w, int x_lo, int x_hi, int y_lo, 
     hi = bx1;
   }
   const bool valid = by0 + r <= by1 && (split || q == 0);
-  int s0 = 0, len = 0;
+  // every load is issued before any is used (one memory round trip)
+  int s0 = 0, e1 = 0;
   if (valid) {
     const int row = wrap_once(by0 + r, nby) * nbx;
     s0 = bin_off[row + lo];
-    len = bin_off[row + hi + 1] - s0;
+    e1 = bin_off[row + hi + 1];
   }
-  int incl = len;
+  // the box spans at most 8 bin columns (tile + 2 R + 3 <= 51 cells) and
+  // 16 bin rows; lane (rr, cc) = (lane / 8, lane % 8) covers 4 rows per round
+  int mlo[4], mhi[4];
+  if (max_count) {
+    const int ncol = bx1 - bx0 + 1, nrow = by1 - by0 + 1;
+    const int cc = lane & 7;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int rr = (lane >> 3) + 4 * k;
+      mlo[k] = 0;
+      mhi[k] = 0;
+      if (rr < nrow && cc < ncol) {
+        const int bin = wrap_once(by0 + rr, nby) * nbx + wrap_once(bx0 + cc, nbx);
+        mlo[k] = bin_off[bin];
+        mhi[k] = bin_off[bin + 1];
+      }
+    }
+  }
+  int incl = e1 - s0;
   for (int o = 1; o < 32; o <<= 1) {
     const int y = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += y;
@@ -130,17 +149,9 @@ __device__ void build_segments(const WorldDev& w, int x_lo, int x_hi, int y_lo, 
   s_pre[lane + 1] = incl;
   if (lane == 0) s_pre[0] = 0;
   if (max_count) {
-    // the box spans at most 8 bin columns (tile + 2 R + 3 <= 51 cells) and
-    // 16 bin rows; lane (rr, cc) = (lane / 8, lane % 8) covers 4 rows per round
     int m = 0;
-    const int ncol = bx1 - bx0 + 1, nrow = by1 - by0 + 1;
-    const int cc = lane & 7;
-    for (int rr = lane >> 3; rr < nrow; rr += 4) {
-      if (cc < ncol) {
-        const int bin = wrap_once(by0 + rr, nby) * nbx + wrap_once(bx0 + cc, nbx);
-        m = max(m, bin_off[bin + 1] - bin_off[bin]);
-      }
-    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) m = max(m, mhi[k] - mlo[k]);
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) *max_count = m;
   }
