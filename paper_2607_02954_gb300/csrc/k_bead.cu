@@ -611,6 +611,9 @@ __global__ void __launch_bounds__(kBeadChunk) k_bin_scatter(const WorldDev* __re
   const int lane = threadIdx.x & 31;
   const bool valid = i < w.N;
   const int bin = valid ? w.bead_bin[i] : -1 - lane;
+  // the record is loaded before the cursor atomic, so its latency overlaps
+  const float4 p = valid ? w.pos[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  const float2 fe = valid ? w.fel[i] : make_float2(0.0f, 0.0f);
   const unsigned peers = __match_any_sync(0xffffffffu, bin);
   const int leader = __ffs(peers) - 1;
   int base = 0;
@@ -618,8 +621,8 @@ __global__ void __launch_bounds__(kBeadChunk) k_bin_scatter(const WorldDev* __re
   base = __shfl_sync(0xffffffffu, base, leader);
   if (valid) {
     const int slot = base + __popc(peers & ((1u << lane) - 1u));
-    w.spos[slot] = w.pos[i];
-    w.sfel[slot] = w.fel[i];
+    w.spos[slot] = p;
+    w.sfel[slot] = fe;
     w.sid[slot] = i;
     if (w.bead_slot) w.bead_slot[i] = slot;   // direct forcing: U_s goes to the bead's slot
   }
