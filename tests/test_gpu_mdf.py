@@ -41,10 +41,12 @@ def _mdf(spec, m):
     return spec
 
 
-@pytest.mark.parametrize("case,m", [("c1", 1), ("c1", 4), ("fluid", 4), ("tiny", 3), ("long", 2), ("dense", 3)])
+@pytest.mark.parametrize("case,m", [("c1", 1), ("c1", 4), ("fluid", 4), ("tiny", 3), ("long", 2), ("dense", 3),
+                                    ("ragged", 2)])
 def test_mdf_one_step_matches_oracle(case, m):
     """("dense": 2560 beads on 64^2, so more beads reach a tile than one
-    staging pass holds, and the pass kernel evaluates dF twice.)"""
+    staging pass holds, and the pass kernel evaluates dF twice; "ragged":
+    a 40 x 72 grid, whose last tile column and row are partial.)"""
     from tests.test_gpu_parity import _compare_one_step
     if case == "c1":
         spec = synth.world_c1(2)
@@ -55,8 +57,10 @@ def test_mdf_one_step_matches_oracle(case, m):
         spec = synth.tiny_world(3, side=16, lengths=(6, 5, 3))
     elif case == "long":
         spec = synth.world_random(6, 64, 3, lengths=[80, 70, 12])   # filaments beyond 64 beads
-    else:
+    elif case == "dense":
         spec = synth.world_random(8, 64, 40, lengths=[64] * 40)
+    else:
+        spec = synth.world_random(9, (40, 72), 6)
     _compare_one_step(_mdf(spec, m))
 
 
