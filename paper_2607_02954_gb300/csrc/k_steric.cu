@@ -20,10 +20,12 @@
 // Beads are sorted by 8x8-cell bins in row-major order, so the beads that
 // can reach a tile lie in a few contiguous segments of the sorted arrays,
 // one per bin row (two where the row range wraps around the periodic edge).
-// Grid windows and bead records are staged in shared memory with cp.async,
-// every copy in flight at once, and all arithmetic reads shared memory.
-// The staged beads whose stencil reaches the tile are listed first (a
-// block-wide compaction), so the per-bead arithmetic runs on full warps.
+// The force kernel stages grid windows and bead records in shared memory
+// with cp.async, every copy in flight at once, and lists the staged beads
+// whose stencil reaches the tile first (a block-wide compaction), so its
+// per-bead arithmetic runs on full warps.  The deposit, whose per-bead work
+// is 16 atomics, reads each record straight into registers and lets the
+// beads that miss the region drop out.
 //
 // Both kernels are compiled for each filter half width R (1..8) so that the
 // filter loops unroll with the taps in registers; a launch uses the largest R
@@ -49,7 +51,6 @@ namespace {
 constexpr int kMaxSeg = 32;
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kDepCap = 640;              // bead records staged per pass (deposit)
 constexpr int kForceCap = 640;             // bead records staged per pass (force)
 constexpr int kAx = kTile + 6;             // force accumulator edge: the tile and 3 halo cells a side
 constexpr int kWin = kTile + 8;            // rho_bar window edge: the tile and 4 cells a side
@@ -239,10 +240,8 @@ __global__ void __launch_bounds__(kThreads, 8) k_deposit_x(const WorldDev* __res
   pdl_wait();
   using G = Geo<R>;
   __shared__ __align__(16) int acc[G::kDY * G::kDX];
-  __shared__ __align__(16) float4 sp[kDepCap];
-  __shared__ int list[kDepCap];
   __shared__ float tap_s[G::kTaps];
-  __shared__ int s_start[kMaxSeg], s_pre[kMaxSeg + 1], s_maxc, s_cnt;
+  __shared__ int s_start[kMaxSeg], s_pre[kMaxSeg + 1], s_maxc;
   __shared__ int red[kWarps];
   const int2 it = kSingle ? single_tile_item(w1) : items[blockIdx.x];
   const WorldDev& w = kSingle ? w1 : worlds[it.x];
@@ -263,7 +262,6 @@ __global__ void __launch_bounds__(kThreads, 8) k_deposit_x(const WorldDev* __res
   if (warp == 0) build_segments(w, x0 - wR - 2, x0 + tw + wR, y0 - 2, y0 + th, s_start, s_pre, &s_maxc);
   if (warp == 1 && lane < G::kTaps) tap_s[lane] = padded_tap<R>(w, wR, lane);
   for (int c = tid; c < G::kDY * G::kDX / 4; c += kThreads) reinterpret_cast<int4*>(acc)[c] = make_int4(0, 0, 0, 0);
-  if (tid == 0) s_cnt = 0;
   __syncthreads();
   const int total = s_pre[kMaxSeg];
   if (total == 0) {
@@ -284,51 +282,41 @@ __global__ void __launch_bounds__(kThreads, 8) k_deposit_x(const WorldDev* __res
   // bead adds at most 1/4: the cell sum is below the largest bin count
   const int k = fix_exponent((float)s_maxc + 1.0f);
   const float scale = pow2f(k);
-  for (int c0 = 0; c0 < total; c0 += kDepCap) {
-    const int n = min(kDepCap, total - c0);
-    for (int v = tid; v < n; v += kThreads) cp_async16(&sp[v], &spos[seg_slot(c0 + v, s_start, s_pre)]);
-    cp_async_wait_all();
-    __syncthreads();
-    for (int v0 = 0; v0 < n; v0 += kThreads) {
-      const int v = v0 + tid;
-      bool keep = false;
-      int rx = 0, ry = 0;
-      if (v < n) {
-        const float4 p = sp[v];
-        rx = cell_x(p) - cx0;
-        ry = cell_y(p) - y0;
-        keep = true;
-        if (!full_x) {
-          rx = image_lo(rx, W, wR + 2);
-          keep = rx <= tw + wR;
-        }
-        if (!full_y) {
-          ry = image_lo(ry, H, 2);
-          keep = keep && ry <= th;
-        }
-      }
-      list_push(keep, pack_code(v, rx, ry), list, &s_cnt);
+  // each thread deposits the beads v = tid, tid + 256, ... of the segments
+  // straight from the bin-ordered records, two loads in flight at a time;
+  // a bead whose stencil misses the region adds nothing
+  auto deposit = [&](const float4 p) {
+    int rx = cell_x(p) - cx0, ry = cell_y(p) - y0;
+    bool keep = true;
+    if (!full_x) {
+      rx = image_lo(rx, W, wR + 2);
+      keep = rx <= tw + wR;
     }
-    __syncthreads();
-    const int cnt = s_cnt;
-    for (int q = tid; q < cnt; q += kThreads) {
-      const int code = list[q];
-      const float4 p = sp[code_slot(code)];
-      const int rx = code_rx(code), ry = code_ry(code);
-      float wx[4], wy[4];
-      peskin4(p.x, wx);
-      peskin4(p.y, wy);
-      int* base = acc + (ry + 2) * G::kDX + rx - 1 + oxe;
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const float sy = wy[b] * scale;
-#pragma unroll
-        for (int a = 0; a < 4; ++a) atomicAdd(base + b * G::kDX + a, __float2int_rn(wx[a] * sy));
-      }
+    if (!full_y) {
+      ry = image_lo(ry, H, 2);
+      keep = keep && ry <= th;
     }
-    __syncthreads();
-    if (tid == 0) s_cnt = 0;
+    if (!keep) return;
+    float wx[4], wy[4];
+    peskin4(p.x, wx);
+    peskin4(p.y, wy);
+    int* base = acc + (ry + 2) * G::kDX + rx - 1 + oxe;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const float sy = wy[b] * scale;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) atomicAdd(base + b * G::kDX + a, __float2int_rn(wx[a] * sy));
+    }
+  };
+  for (int v0 = tid; v0 < total; v0 += 2 * kThreads) {
+    const int v1 = v0 + kThreads;
+    const float4 p0 = spos[seg_slot(v0, s_start, s_pre)];
+    float4 p1 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (v1 < total) p1 = spos[seg_slot(v1, s_start, s_pre)];
+    deposit(p0);
+    if (v1 < total) deposit(p1);
   }
+  __syncthreads();
   if (full_x || full_y) {
     // fold the stencil cells that wrapped around an axis the region covers whole
     for (int c = tid; c < G::kDY * G::kDX; c += kThreads) {
