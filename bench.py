@@ -46,7 +46,7 @@ if ROOT not in sys.path:
 STAGES = [("pbd", 0), ("bin_scan", 1), ("bin_scatter", 2), ("deposit_x", 3), ("force_lbm", 7), ("interp_advance", 6)]
 KERNELS_PER_STEP = 7
 GRAPH_STEPS = 16   # mc_step replays graphs of 16 steps: PBD, then 15 x (previous advance + PBD), 16 x (scan (2),
-                   # scatter, deposit, force + LBM), and the last advance = 97 kernels; leftover steps run 7 each
+                   # scatter, deposit, force + LBM), and the last advance = 97 kernels
 
 
 def mdf_launches(steps: int, m: int) -> int:
@@ -57,7 +57,11 @@ def mdf_launches(steps: int, m: int) -> int:
 
 
 def graph_launches(steps: int) -> int:
-    return (steps // GRAPH_STEPS) * (2 + GRAPH_STEPS * 6 - 1) + (steps % GRAPH_STEPS) * KERNELS_PER_STEP
+    """Kernels of a run of `steps` steps: 16-step graphs, then the leftover r steps in the same fused
+    order (r PBDs, 5 r of scan (2), scatter, deposit and force + LBM, one advance; one step alone runs
+    the seven kernels of the six stages)."""
+    r = steps % GRAPH_STEPS
+    return (steps // GRAPH_STEPS) * (GRAPH_STEPS * 6 + 1) + (6 * r + 1 if r else 0)
 # k_force_lbm, the dominant kernel: per cell read f 36 + rho_x 4, write f' 36 + u 8;
 # per bead read the binned record (position 16, F_el 8, id 4), write F_s 8
 FORCE_LBM_BYTES_PER_CELL = 84
@@ -327,7 +331,7 @@ def bench_batched(args):
                        "description": "1024 worlds, side ~U{64,128,256}, 1-64 filaments x 8-64 beads (log-uniform)"},
             "plain_per_world": {"value": plain, "ms_per_step": ms_plain / plain_steps,
                                 "launches_per_step": len(worlds) * KERNELS_PER_STEP},
-            "batched_over_plain": batched / plain, "gpu_launches": args.steps * KERNELS_PER_STEP,
+            "batched_over_plain": batched / plain, "gpu_launches": graph_launches(args.steps),
             "clocks": clk.summary()}
 
 
