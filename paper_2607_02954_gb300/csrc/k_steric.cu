@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_deposit_x(const WorldDev* __res
   __shared__ __align__(16) int acc[G::kDY * G::kDX];
   __shared__ float tap_s[G::kTaps];
   __shared__ int s_start[kMaxSeg], s_pre[kMaxSeg + 1], s_maxc;
-  __shared__ int red[kWarps];
+  __shared__ float red[kWarps];
   const int2 it = kSingle ? single_tile_item(w1) : items[blockIdx.x];
   const WorldDev& w = kSingle ? w1 : worlds[it.x];
   const int W = w.W, H = w.H, wR = w.R, ntx = w.ntx, nty = w.nty;
@@ -334,17 +334,10 @@ __global__ void __launch_bounds__(kThreads, 8) k_deposit_x(const WorldDev* __res
   }
   const float inv = pow2f(-k);
   const int col0 = x0 - cx0 + oxe;              // accumulator column of tile column 0
-  int vmax = 0;
-  for (int c = tid; c < th * kTile; c += kThreads) {
-    const int ly = c >> 5, lx = c & 31;
-    if (lx < tw) {
-      const int v = acc[(ly + 3) * G::kDX + col0 + lx];
-      vmax = max(vmax, v);
-      if (store_fields) rho_s_out[(size_t)(y0 + ly) * W + x0 + lx] = (float)v * inv;
-    }
-  }
-  vmax = block_max(vmax, red);
-  if (tid == 0) tile_max[tile] = (float)vmax * inv;
+  // the tile's largest rho_s, and rho_s itself when asked for, come with the
+  // x pass (the largest converted sum is the converted largest sum: the
+  // conversion is monotone, and every sum is non-negative)
+  float vmax = 0.0f;
   // x pass with the fixed-point scale folded into the taps (a power of two:
   // the same products as converting first)
   float tp[G::kTaps];
@@ -371,9 +364,22 @@ __global__ void __launch_bounds__(kThreads, 8) k_deposit_x(const WorldDev* __res
         for (int m = 0; m < G::kTaps; ++m) sacc = fmaf(tp[m], v[j + m], sacc);
         o[j] = sacc;
       }
-      *reinterpret_cast<float4*>(rho_x + (size_t)(y0 + ly) * W + x0 + 4 * s) = make_float4(o[0], o[1], o[2], o[3]);
+      const size_t c = (size_t)(y0 + ly) * W + x0 + 4 * s;
+      *reinterpret_cast<float4*>(rho_x + c) = make_float4(o[0], o[1], o[2], o[3]);
+      // the strip's own cells are v[R .. R + 3]
+      vmax = fmaxf(fmaxf(v[R], v[R + 1]), fmaxf(v[R + 2], v[R + 3]));
+      if (store_fields)
+        *reinterpret_cast<float4*>(rho_s_out + c) = make_float4(v[R] * inv, v[R + 1] * inv, v[R + 2] * inv, v[R + 3] * inv);
     }
   } else {
+    for (int c = tid; c < th * kTile; c += kThreads) {
+      const int ly = c >> 5, lx = c & 31;
+      if (lx < tw) {
+        const float v = (float)acc[(ly + 3) * G::kDX + col0 + lx];
+        vmax = fmaxf(vmax, v);
+        if (store_fields) rho_s_out[(size_t)(y0 + ly) * W + x0 + lx] = v * inv;
+      }
+    }
     for (int c = tid; c < th * tw; c += kThreads) {
       const int ly = c / tw, lx = c - ly * tw;
       const int* r = acc + (ly + 3) * G::kDX + oxe;
@@ -383,6 +389,8 @@ __global__ void __launch_bounds__(kThreads, 8) k_deposit_x(const WorldDev* __res
       rho_x[(size_t)(y0 + ly) * W + x0 + lx] = sacc;
     }
   }
+  vmax = block_max(vmax, red);
+  if (tid == 0) tile_max[tile] = vmax * inv;
 }
 
 // ---------------------------------------------------------------------------
