@@ -291,6 +291,14 @@ __device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, 
   const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   float4 P0 = hb0 ? w.pos[b0 + i0] : z4;
   float4 P1 = hb1 ? w.pos[b0 + i1] : z4;
+  // the filament's own inputs first: their loads and the drive's sines
+  // overlap the advance's gathers
+  float th0 = he0 ? w.theta[e0 + i0] : 0.0f;
+  float th1 = he1 ? w.theta[e0 + i1] : 0.0f;
+  const float L0 = he0 ? (kExt ? rest_length(w, e0 + i0, t) : w.L_rest[e0 + i0]) : 1.0f;
+  const float L1 = he1 ? (kExt ? rest_length(w, e0 + i1, t) : w.L_rest[e0 + i1]) : 1.0f;
+  const float thr0 = hj0 ? drive_angle(w.drive[j0 + i0], t) : 0.0f;
+  const float thr1 = hj1 ? drive_angle(w.drive[j0 + i1], t) : 0.0f;
   if (kMode == 1) {
     // a8 of the previous step for the lane's beads, then this step's PBD from X^n
     long long q = 0;
@@ -316,12 +324,6 @@ __device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, 
       P1 = advance_pos(w, P1, U.x, U.y);
     }
   }
-  float th0 = he0 ? w.theta[e0 + i0] : 0.0f;
-  float th1 = he1 ? w.theta[e0 + i1] : 0.0f;
-  const float L0 = he0 ? (kExt ? rest_length(w, e0 + i0, t) : w.L_rest[e0 + i0]) : 1.0f;
-  const float L1 = he1 ? (kExt ? rest_length(w, e0 + i1, t) : w.L_rest[e0 + i1]) : 1.0f;
-  const float thr0 = hj0 ? drive_angle(w.drive[j0 + i0], t) : 0.0f;
-  const float thr1 = hj1 ? drive_angle(w.drive[j0 + i1], t) : 0.0f;
   float4 Pn;   // bead 2l + 2
   Pn.x = __shfl_down_sync(kAll, P0.x, 1);
   Pn.y = __shfl_down_sync(kAll, P0.y, 1);
