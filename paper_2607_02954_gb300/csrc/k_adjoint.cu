@@ -602,16 +602,20 @@ __global__ void k_set_counter(long long* t, long long v, unsigned* fel_max) {
 // Launchers (one world).
 // ---------------------------------------------------------------------------
 static int blocks(int n) { return (n + 255) / 256; }
+// the per-bead adjoint kernels run 64-thread blocks: a few thousand beads
+// then spread over several times more SMs
+constexpr int kAdjBeadThreads = 64;
+static int bead_blocks(int n) { return (n + kAdjBeadThreads - 1) / kAdjBeadThreads; }
 
 void launch_adj_step(const Plan& p, const WorldDev& h, AdjDev a, int src_parity, cudaStream_t s) {
   const WorldDev* wd = p.d_worlds;
   const int HW = h.H * h.W;
   // (u_bar and Q are cleared by the caller before each step)
-  if (h.N) k_adj_spread_u<<<blocks(h.N), 256, 0, s>>>(wd, a);
+  if (h.N) k_adj_spread_u<<<bead_blocks(h.N), kAdjBeadThreads, 0, s>>>(wd, a);
   k_adj_lbm<<<blocks(HW), 256, 0, s>>>(wd, a, src_parity);
-  if (h.N) k_adj_bead_a<<<blocks(h.N), 256, 0, s>>>(wd, a);
+  if (h.N) k_adj_bead_a<<<bead_blocks(h.N), kAdjBeadThreads, 0, s>>>(wd, a);
   k_adj_rho_blur<<<h.ntx * h.nty, 256, 0, s>>>(wd, a);
-  if (h.N) k_adj_bead_b<<<blocks(h.N), 256, 0, s>>>(wd, a);
+  if (h.N) k_adj_bead_b<<<bead_blocks(h.N), kAdjBeadThreads, 0, s>>>(wd, a);
   if (p.n_fil_items) {
     const int mb = (p.max_B + 3) & ~3;
     const size_t smem = adj_pbd_smem_per_filament(mb, h.n_pbd);

@@ -796,10 +796,28 @@ __global__ void k_cells_out(const float4* __restrict__ pos, int N, int W, int* c
 // ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
-static int pbd_warps_per_block(int maxB) {
+// Warps (filaments) per block: at most 8, at most what 48 KB of shared
+// memory holds, and few enough that a small launch still spreads over every
+// SM (each warp's filament is a serial chain; warps sharing an SM's
+// schedulers only delay one another).
+static int num_sms() {
+  // first asked by kernel_setup, outside any stream capture
+  static const int sms = [] {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+  }();
+  return sms;
+}
+
+static int pbd_warps_per_block(int maxB, int n_items) {
+  const int sms = num_sms();
   const int per_warp = maxB * kPbdFloatsPerBead * (int)sizeof(float);
   int wpb = (48 * 1024) / per_warp;
   if (wpb > 8) wpb = 8;
+  const int spread = (n_items + sms - 1) / sms;
+  if (wpb > spread) wpb = spread;
   if (wpb < 1) wpb = 1;
   return wpb;
 }
@@ -807,7 +825,7 @@ static int pbd_warps_per_block(int maxB) {
 void launch_pbd(const Plan& p, cudaStream_t s) {
   if (p.n_fil_items == 0) return;
   const int mb = (p.max_B + 3) & ~3;
-  const int wpb = pbd_warps_per_block(mb);
+  const int wpb = pbd_warps_per_block(mb, p.n_fil_items);
   // filaments of at most 64 beads need no shared memory
   const size_t smem = p.max_B <= 64 ? 0 : (size_t)wpb * mb * kPbdFloatsPerBead * sizeof(float);
   const int grid = (p.n_fil_items + wpb - 1) / wpb;
@@ -824,7 +842,7 @@ void launch_pbd(const Plan& p, cudaStream_t s) {
 void launch_pbd_mdf(const Plan& p, cudaStream_t s) {
   if (p.n_fil_items == 0) return;
   const int mb = (p.max_B + 3) & ~3;
-  const int wpb = pbd_warps_per_block(mb);
+  const int wpb = pbd_warps_per_block(mb, p.n_fil_items);
   const size_t smem = p.max_B <= 64 ? 0 : (size_t)wpb * mb * kPbdFloatsPerBead * sizeof(float);
   const int grid = (p.n_fil_items + wpb - 1) / wpb;
   auto kern = p.n_worlds == 1 ? k_pbd<true, 2, true> : k_pbd<true, 2, false>;
@@ -836,7 +854,7 @@ void launch_pbd_mdf(const Plan& p, cudaStream_t s) {
 void launch_advance_pbd(const Plan& p, cudaStream_t s) {
   if (p.n_fil_items == 0) return;
   const int mb = (p.max_B + 3) & ~3;
-  const int wpb = pbd_warps_per_block(mb);
+  const int wpb = pbd_warps_per_block(mb, p.n_fil_items);
   const size_t smem = p.max_B <= 64 ? 0 : (size_t)wpb * mb * kPbdFloatsPerBead * sizeof(float);
   const int grid = (p.n_fil_items + wpb - 1) / wpb;
   const bool one = p.n_worlds == 1;
@@ -850,6 +868,7 @@ void launch_advance_pbd(const Plan& p, cudaStream_t s) {
 void kernel_setup() {
   static std::once_flag once;
   std::call_once(once, [] {
+    num_sms();
     const int most = 227 * 1024;
     for (auto f : {k_pbd<false, 0, false>, k_pbd<true, 0, false>, k_pbd<false, 1, false>, k_pbd<true, 1, false>,
                    k_pbd<true, 2, false>, k_pbd<false, 0, true>, k_pbd<true, 0, true>, k_pbd<false, 1, true>,
