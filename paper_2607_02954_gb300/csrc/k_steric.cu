@@ -793,7 +793,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_force_lbm(const WorldDev* __res
   const TileBox tb = tile_box(w, it.y);
   const bool layered = w.layers == 2;
   if (!layered) prefetch_populations(w, tb);
-  const int k = force_tile<R>(sm, w, (tb.y0 / kTile) * w.ntx + tb.x0 / kTile, tb, 0, 0);
+  const int tile = (tb.y0 / kTile) * w.ntx + tb.x0 / kTile;
+  int k = 40;
+  if (!kSingle && !layered && w.tile_rho_max[tile] == 0.0f) {
+    // no bead puts weight on this tile's cells (its largest rho_s is 0), so
+    // it owns no bead and every spread term on it is zero: F = 0, as the
+    // force pass would give.  Sparse batched worlds have many such tiles.
+    tile_clear(sm.wk);
+  } else {
+    k = force_tile<R>(sm, w, tile, tb, 0, 0);
+  }
   // two-layer worlds: F_s only; their layer spread and collision follow in their own kernels
   if (!layered) tile_lbm(sm.wk, w, tb, k);
 }
