@@ -42,7 +42,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-# the stages one step runs, with their mc_step_stage ids (the scan stage is two kernels)
+# the stages one step runs, with their mc_step_stage ids (the scan stage is two kernels, one when every
+# world fits one scan block)
 STAGES = [("pbd", 0), ("bin_scan", 1), ("bin_scatter", 2), ("deposit_x", 3), ("force_lbm", 7), ("interp_advance", 6)]
 KERNELS_PER_STEP = 7
 GRAPH_STEPS = 16   # mc_step replays graphs of 16 steps: PBD, then 15 x (previous advance + PBD), 16 x (scan (2),
@@ -56,12 +57,18 @@ def mdf_launches(steps: int, m: int) -> int:
     return steps * (11 + m)
 
 
-def graph_launches(steps: int) -> int:
+def scan_kernels(specs) -> int:
+    """The bin-offset scan is one kernel when every world's bins fit one 1024-bin scan block, else two."""
+    return 1 if all((sp.H // 8) * (sp.W // 8) <= 1024 for sp in specs) else 2
+
+
+def graph_launches(steps: int, scans: int = 2) -> int:
     """Kernels of a run of `steps` steps: 16-step graphs, then the leftover r steps in the same fused
-    order (r PBDs, 5 r of scan (2), scatter, deposit and force + LBM, one advance; one step alone runs
-    the seven kernels of the six stages)."""
+    order (r PBDs, r x (scan, scatter, deposit, force + LBM), one advance; one step alone runs the
+    six stages)."""
+    per = 4 + scans   # PBD, scan, scatter, deposit, force + LBM per step, plus the last advance
     r = steps % GRAPH_STEPS
-    return (steps // GRAPH_STEPS) * (GRAPH_STEPS * 6 + 1) + (6 * r + 1 if r else 0)
+    return (steps // GRAPH_STEPS) * (GRAPH_STEPS * per + 1) + (per * r + 1 if r else 0)
 # k_force_lbm, the dominant kernel: per cell read f 36 + rho_x 4, write f' 36 + u 8;
 # per bead read the binned record (position 16, F_el 8, id 4), write F_s 8
 FORCE_LBM_BYTES_PER_CELL = 84
@@ -330,8 +337,8 @@ def bench_batched(args):
             "config": {"workload": "c4", "worlds": len(specs), "beads": n_beads, "cells": n_cells,
                        "description": "1024 worlds, side ~U{64,128,256}, 1-64 filaments x 8-64 beads (log-uniform)"},
             "plain_per_world": {"value": plain, "ms_per_step": ms_plain / plain_steps,
-                                "launches_per_step": len(worlds) * KERNELS_PER_STEP},
-            "batched_over_plain": batched / plain, "gpu_launches": graph_launches(args.steps),
+                                "launches_per_step": len(worlds) * (KERNELS_PER_STEP - 2 + scan_kernels(specs))},
+            "batched_over_plain": batched / plain, "gpu_launches": graph_launches(args.steps, scan_kernels(specs)),
             "clocks": clk.summary()}
 
 
@@ -576,7 +583,8 @@ def main():
                    "l2": "state 1.8 GB > L2: no flush needed" if C >= 4096 * 4096 else "state may fit in L2; per-step timing includes no flush"},
         "e2e": {"value": e2e_val, "unit": "particle-steps/s", "steps": e2e_steps,
                 "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps},
-        "gpu_launches": mdf_launches(args.steps, args.mdf_iters) if mdf else graph_launches(args.steps),
+        "gpu_launches": (mdf_launches(args.steps, args.mdf_iters) - (2 - scan_kernels([spec])) * args.steps if mdf
+                         else graph_launches(args.steps, scan_kernels([spec]))),
         "roofline": None if mdf else {
             "bound": "hbm", "kernel": "k_force_lbm", "achieved": top_gbs, "peak": hbm_peak, "unit": "GB/s",
             "frac": top_gbs / hbm_peak, "peak_kind": peak_kind,

@@ -54,8 +54,11 @@ __global__ void __launch_bounds__(256) k_scan_sums(const WorldDev* __restrict__ 
 }
 
 template <bool kSingle>
+// With book (plans whose worlds fit one scan block each, where k_scan_sums
+// is not launched: a first block has no earlier blocks to add up) it also
+// keeps k_scan_sums' step-counter bookkeeping.
 __global__ void __launch_bounds__(256) k_scan_apply(const WorldDev* __restrict__ worlds,
-                                                    const int2* __restrict__ items,
+                                                    const int2* __restrict__ items, int book, int inc_t,
                                                     const __grid_constant__ WorldDev w1) {
   pdl_trigger();
   pdl_wait();
@@ -63,6 +66,11 @@ __global__ void __launch_bounds__(256) k_scan_apply(const WorldDev* __restrict__
   __shared__ int warp_tot[8];
   const int2 it = kSingle ? make_int2(0, (int)blockIdx.x) : items[blockIdx.x];
   const WorldDev& w = kSingle ? w1 : worlds[it.x];
+  if (book && it.y == 0 && threadIdx.x == 0) {
+    const long long t = *w.t + inc_t;
+    if (inc_t) *w.t = t;
+    w.fel_max[(t + 1) & 1] = 0u;
+  }
   int pre = 0;
   for (int k = threadIdx.x; k < it.y; k += blockDim.x) pre += w.chunk_sum[k];
   pre = block_sum_256(pre, red);
@@ -134,12 +142,14 @@ __global__ void __launch_bounds__(kCellChunk) k_lbm(const WorldDev* __restrict__
 // Launchers and the step sequence.
 // ---------------------------------------------------------------------------
 void launch_bin_scan(const Plan& p, cudaStream_t s, int inc_t) {
+  // worlds of one scan block each need no block sums: one kernel
+  const int book = p.one_chunk ? 1 : 0;
   if (p.n_worlds == 1) {   // integer work only: the single-world path cannot change a result
-    launch_pdl(k_scan_sums<true>, p.n_scan_items, 256, 0, s, p.d_worlds, p.d_scan_items, inc_t, p.h_world0);
-    launch_pdl(k_scan_apply<true>, p.n_scan_items, 256, 0, s, p.d_worlds, p.d_scan_items, p.h_world0);
+    if (!book) launch_pdl(k_scan_sums<true>, p.n_scan_items, 256, 0, s, p.d_worlds, p.d_scan_items, inc_t, p.h_world0);
+    launch_pdl(k_scan_apply<true>, p.n_scan_items, 256, 0, s, p.d_worlds, p.d_scan_items, book, inc_t, p.h_world0);
   } else {
-    launch_pdl(k_scan_sums<false>, p.n_scan_items, 256, 0, s, p.d_worlds, p.d_scan_items, inc_t, p.h_world0);
-    launch_pdl(k_scan_apply<false>, p.n_scan_items, 256, 0, s, p.d_worlds, p.d_scan_items, p.h_world0);
+    if (!book) launch_pdl(k_scan_sums<false>, p.n_scan_items, 256, 0, s, p.d_worlds, p.d_scan_items, inc_t, p.h_world0);
+    launch_pdl(k_scan_apply<false>, p.n_scan_items, 256, 0, s, p.d_worlds, p.d_scan_items, book, inc_t, p.h_world0);
   }
 }
 

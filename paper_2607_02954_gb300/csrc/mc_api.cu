@@ -140,6 +140,7 @@ mc_status build_plan(mc_world* const* ws, int n, cudaStream_t s, Plan& out) {
   p.any_mdf = false;
   p.max_mdf = 0;
   p.any_ext = false;
+  p.one_chunk = true;
   std::vector<int2> fil, bead, tile, cell, scan;
   std::vector<WorldDev> table(n);
   for (int k = 0; k < n; ++k) {
@@ -151,6 +152,7 @@ mc_status build_plan(mc_world* const* ws, int n, cudaStream_t s, Plan& out) {
     p.any_mdf = p.any_mdf || w->h.ib == 1;
     p.max_mdf = std::max(p.max_mdf, w->h.mdf_iters);
     p.any_ext = p.any_ext || w->h.layers == 2 || w->h.observe || w->h.has_ldrive || w->h.ib == 1;
+    p.one_chunk = p.one_chunk && w->h.n_chunks <= 1;
     for (int f = 0; f < w->h.n_fil; ++f) fil.push_back(make_int2(k, f));
     const int nb = std::max(w->h.N, 1);
     for (int b = 0; b < nb; b += mc::kBeadChunk) bead.push_back(make_int2(k, b));

@@ -128,6 +128,7 @@ struct Plan {
   bool any_mdf = false;          // some world couples by direct forcing (ib == 1)
   int max_mdf = 0;               // most MDF passes of a world
   bool any_ext = false;          // some world has two layers, observables, a rest-length drive or direct forcing
+  bool one_chunk = false;        // every world's bins fit one scan block (its offsets need no block sums)
   int n_fil_items = 0, n_bead_items = 0, n_tile_items = 0, n_cell_items = 0, n_scan_items = 0;
   WorldDev* d_worlds = nullptr;  // [n_worlds]
   int2* d_fil_items = nullptr;   // (world, filament)
