@@ -8,8 +8,10 @@ namespace mc {
 // ---------------------------------------------------------------------------
 // a2: exclusive prefix sum of the per-bin bead counts, in blocks of
 // kScanChunk bins: k_scan_sums adds up each block, k_scan_apply offsets each
-// block by the sum of the world's earlier blocks and scans it.  Also resets
-// the counts for the next step and primes the scatter cursors.
+// block by the sum of the world's earlier blocks and scans it.  When every
+// world of a plan fits one block, k_scan_apply runs alone (one kernel, no
+// block sums), else both run.  Also resets the counts for the next step and
+// primes the scatter cursors.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int block_sum_256(int v, int* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -53,10 +55,10 @@ __global__ void __launch_bounds__(256) k_scan_sums(const WorldDev* __restrict__ 
   if (threadIdx.x == 0) w.chunk_sum[it.y] = s;
 }
 
-template <bool kSingle>
 // With book (plans whose worlds fit one scan block each, where k_scan_sums
 // is not launched: a first block has no earlier blocks to add up) it also
 // keeps k_scan_sums' step-counter bookkeeping.
+template <bool kSingle>
 __global__ void __launch_bounds__(256) k_scan_apply(const WorldDev* __restrict__ worlds,
                                                     const int2* __restrict__ items, int book, int inc_t,
                                                     const __grid_constant__ WorldDev w1) {
@@ -193,7 +195,7 @@ void enqueue_step(const Plan& p, cudaStream_t s) {
     return;
   }
   launch_pbd(p, s);              // a1 + a3 + a2 histogram
-  launch_bin_scan(p, s);         // a2 offsets (two kernels)
+  launch_bin_scan(p, s);         // a2 offsets (one or two kernels)
   launch_bin_scatter(p, s);      // a2 scatter
   launch_deposit_x(p, s, 0);     // a4 + x pass of a5
   launch_force_lbm(p, s);        // y pass of a5 + a6 + a7

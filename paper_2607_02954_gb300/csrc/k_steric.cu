@@ -9,7 +9,8 @@
 // k_deposit_x    deposits rho_s on the tile plus R columns on each side in
 //                shared memory, applies the x pass of the filter and writes
 //                the x-filtered density rho_x of the tile (4 B per cell) and
-//                the tile's largest rho_s.
+//                a bound of the tile's rho_s (its largest deposited sum plus
+//                the rounding the fixed point can hide).
 // k_force_spread loads rho_x on the tile plus 4 + R rows and 4 columns,
 //                applies the y pass (rho_bar on the tile plus 4 cells),
 //                gathers the steric force of every bead whose stencil touches
@@ -231,56 +232,34 @@ __device__ __forceinline__ float padded_tap(const WorldDev& w, int wR, int m) {
 // columns a side (origin x0, oxe = R + 4, so every 4-column strip of the x
 // pass starts on a 16-byte boundary) or, when that would cover the axis
 // more than once, the whole axis (origin 0, oxe = 4, folded).
+//
+// The fixed-point scale 2^k comes from a bound on the cell sums: a cell's
+// 4x4 stencil neighbourhood overlaps at most 2x2 bins and each bead adds at
+// most 1/4, so a cell sum is below the largest bin count near the tile.
+// That bound leaves at least 24 fractional bits up to about one bead per
+// cell.  It is loose (a bead adds 1/16 to a cell on average), so a denser
+// tile (k < 24) deposits twice: the first pass measures the largest sum of
+// the accumulator (plus the rounding its terms can hide), which gives a
+// tight scale for the second.
 // ---------------------------------------------------------------------------
-template <int R, bool kSingle>
-__global__ void __launch_bounds__(kThreads, 8) k_deposit_x(const WorldDev* __restrict__ worlds,
-                                                        const int2* __restrict__ items, int store_fields,
-                                                        const __grid_constant__ WorldDev w1) {
-  pdl_trigger();
-  pdl_wait();
+
+// Geometry of one deposit tile.
+struct DepTile {
+  int W, H, wR, x0, y0, tw, th, cx0, oxe, tile, total;
+  bool full_x, full_y;
+};
+
+// Deposits the tile's beads at scale 2^k into acc (zeroed) and folds the
+// wrapped cells.  Ends with the block synchronised.
+template <int R>
+__device__ __forceinline__ void deposit_accumulate(int* acc, const WorldDev& w, const DepTile& d, int k,
+                                                   const int* s_start, const int* s_pre) {
   using G = Geo<R>;
-  __shared__ __align__(16) int acc[G::kDY * G::kDX];
-  __shared__ float tap_s[G::kTaps];
-  __shared__ int s_start[kMaxSeg], s_pre[kMaxSeg + 1], s_maxc;
-  __shared__ float red[kWarps];
-  const int2 it = kSingle ? single_tile_item(w1) : items[blockIdx.x];
-  const WorldDev& w = kSingle ? w1 : worlds[it.x];
-  const int W = w.W, H = w.H, wR = w.R, ntx = w.ntx, nty = w.nty;
+  const int tid = threadIdx.x;
+  const int W = d.W, H = d.H, wR = d.wR, x0 = d.x0, y0 = d.y0, tw = d.tw, th = d.th;
+  const int cx0 = d.cx0, oxe = d.oxe, total = d.total;
+  const bool full_x = d.full_x, full_y = d.full_y;
   const float4* __restrict__ spos = w.spos;
-  float* __restrict__ rho_x = w.rho_x;
-  float* __restrict__ rho_s_out = w.rho_s;
-  float* __restrict__ tile_max = w.tile_rho_max;
-  const int tx = it.y & 0xffff, ty = it.y >> 16;
-  const int tile = ty * ntx + tx;
-  const int x0 = tx * kTile, y0 = ty * kTile;
-  const int tw = min(kTile, W - x0), th = min(kTile, H - y0);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const bool full_x = W < tw + 2 * wR + 3;
-  const bool full_y = nty == 1;
-  const int cx0 = full_x ? 0 : x0;              // region column origin
-  const int oxe = full_x ? 4 : R + 4;           // accumulator column of region column 0
-  if (warp == 0) build_segments(w, x0 - wR - 2, x0 + tw + wR, y0 - 2, y0 + th, s_start, s_pre, &s_maxc);
-  if (warp == 1 && lane < G::kTaps) tap_s[lane] = padded_tap<R>(w, wR, lane);
-  for (int c = tid; c < G::kDY * G::kDX / 4; c += kThreads) reinterpret_cast<int4*>(acc)[c] = make_int4(0, 0, 0, 0);
-  __syncthreads();
-  const int total = s_pre[kMaxSeg];
-  if (total == 0) {
-    // no bead reaches the region: rho_s, rho_x and the tile maximum are zero
-    // (what the passes below give for an empty accumulator, bitwise)
-    // (tw is a multiple of 8, so each 4-column strip is whole and aligned)
-    const int ly = tid >> 3, s = tid & 7;
-    if (ly < th && 4 * s < tw) {
-      const size_t c = (size_t)(y0 + ly) * W + x0 + 4 * s;
-      const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      *reinterpret_cast<float4*>(rho_x + c) = z;
-      if (store_fields) *reinterpret_cast<float4*>(rho_s_out + c) = z;
-    }
-    if (tid == 0) tile_max[tile] = 0.0f;
-    return;
-  }
-  // a cell's 4x4 stencil neighbourhood overlaps at most 2x2 bins and each
-  // bead adds at most 1/4: the cell sum is below the largest bin count
-  const int k = fix_exponent((float)s_maxc + 1.0f);
   const float scale = pow2f(k);
   // each thread deposits the beads v = tid, tid + 256, ... of the segments
   // straight from the bin-ordered records, two loads in flight at a time;
@@ -332,8 +311,20 @@ __global__ void __launch_bounds__(kThreads, 8) k_deposit_x(const WorldDev* __res
     }
     __syncthreads();
   }
+}
+
+// The x pass of the accumulated sums at scale 2^k, rho_s when asked for,
+// and the tile's bound (see k_deposit_x).
+template <int R>
+__device__ __forceinline__ void deposit_xpass(const int* acc, const WorldDev& w, const DepTile& d, int k,
+                                              const float* tap_s, float* red, int store_fields) {
+  using G = Geo<R>;
+  const int tid = threadIdx.x;
+  const int W = d.W, x0 = d.x0, y0 = d.y0, tw = d.tw, th = d.th, oxe = d.oxe;
+  float* __restrict__ rho_x = w.rho_x;
+  float* __restrict__ rho_s_out = w.rho_s;
   const float inv = pow2f(-k);
-  const int col0 = x0 - cx0 + oxe;              // accumulator column of tile column 0
+  const int col0 = x0 - d.cx0 + oxe;            // accumulator column of tile column 0
   // the tile's largest rho_s, and rho_s itself when asked for, come with the
   // x pass (the largest converted sum is the converted largest sum: the
   // conversion is monotone, and every sum is non-negative)
@@ -343,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_deposit_x(const WorldDev* __res
   float tp[G::kTaps];
 #pragma unroll
   for (int m = 0; m < G::kTaps; ++m) tp[m] = tap_s[m] * inv;
-  if (!full_x) {
+  if (!d.full_x) {
     const int ly = tid >> 3, s = tid & 7;       // row, strip of 4 columns
     if (ly < th && 4 * s < tw) {
       const int4* src = reinterpret_cast<const int4*>(acc + (ly + 3) * G::kDX + 4 * s + oxe - R);
@@ -390,7 +381,83 @@ __global__ void __launch_bounds__(kThreads, 8) k_deposit_x(const WorldDev* __res
     }
   }
   vmax = block_max(vmax, red);
-  if (tid == 0) tile_max[tile] = vmax * inv;
+  // Stored bound of the tile's cell sums of the kernel weights, used for
+  // the fixed-point scales of the spread: the largest deposited sum plus the
+  // largest rounding its terms can hide (half a unit per bead of the
+  // covering bins, at most one term per cell each).  It is 0 exactly when
+  // the covering bins hold no bead (written by the early exit of
+  // k_deposit_x), and then no bead's stencil reaches the tile: the batched
+  // force pass skips such a tile with no effect on any result.
+  if (tid == 0) w.tile_rho_max[d.tile] = (vmax + 0.5f * (float)d.total) * inv;
+}
+
+template <int R, bool kSingle>
+__global__ void __launch_bounds__(kThreads, 8) k_deposit_x(const WorldDev* __restrict__ worlds,
+                                                        const int2* __restrict__ items, int store_fields,
+                                                        const __grid_constant__ WorldDev w1) {
+  pdl_trigger();
+  pdl_wait();
+  using G = Geo<R>;
+  __shared__ __align__(16) int acc[G::kDY * G::kDX];
+  __shared__ float tap_s[G::kTaps];
+  __shared__ int s_start[kMaxSeg], s_pre[kMaxSeg + 1], s_maxc;
+  __shared__ float red[kWarps];
+  const int2 it = kSingle ? single_tile_item(w1) : items[blockIdx.x];
+  const WorldDev& w = kSingle ? w1 : worlds[it.x];
+  DepTile d;
+  d.W = w.W;
+  d.H = w.H;
+  d.wR = w.R;
+  const int ntx = w.ntx;
+  const int tx = it.y & 0xffff, ty = it.y >> 16;
+  d.tile = ty * ntx + tx;
+  d.x0 = tx * kTile;
+  d.y0 = ty * kTile;
+  d.tw = min(kTile, d.W - d.x0);
+  d.th = min(kTile, d.H - d.y0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  d.full_x = d.W < d.tw + 2 * d.wR + 3;
+  d.full_y = w.nty == 1;
+  d.cx0 = d.full_x ? 0 : d.x0;                  // region column origin
+  d.oxe = d.full_x ? 4 : R + 4;                 // accumulator column of region column 0
+  if (warp == 0)
+    build_segments(w, d.x0 - d.wR - 2, d.x0 + d.tw + d.wR, d.y0 - 2, d.y0 + d.th, s_start, s_pre, &s_maxc);
+  if (warp == 1 && lane < G::kTaps) tap_s[lane] = padded_tap<R>(w, d.wR, lane);
+  for (int c = tid; c < G::kDY * G::kDX / 4; c += kThreads) reinterpret_cast<int4*>(acc)[c] = make_int4(0, 0, 0, 0);
+  __syncthreads();
+  d.total = s_pre[kMaxSeg];
+  if (d.total == 0) {
+    // no bead reaches the region: rho_s, rho_x and the tile maximum are zero
+    // (what the passes below give for an empty accumulator, bitwise)
+    // (tw is a multiple of 8, so each 4-column strip is whole and aligned)
+    const int ly = tid >> 3, s = tid & 7;
+    if (ly < d.th && 4 * s < d.tw) {
+      const size_t c = (size_t)(d.y0 + ly) * d.W + d.x0 + 4 * s;
+      const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      *reinterpret_cast<float4*>(w.rho_x + c) = z;
+      if (store_fields) *reinterpret_cast<float4*>(w.rho_s + c) = z;
+    }
+    if (tid == 0) w.tile_rho_max[d.tile] = 0.0f;
+    return;
+  }
+  int k = fix_exponent((float)s_maxc + 1.0f);
+  deposit_accumulate<R>(acc, w, d, k, s_start, s_pre);
+  if (k < 24) {
+    // dense tile: the largest accumulated sum plus the rounding of its terms
+    // (half a unit per bead of the covering bins, at most one term per cell
+    // each) bounds every sum; deposit again at the scale that bound gives
+    int m = 0;
+    for (int c = tid; c < G::kDY * G::kDX; c += kThreads) m = max(m, acc[c]);
+    m = block_max(m, reinterpret_cast<int*>(red));
+    const int k2 = fix_exponent(((float)m + 0.5f * (float)d.total) * pow2f(-k) * 1.0001f);
+    if (k2 > k) {
+      for (int c = tid; c < G::kDY * G::kDX / 4; c += kThreads) reinterpret_cast<int4*>(acc)[c] = make_int4(0, 0, 0, 0);
+      __syncthreads();
+      k = k2;
+      deposit_accumulate<R>(acc, w, d, k, s_start, s_pre);
+    }
+  }
+  deposit_xpass<R>(acc, w, d, k, tap_s, red, store_fields);
 }
 
 // ---------------------------------------------------------------------------
@@ -796,9 +863,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_force_lbm(const WorldDev* __res
   const int tile = (tb.y0 / kTile) * w.ntx + tb.x0 / kTile;
   int k = 40;
   if (!kSingle && !layered && w.tile_rho_max[tile] == 0.0f) {
-    // no bead puts weight on this tile's cells (its largest rho_s is 0), so
-    // it owns no bead and every spread term on it is zero: F = 0, as the
-    // force pass would give.  Sparse batched worlds have many such tiles.
+    // no bead's stencil reaches this tile's cells (the deposit's bound is 0
+    // exactly then), so it owns no bead and the spread has no term on it:
+    // F = 0, as the force pass would give.  Sparse batched worlds have many
+    // such tiles.
     tile_clear(sm.wk);
   } else {
     k = force_tile<R>(sm, w, tile, tb, 0, 0);

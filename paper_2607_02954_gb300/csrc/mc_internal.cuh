@@ -67,7 +67,7 @@ struct WorldDev {
   float* rho_s;           // [H * W] (written only on request)
   float* rho_x;           // [H * W] x-filtered density
   float* rho_b;           // [H * W] (written only on request)
-  float* tile_rho_max;    // [n_tiles] largest rho_s of each tile (fixed-point bound)
+  float* tile_rho_max;    // [n_tiles] bound of each tile's rho_s (largest deposited sum + its rounding; 0 iff no bead reaches the tile)
   long long* t;           // step counter
   unsigned* fel_max;      // [2] largest |F_el| component of the step, by step parity (float bits)
   unsigned* flags;        // watchdog flags
@@ -143,7 +143,7 @@ struct Plan {
 
 // --- stage launchers (one launch covers every world of the plan) ---------
 void launch_pbd(const Plan& p, cudaStream_t s);
-void launch_bin_scan(const Plan& p, cudaStream_t s, int inc_t = 0);      // two kernels
+void launch_bin_scan(const Plan& p, cudaStream_t s, int inc_t = 0);      // one kernel when every world fits one scan block, else two
 void launch_bin_scatter(const Plan& p, cudaStream_t s);
 // a4 + x pass of a5; store_fields also writes rho_s of each tile
 void launch_deposit_x(const Plan& p, cudaStream_t s, int store_fields);

@@ -172,7 +172,7 @@ def place_rows(rng, H, W, n_fil, B, pitch, slot=64):
     (+x or -x) and a random sub-cell offset in [0, 0.5) on both axes."""
     assert B <= slot
     per_row = W // slot
-    rows = H // pitch
+    rows = int(round(H / pitch))
     assert per_row * rows >= n_fil, "world too small for the requested filaments"
     xs, ys, th = [], [], []
     for fidx in range(n_fil):
@@ -257,6 +257,26 @@ def world_rows(side, n_beads, seed=0, B=64, name=None):
     theta0 = rng.normal(0.0, 0.1, J)
     amp, freq, phase = _travelling_wave(rng, lengths)
     return _world(name or f"rows_{side}_{n_beads}", side, side, lengths, x, y, theta,
+                  theta0, amp, freq, phase)
+
+
+def world_dense(side, n_beads, seed=0, B=64, name=None):
+    """World denser than one bead per cell (the paper's scalability runs keep
+    a 256^2 grid and go up to 500k particles, about 7.6 beads per cell):
+    filaments of B beads on a jittered row lattice whose rows are
+    side^2 / n_beads cells apart (below one cell, so rows interleave within a
+    cell), rest angles ~N(0, 0.1) and the same travelling-wave drive as
+    world_rows."""
+    rng = np.random.default_rng(seed)
+    n_fil = n_beads // B
+    assert n_fil * B == n_beads and side % 64 == 0
+    pitch = (side * side) / float(n_beads)
+    lengths = [B] * n_fil
+    x, y, theta = place_rows(rng, side, side, n_fil, B, pitch)
+    _, E, J = _counts(lengths)
+    theta0 = rng.normal(0.0, 0.1, J)
+    amp, freq, phase = _travelling_wave(rng, lengths)
+    return _world(name or f"dense_{side}_{n_beads}", side, side, lengths, x, y, theta,
                   theta0, amp, freq, phase)
 
 

@@ -160,6 +160,16 @@ def test_one_step_edge_cases(case):
     _compare_one_step(spec)
 
 
+@pytest.mark.parametrize("n_beads", [2 ** 18, 2 ** 19])
+def test_one_step_above_one_bead_per_cell(n_beads):
+    """The shape of the paper's scalability runs (a 256^2 grid with up to
+    500k particles): 4 and 8 beads per cell.  A 32 x 32 tile then holds 4k
+    to 8k beads, so the force kernel stages its records in several chunks,
+    and the deposit's fixed-point scale comes from bins of 256 to 512
+    beads."""
+    _compare_one_step(synth.world_dense(256, n_beads, seed=4))
+
+
 def test_one_step_c2_full_size():
     """512 x 512 grid with 262,144 beads: the whole step against the oracle."""
     _compare_one_step(synth.world_c2(0))
@@ -261,8 +271,10 @@ def test_rollout_100_steps_c1():
 # ---------------------------------------------------------------------------
 def test_batched_equals_alone_bitwise():
     from paper_2607_02954_gb300 import step_batched
+    # the C4 range (sides 64..256, up to 64 filaments) plus a 512^2 world,
+    # whose 4096 bins span four scan blocks (the plan runs both scan kernels)
     specs = [synth.world_random(s, side, nf) for s, side, nf in
-             [(1, 64, 3), (2, 128, 17), (3, 64, 1), (4, 256, 40), (5, 128, 8)]]
+             [(1, 64, 3), (2, 128, 17), (3, 64, 1), (4, 256, 40), (5, 128, 8), (6, 256, 64), (7, 512, 30)]]
     specs[2].params = synth.Params(pbd_order=1, sigma=0.6)   # a red-black world with a narrower filter
     specs[3].params = synth.Params(layers=2, layer_half=0.9)  # a two-layer world
     alone = []
@@ -279,6 +291,56 @@ def test_batched_equals_alone_bitwise():
         for k in a:
             assert np.array_equal(a[k], b[k]), k
         assert w.info()["t"] == 37
+        w.close()
+
+
+def _edge_reach_world():
+    """64^2 world whose tile x in [32, 64) is reached by one bead only, with
+    a kernel weight too small for the deposit's fixed point: a 48-bead snake
+    fills one 8 x 8 bin left of the tile edge (its count sets the deposit
+    scale to 2^24, and no snake bead reaches column 32), and a stretched
+    2-bead filament has its first bead at x = 30.0002, whose stencil reaches
+    column 32 with weight phi(1.9998) ~ 1.5e-8 in float32."""
+    xs, ys = [], []
+    for r in range(8):
+        row = [24.3 + k for k in range(6)]
+        xs += row if r % 2 == 0 else row[::-1]
+        ys += [0.5 + r] * 6
+    xs += [30.0002, 28.5002]
+    ys += [12.5, 12.5]
+    x, y = np.array(xs, np.float32), np.array(ys, np.float32)
+    d = np.stack([np.diff(x[:48]), np.diff(y[:48])], 1)
+    th_snake = np.arctan2(d[:, 1], d[:, 0])
+    theta = np.concatenate([th_snake, [np.pi]]).astype(np.float32)
+    theta0 = np.diff(th_snake)   # the snake's rest shape is its start shape
+    z = np.zeros(len(theta0))
+    return synth._world("edge_reach", 64, 64, [48, 2], x, y, theta, theta0, z, z, z)
+
+
+def test_batched_tile_skip_is_exact():
+    """The batched force pass skips tiles that no bead's stencil reaches.  A
+    tile reached only by a weight that the deposit's fixed point rounds to 0
+    must still get its (tiny) spread: the world stepped alone (which never
+    skips) and in a batch stay bitwise equal."""
+    from paper_2607_02954_gb300 import step_batched
+    spec = _edge_reach_world()
+    probe = _gpu_world(spec)
+    probe.step(1)
+    rho, F = probe.field("rho_s"), probe.field("force")
+    # the case this test is about: nothing deposited on column 32, a spread there
+    assert np.all(rho[8:18, 32] == 0.0)
+    assert np.any(F[8:18, 32] != 0.0)
+    probe.close()
+    alone = _gpu_world(spec)
+    alone.step(6)
+    want = alone.state(fluid=True)
+    alone.close()
+    ws = [_gpu_world(spec), _gpu_world(synth.world_random(3, 64, 4))]
+    step_batched(ws, 6)
+    got = ws[0].state(fluid=True)
+    for k in want:
+        assert np.array_equal(want[k], got[k]), k
+    for w in ws:
         w.close()
 
 

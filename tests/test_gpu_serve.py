@@ -55,6 +55,28 @@ def test_served_results_equal_alone_and_direct():
         assert np.allclose(direct, r["com_disp"], rtol=1e-5, atol=1e-7)
 
 
+def test_served_c4_range_and_large_worlds_equal_alone():
+    """Worlds at the top of the C4 range (256^2 grids with up to 64
+    filaments of up to 64 beads) and a 512^2 world, whose bins span four
+    scan blocks, so the mixed plan runs the two-kernel bin scan while plans
+    of the smaller worlds alone run the one-kernel scan: each rollout's
+    result is bitwise the same in the mix and alone."""
+    from paper_2607_02954_gb300 import Server
+    rng = np.random.default_rng(17)
+    specs = [(synth.world_random(300 + k, 256, int(rng.integers(32, 65))), int(rng.integers(25, 50)))
+             for k in range(6)]
+    specs.append((synth.world_random(399, 512, 48), 33))
+    srv = Server(max_slots=4, steps_per_tick=6)
+    mixed = [srv.wait(t) for t in [srv.submit(sp, n) for sp, n in specs]]
+    srv.close()
+    for (sp, n), r in zip(specs, mixed):
+        assert r["status"] == 0 and r["n_steps"] == n
+        alone = Server(max_slots=1, steps_per_tick=11)
+        ra = alone.wait(alone.submit(sp, n))
+        alone.close()
+        assert ra["com_disp"] == r["com_disp"], (ra, r)
+
+
 def test_served_result_matches_oracle_displacement():
     from paper_2607_02954_gb300 import Server
     sp = synth.world_c1(2)
