@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define MC_ABI_VERSION 5
+#define MC_ABI_VERSION 6
 
 typedef enum mc_status {
   MC_OK = 0,
@@ -55,7 +55,8 @@ typedef enum mc_status {
   MC_ERR_TIMEOUT = 4,      /* a bounded wait gave up */
   MC_ERR_UNSTABLE = 5,     /* the velocity watchdog tripped (|U| too large or not finite) */
   MC_ERR_BUSY = 6,         /* result not ready yet / queue full */
-  MC_ERR_NOT_FOUND = 7     /* unknown ticket or handle */
+  MC_ERR_NOT_FOUND = 7,    /* unknown ticket or handle */
+  MC_ERR_CANCELLED = 8     /* the rollout was cancelled (mc_serve_cancel) */
 } mc_status;
 
 typedef enum mc_mem_kind { MC_MEM_HOST = 0, MC_MEM_DEVICE = 1 } mc_mem_kind;
@@ -195,7 +196,8 @@ mc_status mc_step_batched(mc_world* const* worlds, int n_worlds, int n_steps, vo
 
 /* Enqueues one stage of the next step on `stream` (for per-stage timing).
  * Stages: 0 drive + PBD + elastic force + bin histogram (a1-a3), 1 bin
- * offsets (two kernels), 2 bin scatter (a2), 3 steric deposit + x pass of
+ * offsets (one kernel, or two when the bins span several scan blocks),
+ * 2 bin scatter (a2), 3 steric deposit + x pass of
  * the Gaussian filter (a4, a5), 7 y pass + steric force + spread + LBM
  * (a5-a7, one kernel, the force density handed to the collision in shared
  * memory), 6 interpolation + advance (a8).  Enqueuing stages 0, 1, 2, 3, 7, 6
@@ -413,6 +415,28 @@ mc_status mc_serve_poll(mc_server* s, uint64_t ticket, mc_result* out);
 mc_status mc_serve_wait(mc_server* s, uint64_t ticket, int timeout_ms, mc_result* out);
 
 mc_status mc_server_stats_get(mc_server* s, mc_server_stats* out);
+
+/* Cancels a rollout that is queued or running.  A queued request leaves the
+ * queue at once; a running one leaves the batch at the scheduler's next
+ * tick (its world is freed once the device has finished the ticks that used
+ * it), so the rollouts around it continue unchanged.  Its result is then
+ * published with status MC_ERR_CANCELLED (collect it with poll or wait;
+ * com_disp and the observables are zero), unless the rollout completed in
+ * a tick the scheduler had already enqueued, in which case its normal
+ * result stands.  Returns MC_OK when the ticket was queued or running,
+ * MC_ERR_NOT_FOUND when it is unknown, finished (its result stays
+ * collectable) or collected. */
+mc_status mc_serve_cancel(mc_server* s, uint64_t ticket);
+
+/* Test support for the allocation-failure path (host side only; nothing is
+ * done on the device).  Arms a fake of the world allocation: the nth world
+ * allocation from now (1 = the next; mc_world_create's arena, including the
+ * worlds a server's scheduler creates) reports an out-of-memory failure as
+ * cudaMallocAsync would, without calling it, and that creation returns
+ * MC_ERR_OOM (a served request reports it in its result's status).  Other
+ * allocations are real.  0 disarms.  Process-wide.  Errors:
+ * MC_ERR_INVALID_ARG for nth < 0. */
+mc_status mc_inject_world_alloc_failure(int nth);
 
 /* Stops the scheduler, drops queued requests and frees everything.  No
  * other call on this server may run concurrently or afterwards. */

@@ -15,7 +15,8 @@ MC_OK = 0
 MC_MEM_HOST = 0
 MC_MEM_DEVICE = 1
 STATUS_NAMES = {0: "MC_OK", 1: "MC_ERR_INVALID_ARG", 2: "MC_ERR_OOM", 3: "MC_ERR_CUDA",
-                4: "MC_ERR_TIMEOUT", 5: "MC_ERR_UNSTABLE", 6: "MC_ERR_BUSY", 7: "MC_ERR_NOT_FOUND"}
+                4: "MC_ERR_TIMEOUT", 5: "MC_ERR_UNSTABLE", 6: "MC_ERR_BUSY", 7: "MC_ERR_NOT_FOUND",
+                8: "MC_ERR_CANCELLED"}
 
 FIELDS = {"fel": 0, "fs": 1, "ubead": 2, "rho_s": 3, "rho_bar": 4, "force": 5, "u": 6,
           "cell": 7, "bin": 8, "bin_off": 9, "bin_beads": 10, "ebead": 11}
@@ -98,6 +99,8 @@ SIGNATURES = {
     "mc_serve_wait": (_i, [_vp, ctypes.c_uint64, _i, ctypes.POINTER(mc_result)]),
     "mc_server_stats_get": (_i, [_vp, ctypes.POINTER(mc_server_stats)]),
     "mc_server_destroy": (_i, [_vp]),
+    "mc_serve_cancel": (_i, [_vp, ctypes.c_uint64]),
+    "mc_inject_world_alloc_failure": (_i, [_i]),
     "mc_last_error": (ctypes.c_char_p, []),
     "mc_abi_version": (_i, []),
 }
@@ -105,7 +108,7 @@ SIGNATURES = {
 _lib = None
 
 
-ABI_VERSION = 5   # MC_ABI_VERSION of include/mc.h that these structures mirror
+ABI_VERSION = 6   # MC_ABI_VERSION of include/mc.h that these structures mirror
 
 
 def load():

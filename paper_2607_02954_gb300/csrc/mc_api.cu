@@ -1,6 +1,7 @@
 // C ABI of libmc: world life cycle, plans (world tables + work items), step
 // replay through CUDA graphs, and state read-out.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -33,6 +34,19 @@ mc_status cuda_fail(cudaError_t e, const char* what) {
     cudaError_t e_ = (call);                               \
     if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
   } while (0)
+
+// Fake of the world allocation for tests of the out-of-memory path: when
+// armed with n, the nth world allocation from then on reports
+// cudaErrorMemoryAllocation without calling the allocator.
+std::atomic<int> g_fail_world_alloc{0};
+
+cudaError_t world_alloc(void** p, size_t bytes, cudaStream_t s) {
+  int k = g_fail_world_alloc.load();
+  while (k > 0 && !g_fail_world_alloc.compare_exchange_weak(k, k - 1)) {
+  }
+  if (k == 1) return cudaErrorMemoryAllocation;
+  return cudaMallocAsync(p, bytes, s);
+}
 
 // Bump allocator inside one arena.
 struct Layout {
@@ -370,6 +384,12 @@ void plan_free(Plan& p, cudaStream_t s) { free_plan(p, s); }
 extern "C" {
 
 const char* mc_last_error(void) { return g_last_error.c_str(); }
+
+mc_status mc_inject_world_alloc_failure(int nth) {
+  if (nth < 0) return fail(MC_ERR_INVALID_ARG, "nth must be >= 0");
+  g_fail_world_alloc.store(nth);
+  return MC_OK;
+}
 int mc_abi_version(void) { return MC_ABI_VERSION; }
 
 mc_status mc_params_default(mc_params* p) {
@@ -478,7 +498,7 @@ mc_status mc_world_create(const mc_world_desc* d, void* stream, mc_world** out) 
   h.observe = d->observe;
 
   w->bytes = mc::world_layout(h, nullptr);
-  cudaError_t e = cudaMallocAsync(&w->arena, w->bytes, s);
+  cudaError_t e = world_alloc(&w->arena, w->bytes, s);
   if (e != cudaSuccess) {
     delete w;
     return fail(MC_ERR_OOM, std::string("world allocation: ") + cudaGetErrorString(e));

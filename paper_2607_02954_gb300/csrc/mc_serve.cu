@@ -28,6 +28,7 @@
 #include <string>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "mc_internal.cuh"
@@ -60,13 +61,17 @@ struct Slot {
   int n_steps = 0;
   size_t bytes = 0;
   int64_t t_submit = 0, t_admit = 0;
+  int64_t first_tick = 0;   // the first tick that steps the world
 };
 
 // The rollouts a tick finished: read back (into output buffer `buf`) by the
-// tick itself, published once its event has completed.
+// tick itself, published once its event has completed.  Cancelled rollouts
+// are released the same way, after the last tick that used their worlds,
+// with no read-back.
 struct Retire {
   std::vector<Slot> slots;
   int buf = 0;
+  bool cancelled = false;
 };
 
 constexpr size_t kRec = 40;   // 3 floats (mean displacement, flags) + pad, 3 int64 observables
@@ -118,6 +123,7 @@ struct mc_server {
   std::deque<Request> pending;
   std::unordered_map<uint64_t, mc_result> done;
   std::unordered_map<uint64_t, int> in_flight;   // ticket -> 1 while pending or active
+  std::unordered_set<uint64_t> cancel;           // running rollouts asked to stop
   uint64_t next_ticket = 1;
   bool stop = false;
   // scheduler-thread state
@@ -170,6 +176,20 @@ bool retire_oldest(mc_server* s, bool block) {
   for (size_t j = 0; j < r.slots.size(); ++j) {
     const Slot& sl = r.slots[j];
     mc_result res{};
+    if (r.cancelled) {
+      res.status = MC_ERR_CANCELLED;
+      res.n_steps = sl.n_steps;
+      res.t_submit_ns = sl.t_submit;
+      res.t_admit_ns = sl.t_admit;
+      res.t_done_ns = t;
+      mc_world_destroy(sl.w);
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->bytes_in_use -= sl.bytes;
+      }
+      publish(s, sl.ticket, res);
+      continue;
+    }
     float rec[3];
     std::memcpy(rec, out + kRec * j, sizeof(rec));
     res.com_disp[0] = rec[0];
@@ -268,6 +288,7 @@ void scheduler(mc_server* s) {
       sl.bytes = r.bytes;
       sl.t_submit = r.t_submit;
       sl.t_admit = t;
+      sl.first_tick = s->n_ticks;
       s->active.push_back(sl);
       set_changed = true;
       created = true;
@@ -276,6 +297,54 @@ void scheduler(mc_server* s) {
       // the new worlds' set-up precedes their first step
       cudaEventRecord(s->adm_ev, s->adm_stream);
       cudaStreamWaitEvent(s->stream, s->adm_ev, 0);
+    }
+    // cancelled running rollouts leave the batch before this tick; their
+    // worlds are released once the last tick that stepped them is done (at
+    // once when none did)
+    {
+      std::vector<Slot> gone;
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (!s->cancel.empty()) {
+          for (int i = 0; i < (int)s->active.size();) {
+            if (s->cancel.erase(s->active[i].ticket)) {
+              gone.push_back(s->active[i]);
+              s->active.erase(s->active.begin() + i);
+            } else {
+              ++i;
+            }
+          }
+          s->cancel.clear();   // tickets no longer running (finished meanwhile)
+        }
+      }
+      if (!gone.empty()) {
+        set_changed = true;
+        Retire late;
+        late.cancelled = true;
+        late.buf = (int)((s->n_ticks - 1) & 1);
+        for (auto& sl : gone) {
+          if (sl.first_tick < s->n_ticks) {
+            late.slots.push_back(sl);
+            continue;
+          }
+          // never stepped: only its set-up on the creation stream used it
+          cudaStreamSynchronize(s->adm_stream);
+          mc_result res{};
+          res.status = MC_ERR_CANCELLED;
+          res.n_steps = sl.n_steps;
+          res.t_submit_ns = sl.t_submit;
+          res.t_admit_ns = sl.t_admit;
+          res.t_done_ns = now_ns();
+          mc_world_destroy(sl.w);
+          {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->bytes_in_use -= sl.bytes;
+          }
+          publish(s, sl.ticket, res);
+        }
+        // after every tick enqueued so far, on that last tick's event
+        if (!late.slots.empty()) s->retiring.push_back(std::move(late));
+      }
     }
     while (retire_oldest(s, false)) {
     }
@@ -504,6 +573,30 @@ mc_status mc_server_stats_get(mc_server* s, mc_server_stats* out) {
   std::lock_guard<std::mutex> lk(s->mu);
   *out = s->stats;
   out->pending = (int64_t)s->pending.size();
+  return MC_OK;
+}
+
+mc_status mc_serve_cancel(mc_server* s, uint64_t ticket) {
+  if (!s) return serve_fail(MC_ERR_INVALID_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (!s->in_flight.count(ticket)) return serve_fail(MC_ERR_NOT_FOUND, "ticket is not queued or running");
+  for (auto it = s->pending.begin(); it != s->pending.end(); ++it) {
+    if (it->ticket != ticket) continue;
+    mc_result res{};
+    res.status = MC_ERR_CANCELLED;
+    res.n_steps = it->n_steps;
+    res.t_submit_ns = it->t_submit;
+    res.t_admit_ns = res.t_done_ns = now_ns();
+    s->pending.erase(it);
+    s->done[ticket] = res;
+    s->in_flight.erase(ticket);
+    s->stats.completed += 1;
+    s->cv_done.notify_all();
+    return MC_OK;
+  }
+  // admitted: the scheduler takes it out of the batch at its next tick
+  s->cancel.insert(ticket);
+  s->cv_work.notify_one();
   return MC_OK;
 }
 

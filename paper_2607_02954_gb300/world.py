@@ -313,6 +313,15 @@ class Server:
         L.check(self._lib.mc_serve_wait(self._h, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(r)))
         return _result_dict(r)
 
+    def cancel(self, ticket: int) -> bool:
+        """Cancels a queued or running rollout (its result then carries status
+        MC_ERR_CANCELLED); False when the ticket is not queued or running."""
+        st = self._lib.mc_serve_cancel(self._h, ctypes.c_uint64(ticket))
+        if st == 7:   # MC_ERR_NOT_FOUND
+            return False
+        L.check(st)
+        return True
+
     def stats(self) -> Dict:
         s = L.mc_server_stats()
         L.check(self._lib.mc_server_stats_get(self._h, ctypes.byref(s)))

@@ -112,3 +112,10 @@ def test_step_rejects_null_world():
     lib = L.load()
     assert lib.mc_step(None, 1, None) == 1
     assert lib.mc_step_batched(None, 1, 1, None) == 1
+
+
+def test_fault_injection_and_cancel_validate_arguments():
+    lib = L.load()
+    assert lib.mc_inject_world_alloc_failure(-1) == 1
+    assert lib.mc_inject_world_alloc_failure(0) == 0
+    assert lib.mc_serve_cancel(None, 1) == 1
