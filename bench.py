@@ -113,6 +113,8 @@ def parse():
     ap.add_argument("--duration", type=float, default=2.0, help="served: seconds of arrivals")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline only: skip the batched (c4) and served summaries of the default line")
     ap.add_argument("--stage-steps", type=int, default=50, help="steps of the per-stage timing pass")
     return ap.parse_args()
 
@@ -252,21 +254,36 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def run_oracle_sample(spec, min_seconds: float, max_steps: int = 1000):
-    """Times oracle steps on the sample until min_seconds of CPU work."""
+def host_cores() -> int:
+    """Logical CPU cores of this host (what nproc reports)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_oracle_sample(spec, min_seconds: float, max_steps: int = 1000, threads: int = 0):
+    """Times oracle steps on the sample until min_seconds of CPU work, with
+    `threads` intra-op threads (0: every host core)."""
     import torch
     import oracle as O
-    ow = O.World(spec)
-    st = ow.initial_state()
-    t0 = time.perf_counter()
-    n = 0
-    while True:
-        st, _ = O.step(ow, st)
-        n += 1
-        el = time.perf_counter() - t0
-        if el >= min_seconds or n >= max_steps:
-            break
-    return spec.N * n / el, n, el, torch.get_num_threads()
+    old = torch.get_num_threads()
+    torch.set_num_threads(threads or host_cores())
+    try:
+        ow = O.World(spec)
+        st = ow.initial_state()
+        t0 = time.perf_counter()
+        n = 0
+        while True:
+            st, _ = O.step(ow, st)
+            n += 1
+            el = time.perf_counter() - t0
+            if el >= min_seconds or n >= max_steps:
+                break
+        used = torch.get_num_threads()
+    finally:
+        torch.set_num_threads(old)
+    return spec.N * n / el, n, el, used
 
 
 def reference_arm(args):
@@ -276,6 +293,7 @@ def reference_arm(args):
     spec, desc = sample_spec(args.workload, 1)
     import torch
     import oracle as O
+    torch.set_num_threads(host_cores())
     ow = O.World(spec)
     st = ow.initial_state()
     for _ in range(args.warmup):
@@ -290,17 +308,20 @@ def reference_arm(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "sample": desc},
             "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": torch.get_num_threads(),
-                             "kind": "oracle", "sample": desc},
+                             "kind": "oracle", "sample": desc, "host_cores": host_cores()},
             "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def bench_batched(args):
+def bench_batched(args, steps=None):
     """1024 uneven worlds: batched steps (one launch per stage for all worlds,
-    replayed from a CUDA graph) against plain per-world launches."""
+    replayed from a CUDA graph) against two per-world arms: each world's own
+    16-step graph replay (mc_step(w, 16), the strongest per-world path) and
+    single direct steps (mc_step(w, 1), seven launches per world and step)."""
     import torch
     from paper_2607_02954_gb300 import World, step_batched, synth
+    steps = steps or args.steps
     specs = synth.batch_c4(0)
     worlds = [World(sp) for sp in specs]
     n_beads = sum(sp.N for sp in specs)
@@ -311,11 +332,22 @@ def bench_batched(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
         e0.record(stream)
-        step_batched(worlds, args.steps)
+        step_batched(worlds, steps)
         e1.record(stream)
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    batched = n_beads * args.steps / (ms * 1e-3)
+    batched = n_beads * steps / (ms * 1e-3)
+    # per-world graph replays: one 16-step graph per world (captured in the warm-up)
+    for w in worlds:
+        w.step(16)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for w in worlds:
+        w.step(16)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_graph = e0.elapsed_time(e1)
+    plain_graph = n_beads * 16 / (ms_graph * 1e-3)
     plain_steps = 3
     for w in worlds:
         w.step(1)
@@ -332,13 +364,17 @@ def bench_batched(args):
         w.check()
         w.close()
     return {"metric": "particle-steps/s", "value": batched, "unit": "particle-steps/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "c4", "worlds": len(specs), "beads": n_beads, "cells": n_cells,
                        "description": "1024 worlds, side ~U{64,128,256}, 1-64 filaments x 8-64 beads (log-uniform)"},
+            "plain_per_world_graph": {"value": plain_graph, "ms_per_step": ms_graph / 16,
+                                      "description": "each world's own 16-step CUDA graph, replayed world after world"},
             "plain_per_world": {"value": plain, "ms_per_step": ms_plain / plain_steps,
-                                "launches_per_step": len(worlds) * (KERNELS_PER_STEP - 2 + scan_kernels(specs))},
-            "batched_over_plain": batched / plain, "gpu_launches": graph_launches(args.steps, scan_kernels(specs)),
+                                "launches_per_step": len(worlds) * (KERNELS_PER_STEP - 2 + scan_kernels(specs)),
+                                "description": "single direct steps, world after world"},
+            "batched_over_plain_graph": batched / plain_graph, "batched_over_plain": batched / plain,
+            "gpu_launches": graph_launches(steps, scan_kernels(specs)),
             "clocks": clk.summary()}
 
 
@@ -597,11 +633,31 @@ def main():
     }
     if mdf:
         line["step_roofline"]["note"] = "penalty-step bytes: a lower bound of the direct-forcing step's traffic"
+    if not args.no_extras and ws == 1:
+        # the batched and served workloads (1024 uneven worlds), summarised
+        # beside the headline; each is its own line with --workload c4 / served
+        b = bench_batched(args, steps=max(64, min(args.steps, 512)))
+        line["batched_c4"] = {"value": b["value"], "unit": "particle-steps/s", "ms_per_step": b["ms_per_step"],
+                              "steps": b["steps"], "worlds": b["config"]["worlds"],
+                              "plain_per_world_graph": b["plain_per_world_graph"]["value"],
+                              "plain_per_world": b["plain_per_world"]["value"],
+                              "batched_over_plain_graph": b["batched_over_plain_graph"],
+                              "batched_over_plain": b["batched_over_plain"]}
+        sv = bench_served(args)
+        line["served_c4"] = {"value": sv["value"], "unit": "particle-steps/s", "latency_ms": sv["latency_ms"],
+                             "requests": sv["config"]["requests"],
+                             "arrival_rate_per_s": sv["config"]["arrival_rate_per_s"],
+                             "rollout_steps": sv["config"]["rollout_steps"],
+                             "completed_per_s": sv["completed_per_s"], "failed": sv["failed"]}
     if not args.no_cpu_baseline and ws == 1:
         sspec, sdesc = sample_spec(args.workload, 1, params=spec.params)
         v, n, el, cores = run_oracle_sample(sspec, 10.0)
+        v1, n1, el1, _ = run_oracle_sample(sspec, 5.0, threads=1)
         line["cpu_baseline"] = {"value": v, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
-                                "sample": f"{sdesc}; {n} step(s) in {el:.1f} s"}
+                                "sample": f"{sdesc}; {n} step(s) in {el:.1f} s on {cores} threads",
+                                "host_cores": host_cores(),
+                                "single_thread": {"value": v1, "unit": "particle-steps/s", "cores": 1,
+                                                  "sample": f"{sdesc}; {n1} step(s) in {el1:.1f} s"}}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
