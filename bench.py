@@ -69,6 +69,14 @@ def graph_launches(steps: int, scans: int = 2) -> int:
     per = 4 + scans   # PBD, scan, scatter, deposit, force + LBM per step, plus the last advance
     r = steps % GRAPH_STEPS
     return (steps // GRAPH_STEPS) * (GRAPH_STEPS * per + 1) + (per * r + 1 if r else 0)
+def run_launches(steps: int, cfg: dict, scans: int) -> int:
+    """Kernels of a run of `steps` steps in a launch configuration: the persistent step is one cooperative
+    launch per run; otherwise the graph sequence above (two scan kernels when the configuration asks)."""
+    if cfg.get("persistent"):
+        return 1
+    return graph_launches(steps, 2 if cfg.get("scan_kernels") == 2 else scans)
+
+
 # k_force_lbm, the dominant kernel: per cell read f 36 + rho_x 4, write f' 36 + u 8;
 # per bead read the binned record (position 16, F_el 8, id 4), write F_s 8
 FORCE_LBM_BYTES_PER_CELL = 84
@@ -321,14 +329,16 @@ def bench_batched(args, steps=None):
     single direct steps (mc_step(w, 1), seven launches per world and step)."""
     import torch
     from paper_2607_02954_gb300 import World, step_batched, synth
+    from paper_2607_02954_gb300 import launch_config, set_launch_config
     steps = steps or args.steps
     specs = synth.batch_c4(0)
     worlds = [World(sp) for sp in specs]
     n_beads = sum(sp.N for sp in specs)
     n_cells = sum(sp.H * sp.W for sp in specs)
     stream = torch.cuda.current_stream()
-    step_batched(worlds, max(args.warmup, 16))
+    step_batched(worlds, max(args.warmup, 16))   # the first run of 16 steps tunes the batch's plan
     torch.cuda.synchronize()
+    tuned = launch_config(worlds)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
         e0.record(stream)
@@ -337,6 +347,20 @@ def bench_batched(args, steps=None):
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     batched = n_beads * steps / (ms * 1e-3)
+    # each launch configuration the tuner chose from, timed on the same worlds
+    configs = {}
+    for name, cfg in (("stage_graph", dict(persistent=0, pbd_warps=8, scan_kernels=0)),
+                      ("persistent_4", dict(persistent=4, pbd_warps=8, scan_kernels=0)),
+                      ("persistent_3", dict(persistent=3, pbd_warps=8, scan_kernels=0)),
+                      ("stage_graph_pbd4", dict(persistent=0, pbd_warps=4, scan_kernels=0))):
+        set_launch_config(worlds, **cfg)
+        step_batched(worlds, 16)
+        e0.record(stream)
+        step_batched(worlds, 64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        configs[name] = e0.elapsed_time(e1) / 64
+    set_launch_config(worlds, **tuned)
     # per-world graph replays: one 16-step graph per world (captured in the warm-up)
     for w in worlds:
         w.step(16)
@@ -374,7 +398,8 @@ def bench_batched(args, steps=None):
                                 "launches_per_step": len(worlds) * (KERNELS_PER_STEP - 2 + scan_kernels(specs)),
                                 "description": "single direct steps, world after world"},
             "batched_over_plain_graph": batched / plain_graph, "batched_over_plain": batched / plain,
-            "gpu_launches": graph_launches(steps, scan_kernels(specs)),
+            "launch_config": tuned, "config_ms_per_step": configs,
+            "gpu_launches": run_launches(steps, tuned, scan_kernels(specs)),
             "clocks": clk.summary()}
 
 
@@ -542,9 +567,11 @@ def main():
     stream = torch.cuda.current_stream()
     sh = ctypes.c_void_p(stream.cuda_stream)
 
-    # warm-up (includes the one-time graph capture)
+    # warm-up (includes the one-time tuning of the launch configuration and the graph capture)
     world.step(max(args.warmup, 16))
     torch.cuda.synchronize()
+    from paper_2607_02954_gb300 import launch_config
+    tuned = launch_config([world])
 
     def barrier():
         if dist is not None:
@@ -620,7 +647,8 @@ def main():
         "e2e": {"value": e2e_val, "unit": "particle-steps/s", "steps": e2e_steps,
                 "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps},
         "gpu_launches": (mdf_launches(args.steps, args.mdf_iters) - (2 - scan_kernels([spec])) * args.steps if mdf
-                         else graph_launches(args.steps, scan_kernels([spec]))),
+                         else run_launches(args.steps, tuned, scan_kernels([spec]))),
+        "launch_config": tuned,
         "roofline": None if mdf else {
             "bound": "hbm", "kernel": "k_force_lbm", "achieved": top_gbs, "peak": hbm_peak, "unit": "GB/s",
             "frac": top_gbs / hbm_peak, "peak_kind": peak_kind,
@@ -639,6 +667,7 @@ def main():
         b = bench_batched(args, steps=max(64, min(args.steps, 512)))
         line["batched_c4"] = {"value": b["value"], "unit": "particle-steps/s", "ms_per_step": b["ms_per_step"],
                               "steps": b["steps"], "worlds": b["config"]["worlds"],
+                              "launch_config": b["launch_config"], "config_ms_per_step": b["config_ms_per_step"],
                               "plain_per_world_graph": b["plain_per_world_graph"]["value"],
                               "plain_per_world": b["plain_per_world"]["value"],
                               "batched_over_plain_graph": b["batched_over_plain_graph"],

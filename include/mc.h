@@ -194,6 +194,64 @@ mc_status mc_step(mc_world* w, int n_steps, void* stream);
  * worlds is a host array of n_worlds distinct handles. */
 mc_status mc_step_batched(mc_world* const* worlds, int n_worlds, int n_steps, void* stream);
 
+/* ---- Launch configuration and autotuner -----------------------------------
+ * The steps of a plan (one world, or one batch of worlds as passed to
+ * mc_step_batched) can run in several launch configurations, all of which
+ * advance the worlds bitwise the same:
+ *   persistent    0: the stage kernels (one launch per stage per step,
+ *                 covering every world), replayed from a captured CUDA
+ *                 graph of 16 steps; 3 or 4: one persistent cooperative
+ *                 launch per run of steps with that many blocks per SM, the
+ *                 stages separated by grid-wide barriers (plans without
+ *                 direct forcing or two layers, filaments of at most 64
+ *                 beads, sigma in (0.75, 1]).  Each barrier wait is bounded
+ *                 (1 s); when it runs out the kernel ends and the worlds'
+ *                 check reports MC_ERR_TIMEOUT (their state is then
+ *                 unspecified).
+ *   pbd_warps     most filaments per block of the PBD kernels: 8, 4 or 2
+ *   scan_kernels  0: one bin-offset kernel when every world's bins fit one
+ *                 scan block (1024 bins), else two; 2: always two
+ * The autotuner measures the candidates on device copies of the plan's
+ * worlds (the worlds do not move) and caches its choice per class of plan
+ * (world count, sizes, tile and bead counts) for the life of the process.
+ * By default the first mc_step / mc_step_batched of at least 16 steps of a
+ * plan looks the class up and, when it is not cached yet, tunes it then,
+ * which synchronizes `stream` (single worlds below 2^20 cells and 2^18 beads
+ * keep the defaults unless tuned explicitly; nothing is measured while
+ * `stream` is being captured).  The plan of a batch is the one
+ * mc_step_batched caches for that exact list of handles. */
+typedef struct mc_launch_config {
+  int persistent;     /* 0, 3 or 4 */
+  int pbd_warps;      /* 8, 4 or 2 */
+  int scan_kernels;   /* 0 or 2 */
+} mc_launch_config;
+
+/* Tunes the plan of worlds[0..n_worlds) now (or takes its class's cached
+ * choice) and returns the configuration in *chosen (may be NULL).
+ * Synchronizes `stream`; needs device memory for a copy of the worlds (if
+ * it cannot get it, the defaults stay).  Errors: MC_ERR_INVALID_ARG. */
+mc_status mc_autotune(mc_world* const* worlds, int n_worlds, void* stream, mc_launch_config* chosen);
+
+/* The configuration the plan of worlds[0..n_worlds) runs with. */
+mc_status mc_launch_config_get(mc_world* const* worlds, int n_worlds, mc_launch_config* out);
+
+/* Pins the configuration of the plan of worlds[0..n_worlds) (no tuning
+ * afterwards).  Errors: MC_ERR_INVALID_ARG for a value out of range or a
+ * persistent step on a plan it does not support. */
+mc_status mc_launch_config_set(mc_world* const* worlds, int n_worlds, const mc_launch_config* cfg);
+
+/* 1 (default): the first run of at least 16 steps of an untuned plan tunes
+ * it as described above; 0: plans keep the defaults unless mc_autotune is
+ * called.  Process-wide. */
+mc_status mc_autotune_mode(int mode);
+
+/* Test support for the bounded barrier of the persistent step (process-wide;
+ * defaults 0 and 1 s): each barrier waits for extra_arrivals (0 or 1) more
+ * blocks than the launch has, and gives up after timeout_ns (1e3 to 1e10).
+ * With 1 no barrier completes, so a persistent run ends at its first
+ * barrier with the timeout reported; nothing else changes. */
+mc_status mc_debug_barrier_test(unsigned extra_arrivals, int64_t timeout_ns);
+
 /* Enqueues one stage of the next step on `stream` (for per-stage timing).
  * Stages: 0 drive + PBD + elastic force + bin histogram (a1-a3), 1 bin
  * offsets (one kernel, or two when the bins span several scan blocks),

@@ -9,7 +9,8 @@ from .synth import Params, WorldSpec  # noqa: F401
 
 
 def __getattr__(name):
-    if name in ("World", "Server", "step_batched", "default_params", "stream_handle"):
+    if name in ("World", "Server", "step_batched", "default_params", "stream_handle", "autotune", "launch_config",
+                "set_launch_config"):
         from . import world
         return getattr(world, name)
     raise AttributeError(name)

@@ -66,6 +66,10 @@ class mc_result(ctypes.Structure):
                 ("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64), ("t_done_ns", ctypes.c_int64)]
 
 
+class mc_launch_config(ctypes.Structure):
+    _fields_ = [("persistent", ctypes.c_int), ("pbd_warps", ctypes.c_int), ("scan_kernels", ctypes.c_int)]
+
+
 class mc_server_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "steps_run", "ticks", "pending")]
 
@@ -80,6 +84,11 @@ SIGNATURES = {
     "mc_step": (_i, [_vp, _i, _vp]),
     "mc_step_batched": (_i, [ctypes.POINTER(_vp), _i, _i, _vp]),
     "mc_step_stage": (_i, [_vp, _i, _vp]),
+    "mc_autotune": (_i, [ctypes.POINTER(_vp), _i, _vp, ctypes.POINTER(mc_launch_config)]),
+    "mc_launch_config_get": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(mc_launch_config)]),
+    "mc_launch_config_set": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(mc_launch_config)]),
+    "mc_autotune_mode": (_i, [_i]),
+    "mc_debug_barrier_test": (_i, [ctypes.c_uint, ctypes.c_int64]),
     "mc_world_get_state": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, _vp]),
     "mc_world_get_positions_noalloc": (_i, [_vp, _vp, _vp, _vp]),
     "mc_world_get_field": (_i, [_vp, _i, _vp, _i, _vp]),

@@ -183,6 +183,7 @@ mc_status build_plan(mc_world* const* ws, int n, cudaStream_t s, Plan& out) {
   const size_t o_t = L.take<int2>(tile.size());
   const size_t o_c = L.take<int2>(cell.size());
   const size_t o_s = L.take<int2>(scan.size());
+  const size_t o_bar = L.take<unsigned>(4);
   std::vector<char> host(L.off);
   std::memcpy(host.data() + o_w, table.data(), n * sizeof(WorldDev));
   if (!fil.empty()) std::memcpy(host.data() + o_f, fil.data(), fil.size() * sizeof(int2));
@@ -201,6 +202,7 @@ mc_status build_plan(mc_world* const* ws, int n, cudaStream_t s, Plan& out) {
   p.d_tile_items = at<int2>(p.d_mem, o_t);
   p.d_cell_items = at<int2>(p.d_mem, o_c);
   p.d_scan_items = at<int2>(p.d_mem, o_s);
+  p.d_persist_bar = at<unsigned>(p.d_mem, o_bar);
   p.n_fil_items = (int)fil.size();
   p.n_bead_items = (int)bead.size();
   p.n_tile_items = (int)tile.size();
@@ -220,6 +222,12 @@ cudaStream_t capture_stream() {
 }
 
 mc_status run_steps(Plan& p, int n, cudaStream_t s) {
+  if (p.cfg.persistent && mc::persistent_supported(p)) {
+    // one cooperative launch for the whole run
+    if (n > 0) MC_CUDA(mc::launch_persistent(p, n, s));
+    MC_CUDA(cudaGetLastError());
+    return MC_OK;
+  }
   if (n >= kGraphSteps) {
     if (!p.graph) {
       cudaStream_t cs = capture_stream();
@@ -262,6 +270,34 @@ void drop_plans_with(mc_world* w) {
       ++it;
     }
   }
+}
+
+
+// The plan of a world (n == 1) or the cached plan of a batch of distinct
+// worlds (built on first use).
+mc_status find_plan(mc_world* const* ws, int n, cudaStream_t s, Plan** out) {
+  if (!ws || n < 1) return fail(MC_ERR_INVALID_ARG, "no worlds");
+  for (int k = 0; k < n; ++k) {
+    if (!ws[k]) return fail(MC_ERR_INVALID_ARG, "NULL world in batch");
+    for (int j = 0; j < k; ++j)
+      if (ws[j] == ws[k]) return fail(MC_ERR_INVALID_ARG, "a world appears twice in the batch");
+  }
+  if (n == 1) {
+    *out = &ws[0]->plan;
+    return MC_OK;
+  }
+  std::vector<mc_world*> key(ws, ws + n);
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  auto& m = plan_cache();
+  auto it = m.find(key);
+  if (it == m.end()) {
+    Plan p;
+    mc_status st = build_plan(ws, n, s, p);
+    if (st != MC_OK) return st;
+    it = m.emplace(key, p).first;
+  }
+  *out = &it->second;
+  return MC_OK;
 }
 
 }  // namespace
@@ -376,6 +412,38 @@ size_t world_layout(WorldDev& h, void* A) {
 
 // Plan and step helpers shared with the rollout server.
 mc_status plan_build(mc_world* const* ws, int n, cudaStream_t s, Plan& out) { return build_plan(ws, n, s, out); }
+void plan_set_cfg(Plan& p, const LaunchCfg& c) {
+  if (c.persistent == p.cfg.persistent && c.pbd_warps == p.cfg.pbd_warps && c.scan_kernels == p.cfg.scan_kernels)
+    return;
+  p.cfg = c;
+  if (p.graph) {
+    cudaGraphExecDestroy(p.graph);
+    p.graph = nullptr;
+  }
+}
+
+mc_world* world_clone(const mc_world* w, cudaStream_t s) {
+  mc_world* c = new mc_world();
+  c->h = w->h;
+  c->bytes = w->bytes;
+  c->stream = s;
+  c->t = w->t;
+  c->max_B = w->max_B;
+  c->fil_off = w->fil_off;
+  c->params = w->params;
+  if (cudaMallocAsync(&c->arena, c->bytes, s) != cudaSuccess) {
+    (void)cudaGetLastError();
+    delete c;
+    return nullptr;
+  }
+  if (cudaMemcpyAsync(c->arena, w->arena, c->bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+    cudaFreeAsync(c->arena, s);
+    delete c;
+    return nullptr;
+  }
+  world_layout(c->h, c->arena);
+  return c;   // no plan of its own: a copy is only stepped within the plan it is made for
+}
 mc_status plan_run(Plan& p, int n_steps, cudaStream_t s) { return run_steps(p, n_steps, s); }
 void plan_free(Plan& p, cudaStream_t s) { free_plan(p, s); }
 
@@ -614,7 +682,13 @@ mc_status mc_world_info_get(const mc_world* w, mc_world_info* out) {
 mc_status mc_step(mc_world* w, int n_steps, void* stream) {
   if (!w || n_steps < 0) return fail(MC_ERR_INVALID_ARG, "bad world or n_steps");
   if (w->t + n_steps >= (int64_t(1) << 24)) return fail(MC_ERR_INVALID_ARG, "step counter would reach 2^24");
-  mc_status st = run_steps(w->plan, n_steps, static_cast<cudaStream_t>(stream));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!w->plan.tuned && n_steps >= kGraphSteps) {
+    mc_world* self = w;
+    mc_status st = mc::plan_tune(&self, 1, w->plan, s, true);
+    if (st != MC_OK) return st;
+  }
+  mc_status st = run_steps(w->plan, n_steps, s);
   if (st == MC_OK) w->t += n_steps;
   return st;
 }
@@ -622,31 +696,72 @@ mc_status mc_step(mc_world* w, int n_steps, void* stream) {
 mc_status mc_step_batched(mc_world* const* ws, int n, int n_steps, void* stream) {
   if (!ws || n < 0 || n_steps < 0) return fail(MC_ERR_INVALID_ARG, "bad arguments");
   if (n == 0 || n_steps == 0) return MC_OK;
-  std::vector<mc_world*> key(ws, ws + n);
-  for (int k = 0; k < n; ++k) {
-    if (!ws[k]) return fail(MC_ERR_INVALID_ARG, "NULL world in batch");
-    for (int j = 0; j < k; ++j)
-      if (ws[j] == ws[k]) return fail(MC_ERR_INVALID_ARG, "a world appears twice in the batch");
-    if (ws[k]->t + n_steps >= (int64_t(1) << 24)) return fail(MC_ERR_INVALID_ARG, "step counter would reach 2^24");
-  }
+  for (int k = 0; k < n; ++k)
+    if (ws[k] && ws[k]->t + n_steps >= (int64_t(1) << 24))
+      return fail(MC_ERR_INVALID_ARG, "step counter would reach 2^24");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  Plan* plan = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_plan_mu);
-    auto& m = plan_cache();
-    auto it = m.find(key);
-    if (it == m.end()) {
-      Plan p;
-      mc_status st = build_plan(ws, n, s, p);
-      if (st != MC_OK) return st;
-      it = m.emplace(key, p).first;
-    }
-    plan = &it->second;
+  Plan* plan = nullptr;   // a batch of one runs the world's own plan
+  mc_status st = find_plan(ws, n, s, &plan);
+  if (st != MC_OK) return st;
+  if (!plan->tuned && n_steps >= kGraphSteps) {
+    st = mc::plan_tune(ws, n, *plan, s, true);
+    if (st != MC_OK) return st;
   }
-  mc_status st = run_steps(*plan, n_steps, s);
+  st = run_steps(*plan, n_steps, s);
   if (st == MC_OK)
     for (int k = 0; k < n; ++k) ws[k]->t += n_steps;
   return st;
+}
+
+mc_status mc_launch_config_get(mc_world* const* ws, int n, mc_launch_config* out) {
+  if (!out) return fail(MC_ERR_INVALID_ARG, "out is NULL");
+  Plan* p = nullptr;
+  mc_status st = find_plan(ws, n, nullptr, &p);
+  if (st != MC_OK) return st;
+  out->persistent = p->cfg.persistent;
+  out->pbd_warps = p->cfg.pbd_warps;
+  out->scan_kernels = p->cfg.scan_kernels;
+  return MC_OK;
+}
+
+mc_status mc_launch_config_set(mc_world* const* ws, int n, const mc_launch_config* cfg) {
+  if (!cfg) return fail(MC_ERR_INVALID_ARG, "cfg is NULL");
+  if (cfg->persistent != 0 && cfg->persistent != 3 && cfg->persistent != 4)
+    return fail(MC_ERR_INVALID_ARG, "persistent must be 0, 3 or 4");
+  if (cfg->pbd_warps != 8 && cfg->pbd_warps != 4 && cfg->pbd_warps != 2)
+    return fail(MC_ERR_INVALID_ARG, "pbd_warps must be 8, 4 or 2");
+  if (cfg->scan_kernels != 0 && cfg->scan_kernels != 2) return fail(MC_ERR_INVALID_ARG, "scan_kernels must be 0 or 2");
+  Plan* p = nullptr;
+  mc_status st = find_plan(ws, n, nullptr, &p);
+  if (st != MC_OK) return st;
+  mc::LaunchCfg c;
+  c.persistent = cfg->persistent;
+  c.pbd_warps = cfg->pbd_warps;
+  c.scan_kernels = cfg->scan_kernels;
+  if (c.persistent && !mc::persistent_supported(*p))
+    return fail(MC_ERR_INVALID_ARG, "the persistent step does not support this plan (direct forcing, two layers, "
+                                    "filaments over 64 beads or a filter half width other than 4)");
+  mc::plan_set_cfg(*p, c);
+  p->tuned = true;
+  return MC_OK;
+}
+
+mc_status mc_autotune(mc_world* const* ws, int n, void* stream, mc_launch_config* chosen) {
+  Plan* p = nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  mc_status st = find_plan(ws, n, s, &p);
+  if (st != MC_OK) return st;
+  st = mc::plan_tune(ws, n, *p, s, false);
+  if (st != MC_OK) return st;
+  if (chosen) return mc_launch_config_get(ws, n, chosen);
+  return MC_OK;
+}
+
+mc_status mc_debug_barrier_test(unsigned extra_arrivals, int64_t timeout_ns) {
+  if (extra_arrivals > 1 || timeout_ns < 1000 || timeout_ns > 10000000000LL)
+    return fail(MC_ERR_INVALID_ARG, "extra_arrivals must be 0 or 1 and timeout_ns in [1e3, 1e10]");
+  mc::persistent_test_settings(extra_arrivals, (unsigned long long)timeout_ns);
+  return MC_OK;
 }
 
 mc_status mc_step_stage(mc_world* w, int stage, void* stream) {
@@ -793,6 +908,8 @@ mc_status mc_world_check(const mc_world* w, void* stream) {
   unsigned flags = 0;
   MC_CUDA(cudaMemcpyAsync(&flags, w->h.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   MC_CUDA(cudaStreamSynchronize(s));
+  if (flags & mc::kFlagTimeout)
+    return fail(MC_ERR_TIMEOUT, "a grid barrier of the persistent batched step ran out of time; the world's state is unspecified");
   if (flags & mc::kFlagUnstable) return fail(MC_ERR_UNSTABLE, "bead velocity watchdog tripped (|U| > 0.5 or not finite)");
   return MC_OK;
 }

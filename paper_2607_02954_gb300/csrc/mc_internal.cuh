@@ -29,7 +29,10 @@ constexpr int kMaxNpbd = 64;
 // (B 2^k < 2^30, k in [8, 40]), so no sum can overflow; the bound and hence
 // the scale depend only on the data.
 
-enum : unsigned { kFlagUnstable = 1u };
+enum : unsigned {
+  kFlagUnstable = 1u,   // the velocity watchdog tripped
+  kFlagTimeout = 2u     // a grid barrier of the persistent batched step ran out of time
+};
 
 // Everything the kernels need to know about one world.  Lives in device
 // memory as one entry of a world table; all pointers are device pointers.
@@ -111,6 +114,15 @@ struct AdjDev {
   const float* theta_n;    // [E] edge angles at the start of the step
 };
 
+// Launch configuration of a plan's steps.  Every choice advances the worlds
+// bitwise the same; the autotuner (mc_tune.cu) picks the fastest one for
+// each class of plan.
+struct LaunchCfg {
+  int persistent = 0;     // 3 or 4: one cooperative launch per run of steps with that many blocks per SM (k_persist.cu)
+  int pbd_warps = 8;      // most filaments (warps) per block of the PBD kernels: 8, 4 or 2
+  int scan_kernels = 0;   // 0: one scan kernel when every world fits one scan block; 2: always two
+};
+
 // A set of worlds advanced together, with the work items of each stage.
 struct Plan {
   int n_worlds = 0;
@@ -137,9 +149,18 @@ struct Plan {
   int2* d_cell_items = nullptr;  // (world, first cell)
   int2* d_scan_items = nullptr;  // (world, scan chunk)
   void* d_mem = nullptr;
+  unsigned* d_persist_bar = nullptr;   // [3] barrier words and status of the persistent step
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
+  LaunchCfg cfg;
+  bool tuned = false;                  // cfg has been looked up or measured for this plan
 };
+
+// --- persistent batched step (k_persist.cu) ---------------------------------
+bool persistent_supported(const Plan& p);
+cudaError_t launch_persistent(const Plan& p, int n, cudaStream_t s);
+void persistent_setup();   // host set-up (occupancy queries) outside any stream capture
+void persistent_test_settings(unsigned extra_arrivals, unsigned long long timeout_ns);
 
 // --- stage launchers (one launch covers every world of the plan) ---------
 void launch_pbd(const Plan& p, cudaStream_t s);
@@ -213,6 +234,17 @@ size_t world_layout(WorldDev& h, void* arena);
 mc_status plan_build(mc_world* const* ws, int n, cudaStream_t s, Plan& out);
 mc_status plan_run(Plan& p, int n_steps, cudaStream_t s);
 void plan_free(Plan& p, cudaStream_t s);
+void plan_set_cfg(Plan& p, const LaunchCfg& c);   // drops the captured graph when the configuration changes
+// A device copy of a world (same state, its own arena; no plan of its own)
+// made on stream s, or nullptr when its memory cannot be allocated.
+mc_world* world_clone(const mc_world* w, cudaStream_t s);
+
+// --- autotuner (mc_tune.cu) -------------------------------------------------
+// Looks up, or measures on device copies of the worlds, the launch
+// configuration of plan p of worlds ws[0..n) (see mc_autotune); with
+// `automatic`, only for plans large enough to repay the measurement and only
+// when the tuner is enabled.
+mc_status plan_tune(mc_world* const* ws, int n, Plan& p, cudaStream_t s, bool automatic);
 
 // --- host accessors for code outside the ABI translation unit ------------
 const WorldDev& world_dev(const mc_world* w);

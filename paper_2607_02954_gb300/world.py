@@ -276,6 +276,35 @@ def step_batched(worlds: Sequence[World], n_steps: int, stream=None):
     L.check(L.load().mc_step_batched(arr, len(worlds), int(n_steps), stream_handle(stream)))
 
 
+def _handles(worlds: Sequence[World]):
+    return (ctypes.c_void_p * len(worlds))(*[w.handle.value for w in worlds])
+
+
+def _cfg_dict(c: L.mc_launch_config) -> Dict:
+    return {"persistent": c.persistent, "pbd_warps": c.pbd_warps, "scan_kernels": c.scan_kernels}
+
+
+def autotune(worlds: Sequence[World], stream=None) -> Dict:
+    """Tunes the launch configuration of the plan of these worlds (one world,
+    or the batch as step_batched passes it) and returns the choice."""
+    c = L.mc_launch_config()
+    L.check(L.load().mc_autotune(_handles(worlds), len(worlds), stream_handle(stream), ctypes.byref(c)))
+    return _cfg_dict(c)
+
+
+def launch_config(worlds: Sequence[World]) -> Dict:
+    """The launch configuration the plan of these worlds runs with."""
+    c = L.mc_launch_config()
+    L.check(L.load().mc_launch_config_get(_handles(worlds), len(worlds), ctypes.byref(c)))
+    return _cfg_dict(c)
+
+
+def set_launch_config(worlds: Sequence[World], persistent: int = 0, pbd_warps: int = 8, scan_kernels: int = 0):
+    """Pins the launch configuration of the plan of these worlds."""
+    c = L.mc_launch_config(persistent=int(persistent), pbd_warps=int(pbd_warps), scan_kernels=int(scan_kernels))
+    L.check(L.load().mc_launch_config_set(_handles(worlds), len(worlds), ctypes.byref(c)))
+
+
 def _result_dict(r: L.mc_result) -> Dict:
     return {"com_disp": (r.com_disp[0], r.com_disp[1]), "e_bend": r.e_bend, "e_pos": r.e_pos,
             "energy": r.energy, "status": r.status, "n_steps": r.n_steps,

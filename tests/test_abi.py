@@ -119,3 +119,15 @@ def test_fault_injection_and_cancel_validate_arguments():
     assert lib.mc_inject_world_alloc_failure(-1) == 1
     assert lib.mc_inject_world_alloc_failure(0) == 0
     assert lib.mc_serve_cancel(None, 1) == 1
+
+
+def test_launch_config_calls_validate_arguments():
+    lib = L.load()
+    c = L.mc_launch_config(persistent=0, pbd_warps=8, scan_kernels=0)
+    assert lib.mc_launch_config_set(None, 0, ctypes.byref(c)) == 1
+    assert lib.mc_launch_config_get(None, 1, ctypes.byref(c)) == 1
+    assert lib.mc_autotune(None, 1, None, None) == 1
+    assert lib.mc_autotune_mode(2) == 1
+    assert lib.mc_autotune_mode(1) == 0
+    assert lib.mc_debug_barrier_test(2, 1000) == 1
+    assert lib.mc_debug_barrier_test(0, 10) == 1
