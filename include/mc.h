@@ -78,7 +78,7 @@ typedef enum mc_mem_kind { MC_MEM_HOST = 0, MC_MEM_DEVICE = 1 } mc_mem_kind;
  *            before it); 1: red-black passes (within each pass the joints or
  *            edges of even index in their filament first, then the odd ones
  *            from the updated state: a two-colour Gauss-Seidel sweep).  The
- *            reverse mode supports order 0 only.
+ *            reverse mode supports both.
  *   layers   1: the beads are the immersed-boundary points; 2: two-layer
  *            filament (Fluid-filament Interaction): each bead couples to the
  *            fluid at X +- layer_half n (n the filament's unit normal at the
@@ -389,16 +389,18 @@ mc_status mc_rollout_backward(mc_world* w, const float* dL_dx, const float* dL_d
  *              length;
  *   dL_dk      [3] (device, may be NULL): with respect to k_bend,
  *              k_stretch, k_shear of the world.
- * The stiffness gradients are sums over all edges, joints, passes and steps
- * taken with float atomics (not bitwise repeatable).  Errors as
- * mc_rollout_backward. */
+ * The stiffness gradients are sums over all edges, joints, passes and steps,
+ * added per filament and then over filaments in a fixed order.  Every
+ * gradient of the reverse mode is bitwise repeatable: its scatters sum in
+ * 64-bit fixed point.  Errors as mc_rollout_backward. */
 mc_status mc_rollout_backward_params(mc_world* w, const float* dL_dx, const float* dL_dy, float* dL_dtheta0,
                                      float* dL_dL_rest, float* dL_dk, void* stream);
 
 /* Folding loss with a polyline target (device arrays): loss[0] = mean over
  * beads of the squared distance from the unwrapped position to the nearest
  * segment of the polyline poly_xy [n_vertices][2]; dL_dx, dL_dy [N] its
- * gradient.  loss is one device float (accumulated with atomics). */
+ * gradient.  loss is one device float (written; summed in a fixed order, so
+ * bitwise repeatable). */
 mc_status mc_loss_polyline(mc_world* w, const float* poly_xy, int n_vertices, float* loss, float* dL_dx,
                            float* dL_dy, void* stream);
 

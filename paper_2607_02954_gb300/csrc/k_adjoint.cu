@@ -12,11 +12,27 @@
 //   a1  theta_rest = theta0 + drive(t)
 // w(c - X) = phi(c_x - X_x) phi(c_y - X_y) (Peskin 4-point); its gradient
 // with respect to X uses phi' at the same four cells per axis.  The adjoint
-// scatters (transposed gathers) use float atomics: gradients agree with the
-// exact reverse-mode result to rounding, not bitwise between runs.
+// scatters (transposed gathers) accumulate in 64-bit fixed point: each term
+// is rounded once to a scale 2^k with N max|term| 2^k < 2^62, the bound
+// taken from the largest term's factor (a grid-wide maximum, which does not
+// depend on order), so the integer sums, and every gradient, are bitwise
+// repeatable.  The stiffness gradients are summed per filament and then
+// over filaments in a fixed order.
 #include "mc_internal.cuh"
 
 namespace mc {
+
+// The largest |v| of the warp's lanes into *slot (float bits; non-negative
+// floats order like their bit patterns).
+__device__ __forceinline__ void warp_max_abs(unsigned* slot, float v) {
+  v = fabsf(v);
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0 && v > 0.0f) atomicMax(slot, __float_as_uint(v));
+}
+
+// A 64-bit fixed-point term (two's complement in the unsigned accumulator).
+__device__ __forceinline__ unsigned long long fx64(float v) { return (unsigned long long)__float2ll_rn(v); }
+__device__ __forceinline__ float fx64_value(unsigned long long q, float inv) { return (float)(long long)q * inv; }
 
 // Peskin weights and their derivatives with respect to the bead coordinate:
 // with s = sqrt(1 + 4a - 4a^2), s' = (2 - 4a)/s.
@@ -53,23 +69,30 @@ __device__ __forceinline__ Stencil make_stencil(const float4& p, int W, int H) {
 }
 
 // ---------------------------------------------------------------------------
-// a8 transposed: u_bar(c) += sum_i w(c - X_i) dt X_bar_i (float atomics).
+// a8 transposed: u_bar(c) += sum_i w(c - X_i) dt X_bar_i, fixed point with
+// the bound N max|dt X_bar| (slot a.par of amax, written by the kernel that
+// produced X_bar).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int ubar_exponent(const WorldDev& w, const AdjDev& a) {
+  return fix_exponent64((float)w.N * __uint_as_float(a.amax[a.par]));
+}
+
 __global__ void __launch_bounds__(256) k_adj_spread_u(const WorldDev* __restrict__ wd, AdjDev a) {
   const WorldDev& w = *wd;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= w.N) return;
+  const float scale = pow2f(ubar_exponent(w, a));
   const Stencil s = make_stencil(w.pos[i], w.W, w.H);
   const float2 xb = a.adjX[i];
-  const float ux = w.dt * xb.x, uy = w.dt * xb.y;
+  const float ux = w.dt * xb.x * scale, uy = w.dt * xb.y * scale;
 #pragma unroll
   for (int b = 0; b < 4; ++b)
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const float wgt = s.wx[c] * s.wy[b];
-      float2* g = &a.ubar[s.iy[b] + s.ix[c]];
-      atomicAdd(&g->x, wgt * ux);
-      atomicAdd(&g->y, wgt * uy);
+      unsigned long long* g = &a.ubar[2 * (s.iy[b] + s.ix[c])];
+      atomicAdd(g, fx64(wgt * ux));
+      atomicAdd(g + 1, fx64(wgt * uy));
     }
 }
 
@@ -87,11 +110,22 @@ __global__ void __launch_bounds__(256) k_adj_spread_u(const WorldDev* __restrict
 // returns d_bar and F_bar; d_bar_i is pushed to the cell the population was
 // pulled from, so every adjoint population is written once.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 adj_lbm_cell(const WorldDev& w, const AdjDev& a, int src_parity, int c);
+
 __global__ void __launch_bounds__(256) k_adj_lbm(const WorldDev* __restrict__ wd, AdjDev a, int src_parity) {
   const WorldDev& w = *wd;
-  const int W = w.W, H = w.H, HW = H * W;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= HW) return;
+  float m = 0.0f;
+  if (c < w.H * w.W) {
+    const float2 fb = adj_lbm_cell(w, a, src_parity, c);
+    m = fmaxf(fabsf(fb.x), fabsf(fb.y));
+  }
+  warp_max_abs(&a.amax[2], m);   // the bound of the steric spread Q (k_adj_bead_a)
+}
+
+// One cell of k_adj_lbm: writes the population adjoints and F_bar, returns F_bar.
+__device__ __forceinline__ float2 adj_lbm_cell(const WorldDev& w, const AdjDev& a, int src_parity, int c) {
+  const int W = w.W, H = w.H, HW = H * W;
   const int y = c / W, x = c - y * W;
   const int xm = x == 0 ? W - 1 : x - 1, xp = x == W - 1 ? 0 : x + 1;
   const int ym = y == 0 ? H - 1 : y - 1, yp = y == H - 1 ? 0 : y + 1;
@@ -115,7 +149,8 @@ __global__ void __launch_bounds__(256) k_adj_lbm(const WorldDev* __restrict__ wd
   float ob[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) ob[i] = a.adjG_next[i * HW + c];
-  const float2 ubx = a.ubar[c];
+  const float uinv = pow2f(-ubar_exponent(w, a));
+  const float2 ubx = make_float2(fx64_value(a.ubar[2 * c], uinv), fx64_value(a.ubar[2 * c + 1], uinv));
   float db[9];
   float drho_b = 0.0f, rho_b = 0.0f, uu_b = 0.0f, uF_b = 0.0f;
   float uxb = ubx.x, uyb = ubx.y, Fxb = 0.0f, Fyb = 0.0f;
@@ -181,18 +216,25 @@ __global__ void __launch_bounds__(256) k_adj_lbm(const WorldDev* __restrict__ wd
     a.adjG_cur[i * HW + src[i]] = v;   // adjoint of the pulled post-collision value
   }
   a.Fbar[c] = make_float2(Fxb, Fyb);
+  return make_float2(Fxb, Fyb);
 }
 
 // ---------------------------------------------------------------------------
 // a8 and a6 gathers transposed, per bead:
 //   Ftot_bar_i = sum_c w F_bar(c)
 //   X_bar_i   += sum_c grad_X w [u(c).U_bar_i + F_bar(c).Ftot_i]
-// then Q(c) += w(c - X_i) Ftot_bar_i (float atomics) for the steric chain.
+// then Q(c) += w(c - X_i) Ftot_bar_i for the steric chain, fixed point with
+// the bound N max|F_bar| (|Ftot_bar_i| <= max|F_bar|: the weights sum to 1).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int q_exponent(const WorldDev& w, const AdjDev& a) {
+  return fix_exponent64((float)w.N * __uint_as_float(a.amax[2]));
+}
+
 __global__ void __launch_bounds__(256) k_adj_bead_a(const WorldDev* __restrict__ wd, AdjDev a) {
   const WorldDev& w = *wd;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= w.N) return;
+  const float qscale = pow2f(q_exponent(w, a));
   const Stencil s = make_stencil(w.pos[i], w.W, w.H);
   const float2 xb = a.adjX[i];
   const float Ubx = w.dt * xb.x, Uby = w.dt * xb.y;
@@ -215,14 +257,15 @@ __global__ void __launch_bounds__(256) k_adj_bead_a(const WorldDev* __restrict__
     }
   a.adjX[i] = make_float2(xb.x + gx, xb.y + gy);
   a.fbt[i] = make_float2(ftbx, ftby);
+  const float qx = ftbx * qscale, qy = ftby * qscale;
 #pragma unroll
   for (int b = 0; b < 4; ++b)
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const float wgt = s.wx[c] * s.wy[b];
-      float2* q = &a.Q[s.iy[b] + s.ix[c]];
-      atomicAdd(&q->x, wgt * ftbx);
-      atomicAdd(&q->y, wgt * ftby);
+      unsigned long long* q = &a.Q[2 * (s.iy[b] + s.ix[c])];
+      atomicAdd(q, fx64(wgt * qx));
+      atomicAdd(q + 1, fx64(wgt * qy));
     }
 }
 
@@ -250,17 +293,18 @@ __global__ void __launch_bounds__(256) k_adj_rho_blur(const WorldDev* __restrict
   const int ew = tw + 2 * R, eh = th + 2 * R;   // region: rows y0 - R .., columns x0 - R ..
   const int qw = ew + 2, qh = eh + 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const float qinv = pow2f(-q_exponent(w, a));
   // rows by warp, columns by lane (no divisions); wrap by at most two periods
   for (int i = warp; i < qh; i += nw) {
     int gy = y0 - R - 1 + i;
     while (gy < 0) gy += H;
     while (gy >= H) gy -= H;
-    const float2* __restrict__ row = a.Q + (size_t)gy * W;
+    const unsigned long long* __restrict__ row = a.Q + 2 * (size_t)gy * W;
     for (int j = lane; j < qw; j += 32) {
       int gx = x0 - R - 1 + j;
       while (gx < 0) gx += W;
       while (gx >= W) gx -= W;
-      q[i * kQ + j] = row[gx];
+      q[i * kQ + j] = make_float2(fx64_value(row[2 * gx], qinv), fx64_value(row[2 * gx + 1], qinv));
     }
   }
   __syncthreads();
@@ -343,13 +387,67 @@ __global__ void __launch_bounds__(256) k_adj_bead_b(const WorldDev* __restrict__
 // L_rest_bar += (per edge), and (k_bend, k_stretch, k_shear)_bar += (float
 // atomics, one per warp).
 // ---------------------------------------------------------------------------
+//
+// Red-black passes (kRB, pbd_order 1) reverse colour by colour: the tape
+// keeps, per pass, theta before the bending pass, after its even joints and
+// after it, and the corrections d before the even and before the odd edges
+// of the position pass; the reverse runs odd edges, even edges, odd joints,
+// even joints, each colour's constraints independent of one another.
+// ---------------------------------------------------------------------------
 constexpr int kAdjPbdThreads = 64;  // threads per filament
 constexpr int kAdjPbdPerBead = 12;   // floats of working arrays per bead slot
-constexpr int kAdjTapePerPass = 4;   // per pass: theta before and after the bend pass, d (x, y)
+constexpr int kAdjTapePerPass = 4;   // Jacobi, per pass: theta before and after the bend pass, d (x, y)
+constexpr int kAdjTapePerPassRB = 7; // red-black, per pass: theta x 3, d (x, y) before each edge colour
 
+// The position correction of edge e (Eqs. 2-4) from the edge vector v0 plus
+// corrections d, its frame angle th (turned in place): D into (Dx, Dy).
+__device__ __forceinline__ void adj_edge_forward(float vx, float vy, float L, float& th, float hs, float ksh,
+                                                 float ko, float& Dx, float& Dy) {
+  const float ell = sqrtf(vx * vx + vy * vy);
+  const float sc = (ell - L) / ell;
+  float sn, cs;
+  sincosf(th, &sn, &cs);
+  Dx = hs * (sc * vx + ksh * (vx - L * cs - sc * vx));
+  Dy = hs * (sc * vy + ksh * (vy - L * sn - sc * vy));
+  th += ko * (cs * vy - sn * vx) / L;
+}
+
+// The reverse of adj_edge_forward for edge vector (x, y), rest length L,
+// forward angle tb, given D_bar and the angle's adjoint thb after it:
+// returns the edge vector's adjoint and the angle's adjoint before it, and
+// adds the parameter adjoints.
+__device__ __forceinline__ void adj_edge_reverse(float x, float y, float L, float tb, float Dbx, float Dby,
+                                                 float thb, float hs, float ksh, float ko, float orient,
+                                                 float& xbx, float& xby, float& thb_new, float& hsb, float& kshb,
+                                                 float& gL) {
+  const float ell = sqrtf(x * x + y * y);
+  const float sc = (ell - L) / ell;
+  float sn, cs;
+  sincosf(tb, &sn, &cs);
+  // D = hs [(1 - ksh) sc x + ksh x - ksh L d]
+  const float xd = x * Dbx + y * Dby;
+  const float kq = hs * (1.0f - ksh) * (L / (ell * ell * ell)) * xd;
+  xbx = hs * ((1.0f - ksh) * sc + ksh) * Dbx + kq * x;
+  xby = hs * ((1.0f - ksh) * sc + ksh) * Dby + kq * y;
+  thb_new = thb + (-hs * ksh * L) * (-sn * Dbx + cs * Dby);
+  // theta += ko (cs y - sn x) / L
+  const float turn = (cs * y - sn * x) / L;
+  thb_new += thb * ko * (-sn * y - cs * x) / L;
+  xbx += thb * ko * (-sn) / L;
+  xby += thb * ko * cs / L;
+  // parameters: D = hs G, ko = orient hs ksh
+  const float rx = x - L * cs - sc * x, ry = y - L * sn - sc * y;
+  const float Gx = sc * x + ksh * rx, Gy = sc * y + ksh * ry;
+  hsb += Gx * Dbx + Gy * Dby + thb * orient * ksh * turn;
+  kshb += hs * (rx * Dbx + ry * Dby) + thb * orient * hs * turn;
+  gL += hs * (-(1.0f - ksh) * xd / ell - ksh * (cs * Dbx + sn * Dby)) - thb * ko * turn / L;
+}
+
+template <bool kRB>
 __global__ void __launch_bounds__(kAdjPbdThreads) k_adj_pbd(const WorldDev* __restrict__ wd, AdjDev a,
                                                             const int2* __restrict__ items, int n_items,
                                                             int maxB, int n_pbd) {
+  constexpr int kTape = kRB ? kAdjTapePerPassRB : kAdjTapePerPass;
   extern __shared__ __align__(16) float smem[];
   const WorldDev& w = *wd;
   const int tid = threadIdx.x, lane = tid & 31;
@@ -400,8 +498,41 @@ __global__ void __launch_bounds__(kAdjPbdThreads) k_adj_pbd(const WorldDev* __re
   const float orient = w.orient;
   const float ko = orient * hs * ksh;
   // ---- forward recompute with tape ----
-  for (int it = 0; it < n_pbd; ++it) {
-    float* tp = tape + it * kAdjTapePerPass * maxB;
+  constexpr int T2 = 2 * kAdjPbdThreads;
+  for (int it = 0; kRB && it < n_pbd; ++it) {
+    float* tp = tape + it * kTape * maxB;
+    for (int e = tid; e < nE; e += kAdjPbdThreads) tp[e] = th[e];
+    __syncthreads();
+    for (int c = 0; c < 2; ++c) {   // bending pass, even joints then odd ones
+      for (int j = 2 * tid + c; j < nJ; j += T2) {
+        const float Cj = th[j + 1] - th[j] - thr[j];
+        th[j] += hb * Cj;
+        th[j + 1] -= hb * Cj;
+      }
+      __syncthreads();
+      for (int e = tid; e < nE; e += kAdjPbdThreads) tp[(c + 1) * maxB + e] = th[e];
+      __syncthreads();
+    }
+    for (int c = 0; c < 2; ++c) {   // position pass, even edges then odd ones
+      for (int i = tid; i < B; i += kAdjPbdThreads) {
+        tp[(3 + 2 * c) * maxB + i] = dx[i];
+        tp[(4 + 2 * c) * maxB + i] = dy[i];
+      }
+      __syncthreads();
+      for (int e = 2 * tid + c; e < nE; e += T2) {
+        float Dxe, Dye;
+        adj_edge_forward(vx[e] + (dx[e + 1] - dx[e]), vy[e] + (dy[e + 1] - dy[e]), Lr[e], th[e], hs, ksh, ko,
+                         Dxe, Dye);
+        dx[e] += Dxe;
+        dy[e] += Dye;
+        dx[e + 1] -= Dxe;
+        dy[e + 1] -= Dye;
+      }
+      __syncthreads();
+    }
+  }
+  for (int it = 0; !kRB && it < n_pbd; ++it) {
+    float* tp = tape + it * kTape * maxB;
     for (int e = tid; e < nE; e += kAdjPbdThreads) tp[e] = th[e];
     for (int j = tid; j < nJ; j += kAdjPbdThreads) Cb[j] = th[j + 1] - th[j] - thr[j];
     __syncthreads();
@@ -445,7 +576,7 @@ __global__ void __launch_bounds__(kAdjPbdThreads) k_adj_pbd(const WorldDev* __re
     dy[i] = db.y;
   }
   for (int e = tid; e < nE; e += kAdjPbdThreads) th[e] = a.adjTh[e0 + e];
-  float* v0bx = tape + n_pbd * kAdjTapePerPass * maxB;
+  float* v0bx = tape + n_pbd * kTape * maxB;
   float* v0by = v0bx + maxB;
   for (int e = tid; e < nE; e += kAdjPbdThreads) {
     v0bx[e] = 0.0f;
@@ -453,8 +584,51 @@ __global__ void __launch_bounds__(kAdjPbdThreads) k_adj_pbd(const WorldDev* __re
   }
   float hbb = 0.0f, hsb = 0.0f, kshb = 0.0f;
   __syncthreads();
-  for (int it = n_pbd - 1; it >= 0; --it) {
-    const float* tp = tape + it * kAdjTapePerPass * maxB;
+  for (int it = n_pbd - 1; kRB && it >= 0; --it) {
+    const float* tp = tape + it * kTape * maxB;
+    for (int c = 1; c >= 0; --c) {   // position pass: odd edges, then even ones
+      const float* dX = tp + (3 + 2 * c) * maxB;
+      const float* dY = tp + (4 + 2 * c) * maxB;
+      for (int e = tid; e < nE; e += kAdjPbdThreads) {
+        if ((e & 1) != c) {   // the other colour's edges add nothing in this phase
+          Dx[e] = 0.0f;
+          Dy[e] = 0.0f;
+          continue;
+        }
+        float xbx, xby, thb_new;
+        adj_edge_reverse(vx[e] + (dX[e + 1] - dX[e]), vy[e] + (dY[e + 1] - dY[e]), Lr[e], tp[2 * maxB + e],
+                         dx[e] - dx[e + 1], dy[e] - dy[e + 1], th[e], hs, ksh, ko, orient, xbx, xby, thb_new, hsb,
+                         kshb, gLa[e]);
+        Dx[e] = xbx;
+        Dy[e] = xby;
+        th[e] = thb_new;
+        v0bx[e] += xbx;
+        v0by[e] += xby;
+      }
+      __syncthreads();
+      for (int i = tid; i < B; i += kAdjPbdThreads) {
+        const float ax = i < nE ? Dx[i] : 0.0f, ay = i < nE ? Dy[i] : 0.0f;
+        const float bx = i > 0 ? Dx[i - 1] : 0.0f, by = i > 0 ? Dy[i - 1] : 0.0f;
+        dx[i] += bx - ax;
+        dy[i] += by - ay;
+      }
+      __syncthreads();
+    }
+    for (int c = 1; c >= 0; --c) {   // bending pass: odd joints, then even ones
+      const float* tb = tp + c * maxB;   // angles before this colour
+      for (int j = 2 * tid + c; j < nJ; j += T2) {
+        const float dth = th[j] - th[j + 1];
+        hbb += (tb[j + 1] - tb[j] - thr[j]) * dth;
+        const float Cbj = hb * dth;
+        th[j] -= Cbj;
+        th[j + 1] += Cbj;
+        thrb[j] -= Cbj;
+      }
+      __syncthreads();
+    }
+  }
+  for (int it = n_pbd - 1; !kRB && it >= 0; --it) {
+    const float* tp = tape + it * kTape * maxB;
     // position pass reverse: D_bar_e = d_bar_e - d_bar_{e+1}
     for (int e = tid; e < nE; e += kAdjPbdThreads) {
       const float Dbx = dx[e] - dx[e + 1], Dby = dy[e] - dy[e + 1];
@@ -524,29 +698,69 @@ __global__ void __launch_bounds__(kAdjPbdThreads) k_adj_pbd(const WorldDev* __re
     a.gL[e0 + e] += gLa[e] * dLdL0;
   }
   for (int j = tid; j < nJ; j += kAdjPbdThreads) a.gth0[j0 + j] += thrb[j];
-  for (int i = tid; i < B; i += kAdjPbdThreads) {
-    const float ax = i < nE ? v0bx[i] : 0.0f, ay = i < nE ? v0by[i] : 0.0f;        // X_i is x_1 of edge i
-    const float bx = i > 0 ? v0bx[i - 1] : 0.0f, by = i > 0 ? v0by[i - 1] : 0.0f;  // ... x_2 of edge i-1
-    float2 xb = a.adjX[b0 + i];
-    xb.x += bx - ax;
-    xb.y += by - ay;
-    a.adjX[b0 + i] = xb;
+  // X_bar is final for this step: its largest |dt X_bar| bounds the next
+  // reversed step's u_bar (slot par ^ 1; every lane takes part)
+  float xm = 0.0f;
+  for (int i0 = 0; i0 < B; i0 += kAdjPbdThreads) {
+    const int i = i0 + tid;
+    if (i < B) {
+      const float ax = i < nE ? v0bx[i] : 0.0f, ay = i < nE ? v0by[i] : 0.0f;        // X_i is x_1 of edge i
+      const float bx = i > 0 ? v0bx[i - 1] : 0.0f, by = i > 0 ? v0by[i - 1] : 0.0f;  // ... x_2 of edge i-1
+      float2 xb = a.adjX[b0 + i];
+      xb.x += bx - ax;
+      xb.y += by - ay;
+      a.adjX[b0 + i] = xb;
+      xm = fmaxf(xm, w.dt * fmaxf(fabsf(xb.x), fabsf(xb.y)));
+    }
   }
-  // k_bend = 2 hb, k_stretch = 2 hs, k_shear = ksh
+  warp_max_abs(&a.amax[a.par ^ 1], xm);
+  // k_bend = 2 hb, k_stretch = 2 hs, k_shear = ksh: the filament's sums
+  // (warps reduced in a fixed order) added to its own accumulator
   for (int o = 16; o > 0; o >>= 1) {
     hbb += __shfl_xor_sync(0xffffffffu, hbb, o);
     hsb += __shfl_xor_sync(0xffffffffu, hsb, o);
     kshb += __shfl_xor_sync(0xffffffffu, kshb, o);
   }
-  if (lane == 0) {   // one partial per warp
-    atomicAdd(&a.gk[0], 0.5f * hbb);
-    atomicAdd(&a.gk[1], 0.5f * hsb);
-    atomicAdd(&a.gk[2], kshb);
+  __shared__ float part[3 * (kAdjPbdThreads / 32)];
+  if (lane == 0) {
+    part[3 * (tid >> 5)] = hbb;
+    part[3 * (tid >> 5) + 1] = hsb;
+    part[3 * (tid >> 5) + 2] = kshb;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float sb = 0.0f, ss = 0.0f, sk = 0.0f;
+    for (int k = 0; k < kAdjPbdThreads / 32; ++k) {
+      sb += part[3 * k];
+      ss += part[3 * k + 1];
+      sk += part[3 * k + 2];
+    }
+    a.gkf[3 * f] += 0.5f * sb;
+    a.gkf[3 * f + 1] += 0.5f * ss;
+    a.gkf[3 * f + 2] += sk;
   }
 }
 
-size_t adj_pbd_smem_per_filament(int maxB, int n_pbd) {
-  return (size_t)maxB * (kAdjPbdPerBead + kAdjTapePerPass * n_pbd + 2) * sizeof(float);
+// The stiffness gradients: the per-filament sums added over filaments in
+// index order (one block).
+__global__ void __launch_bounds__(256) k_adj_gk_reduce(const float* __restrict__ gkf, int n_fil, float* gk) {
+  __shared__ float red[3][256];
+  float s[3] = {0.0f, 0.0f, 0.0f};
+  for (int f = threadIdx.x; f < n_fil; f += blockDim.x)
+    for (int c = 0; c < 3; ++c) s[c] += gkf[3 * f + c];
+  for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = s[c];
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h)
+      for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) gk[threadIdx.x] = red[threadIdx.x][0];
+}
+
+size_t adj_pbd_smem_per_filament(int maxB, int n_pbd, int order) {
+  const int per = order == 1 ? kAdjTapePerPassRB : kAdjTapePerPass;
+  return (size_t)maxB * (kAdjPbdPerBead + per * n_pbd + 2) * sizeof(float);
 }
 
 // ---------------------------------------------------------------------------
@@ -554,14 +768,16 @@ size_t adj_pbd_smem_per_filament(int maxB, int n_pbd) {
 // over beads of the squared distance from the unwrapped position
 // P_i = X0_i + D_i to the nearest segment of the polyline, and dL/dP_i.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_loss_polyline(const WorldDev* __restrict__ wd, const float2* __restrict__ pos0,
-                                                       const float2* __restrict__ poly, int nv, float* loss,
-                                                       float* gx, float* gy) {
+__global__ void __launch_bounds__(1024) k_loss_polyline(const WorldDev* __restrict__ wd, const float2* __restrict__ pos0,
+                                                        const float2* __restrict__ poly, int nv, float* loss,
+                                                        float* gx, float* gy) {
+  // one block: each thread sums its beads in index order, then a fixed tree
+  // (the loss is bitwise repeatable)
   const WorldDev& w = *wd;
-  __shared__ float red[256];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ float red[1024];
+  const float invN = 1.0f / (float)max(w.N, 1);
   float l = 0.0f;
-  if (i < w.N) {
+  for (int i = threadIdx.x; i < w.N; i += blockDim.x) {
     const float2 d = w.disp[i];
     const float px = pos0[i].x + d.x, py = pos0[i].y + d.y;
     float best = 3.0e38f, qx = px, qy = py;
@@ -578,18 +794,17 @@ __global__ void __launch_bounds__(256) k_loss_polyline(const WorldDev* __restric
         qy = cy;
       }
     }
-    const float invN = 1.0f / (float)w.N;
-    l = best * invN;
+    l += best * invN;
     gx[i] = 2.0f * (px - qx) * invN;
     gy[i] = 2.0f * (py - qy) * invN;
   }
   red[threadIdx.x] = l;
   __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
+  for (int s = 512; s > 0; s >>= 1) {
     if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
     __syncthreads();
   }
-  if (threadIdx.x == 0) atomicAdd(loss, red[0]);
+  if (threadIdx.x == 0) *loss = red[0];
 }
 
 __global__ void k_set_counter(long long* t, long long v, unsigned* fel_max) {
@@ -618,15 +833,25 @@ void launch_adj_step(const Plan& p, const WorldDev& h, AdjDev a, int src_parity,
   if (h.N) k_adj_bead_b<<<bead_blocks(h.N), kAdjBeadThreads, 0, s>>>(wd, a);
   if (p.n_fil_items) {
     const int mb = (p.max_B + 3) & ~3;
-    const size_t smem = adj_pbd_smem_per_filament(mb, h.n_pbd);
-    k_adj_pbd<<<p.n_fil_items, kAdjPbdThreads, smem, s>>>(wd, a, p.d_fil_items, p.n_fil_items, mb, h.n_pbd);
+    const size_t smem = adj_pbd_smem_per_filament(mb, h.n_pbd, h.pbd_order);
+    if (h.pbd_order == 1)
+      k_adj_pbd<true><<<p.n_fil_items, kAdjPbdThreads, smem, s>>>(wd, a, p.d_fil_items, p.n_fil_items, mb, h.n_pbd);
+    else
+      k_adj_pbd<false><<<p.n_fil_items, kAdjPbdThreads, smem, s>>>(wd, a, p.d_fil_items, p.n_fil_items, mb, h.n_pbd);
   }
+}
+
+void launch_adj_gk_reduce(const AdjDev& a, int n_fil, cudaStream_t s) {
+  k_adj_gk_reduce<<<1, 256, 0, s>>>(a.gkf, n_fil, a.gk);
 }
 
 void adj_setup(const Plan& p, const WorldDev& h) {
   const int mb = (p.max_B + 3) & ~3;
-  const size_t per = adj_pbd_smem_per_filament(mb, h.n_pbd);
-  if (per > 48 * 1024) cudaFuncSetAttribute(k_adj_pbd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)per);
+  const size_t per = adj_pbd_smem_per_filament(mb, h.n_pbd, h.pbd_order);
+  if (per > 48 * 1024) {
+    cudaFuncSetAttribute(k_adj_pbd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)per);
+    cudaFuncSetAttribute(k_adj_pbd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)per);
+  }
 }
 
 // theta0 [J] into the drive records' first component, L_rest [E] into the
@@ -745,8 +970,8 @@ void launch_loss_splat(const Plan& p, const WorldDev& h, const float* target, in
 
 void launch_loss_polyline(const Plan& p, const WorldDev& h, const float2* pos0, const float2* poly, int nv,
                           float* loss, float* gx, float* gy, cudaStream_t s) {
-  cudaMemsetAsync(loss, 0, sizeof(float), s);
-  if (h.N) k_loss_polyline<<<blocks(h.N), 256, 0, s>>>(p.d_worlds, pos0, poly, nv, loss, gx, gy);
+  if (h.N) k_loss_polyline<<<1, 1024, 0, s>>>(p.d_worlds, pos0, poly, nv, loss, gx, gy);
+  else cudaMemsetAsync(loss, 0, sizeof(float), s);
 }
 
 void launch_set_counter(const WorldDev& h, long long t, cudaStream_t s) {

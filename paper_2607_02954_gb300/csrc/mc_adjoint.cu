@@ -132,7 +132,7 @@ __global__ void k_seg_save(const mc::WorldDev* __restrict__ wd, char* cur, char*
 // `par` and intermediates from the record, the step counter, and the
 // per-step adjoint accumulators (u_bar, Q) cleared.
 __global__ void k_seg_restore(const mc::WorldDev* __restrict__ wd, const char* rec, int par, long long t,
-                              StepSlot sl, float2* ubar, float2* Q) {
+                              StepSlot sl, mc::AdjDev a) {
   const mc::WorldDev& h = *wd;
   const size_t HW = (size_t)h.H * h.W, n9 = 9 * HW;
   const size_t total = n9 > (size_t)h.N ? n9 : (size_t)h.N;
@@ -141,6 +141,10 @@ __global__ void k_seg_restore(const mc::WorldDev* __restrict__ wd, const char* r
     *h.t = t;
     h.fel_max[0] = 0u;
     h.fel_max[1] = 0u;
+    // the bounds this step's adjoint kernels produce: of Q, and of the
+    // next reversed step's u_bar (this step's u_bar reads slot a.par)
+    a.amax[2] = 0u;
+    a.amax[a.par ^ 1] = 0u;
   }
   for (size_t i = i0; i < total; i += (size_t)gridDim.x * blockDim.x) {
     if (i < (size_t)h.N) {
@@ -152,16 +156,27 @@ __global__ void k_seg_restore(const mc::WorldDev* __restrict__ wd, const char* r
       h.rho_b[i] = reinterpret_cast<const float*>(rec + sl.rho_b)[i];
       h.u[i] = reinterpret_cast<const float2*>(rec + sl.u)[i];
       h.F[i] = reinterpret_cast<const float2*>(rec + sl.F)[i];
-      ubar[i] = make_float2(0.0f, 0.0f);
-      Q[i] = make_float2(0.0f, 0.0f);
+      a.ubar[2 * i] = 0ull;
+      a.ubar[2 * i + 1] = 0ull;
+      a.Q[2 * i] = 0ull;
+      a.Q[2 * i + 1] = 0ull;
     }
     if (i < n9) h.g[par][i] = reinterpret_cast<const float*>(rec + sl.st.g)[i];
   }
 }
 
-__global__ void k_interleave(const float* gx, const float* gy, float2* out, int n) {
+// X_bar of the final positions from the caller's gradient, and its largest
+// |dt X_bar| (slot 0 of amax, zeroed before: the first reversed step's u_bar
+// bound).
+__global__ void k_interleave(const float* gx, const float* gy, float2* out, int n, float dt, unsigned* amax0) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = make_float2(gx[i], gy[i]);
+  float m = 0.0f;
+  if (i < n) {
+    out[i] = make_float2(gx[i], gy[i]);
+    m = dt * fmaxf(fabsf(gx[i]), fabsf(gy[i]));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(amax0, __float_as_uint(m));
 }
 
 }  // namespace
@@ -282,7 +297,7 @@ mc_status sweep(mc_world* w, mc::AdjDev a, float* const adjG[2], char* obs_keep,
   if (h.E) MC_ACUDA(cudaMemsetAsync(a.adjTh, 0, h.E * sizeof(float), s));
   if (h.J) MC_ACUDA(cudaMemsetAsync(a.gth0, 0, h.J * sizeof(float), s));
   if (h.E) MC_ACUDA(cudaMemsetAsync(a.gL, 0, h.E * sizeof(float), s));
-  MC_ACUDA(cudaMemsetAsync(a.gk, 0, 3 * sizeof(float), s));
+  if (h.n_fil) MC_ACUDA(cudaMemsetAsync(a.gkf, 0, 3 * (size_t)h.n_fil * sizeof(float), s));
   MC_ACUDA(cudaMemsetAsync(adjG[0], 0, 9 * HW * sizeof(float), s));
   int cur = 0;   // adjG[cur] holds the adjoint of the populations after the step being reversed
   const int64_t t0 = w->tape_t0;
@@ -312,15 +327,17 @@ mc_status sweep(mc_world* w, mc::AdjDev a, float* const adjG[2], char* obs_keep,
       const int64_t tn = tk + q;
       const int par = (int)(tn & 1);
       const char* rec = seg + (size_t)q * ss.bytes;
-      k_seg_restore<<<grid, 256, 0, s>>>(wd, rec, par, (long long)tn, ss, a.ubar, a.Q);
       a.adjG_next = adjG[cur];
       a.adjG_cur = adjG[cur ^ 1];
       a.theta_n = reinterpret_cast<const float*>(rec + ss.st.theta);
+      a.par = cur;   // reversed steps alternate the u_bar bound slots, the first reads slot 0
+      k_seg_restore<<<grid, 256, 0, s>>>(wd, rec, par, (long long)tn, ss, a);
       mc::launch_adj_step(w->plan, h, a, par, s);
       cur ^= 1;
     }
     MC_ACUDA(cudaGetLastError());
   }
+  mc::launch_adj_gk_reduce(a, h.n_fil, s);
   // back to the final state of the rollout
   const int64_t tf = t0 + n;
   const TapeTail tl = tape_tail(h, n_ck, sl);
@@ -341,11 +358,10 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
     return afail(MC_ERR_INVALID_ARG, "the world was stepped after mc_rollout_forward");
   const mc::WorldDev& h = w->h;
   if ((h.N && (!dL_dx || !dL_dy)) || (h.J && !dL_dtheta0)) return afail(MC_ERR_INVALID_ARG, "NULL gradient pointer");
-  if (h.pbd_order != 0) return afail(MC_ERR_INVALID_ARG, "the reverse mode supports Jacobi PBD (pbd_order 0) only");
   if (h.layers != 1) return afail(MC_ERR_INVALID_ARG, "the reverse mode supports layers = 1 only");
   if (h.ib != 0) return afail(MC_ERR_INVALID_ARG, "the reverse mode supports the penalty coupling (ib = 0) only");
   const int mb = (w->max_B + 3) & ~3;
-  if (mc::adj_pbd_smem_per_filament(mb, h.n_pbd) > 220 * 1024)
+  if (mc::adj_pbd_smem_per_filament(mb, h.n_pbd, h.pbd_order) > 220 * 1024)
     return afail(MC_ERR_INVALID_ARG, "filaments too long for the adjoint (reduce beads per filament or n_pbd)");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t HW = (size_t)h.H * h.W;
@@ -367,9 +383,11 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
   const size_t o_obs = take(3 * sizeof(unsigned long long));
   const size_t o_g0 = take(9 * HW * sizeof(float));
   const size_t o_g1 = take(9 * HW * sizeof(float));
-  const size_t o_ub = take(HW * sizeof(float2));
+  const size_t o_ub = take(2 * HW * sizeof(unsigned long long));
   const size_t o_Fb = take(HW * sizeof(float2));
-  const size_t o_Q = take(HW * sizeof(float2));
+  const size_t o_Q = take(2 * HW * sizeof(unsigned long long));
+  const size_t o_amax = take(4 * sizeof(unsigned));
+  const size_t o_gkf = take(3 * (size_t)h.n_fil * sizeof(float));
   const size_t o_rsb = take(HW * sizeof(float));
   const size_t o_fbt = take(h.N * sizeof(float2));
   const size_t o_dbar = take(h.N * sizeof(float2));
@@ -392,15 +410,18 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
   a.gL = reinterpret_cast<float*>(A + o_gL);
   a.gk = reinterpret_cast<float*>(A + o_gk);
   float* adjG[2] = {reinterpret_cast<float*>(A + o_g0), reinterpret_cast<float*>(A + o_g1)};
-  a.ubar = reinterpret_cast<float2*>(A + o_ub);
+  a.ubar = reinterpret_cast<unsigned long long*>(A + o_ub);
   a.Fbar = reinterpret_cast<float2*>(A + o_Fb);
-  a.Q = reinterpret_cast<float2*>(A + o_Q);
+  a.Q = reinterpret_cast<unsigned long long*>(A + o_Q);
+  a.amax = reinterpret_cast<unsigned*>(A + o_amax);
+  a.gkf = reinterpret_cast<float*>(A + o_gkf);
   a.rsb = reinterpret_cast<float*>(A + o_rsb);
   a.fbt = reinterpret_cast<float2*>(A + o_fbt);
   a.dbar = reinterpret_cast<float2*>(A + o_dbar);
 
   // inputs (caller memory): outside the cached graph
-  if (h.N) k_interleave<<<(h.N + 255) / 256, 256, 0, s>>>(dL_dx, dL_dy, a.adjX, h.N);
+  MC_ACUDA(cudaMemsetAsync(a.amax, 0, 4 * sizeof(unsigned), s));
+  if (h.N) k_interleave<<<(h.N + 255) / 256, 256, 0, s>>>(dL_dx, dL_dy, a.adjX, h.N, h.dt, a.amax);
   MC_ACUDA(cudaGetLastError());
   // the reverse sweep, captured once per (rollout length, checkpoint spacing,
   // start step, buffers) and replayed

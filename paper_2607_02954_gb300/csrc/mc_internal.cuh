@@ -105,14 +105,28 @@ struct AdjDev {
   float* gk;               // [3] accumulated gradient with respect to k_bend, k_stretch, k_shear
   const float* adjG_next;  // [9 H W] adjoint of the populations after the step
   float* adjG_cur;         // [9 H W] adjoint of the populations before it
-  float2* ubar;            // [H W] adjoint of the fluid velocity
+  unsigned long long* ubar;  // [2 H W] adjoint of the fluid velocity, 64-bit fixed point (x, y interleaved)
   float2* Fbar;            // [H W] adjoint of the force density
-  float2* Q;               // [H W] spread of the steric-force adjoint
+  unsigned long long* Q;   // [2 H W] spread of the steric-force adjoint, 64-bit fixed point
   float* rsb;              // [H W] adjoint of rho_s
   float2* fbt;             // [N] adjoint of F_el + F_s per bead
   float2* dbar;            // [N] adjoint of the PBD correction
   const float* theta_n;    // [E] edge angles at the start of the step
+  unsigned* amax;          // [3] bounds of the fixed-point sums (float bits): max |dt X_bar| by step
+                           // parity (slots 0, 1), max |F_bar| (slot 2)
+  float* gkf;              // [3 n_fil] per-filament sums of the stiffness gradients
+  int par;                 // parity of the step being reversed (the slot of amax its u_bar reads)
 };
+
+// Exponent k of a 64-bit fixed-point scale 2^k for sums of terms whose
+// total magnitude is below `bound` (bound 2^k < 2^62; k in [-64, 120]).
+__device__ __forceinline__ int fix_exponent64(float bound) {
+  if (!(bound > 0.0f)) return 62;
+  if (!(bound < 3.0e38f)) return -64;
+  const int e = ((__float_as_int(bound) >> 23) & 255) - 126;
+  const int k = 62 - e;
+  return k < -64 ? -64 : (k > 120 ? 120 : k);
+}
 
 // Launch configuration of a plan's steps.  Every choice advances the worlds
 // bitwise the same; the autotuner (mc_tune.cu) picks the fastest one for
@@ -188,7 +202,8 @@ constexpr int kKernelsPerStep = 8;
 
 // --- adjoint (one world) ----------------------------------------------------
 void launch_adj_step(const Plan& p, const WorldDev& h, AdjDev a, int src_parity, cudaStream_t s);
-size_t adj_pbd_smem_per_filament(int maxB, int n_pbd);
+void launch_adj_gk_reduce(const AdjDev& a, int n_fil, cudaStream_t s);   // gk = sum over filaments of gkf
+size_t adj_pbd_smem_per_filament(int maxB, int n_pbd, int order);
 void adj_setup(const Plan& p, const WorldDev& h);   // host set-up of the adjoint kernels (before capture)
 void launch_set_rest(const WorldDev& h, const float* theta0, const float* L_rest, cudaStream_t s);
 // Launches kernel k, with programmatic stream serialization (see pdl_wait)

@@ -45,11 +45,17 @@ def _oracle_grad(spec, n, gx, gy):
                                          torch.as_tensor(gy, dtype=torch.float64)))
 
 
-@pytest.mark.parametrize("case", ["tiny", "c1", "custom"])
+@pytest.mark.parametrize("case", ["tiny", "c1", "custom", "red_black", "red_black_c1"])
 def test_adjoint_matches_oracle_reverse_mode(case):
     rng = np.random.default_rng(3)
     if case == "tiny":
         spec, n, K = synth.tiny_world(3, side=32, lengths=(9, 7, 6)), 30, 7
+    elif case == "red_black":
+        spec, n, K = synth.tiny_world(3, side=32, lengths=(9, 8, 6, 2)), 30, 7
+        spec.params = synth.Params(pbd_order=1, k_bend=0.7, k_stretch=0.6, k_shear=0.4)
+    elif case == "red_black_c1":
+        spec, n, K = synth.world_c1(1), 20, 8
+        spec.params = synth.Params(pbd_order=1)
     elif case == "c1":
         spec, n, K = synth.world_c1(1), 20, 8
     else:
@@ -153,7 +159,7 @@ def test_rollout_fn_autograd_bridge():
     w.close()
 
 
-@pytest.mark.parametrize("case", ["tiny", "custom"])
+@pytest.mark.parametrize("case", ["tiny", "custom", "red_black"])
 def test_rest_length_and_stiffness_gradients_match_oracle(case):
     """mc_rollout_backward_params: gradients with respect to theta0, every
     edge's rest length and (k_bend, k_stretch, k_shear) against the FP64
@@ -162,6 +168,10 @@ def test_rest_length_and_stiffness_gradients_match_oracle(case):
     rng = np.random.default_rng(11)
     if case == "tiny":
         spec, n, K = synth.tiny_world(4, side=32, lengths=(9, 7, 6)), 25, 6
+    elif case == "red_black":
+        spec, n, K = synth.world_random(13, 64, 5), 20, 7
+        spec.params = synth.Params(nu=0.3, kappa=0.2, k_bend=0.7, k_stretch=0.6, k_shear=0.5, k_rep=1.0,
+                                   sigma=0.8, orient=1.0, n_pbd=3, pbd_order=1)
     else:
         spec, n, K = synth.world_random(12, 64, 5), 20, 7
         spec.params = synth.Params(nu=0.3, kappa=0.2, k_bend=0.7, k_stretch=0.6, k_shear=0.5, k_rep=1.0,
@@ -184,8 +194,8 @@ def test_rest_length_and_stiffness_gradients_match_oracle(case):
         assert err <= RTOL * scale, (key, err, scale)
 
 
-@pytest.mark.parametrize("params", [dict(pbd_order=1), dict(layers=2, layer_half=0.5)])
-def test_reverse_mode_rejects_red_black_pbd_and_two_layers(params):
+@pytest.mark.parametrize("params", [dict(layers=2, layer_half=0.5), dict(ib=1, mdf_iters=2)])
+def test_reverse_mode_rejects_two_layers_and_direct_forcing(params):
     from paper_2607_02954_gb300 import World
     from paper_2607_02954_gb300._lib import MCError
     spec = synth.tiny_world(7, side=32, lengths=(8, 6))
@@ -271,8 +281,8 @@ def test_rewind_and_set_rest_reproduce_fresh_worlds_bitwise():
 
 def test_replayed_reverse_sweep_matches_the_captured_one():
     """The second backward of the same rollout (rewind + forward) replays the
-    captured sweep; the gradient agrees with the first one (float atomics:
-    to rounding) and with the oracle."""
+    captured sweep; the gradient equals the first one bitwise (fixed-point
+    scatters) and agrees with the oracle."""
     from paper_2607_02954_gb300 import World
     spec = synth.tiny_world(11, side=32, lengths=(9, 8))
     n, K = 24, 5
@@ -286,8 +296,27 @@ def test_replayed_reverse_sweep_matches_the_captured_one():
     w.rollout_forward(n, K)
     g2 = t2n(w.rollout_backward(gx, gy)).astype(np.float64)
     w.close()
-    scale = np.max(np.abs(g1))
-    assert np.max(np.abs(g1 - g2)) <= 1e-5 * scale
+    assert np.array_equal(g1, g2)
     go = t2n(O.final_position_gradient(O.World(spec), n, torch.as_tensor(t2n(gx), dtype=torch.float64),
                                        torch.as_tensor(t2n(gy), dtype=torch.float64)))
     assert np.max(np.abs(g2 - go)) <= RTOL * np.max(np.abs(go))
+
+
+def test_reverse_mode_is_bitwise_repeatable():
+    """Two worlds with the same rollout give bitwise the same loss and
+    gradients with respect to theta0, the rest lengths and the stiffnesses
+    (the adjoint's scatters and sums do not depend on thread order)."""
+    from paper_2607_02954_gb300 import World
+    spec, poly = synth.world_c5(2)
+    n, K = 60, 20
+    outs = []
+    for _ in range(2):
+        w = World(spec)
+        w.rollout_forward(n, K)
+        loss, gx, gy = w.loss_polyline(poly)
+        g = w.rollout_backward_params(gx, gy)
+        outs.append((t2n(loss).copy(), {k: t2n(v).copy() for k, v in g.items()}))
+        w.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    for k in outs[0][1]:
+        assert np.array_equal(outs[0][1][k], outs[1][1][k]), k

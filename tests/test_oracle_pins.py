@@ -832,11 +832,13 @@ def _objective(w, n_steps, gx, gy, L_rest=None, ks=None):
     return float((st.D[:, 0] * gx).sum() + (st.D[:, 1] * gy).sum())
 
 
-def test_T10_parameter_gradient_matches_finite_differences():
+@pytest.mark.parametrize("order", [0, 1])
+def test_T10_parameter_gradient_matches_finite_differences(order):
     """Gradients with respect to the rest lengths and the three stiffnesses
-    against FP64 central differences of the same objective."""
+    against FP64 central differences of the same objective, with Jacobi and
+    with red-black PBD passes."""
     spec = synth.tiny_world(2, side=16, lengths=(7, 6))
-    spec.params = synth.Params(k_bend=0.6, k_stretch=0.7, k_shear=0.4, orient=1.0)
+    spec.params = synth.Params(k_bend=0.6, k_stretch=0.7, k_shear=0.4, orient=1.0, pbd_order=order)
     w = O.World(spec)
     rng = np.random.default_rng(5)
     gx = torch.tensor(rng.standard_normal(spec.N), dtype=F64)
