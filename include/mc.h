@@ -211,6 +211,11 @@ mc_status mc_step_batched(mc_world* const* worlds, int n_worlds, int n_steps, vo
  *   pbd_warps     most filaments per block of the PBD kernels: 8, 4 or 2
  *   scan_kernels  0: one bin-offset kernel when every world's bins fit one
  *                 scan block (1024 bins), else two; 2: always two
+ *   force_kernel  0: the fused force + LBM kernel with one 32x32 tile per
+ *                 block; 1: its warp-specialised persistent form (half of
+ *                 each block's warps run a tile's force phase while the
+ *                 other half collide the previous tile; worlds without two
+ *                 layers)
  * The autotuner measures the candidates on device copies of the plan's
  * worlds (the worlds do not move) and caches its choice per class of plan
  * (world count, sizes, tile and bead counts) for the life of the process.
@@ -224,6 +229,7 @@ typedef struct mc_launch_config {
   int persistent;     /* 0, 3 or 4 */
   int pbd_warps;      /* 8, 4 or 2 */
   int scan_kernels;   /* 0 or 2 */
+  int force_kernel;   /* 0 or 1 */
 } mc_launch_config;
 
 /* Tunes the plan of worlds[0..n_worlds) now (or takes its class's cached

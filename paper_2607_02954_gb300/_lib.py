@@ -67,7 +67,8 @@ class mc_result(ctypes.Structure):
 
 
 class mc_launch_config(ctypes.Structure):
-    _fields_ = [("persistent", ctypes.c_int), ("pbd_warps", ctypes.c_int), ("scan_kernels", ctypes.c_int)]
+    _fields_ = [("persistent", ctypes.c_int), ("pbd_warps", ctypes.c_int), ("scan_kernels", ctypes.c_int),
+                ("force_kernel", ctypes.c_int)]
 
 
 class mc_server_stats(ctypes.Structure):

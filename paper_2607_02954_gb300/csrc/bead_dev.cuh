@@ -37,12 +37,15 @@ __device__ __forceinline__ float4 advance_pos(const WorldDev& w, float4 p, float
   return make_float4(fx, fy, __int_as_float(cx), __int_as_float(cy));
 }
 
-// a8 for one bead at p = X^n with velocity U: the velocity record, the
-// watchdog (|U| > u_max or non-finite: flag the world, keep the bead),
+// a8 for one bead at p = X^n with velocity U: the velocity record (kRecord;
+// the advance fused into the next step's PBD skips it, since a run of steps
+// ends with a standalone advance that writes the last step's), the watchdog
+// (|U| > u_max or non-finite: flag the world, keep the bead),
 // X^{n+1} = wrap(X^n + dt U) in cell + fraction form, D += dt U.
 // Returns X^{n+1} (X^n when the watchdog fired).
+template <bool kRecord = true>
 __device__ __forceinline__ float4 advance_tail(const WorldDev& w, int i, float4 p, float Ux, float Uy) {
-  w.ubead[i] = make_float2(Ux, Uy);
+  if (kRecord) w.ubead[i] = make_float2(Ux, Uy);
   const float m2 = Ux * Ux + Uy * Uy;
   if (!(m2 <= w.u_max * w.u_max)) {   // also catches NaN
     atomicOr(w.flags, kFlagUnstable);
@@ -206,19 +209,28 @@ __device__ __forceinline__ float2 edge_vec(const float4 pa, const float4 pb, int
   return make_float2((float)dcx + (pb.x - pa.x), (float)dcy + (pb.y - pa.y));
 }
 
+// The per-edge factors of the position pass: sc = (l - L)/l = 1 - L/l with
+// l = |(x, y)| (from the hardware reciprocal square root), and the sine and
+// cosine of the frame angle (the hardware's, of the angle reduced to
+// [-pi, pi]).  Their errors (a few 1e-7) stay below the step's float32
+// resolution of the elastic force.
+__device__ __forceinline__ void pbd_edge_terms(float x, float y, float L, float th, float& sc, float& sn, float& cs) {
+  sc = fmaf(-L, rsqrtf(x * x + y * y), 1.0f);
+  const float tr = fmaf(-6.28318548f, rintf(th * 0.159154943f), th);
+  __sincosf(tr, &sn, &cs);
+}
+
 // Position pass of one edge (Eqs. 2-4) with current edge vector (x, y),
 // rest length L and frame angle th: the correction (ddx, ddy) of its first
 // bead (the second gets the opposite), and the frame's turn toward the edge.
 __device__ __forceinline__ void edge_correction(float x, float y, float L, float& th, const PbdConst& k, float& ddx,
                                                 float& ddy) {
-  const float ell = sqrtf(x * x + y * y);
-  const float sc = (ell - L) / ell;
+  float sc, sn, cs;
+  pbd_edge_terms(x, y, L, th, sc, sn, cs);
   const float csx = sc * x, csy = sc * y;
-  float sn, cs;
-  sincosf(th, &sn, &cs);
   ddx = k.hs * (csx + k.ksh * (x - L * cs - csx));
   ddy = k.hs * (csy + k.ksh * (y - L * sn - csy));
-  th += k.ko * (cs * y - sn * x) / L;   // frame turns toward the edge (orient)
+  th += k.ko * (cs * y - sn * x) * __frcp_rn(L);   // frame turns toward the edge (orient)
 }
 
 // Unit normal of the filament at a bead (two-layer coupling): t is the
@@ -304,11 +316,11 @@ __device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, 
     long long q = 0;
     if (hb0) {
       const float2 U = bead_velocity<kExt>(w, b0 + i0, P0, q);
-      P0 = advance_tail(w, b0 + i0, P0, U.x, U.y);
+      P0 = advance_tail<false>(w, b0 + i0, P0, U.x, U.y);
     }
     if (hb1) {
       const float2 U = bead_velocity<kExt>(w, b0 + i1, P1, q);
-      P1 = advance_tail(w, b0 + i1, P1, U.x, U.y);
+      P1 = advance_tail<false>(w, b0 + i1, P1, U.x, U.y);
     }
     if (kExt && w.observe && w.energy) obs_add_warp(&w.obs[2], q);
   } else if (kMode == 2) {
@@ -452,7 +464,7 @@ __device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, 
     for (int i = lane; i < B; i += 32) {
       const float4 p = w.pos[b0 + i];
       const float2 U = bead_velocity<kExt>(w, b0 + i, p, q);
-      P[i] = advance_tail(w, b0 + i, p, U.x, U.y);
+      P[i] = advance_tail<false>(w, b0 + i, p, U.x, U.y);
     }
     if (kExt && w.observe && w.energy) obs_add_warp(&w.obs[2], q);
   } else if (kMode == 2) {

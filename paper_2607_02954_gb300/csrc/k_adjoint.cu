@@ -401,15 +401,16 @@ constexpr int kAdjTapePerPassRB = 7; // red-black, per pass: theta x 3, d (x, y)
 
 // The position correction of edge e (Eqs. 2-4) from the edge vector v0 plus
 // corrections d, its frame angle th (turned in place): D into (Dx, Dy).
+// (the forward kernel's arithmetic: the same fast forms)
 __device__ __forceinline__ void adj_edge_forward(float vx, float vy, float L, float& th, float hs, float ksh,
                                                  float ko, float& Dx, float& Dy) {
-  const float ell = sqrtf(vx * vx + vy * vy);
-  const float sc = (ell - L) / ell;
+  const float sc = fmaf(-L, rsqrtf(vx * vx + vy * vy), 1.0f);
   float sn, cs;
-  sincosf(th, &sn, &cs);
-  Dx = hs * (sc * vx + ksh * (vx - L * cs - sc * vx));
-  Dy = hs * (sc * vy + ksh * (vy - L * sn - sc * vy));
-  th += ko * (cs * vy - sn * vx) / L;
+  __sincosf(fmaf(-6.28318548f, rintf(th * 0.159154943f), th), &sn, &cs);
+  const float csx = sc * vx, csy = sc * vy;
+  Dx = hs * (csx + ksh * (vx - L * cs - csx));
+  Dy = hs * (csy + ksh * (vy - L * sn - csy));
+  th += ko * (cs * vy - sn * vx) * __frcp_rn(L);
 }
 
 // The reverse of adj_edge_forward for edge vector (x, y), rest length L,
@@ -547,16 +548,10 @@ __global__ void __launch_bounds__(kAdjPbdThreads) k_adj_pbd(const WorldDev* __re
       tp[3 * maxB + i] = dy[i];
     }
     for (int e = tid; e < nE; e += kAdjPbdThreads) {
-      const float x = vx[e] + (dx[e + 1] - dx[e]);
-      const float y = vy[e] + (dy[e + 1] - dy[e]);
-      const float L = Lr[e];
-      const float ell = sqrtf(x * x + y * y);
-      const float sc = (ell - L) / ell;
-      float sn, cs;
-      sincosf(th[e], &sn, &cs);
-      Dx[e] = hs * (sc * x + ksh * (x - L * cs - sc * x));
-      Dy[e] = hs * (sc * y + ksh * (y - L * sn - sc * y));
-      th[e] += ko * (cs * y - sn * x) / L;
+      float Dxe, Dye;
+      adj_edge_forward(vx[e] + (dx[e + 1] - dx[e]), vy[e] + (dy[e + 1] - dy[e]), Lr[e], th[e], hs, ksh, ko, Dxe, Dye);
+      Dx[e] = Dxe;
+      Dy[e] = Dye;
     }
     __syncthreads();
     for (int i = tid; i < B; i += kAdjPbdThreads) {

@@ -249,7 +249,7 @@ void launch_advance_pbd(const Plan& p, cudaStream_t s) {
 void kernel_setup() {
   static std::once_flag once;
   std::call_once(once, [] {
-    num_sms();
+    steric_setup(num_sms());
     persistent_setup();
     const int most = 227 * 1024;
     for (auto f : {k_pbd<false, 0, false>, k_pbd<true, 0, false>, k_pbd<false, 1, false>, k_pbd<true, 1, false>,

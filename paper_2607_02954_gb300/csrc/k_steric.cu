@@ -43,6 +43,8 @@
 // Periodic images: with several tiles on an axis a bead is taken at the one
 // image of it that can reach the tile (the reachable range is shorter than
 // the axis); with one tile the tile is the whole axis.
+#include <algorithm>
+
 #include "steric_dev.cuh"
 
 namespace mc {
@@ -93,7 +95,98 @@ __global__ void __launch_bounds__(kThreads, 4) k_force_lbm(const WorldDev* __res
   pdl_trigger();
   pdl_wait();
   __shared__ __align__(16) ForceSmem<R> sm;
-  force_lbm_body<R, kSingle>(worlds, items, w1, blockIdx.x, sm);
+  // tiles in reverse order: the first rows' velocities, written last, are
+  // still in L2 when the next PBD (filaments in index order) interpolates
+  // them, and the last rows' x-filtered densities, which the deposit wrote
+  // last, are read first
+  force_lbm_body<R, kSingle>(worlds, items, w1, gridDim.x - 1 - blockIdx.x, sm);
+}
+
+// y pass of a5 + a6 + a7, warp-specialised and persistent: each block walks
+// the tiles blockIdx.x, blockIdx.x + gridDim.x, ...; warps 0-3 run the force
+// phase of a tile (staging, y pass, steric gather, spread) while warps 4-7
+// collide the previous tile, so the collision's memory traffic overlaps the
+// force phase's arithmetic.  The force warps hand the tile's F over in a
+// shared buffer: they fill it once the collision warps have released it
+// (named barrier 4) and signal it full (named barrier 3); each tile's F and
+// collision are computed exactly as in k_force_lbm (bitwise the same
+// results).  Worlds without two layers only.
+constexpr int kWsForce = kThreads / 2;   // threads of the force group
+constexpr int kWsLbmWarps = (kThreads - kWsForce) / 32;
+
+template <int R>
+struct WsSmem {
+  ForceSmem<R> f;
+  float2 Fh[kTile * kTile];   // the hand-off buffer: F of the tile being collided
+};
+
+__device__ __forceinline__ void ws_bar_sync(int id) { asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(kThreads) : "memory"); }
+__device__ __forceinline__ void ws_bar_arrive(int id) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "n"(kThreads) : "memory");
+}
+constexpr int kWsFull = 3, kWsEmpty = 4;
+
+template <int R, bool kSingle>
+__global__ void __launch_bounds__(kThreads, 4) k_force_lbm_ws(const WorldDev* __restrict__ worlds,
+                                                              const int2* __restrict__ items, int n_items,
+                                                              const __grid_constant__ WorldDev w1) {
+  pdl_trigger();
+  pdl_wait();
+  extern __shared__ __align__(16) unsigned char ws_raw[];
+  WsSmem<R>& sm = *reinterpret_cast<WsSmem<R>*>(ws_raw);
+  const bool force_group = threadIdx.x < kWsForce;
+  int done = 0;   // tiles of this block handed over so far
+  for (int i = blockIdx.x; i < n_items; i += gridDim.x, ++done) {
+    const int2 it = kSingle ? single_tile_item(w1, (unsigned)i) : items[i];
+    const WorldDev& w = kSingle ? w1 : worlds[it.x];
+    const TileBox tb = tile_box(w, it.y);
+    if (force_group) {
+      prefetch_populations<kWsForce>(w, tb);
+      const int tile = (tb.y0 / kTile) * w.ntx + tb.x0 / kTile;
+      int k = 40;
+      if (!kSingle && w.tile_rho_max[tile] == 0.0f) {
+        tile_clear<kWsForce>(sm.f.wk);   // no bead reaches the tile: F = 0 (see k_force_lbm)
+      } else {
+        k = force_tile<R, kWsForce>(sm.f, w, tile, tb, 0, 0);
+      }
+      force_sync<kWsForce>();
+      force_fold<TileWork, kWsForce>(sm.f.wk, tb, w.ntx, w.nty);
+      if (done > 0) ws_bar_sync(kWsEmpty);   // the collision warps are done with the previous F
+      const float inv = pow2f(-k);
+      for (int c = threadIdx.x; c < kTile * kTile; c += kWsForce) {
+        const int s = ((c >> 5) + 3) * kAx + (c & 31) + 3;
+        sm.Fh[c] = make_float2((float)sm.f.wk.accx[s] * inv, (float)sm.f.wk.accy[s] * inv);
+      }
+      force_sync<kWsForce>();   // the accumulators are read: the next tile may clear them
+      ws_bar_arrive(kWsFull);
+    } else {
+      const int W = w.W, H = w.H, HW = H * W;
+      const long long t = *w.t;
+      const float* __restrict__ src = w.g[t & 1];
+      float* __restrict__ dst = w.g[(t + 1) & 1];
+      float2* __restrict__ u_out = w.u;
+      const LbmConst kc{w.om_p, w.om_m, w.src_p, w.src_m};
+      const int lane = threadIdx.x & 31, lw = (threadIdx.x - kWsForce) >> 5;
+      const bool active = lane < tb.tw && lw < tb.th;
+      const int x = tb.x0 + lane;
+      const int xm = x == 0 ? W - 1 : x - 1, xp = x == W - 1 ? 0 : x + 1;
+      LbmPull q;
+      int y = tb.y0 + lw;
+      // the first row's populations are pulled while the force warps finish
+      if (active) lbm_pull(src, HW, y * W, (y == 0 ? H - 1 : y - 1) * W, (y == H - 1 ? 0 : y + 1) * W, x, xm, xp, q);
+      ws_bar_sync(kWsFull);
+      if (active) {
+        for (int ly = lw; ly < tb.th; ly += kWsLbmWarps) {
+          if (ly != lw)
+            lbm_pull(src, HW, y * W, (y == 0 ? H - 1 : y - 1) * W, (y == H - 1 ? 0 : y + 1) * W, x, xm, xp, q);
+          u_out[(size_t)y * W + x] = lbm_collide(q, dst, HW, y * W + x, sm.Fh[ly * kTile + lane], kc);
+          y += kWsLbmWarps;
+        }
+      }
+      ws_bar_arrive(kWsEmpty);
+    }
+  }
+  if (force_group && done > 0) ws_bar_sync(kWsEmpty);   // the last F has been read
 }
 
 // One MDF pass of the direct-forcing worlds on one tile, Jacobi in u.  Every
@@ -317,6 +410,25 @@ __global__ void __launch_bounds__(kThreads) k_mdf_pass(const WorldDev* __restric
 
 namespace {
 
+// Blocks of the warp-specialised force + LBM kernel: as many as fit on every
+// SM at once (set up outside any stream capture by steric_setup).
+int g_ws_grid[kMaxR + 1] = {};
+
+template <int R>
+int ws_grid() {
+  return g_ws_grid[R] > 0 ? g_ws_grid[R] : 1;
+}
+
+template <int R>
+void ws_setup(int sms) {
+  const int bytes = (int)sizeof(WsSmem<R>);
+  cudaFuncSetAttribute(k_force_lbm_ws<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_force_lbm_ws<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_force_lbm_ws<R, false>, kThreads, bytes);
+  g_ws_grid[R] = (per > 0 ? per : 1) * sms;
+}
+
 template <int R>
 void launch_steric(const Plan& p, cudaStream_t s, int which, int store_fields, int after_step) {
   if (which == 0) {
@@ -326,6 +438,14 @@ void launch_steric(const Plan& p, cudaStream_t s, int which, int store_fields, i
       launch_pdl(k_deposit_x<R, false>, p.n_tile_items, kThreads, 0, s, p.d_worlds, p.d_tile_items, store_fields, p.h_world0);
   } else if (which == 1) {
     k_force_spread<R><<<p.n_tile_items, kThreads, 0, s>>>(p.d_worlds, p.d_tile_items, store_fields, after_step);
+  } else if (p.cfg.force_ws && !p.any_layered) {
+    const int grid = std::min(p.n_tile_items, ws_grid<R>());
+    if (p.n_worlds == 1)
+      launch_pdl(k_force_lbm_ws<R, true>, grid, kThreads, sizeof(WsSmem<R>), s, p.d_worlds, p.d_tile_items,
+                 p.n_tile_items, p.h_world0);
+    else
+      launch_pdl(k_force_lbm_ws<R, false>, grid, kThreads, sizeof(WsSmem<R>), s, p.d_worlds, p.d_tile_items,
+                 p.n_tile_items, p.h_world0);
   } else {
     if (p.n_worlds == 1)
       launch_pdl(k_force_lbm<R, true>, p.n_tile_items, kThreads, 0, s, p.d_worlds, p.d_tile_items, p.h_world0);
@@ -349,6 +469,17 @@ void dispatch_steric(const Plan& p, cudaStream_t s, int which, int store_fields,
 }
 
 }  // namespace
+
+void steric_setup(int sms) {
+  ws_setup<1>(sms);
+  ws_setup<2>(sms);
+  ws_setup<3>(sms);
+  ws_setup<4>(sms);
+  ws_setup<5>(sms);
+  ws_setup<6>(sms);
+  ws_setup<7>(sms);
+  ws_setup<8>(sms);
+}
 
 void launch_deposit_x(const Plan& p, cudaStream_t s, int store_fields) { dispatch_steric(p, s, 0, store_fields, 0); }
 

@@ -413,7 +413,8 @@ size_t world_layout(WorldDev& h, void* A) {
 // Plan and step helpers shared with the rollout server.
 mc_status plan_build(mc_world* const* ws, int n, cudaStream_t s, Plan& out) { return build_plan(ws, n, s, out); }
 void plan_set_cfg(Plan& p, const LaunchCfg& c) {
-  if (c.persistent == p.cfg.persistent && c.pbd_warps == p.cfg.pbd_warps && c.scan_kernels == p.cfg.scan_kernels)
+  if (c.persistent == p.cfg.persistent && c.pbd_warps == p.cfg.pbd_warps && c.scan_kernels == p.cfg.scan_kernels &&
+      c.force_ws == p.cfg.force_ws)
     return;
   p.cfg = c;
   if (p.graph) {
@@ -721,6 +722,7 @@ mc_status mc_launch_config_get(mc_world* const* ws, int n, mc_launch_config* out
   out->persistent = p->cfg.persistent;
   out->pbd_warps = p->cfg.pbd_warps;
   out->scan_kernels = p->cfg.scan_kernels;
+  out->force_kernel = p->cfg.force_ws;
   return MC_OK;
 }
 
@@ -731,6 +733,7 @@ mc_status mc_launch_config_set(mc_world* const* ws, int n, const mc_launch_confi
   if (cfg->pbd_warps != 8 && cfg->pbd_warps != 4 && cfg->pbd_warps != 2)
     return fail(MC_ERR_INVALID_ARG, "pbd_warps must be 8, 4 or 2");
   if (cfg->scan_kernels != 0 && cfg->scan_kernels != 2) return fail(MC_ERR_INVALID_ARG, "scan_kernels must be 0 or 2");
+  if (cfg->force_kernel != 0 && cfg->force_kernel != 1) return fail(MC_ERR_INVALID_ARG, "force_kernel must be 0 or 1");
   Plan* p = nullptr;
   mc_status st = find_plan(ws, n, nullptr, &p);
   if (st != MC_OK) return st;
@@ -738,6 +741,7 @@ mc_status mc_launch_config_set(mc_world* const* ws, int n, const mc_launch_confi
   c.persistent = cfg->persistent;
   c.pbd_warps = cfg->pbd_warps;
   c.scan_kernels = cfg->scan_kernels;
+  c.force_ws = cfg->force_kernel;
   if (c.persistent && !mc::persistent_supported(*p))
     return fail(MC_ERR_INVALID_ARG, "the persistent step does not support this plan (direct forcing, two layers, "
                                     "filaments over 64 beads or a filter half width other than 4)");

@@ -135,6 +135,7 @@ struct LaunchCfg {
   int persistent = 0;     // 3 or 4: one cooperative launch per run of steps with that many blocks per SM (k_persist.cu)
   int pbd_warps = 8;      // most filaments (warps) per block of the PBD kernels: 8, 4 or 2
   int scan_kernels = 0;   // 0: one scan kernel when every world fits one scan block; 2: always two
+  int force_ws = 0;       // 1: the warp-specialised persistent force + LBM kernel (worlds without two layers)
 };
 
 // A set of worlds advanced together, with the work items of each stage.
@@ -175,6 +176,7 @@ bool persistent_supported(const Plan& p);
 cudaError_t launch_persistent(const Plan& p, int n, cudaStream_t s);
 void persistent_setup();   // host set-up (occupancy queries) outside any stream capture
 void persistent_test_settings(unsigned extra_arrivals, unsigned long long timeout_ns);
+void steric_setup(int sms);   // host set-up of the tile kernels (k_steric.cu), outside any stream capture
 
 // --- stage launchers (one launch covers every world of the plan) ---------
 void launch_pbd(const Plan& p, cudaStream_t s);

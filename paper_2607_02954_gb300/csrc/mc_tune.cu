@@ -118,6 +118,11 @@ mc_status plan_tune(mc_world* const* ws, int n, Plan& p, cudaStream_t s, bool au
             consider(c);
           }
         }
+        if (!cp.any_layered && !best.persistent) {
+          LaunchCfg c = best;
+          c.force_ws = 1;
+          consider(c);
+        }
         for (int wp : {4, 2}) {
           LaunchCfg c = best;
           c.pbd_warps = wp;

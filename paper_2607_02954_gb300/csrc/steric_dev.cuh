@@ -471,12 +471,21 @@ struct TileBox {
   int x0, y0, tw, th;
 };
 
+// Barrier of the NT threads that run a tile's force phase: the whole block
+// (NT == kThreads), or warps 0 .. NT/32 - 1 on named barrier 1 (the
+// warp-specialised kernel, whose other warps collide).
+template <int NT>
+__device__ __forceinline__ void force_sync() {
+  if (NT == kThreads) __syncthreads();
+  else asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+}
+
 // Lists the n staged beads whose stencil reaches the tile (image taken on
 // axes with several tiles), packed with their tile-relative cell.
-template <int R>
+template <int R, int NT = kThreads>
 __device__ __forceinline__ void force_compact(const TileIn<R>& in, TileWork& wk, int n, const TileBox& tb, int W,
                                               int H, int ntx, int nty) {
-  for (int v0 = 0; v0 < n; v0 += kThreads) {
+  for (int v0 = 0; v0 < n; v0 += NT) {
     const int v = v0 + threadIdx.x;
     bool keep = false;
     int rx = 0, ry = 0;
@@ -502,7 +511,7 @@ __device__ __forceinline__ void force_compact(const TileIn<R>& in, TileWork& wk,
 // columns [x0 - 4, x0 + tw + 4) in 16-byte cp.async chunks (independent of
 // the beads).  A 4-column chunk never straddles the periodic edge (x0 and W
 // are multiples of 8); rows reach at most 4 + R <= 12 cells outside the axis.
-template <int R>
+template <int R, int NT = kThreads>
 __device__ __forceinline__ void tile_stage_window(TileIn<R>& in, const WorldDev& w, const TileBox& tb) {
   const int W = w.W, H = w.H, tid = threadIdx.x;
   const float* __restrict__ rho_x = w.rho_x;
@@ -510,10 +519,10 @@ __device__ __forceinline__ void tile_stage_window(TileIn<R>& in, const WorldDev&
   const int nq = ww >> 2;
   int rows_per_pass, i0;
   if (nq == kWin / 4) {   // full tile: constant divisor
-    rows_per_pass = kThreads / (kWin / 4);
+    rows_per_pass = NT / (kWin / 4);
     i0 = tid / (kWin / 4);
   } else {
-    rows_per_pass = kThreads / nq;
+    rows_per_pass = NT / nq;
     i0 = tid / nq;
   }
   const int q = tid - i0 * nq;
@@ -547,13 +556,13 @@ __device__ __forceinline__ void tile_stage_meta(TileIn<R>& in, const WorldDev& w
 
 // Stage 3 (after stage 2 is visible to the block): cp.async of the bead
 // records of the first chunk.
-template <int R>
+template <int R, int NT = kThreads>
 __device__ __forceinline__ void tile_stage_records(TileIn<R>& in, const WorldDev& w) {
   const int n0 = min(kForceCap, in.s_pre[kMaxSeg]);
   const float4* __restrict__ spos = w.spos;
   const float2* __restrict__ sfel = w.sfel;
   const int* __restrict__ sid = w.sid;
-  for (int v = threadIdx.x; v < n0; v += kThreads) {
+  for (int v = threadIdx.x; v < n0; v += NT) {
     const int slot = seg_slot(v, in.s_start, in.s_pre);
     cp_async16(&in.sp[v], &spos[slot]);
     cp_async8(&in.sf[v], &sfel[slot]);
@@ -563,8 +572,9 @@ __device__ __forceinline__ void tile_stage_records(TileIn<R>& in, const WorldDev
 
 // Zeroes the spread accumulators and the list count (before the barrier
 // that precedes tile_compute).
+template <int NT = kThreads>
 __device__ __forceinline__ void tile_clear(TileWork& wk) {
-  for (int c = threadIdx.x; c < kAx * kAx / 4; c += kThreads) {
+  for (int c = threadIdx.x; c < kAx * kAx / 4; c += NT) {
     reinterpret_cast<int4*>(wk.accx)[c] = make_int4(0, 0, 0, 0);
     reinterpret_cast<int4*>(wk.accy)[c] = make_int4(0, 0, 0, 0);
   }
@@ -575,7 +585,7 @@ __device__ __forceinline__ void tile_clear(TileWork& wk) {
 // complete and visible, accumulators cleared).  Returns k: after the caller
 // synchronises the block, accx/accy hold the tile's F 2^k (before folding,
 // see force_fold).
-template <int R>
+template <int R, int NT = kThreads>
 __device__ __forceinline__ int tile_compute(TileIn<R>& in, TileWork& wk, const WorldDev& w, int tile,
                                             const TileBox& tb, int store_fields, int after_step) {
   using G = Geo<R>;
@@ -599,7 +609,7 @@ __device__ __forceinline__ int tile_compute(TileIn<R>& in, TileWork& wk, const W
   const int k = fix_exponent((fmax_el + 0.5f * k_rep * rho_nb) * rho_max * 1.0001f + 1e-30f);
   const float scale = pow2f(k);
   // list the first chunk's beads that reach the tile, then the y pass
-  force_compact(in, wk, n0, tb, W, H, ntx, nty);
+  force_compact<R, NT>(in, wk, n0, tb, W, H, ntx, nty);
   if (total > 0 || store_fields) {
     // y pass, 8 window rows per thread (only the beads' gradients and the
     // rho_bar field read it)
@@ -607,7 +617,7 @@ __device__ __forceinline__ int tile_compute(TileIn<R>& in, TileWork& wk, const W
 #pragma unroll
     for (int m = 0; m < G::kTaps; ++m) tp[m] = in.tap_s[m];
     const int nstrip = wh >> 3;
-    for (int c = tid; c < nstrip * ww; c += kThreads) {
+    for (int c = tid; c < nstrip * ww; c += NT) {
       int s;
       if (ww == kWin) s = c / kWin;   // full tile: constant divisor
       else s = c / ww;
@@ -628,10 +638,10 @@ __device__ __forceinline__ int tile_compute(TileIn<R>& in, TileWork& wk, const W
       }
     }
   }
-  __syncthreads();
+  force_sync<NT>();
   for (int c0 = 0;;) {
     const int cnt = wk.s_cnt;
-    for (int q = tid; q < cnt; q += kThreads) {
+    for (int q = tid; q < cnt; q += NT) {
       const int code = wk.list[q];
       const int v = code_slot(code), rx = code_rx(code), ry = code_ry(code);
       const float4 p = in.sp[v];
@@ -680,44 +690,44 @@ __device__ __forceinline__ int tile_compute(TileIn<R>& in, TileWork& wk, const W
     }
     c0 += kForceCap;
     if (c0 >= total) break;
-    __syncthreads();   // every thread is done with this chunk
+    force_sync<NT>();   // every thread is done with this chunk
     if (tid == 0) wk.s_cnt = 0;
     const int n = min(kForceCap, total - c0);
-    for (int v = tid; v < n; v += kThreads) {
+    for (int v = tid; v < n; v += NT) {
       const int slot = seg_slot(c0 + v, in.s_start, in.s_pre);
       cp_async16(&in.sp[v], &spos[slot]);
       cp_async8(&in.sf[v], &sfel[slot]);
       cp_async4(&in.si[v], &sid[slot]);
     }
     cp_async_wait_all();
-    __syncthreads();
-    force_compact(in, wk, n, tb, W, H, ntx, nty);
-    __syncthreads();
+    force_sync<NT>();
+    force_compact<R, NT>(in, wk, n, tb, W, H, ntx, nty);
+    force_sync<NT>();
   }
   return k;   // the caller synchronises before it reads the accumulators
 }
 
 // One tile staged and computed (the non-persistent kernels).
-template <int R>
+template <int R, int NT = kThreads>
 __device__ __forceinline__ int force_tile(ForceSmem<R>& sm, const WorldDev& w, int tile, const TileBox& tb,
                                           int store_fields, int after_step) {
-  tile_stage_window(sm.in, w, tb);
+  tile_stage_window<R, NT>(sm.in, w, tb);
   tile_stage_meta(sm.in, w, tb);
-  tile_clear(sm.wk);
-  __syncthreads();
-  tile_stage_records(sm.in, w);
+  tile_clear<NT>(sm.wk);
+  force_sync<NT>();
+  tile_stage_records<R, NT>(sm.in, w);
   cp_async_wait_all();
-  __syncthreads();
-  return tile_compute(sm.in, sm.wk, w, tile, tb, store_fields, after_step);
+  force_sync<NT>();
+  return tile_compute<R, NT>(sm.in, sm.wk, w, tile, tb, store_fields, after_step);
 }
 
 // Folds the stencil cells that wrapped around an axis the tile covers whole
 // (one tile on that axis); call after the block has synchronised.
-template <class Work>
+template <class Work, int NT = kThreads>
 __device__ __forceinline__ void force_fold(Work& wk, const TileBox& tb, int ntx, int nty) {
   if (ntx > 1 && nty > 1) return;
   const bool fx = ntx == 1, fy = nty == 1;
-  for (int c = threadIdx.x; c < kAx * kAx; c += kThreads) {
+  for (int c = threadIdx.x; c < kAx * kAx; c += NT) {
     const int ly = c / kAx - 3, lx = c % kAx - 3;
     const bool out_y = ly < 0 || ly >= tb.th, out_x = lx < 0 || lx >= tb.tw;
     if ((!out_y && !out_x) || (out_y && !fy) || (out_x && !fx)) continue;
@@ -726,7 +736,7 @@ __device__ __forceinline__ void force_fold(Work& wk, const TileBox& tb, int ntx,
     if (vx) atomicAdd(&wk.accx[t2], vx);
     if (vy) atomicAdd(&wk.accy[t2], vy);
   }
-  __syncthreads();
+  force_sync<NT>();
 }
 
 __device__ __forceinline__ TileBox tile_box(const WorldDev& w, int packed) {
@@ -740,11 +750,12 @@ __device__ __forceinline__ TileBox tile_box(const WorldDev& w, int packed) {
 }
 
 // The tile's population rows (plane i, rows y - c_iy, 128-byte segments) to L2.
+template <int NT = kThreads>
 __device__ __forceinline__ void prefetch_populations(const WorldDev& w, const TileBox& tb) {
   const float* src = w.g[*w.t & 1];
   const int W = w.W, H = w.H;
   const size_t HW = (size_t)H * W;
-  for (int c = threadIdx.x; c < 9 * kTile; c += kThreads) {
+  for (int c = threadIdx.x; c < 9 * kTile; c += NT) {
     const int i = c >> 5, r = c & (kTile - 1);
     if (r >= tb.th) continue;
     const int y = wrap_once(tb.y0 + r - kLbmCy[i], H);

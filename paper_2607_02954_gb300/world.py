@@ -281,7 +281,8 @@ def _handles(worlds: Sequence[World]):
 
 
 def _cfg_dict(c: L.mc_launch_config) -> Dict:
-    return {"persistent": c.persistent, "pbd_warps": c.pbd_warps, "scan_kernels": c.scan_kernels}
+    return {"persistent": c.persistent, "pbd_warps": c.pbd_warps, "scan_kernels": c.scan_kernels,
+            "force_kernel": c.force_kernel}
 
 
 def autotune(worlds: Sequence[World], stream=None) -> Dict:
@@ -299,9 +300,11 @@ def launch_config(worlds: Sequence[World]) -> Dict:
     return _cfg_dict(c)
 
 
-def set_launch_config(worlds: Sequence[World], persistent: int = 0, pbd_warps: int = 8, scan_kernels: int = 0):
+def set_launch_config(worlds: Sequence[World], persistent: int = 0, pbd_warps: int = 8, scan_kernels: int = 0,
+                      force_kernel: int = 0):
     """Pins the launch configuration of the plan of these worlds."""
-    c = L.mc_launch_config(persistent=int(persistent), pbd_warps=int(pbd_warps), scan_kernels=int(scan_kernels))
+    c = L.mc_launch_config(persistent=int(persistent), pbd_warps=int(pbd_warps), scan_kernels=int(scan_kernels),
+                           force_kernel=int(force_kernel))
     L.check(L.load().mc_launch_config_set(_handles(worlds), len(worlds), ctypes.byref(c)))
 
 

@@ -17,7 +17,9 @@ pytestmark = pytest.mark.gpu
 
 CONFIGS = [dict(persistent=0, pbd_warps=8, scan_kernels=0), dict(persistent=4, pbd_warps=8, scan_kernels=0),
            dict(persistent=3, pbd_warps=8, scan_kernels=0), dict(persistent=0, pbd_warps=4, scan_kernels=0),
-           dict(persistent=0, pbd_warps=2, scan_kernels=2), dict(persistent=4, pbd_warps=2, scan_kernels=2)]
+           dict(persistent=0, pbd_warps=2, scan_kernels=2), dict(persistent=4, pbd_warps=2, scan_kernels=2),
+           dict(persistent=0, pbd_warps=8, scan_kernels=0, force_kernel=1),
+           dict(persistent=0, pbd_warps=4, scan_kernels=2, force_kernel=1)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -81,6 +83,37 @@ def test_every_launch_config_advances_one_world_bitwise_the_same():
             assert np.array_equal(states[0][k], s[k]), k
 
 
+@pytest.mark.parametrize("maker", ["c2", "ragged", "tiny8", "one_tile_row", "dense"])
+def test_warp_specialised_force_kernel_is_bitwise_the_same(maker):
+    """The warp-specialised persistent force + LBM kernel against the
+    one-tile-per-block kernel on one world: the 512^2 world (many tiles per
+    block), ragged tiles, a single 8 x 8 tile and a single tile row (the
+    periodic folds of an axis one tile covers), and 4 beads per cell (the
+    force staging in several chunks)."""
+    from paper_2607_02954_gb300 import World, set_launch_config
+    if maker == "c2":
+        spec = synth.world_c2(3)
+    elif maker == "ragged":
+        spec = synth.world_random(3, (40, 72), 6)
+    elif maker == "tiny8":
+        spec = synth.tiny_world(2, side=8, lengths=(3, 2))
+    elif maker == "one_tile_row":
+        spec = synth.world_random(5, (24, 128), 6)
+    else:
+        spec = synth.world_dense(256, 2 ** 18, seed=4)
+    n = 3 if maker == "dense" else 19   # the dense world speeds up: a few steps stay below the watchdog
+    states = []
+    for fk in (0, 1):
+        w = World(spec)
+        set_launch_config([w], force_kernel=fk)
+        w.step(n)
+        w.check()
+        states.append(w.state(fluid=True))
+        w.close()
+    for k in states[0]:
+        assert np.array_equal(states[0][k], states[1][k]), k
+
+
 def test_autotune_choice_is_cached_and_leaves_the_worlds_alone():
     from paper_2607_02954_gb300 import World, autotune, launch_config, step_batched
     specs = _batch(False)
@@ -88,6 +121,7 @@ def test_autotune_choice_is_cached_and_leaves_the_worlds_alone():
     before = [w.state(fluid=True) for w in ws]
     cfg = autotune(ws)
     assert cfg["persistent"] in (0, 3, 4) and cfg["pbd_warps"] in (8, 4, 2) and cfg["scan_kernels"] in (0, 2)
+    assert cfg["force_kernel"] in (0, 1)
     assert launch_config(ws) == cfg
     for w, b in zip(ws, before):            # measured on copies: the worlds did not move
         a = w.state(fluid=True)
