@@ -121,6 +121,8 @@ def parse():
     ap.add_argument("--duration", type=float, default=2.0, help="served: seconds of arrivals")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default launch configuration (no autotuning; profiling runs)")
     ap.add_argument("--no-extras", action="store_true",
                     help="headline only: skip the batched (c4) and served summaries of the default line")
     ap.add_argument("--stage-steps", type=int, default=50, help="steps of the per-stage timing pass")
@@ -558,6 +560,8 @@ def main():
         from paper_2607_02954_gb300.build import build
         build()
     lib = _lib.load()
+    if args.no_tune:
+        _lib.check(lib.mc_autotune_mode(0))
 
     spec, desc = make_spec(args.workload, seed=rank, pbd_order=args.pbd_order, observe=args.observe,
                            mdf_iters=args.mdf_iters)

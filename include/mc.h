@@ -181,6 +181,21 @@ mc_status mc_world_create(const mc_world_desc* desc, void* stream, mc_world** ou
  * ordered before the stream the world was created on. */
 mc_status mc_world_destroy(mc_world* w);
 
+/* Checkpoint and resume (a library service; the paper has no counterpart).
+ * mc_world_save writes an image of the world after the work enqueued on
+ * `stream` (every field of its state: beads, angles, drives, populations,
+ * bins, step counter, observables, optional fields) into a host buffer of
+ * at least mc_world_save_size bytes, and synchronizes `stream`.  The image
+ * holds no recorded rollout (mc_rollout_forward's checkpoints).
+ * mc_world_load creates a world from such an image (its memory allocated on
+ * `stream`, which it synchronizes before returning); stepping it continues
+ * the saved world bitwise.  Errors: MC_ERR_INVALID_ARG (NULL, a buffer too
+ * small, an image that is corrupt or from another C ABI version),
+ * MC_ERR_OOM, MC_ERR_CUDA. */
+mc_status mc_world_save_size(const mc_world* w, size_t* bytes);
+mc_status mc_world_save(const mc_world* w, void* buf, size_t bytes, void* stream);
+mc_status mc_world_load(const void* buf, size_t bytes, void* stream, mc_world** out);
+
 mc_status mc_world_info_get(const mc_world* w, mc_world_info* out);
 
 /* Advances one world by n_steps >= 0 time steps (a1..a8 each), enqueued on

@@ -81,6 +81,9 @@ SIGNATURES = {
     "mc_params_default": (_i, [ctypes.POINTER(mc_params)]),
     "mc_world_create": (_i, [ctypes.POINTER(mc_world_desc), _vp, ctypes.POINTER(_vp)]),
     "mc_world_destroy": (_i, [_vp]),
+    "mc_world_save_size": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "mc_world_save": (_i, [_vp, _vp, ctypes.c_size_t, _vp]),
+    "mc_world_load": (_i, [_vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
     "mc_world_info_get": (_i, [_vp, ctypes.POINTER(mc_world_info)]),
     "mc_step": (_i, [_vp, _i, _vp]),
     "mc_step_batched": (_i, [ctypes.POINTER(_vp), _i, _i, _vp]),

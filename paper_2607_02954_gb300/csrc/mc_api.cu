@@ -653,6 +653,124 @@ mc_status mc_world_create(const mc_world_desc* d, void* stream, mc_world** out) 
   return MC_OK;
 }
 
+// ---- checkpoint / resume --------------------------------------------------
+// Image of a world: a header, the filament offsets, then the device arena
+// byte for byte (it holds no pointers: the arrays are placed again from the
+// sizes on load).
+namespace {
+struct SaveHeader {
+  char magic[8];          // "MCWORLD1"
+  int abi;                // MC_ABI_VERSION of the writer
+  int H, W, n_fil, N;
+  int has_ldrive, has_energy, observe;
+  int max_B;
+  long long t;            // step counter (host view; the device one is in the arena)
+  unsigned long long arena_bytes;
+  mc_params params;
+};
+constexpr char kSaveMagic[8] = {'M', 'C', 'W', 'O', 'R', 'L', 'D', '1'};
+
+size_t save_size(const mc_world* w) {
+  return sizeof(SaveHeader) + (size_t)(w->h.n_fil + 1) * sizeof(int) + w->bytes;
+}
+}  // namespace
+
+mc_status mc_world_save_size(const mc_world* w, size_t* bytes) {
+  if (!w || !bytes) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+  *bytes = save_size(w);
+  return MC_OK;
+}
+
+mc_status mc_world_save(const mc_world* w, void* buf, size_t bytes, void* stream) {
+  if (!w || !buf) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+  if (bytes < save_size(w)) return fail(MC_ERR_INVALID_ARG, "buffer smaller than mc_world_save_size");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  SaveHeader hd{};
+  std::memcpy(hd.magic, kSaveMagic, 8);
+  hd.abi = MC_ABI_VERSION;
+  hd.H = w->h.H;
+  hd.W = w->h.W;
+  hd.n_fil = w->h.n_fil;
+  hd.N = w->h.N;
+  hd.has_ldrive = w->h.has_ldrive;
+  hd.has_energy = w->h.has_energy;
+  hd.observe = w->h.observe;
+  hd.max_B = w->max_B;
+  hd.t = w->t;
+  hd.arena_bytes = w->bytes;
+  hd.params = w->params;
+  char* out = static_cast<char*>(buf);
+  std::memcpy(out, &hd, sizeof(hd));
+  std::memcpy(out + sizeof(hd), w->fil_off.data(), (size_t)(w->h.n_fil + 1) * sizeof(int));
+  MC_CUDA(cudaMemcpyAsync(out + sizeof(hd) + (size_t)(w->h.n_fil + 1) * sizeof(int), w->arena, w->bytes,
+                          cudaMemcpyDeviceToHost, s));
+  MC_CUDA(cudaStreamSynchronize(s));
+  return MC_OK;
+}
+
+mc_status mc_world_load(const void* buf, size_t bytes, void* stream, mc_world** out) {
+  if (!buf || !out) return fail(MC_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  SaveHeader hd{};
+  if (bytes < sizeof(hd)) return fail(MC_ERR_INVALID_ARG, "buffer too small for a world image");
+  std::memcpy(&hd, buf, sizeof(hd));
+  if (std::memcmp(hd.magic, kSaveMagic, 8) != 0) return fail(MC_ERR_INVALID_ARG, "not a world image");
+  if (hd.abi != MC_ABI_VERSION) return fail(MC_ERR_INVALID_ARG, "world image written by another C ABI version");
+  if (hd.H < 8 || hd.W < 8 || hd.H % 8 || hd.W % 8 || hd.H > 8192 || hd.W > 8192 || hd.n_fil < 0 || hd.N < 0 ||
+      hd.t < 0 || hd.t >= (int64_t(1) << 24) || hd.max_B < 2 || hd.max_B > 3072)
+    return fail(MC_ERR_INVALID_ARG, "corrupt world image header");
+  mc_status st = validate_params(hd.params);
+  if (st != MC_OK) return st;
+  const size_t fo_bytes = (size_t)(hd.n_fil + 1) * sizeof(int);
+  if (bytes < sizeof(hd) + fo_bytes) return fail(MC_ERR_INVALID_ARG, "world image truncated");
+  std::vector<int> fo(hd.n_fil + 1);
+  std::memcpy(fo.data(), static_cast<const char*>(buf) + sizeof(hd), fo_bytes);
+  if (fo[0] != 0 || fo[hd.n_fil] != hd.N) return fail(MC_ERR_INVALID_ARG, "corrupt filament table in world image");
+  for (int f = 0; f < hd.n_fil; ++f)
+    if (fo[f + 1] - fo[f] < 2 || fo[f + 1] - fo[f] > hd.max_B)
+      return fail(MC_ERR_INVALID_ARG, "corrupt filament table in world image");
+  mc_world* w = new mc_world();
+  w->stream = static_cast<cudaStream_t>(stream);
+  w->t = hd.t;
+  w->max_B = hd.max_B;
+  w->fil_off = fo;
+  w->params = hd.params;
+  WorldDev& h = w->h;
+  mc::world_sizes(h, hd.H, hd.W, hd.n_fil, hd.N);
+  fill_constants(h, hd.params);
+  h.has_ldrive = hd.has_ldrive;
+  h.has_energy = hd.has_energy;
+  h.observe = hd.observe;
+  w->bytes = mc::world_layout(h, nullptr);
+  if (w->bytes != hd.arena_bytes || bytes < sizeof(hd) + fo_bytes + w->bytes) {
+    delete w;
+    return fail(MC_ERR_INVALID_ARG, "world image size does not match its header");
+  }
+  cudaError_t e = world_alloc(&w->arena, w->bytes, w->stream);
+  if (e != cudaSuccess) {
+    delete w;
+    return fail(MC_ERR_OOM, std::string("world allocation: ") + cudaGetErrorString(e));
+  }
+  mc::world_layout(h, w->arena);
+  e = cudaMemcpyAsync(w->arena, static_cast<const char*>(buf) + sizeof(hd) + fo_bytes, w->bytes,
+                      cudaMemcpyHostToDevice, w->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);   // the caller may reuse the buffer at once
+  if (e != cudaSuccess) {
+    cudaFreeAsync(w->arena, w->stream);
+    delete w;
+    return cuda_fail(e, "world image upload");
+  }
+  mc_world* self = w;
+  st = build_plan(&self, 1, w->stream, w->plan);
+  if (st != MC_OK) {
+    cudaFreeAsync(w->arena, w->stream);
+    delete w;
+    return st;
+  }
+  *out = w;
+  return MC_OK;
+}
+
 mc_status mc_world_destroy(mc_world* w) {
   if (!w) return MC_OK;
   drop_plans_with(w);

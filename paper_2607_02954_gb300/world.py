@@ -121,6 +121,28 @@ class World:
         except Exception:
             pass
 
+    def save(self, stream=None) -> bytes:
+        """Image of the world after the enqueued work (mc_world_save)."""
+        n = ctypes.c_size_t()
+        L.check(self._lib.mc_world_save_size(self.handle, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        L.check(self._lib.mc_world_save(self.handle, buf, n.value, stream_handle(stream)))
+        return buf.raw
+
+    @classmethod
+    def load(cls, image: bytes, spec: WorldSpec, stream=None) -> "World":
+        """A world resumed from an image of save(); spec describes it (sizes,
+        for the Python-side helpers) and is not sent to the library."""
+        lib = L.load()
+        obj = cls.__new__(cls)
+        obj.spec = spec
+        obj._lib = lib
+        h = ctypes.c_void_p()
+        buf = ctypes.create_string_buffer(image, len(image))
+        L.check(lib.mc_world_load(buf, len(image), stream_handle(stream), ctypes.byref(h)))
+        obj._h = h
+        return obj
+
     def info(self) -> Dict[str, int]:
         i = L.mc_world_info()
         L.check(self._lib.mc_world_info_get(self.handle, ctypes.byref(i)))

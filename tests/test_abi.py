@@ -131,3 +131,14 @@ def test_launch_config_calls_validate_arguments():
     assert lib.mc_autotune_mode(1) == 0
     assert lib.mc_debug_barrier_test(2, 1000) == 1
     assert lib.mc_debug_barrier_test(0, 10) == 1
+
+
+def test_world_load_rejects_corrupt_images_on_host():
+    lib = L.load()
+    h = ctypes.c_void_p()
+    junk = ctypes.create_string_buffer(b"not a world image at all" * 8)
+    assert lib.mc_world_load(junk, len(junk), None, ctypes.byref(h)) == 1
+    assert h.value is None
+    assert lib.mc_world_load(junk, 4, None, ctypes.byref(h)) == 1
+    n = ctypes.c_size_t()
+    assert lib.mc_world_save_size(None, ctypes.byref(n)) == 1

@@ -114,3 +114,31 @@ def test_world_allocation_failure_reports_oom_and_spares_the_others():
     for k in (0, 1, 3, 4):
         assert res[k]["status"] == 0
         assert res[k]["com_disp"] == _alone(*specs[k])["com_disp"]
+
+
+@pytest.mark.parametrize("observe", [False, True])
+def test_save_and_resume_continue_the_world_bitwise(observe):
+    """Checkpoint and resume: a world saved after 13 steps, destroyed, and
+    loaded again continues exactly as the world that never stopped (state,
+    fluid, observables, step counter)."""
+    from paper_2607_02954_gb300 import World
+    spec = synth.world_random(61, 128, 12)
+    if observe:
+        spec = synth.with_observables(spec, 61)
+    a = World(spec)
+    a.step(30)
+    want, want_obs = a.state(fluid=True), a.observables()
+    a.close()
+    b = World(spec)
+    b.step(13)
+    image = b.save()
+    b.close()
+    c = World.load(image, spec)
+    assert c.info()["t"] == 13
+    c.step(17)
+    got = c.state(fluid=True)
+    for k in want:
+        assert np.array_equal(want[k], got[k]), k
+    assert c.observables() == want_obs
+    assert c.info()["t"] == 30
+    c.close()
