@@ -85,7 +85,7 @@ typedef enum mc_mem_kind { MC_MEM_HOST = 0, MC_MEM_DEVICE = 1 } mc_mem_kind;
  *            bead), spreading half its force at each point and moving with
  *            the mean of the two interpolated velocities; 0 < layer_half <= 2
  *            cells.  The steric field stays on the beads.  The reverse mode
- *            supports layers = 1 only.
+ *            supports both.
  *   ib       immersed-boundary coupling (Fluid-filament Interaction).
  *            0: penalty, F_el = kappa (x_hat - X)/dt spread as a force and
  *            the beads move with the interpolated fluid velocity.

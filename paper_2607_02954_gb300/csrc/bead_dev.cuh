@@ -91,21 +91,6 @@ __device__ __forceinline__ float2 interp_u(const WorldDev& w, const float4 p) {
 // Two-layer filament (Fluid-filament Interaction): the immersed-boundary
 // points of bead i are X_i +- delta n_i.
 // ---------------------------------------------------------------------------
-// Cell and fraction of the point X + d n for X = (cell, fraction) in p.
-__device__ __forceinline__ void layer_cell(const float4 p, float2 n, float d, int W, int H, int& cx, int& cy,
-                                           float& fx, float& fy) {
-  fx = p.x + d * n.x;
-  fy = p.y + d * n.y;
-  const float kx = floorf(fx), ky = floorf(fy);
-  fx -= kx;
-  fy -= ky;
-  cx = cell_x(p) + (int)kx;
-  cy = cell_y(p) + (int)ky;
-  if (fx >= 1.0f) { fx = 0.0f; cx += 1; }
-  if (fy >= 1.0f) { fy = 0.0f; cy += 1; }
-  cx = wrap_once(cx, W);   // |d| <= 2 keeps the offset within one period (W, H >= 8)
-  cy = wrap_once(cy, H);
-}
 
 __device__ __forceinline__ float2 layer_velocity(const WorldDev& w, const float4 p, float2 n, float d) {
   int cx, cy;

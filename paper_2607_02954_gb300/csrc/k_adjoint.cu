@@ -55,6 +55,23 @@ struct Stencil {
   int ix[4], iy[4];   // wrapped column / row-start indices
 };
 
+// The stencil of the two-layer point X + d n of bead p (the forward's
+// layer_cell: cell and fraction of the shifted point).
+__device__ __forceinline__ Stencil make_layer_stencil(const float4& p, float2 n, float d, int W, int H) {
+  int cx, cy;
+  float fx, fy;
+  layer_cell(p, n, d, W, H, cx, cy, fx, fy);
+  Stencil s;
+  peskin4_d(fx, s.wx, s.dx);
+  peskin4_d(fy, s.wy, s.dy);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    s.ix[a] = wrap_once(cx - 1 + a, W);
+    s.iy[a] = wrap_once(cy - 1 + a, H) * W;
+  }
+  return s;
+}
+
 __device__ __forceinline__ Stencil make_stencil(const float4& p, int W, int H) {
   Stencil s;
   peskin4_d(p.x, s.wx, s.dx);
@@ -82,18 +99,28 @@ __global__ void __launch_bounds__(256) k_adj_spread_u(const WorldDev* __restrict
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= w.N) return;
   const float scale = pow2f(ubar_exponent(w, a));
-  const Stencil s = make_stencil(w.pos[i], w.W, w.H);
   const float2 xb = a.adjX[i];
   const float ux = w.dt * xb.x * scale, uy = w.dt * xb.y * scale;
+  auto spread = [&](const Stencil& s, float h) {
 #pragma unroll
-  for (int b = 0; b < 4; ++b)
+    for (int b = 0; b < 4; ++b)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const float wgt = s.wx[c] * s.wy[b];
-      unsigned long long* g = &a.ubar[2 * (s.iy[b] + s.ix[c])];
-      atomicAdd(g, fx64(wgt * ux));
-      atomicAdd(g + 1, fx64(wgt * uy));
-    }
+      for (int c = 0; c < 4; ++c) {
+        const float wgt = s.wx[c] * s.wy[b] * h;
+        unsigned long long* g = &a.ubar[2 * (s.iy[b] + s.ix[c])];
+        atomicAdd(g, fx64(wgt * ux));
+        atomicAdd(g + 1, fx64(wgt * uy));
+      }
+  };
+  if (w.layers == 2) {
+    // U = (I[u](X + d n) + I[u](X - d n)) / 2
+    const float4 p = w.pos[i];
+    const float2 n = a.nrm[i];
+    spread(make_layer_stencil(p, n, w.layer_half, w.W, w.H), 0.5f);
+    spread(make_layer_stencil(p, n, -w.layer_half, w.W, w.H), 0.5f);
+  } else {
+    spread(make_stencil(w.pos[i], w.W, w.H), 1.0f);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -235,26 +262,44 @@ __global__ void __launch_bounds__(256) k_adj_bead_a(const WorldDev* __restrict__
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= w.N) return;
   const float qscale = pow2f(q_exponent(w, a));
-  const Stencil s = make_stencil(w.pos[i], w.W, w.H);
+  const float4 p = w.pos[i];
+  const Stencil s = make_stencil(p, w.W, w.H);
   const float2 xb = a.adjX[i];
   const float Ubx = w.dt * xb.x, Uby = w.dt * xb.y;
   const float2 fe = w.fel[i], fs = w.fs[i];
   const float Ftx = fe.x + fs.x, Fty = fe.y + fs.y;
+  // over the stencil st (weights scaled by h): the force's adjoint and the
+  // position gradient of u.U_bar + F_bar.Ftot
+  auto gather = [&](const Stencil& st, float h, float& ftbx, float& ftby, float& gx, float& gy) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int k = st.iy[b] + st.ix[c];
+        const float2 u = w.u[k];
+        const float2 fb = a.Fbar[k];
+        const float wgt = st.wx[c] * st.wy[b] * h;
+        ftbx = fmaf(wgt, fb.x, ftbx);
+        ftby = fmaf(wgt, fb.y, ftby);
+        const float q = (u.x * Ubx + u.y * Uby + fb.x * Ftx + fb.y * Fty) * h;
+        gx = fmaf(st.dx[c] * st.wy[b], q, gx);
+        gy = fmaf(st.wx[c] * st.dy[b], q, gy);
+      }
+  };
   float ftbx = 0.0f, ftby = 0.0f, gx = 0.0f, gy = 0.0f;
-#pragma unroll
-  for (int b = 0; b < 4; ++b)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int k = s.iy[b] + s.ix[c];
-      const float2 u = w.u[k];
-      const float2 fb = a.Fbar[k];
-      const float wgt = s.wx[c] * s.wy[b];
-      ftbx = fmaf(wgt, fb.x, ftbx);
-      ftby = fmaf(wgt, fb.y, ftby);
-      const float q = u.x * Ubx + u.y * Uby + fb.x * Ftx + fb.y * Fty;
-      gx = fmaf(s.dx[c] * s.wy[b], q, gx);
-      gy = fmaf(s.wx[c] * s.dy[b], q, gy);
-    }
+  if (w.layers == 2) {
+    // both layer points take half of the force and half of the velocity;
+    // X +- d n moves with X and (by +-d) with the normal
+    const float2 n = a.nrm[i];
+    float gpx = 0.0f, gpy = 0.0f, gmx = 0.0f, gmy = 0.0f;
+    gather(make_layer_stencil(p, n, w.layer_half, w.W, w.H), 0.5f, ftbx, ftby, gpx, gpy);
+    gather(make_layer_stencil(p, n, -w.layer_half, w.W, w.H), 0.5f, ftbx, ftby, gmx, gmy);
+    gx = gpx + gmx;
+    gy = gpy + gmy;
+    a.nbar[i] = make_float2(w.layer_half * (gpx - gmx), w.layer_half * (gpy - gmy));
+  } else {
+    gather(s, 1.0f, ftbx, ftby, gx, gy);
+  }
   a.adjX[i] = make_float2(xb.x + gx, xb.y + gy);
   a.fbt[i] = make_float2(ftbx, ftby);
   const float qx = ftbx * qscale, qy = ftby * qscale;
@@ -573,9 +618,66 @@ __global__ void __launch_bounds__(kAdjPbdThreads) k_adj_pbd(const WorldDev* __re
   for (int e = tid; e < nE; e += kAdjPbdThreads) th[e] = a.adjTh[e0 + e];
   float* v0bx = tape + n_pbd * kTape * maxB;
   float* v0by = v0bx + maxB;
-  for (int e = tid; e < nE; e += kAdjPbdThreads) {
-    v0bx[e] = 0.0f;
-    v0by[e] = 0.0f;
+  if (w.layers == 2) {
+    // the two-layer normals n = (-t_y, t_x), t = s/|s|, s = out + in (the
+    // unit vectors of the bead's edges at X^n; a folded chain takes out, or
+    // in at the last bead): per bead the adjoints of its out and in unit
+    // vectors (Dx: out, Dy: in, as 2 floats each in Dx/Dy pairs of slots)
+    for (int i = tid; i < B; i += kAdjPbdThreads) {
+      const float2 nb = a.nbar[b0 + i];
+      const float tbx = nb.y, tby = -nb.x;
+      const bool ho = i < nE, hi = i > 0;
+      float ox = 0.0f, oy = 0.0f, ix = 0.0f, iy = 0.0f;
+      if (ho) {
+        const float r = rsqrtf(vx[i] * vx[i] + vy[i] * vy[i]);
+        ox = vx[i] * r;
+        oy = vy[i] * r;
+      }
+      if (hi) {
+        const float r = rsqrtf(vx[i - 1] * vx[i - 1] + vy[i - 1] * vy[i - 1]);
+        ix = vx[i - 1] * r;
+        iy = vy[i - 1] * r;
+      }
+      const float sx = ox + ix, sy = oy + iy;
+      const float ns = sqrtf(sx * sx + sy * sy);
+      float obx = 0.0f, oby = 0.0f, ibx = 0.0f, iby = 0.0f;
+      if (ns >= 1e-3f) {
+        const float tx = sx / ns, ty = sy / ns;
+        const float dot = tbx * tx + tby * ty;
+        const float sbx = (tbx - dot * tx) / ns, sby = (tby - dot * ty) / ns;
+        if (ho) { obx = sbx; oby = sby; }
+        if (hi) { ibx = sbx; iby = sby; }
+      } else if (ho) {
+        obx = tbx;
+        oby = tby;
+      } else {
+        ibx = tbx;
+        iby = tby;
+      }
+      Dx[i] = obx;   // adjoint of the unit vector of edge i (as the bead's out)
+      Dy[i] = oby;
+      Cb[i] = ibx;   // adjoint of the unit vector of edge i - 1 (as the bead's in)
+      thrb[i] = iby;
+    }
+    __syncthreads();
+    // edge e: unit vector u = v/|v| with adjoint ub from bead e (out) and
+    // bead e + 1 (in): v_bar = (ub - (ub.u) u)/|v|
+    for (int e = tid; e < nE; e += kAdjPbdThreads) {
+      const float r = rsqrtf(vx[e] * vx[e] + vy[e] * vy[e]);
+      const float ux = vx[e] * r, uy = vy[e] * r;
+      const float ubx = Dx[e] + Cb[e + 1], uby = Dy[e] + thrb[e + 1];
+      const float dot = ubx * ux + uby * uy;
+      v0bx[e] = (ubx - dot * ux) * r;
+      v0by[e] = (uby - dot * uy) * r;
+    }
+    __syncthreads();
+    for (int j = tid; j < B; j += kAdjPbdThreads) thrb[j] = 0.0f;   // back to the rest-angle adjoint
+    __syncthreads();
+  } else {
+    for (int e = tid; e < nE; e += kAdjPbdThreads) {
+      v0bx[e] = 0.0f;
+      v0by[e] = 0.0f;
+    }
   }
   float hbb = 0.0f, hsb = 0.0f, kshb = 0.0f;
   __syncthreads();

@@ -88,7 +88,7 @@ mc_status load_state(const mc::WorldDev& h, int parity, const char* rec, const S
 // checkpoint) followed by the step's intermediates the adjoint reads.
 struct StepSlot {
   StateSlot st;
-  size_t fel, fs, rho_b, u, F;
+  size_t fel, fs, rho_b, u, F, nrm;
   size_t bytes;
 };
 
@@ -101,7 +101,8 @@ StepSlot step_slot(const mc::WorldDev& h) {
   s.rho_b = s.fs + align256((size_t)h.N * sizeof(float2));
   s.u = s.rho_b + align256(HW * sizeof(float));
   s.F = s.u + align256(HW * sizeof(float2));
-  s.bytes = s.F + align256(HW * sizeof(float2));
+  s.nrm = s.F + align256(HW * sizeof(float2));
+  s.bytes = s.nrm + align256(h.layers == 2 ? (size_t)h.N * sizeof(float2) : 0);
   return s;
 }
 
@@ -116,6 +117,7 @@ __global__ void k_seg_save(const mc::WorldDev* __restrict__ wd, char* cur, char*
     if (i < (size_t)h.N) {
       reinterpret_cast<float2*>(cur + sl.fel)[i] = h.fel[i];
       reinterpret_cast<float2*>(cur + sl.fs)[i] = h.fs[i];
+      if (h.nrm) reinterpret_cast<float2*>(cur + sl.nrm)[i] = h.nrm[i];
       if (next) reinterpret_cast<float4*>(next + sl.st.pos)[i] = h.pos[i];
     }
     if (next && i < (size_t)h.E) reinterpret_cast<float*>(next + sl.st.theta)[i] = h.theta[i];
@@ -330,6 +332,7 @@ mc_status sweep(mc_world* w, mc::AdjDev a, float* const adjG[2], char* obs_keep,
       a.adjG_next = adjG[cur];
       a.adjG_cur = adjG[cur ^ 1];
       a.theta_n = reinterpret_cast<const float*>(rec + ss.st.theta);
+      a.nrm = reinterpret_cast<const float2*>(rec + ss.nrm);
       a.par = cur;   // reversed steps alternate the u_bar bound slots, the first reads slot 0
       k_seg_restore<<<grid, 256, 0, s>>>(wd, rec, par, (long long)tn, ss, a);
       mc::launch_adj_step(w->plan, h, a, par, s);
@@ -358,7 +361,6 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
     return afail(MC_ERR_INVALID_ARG, "the world was stepped after mc_rollout_forward");
   const mc::WorldDev& h = w->h;
   if ((h.N && (!dL_dx || !dL_dy)) || (h.J && !dL_dtheta0)) return afail(MC_ERR_INVALID_ARG, "NULL gradient pointer");
-  if (h.layers != 1) return afail(MC_ERR_INVALID_ARG, "the reverse mode supports layers = 1 only");
   if (h.ib != 0) return afail(MC_ERR_INVALID_ARG, "the reverse mode supports the penalty coupling (ib = 0) only");
   const int mb = (w->max_B + 3) & ~3;
   if (mc::adj_pbd_smem_per_filament(mb, h.n_pbd, h.pbd_order) > 220 * 1024)
@@ -391,6 +393,7 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
   const size_t o_rsb = take(HW * sizeof(float));
   const size_t o_fbt = take(h.N * sizeof(float2));
   const size_t o_dbar = take(h.N * sizeof(float2));
+  const size_t o_nbar = take(h.N * sizeof(float2));
   const size_t o_seg = take((size_t)K * step_slot(h).bytes);
   if (w->adj_bytes < off) {
     if (w->adj) cudaFreeAsync(w->adj, w->stream);
@@ -418,6 +421,7 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
   a.rsb = reinterpret_cast<float*>(A + o_rsb);
   a.fbt = reinterpret_cast<float2*>(A + o_fbt);
   a.dbar = reinterpret_cast<float2*>(A + o_dbar);
+  a.nbar = reinterpret_cast<float2*>(A + o_nbar);
 
   // inputs (caller memory): outside the cached graph
   MC_ACUDA(cudaMemsetAsync(a.amax, 0, 4 * sizeof(unsigned), s));

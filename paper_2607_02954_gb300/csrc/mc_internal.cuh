@@ -112,6 +112,8 @@ struct AdjDev {
   float2* fbt;             // [N] adjoint of F_el + F_s per bead
   float2* dbar;            // [N] adjoint of the PBD correction
   const float* theta_n;    // [E] edge angles at the start of the step
+  float2* nbar;            // [N] adjoint of the filament normal at each bead (two-layer worlds)
+  const float2* nrm;       // [N] the step's filament normals (two-layer worlds)
   unsigned* amax;          // [3] bounds of the fixed-point sums (float bits): max |dt X_bar| by step
                            // parity (slots 0, 1), max |F_bar| (slot 2)
   float* gkf;              // [3 n_fil] per-filament sums of the stiffness gradients
@@ -435,6 +437,22 @@ __device__ __forceinline__ void obs_add_warp(unsigned long long* acc, long long 
 
 __device__ __forceinline__ int cell_x(const float4& p) { return __float_as_int(p.z); }
 __device__ __forceinline__ int cell_y(const float4& p) { return __float_as_int(p.w); }
+
+// Cell and fraction of the point X + d n for X = (cell, fraction) in p.
+__device__ __forceinline__ void layer_cell(const float4 p, float2 n, float d, int W, int H, int& cx, int& cy,
+                                           float& fx, float& fy) {
+  fx = p.x + d * n.x;
+  fy = p.y + d * n.y;
+  const float kx = floorf(fx), ky = floorf(fy);
+  fx -= kx;
+  fy -= ky;
+  cx = cell_x(p) + (int)kx;
+  cy = cell_y(p) + (int)ky;
+  if (fx >= 1.0f) { fx = 0.0f; cx += 1; }
+  if (fy >= 1.0f) { fy = 0.0f; cy += 1; }
+  cx = wrap_once(cx, W);   // |d| <= 2 keeps the offset within one period (W, H >= 8)
+  cy = wrap_once(cy, H);
+}
 
 // Exponent k of the per-tile fixed-point scale for a bound on |cell sums|:
 // the largest k in [8, 40] with bound * 2^k < 2^30.  With bound = m 2^e,

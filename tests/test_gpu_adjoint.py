@@ -45,10 +45,16 @@ def _oracle_grad(spec, n, gx, gy):
                                          torch.as_tensor(gy, dtype=torch.float64)))
 
 
-@pytest.mark.parametrize("case", ["tiny", "c1", "custom", "red_black", "red_black_c1"])
+@pytest.mark.parametrize("case", ["tiny", "c1", "custom", "red_black", "red_black_c1", "two_layer", "two_layer_c1"])
 def test_adjoint_matches_oracle_reverse_mode(case):
     rng = np.random.default_rng(3)
-    if case == "tiny":
+    if case == "two_layer":
+        spec, n, K = synth.tiny_world(5, side=32, lengths=(9, 8, 6, 2)), 30, 7
+        spec.params = synth.Params(layers=2, layer_half=0.8)
+    elif case == "two_layer_c1":
+        spec, n, K = synth.world_c1(2), 20, 8
+        spec.params = synth.Params(layers=2, layer_half=1.3, pbd_order=1)
+    elif case == "tiny":
         spec, n, K = synth.tiny_world(3, side=32, lengths=(9, 7, 6)), 30, 7
     elif case == "red_black":
         spec, n, K = synth.tiny_world(3, side=32, lengths=(9, 8, 6, 2)), 30, 7
@@ -159,7 +165,7 @@ def test_rollout_fn_autograd_bridge():
     w.close()
 
 
-@pytest.mark.parametrize("case", ["tiny", "custom", "red_black"])
+@pytest.mark.parametrize("case", ["tiny", "custom", "red_black", "two_layer"])
 def test_rest_length_and_stiffness_gradients_match_oracle(case):
     """mc_rollout_backward_params: gradients with respect to theta0, every
     edge's rest length and (k_bend, k_stretch, k_shear) against the FP64
@@ -172,6 +178,10 @@ def test_rest_length_and_stiffness_gradients_match_oracle(case):
         spec, n, K = synth.world_random(13, 64, 5), 20, 7
         spec.params = synth.Params(nu=0.3, kappa=0.2, k_bend=0.7, k_stretch=0.6, k_shear=0.5, k_rep=1.0,
                                    sigma=0.8, orient=1.0, n_pbd=3, pbd_order=1)
+    elif case == "two_layer":
+        spec, n, K = synth.world_random(14, 64, 5), 20, 7
+        spec.params = synth.Params(nu=0.3, kappa=0.2, k_bend=0.7, k_stretch=0.6, k_shear=0.5, k_rep=1.0,
+                                   sigma=0.8, orient=1.0, n_pbd=3, layers=2, layer_half=0.6)
     else:
         spec, n, K = synth.world_random(12, 64, 5), 20, 7
         spec.params = synth.Params(nu=0.3, kappa=0.2, k_bend=0.7, k_stretch=0.6, k_shear=0.5, k_rep=1.0,
@@ -194,8 +204,8 @@ def test_rest_length_and_stiffness_gradients_match_oracle(case):
         assert err <= RTOL * scale, (key, err, scale)
 
 
-@pytest.mark.parametrize("params", [dict(layers=2, layer_half=0.5), dict(ib=1, mdf_iters=2)])
-def test_reverse_mode_rejects_two_layers_and_direct_forcing(params):
+@pytest.mark.parametrize("params", [dict(ib=1, mdf_iters=2), dict(ib=1, mdf_iters=0)])
+def test_reverse_mode_rejects_direct_forcing(params):
     from paper_2607_02954_gb300 import World
     from paper_2607_02954_gb300._lib import MCError
     spec = synth.tiny_world(7, side=32, lengths=(8, 6))
