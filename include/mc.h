@@ -97,7 +97,8 @@ typedef enum mc_mem_kind { MC_MEM_HOST = 0, MC_MEM_DEVICE = 1 } mc_mem_kind;
  *            mdf_iters passes force the fluid to follow it (per bead
  *            dF = 2 I[rho](X) (U_s - I[u](X)), F += S[dF], u += S[dF]/(2 rho)),
  *            the LBM steps with the total force and X^{n+1} = X + dt U_s.
- *            kappa is unused; needs layers = 1; no reverse mode.
+ *            kappa is unused; needs layers = 1.  The reverse mode supports
+ *            it (the passes, the drag and the moments reversed).
  *   mdf_iters  MDF passes per step with ib = 1, 0 <= mdf_iters <= 64 (0: the
  *            filament does not force the fluid). */
 typedef struct mc_params {
@@ -370,7 +371,9 @@ mc_status mc_world_get_observables(const mc_world* w, double* out, void* stream)
  * every ckpt_every steps, the backward re-runs one segment at a time from
  * its checkpoint and reverses it step by step.  Device memory: one state
  * record (16 N + 4 E + 36 H W bytes) per checkpoint and per step of one
- * segment, plus adjoint buffers of about 150 bytes per cell. */
+ * segment, plus adjoint buffers of about 150 bytes per cell; with direct
+ * forcing each step of the segment also keeps 8 H W bytes per MDF pass,
+ * 4 H W and 8 N, and the adjoint about 60 bytes more per cell. */
 
 /* Advances the world n_steps >= 1 steps (like mc_step) recording
  * checkpoints every ckpt_every >= 1 steps.  Errors: MC_ERR_INVALID_ARG,

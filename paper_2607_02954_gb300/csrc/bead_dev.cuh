@@ -60,9 +60,9 @@ __device__ __forceinline__ float4 advance_tail(const WorldDev& w, int i, float4 
   return q;
 }
 
-// U_i = sum_c delta_h(c - X_i) u(c) over the 4x4 stencil of p.
-__device__ __forceinline__ float2 interp_u(const WorldDev& w, const float4 p) {
-  const int W = w.W, H = w.H;
+// U_i = sum_c delta_h(c - X_i) u(c) over the 4x4 stencil of p, for the
+// velocity field u of a W x H grid.
+__device__ __forceinline__ float2 interp_field(const float2* __restrict__ u, int W, int H, const float4 p) {
   const int cx = cell_x(p), cy = cell_y(p);
   float wx[4], wy[4];
   peskin4(p.x, wx);
@@ -73,7 +73,7 @@ __device__ __forceinline__ float2 interp_u(const WorldDev& w, const float4 p) {
   float Ux = 0.0f, Uy = 0.0f;
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
-    const float2* row = w.u + (size_t)wrap_once(cy - 1 + b, H) * W;
+    const float2* row = u + (size_t)wrap_once(cy - 1 + b, H) * W;
     float rx = 0.0f, ry = 0.0f;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
@@ -86,6 +86,9 @@ __device__ __forceinline__ float2 interp_u(const WorldDev& w, const float4 p) {
   }
   return make_float2(Ux, Uy);
 }
+
+// The world's fluid velocity at bead position p.
+__device__ __forceinline__ float2 interp_u(const WorldDev& w, const float4 p) { return interp_field(w.u, w.W, w.H, p); }
 
 // ---------------------------------------------------------------------------
 // Two-layer filament (Fluid-filament Interaction): the immersed-boundary

@@ -18,72 +18,9 @@
 // depend on order), so the integer sums, and every gradient, are bitwise
 // repeatable.  The stiffness gradients are summed per filament and then
 // over filaments in a fixed order.
-#include "mc_internal.cuh"
+#include "adj_dev.cuh"
 
 namespace mc {
-
-// The largest |v| of the warp's lanes into *slot (float bits; non-negative
-// floats order like their bit patterns).
-__device__ __forceinline__ void warp_max_abs(unsigned* slot, float v) {
-  v = fabsf(v);
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if ((threadIdx.x & 31) == 0 && v > 0.0f) atomicMax(slot, __float_as_uint(v));
-}
-
-// A 64-bit fixed-point term (two's complement in the unsigned accumulator).
-__device__ __forceinline__ unsigned long long fx64(float v) { return (unsigned long long)__float2ll_rn(v); }
-__device__ __forceinline__ float fx64_value(unsigned long long q, float inv) { return (float)(long long)q * inv; }
-
-// Peskin weights and their derivatives with respect to the bead coordinate:
-// with s = sqrt(1 + 4a - 4a^2), s' = (2 - 4a)/s.
-__device__ __forceinline__ void peskin4_d(float a, float w[4], float dw[4]) {
-  const float s = sqrtf(fmaf(-4.0f * a, a, fmaf(4.0f, a, 1.0f)));
-  const float ds = (2.0f - 4.0f * a) / s;
-  const float p = 3.0f - 2.0f * a, q = 1.0f + 2.0f * a;
-  w[0] = (p - s) * 0.125f;
-  w[1] = (p + s) * 0.125f;
-  w[2] = (q + s) * 0.125f;
-  w[3] = (q - s) * 0.125f;
-  dw[0] = (-2.0f - ds) * 0.125f;
-  dw[1] = (-2.0f + ds) * 0.125f;
-  dw[2] = (2.0f + ds) * 0.125f;
-  dw[3] = (2.0f - ds) * 0.125f;
-}
-
-struct Stencil {
-  float wx[4], wy[4], dx[4], dy[4];
-  int ix[4], iy[4];   // wrapped column / row-start indices
-};
-
-// The stencil of the two-layer point X + d n of bead p (the forward's
-// layer_cell: cell and fraction of the shifted point).
-__device__ __forceinline__ Stencil make_layer_stencil(const float4& p, float2 n, float d, int W, int H) {
-  int cx, cy;
-  float fx, fy;
-  layer_cell(p, n, d, W, H, cx, cy, fx, fy);
-  Stencil s;
-  peskin4_d(fx, s.wx, s.dx);
-  peskin4_d(fy, s.wy, s.dy);
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    s.ix[a] = wrap_once(cx - 1 + a, W);
-    s.iy[a] = wrap_once(cy - 1 + a, H) * W;
-  }
-  return s;
-}
-
-__device__ __forceinline__ Stencil make_stencil(const float4& p, int W, int H) {
-  Stencil s;
-  peskin4_d(p.x, s.wx, s.dx);
-  peskin4_d(p.y, s.wy, s.dy);
-  const int cx = cell_x(p), cy = cell_y(p);
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    s.ix[a] = wrap_once(cx - 1 + a, W);
-    s.iy[a] = wrap_once(cy - 1 + a, H) * W;
-  }
-  return s;
-}
 
 // ---------------------------------------------------------------------------
 // a8 transposed: u_bar(c) += sum_i w(c - X_i) dt X_bar_i, fixed point with
@@ -265,8 +202,11 @@ __global__ void __launch_bounds__(256) k_adj_bead_a(const WorldDev* __restrict__
   const float4 p = w.pos[i];
   const Stencil s = make_stencil(p, w.W, w.H);
   const float2 xb = a.adjX[i];
-  const float Ubx = w.dt * xb.x, Uby = w.dt * xb.y;
-  const float2 fe = w.fel[i], fs = w.fs[i];
+  // direct forcing: the advance does not read u, and the steric spread
+  // carries F_s alone (the MDF passes' own adjoints are k_adj_mdf.cu's)
+  const bool df = w.ib == 1;
+  const float Ubx = df ? 0.0f : w.dt * xb.x, Uby = df ? 0.0f : w.dt * xb.y;
+  const float2 fe = df ? make_float2(0.0f, 0.0f) : w.fel[i], fs = w.fs[i];
   const float Ftx = fe.x + fs.x, Fty = fe.y + fs.y;
   // over the stencil st (weights scaled by h): the force's adjoint and the
   // position gradient of u.U_bar + F_bar.Ftot
@@ -412,7 +352,7 @@ __global__ void __launch_bounds__(256) k_adj_bead_b(const WorldDev* __restrict__
   }
   const float2 xb = a.adjX[i];
   a.adjX[i] = make_float2(xb.x + gx, xb.y + gy);
-  a.dbar[i] = make_float2(w.kappa_dt * fb.x, w.kappa_dt * fb.y);
+  if (w.ib != 1) a.dbar[i] = make_float2(w.kappa_dt * fb.x, w.kappa_dt * fb.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -520,8 +460,9 @@ __global__ void __launch_bounds__(kAdjPbdThreads) k_adj_pbd(const WorldDev* __re
   float* tape = s + 12 * maxB;  // per pass: theta before bend, theta after bend, d (x), d (y)
   const int W = w.W, H = w.H;
   const long long t = *w.t;
+  const float4* __restrict__ P = a.xt ? a.xt : w.pos;   // the PBD's start: X~ with direct forcing
   for (int e = tid; e < nE; e += kAdjPbdThreads) {
-    const float4 pa = w.pos[b0 + e], pb = w.pos[b0 + e + 1];
+    const float4 pa = P[b0 + e], pb = P[b0 + e + 1];
     int dcx = cell_x(pb) - cell_x(pa), dcy = cell_y(pb) - cell_y(pa);
     if (2 * dcx > W) dcx -= W; else if (2 * dcx < -W) dcx += W;
     if (2 * dcy > H) dcy -= H; else if (2 * dcy < -H) dcy += H;
@@ -807,6 +748,7 @@ __global__ void __launch_bounds__(kAdjPbdThreads) k_adj_pbd(const WorldDev* __re
       xb.x += bx - ax;
       xb.y += by - ay;
       a.adjX[b0 + i] = xb;
+      if (a.xtb) a.xtb[b0 + i] = make_float2(bx - ax, by - ay);
       xm = fmaxf(xm, w.dt * fmaxf(fabsf(xb.x), fabsf(xb.y)));
     }
   }
@@ -919,23 +861,41 @@ static int blocks(int n) { return (n + 255) / 256; }
 constexpr int kAdjBeadThreads = 64;
 static int bead_blocks(int n) { return (n + kAdjBeadThreads - 1) / kAdjBeadThreads; }
 
-void launch_adj_step(const Plan& p, const WorldDev& h, AdjDev a, int src_parity, cudaStream_t s) {
+// One reversed step.  Penalty coupling: a8, a7, a6/a4 gathers, a5, a6
+// gradient/a4, then a3/a1.  Direct forcing (m != NULL): a7, the MDF passes
+// and the drag (k_adj_mdf.cu) around a3/a1, then the steric chain.
+void launch_adj_step(const Plan& p, const WorldDev& h, AdjDev a, const AdjMdf* m, int src_parity, cudaStream_t s) {
   const WorldDev* wd = p.d_worlds;
   const int HW = h.H * h.W;
+  auto pbd = [&](const AdjDev& ap) {
+    if (!p.n_fil_items) return;
+    const int mb = (p.max_B + 3) & ~3;
+    const size_t smem = adj_pbd_smem_per_filament(mb, h.n_pbd, h.pbd_order);
+    if (h.pbd_order == 1)
+      k_adj_pbd<true><<<p.n_fil_items, kAdjPbdThreads, smem, s>>>(wd, ap, p.d_fil_items, p.n_fil_items, mb, h.n_pbd);
+    else
+      k_adj_pbd<false><<<p.n_fil_items, kAdjPbdThreads, smem, s>>>(wd, ap, p.d_fil_items, p.n_fil_items, mb, h.n_pbd);
+  };
   // (u_bar and Q are cleared by the caller before each step)
+  if (m) {
+    k_adj_lbm<<<blocks(HW), 256, 0, s>>>(wd, a, src_parity);
+    launch_adj_mdf_passes(h, wd, a, *m, s);
+    AdjDev ap = a;
+    ap.xt = m->xt;
+    ap.xtb = m->xtb;
+    pbd(ap);
+    launch_adj_mdf_moments(h, wd, a, *m, s);
+    if (h.N) k_adj_bead_a<<<bead_blocks(h.N), kAdjBeadThreads, 0, s>>>(wd, a);
+    k_adj_rho_blur<<<h.ntx * h.nty, 256, 0, s>>>(wd, a);
+    if (h.N) k_adj_bead_b<<<bead_blocks(h.N), kAdjBeadThreads, 0, s>>>(wd, a);
+    return;
+  }
   if (h.N) k_adj_spread_u<<<bead_blocks(h.N), kAdjBeadThreads, 0, s>>>(wd, a);
   k_adj_lbm<<<blocks(HW), 256, 0, s>>>(wd, a, src_parity);
   if (h.N) k_adj_bead_a<<<bead_blocks(h.N), kAdjBeadThreads, 0, s>>>(wd, a);
   k_adj_rho_blur<<<h.ntx * h.nty, 256, 0, s>>>(wd, a);
   if (h.N) k_adj_bead_b<<<bead_blocks(h.N), kAdjBeadThreads, 0, s>>>(wd, a);
-  if (p.n_fil_items) {
-    const int mb = (p.max_B + 3) & ~3;
-    const size_t smem = adj_pbd_smem_per_filament(mb, h.n_pbd, h.pbd_order);
-    if (h.pbd_order == 1)
-      k_adj_pbd<true><<<p.n_fil_items, kAdjPbdThreads, smem, s>>>(wd, a, p.d_fil_items, p.n_fil_items, mb, h.n_pbd);
-    else
-      k_adj_pbd<false><<<p.n_fil_items, kAdjPbdThreads, smem, s>>>(wd, a, p.d_fil_items, p.n_fil_items, mb, h.n_pbd);
-  }
+  pbd(a);
 }
 
 void launch_adj_gk_reduce(const AdjDev& a, int n_fil, cudaStream_t s) {

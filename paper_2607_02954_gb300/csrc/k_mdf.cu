@@ -94,4 +94,23 @@ void launch_mdf(const Plan& p, cudaStream_t s) {
   for (int k = 0; k < p.max_mdf; ++k) launch_mdf_pass(p, s, k);
 }
 
+// launch_mdf for the one world h of plan p, keeping u_0 (the drag's
+// velocity) and each pass's input velocity (u_0 .. u_{m-1}, m =
+// h.mdf_iters) in mu[k H W ..] for the reverse mode.
+cudaError_t launch_mdf_recorded(const Plan& p, const WorldDev& h, float2* mu, cudaStream_t s) {
+  const size_t bytes = (size_t)h.H * h.W * sizeof(float2);
+  if (p.n_cell_items) k_mdf_moments<<<p.n_cell_items, kCellChunk, 0, s>>>(p.d_worlds, p.d_cell_items);
+  cudaError_t e = cudaSuccess;
+  e = cudaMemcpyAsync(mu, h.u, bytes, cudaMemcpyDeviceToDevice, s);
+  launch_pbd_mdf(p, s);
+  for (int k = 0; k < h.mdf_iters && e == cudaSuccess; ++k) {
+    launch_mdf_pass(p, s, k);
+    // pass k writes u2 (k even) or u (k odd)
+    if (k + 1 < h.mdf_iters)
+      e = cudaMemcpyAsync(reinterpret_cast<char*>(mu) + (k + 1) * bytes, (k & 1) ? h.u : h.u2, bytes,
+                          cudaMemcpyDeviceToDevice, s);
+  }
+  return e;
+}
+
 }  // namespace mc

@@ -89,6 +89,7 @@ mc_status load_state(const mc::WorldDev& h, int parity, const char* rec, const S
 struct StepSlot {
   StateSlot st;
   size_t fel, fs, rho_b, u, F, nrm;
+  size_t mu, mrho, us;   // direct forcing: the MDF passes' input velocities, the density, U_s
   size_t bytes;
 };
 
@@ -102,7 +103,11 @@ StepSlot step_slot(const mc::WorldDev& h) {
   s.u = s.rho_b + align256(HW * sizeof(float));
   s.F = s.u + align256(HW * sizeof(float2));
   s.nrm = s.F + align256(HW * sizeof(float2));
-  s.bytes = s.nrm + align256(h.layers == 2 ? (size_t)h.N * sizeof(float2) : 0);
+  const bool df = h.ib == 1;
+  s.mu = s.nrm + align256(h.layers == 2 ? (size_t)h.N * sizeof(float2) : 0);
+  s.mrho = s.mu + align256(df ? (size_t)std::max(h.mdf_iters, 1) * HW * sizeof(float2) : 0);   // u_0 at least
+  s.us = s.mrho + align256(df ? HW * sizeof(float) : 0);
+  s.bytes = s.us + align256(df ? (size_t)h.N * sizeof(float2) : 0);
   return s;
 }
 
@@ -118,6 +123,7 @@ __global__ void k_seg_save(const mc::WorldDev* __restrict__ wd, char* cur, char*
       reinterpret_cast<float2*>(cur + sl.fel)[i] = h.fel[i];
       reinterpret_cast<float2*>(cur + sl.fs)[i] = h.fs[i];
       if (h.nrm) reinterpret_cast<float2*>(cur + sl.nrm)[i] = h.nrm[i];
+      if (h.ib == 1) reinterpret_cast<float2*>(cur + sl.us)[i] = h.ubead[i];   // U_s (the advance's velocity)
       if (next) reinterpret_cast<float4*>(next + sl.st.pos)[i] = h.pos[i];
     }
     if (next && i < (size_t)h.E) reinterpret_cast<float*>(next + sl.st.theta)[i] = h.theta[i];
@@ -125,6 +131,7 @@ __global__ void k_seg_save(const mc::WorldDev* __restrict__ wd, char* cur, char*
       reinterpret_cast<float*>(cur + sl.rho_b)[i] = h.rho_b[i];
       reinterpret_cast<float2*>(cur + sl.u)[i] = h.u[i];
       reinterpret_cast<float2*>(cur + sl.F)[i] = h.F[i];
+      if (h.ib == 1) reinterpret_cast<float*>(cur + sl.mrho)[i] = h.mrho[i];
     }
     if (next && i < n9) reinterpret_cast<float*>(next + sl.st.g)[i] = h.g[par][i];
   }
@@ -284,8 +291,8 @@ namespace {
 // The reverse sweep proper (no caller memory: captured into a graph):
 // zero the adjoints, re-run each segment from its checkpoint keeping every
 // step's state, reverse its steps, and return to the rollout's final state.
-mc_status sweep(mc_world* w, mc::AdjDev a, float* const adjG[2], char* obs_keep, char* seg, const StateSlot& sl,
-                int n_ck, cudaStream_t s) {
+mc_status sweep(mc_world* w, mc::AdjDev a, const mc::AdjMdf* mdf, float* const adjG[2], char* obs_keep, char* seg,
+                const StateSlot& sl, int n_ck, cudaStream_t s) {
   const mc::WorldDev& h = w->h;
   const size_t HW = (size_t)h.H * h.W;
   const int K = w->tape_every, n = w->tape_steps;
@@ -301,6 +308,14 @@ mc_status sweep(mc_world* w, mc::AdjDev a, float* const adjG[2], char* obs_keep,
   if (h.E) MC_ACUDA(cudaMemsetAsync(a.gL, 0, h.E * sizeof(float), s));
   if (h.n_fil) MC_ACUDA(cudaMemsetAsync(a.gkf, 0, 3 * (size_t)h.n_fil * sizeof(float), s));
   MC_ACUDA(cudaMemsetAsync(adjG[0], 0, 9 * HW * sizeof(float), s));
+  if (mdf) {   // the pass accumulators (each reversed step leaves them cleared)
+    MC_ACUDA(cudaMemsetAsync(mdf->ubf, 0, HW * sizeof(float2), s));
+    MC_ACUDA(cudaMemsetAsync(mdf->rhob, 0, HW * sizeof(float), s));
+    MC_ACUDA(cudaMemsetAsync(mdf->su, 0, 2 * HW * sizeof(unsigned long long), s));
+    MC_ACUDA(cudaMemsetAsync(mdf->sr, 0, HW * sizeof(unsigned long long), s));
+    MC_ACUDA(cudaMemsetAsync(mdf->ss, 0, 2 * HW * sizeof(unsigned long long), s));
+    MC_ACUDA(cudaMemsetAsync(mdf->bnd, 0, 5 * sizeof(unsigned), s));
+  }
   int cur = 0;   // adjG[cur] holds the adjoint of the populations after the step being reversed
   const int64_t t0 = w->tape_t0;
   for (int k = n_ck - 1; k >= 0; --k) {
@@ -314,11 +329,23 @@ mc_status sweep(mc_world* w, mc::AdjDev a, float* const adjG[2], char* obs_keep,
     // the segment's forward, keeping every step's state and intermediates
     // (the unfused stages: the same step bitwise, with rho_bar and u in memory)
     for (int q = 0; q < steps; ++q) {
-      mc::launch_pbd(w->plan, s);
-      mc::launch_bin_scan(w->plan, s);
-      mc::launch_bin_scatter(w->plan, s);
-      mc::launch_deposit_x(w->plan, s, 0);
-      mc::launch_force_spread(w->plan, s, 1, 0);
+      if (mdf) {
+        // direct forcing: F = S[F_s], then the density fields (a re-run
+        // that leaves F), the MDF passes keeping their input velocities
+        mc::launch_mdf_bins(w->plan, s);
+        mc::launch_bin_scan(w->plan, s);
+        mc::launch_bin_scatter(w->plan, s);
+        mc::launch_deposit_x(w->plan, s, 0);
+        mc::launch_force_spread(w->plan, s, 0, 0);
+        mc::launch_force_spread(w->plan, s, 1, 0);
+        MC_ACUDA(mc::launch_mdf_recorded(w->plan, h, reinterpret_cast<float2*>(seg + (size_t)q * ss.bytes + ss.mu), s));
+      } else {
+        mc::launch_pbd(w->plan, s);
+        mc::launch_bin_scan(w->plan, s);
+        mc::launch_bin_scatter(w->plan, s);
+        mc::launch_deposit_x(w->plan, s, 0);
+        mc::launch_force_spread(w->plan, s, 1, 0);
+      }
       mc::launch_lbm(w->plan, s);
       mc::launch_interp_advance(w->plan, s);
       char* next = q + 1 < steps ? seg + (size_t)(q + 1) * ss.bytes : nullptr;
@@ -335,7 +362,15 @@ mc_status sweep(mc_world* w, mc::AdjDev a, float* const adjG[2], char* obs_keep,
       a.nrm = reinterpret_cast<const float2*>(rec + ss.nrm);
       a.par = cur;   // reversed steps alternate the u_bar bound slots, the first reads slot 0
       k_seg_restore<<<grid, 256, 0, s>>>(wd, rec, par, (long long)tn, ss, a);
-      mc::launch_adj_step(w->plan, h, a, par, s);
+      if (mdf) {
+        mc::AdjMdf m = *mdf;
+        m.mu = reinterpret_cast<const float2*>(rec + ss.mu);
+        m.rho = reinterpret_cast<const float*>(rec + ss.mrho);
+        m.Us = reinterpret_cast<const float2*>(rec + ss.us);
+        mc::launch_adj_step(w->plan, h, a, &m, par, s);
+      } else {
+        mc::launch_adj_step(w->plan, h, a, nullptr, par, s);
+      }
       cur ^= 1;
     }
     MC_ACUDA(cudaGetLastError());
@@ -361,7 +396,6 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
     return afail(MC_ERR_INVALID_ARG, "the world was stepped after mc_rollout_forward");
   const mc::WorldDev& h = w->h;
   if ((h.N && (!dL_dx || !dL_dy)) || (h.J && !dL_dtheta0)) return afail(MC_ERR_INVALID_ARG, "NULL gradient pointer");
-  if (h.ib != 0) return afail(MC_ERR_INVALID_ARG, "the reverse mode supports the penalty coupling (ib = 0) only");
   const int mb = (w->max_B + 3) & ~3;
   if (mc::adj_pbd_smem_per_filament(mb, h.n_pbd, h.pbd_order) > 220 * 1024)
     return afail(MC_ERR_INVALID_ARG, "filaments too long for the adjoint (reduce beads per filament or n_pbd)");
@@ -394,6 +428,20 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
   const size_t o_fbt = take(h.N * sizeof(float2));
   const size_t o_dbar = take(h.N * sizeof(float2));
   const size_t o_nbar = take(h.N * sizeof(float2));
+  const bool df = h.ib == 1;
+  const size_t o_mGb = take(df ? HW * sizeof(float2) : 0);
+  const size_t o_mub = take(df ? HW * sizeof(float2) : 0);
+  const size_t o_mrb = take(df ? HW * sizeof(float) : 0);
+  const size_t o_msu = take(df ? 2 * HW * sizeof(unsigned long long) : 0);
+  const size_t o_msr = take(df ? HW * sizeof(unsigned long long) : 0);
+  const size_t o_mss = take(df ? 2 * HW * sizeof(unsigned long long) : 0);
+  const size_t o_musb = take(df ? h.N * sizeof(float2) : 0);
+  const size_t o_miub = take(df ? h.N * sizeof(float2) : 0);
+  const size_t o_mrbb = take(df ? h.N * sizeof(float) : 0);
+  const size_t o_mxt = take(df ? h.N * sizeof(float4) : 0);
+  const size_t o_mxtb = take(df ? h.N * sizeof(float2) : 0);
+  const size_t o_must = take(df ? h.N * sizeof(float2) : 0);
+  const size_t o_mbnd = take(df ? 8 * sizeof(unsigned) : 0);
   const size_t o_seg = take((size_t)K * step_slot(h).bytes);
   if (w->adj_bytes < off) {
     if (w->adj) cudaFreeAsync(w->adj, w->stream);
@@ -422,6 +470,23 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
   a.fbt = reinterpret_cast<float2*>(A + o_fbt);
   a.dbar = reinterpret_cast<float2*>(A + o_dbar);
   a.nbar = reinterpret_cast<float2*>(A + o_nbar);
+  mc::AdjMdf m{};
+  if (df) {
+    m.m = h.mdf_iters;
+    m.Gbar = reinterpret_cast<float2*>(A + o_mGb);
+    m.ubf = reinterpret_cast<float2*>(A + o_mub);
+    m.rhob = reinterpret_cast<float*>(A + o_mrb);
+    m.su = reinterpret_cast<unsigned long long*>(A + o_msu);
+    m.sr = reinterpret_cast<unsigned long long*>(A + o_msr);
+    m.ss = reinterpret_cast<unsigned long long*>(A + o_mss);
+    m.usb = reinterpret_cast<float2*>(A + o_musb);
+    m.iub = reinterpret_cast<float2*>(A + o_miub);
+    m.rbb = reinterpret_cast<float*>(A + o_mrbb);
+    m.xt = reinterpret_cast<float4*>(A + o_mxt);
+    m.xtb = reinterpret_cast<float2*>(A + o_mxtb);
+    m.ust = reinterpret_cast<float2*>(A + o_must);
+    m.bnd = reinterpret_cast<unsigned*>(A + o_mbnd);
+  }
 
   // inputs (caller memory): outside the cached graph
   MC_ACUDA(cudaMemsetAsync(a.amax, 0, 4 * sizeof(unsigned), s));
@@ -436,7 +501,7 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
     mc::adj_setup(w->plan, h);
     cudaStream_t cs = adj_capture_stream();
     MC_ACUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    const mc_status st = sweep(w, a, adjG, A + o_obs, seg, sl, n_ck, cs);
+    const mc_status st = sweep(w, a, df ? &m : nullptr, adjG, A + o_obs, seg, sl, n_ck, cs);
     cudaGraph_t g = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(cs, &g);
     if (st != MC_OK) {

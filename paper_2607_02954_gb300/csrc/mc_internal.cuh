@@ -118,6 +118,31 @@ struct AdjDev {
                            // parity (slots 0, 1), max |F_bar| (slot 2)
   float* gkf;              // [3 n_fil] per-filament sums of the stiffness gradients
   int par;                 // parity of the step being reversed (the slot of amax its u_bar reads)
+  const float4* xt;        // [N] direct forcing: the positions the PBD started from (X~); NULL: X^n
+  float2* xtb;             // [N] direct forcing: the PBD's adjoint of X~ through its edge vectors
+};
+
+// Reverse-mode buffers of a direct-forcing step (k_adj_mdf.cu): the step's
+// record (the passes' input velocities, the density, U_s) and the pass
+// adjoints.
+struct AdjMdf {
+  int m;                       // MDF passes per step
+  const float2* mu;            // [max(m, 1) H W] input velocity of pass k (u_0 = u* of the moments)
+  const float* rho;            // [H W] density of the moments
+  const float2* Us;            // [N] the beads' velocity U_s
+  float2* Gbar;                // [H W] adjoint of a pass's spread S[dF]
+  float2* ubf;                 // [H W] adjoint of the next pass's input velocity
+  float* rhob;                 // [H W] adjoint of rho, from the passes
+  unsigned long long* su;      // [2 H W] S of a pass's velocity adjoints (64-bit fixed point)
+  unsigned long long* sr;      // [H W] S of a pass's density adjoints
+  unsigned long long* ss;      // [2 H W] S of the drag velocity's adjoint
+  float2* usb;                 // [N] adjoint of U_s
+  float2* iub;                 // [N] adjoint of I[u_k] of a pass
+  float* rbb;                  // [N] adjoint of I[rho] of a pass
+  float4* xt;                  // [N] X~ = X + dt I[u_0](X)
+  float2* xtb;                 // [N] the PBD's adjoint of X~
+  float2* ust;                 // [N] adjoint of the drag velocity U* = I[u_0](X)
+  unsigned* bnd;               // [5] bounds (float bits): su by pass parity (0, 1), sr (2, 3), ss (4)
 };
 
 // Exponent k of a 64-bit fixed-point scale 2^k for sums of terms whose
@@ -198,6 +223,7 @@ void launch_interp_advance(const Plan& p, cudaStream_t s);
 // MDF passes after it
 void launch_mdf_bins(const Plan& p, cudaStream_t s);
 void launch_mdf(const Plan& p, cudaStream_t s);
+cudaError_t launch_mdf_recorded(const Plan& p, const WorldDev& h, float2* mu, cudaStream_t s);   // one world, passes' inputs kept
 void launch_mdf_pass(const Plan& p, cudaStream_t s, int pass);   // k_steric.cu: one MDF pass (tile kernel)
 void enqueue_step(const Plan& p, cudaStream_t s);
 void enqueue_steps(const Plan& p, int n, cudaStream_t s);   // n steps, fused bead stages where possible
@@ -205,7 +231,11 @@ void launch_advance_pbd(const Plan& p, cudaStream_t s);
 constexpr int kKernelsPerStep = 8;
 
 // --- adjoint (one world) ----------------------------------------------------
-void launch_adj_step(const Plan& p, const WorldDev& h, AdjDev a, int src_parity, cudaStream_t s);
+void launch_adj_step(const Plan& p, const WorldDev& h, AdjDev a, const AdjMdf* m, int src_parity, cudaStream_t s);
+// direct forcing (k_adj_mdf.cu): the passes reversed and X~ with the PBD's
+// d_bar; then, after the PBD's reverse, the drag and the moments reversed
+void launch_adj_mdf_passes(const WorldDev& h, const WorldDev* wd, const AdjDev& a, const AdjMdf& m, cudaStream_t s);
+void launch_adj_mdf_moments(const WorldDev& h, const WorldDev* wd, const AdjDev& a, const AdjMdf& m, cudaStream_t s);
 void launch_adj_gk_reduce(const AdjDev& a, int n_fil, cudaStream_t s);   // gk = sum over filaments of gkf
 size_t adj_pbd_smem_per_filament(int maxB, int n_pbd, int order);
 void adj_setup(const Plan& p, const WorldDev& h);   // host set-up of the adjoint kernels (before capture)

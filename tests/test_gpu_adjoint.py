@@ -45,10 +45,24 @@ def _oracle_grad(spec, n, gx, gy):
                                          torch.as_tensor(gy, dtype=torch.float64)))
 
 
-@pytest.mark.parametrize("case", ["tiny", "c1", "custom", "red_black", "red_black_c1", "two_layer", "two_layer_c1"])
+@pytest.mark.parametrize("case", ["tiny", "c1", "custom", "red_black", "red_black_c1", "two_layer", "two_layer_c1",
+                                  "direct", "direct_c1", "direct_no_passes", "direct_red_black"])
 def test_adjoint_matches_oracle_reverse_mode(case):
     rng = np.random.default_rng(3)
-    if case == "two_layer":
+    if case == "direct":
+        spec, n, K = synth.tiny_world(5, side=32, lengths=(9, 8, 6, 2)), 30, 7
+        spec.params = synth.Params(ib=1, mdf_iters=2)
+    elif case == "direct_c1":
+        spec, n, K = synth.world_c1(3), 20, 8
+        spec.params = synth.Params(ib=1, mdf_iters=3)
+    elif case == "direct_no_passes":
+        spec, n, K = synth.tiny_world(6, side=32, lengths=(9, 7, 6)), 25, 6
+        spec.params = synth.Params(ib=1, mdf_iters=0)
+    elif case == "direct_red_black":
+        spec, n, K = synth.world_random(15, 64, 4), 20, 7
+        spec.params = synth.Params(nu=0.3, kappa=0.2, k_bend=0.7, k_stretch=0.6, k_shear=0.5, k_rep=1.0,
+                                   sigma=0.8, orient=1.0, n_pbd=3, pbd_order=1, ib=1, mdf_iters=1)
+    elif case == "two_layer":
         spec, n, K = synth.tiny_world(5, side=32, lengths=(9, 8, 6, 2)), 30, 7
         spec.params = synth.Params(layers=2, layer_half=0.8)
     elif case == "two_layer_c1":
@@ -165,7 +179,7 @@ def test_rollout_fn_autograd_bridge():
     w.close()
 
 
-@pytest.mark.parametrize("case", ["tiny", "custom", "red_black", "two_layer"])
+@pytest.mark.parametrize("case", ["tiny", "custom", "red_black", "two_layer", "direct"])
 def test_rest_length_and_stiffness_gradients_match_oracle(case):
     """mc_rollout_backward_params: gradients with respect to theta0, every
     edge's rest length and (k_bend, k_stretch, k_shear) against the FP64
@@ -182,6 +196,10 @@ def test_rest_length_and_stiffness_gradients_match_oracle(case):
         spec, n, K = synth.world_random(14, 64, 5), 20, 7
         spec.params = synth.Params(nu=0.3, kappa=0.2, k_bend=0.7, k_stretch=0.6, k_shear=0.5, k_rep=1.0,
                                    sigma=0.8, orient=1.0, n_pbd=3, layers=2, layer_half=0.6)
+    elif case == "direct":
+        spec, n, K = synth.world_random(16, 64, 5), 20, 7
+        spec.params = synth.Params(nu=0.3, kappa=0.2, k_bend=0.7, k_stretch=0.6, k_shear=0.5, k_rep=1.0,
+                                   sigma=0.8, orient=1.0, n_pbd=3, ib=1, mdf_iters=2)
     else:
         spec, n, K = synth.world_random(12, 64, 5), 20, 7
         spec.params = synth.Params(nu=0.3, kappa=0.2, k_bend=0.7, k_stretch=0.6, k_shear=0.5, k_rep=1.0,
@@ -202,20 +220,6 @@ def test_rest_length_and_stiffness_gradients_match_oracle(case):
         assert scale > 0, key
         err = np.max(np.abs(got - want))
         assert err <= RTOL * scale, (key, err, scale)
-
-
-@pytest.mark.parametrize("params", [dict(ib=1, mdf_iters=2), dict(ib=1, mdf_iters=0)])
-def test_reverse_mode_rejects_direct_forcing(params):
-    from paper_2607_02954_gb300 import World
-    from paper_2607_02954_gb300._lib import MCError
-    spec = synth.tiny_world(7, side=32, lengths=(8, 6))
-    spec.params = synth.Params(**params)
-    w = World(spec)
-    w.rollout_forward(5, 2)
-    with pytest.raises(MCError) as ei:
-        w.rollout_backward(torch.zeros(spec.N, device="cuda"), torch.zeros(spec.N, device="cuda"))
-    assert ei.value.status == 1
-    w.close()
 
 
 @pytest.mark.parametrize("R,sigma", [(128, 1.0), (64, 2.3)])
@@ -312,12 +316,17 @@ def test_replayed_reverse_sweep_matches_the_captured_one():
     assert np.max(np.abs(g2 - go)) <= RTOL * np.max(np.abs(go))
 
 
-def test_reverse_mode_is_bitwise_repeatable():
+@pytest.mark.parametrize("ib", [0, 1])
+def test_reverse_mode_is_bitwise_repeatable(ib):
     """Two worlds with the same rollout give bitwise the same loss and
     gradients with respect to theta0, the rest lengths and the stiffnesses
-    (the adjoint's scatters and sums do not depend on thread order)."""
+    (the adjoint's scatters and sums do not depend on thread order), with
+    the penalty coupling and with direct forcing."""
+    import dataclasses
     from paper_2607_02954_gb300 import World
     spec, poly = synth.world_c5(2)
+    if ib:
+        spec.params = dataclasses.replace(spec.params, ib=1, mdf_iters=2)
     n, K = 60, 20
     outs = []
     for _ in range(2):

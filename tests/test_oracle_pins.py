@@ -832,14 +832,15 @@ def _objective(w, n_steps, gx, gy, L_rest=None, ks=None):
     return float((st.D[:, 0] * gx).sum() + (st.D[:, 1] * gy).sum())
 
 
-@pytest.mark.parametrize("order,layers", [(0, 1), (1, 1), (0, 2)])
-def test_T10_parameter_gradient_matches_finite_differences(order, layers):
+@pytest.mark.parametrize("order,layers,ib", [(0, 1, 0), (1, 1, 0), (0, 2, 0), (0, 1, 1)])
+def test_T10_parameter_gradient_matches_finite_differences(order, layers, ib):
     """Gradients with respect to the rest lengths and the three stiffnesses
     against FP64 central differences of the same objective, with Jacobi and
-    with red-black PBD passes, and for a two-layer filament."""
+    with red-black PBD passes, for a two-layer filament, and with direct
+    forcing (two MDF passes)."""
     spec = synth.tiny_world(2, side=16, lengths=(7, 6))
     spec.params = synth.Params(k_bend=0.6, k_stretch=0.7, k_shear=0.4, orient=1.0, pbd_order=order,
-                               layers=layers, layer_half=0.7)
+                               layers=layers, layer_half=0.7, ib=ib, mdf_iters=2)
     w = O.World(spec)
     rng = np.random.default_rng(5)
     gx = torch.tensor(rng.standard_normal(spec.N), dtype=F64)
