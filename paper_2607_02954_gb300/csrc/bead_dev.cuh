@@ -311,6 +311,12 @@ __device__ __forceinline__ float pbd_regs(const WorldDev& w, const PbdConst& k, 
       P1 = advance_tail<false>(w, b0 + i1, P1, U.x, U.y);
     }
     if (kExt && w.observe && w.energy) obs_add_warp(&w.obs[2], q);
+  } else if (kMode == 0 && w.rec_pos) {
+    // the step's start, into the reverse mode's record
+    if (hb0) w.rec_pos[b0 + i0] = P0;
+    if (hb1) w.rec_pos[b0 + i1] = P1;
+    if (he0) w.rec_theta[e0 + i0] = th0;
+    if (he1) w.rec_theta[e0 + i1] = th1;
   } else if (kMode == 2) {
     // direct forcing: the fluid (u* in u) carries the beads, PBD starts there
     if (hb0) {
@@ -474,6 +480,10 @@ __device__ __forceinline__ float pbd_smem(const WorldDev& w, const PbdConst& k, 
   for (int j = lane; j < nJ; j += 32) cpa16(&D[j], &w.drive[j0 + j]);
   cpa_wait_all();
   __syncwarp();
+  if (kMode == 0 && w.rec_pos) {   // the step's start, into the reverse mode's record
+    for (int i = lane; i < B; i += 32) w.rec_pos[b0 + i] = P[i];
+    for (int e = lane; e < nE; e += 32) w.rec_theta[e0 + e] = th[e];
+  }
   for (int e = lane; e < nE; e += 32) {
     const float2 v = edge_vec(P[e], P[e + 1], k.W, k.H);
     vx[e] = v.x;

@@ -18,6 +18,8 @@
 // depend on order), so the integer sums, and every gradient, are bitwise
 // repeatable.  The stiffness gradients are summed per filament and then
 // over filaments in a fixed order.
+#include <algorithm>
+
 #include "adj_dev.cuh"
 
 namespace mc {
@@ -34,6 +36,14 @@ __device__ __forceinline__ int ubar_exponent(const WorldDev& w, const AdjDev& a)
 __global__ void __launch_bounds__(256) k_adj_spread_u(const WorldDev* __restrict__ wd, AdjDev a) {
   const WorldDev& w = *wd;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a.setup && i == 0) {
+    // the step's counter, and the bounds this step's kernels produce: of Q
+    // (k_adj_lbm) and of the next reversed step's u_bar (k_adj_pbd; this
+    // step's u_bar reads slot a.par)
+    *w.t = a.t_step;
+    a.amax[2] = 0u;
+    a.amax[a.par ^ 1] = 0u;
+  }
   if (i >= w.N) return;
   const float scale = pow2f(ubar_exponent(w, a));
   const float2 xb = a.adjX[i];
@@ -83,6 +93,12 @@ __global__ void __launch_bounds__(256) k_adj_lbm(const WorldDev* __restrict__ wd
   if (c < w.H * w.W) {
     const float2 fb = adj_lbm_cell(w, a, src_parity, c);
     m = fmaxf(fabsf(fb.x), fabsf(fb.y));
+    // u_bar is read, and the previous reversed step's Q is dead: both start
+    // the next reversed step at zero
+    a.ubar[2 * c] = 0ull;
+    a.ubar[2 * c + 1] = 0ull;
+    a.Q[2 * c] = 0ull;
+    a.Q[2 * c + 1] = 0ull;
   }
   warp_max_abs(&a.amax[2], m);   // the bound of the steric spread Q (k_adj_bead_a)
 }
@@ -326,10 +342,8 @@ __global__ void __launch_bounds__(256) k_adj_rho_blur(const WorldDev* __restrict
 //   X_bar_i += sum_c grad_X w [rho_s_bar(c) - k_rep grad rho_bar(c) . Ftot_bar_i]
 // and the elastic-force adjoint d_bar_i = kappa/dt Ftot_bar_i for the PBD.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_adj_bead_b(const WorldDev* __restrict__ wd, AdjDev a) {
-  const WorldDev& w = *wd;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= w.N) return;
+// Bead i: adds its a4 / a6-gradient terms to X_bar, returns Ftot_bar_i.
+__device__ __forceinline__ float2 adj_bead_b_one(const WorldDev& w, const AdjDev& a, int i) {
   const int W = w.W, H = w.H;
   const float4 p = w.pos[i];
   const Stencil s = make_stencil(p, W, H);
@@ -352,6 +366,16 @@ __global__ void __launch_bounds__(256) k_adj_bead_b(const WorldDev* __restrict__
   }
   const float2 xb = a.adjX[i];
   a.adjX[i] = make_float2(xb.x + gx, xb.y + gy);
+  return fb;
+}
+
+// (as its own kernel for direct forcing, whose PBD reverse comes before the
+// steric chain; the penalty step runs it inside k_adj_pbd)
+__global__ void __launch_bounds__(256) k_adj_bead_b(const WorldDev* __restrict__ wd, AdjDev a) {
+  const WorldDev& w = *wd;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= w.N) return;
+  const float2 fb = adj_bead_b_one(w, a, i);
   if (w.ib != 1) a.dbar[i] = make_float2(w.kappa_dt * fb.x, w.kappa_dt * fb.y);
 }
 
@@ -552,7 +576,13 @@ __global__ void __launch_bounds__(kAdjPbdThreads) k_adj_pbd(const WorldDev* __re
   // adjoint state: d_bar in dx/dy, theta_bar in th, edge-vector adjoint
   // v0_bar after the tape; per-lane sums of the stiffness adjoints
   for (int i = tid; i < B; i += kAdjPbdThreads) {
-    const float2 db = a.dbar[b0 + i];
+    float2 db;
+    if (a.xt) {   // direct forcing: d_bar from the bead velocities' adjoint
+      db = a.dbar[b0 + i];
+    } else {      // penalty: a4 and the a6 gradient of the bead first, d_bar = kappa/dt Ftot_bar
+      const float2 fb = adj_bead_b_one(w, a, b0 + i);
+      db = make_float2(w.kappa_dt * fb.x, w.kappa_dt * fb.y);
+    }
     dx[i] = db.x;
     dy[i] = db.y;
   }
@@ -890,12 +920,11 @@ void launch_adj_step(const Plan& p, const WorldDev& h, AdjDev a, const AdjMdf* m
     if (h.N) k_adj_bead_b<<<bead_blocks(h.N), kAdjBeadThreads, 0, s>>>(wd, a);
     return;
   }
-  if (h.N) k_adj_spread_u<<<bead_blocks(h.N), kAdjBeadThreads, 0, s>>>(wd, a);
+  if (h.N || a.setup) k_adj_spread_u<<<std::max(bead_blocks(h.N), 1), kAdjBeadThreads, 0, s>>>(wd, a);
   k_adj_lbm<<<blocks(HW), 256, 0, s>>>(wd, a, src_parity);
   if (h.N) k_adj_bead_a<<<bead_blocks(h.N), kAdjBeadThreads, 0, s>>>(wd, a);
   k_adj_rho_blur<<<h.ntx * h.nty, 256, 0, s>>>(wd, a);
-  if (h.N) k_adj_bead_b<<<bead_blocks(h.N), kAdjBeadThreads, 0, s>>>(wd, a);
-  pbd(a);
+  pbd(a);   // with a4 and the a6 gradient per bead (k_adj_bead_b's work) first
 }
 
 void launch_adj_gk_reduce(const AdjDev& a, int n_fil, cudaStream_t s) {

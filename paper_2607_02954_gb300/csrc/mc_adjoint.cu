@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "mc_internal.cuh"
 
@@ -288,11 +289,41 @@ mc_status mc_world_set_rest(mc_world* w, const float* theta0, const float* L_res
 
 namespace {
 
+// Descriptors of the reverse sweep's steps (penalty coupling), so that
+// neither the recompute nor the reverse copies a step's fields: the world's
+// own descriptor with the step's fields in its slot q of the segment record.
+// Recompute of step q (population parity par): populations in from slot q
+// and out to slot q + 1 (the world's own buffer after the last slot), F, u,
+// rho_bar, F_el, F_s and the normals written into slot q, and the unfused
+// PBD records the positions and edge angles it starts from there.  Reverse
+// of step q: the same slot, with the positions read from it.
+mc::WorldDev bind_step(const mc::WorldDev& h, char* seg, const StepSlot& ss, int K, int q, int par, bool reverse) {
+  mc::WorldDev b = h;
+  char* rec = seg + (size_t)q * ss.bytes;
+  b.g[par] = reinterpret_cast<float*>(rec + ss.st.g);
+  if (q + 1 < K) b.g[par ^ 1] = reinterpret_cast<float*>(seg + (size_t)(q + 1) * ss.bytes + ss.st.g);
+  b.F = reinterpret_cast<float2*>(rec + ss.F);
+  b.u = reinterpret_cast<float2*>(rec + ss.u);
+  b.rho_b = reinterpret_cast<float*>(rec + ss.rho_b);
+  b.fel = reinterpret_cast<float2*>(rec + ss.fel);
+  b.fs = reinterpret_cast<float2*>(rec + ss.fs);
+  if (h.layers == 2) b.nrm = reinterpret_cast<float2*>(rec + ss.nrm);
+  if (reverse) {
+    b.pos = reinterpret_cast<float4*>(rec + ss.st.pos);
+  } else {
+    b.rec_pos = reinterpret_cast<float4*>(rec + ss.st.pos);
+    b.rec_theta = reinterpret_cast<float*>(rec + ss.st.theta);
+  }
+  return b;
+}
+
+size_t bind_index(int K, int q, int par, bool reverse) { return ((size_t)(reverse ? 2 : 0) + par) * K + q; }
+
 // The reverse sweep proper (no caller memory: captured into a graph):
 // zero the adjoints, re-run each segment from its checkpoint keeping every
 // step's state, reverse its steps, and return to the rollout's final state.
 mc_status sweep(mc_world* w, mc::AdjDev a, const mc::AdjMdf* mdf, float* const adjG[2], char* obs_keep, char* seg,
-                const StateSlot& sl, int n_ck, cudaStream_t s) {
+                const StateSlot& sl, int n_ck, const mc::WorldDev* bind_h, mc::WorldDev* bind_d, cudaStream_t s) {
   const mc::WorldDev& h = w->h;
   const size_t HW = (size_t)h.H * h.W;
   const int K = w->tape_every, n = w->tape_steps;
@@ -308,6 +339,16 @@ mc_status sweep(mc_world* w, mc::AdjDev a, const mc::AdjMdf* mdf, float* const a
   if (h.E) MC_ACUDA(cudaMemsetAsync(a.gL, 0, h.E * sizeof(float), s));
   if (h.n_fil) MC_ACUDA(cudaMemsetAsync(a.gkf, 0, 3 * (size_t)h.n_fil * sizeof(float), s));
   MC_ACUDA(cudaMemsetAsync(adjG[0], 0, 9 * HW * sizeof(float), s));
+  MC_ACUDA(cudaMemsetAsync(a.ubar, 0, 2 * HW * sizeof(unsigned long long), s));
+  MC_ACUDA(cudaMemsetAsync(a.Q, 0, 2 * HW * sizeof(unsigned long long), s));
+  // a step's plan with the step's descriptor (penalty coupling)
+  auto step_plan = [&](int q, int par, bool reverse) {
+    mc::Plan p = w->plan;
+    const size_t i = bind_index(K, q, par, reverse);
+    p.d_worlds = bind_d + i;
+    p.h_world0 = bind_h[i];
+    return p;
+  };
   if (mdf) {   // the pass accumulators (each reversed step leaves them cleared)
     MC_ACUDA(cudaMemsetAsync(mdf->ubf, 0, HW * sizeof(float2), s));
     MC_ACUDA(cudaMemsetAsync(mdf->rhob, 0, HW * sizeof(float), s));
@@ -339,17 +380,21 @@ mc_status sweep(mc_world* w, mc::AdjDev a, const mc::AdjMdf* mdf, float* const a
         mc::launch_force_spread(w->plan, s, 0, 0);
         mc::launch_force_spread(w->plan, s, 1, 0);
         MC_ACUDA(mc::launch_mdf_recorded(w->plan, h, reinterpret_cast<float2*>(seg + (size_t)q * ss.bytes + ss.mu), s));
+        mc::launch_lbm(w->plan, s);
+        mc::launch_interp_advance(w->plan, s);
+        char* next = q + 1 < steps ? seg + (size_t)(q + 1) * ss.bytes : nullptr;
+        k_seg_save<<<grid, 256, 0, s>>>(wd, seg + (size_t)q * ss.bytes, next, (int)((tk + q + 1) & 1), ss);
       } else {
-        mc::launch_pbd(w->plan, s);
-        mc::launch_bin_scan(w->plan, s);
-        mc::launch_bin_scatter(w->plan, s);
-        mc::launch_deposit_x(w->plan, s, 0);
-        mc::launch_force_spread(w->plan, s, 1, 0);
+        // the step's fields go straight into its record (bind_step)
+        const mc::Plan p = step_plan(q, (int)((tk + q) & 1), false);
+        mc::launch_pbd(p, s);
+        mc::launch_bin_scan(p, s);
+        mc::launch_bin_scatter(p, s);
+        mc::launch_deposit_x(p, s, 0);
+        mc::launch_force_spread(p, s, 1, 0);
+        mc::launch_lbm(p, s);
+        mc::launch_interp_advance(p, s);
       }
-      mc::launch_lbm(w->plan, s);
-      mc::launch_interp_advance(w->plan, s);
-      char* next = q + 1 < steps ? seg + (size_t)(q + 1) * ss.bytes : nullptr;
-      k_seg_save<<<grid, 256, 0, s>>>(wd, seg + (size_t)q * ss.bytes, next, (int)((tk + q + 1) & 1), ss);
     }
     MC_ACUDA(cudaGetLastError());
     for (int q = steps - 1; q >= 0; --q) {
@@ -361,15 +406,18 @@ mc_status sweep(mc_world* w, mc::AdjDev a, const mc::AdjMdf* mdf, float* const a
       a.theta_n = reinterpret_cast<const float*>(rec + ss.st.theta);
       a.nrm = reinterpret_cast<const float2*>(rec + ss.nrm);
       a.par = cur;   // reversed steps alternate the u_bar bound slots, the first reads slot 0
-      k_seg_restore<<<grid, 256, 0, s>>>(wd, rec, par, (long long)tn, ss, a);
       if (mdf) {
+        k_seg_restore<<<grid, 256, 0, s>>>(wd, rec, par, (long long)tn, ss, a);
         mc::AdjMdf m = *mdf;
         m.mu = reinterpret_cast<const float2*>(rec + ss.mu);
         m.rho = reinterpret_cast<const float*>(rec + ss.mrho);
         m.Us = reinterpret_cast<const float2*>(rec + ss.us);
         mc::launch_adj_step(w->plan, h, a, &m, par, s);
       } else {
-        mc::launch_adj_step(w->plan, h, a, nullptr, par, s);
+        mc::AdjDev ab = a;
+        ab.setup = 1;   // counter and bound slots (the fields are read from the record in place)
+        ab.t_step = (long long)tn;
+        mc::launch_adj_step(step_plan(q, par, true), h, ab, nullptr, par, s);
       }
       cur ^= 1;
     }
@@ -442,6 +490,7 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
   const size_t o_mxtb = take(df ? h.N * sizeof(float2) : 0);
   const size_t o_must = take(df ? h.N * sizeof(float2) : 0);
   const size_t o_mbnd = take(df ? 8 * sizeof(unsigned) : 0);
+  const size_t o_bind = take(df ? 0 : 4 * (size_t)K * sizeof(mc::WorldDev));
   const size_t o_seg = take((size_t)K * step_slot(h).bytes);
   if (w->adj_bytes < off) {
     if (w->adj) cudaFreeAsync(w->adj, w->stream);
@@ -499,9 +548,21 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
     if (w->bwd_exec) cudaGraphExecDestroy(w->bwd_exec);
     w->bwd_exec = nullptr;
     mc::adj_setup(w->plan, h);
+    // the per-step descriptors (penalty coupling), uploaded before the capture
+    std::vector<mc::WorldDev> bind_h;
+    mc::WorldDev* bind_d = reinterpret_cast<mc::WorldDev*>(A + o_bind);
+    if (!df) {
+      const StepSlot ssl = step_slot(h);
+      bind_h.resize(4 * (size_t)K);
+      for (int rv = 0; rv < 2; ++rv)
+        for (int par = 0; par < 2; ++par)
+          for (int q = 0; q < K; ++q) bind_h[bind_index(K, q, par, rv)] = bind_step(h, seg, ssl, K, q, par, rv);
+      MC_ACUDA(cudaMemcpyAsync(bind_d, bind_h.data(), bind_h.size() * sizeof(mc::WorldDev), cudaMemcpyHostToDevice, s));
+      MC_ACUDA(cudaStreamSynchronize(s));
+    }
     cudaStream_t cs = adj_capture_stream();
     MC_ACUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    const mc_status st = sweep(w, a, df ? &m : nullptr, adjG, A + o_obs, seg, sl, n_ck, cs);
+    const mc_status st = sweep(w, a, df ? &m : nullptr, adjG, A + o_obs, seg, sl, n_ck, bind_h.data(), bind_d, cs);
     cudaGraph_t g = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(cs, &g);
     if (st != MC_OK) {

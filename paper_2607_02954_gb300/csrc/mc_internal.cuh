@@ -89,6 +89,10 @@ struct WorldDev {
   const float* energy;    // [H * W] energy field, or nullptr
   float* ebead;           // [N] energy sampled at each bead (observe and energy)
   unsigned long long* obs;  // [3] E_bend, E_pos, energy collected, fixed point 2^-24 (two's complement)
+  // reverse mode: where an unfused PBD records the positions and edge angles
+  // it starts from (nullptr outside the reverse sweep's recompute)
+  float4* rec_pos;        // [N]
+  float* rec_theta;       // [E]
 };
 
 // Fixed-point scale of the observable sums (units of 2^-24): a warp's
@@ -120,6 +124,8 @@ struct AdjDev {
   int par;                 // parity of the step being reversed (the slot of amax its u_bar reads)
   const float4* xt;        // [N] direct forcing: the positions the PBD started from (X~); NULL: X^n
   float2* xtb;             // [N] direct forcing: the PBD's adjoint of X~ through its edge vectors
+  long long t_step;        // the reversed step's counter value (set by k_adj_spread_u when setup != 0)
+  int setup;               // 1: k_adj_spread_u sets the counter and clears this step's bound slots
 };
 
 // Reverse-mode buffers of a direct-forcing step (k_adj_mdf.cu): the step's
