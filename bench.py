@@ -88,7 +88,7 @@ STEP_BYTES_PER_BEAD = 32
 # kernel, from an ncu capture of the workload, keyed by the fingerprint of the
 # sources the kernel is built from (reported only while they are unchanged)
 KERNEL_TRAFFIC = {("c3_22", "af7be0aa2b2a71a7"): 1591396096}
-KERNEL_SOURCES = ["k_steric.cu", "mc_internal.cuh"]
+KERNEL_SOURCES = ["steric_dev.cuh", "k_steric.cu", "mc_internal.cuh"]
 
 
 def kernel_fingerprint() -> str:
@@ -153,6 +153,11 @@ def _make_spec(name: str, seed: int):
         n = int(name.split("_")[1])
         side = synth.c3_side(n)
         return synth.world_c3(n, seed), f"c3: 2^{n} beads as 64-bead filaments on {side}^2, FP32"
+    if name.startswith("dense_"):
+        n = int(name.split("_")[1])
+        return (synth.world_dense(256, 2 ** n, seed),
+                f"dense: 2^{n} beads as 64-bead filaments on 256^2 ({2 ** n / 65536:g} per cell; the paper's "
+                "scalability shape), FP32")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -160,6 +165,12 @@ def sample_spec(name: str, seed: int, params=None):
     """Bounded sample of the workload for the CPU oracle: same density and
     filament shape, 1/16 of the area for the big sweep points."""
     from paper_2607_02954_gb300 import synth
+    if name.startswith("dense_"):
+        n = int(name.split("_")[1])
+        spec = synth.world_dense(256, 2 ** n, seed)
+        if params is not None:
+            spec.params = params
+        return spec, f"one oracle step of the full dense world (2^{n} beads on 256^2)"
     if name.startswith("c3_"):
         n = int(name.split("_")[1])
         side = synth.c3_side(n)
