@@ -416,6 +416,12 @@ def bench_batched(args, steps=None):
             "clocks": clk.summary()}
 
 
+def stored_bytes_per_step(spec) -> int:
+    """Step record of a stored rollout (include/mc.h): 32 N + 4 E + 56 H W
+    bytes (+ 8 N with two layers), before 256-byte alignment."""
+    return 32 * spec.N + 4 * spec.E + 56 * spec.H * spec.W
+
+
 def bench_gradient(args):
     """Folding gradient (reverse mode, the Filament Folding experiment's
     loop): a 2000-step rollout of the folding world (256^2 grid, 64 x 48
@@ -459,7 +465,35 @@ def bench_gradient(args):
             theta0 = theta0 - 1e-3 * t2n_host(g["theta0"]).astype(np.float32)   # a gradient step
     w.check()
     grad_norm = float(torch.linalg.vector_norm(g["theta0"]).item())
+    g_ck = {k: t2n_host(v).copy() for k, v in g.items()}
+    # the same loop with every step's record kept (mc_rollout_forward_stored:
+    # the backward re-runs no step), from the same start
+    theta0 = spec.theta0.copy()
+    w.rollout_rewind()
+    w.set_rest(theta0=theta0)
+    w.rollout_forward(n, stored=True)
+    loss, gx, gy = loss_fn(w)
+    w.rollout_backward_params(gx, gy)
+    torch.cuda.synchronize()
+    fwd_s, bwd_s = [], []
+    for _ in range(reps):
+        w.rollout_rewind()
+        w.set_rest(theta0=theta0)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        w.rollout_forward(n, stored=True)
+        e[1].record(stream)
+        loss, gx, gy = loss_fn(w)
+        g = w.rollout_backward_params(gx, gy)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        fwd_s.append(e[0].elapsed_time(e[1]))
+        bwd_s.append(e[1].elapsed_time(e[2]))
+        theta0 = theta0 - 1e-3 * t2n_host(g["theta0"]).astype(np.float32)
+    w.check()
+    same = all(np.array_equal(t2n_host(g[k]), g_ck[k]) for k in g_ck)
     w.close()
+    ms_fs, ms_bs = statistics.median(fwd_s), statistics.median(bwd_s)
     ms_f, ms_b = statistics.median(fwd), statistics.median(bwd)
     value = spec.N * n / ((ms_f + ms_b) * 1e-3)
     line = {"metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": 1,
@@ -471,6 +505,9 @@ def bench_gradient(args):
                        "description": f"folding gradient: checkpointed forward + {args.loss} loss + reverse sweep "
                                       "(theta0, L_rest, k_bend, k_stretch, k_shear)"},
             "forward_ms": ms_f, "backward_ms": ms_b, "backward_over_forward": ms_b / ms_f,
+            "stored": {"forward_ms": ms_fs, "backward_ms": ms_bs, "backward_over_forward": ms_bs / ms_fs,
+                       "value": spec.N * n / ((ms_fs + ms_bs) * 1e-3), "gradients_equal_checkpointed": same,
+                       "tape_bytes_per_step": stored_bytes_per_step(spec)},
             "grad_norm_theta0": grad_norm, "clocks": clk.summary()}
     if not args.no_cpu_baseline:
         import oracle as O

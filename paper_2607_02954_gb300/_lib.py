@@ -101,6 +101,7 @@ SIGNATURES = {
     "mc_world_get_observables": (_i, [_vp, _vp, _vp]),
     "mc_rollout_forward": (_i, [_vp, _i, _i, _vp]),
     "mc_rollout_backward": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "mc_rollout_forward_stored": (_i, [_vp, _i, _vp]),
     "mc_rollout_rewind": (_i, [_vp, _vp]),
     "mc_world_set_rest": (_i, [_vp, _vp, _vp, _i, _vp]),
     "mc_rollout_backward_params": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -121,7 +122,7 @@ SIGNATURES = {
 _lib = None
 
 
-ABI_VERSION = 6   # MC_ABI_VERSION of include/mc.h that these structures mirror
+ABI_VERSION = 7   # MC_ABI_VERSION of include/mc.h that these structures mirror
 
 
 def load():

@@ -175,6 +175,63 @@ __global__ void k_seg_restore(const mc::WorldDev* __restrict__ wd, const char* r
   }
 }
 
+// Descriptors of the reverse sweep's steps (penalty coupling), so that
+// neither the recompute nor the reverse copies a step's fields: the world's
+// own descriptor with the step's fields in its slot q of the segment record.
+// Recompute of step q (population parity par): populations in from slot q
+// and out to slot q + 1 (the world's own buffer after the last slot), F, u,
+// rho_bar, F_el, F_s and the normals written into slot q, and the unfused
+// PBD records the positions and edge angles it starts from there.  Reverse
+// of step q: the same slot, with the positions read from it.
+mc::WorldDev bind_step(const mc::WorldDev& h, char* seg, const StepSlot& ss, int K, int q, int par, bool reverse) {
+  mc::WorldDev b = h;
+  char* rec = seg + (size_t)q * ss.bytes;
+  b.g[par] = reinterpret_cast<float*>(rec + ss.st.g);
+  if (q + 1 < K) b.g[par ^ 1] = reinterpret_cast<float*>(seg + (size_t)(q + 1) * ss.bytes + ss.st.g);
+  b.F = reinterpret_cast<float2*>(rec + ss.F);
+  b.u = reinterpret_cast<float2*>(rec + ss.u);
+  b.rho_b = reinterpret_cast<float*>(rec + ss.rho_b);
+  b.fel = reinterpret_cast<float2*>(rec + ss.fel);
+  b.fs = reinterpret_cast<float2*>(rec + ss.fs);
+  if (h.layers == 2) b.nrm = reinterpret_cast<float2*>(rec + ss.nrm);
+  if (reverse) {
+    b.pos = reinterpret_cast<float4*>(rec + ss.st.pos);
+  } else {
+    b.rec_pos = reinterpret_cast<float4*>(rec + ss.st.pos);
+    b.rec_theta = reinterpret_cast<float*>(rec + ss.st.theta);
+  }
+  return b;
+}
+
+size_t bind_index(int K, int q, int par, bool reverse) { return ((size_t)(reverse ? 2 : 0) + par) * K + q; }
+
+// A stored rollout's tape: the start and final state records and the tail
+// (tape_tail with one checkpoint), then one step record per step, then the
+// recorded forward's step descriptors.
+struct StoredLayout {
+  size_t steps, desc, end;
+};
+
+StoredLayout stored_layout(const mc::WorldDev& h, int n) {
+  StoredLayout L;
+  L.steps = align256(tape_tail(h, 1, state_slot(h)).end);
+  L.desc = L.steps + (size_t)n * step_slot(h).bytes;
+  L.end = L.desc + align256((size_t)n * sizeof(mc::WorldDev));
+  return L;
+}
+
+// One step of the penalty path in unfused stages, with p's descriptor
+// binding the step's fields to its record (bind_step).
+void run_recorded_step(const mc::Plan& p, cudaStream_t s) {
+  mc::launch_pbd(p, s);
+  mc::launch_bin_scan(p, s);
+  mc::launch_bin_scatter(p, s);
+  mc::launch_deposit_x(p, s, 0);
+  mc::launch_force_spread(p, s, 1, 0);
+  mc::launch_lbm(p, s);
+  mc::launch_interp_advance(p, s);
+}
+
 // X_bar of the final positions from the caller's gradient, and its largest
 // |dt X_bar| (slot 0 of amax, zeroed before: the first reversed step's u_bar
 // bound).
@@ -214,6 +271,7 @@ mc_status mc_rollout_forward(mc_world* w, int n_steps, int ckpt_every, void* str
   w->tape_t0 = w->t;
   w->tape_steps = n_steps;
   w->tape_every = ckpt_every;
+  w->tape_stored = false;
   // the start's displacement and observables (the checkpoints hold the rest), for mc_rollout_rewind
   if (h.N) MC_ACUDA(cudaMemcpyAsync(tape + tl.disp0, h.disp, h.N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
   MC_ACUDA(cudaMemcpyAsync(tape + tl.obs0, h.obs, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
@@ -231,6 +289,66 @@ mc_status mc_rollout_forward(mc_world* w, int n_steps, int ckpt_every, void* str
   if (st != MC_OK) return st;
   if (h.N) MC_ACUDA(cudaMemcpyAsync(tape + tl.disp_end, h.disp, h.N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
   return MC_OK;
+}
+
+mc_status mc_rollout_forward_stored(mc_world* w, int n_steps, void* stream) {
+  if (!w || n_steps < 1) return afail(MC_ERR_INVALID_ARG, "need a world and n_steps >= 1");
+  if (w->t + n_steps >= (int64_t(1) << 24)) return afail(MC_ERR_INVALID_ARG, "step counter would reach 2^24");
+  const mc::WorldDev& h = w->h;
+  if (h.ib != 0) return afail(MC_ERR_INVALID_ARG, "stored rollouts need the penalty coupling (ib = 0)");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t HW = (size_t)h.H * h.W;
+  const StateSlot sl = state_slot(h);
+  const StepSlot ss = step_slot(h);
+  const StoredLayout L = stored_layout(h, n_steps);
+  if (w->tape_bytes < L.end) {
+    if (w->tape) cudaFreeAsync(w->tape, w->stream);
+    w->tape = nullptr;
+    w->tape_bytes = 0;
+    cudaError_t e = cudaMallocAsync(&w->tape, L.end, s);
+    if (e != cudaSuccess) return afail(MC_ERR_OOM, std::string("stored rollout allocation: ") + cudaGetErrorString(e));
+    w->tape_bytes = L.end;
+  }
+  char* tape = static_cast<char*>(w->tape);
+  char* seg = tape + L.steps;
+  const int64_t t0 = w->t;
+  w->tape_t0 = t0;
+  w->tape_steps = n_steps;
+  w->tape_every = n_steps;
+  w->tape_stored = true;
+  const TapeTail tl = tape_tail(h, 1, sl);
+  if (h.N) MC_ACUDA(cudaMemcpyAsync(tape + tl.disp0, h.disp, h.N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  MC_ACUDA(cudaMemcpyAsync(tape + tl.obs0, h.obs, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
+  mc_status st = save_state(h, (int)(t0 & 1), tape, sl, s);   // the start (mc_rollout_rewind)
+  if (st != MC_OK) return st;
+  // step 0 reads its populations from its record
+  MC_ACUDA(cudaMemcpyAsync(seg + ss.st.g, h.g[t0 & 1], 9 * HW * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  std::vector<mc::WorldDev> desc(n_steps);
+  for (int q = 0; q < n_steps; ++q) desc[q] = bind_step(h, seg, ss, n_steps, q, (int)((t0 + q) & 1), false);
+  mc::WorldDev* d_desc = reinterpret_cast<mc::WorldDev*>(tape + L.desc);
+  MC_ACUDA(cudaMemcpyAsync(d_desc, desc.data(), desc.size() * sizeof(mc::WorldDev), cudaMemcpyHostToDevice, s));
+  for (int q = 0; q < n_steps; ++q) {
+    mc::Plan p = w->plan;
+    p.d_worlds = d_desc + q;
+    p.h_world0 = desc[q];
+    run_recorded_step(p, s);
+  }
+  MC_ACUDA(cudaGetLastError());
+  w->t += n_steps;
+  // the world's own field buffers get the last step's fields
+  char* last = seg + (size_t)(n_steps - 1) * ss.bytes;
+  if (h.N) {
+    MC_ACUDA(cudaMemcpyAsync(h.fel, last + ss.fel, h.N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    MC_ACUDA(cudaMemcpyAsync(h.fs, last + ss.fs, h.N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    if (h.layers == 2) MC_ACUDA(cudaMemcpyAsync(h.nrm, last + ss.nrm, h.N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  }
+  MC_ACUDA(cudaMemcpyAsync(h.u, last + ss.u, HW * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  MC_ACUDA(cudaMemcpyAsync(h.F, last + ss.F, HW * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  MC_ACUDA(cudaMemcpyAsync(h.rho_b, last + ss.rho_b, HW * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  st = save_state(h, (int)(w->t & 1), tape + sl.bytes, sl, s);   // the final state
+  if (st != MC_OK) return st;
+  if (h.N) MC_ACUDA(cudaMemcpyAsync(tape + tl.disp_end, h.disp, h.N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  return MC_OK;   // (a copy from pageable memory returns once it has read the host descriptors)
 }
 
 mc_status mc_rollout_rewind(mc_world* w, void* stream) {
@@ -289,41 +407,13 @@ mc_status mc_world_set_rest(mc_world* w, const float* theta0, const float* L_res
 
 namespace {
 
-// Descriptors of the reverse sweep's steps (penalty coupling), so that
-// neither the recompute nor the reverse copies a step's fields: the world's
-// own descriptor with the step's fields in its slot q of the segment record.
-// Recompute of step q (population parity par): populations in from slot q
-// and out to slot q + 1 (the world's own buffer after the last slot), F, u,
-// rho_bar, F_el, F_s and the normals written into slot q, and the unfused
-// PBD records the positions and edge angles it starts from there.  Reverse
-// of step q: the same slot, with the positions read from it.
-mc::WorldDev bind_step(const mc::WorldDev& h, char* seg, const StepSlot& ss, int K, int q, int par, bool reverse) {
-  mc::WorldDev b = h;
-  char* rec = seg + (size_t)q * ss.bytes;
-  b.g[par] = reinterpret_cast<float*>(rec + ss.st.g);
-  if (q + 1 < K) b.g[par ^ 1] = reinterpret_cast<float*>(seg + (size_t)(q + 1) * ss.bytes + ss.st.g);
-  b.F = reinterpret_cast<float2*>(rec + ss.F);
-  b.u = reinterpret_cast<float2*>(rec + ss.u);
-  b.rho_b = reinterpret_cast<float*>(rec + ss.rho_b);
-  b.fel = reinterpret_cast<float2*>(rec + ss.fel);
-  b.fs = reinterpret_cast<float2*>(rec + ss.fs);
-  if (h.layers == 2) b.nrm = reinterpret_cast<float2*>(rec + ss.nrm);
-  if (reverse) {
-    b.pos = reinterpret_cast<float4*>(rec + ss.st.pos);
-  } else {
-    b.rec_pos = reinterpret_cast<float4*>(rec + ss.st.pos);
-    b.rec_theta = reinterpret_cast<float*>(rec + ss.st.theta);
-  }
-  return b;
-}
-
-size_t bind_index(int K, int q, int par, bool reverse) { return ((size_t)(reverse ? 2 : 0) + par) * K + q; }
 
 // The reverse sweep proper (no caller memory: captured into a graph):
 // zero the adjoints, re-run each segment from its checkpoint keeping every
 // step's state, reverse its steps, and return to the rollout's final state.
 mc_status sweep(mc_world* w, mc::AdjDev a, const mc::AdjMdf* mdf, float* const adjG[2], char* obs_keep, char* seg,
-                const StateSlot& sl, int n_ck, const mc::WorldDev* bind_h, mc::WorldDev* bind_d, cudaStream_t s) {
+                const StateSlot& sl, int n_ck, const mc::WorldDev* bind_h, mc::WorldDev* bind_d, bool stored,
+                cudaStream_t s) {
   const mc::WorldDev& h = w->h;
   const size_t HW = (size_t)h.H * h.W;
   const int K = w->tape_every, n = w->tape_steps;
@@ -362,14 +452,17 @@ mc_status sweep(mc_world* w, mc::AdjDev a, const mc::AdjMdf* mdf, float* const a
   for (int k = n_ck - 1; k >= 0; --k) {
     const int steps = std::min(K, n - k * K);
     const int64_t tk = t0 + (int64_t)k * K;
-    mc_status st = load_state(h, (int)(tk & 1), tape + (size_t)k * sl.bytes, sl, s);
-    if (st != MC_OK) return st;
-    mc::launch_set_counter(h, tk, s);
-    st = save_state(h, (int)(tk & 1), seg, sl, s);   // the segment's first state
-    if (st != MC_OK) return st;
+    if (!stored) {
+      mc_status st = load_state(h, (int)(tk & 1), tape + (size_t)k * sl.bytes, sl, s);
+      if (st != MC_OK) return st;
+      mc::launch_set_counter(h, tk, s);
+      st = save_state(h, (int)(tk & 1), seg, sl, s);   // the segment's first state
+      if (st != MC_OK) return st;
+    }
     // the segment's forward, keeping every step's state and intermediates
-    // (the unfused stages: the same step bitwise, with rho_bar and u in memory)
-    for (int q = 0; q < steps; ++q) {
+    // (the unfused stages: the same step bitwise, with rho_bar and u in
+    // memory); a stored rollout has them all already
+    for (int q = 0; q < steps && !stored; ++q) {
       if (mdf) {
         // direct forcing: F = S[F_s], then the density fields (a re-run
         // that leaves F), the MDF passes keeping their input velocities
@@ -386,14 +479,7 @@ mc_status sweep(mc_world* w, mc::AdjDev a, const mc::AdjMdf* mdf, float* const a
         k_seg_save<<<grid, 256, 0, s>>>(wd, seg + (size_t)q * ss.bytes, next, (int)((tk + q + 1) & 1), ss);
       } else {
         // the step's fields go straight into its record (bind_step)
-        const mc::Plan p = step_plan(q, (int)((tk + q) & 1), false);
-        mc::launch_pbd(p, s);
-        mc::launch_bin_scan(p, s);
-        mc::launch_bin_scatter(p, s);
-        mc::launch_deposit_x(p, s, 0);
-        mc::launch_force_spread(p, s, 1, 0);
-        mc::launch_lbm(p, s);
-        mc::launch_interp_advance(p, s);
+        run_recorded_step(step_plan(q, (int)((tk + q) & 1), false), s);
       }
     }
     MC_ACUDA(cudaGetLastError());
@@ -490,8 +576,9 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
   const size_t o_mxtb = take(df ? h.N * sizeof(float2) : 0);
   const size_t o_must = take(df ? h.N * sizeof(float2) : 0);
   const size_t o_mbnd = take(df ? 8 * sizeof(unsigned) : 0);
+  const bool stored = w->tape_stored;
   const size_t o_bind = take(df ? 0 : 4 * (size_t)K * sizeof(mc::WorldDev));
-  const size_t o_seg = take((size_t)K * step_slot(h).bytes);
+  const size_t o_seg = take(stored ? 0 : (size_t)K * step_slot(h).bytes);
   if (w->adj_bytes < off) {
     if (w->adj) cudaFreeAsync(w->adj, w->stream);
     w->adj = nullptr;
@@ -502,7 +589,7 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
   }
   char* A = static_cast<char*>(w->adj);
   char* tape = static_cast<char*>(w->tape);
-  char* seg = A + o_seg;
+  char* seg = stored ? tape + stored_layout(h, n).steps : A + o_seg;
   mc::AdjDev a{};
   a.adjX = reinterpret_cast<float2*>(A + o_adjX);
   a.adjTh = reinterpret_cast<float*>(A + o_adjTh);
@@ -543,7 +630,7 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
   MC_ACUDA(cudaGetLastError());
   // the reverse sweep, captured once per (rollout length, checkpoint spacing,
   // start step, buffers) and replayed
-  const BwdKey key{n, K, w->tape_t0, w->tape, w->adj};
+  const BwdKey key{n, K, w->tape_t0, w->tape, w->adj, stored};
   if (!w->bwd_exec || !(key == w->bwd_key)) {
     if (w->bwd_exec) cudaGraphExecDestroy(w->bwd_exec);
     w->bwd_exec = nullptr;
@@ -562,7 +649,8 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
     }
     cudaStream_t cs = adj_capture_stream();
     MC_ACUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    const mc_status st = sweep(w, a, df ? &m : nullptr, adjG, A + o_obs, seg, sl, n_ck, bind_h.data(), bind_d, cs);
+    const mc_status st =
+        sweep(w, a, df ? &m : nullptr, adjG, A + o_obs, seg, sl, n_ck, bind_h.data(), bind_d, stored, cs);
     cudaGraph_t g = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(cs, &g);
     if (st != MC_OK) {

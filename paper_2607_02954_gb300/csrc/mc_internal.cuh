@@ -514,7 +514,10 @@ struct BwdKey {
   int64_t t0 = -1;
   void* tape = nullptr;
   void* adj = nullptr;
-  bool operator==(const BwdKey& o) const { return n == o.n && K == o.K && t0 == o.t0 && tape == o.tape && adj == o.adj; }
+  bool stored = false;
+  bool operator==(const BwdKey& o) const {
+    return n == o.n && K == o.K && t0 == o.t0 && tape == o.tape && adj == o.adj && stored == o.stored;
+  }
 };
 
 struct mc_world {
@@ -532,6 +535,7 @@ struct mc_world {
   size_t tape_bytes = 0;
   int tape_steps = 0, tape_every = 0;
   int64_t tape_t0 = 0;
+  bool tape_stored = false;       // the tape holds every step's record (mc_rollout_forward_stored)
   void* adj = nullptr;            // adjoint buffers + per-segment step tape
   size_t adj_bytes = 0;
   cudaGraphExec_t bwd_exec = nullptr;   // captured reverse sweep

@@ -185,8 +185,14 @@ class World:
         return out
 
     # -- reverse mode ---------------------------------------------------------
-    def rollout_forward(self, n_steps: int, ckpt_every: int = 100, stream=None):
-        L.check(self._lib.mc_rollout_forward(self.handle, int(n_steps), int(ckpt_every), stream_handle(stream)))
+    def rollout_forward(self, n_steps: int, ckpt_every: int = 100, stream=None, stored: bool = False):
+        """Advance n_steps recording the rollout for the reverse mode: a
+        checkpoint every ckpt_every steps (the backward re-runs each segment),
+        or with stored=True every step's record (the backward re-runs none)."""
+        if stored:
+            L.check(self._lib.mc_rollout_forward_stored(self.handle, int(n_steps), stream_handle(stream)))
+        else:
+            L.check(self._lib.mc_rollout_forward(self.handle, int(n_steps), int(ckpt_every), stream_handle(stream)))
 
     def rollout_rewind(self, stream=None):
         """Back to the start of the last recorded rollout (see mc_rollout_rewind)."""

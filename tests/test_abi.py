@@ -112,6 +112,8 @@ def test_step_rejects_null_world():
     lib = L.load()
     assert lib.mc_step(None, 1, None) == 1
     assert lib.mc_step_batched(None, 1, 1, None) == 1
+    assert lib.mc_rollout_forward(None, 4, 2, None) == 1
+    assert lib.mc_rollout_forward_stored(None, 4, None) == 1
 
 
 def test_fault_injection_and_cancel_validate_arguments():

@@ -339,3 +339,53 @@ def test_reverse_mode_is_bitwise_repeatable(ib):
     assert np.array_equal(outs[0][0], outs[1][0])
     for k in outs[0][1]:
         assert np.array_equal(outs[0][1][k], outs[1][1][k]), k
+
+
+@pytest.mark.parametrize("case", ["tiny", "red_black", "two_layer"])
+def test_stored_rollout_gives_the_checkpointed_gradient_bitwise(case):
+    """mc_rollout_forward_stored keeps every step's record, so the backward
+    re-runs nothing: the same final state as plain steps, and gradients
+    bitwise equal to the checkpoint-and-recompute sweep's (the same
+    intermediates reach the same adjoint kernels), also after a rewind."""
+    from paper_2607_02954_gb300 import World
+    rng = np.random.default_rng(21)
+    spec = synth.world_random(17, 64, 5)
+    params = dict(nu=0.3, kappa=0.2, k_bend=0.7, k_stretch=0.6, k_shear=0.5, k_rep=1.0, sigma=0.8, orient=1.0,
+                  n_pbd=3)
+    if case == "red_black":
+        params["pbd_order"] = 1
+    elif case == "two_layer":
+        params.update(layers=2, layer_half=0.6)
+    spec.params = synth.Params(**params)
+    n, K = 23, 6
+    gx = torch.as_tensor(rng.standard_normal(spec.N), dtype=torch.float32).cuda()
+    gy = torch.as_tensor(rng.standard_normal(spec.N), dtype=torch.float32).cuda()
+    ref = World(spec)
+    ref.rollout_forward(n, K)
+    g_ck = {k: t2n(v).copy() for k, v in ref.rollout_backward_params(gx, gy).items()}
+    state_ck = ref.state(fluid=True)
+    ref.close()
+    w = World(spec)
+    for rep in range(2):
+        if rep:
+            w.rollout_rewind()
+        w.rollout_forward(n, stored=True)
+        g = {k: t2n(v).copy() for k, v in w.rollout_backward_params(gx, gy).items()}
+        for k in g_ck:
+            assert np.array_equal(g[k], g_ck[k]), (rep, k)
+        st = w.state(fluid=True)
+        for k in state_ck:
+            assert np.array_equal(st[k], state_ck[k]), (rep, k)
+    w.close()
+
+
+def test_stored_rollout_refuses_direct_forcing():
+    from paper_2607_02954_gb300 import World
+    from paper_2607_02954_gb300._lib import MCError
+    spec = synth.tiny_world(7, side=32, lengths=(8, 6))
+    spec.params = synth.Params(ib=1, mdf_iters=2)
+    w = World(spec)
+    with pytest.raises(MCError) as ei:
+        w.rollout_forward(5, stored=True)
+    assert ei.value.status == 1
+    w.close()
