@@ -106,7 +106,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--workload", default="c3_22",
-                    help="c3_<log2 N> (default c3_22), c2, c4 (1024 worlds: batched vs per-world launches), "
+                    help="c3_<log2 N> (default c3_22), c1, c2, dense_<log2 N> (2^N beads on 256^2), "
+                         "c4 (1024 worlds: batched vs per-world launches), "
                          "served (C4 worlds as Poisson-arriving 500-step rollouts) or c5 (folding gradient: "
                          "2000-step checkpointed rollout + loss + reverse sweep)")
     ap.add_argument("--pbd-order", type=int, default=0, choices=[0, 1],
@@ -147,6 +148,8 @@ def make_spec(name: str, seed: int, pbd_order: int = 0, observe: bool = False, m
 
 def _make_spec(name: str, seed: int):
     from paper_2607_02954_gb300 import synth
+    if name == "c1":
+        return synth.world_c1(seed), "c1: 128^2 grid, 16 x 32 beads, FP32"
     if name == "c2":
         return synth.world_c2(seed), "c2: 512^2 grid, 4096 x 64 beads (262,144), FP32"
     if name.startswith("c3_"):
