@@ -271,26 +271,29 @@ __global__ void __launch_bounds__(256) k_adj_bead_a(const WorldDev* __restrict__
 }
 
 // ---------------------------------------------------------------------------
-// a6 gradient transposed and a5 transposed, one 32x32 tile per block:
+// a6 gradient transposed and a5 transposed, one 32 x 8 strip per block:
 //   rho_bar_bar = -k_rep D^T Q with D the central difference,
 //     (D^T v)(c) = (v_x(c - e_x) - v_x(c + e_x) + v_y(c - e_y) - v_y(c + e_y))/2,
 //   then the periodic separable filter (symmetric), x pass then y pass.
-// rho_bar_bar is formed on the tile plus R cells a side from Q staged with
-// one more cell, the x pass on the tile's columns over those rows, the y
-// pass on the tile; the sums run in the same order as cell-wise passes over
+// rho_bar_bar is formed on the strip plus R cells a side from Q staged with
+// one more cell, the x pass on the strip's columns over those rows, the y
+// pass on the strip; the sums run in the same order as cell-wise passes over
 // the whole grid, so the result does not depend on the tiling.
 // ---------------------------------------------------------------------------
+constexpr int kBlurRows = 8;   // rows of a block's strip (32 columns): more, smaller blocks for small grids
+
 __global__ void __launch_bounds__(256) k_adj_rho_blur(const WorldDev* __restrict__ wd, AdjDev a) {
-  constexpr int kE = kTile + 2 * kMaxR;   // row and column capacity of the rho_bar_bar region
-  constexpr int kQ = kE + 2;              // Q window capacity
-  __shared__ float2 q[kQ * kQ];
-  __shared__ float rb[kE * kE];
-  __shared__ float tm[kE * kTile];
+  constexpr int kE = kTile + 2 * kMaxR;        // column capacity of the rho_bar_bar region
+  constexpr int kER = kBlurRows + 2 * kMaxR;   // row capacity
+  constexpr int kQ = kE + 2;                   // Q window capacity
+  __shared__ float2 q[(kER + 2) * kQ];
+  __shared__ float rb[kER * kE];
+  __shared__ float tm[kER * kTile];
   const WorldDev& w = *wd;
   const int W = w.W, H = w.H, R = w.R;
   const int ntx = (W + kTile - 1) / kTile;
-  const int x0 = (int)(blockIdx.x % ntx) * kTile, y0 = (int)(blockIdx.x / ntx) * kTile;
-  const int tw = min(kTile, W - x0), th = min(kTile, H - y0);
+  const int x0 = (int)(blockIdx.x % ntx) * kTile, y0 = (int)(blockIdx.x / ntx) * kBlurRows;
+  const int tw = min(kTile, W - x0), th = min(kBlurRows, H - y0);
   const int ew = tw + 2 * R, eh = th + 2 * R;   // region: rows y0 - R .., columns x0 - R ..
   const int qw = ew + 2, qh = eh + 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -430,27 +433,31 @@ __device__ __forceinline__ void adj_edge_reverse(float x, float y, float L, floa
                                                  float thb, float hs, float ksh, float ko, float orient,
                                                  float& xbx, float& xby, float& thb_new, float& hsb, float& kshb,
                                                  float& gL) {
-  const float ell = sqrtf(x * x + y * y);
-  const float sc = (ell - L) / ell;
+  // (hardware reciprocal square root, reciprocal and reduced-angle
+  // sine/cosine: the adjoint needs relative accuracy far below its 1e-3
+  // budget, not the forward's bits)
+  const float r = rsqrtf(x * x + y * y);   // 1 / |x|
+  const float iL = __frcp_rn(L);
+  const float sc = fmaf(-L, r, 1.0f);      // (|x| - L) / |x|
   float sn, cs;
-  sincosf(tb, &sn, &cs);
+  __sincosf(fmaf(-6.28318548f, rintf(tb * 0.159154943f), tb), &sn, &cs);
   // D = hs [(1 - ksh) sc x + ksh x - ksh L d]
   const float xd = x * Dbx + y * Dby;
-  const float kq = hs * (1.0f - ksh) * (L / (ell * ell * ell)) * xd;
+  const float kq = hs * (1.0f - ksh) * (L * r * r * r) * xd;
   xbx = hs * ((1.0f - ksh) * sc + ksh) * Dbx + kq * x;
   xby = hs * ((1.0f - ksh) * sc + ksh) * Dby + kq * y;
   thb_new = thb + (-hs * ksh * L) * (-sn * Dbx + cs * Dby);
   // theta += ko (cs y - sn x) / L
-  const float turn = (cs * y - sn * x) / L;
-  thb_new += thb * ko * (-sn * y - cs * x) / L;
-  xbx += thb * ko * (-sn) / L;
-  xby += thb * ko * cs / L;
+  const float turn = (cs * y - sn * x) * iL;
+  thb_new += thb * ko * (-sn * y - cs * x) * iL;
+  xbx += thb * ko * (-sn) * iL;
+  xby += thb * ko * cs * iL;
   // parameters: D = hs G, ko = orient hs ksh
   const float rx = x - L * cs - sc * x, ry = y - L * sn - sc * y;
   const float Gx = sc * x + ksh * rx, Gy = sc * y + ksh * ry;
   hsb += Gx * Dbx + Gy * Dby + thb * orient * ksh * turn;
   kshb += hs * (rx * Dbx + ry * Dby) + thb * orient * hs * turn;
-  gL += hs * (-(1.0f - ksh) * xd / ell - ksh * (cs * Dbx + sn * Dby)) - thb * ko * turn / L;
+  gL += hs * (-(1.0f - ksh) * xd * r - ksh * (cs * Dbx + sn * Dby)) - thb * ko * turn * iL;
 }
 
 template <bool kRB>
@@ -697,35 +704,13 @@ __global__ void __launch_bounds__(kAdjPbdThreads) k_adj_pbd(const WorldDev* __re
   }
   for (int it = n_pbd - 1; !kRB && it >= 0; --it) {
     const float* tp = tape + it * kTape * maxB;
-    // position pass reverse: D_bar_e = d_bar_e - d_bar_{e+1}
+    // position pass reverse: D_bar_e = d_bar_e - d_bar_{e+1}, from theta
+    // after the bend pass and the corrections before this pass
     for (int e = tid; e < nE; e += kAdjPbdThreads) {
-      const float Dbx = dx[e] - dx[e + 1], Dby = dy[e] - dy[e + 1];
-      const float thb = th[e];          // adjoint of theta after this pass
-      const float tb = tp[maxB + e];    // forward theta before this pass (after bend)
-      const float x = vx[e] + (tp[2 * maxB + e + 1] - tp[2 * maxB + e]);
-      const float y = vy[e] + (tp[3 * maxB + e + 1] - tp[3 * maxB + e]);
-      const float L = Lr[e];
-      const float ell = sqrtf(x * x + y * y);
-      const float sc = (ell - L) / ell;
-      float sn, cs;
-      sincosf(tb, &sn, &cs);
-      // D = hs [(1 - ksh) sc x + ksh x - ksh L d]
-      const float xd = x * Dbx + y * Dby;
-      const float kq = hs * (1.0f - ksh) * (L / (ell * ell * ell)) * xd;
-      float xbx = hs * ((1.0f - ksh) * sc + ksh) * Dbx + kq * x;
-      float xby = hs * ((1.0f - ksh) * sc + ksh) * Dby + kq * y;
-      float thb_new = thb + (-hs * ksh * L) * (-sn * Dbx + cs * Dby);
-      // theta += ko (cs y - sn x) / L
-      const float turn = (cs * y - sn * x) / L;
-      thb_new += thb * ko * (-sn * y - cs * x) / L;
-      xbx += thb * ko * (-sn) / L;
-      xby += thb * ko * cs / L;
-      // parameters: D = hs G, ko = orient hs ksh
-      const float rx = x - L * cs - sc * x, ry = y - L * sn - sc * y;
-      const float Gx = sc * x + ksh * rx, Gy = sc * y + ksh * ry;
-      hsb += Gx * Dbx + Gy * Dby + thb * orient * ksh * turn;
-      kshb += hs * (rx * Dbx + ry * Dby) + thb * orient * hs * turn;
-      gLa[e] += hs * (-(1.0f - ksh) * xd / ell - ksh * (cs * Dbx + sn * Dby)) - thb * ko * turn / L;
+      float xbx, xby, thb_new;
+      adj_edge_reverse(vx[e] + (tp[2 * maxB + e + 1] - tp[2 * maxB + e]),
+                       vy[e] + (tp[3 * maxB + e + 1] - tp[3 * maxB + e]), Lr[e], tp[maxB + e], dx[e] - dx[e + 1],
+                       dy[e] - dy[e + 1], th[e], hs, ksh, ko, orient, xbx, xby, thb_new, hsb, kshb, gLa[e]);
       Dx[e] = xbx;
       Dy[e] = xby;
       th[e] = thb_new;
@@ -890,6 +875,7 @@ static int blocks(int n) { return (n + 255) / 256; }
 // then spread over several times more SMs
 constexpr int kAdjBeadThreads = 64;
 static int bead_blocks(int n) { return (n + kAdjBeadThreads - 1) / kAdjBeadThreads; }
+static int blur_blocks(const WorldDev& h) { return h.ntx * ((h.H + kBlurRows - 1) / kBlurRows); }
 
 // One reversed step.  Penalty coupling: a8, a7, a6/a4 gathers, a5, a6
 // gradient/a4, then a3/a1.  Direct forcing (m != NULL): a7, the MDF passes
@@ -916,14 +902,14 @@ void launch_adj_step(const Plan& p, const WorldDev& h, AdjDev a, const AdjMdf* m
     pbd(ap);
     launch_adj_mdf_moments(h, wd, a, *m, s);
     if (h.N) k_adj_bead_a<<<bead_blocks(h.N), kAdjBeadThreads, 0, s>>>(wd, a);
-    k_adj_rho_blur<<<h.ntx * h.nty, 256, 0, s>>>(wd, a);
+    k_adj_rho_blur<<<blur_blocks(h), 256, 0, s>>>(wd, a);
     if (h.N) k_adj_bead_b<<<bead_blocks(h.N), kAdjBeadThreads, 0, s>>>(wd, a);
     return;
   }
   if (h.N || a.setup) k_adj_spread_u<<<std::max(bead_blocks(h.N), 1), kAdjBeadThreads, 0, s>>>(wd, a);
   k_adj_lbm<<<blocks(HW), 256, 0, s>>>(wd, a, src_parity);
   if (h.N) k_adj_bead_a<<<bead_blocks(h.N), kAdjBeadThreads, 0, s>>>(wd, a);
-  k_adj_rho_blur<<<h.ntx * h.nty, 256, 0, s>>>(wd, a);
+  k_adj_rho_blur<<<blur_blocks(h), 256, 0, s>>>(wd, a);
   pbd(a);   // with a4 and the a6 gradient per bead (k_adj_bead_b's work) first
 }
 
