@@ -158,10 +158,22 @@ def _make_spec(name: str, seed: int):
         return synth.world_c3(n, seed), f"c3: 2^{n} beads as 64-bead filaments on {side}^2, FP32"
     if name.startswith("dense_"):
         n = int(name.split("_")[1])
-        return (synth.world_dense(256, 2 ** n, seed),
+        return (dense_spec(n, seed),
                 f"dense: 2^{n} beads as 64-bead filaments on 256^2 ({2 ** n / 65536:g} per cell; the paper's "
-                "scalability shape), FP32")
+                "scalability shape; k_rep scaled by 0.25 / density), FP32")
     raise SystemExit(f"unknown workload {name}")
+
+
+def dense_spec(n: int, seed: int):
+    """2^n beads on 256^2 with the steric stiffness scaled by 0.25 / (beads
+    per cell), so a bead feels the steric force it feels at the sweep's
+    0.25 bead per cell (the default stiffness drives the flow past the
+    velocity watchdog at several beads per cell)."""
+    import dataclasses
+    from paper_2607_02954_gb300 import synth
+    spec = synth.world_dense(256, 2 ** n, seed)
+    spec.params = dataclasses.replace(spec.params, k_rep=spec.params.k_rep * 0.25 / (2 ** n / 65536.0))
+    return spec
 
 
 def sample_spec(name: str, seed: int, params=None):
@@ -170,7 +182,7 @@ def sample_spec(name: str, seed: int, params=None):
     from paper_2607_02954_gb300 import synth
     if name.startswith("dense_"):
         n = int(name.split("_")[1])
-        spec = synth.world_dense(256, 2 ** n, seed)
+        spec = dense_spec(n, seed)
         if params is not None:
             spec.params = params
         return spec, f"one oracle step of the full dense world (2^{n} beads on 256^2)"
