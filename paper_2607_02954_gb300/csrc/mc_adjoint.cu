@@ -1,17 +1,25 @@
 // Reverse mode through a rollout: forward with checkpoints, then the adjoint
-// sweep with per-segment recompute (checkpoint-and-recompute every K steps).
+// sweep with per-segment recompute (checkpoint-and-recompute every K steps),
+// or forward with every step's record kept and a sweep that re-runs nothing.
 //
 // mc_rollout_forward   advances the world n steps and stores its state (bead
 //                      positions, edge angles, populations) every K steps and
 //                      at the end.
+// mc_rollout_forward_stored
+//                      advances n steps writing each step's record (start
+//                      state and intermediates) in place.
 // mc_rollout_backward  given dL/d(final unwrapped positions), walks the
 //                      segments from last to first: re-runs the segment's
 //                      forward from its checkpoint keeping every step's
-//                      state and intermediates (F_el, F_s, rho_bar, u, F), then
-//                      for each step from last to first restores them and
-//                      applies the adjoint kernels.
-//                      Accumulates dL/dtheta0 and leaves the world in its
-//                      final state.
+//                      state and intermediates (F_el, F_s, rho_bar, u, F) in
+//                      the step's record, then reverses the steps from last
+//                      to first, each step's kernels reading its record.
+//                      Accumulates the parameter gradients and leaves the
+//                      world in its final state.
+// Penalty worlds bind each step's fields to its record through a per-step
+// world descriptor (bind_step); direct-forcing worlds copy them
+// (k_seg_save / k_seg_restore), since their passes alternate two velocity
+// buffers whose inputs the record keeps.
 #include <algorithm>
 #include <cstring>
 #include <string>
