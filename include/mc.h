@@ -385,11 +385,11 @@ mc_status mc_rollout_forward(mc_world* w, int n_steps, int ckpt_every, void* str
  * mode reads), so the next mc_rollout_backward reverses the steps without
  * re-running any of them: memory for compute.  The steps run the unfused
  * stages (the same results bitwise).  Device memory per step: 32 N + 4 E
- * + 56 H W bytes (+ 8 N with two layers), plus two state records.  For
- * worlds with the penalty coupling (ib = 0).  mc_rollout_rewind,
- * mc_world_set_rest and both backward calls work as after
- * mc_rollout_forward.  Errors: MC_ERR_INVALID_ARG (n_steps < 1, the step
- * counter would reach 2^24, ib = 1), MC_ERR_OOM, MC_ERR_CUDA. */
+ * + 56 H W bytes (+ 8 N with two layers; with direct forcing + 8 H W per MDF
+ * pass (at least one), 4 H W and 8 N), plus two state records.
+ * mc_rollout_rewind, mc_world_set_rest and both backward calls work as
+ * after mc_rollout_forward.  Errors: MC_ERR_INVALID_ARG (n_steps < 1, the
+ * step counter would reach 2^24), MC_ERR_OOM, MC_ERR_CUDA. */
 mc_status mc_rollout_forward_stored(mc_world* w, int n_steps, void* stream);
 
 /* Returns the world to the start of the last mc_rollout_forward (its first

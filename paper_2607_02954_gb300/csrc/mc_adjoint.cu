@@ -240,6 +240,31 @@ void run_recorded_step(const mc::Plan& p, cudaStream_t s) {
   mc::launch_interp_advance(p, s);
 }
 
+// One direct-forcing step in unfused stages, recorded: F = S[F_s], then the
+// density fields (a re-run that leaves F), the MDF passes keeping their
+// input velocities in record q, and afterwards the step's intermediates
+// copied into record q and, when q + 1 < steps, the next step's start
+// state into record q + 1 (populations of the next step's parity).
+mc_status mdf_recorded_step(mc_world* w, char* seg, const StepSlot& ss, int q, int steps, int64_t tk,
+                            cudaStream_t s) {
+  const mc::WorldDev& h = w->h;
+  mc::launch_mdf_bins(w->plan, s);
+  mc::launch_bin_scan(w->plan, s);
+  mc::launch_bin_scatter(w->plan, s);
+  mc::launch_deposit_x(w->plan, s, 0);
+  mc::launch_force_spread(w->plan, s, 0, 0);
+  mc::launch_force_spread(w->plan, s, 1, 0);
+  MC_ACUDA(mc::launch_mdf_recorded(w->plan, h, reinterpret_cast<float2*>(seg + (size_t)q * ss.bytes + ss.mu), s));
+  mc::launch_lbm(w->plan, s);
+  mc::launch_interp_advance(w->plan, s);
+  const size_t total = std::max((size_t)9 * h.H * h.W, (size_t)h.N);
+  const int grid = (int)std::min<size_t>((total + 255) / 256, 4096);
+  char* next = q + 1 < steps ? seg + (size_t)(q + 1) * ss.bytes : nullptr;
+  k_seg_save<<<grid, 256, 0, s>>>(w->plan.d_worlds, seg + (size_t)q * ss.bytes, next, (int)((tk + q + 1) & 1), ss);
+  MC_ACUDA(cudaGetLastError());
+  return MC_OK;
+}
+
 // X_bar of the final positions from the caller's gradient, and its largest
 // |dt X_bar| (slot 0 of amax, zeroed before: the first reversed step's u_bar
 // bound).
@@ -303,7 +328,6 @@ mc_status mc_rollout_forward_stored(mc_world* w, int n_steps, void* stream) {
   if (!w || n_steps < 1) return afail(MC_ERR_INVALID_ARG, "need a world and n_steps >= 1");
   if (w->t + n_steps >= (int64_t(1) << 24)) return afail(MC_ERR_INVALID_ARG, "step counter would reach 2^24");
   const mc::WorldDev& h = w->h;
-  if (h.ib != 0) return afail(MC_ERR_INVALID_ARG, "stored rollouts need the penalty coupling (ib = 0)");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t HW = (size_t)h.H * h.W;
   const StateSlot sl = state_slot(h);
@@ -329,6 +353,21 @@ mc_status mc_rollout_forward_stored(mc_world* w, int n_steps, void* stream) {
   MC_ACUDA(cudaMemcpyAsync(tape + tl.obs0, h.obs, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
   mc_status st = save_state(h, (int)(t0 & 1), tape, sl, s);   // the start (mc_rollout_rewind)
   if (st != MC_OK) return st;
+  if (h.ib == 1) {
+    // direct forcing: the world's own buffers step, each step's record is
+    // copied out after it (the same path as the sweep's recompute)
+    st = save_state(h, (int)(t0 & 1), seg, sl, s);   // step 0's start state
+    if (st != MC_OK) return st;
+    for (int q = 0; q < n_steps; ++q) {
+      st = mdf_recorded_step(w, seg, ss, q, n_steps, t0, s);
+      if (st != MC_OK) return st;
+    }
+    w->t += n_steps;
+    st = save_state(h, (int)(w->t & 1), tape + sl.bytes, sl, s);   // the final state
+    if (st != MC_OK) return st;
+    if (h.N) MC_ACUDA(cudaMemcpyAsync(tape + tl.disp_end, h.disp, h.N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+    return MC_OK;
+  }
   // step 0 reads its populations from its record
   MC_ACUDA(cudaMemcpyAsync(seg + ss.st.g, h.g[t0 & 1], 9 * HW * sizeof(float), cudaMemcpyDeviceToDevice, s));
   std::vector<mc::WorldDev> desc(n_steps);
@@ -472,19 +511,8 @@ mc_status sweep(mc_world* w, mc::AdjDev a, const mc::AdjMdf* mdf, float* const a
     // memory); a stored rollout has them all already
     for (int q = 0; q < steps && !stored; ++q) {
       if (mdf) {
-        // direct forcing: F = S[F_s], then the density fields (a re-run
-        // that leaves F), the MDF passes keeping their input velocities
-        mc::launch_mdf_bins(w->plan, s);
-        mc::launch_bin_scan(w->plan, s);
-        mc::launch_bin_scatter(w->plan, s);
-        mc::launch_deposit_x(w->plan, s, 0);
-        mc::launch_force_spread(w->plan, s, 0, 0);
-        mc::launch_force_spread(w->plan, s, 1, 0);
-        MC_ACUDA(mc::launch_mdf_recorded(w->plan, h, reinterpret_cast<float2*>(seg + (size_t)q * ss.bytes + ss.mu), s));
-        mc::launch_lbm(w->plan, s);
-        mc::launch_interp_advance(w->plan, s);
-        char* next = q + 1 < steps ? seg + (size_t)(q + 1) * ss.bytes : nullptr;
-        k_seg_save<<<grid, 256, 0, s>>>(wd, seg + (size_t)q * ss.bytes, next, (int)((tk + q + 1) & 1), ss);
+        mc_status st = mdf_recorded_step(w, seg, ss, q, steps, tk, s);
+        if (st != MC_OK) return st;
       } else {
         // the step's fields go straight into its record (bind_step)
         run_recorded_step(step_plan(q, (int)((tk + q) & 1), false), s);

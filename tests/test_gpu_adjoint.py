@@ -341,7 +341,7 @@ def test_reverse_mode_is_bitwise_repeatable(ib):
         assert np.array_equal(outs[0][1][k], outs[1][1][k]), k
 
 
-@pytest.mark.parametrize("case", ["tiny", "red_black", "two_layer"])
+@pytest.mark.parametrize("case", ["tiny", "red_black", "two_layer", "direct"])
 def test_stored_rollout_gives_the_checkpointed_gradient_bitwise(case):
     """mc_rollout_forward_stored keeps every step's record, so the backward
     re-runs nothing: the same final state as plain steps, and gradients
@@ -356,6 +356,8 @@ def test_stored_rollout_gives_the_checkpointed_gradient_bitwise(case):
         params["pbd_order"] = 1
     elif case == "two_layer":
         params.update(layers=2, layer_half=0.6)
+    elif case == "direct":
+        params.update(ib=1, mdf_iters=2)
     spec.params = synth.Params(**params)
     n, K = 23, 6
     gx = torch.as_tensor(rng.standard_normal(spec.N), dtype=torch.float32).cuda()
@@ -376,16 +378,4 @@ def test_stored_rollout_gives_the_checkpointed_gradient_bitwise(case):
         st = w.state(fluid=True)
         for k in state_ck:
             assert np.array_equal(st[k], state_ck[k]), (rep, k)
-    w.close()
-
-
-def test_stored_rollout_refuses_direct_forcing():
-    from paper_2607_02954_gb300 import World
-    from paper_2607_02954_gb300._lib import MCError
-    spec = synth.tiny_world(7, side=32, lengths=(8, 6))
-    spec.params = synth.Params(ib=1, mdf_iters=2)
-    w = World(spec)
-    with pytest.raises(MCError) as ei:
-        w.rollout_forward(5, stored=True)
-    assert ei.value.status == 1
     w.close()
