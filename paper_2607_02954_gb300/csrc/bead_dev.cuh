@@ -634,8 +634,7 @@ __device__ __forceinline__ void bin_scatter_body(const WorldDev* __restrict__ wo
   if (valid) {
     const int slot = base + __popc(peers & ((1u << lane) - 1u));
     w.spos[slot] = p;
-    w.sfel[slot] = fe;
-    w.sid[slot] = i;
+    w.srec[slot] = make_float4(fe.x, fe.y, __int_as_float(i), 0.0f);
     if (w.bead_slot) w.bead_slot[i] = slot;   // direct forcing: U_s goes to the bead's slot
   }
 }

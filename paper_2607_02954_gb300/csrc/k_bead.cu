@@ -46,9 +46,10 @@ __global__ void __launch_bounds__(kBeadChunk) k_layer_spread(const WorldDev* __r
   const int slot = it.y + threadIdx.x;
   if (slot >= w.N) return;
   const int W = w.W, H = w.H;
-  const int i = w.sid[slot];
+  const float4 rec = w.srec[slot];
+  const int i = __float_as_int(rec.z);
   const float4 p = w.spos[slot];
-  const float2 n = w.nrm[i], fe = w.sfel[slot], fs = w.fs[i];
+  const float2 n = w.nrm[i], fe = make_float2(rec.x, rec.y), fs = w.fs[i];
   const float hx = 0.5f * (fe.x + fs.x), hy = 0.5f * (fe.y + fs.y);
   for (int side = 0; side < 2; ++side) {
     int cx, cy;

@@ -259,7 +259,7 @@ __device__ __forceinline__ int mdf_stage_chunk(MdfSmem& sm, const WorldDev& w, c
     const int slot = seg_slot(c0 + v, sm.s_start, sm.s_pre);
     cp_async16(&sm.sp[v], &w.spos[slot]);
     cp_async8(&sm.su[v], &w.sus[slot]);
-    cp_async4(&sm.si[v], &w.sid[slot]);
+    cp_async4(&sm.si[v], reinterpret_cast<const int*>(&w.srec[slot]) + 2);   // the record's id
   }
   cp_async_wait_all();
   if (tid == 0) sm.s_cnt = 0;

@@ -343,8 +343,7 @@ size_t world_layout(WorldDev& h, void* A) {
   const size_t o_bcur = L.take<int>(h.n_bins);
   const size_t o_cs = L.take<int>(h.n_chunks);
   const size_t o_sp = L.take<float4>(N);
-  const size_t o_sf = L.take<float2>(N);
-  const size_t o_sid = L.take<int>(N);
+  const size_t o_sr = L.take<float4>(N);
   const size_t o_g0 = L.take<float>(9 * HW);
   const size_t o_g1 = L.take<float>(9 * HW);
   const size_t o_F = L.take<float2>(HW);
@@ -384,8 +383,7 @@ size_t world_layout(WorldDev& h, void* A) {
   h.bin_cursor = at<int>(A, o_bcur);
   h.chunk_sum = at<int>(A, o_cs);
   h.spos = at<float4>(A, o_sp);
-  h.sfel = at<float2>(A, o_sf);
-  h.sid = at<int>(A, o_sid);
+  h.srec = at<float4>(A, o_sr);
   h.g[0] = at<float>(A, o_g0);
   h.g[1] = at<float>(A, o_g1);
   h.F = at<float2>(A, o_F);
@@ -983,7 +981,12 @@ mc_status mc_world_get_field(const mc_world* w, int field, void* out, int mem_ki
     case MC_FIELD_U: src = h.u; bytes = HW * sizeof(float2); break;
     case MC_FIELD_BIN: src = h.bead_bin; bytes = h.N * sizeof(int); break;
     case MC_FIELD_BIN_OFF: src = h.bin_off; bytes = (h.n_bins + 1) * sizeof(int); break;
-    case MC_FIELD_BIN_BEADS: src = h.sid; bytes = h.N * sizeof(int); break;
+    case MC_FIELD_BIN_BEADS:   // the id word of each bin-ordered record
+      if (h.N)
+        MC_CUDA(cudaMemcpy2DAsync(out, sizeof(int), reinterpret_cast<const char*>(h.srec) + 2 * sizeof(float),
+                                  sizeof(float4), sizeof(int), h.N, dk, s));
+      if (host) MC_CUDA(cudaStreamSynchronize(s));
+      return MC_OK;
     case MC_FIELD_EBEAD:
       if (!h.ebead) return fail(MC_ERR_INVALID_ARG, "the world has no energy field");
       src = h.ebead;
@@ -1031,7 +1034,9 @@ mc_status mc_world_check(const mc_world* w, void* stream) {
   MC_CUDA(cudaMemcpyAsync(&flags, w->h.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   MC_CUDA(cudaStreamSynchronize(s));
   if (flags & mc::kFlagTimeout)
-    return fail(MC_ERR_TIMEOUT, "a grid barrier of the persistent batched step ran out of time; the world's state is unspecified");
+    return fail(MC_ERR_TIMEOUT,
+                "a grid barrier of the persistent step or a wait for bulk copies ran out of time; the world's state is "
+                "unspecified");
   if (flags & mc::kFlagUnstable) return fail(MC_ERR_UNSTABLE, "bead velocity watchdog tripped (|U| > 0.5 or not finite)");
   return MC_OK;
 }

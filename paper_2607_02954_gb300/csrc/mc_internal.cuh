@@ -31,7 +31,7 @@ constexpr int kMaxNpbd = 64;
 
 enum : unsigned {
   kFlagUnstable = 1u,   // the velocity watchdog tripped
-  kFlagTimeout = 2u     // a grid barrier of the persistent batched step ran out of time
+  kFlagTimeout = 2u     // a grid barrier of the persistent step, or a wait for bulk copies, ran out of time
 };
 
 // Everything the kernels need to know about one world.  Lives in device
@@ -62,8 +62,7 @@ struct WorldDev {
   int* bin_cursor;        // [n_bins]
   int* chunk_sum;         // [n_chunks]
   float4* spos;           // [N] positions in bin order
-  float2* sfel;           // [N] elastic forces in bin order
-  int* sid;               // [N] bead ids in bin order
+  float4* srec;           // [N] per bead in bin order: F_el (x, y), bead id (int bits), 0
   float* g[2];            // [9 * H * W] post-collision population deviations (ping-pong)
   float2* F;              // [H * W]
   float2* u;              // [H * W]

@@ -42,6 +42,46 @@ __device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Bulk copies into shared memory completing on an mbarrier (the tile's bead
+// records: each bin segment is contiguous in global and in shared memory).
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+// (before the barrier's memory is re-initialised or used for anything else)
+__device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+// Copies `bytes` (a multiple of 16; both addresses 16-byte aligned).
+__device__ __forceinline__ void bulk_copy_g2s(void* sdst, const void* gsrc, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+               ::"r"(smem_addr(sdst)), "l"(gsrc), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(ok)
+               : "r"(smem_addr(bar)), "r"(parity)
+               : "memory");
+  return ok != 0;
+}
+// Waits for phase `parity` of the barrier, for at most ~2^22 polls (each
+// try_wait itself suspends for a while); a wait that runs out flags the
+// world (kFlagTimeout), waits once more as long, and returns.
+__device__ __forceinline__ void mbar_wait_bounded(unsigned long long* bar, unsigned parity, unsigned* flags) {
+  for (int round = 0; round < 2; ++round) {
+    for (int it = 0; it < (1 << 22); ++it)
+      if (mbar_try_wait(bar, parity)) return;
+    if (round == 0 && flags) atomicOr(flags, kFlagTimeout);
+  }
+}
+
 __device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((b - 1 - a) / b); }
 
 // Bead segments of the bins whose cells reach the cell box
@@ -444,9 +484,9 @@ __device__ __forceinline__ void deposit_x_body(const WorldDev* __restrict__ worl
 template <int R>
 struct TileIn {
   float xb[Geo<R>::kLoadRows * kWin];   // rho_x window
-  float4 sp[kForceCap];                 // bead records of the first chunk
-  float2 sf[kForceCap];
-  int si[kForceCap];
+  float4 sp[kForceCap];                 // bead positions of the chunk (bin order)
+  float4 sr[kForceCap];                 // their F_el (x, y) and bead id (int bits)
+  unsigned long long bar;               // completion of the chunk's bulk copies
   int s_start[kMaxSeg], s_pre[kMaxSeg + 1];
   float nbmax[9];                       // largest rho_s of the 3x3 tiles around
   float tap_s[Geo<R>::kTaps];
@@ -554,19 +594,28 @@ __device__ __forceinline__ void tile_stage_meta(TileIn<R>& in, const WorldDev& w
   }
 }
 
-// Stage 3 (after stage 2 is visible to the block): cp.async of the bead
-// records of the first chunk.
-template <int R, int NT = kThreads>
-__device__ __forceinline__ void tile_stage_records(TileIn<R>& in, const WorldDev& w) {
-  const int n0 = min(kForceCap, in.s_pre[kMaxSeg]);
-  const float4* __restrict__ spos = w.spos;
-  const float2* __restrict__ sfel = w.sfel;
-  const int* __restrict__ sid = w.sid;
-  for (int v = threadIdx.x; v < n0; v += NT) {
-    const int slot = seg_slot(v, in.s_start, in.s_pre);
-    cp_async16(&in.sp[v], &spos[slot]);
-    cp_async8(&in.sf[v], &sfel[slot]);
-    cp_async4(&in.si[v], &sid[slot]);
+// Stage 3 (after stage 2 is visible to the block): the bead records c0 ..
+// c0 + n - 1 (n > 0, in segment order) as bulk copies, one lane of warp 0
+// per segment (a bin segment is contiguous in the bin-ordered arrays and in
+// the staging arrays), after lane 0 has announced the bytes on in.bar; the
+// block then waits on in.bar.  Positions and (F_el, id) records are 16 bytes
+// each, so every copy starts and ends on 16-byte boundaries.
+static_assert(kMaxSeg == 32, "one lane of a warp per segment");
+template <int R>
+__device__ __forceinline__ void tile_stage_records(TileIn<R>& in, const WorldDev& w, int c0, int n) {
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  if (lane == 0) {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    mbar_expect_tx(&in.bar, (unsigned)n * 32u);
+  }
+  __syncwarp();
+  const int lo = max(in.s_pre[lane], c0), hi = min(in.s_pre[lane + 1], c0 + n);
+  if (hi > lo) {
+    const int src = in.s_start[lane] + (lo - in.s_pre[lane]);
+    const unsigned bytes = (unsigned)(hi - lo) * 16u;
+    bulk_copy_g2s(&in.sp[lo - c0], &w.spos[src], bytes, &in.bar);
+    bulk_copy_g2s(&in.sr[lo - c0], &w.srec[src], bytes, &in.bar);
   }
 }
 
@@ -591,8 +640,6 @@ __device__ __forceinline__ int tile_compute(TileIn<R>& in, TileWork& wk, const W
   using G = Geo<R>;
   const int W = w.W, H = w.H, ntx = w.ntx, nty = w.nty;
   const float4* __restrict__ spos = w.spos;
-  const float2* __restrict__ sfel = w.sfel;
-  const int* __restrict__ sid = w.sid;
   float2* __restrict__ fs_out = w.fs;
   float* __restrict__ rho_b = w.rho_b;
   const float k_rep = w.k_rep;
@@ -667,9 +714,10 @@ __device__ __forceinline__ int tile_compute(TileIn<R>& in, TileWork& wk, const W
         gsy = fmaf(wy[b], sy, gsy);
       }
       const float Fsx = -0.5f * k_rep * gsx, Fsy = -0.5f * k_rep * gsy;
-      if (rx >= 0 && rx < tw && ry >= 0 && ry < th) fs_out[in.si[v]] = make_float2(Fsx, Fsy);
+      const float4 rec = in.sr[v];
+      if (rx >= 0 && rx < tw && ry >= 0 && ry < th) fs_out[__float_as_int(rec.z)] = make_float2(Fsx, Fsy);
       if (layered) continue;   // two-layer worlds spread at their layer points (k_layer_spread)
-      const float2 fe = in.sf[v];
+      const float2 fe = make_float2(rec.x, rec.y);
       const float Fx = (fe.x + Fsx) * scale, Fy = (fe.y + Fsy) * scale;
       float ax[4], ay[4];
 #pragma unroll
@@ -693,13 +741,8 @@ __device__ __forceinline__ int tile_compute(TileIn<R>& in, TileWork& wk, const W
     force_sync<NT>();   // every thread is done with this chunk
     if (tid == 0) wk.s_cnt = 0;
     const int n = min(kForceCap, total - c0);
-    for (int v = tid; v < n; v += NT) {
-      const int slot = seg_slot(c0 + v, in.s_start, in.s_pre);
-      cp_async16(&in.sp[v], &spos[slot]);
-      cp_async8(&in.sf[v], &sfel[slot]);
-      cp_async4(&in.si[v], &sid[slot]);
-    }
-    cp_async_wait_all();
+    tile_stage_records(in, w, c0, n);
+    mbar_wait_bounded(&in.bar, (unsigned)(c0 / kForceCap) & 1u, w.flags);
     force_sync<NT>();
     force_compact<R, NT>(in, wk, n, tb, W, H, ntx, nty);
     force_sync<NT>();
@@ -714,11 +757,18 @@ __device__ __forceinline__ int force_tile(ForceSmem<R>& sm, const WorldDev& w, i
   tile_stage_window<R, NT>(sm.in, w, tb);
   tile_stage_meta(sm.in, w, tb);
   tile_clear<NT>(sm.wk);
+  if (threadIdx.x == 0) mbar_init(&sm.in.bar);
   force_sync<NT>();
-  tile_stage_records<R, NT>(sm.in, w);
-  cp_async_wait_all();
+  const int n0 = min(kForceCap, sm.in.s_pre[kMaxSeg]);
+  if (n0 > 0) tile_stage_records(sm.in, w, 0, n0);
+  cp_async_wait_all();   // the window (cp.async)
+  if (n0 > 0) mbar_wait_bounded(&sm.in.bar, 0u, w.flags);
   force_sync<NT>();
-  return tile_compute<R, NT>(sm.in, sm.wk, w, tile, tb, store_fields, after_step);
+  const int k = tile_compute<R, NT>(sm.in, sm.wk, w, tile, tb, store_fields, after_step);
+  // every thread is past its last wait on the barrier (tile_compute
+  // synchronises after each chunk's wait), so its memory can be released
+  if (threadIdx.x == 0) mbar_inval(&sm.in.bar);
+  return k;
 }
 
 // Folds the stencil cells that wrapped around an axis the tile covers whole
