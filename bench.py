@@ -728,6 +728,9 @@ def main():
     }
     if mdf:
         line["step_roofline"]["note"] = "penalty-step bytes: a lower bound of the direct-forcing step's traffic"
+    elif line["roofline"]["traffic"]:
+        # the ncu-counted DRAM bytes of one launch over the same live launch time
+        line["roofline"]["achieved_dram"] = line["roofline"]["traffic"] / (stage_ms["force_lbm"] * 1e-3) / 1e9
     if not args.no_extras and ws == 1:
         # the batched and served workloads (1024 uneven worlds), summarised
         # beside the headline; each is its own line with --workload c4 / served
