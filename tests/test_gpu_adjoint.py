@@ -164,12 +164,13 @@ def test_folding_loss_and_gradient_against_finite_differences(n):
         assert abs(ad - fd) <= RTOL * max(abs(fd), 1e-3 * np.linalg.norm(g)), (ad, fd)
 
 
-def test_rollout_fn_autograd_bridge():
+@pytest.mark.parametrize("stored", [False, True])
+def test_rollout_fn_autograd_bridge(stored):
     from paper_2607_02954_gb300 import World
     from paper_2607_02954_gb300.autograd import rollout_displacement
     spec = synth.tiny_world(6, side=32, lengths=(8, 8))
     th0 = torch.tensor(spec.theta0, device="cuda", requires_grad=True)
-    disp = rollout_displacement(th0, spec, 15, 4)
+    disp = rollout_displacement(th0, spec, 15, 4, stored=stored)
     c = torch.linspace(-1, 1, disp.numel(), device="cuda").reshape(disp.shape)
     (disp * c).sum().backward()
     w = World(spec)
