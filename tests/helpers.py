@@ -22,9 +22,21 @@ def max_err(got, want):
 
 
 def assert_field(name, got, want, rtol, floor=1e-12):
-    """|got - want| <= rtol * max|want| + floor, element by element."""
+    """|got - want| <= rtol * max|want| + floor, element by element; and on
+    every entry of at least 1% of the field's scale, |got - want| <=
+    100 rtol |want| + floor (FP32 sums of terms up to the field's scale round
+    at about rtol of the scale, so an entry of 1% of it keeps 100 rtol of its
+    own value)."""
     err, scale = max_err(got, want)
     assert err <= rtol * scale + floor, f"{name}: max err {err:.3e} vs scale {scale:.3e} (rtol {rtol})"
+    g = np.asarray(got, np.float64).ravel()
+    w = np.asarray(want, np.float64).ravel()
+    big = np.abs(w) >= 0.01 * scale
+    if big.any():
+        rel = np.abs(g[big] - w[big]) - floor
+        bad = rel > 100 * rtol * np.abs(w[big])
+        assert not bad.any(), (f"{name}: {int(bad.sum())} entries above 1% of the scale off by more than "
+                               f"{100 * rtol:g} of their value (worst {np.max(rel / np.abs(w[big])):.3e})")
     return err, scale
 
 
