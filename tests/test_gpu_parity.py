@@ -266,6 +266,23 @@ def test_rollout_100_steps_c1():
     gw.close()
 
 
+def test_rollout_100_steps_c2():
+    """The C2 world (262,144 beads on 512^2, one bead per cell) after 100
+    steps: positions and displacements within 1e-4 cells of the FP64 oracle."""
+    spec = synth.world_c2(0)
+    st = O.rollout(O.World(spec), 100)
+    gw = _gpu_world(spec)
+    gw.step(100)
+    gw.check()
+    s = gw.state()
+    X = t2n(st.X)
+    err = max(np.max(np.abs(periodic_diff(s["x"], X[:, 0], spec.W))),
+              np.max(np.abs(periodic_diff(s["y"], X[:, 1], spec.H))))
+    assert err < 1e-4, err
+    assert np.max(np.abs(s["disp"] - t2n(st.D))) < 1e-4
+    gw.close()
+
+
 @pytest.mark.parametrize("seed", [0, 1])
 def test_rollout_1000_steps_c1(seed):
     """The C1 configuration at its full length: positions and displacements
