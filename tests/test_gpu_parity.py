@@ -266,6 +266,27 @@ def test_rollout_100_steps_c1():
     gw.close()
 
 
+@pytest.mark.parametrize("variant", ["red_black", "two_layer", "two_layer_red_black"])
+def test_rollout_100_steps_variants(variant):
+    """C1 worlds with the red-black PBD order and with two-layer filaments:
+    positions and displacements after 100 steps within 1e-4 cells."""
+    spec = synth.world_c1(3)
+    spec.params = {"red_black": synth.Params(pbd_order=1),
+                   "two_layer": synth.Params(layers=2, layer_half=0.8),
+                   "two_layer_red_black": synth.Params(layers=2, layer_half=1.2, pbd_order=1)}[variant]
+    st = O.rollout(O.World(spec), 100)
+    gw = _gpu_world(spec)
+    gw.step(100)
+    gw.check()
+    s = gw.state()
+    X = t2n(st.X)
+    err = max(np.max(np.abs(periodic_diff(s["x"], X[:, 0], spec.W))),
+              np.max(np.abs(periodic_diff(s["y"], X[:, 1], spec.H))))
+    assert err < 1e-4, err
+    assert np.max(np.abs(s["disp"] - t2n(st.D))) < 1e-4
+    gw.close()
+
+
 def test_rollout_100_steps_c2():
     """The C2 world (262,144 beads on 512^2, one bead per cell) after 100
     steps: positions and displacements within 1e-4 cells of the FP64 oracle."""
