@@ -37,10 +37,10 @@ __global__ void __launch_bounds__(256) k_adj_spread_u(const WorldDev* __restrict
   const WorldDev& w = *wd;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (a.setup && i == 0) {
-    // the step's counter, and the bounds this step's kernels produce: of Q
-    // (k_adj_lbm) and of the next reversed step's u_bar (k_adj_pbd; this
-    // step's u_bar reads slot a.par)
-    *w.t = a.t_step;
+    // the bounds this step's kernels produce: of Q (k_adj_lbm) and of the
+    // next reversed step's u_bar (k_adj_pbd; this step's u_bar reads slot
+    // a.par).  (The step's counter comes with a.t_step: the world's own
+    // counter belongs to a recompute that may run meanwhile.)
     a.amax[2] = 0u;
     a.amax[a.par ^ 1] = 0u;
   }
@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(kAdjPbdThreads) k_adj_pbd(const WorldDev* __re
   float* gLa = s + 11 * maxB;   // adjoint of L_rest, this step
   float* tape = s + 12 * maxB;  // per pass: theta before bend, theta after bend, d (x), d (y)
   const int W = w.W, H = w.H;
-  const long long t = *w.t;
+  const long long t = a.setup ? a.t_step : *w.t;
   const float4* __restrict__ P = a.xt ? a.xt : w.pos;   // the PBD's start: X~ with direct forcing
   for (int e = tid; e < nE; e += kAdjPbdThreads) {
     const float4 pa = P[b0 + e], pb = P[b0 + e + 1];

@@ -77,6 +77,14 @@ cudaStream_t adj_capture_stream() {
   return cs;
 }
 
+// The second stream of a captured sweep (segment re-runs), joined into the
+// capture by an event.
+cudaStream_t adj_rerun_stream() {
+  thread_local cudaStream_t cs = nullptr;
+  if (!cs) cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  return cs;
+}
+
 mc_status save_state(const mc::WorldDev& h, int parity, char* rec, const StateSlot& sl, cudaStream_t s) {
   const size_t HW = (size_t)h.H * h.W;
   if (h.N) MC_ACUDA(cudaMemcpyAsync(rec + sl.pos, h.pos, h.N * sizeof(float4), cudaMemcpyDeviceToDevice, s));
@@ -211,7 +219,9 @@ mc::WorldDev bind_step(const mc::WorldDev& h, char* seg, const StepSlot& ss, int
   return b;
 }
 
-size_t bind_index(int K, int q, int par, bool reverse) { return ((size_t)(reverse ? 2 : 0) + par) * K + q; }
+size_t bind_index(int K, int buf, int q, int par, bool reverse) {
+  return (((size_t)buf * 2 + (reverse ? 1 : 0)) * 2 + par) * K + q;
+}
 
 // A stored rollout's tape: the start and final state records and the tail
 // (tape_tail with one checkpoint), then one step record per step, then the
@@ -458,9 +468,23 @@ namespace {
 // The reverse sweep proper (no caller memory: captured into a graph):
 // zero the adjoints, re-run each segment from its checkpoint keeping every
 // step's state, reverse its steps, and return to the rollout's final state.
-mc_status sweep(mc_world* w, mc::AdjDev a, const mc::AdjMdf* mdf, float* const adjG[2], char* obs_keep, char* seg,
-                const StateSlot& sl, int n_ck, const mc::WorldDev* bind_h, mc::WorldDev* bind_d, bool stored,
-                cudaStream_t s) {
+// With a second stream and two segment buffers (penalty worlds recorded
+// with checkpoints), segment k - 1 is re-run on it into one buffer while
+// segment k is reversed from the other: the two chains of small kernels
+// overlap.  The re-run of segment k - 1 waits for the reverse of segment
+// k + 1 (which read the same buffer); the reverse of a segment waits for its
+// re-run.  The reversed steps read their step counter from AdjDev.t_step,
+// not from the world, whose counter the concurrent re-run advances.
+struct SweepSync {
+  cudaStream_t s2 = nullptr;                       // the re-run stream (nullptr: one stream, one buffer)
+  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaEvent_t rerun[2] = {nullptr, nullptr};       // a buffer's re-run done
+  cudaEvent_t reversed[2] = {nullptr, nullptr};    // a buffer's reverse done
+};
+
+mc_status sweep(mc_world* w, mc::AdjDev a, const mc::AdjMdf* mdf, float* const adjG[2], char* obs_keep,
+                char* const seg[2], const StateSlot& sl, int n_ck, const mc::WorldDev* bind_h, mc::WorldDev* bind_d,
+                bool stored, const SweepSync& sy, cudaStream_t s) {
   const mc::WorldDev& h = w->h;
   const size_t HW = (size_t)h.H * h.W;
   const int K = w->tape_every, n = w->tape_steps;
@@ -469,6 +493,8 @@ mc_status sweep(mc_world* w, mc::AdjDev a, const mc::AdjMdf* mdf, float* const a
   const mc::WorldDev* wd = w->plan.d_worlds;
   const size_t total = std::max((size_t)9 * HW, (size_t)h.N);
   const int grid = (int)std::min<size_t>((total + 255) / 256, 4096);
+  const bool overlap = sy.s2 != nullptr;
+  cudaStream_t rs = overlap ? sy.s2 : s;
   // the recompute passes accumulate the observables again: keep the rollout's values
   MC_ACUDA(cudaMemcpyAsync(obs_keep, h.obs, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
   if (h.E) MC_ACUDA(cudaMemsetAsync(a.adjTh, 0, h.E * sizeof(float), s));
@@ -479,9 +505,9 @@ mc_status sweep(mc_world* w, mc::AdjDev a, const mc::AdjMdf* mdf, float* const a
   MC_ACUDA(cudaMemsetAsync(a.ubar, 0, 2 * HW * sizeof(unsigned long long), s));
   MC_ACUDA(cudaMemsetAsync(a.Q, 0, 2 * HW * sizeof(unsigned long long), s));
   // a step's plan with the step's descriptor (penalty coupling)
-  auto step_plan = [&](int q, int par, bool reverse) {
+  auto step_plan = [&](int buf, int q, int par, bool reverse) {
     mc::Plan p = w->plan;
-    const size_t i = bind_index(K, q, par, reverse);
+    const size_t i = bind_index(K, buf, q, par, reverse);
     p.d_worlds = bind_d + i;
     p.h_world0 = bind_h[i];
     return p;
@@ -494,35 +520,41 @@ mc_status sweep(mc_world* w, mc::AdjDev a, const mc::AdjMdf* mdf, float* const a
     MC_ACUDA(cudaMemsetAsync(mdf->ss, 0, 2 * HW * sizeof(unsigned long long), s));
     MC_ACUDA(cudaMemsetAsync(mdf->bnd, 0, 5 * sizeof(unsigned), s));
   }
-  int cur = 0;   // adjG[cur] holds the adjoint of the populations after the step being reversed
   const int64_t t0 = w->tape_t0;
-  for (int k = n_ck - 1; k >= 0; --k) {
+  auto buf_of = [&](int k) { return overlap ? (k & 1) : 0; };
+  // segment k's forward, keeping every step's state and intermediates in
+  // its buffer (the unfused stages: the same step bitwise, with rho_bar and
+  // u in memory), on stream rs
+  auto rerun = [&](int k) -> mc_status {
     const int steps = std::min(K, n - k * K);
     const int64_t tk = t0 + (int64_t)k * K;
-    if (!stored) {
-      mc_status st = load_state(h, (int)(tk & 1), tape + (size_t)k * sl.bytes, sl, s);
-      if (st != MC_OK) return st;
-      mc::launch_set_counter(h, tk, s);
-      st = save_state(h, (int)(tk & 1), seg, sl, s);   // the segment's first state
-      if (st != MC_OK) return st;
-    }
-    // the segment's forward, keeping every step's state and intermediates
-    // (the unfused stages: the same step bitwise, with rho_bar and u in
-    // memory); a stored rollout has them all already
-    for (int q = 0; q < steps && !stored; ++q) {
+    const int b = buf_of(k);
+    mc_status st = load_state(h, (int)(tk & 1), tape + (size_t)k * sl.bytes, sl, rs);
+    if (st != MC_OK) return st;
+    mc::launch_set_counter(h, tk, rs);
+    st = save_state(h, (int)(tk & 1), seg[b], sl, rs);   // the segment's first state
+    if (st != MC_OK) return st;
+    for (int q = 0; q < steps; ++q) {
       if (mdf) {
-        mc_status st = mdf_recorded_step(w, seg, ss, q, steps, tk, s);
+        st = mdf_recorded_step(w, seg[b], ss, q, steps, tk, rs);
         if (st != MC_OK) return st;
       } else {
-        // the step's fields go straight into its record (bind_step)
-        run_recorded_step(step_plan(q, (int)((tk + q) & 1), false), s);
+        run_recorded_step(step_plan(b, q, (int)((tk + q) & 1), false), rs);   // fields straight into the record
       }
     }
     MC_ACUDA(cudaGetLastError());
+    return MC_OK;
+  };
+  int cur = 0;   // adjG[cur] holds the adjoint of the populations after the step being reversed
+  // segment k's steps reversed from its buffer, on stream s
+  auto reverse = [&](int k) -> mc_status {
+    const int steps = std::min(K, n - k * K);
+    const int64_t tk = t0 + (int64_t)k * K;
+    const int b = buf_of(k);
     for (int q = steps - 1; q >= 0; --q) {
       const int64_t tn = tk + q;
       const int par = (int)(tn & 1);
-      const char* rec = seg + (size_t)q * ss.bytes;
+      const char* rec = seg[b] + (size_t)q * ss.bytes;
       a.adjG_next = adjG[cur];
       a.adjG_cur = adjG[cur ^ 1];
       a.theta_n = reinterpret_cast<const float*>(rec + ss.st.theta);
@@ -537,13 +569,45 @@ mc_status sweep(mc_world* w, mc::AdjDev a, const mc::AdjMdf* mdf, float* const a
         mc::launch_adj_step(w->plan, h, a, &m, par, s);
       } else {
         mc::AdjDev ab = a;
-        ab.setup = 1;   // counter and bound slots (the fields are read from the record in place)
+        ab.setup = 1;   // the step's counter and bound slots (fields are read from the record in place)
         ab.t_step = (long long)tn;
-        mc::launch_adj_step(step_plan(q, par, true), h, ab, nullptr, par, s);
+        mc::launch_adj_step(step_plan(b, q, par, true), h, ab, nullptr, par, s);
       }
       cur ^= 1;
     }
     MC_ACUDA(cudaGetLastError());
+    return MC_OK;
+  };
+  if (!overlap) {
+    for (int k = n_ck - 1; k >= 0; --k) {
+      if (!stored) {
+        mc_status st = rerun(k);
+        if (st != MC_OK) return st;
+      }
+      mc_status st = reverse(k);
+      if (st != MC_OK) return st;
+    }
+  } else {
+    MC_ACUDA(cudaEventRecord(sy.fork, s));
+    MC_ACUDA(cudaStreamWaitEvent(rs, sy.fork, 0));
+    mc_status st = rerun(n_ck - 1);
+    if (st != MC_OK) return st;
+    MC_ACUDA(cudaEventRecord(sy.rerun[buf_of(n_ck - 1)], rs));
+    for (int k = n_ck - 1; k >= 0; --k) {
+      if (k >= 1) {
+        // segment k - 1 goes into the buffer segment k + 1 was reversed from
+        if (k + 1 <= n_ck - 1) MC_ACUDA(cudaStreamWaitEvent(rs, sy.reversed[buf_of(k + 1)], 0));
+        st = rerun(k - 1);
+        if (st != MC_OK) return st;
+        MC_ACUDA(cudaEventRecord(sy.rerun[buf_of(k - 1)], rs));
+      }
+      MC_ACUDA(cudaStreamWaitEvent(s, sy.rerun[buf_of(k)], 0));
+      st = reverse(k);
+      if (st != MC_OK) return st;
+      MC_ACUDA(cudaEventRecord(sy.reversed[buf_of(k)], s));
+    }
+    MC_ACUDA(cudaEventRecord(sy.join, rs));
+    MC_ACUDA(cudaStreamWaitEvent(s, sy.join, 0));
   }
   mc::launch_adj_gk_reduce(a, h.n_fil, s);
   // back to the final state of the rollout
@@ -613,8 +677,12 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
   const size_t o_must = take(df ? h.N * sizeof(float2) : 0);
   const size_t o_mbnd = take(df ? 8 * sizeof(unsigned) : 0);
   const bool stored = w->tape_stored;
-  const size_t o_bind = take(df ? 0 : 4 * (size_t)K * sizeof(mc::WorldDev));
-  const size_t o_seg = take(stored ? 0 : (size_t)K * step_slot(h).bytes);
+  // penalty worlds recorded with checkpoints re-run a segment while the
+  // next one is reversed: two segment buffers
+  const bool overlap = !df && !stored;
+  const int n_buf = overlap ? 2 : 1;
+  const size_t o_bind = take(df ? 0 : 4 * (size_t)n_buf * K * sizeof(mc::WorldDev));
+  const size_t o_seg = take(stored ? 0 : (size_t)n_buf * K * step_slot(h).bytes);
   if (w->adj_bytes < off) {
     if (w->adj) cudaFreeAsync(w->adj, w->stream);
     w->adj = nullptr;
@@ -625,7 +693,8 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
   }
   char* A = static_cast<char*>(w->adj);
   char* tape = static_cast<char*>(w->tape);
-  char* seg = stored ? tape + stored_layout(h, n).steps : A + o_seg;
+  char* seg[2] = {stored ? tape + stored_layout(h, n).steps : A + o_seg, nullptr};
+  if (overlap) seg[1] = A + o_seg + (size_t)K * step_slot(h).bytes;
   mc::AdjDev a{};
   a.adjX = reinterpret_cast<float2*>(A + o_adjX);
   a.adjTh = reinterpret_cast<float*>(A + o_adjTh);
@@ -676,19 +745,32 @@ mc_status backward(mc_world* w, const float* dL_dx, const float* dL_dy, float* d
     mc::WorldDev* bind_d = reinterpret_cast<mc::WorldDev*>(A + o_bind);
     if (!df) {
       const StepSlot ssl = step_slot(h);
-      bind_h.resize(4 * (size_t)K);
-      for (int rv = 0; rv < 2; ++rv)
-        for (int par = 0; par < 2; ++par)
-          for (int q = 0; q < K; ++q) bind_h[bind_index(K, q, par, rv)] = bind_step(h, seg, ssl, K, q, par, rv);
+      bind_h.resize(4 * (size_t)n_buf * K);
+      for (int b = 0; b < n_buf; ++b)
+        for (int rv = 0; rv < 2; ++rv)
+          for (int par = 0; par < 2; ++par)
+            for (int q = 0; q < K; ++q)
+              bind_h[bind_index(K, b, q, par, rv)] = bind_step(h, seg[b], ssl, K, q, par, rv);
       MC_ACUDA(cudaMemcpyAsync(bind_d, bind_h.data(), bind_h.size() * sizeof(mc::WorldDev), cudaMemcpyHostToDevice, s));
       MC_ACUDA(cudaStreamSynchronize(s));
     }
     cudaStream_t cs = adj_capture_stream();
+    SweepSync sy;
+    if (overlap) {
+      sy.s2 = adj_rerun_stream();
+      for (cudaEvent_t* e : {&sy.fork, &sy.join, &sy.rerun[0], &sy.rerun[1], &sy.reversed[0], &sy.reversed[1]})
+        MC_ACUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    }
+    auto drop_events = [&]() {
+      for (cudaEvent_t e : {sy.fork, sy.join, sy.rerun[0], sy.rerun[1], sy.reversed[0], sy.reversed[1]})
+        if (e) cudaEventDestroy(e);
+    };
     MC_ACUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     const mc_status st =
-        sweep(w, a, df ? &m : nullptr, adjG, A + o_obs, seg, sl, n_ck, bind_h.data(), bind_d, stored, cs);
+        sweep(w, a, df ? &m : nullptr, adjG, A + o_obs, seg, sl, n_ck, bind_h.data(), bind_d, stored, sy, cs);
     cudaGraph_t g = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+    drop_events();
     if (st != MC_OK) {
       if (g) cudaGraphDestroy(g);
       return st;

@@ -123,8 +123,8 @@ struct AdjDev {
   int par;                 // parity of the step being reversed (the slot of amax its u_bar reads)
   const float4* xt;        // [N] direct forcing: the positions the PBD started from (X~); NULL: X^n
   float2* xtb;             // [N] direct forcing: the PBD's adjoint of X~ through its edge vectors
-  long long t_step;        // the reversed step's counter value (set by k_adj_spread_u when setup != 0)
-  int setup;               // 1: k_adj_spread_u sets the counter and clears this step's bound slots
+  long long t_step;        // the reversed step's counter value (read instead of the world's when setup != 0)
+  int setup;               // 1: k_adj_spread_u clears this step's bound slots, k_adj_pbd reads t_step
 };
 
 // Reverse-mode buffers of a direct-forcing step (k_adj_mdf.cu): the step's
