@@ -87,7 +87,7 @@ STEP_BYTES_PER_BEAD = 32
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the dominant
 # kernel, from an ncu capture of the workload, keyed by the fingerprint of the
 # sources the kernel is built from (reported only while they are unchanged)
-KERNEL_TRAFFIC = {("c3_22", "fedfaa01f77601ff"): 1627616128}
+KERNEL_TRAFFIC = {("c3_22", "4625ff6c212d33be"): 1626334592}
 KERNEL_SOURCES = ["steric_dev.cuh", "k_steric.cu", "mc_internal.cuh"]
 
 
